@@ -1,0 +1,164 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the smoke check.
+
+This module holds the *data model* only (Sec. 1, Eq. (eq:mod_cont): a true signal
+blurred by a shift-invariant PSF, plus Gaussian noise).  It contains none of the
+method's arithmetic: no boundary condition, no transform, no eigenvalue, no
+Tikhonov filter and no GCV.  Both the CUDA path and the FP64 oracle receive the
+arrays produced here as plain inputs.
+
+Data model (stated once, used everywhere):
+  * The true object lives on an *extended* grid: the field of view (n samples per
+    axis) plus m samples on each side, m = PSF half-width.
+  * The observation is the valid part of the discrete convolution
+    g_i = sum_j h_j f_{i-j}, i in the field of view -- the rectangle-rule
+    discretisation of Eq. (eq:mod_cont).  It is *not* generated with any of the
+    boundary models under test, so every model has a genuine boundary error.
+  * Noise: e ~ N(0, I), rescaled so that ||e|| = eta * ||g_clean||.
+
+Workload recipes (sizes and distributions of the paper's experiments; the
+paper's own signals and images exist only as figures, so these stand in):
+  * ``signal_1d``  -- piecewise quadratic with 3 random breakpoints plus
+    sin(2*pi*x*U[1,4]), the 1D experiments of Sec. 5.
+  * ``image_2d``   -- 20 random polynomials of degree <= 2 on random rectangles
+    plus a linear ramp, the image experiments of Sec. 6.1.
+  * ``gaussian_psf_1d``, ``gaussian_psf_2d_separable``,
+    ``gaussian_psf_2d_rotated`` -- Gaussian blurs (symmetric and nonsymmetric).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "gaussian_psf_1d",
+    "gaussian_psf_2d_separable",
+    "gaussian_psf_2d_rotated",
+    "signal_1d",
+    "image_2d",
+    "blur_valid_1d",
+    "blur_valid_2d",
+    "add_noise",
+    "mu_grid",
+    "problem_1d",
+    "problem_2d",
+]
+
+
+def gaussian_psf_1d(sigma: float, taps: int) -> np.ndarray:
+    """Symmetric Gaussian mask h_{-m..m} (taps = 2m+1), normalised to sum 1."""
+    if taps % 2 != 1:
+        raise ValueError("PSF length must be odd")
+    m = taps // 2
+    j = np.arange(-m, m + 1, dtype=np.float64)
+    h = np.exp(-0.5 * (j / sigma) ** 2)
+    return h / h.sum()
+
+
+def gaussian_psf_2d_separable(sigma: float, taps: int) -> np.ndarray:
+    """Outer product of two identical symmetric 1D Gaussians (sum 1)."""
+    h = gaussian_psf_1d(sigma, taps)
+    return np.outer(h, h)
+
+
+def gaussian_psf_2d_rotated(sigma_x: float, sigma_y: float, angle_deg: float,
+                            taps: int, offset_col: float = 0.0,
+                            offset_row: float = 0.0) -> np.ndarray:
+    """Anisotropic Gaussian, rotated, with its centre shifted: a nonsymmetric PSF.
+
+    Array index [r, c] holds h_{r-m, c-m}; rows are the first image axis.
+    """
+    if taps % 2 != 1:
+        raise ValueError("PSF size must be odd")
+    m = taps // 2
+    r, c = np.meshgrid(np.arange(-m, m + 1, dtype=np.float64),
+                       np.arange(-m, m + 1, dtype=np.float64), indexing="ij")
+    x = c - offset_col
+    y = r - offset_row
+    th = np.deg2rad(angle_deg)
+    xr = np.cos(th) * x + np.sin(th) * y
+    yr = -np.sin(th) * x + np.cos(th) * y
+    h = np.exp(-0.5 * ((xr / sigma_x) ** 2 + (yr / sigma_y) ** 2))
+    return h / h.sum()
+
+
+def signal_1d(rng: np.random.Generator, length: int) -> np.ndarray:
+    """Piecewise quadratic (3 random breakpoints) plus sin(2*pi*x*U[1,4]) on x in [0,1]."""
+    x = np.linspace(0.0, 1.0, length)
+    brk = np.sort(rng.uniform(0.1, 0.9, size=3))
+    edges = np.concatenate([[-np.inf], brk, [np.inf]])
+    f = np.zeros(length)
+    for a, b in zip(edges[:-1], edges[1:]):
+        c0, c1, c2 = rng.uniform(-1.0, 1.0, size=3)
+        sel = (x >= a) & (x < b)
+        f[sel] = c0 + c1 * x[sel] + c2 * x[sel] ** 2
+    f += np.sin(2.0 * np.pi * x * rng.uniform(1.0, 4.0))
+    return f
+
+
+def image_2d(rng: np.random.Generator, rows: int, cols: int,
+             pieces: int = 20) -> np.ndarray:
+    """Sum of ``pieces`` random degree-<=2 polynomials on random rectangles plus a ramp."""
+    y, x = np.meshgrid(np.linspace(0.0, 1.0, rows), np.linspace(0.0, 1.0, cols),
+                       indexing="ij")
+    a, b, c = rng.uniform(-1.0, 1.0, size=3)
+    f = a + b * x + c * y
+    for _ in range(pieces):
+        r0, r1 = np.sort(rng.integers(0, rows, size=2))
+        c0, c1 = np.sort(rng.integers(0, cols, size=2))
+        r1 = max(r1, r0 + 1)
+        c1 = max(c1, c0 + 1)
+        k = rng.uniform(-1.0, 1.0, size=6)
+        xs, ys = x[r0:r1, c0:c1], y[r0:r1, c0:c1]
+        f[r0:r1, c0:c1] += (k[0] + k[1] * xs + k[2] * ys + k[3] * xs * xs
+                            + k[4] * xs * ys + k[5] * ys * ys)
+    return f
+
+
+def blur_valid_1d(f_ext: np.ndarray, h: np.ndarray) -> np.ndarray:
+    """g_i = sum_j h_j f_{i-j} over the field of view (len(f_ext) - 2m samples)."""
+    return np.convolve(f_ext, h, mode="valid")
+
+
+def blur_valid_2d(f_ext: np.ndarray, h: np.ndarray) -> np.ndarray:
+    """2D analogue of :func:`blur_valid_1d` (true convolution, valid part)."""
+    from scipy.signal import fftconvolve
+    return fftconvolve(f_ext, h, mode="valid")
+
+
+def add_noise(rng: np.random.Generator, g: np.ndarray, eta: float) -> np.ndarray:
+    """g + e with e Gaussian and ||e|| = eta * ||g||."""
+    e = rng.standard_normal(g.shape)
+    return g + eta * np.linalg.norm(g) / np.linalg.norm(e) * e
+
+
+def mu_grid(k: int, lo: float = 1e-8, hi: float = 1.0) -> np.ndarray:
+    """k log-spaced regularisation parameters, endpoints included."""
+    if k == 1:
+        return np.array([lo], dtype=np.float64)
+    return 10.0 ** np.linspace(np.log10(lo), np.log10(hi), k)
+
+
+def problem_1d(seed: int, n: int, h: np.ndarray, eta: float, count: int = 1):
+    """``count`` seeded 1D problems: returns (g[count, n], f_true[count, n])."""
+    rng = np.random.default_rng(seed)
+    m = len(h) // 2
+    g = np.empty((count, n))
+    ft = np.empty((count, n))
+    for i in range(count):
+        f_ext = signal_1d(rng, n + 2 * m)
+        g[i] = add_noise(rng, blur_valid_1d(f_ext, h), eta)
+        ft[i] = f_ext[m:m + n]
+    return g, ft
+
+
+def problem_2d(seed: int, rows: int, cols: int, h: np.ndarray, eta: float,
+               count: int = 1):
+    """``count`` seeded 2D problems: returns (g[count, rows, cols], f_true[...])."""
+    rng = np.random.default_rng(seed)
+    m0, m1 = h.shape[0] // 2, h.shape[1] // 2
+    g = np.empty((count, rows, cols))
+    ft = np.empty((count, rows, cols))
+    for i in range(count):
+        f_ext = image_2d(rng, rows + 2 * m0, cols + 2 * m1)
+        g[i] = add_noise(rng, blur_valid_2d(f_ext, h), eta)
+        ft[i] = f_ext[m0:m0 + rows, m1:m1 + cols]
+    return g, ft
