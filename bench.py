@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Throughput of spectral Tikhonov deblurring with high-order boundary conditions
+and GCV (Donatelli, arXiv:0906.2704) on 1024 x 1024 images.
+
+Workload (the 1024^2 configuration): 2D images 1024 x 1024, nonsymmetric PSF
+21 x 21 (anisotropic Gaussian sigma_x = 3, sigma_y = 1.5, rotated 30 degrees,
+centre offset (+2 col, -1 row), sum 1), degree-2 boundary condition (Fourier
+family T_F), L = I, GCV over 256 log-spaced mu in [1e-8, 1], 0.5% noise,
+seeded synthetic images.  One step = one deblur call on a batch of images
+(eigenvalues, analysis transform, GCV scan + argmin, filter + synthesis).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank deblurs its own batch (independent problems,
+no collective in the data path); the timed region is bracketed by a barrier
+and a device synchronisation, and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1024² deblurs/s: GCV scan vs learned-μ, equal rel. error; % HBM roofline"
+N_SIDE = 1024
+K_MU = 256
+ETA = 0.005
+WORKLOAD = ("2D 1024x1024, nonsymmetric 21x21 rotated anisotropic Gaussian PSF, degree-2 BC "
+            "(Fourier family), L=I, GCV over 256 mu in [1e-8,1], 0.5% noise")
+
+
+def psf():
+    from paper_0906_2704_gb300 import synth
+    return synth.gaussian_psf_2d_rotated(3.0, 1.5, 30.0, 21, 2.0, -1.0)
+
+
+def make_inputs(batch: int, seed: int, distinct: int = 4):
+    """``batch`` noisy observations built from ``distinct`` seeded clean images."""
+    from paper_0906_2704_gb300 import synth
+    h = psf()
+    clean, truth = synth.problem_2d(seed, N_SIDE, N_SIDE, h, 0.0, count=min(batch, distinct))
+    rng = np.random.default_rng(seed + 1)
+    g = np.empty((batch, N_SIDE, N_SIDE))
+    ft = np.empty_like(g)
+    for i in range(batch):
+        g[i] = synth.add_noise(rng, clean[i % len(clean)], ETA)
+        ft[i] = truth[i % len(clean)]
+    return h, g, ft
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as fh:
+                for line in fh:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def blas_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return max(n)
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def oracle_seconds_per_image(h, g, mus, count: int):
+    """The FP64 oracle (separable dense mode) on ``count`` images; seconds per image."""
+    from oracle import hobc_oracle as O
+    t0 = time.perf_counter()
+    for i in range(count):
+        O.deblur_2d("F", h, g[i], "I", mus)
+    return (time.perf_counter() - t0) / count
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, as it stands, one image per step."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_0906_2704_gb300 import synth
+    h, g, _ = make_inputs(2, seed=11, distinct=2)
+    mus = synth.mu_grid(K_MU)
+    for i in range(args.warmup):
+        oracle_seconds_per_image(h, g[i % 2:i % 2 + 1], mus, 1)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle_seconds_per_image(h, g[i % 2:i % 2 + 1], mus, 1)
+    el = time.perf_counter() - t0
+    value = args.steps / el
+    cores = blas_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "deblurs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch_per_step": 1},
+        "cpu_baseline": {"value": value, "unit": "deblurs/s", "cores": cores, "kind": "oracle",
+                         "sample": "one 1024x1024 image per step (dense FP64 oracle, separable mode)"},
+        "e2e": {"value": value, "unit": "deblurs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_0906_2704_gb300 import hobc, synth
+
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    B = args.batch
+    prec = args.prec
+    npdt = np.float32 if prec == "fp32" else np.float64
+    tdt = torch.float32 if prec == "fp32" else torch.float64
+    h, g, ft = make_inputs(B, seed=100 + rank)
+    mus = synth.mu_grid(K_MU)
+    stream = torch.cuda.current_stream()
+    plan = hobc.Plan(2, (N_SIDE, N_SIDE), h.shape, 2, mus, L="I", prec=prec, family="fourier", batch=B,
+                     stream=stream)
+    g_d = torch.from_numpy(g.astype(npdt)).to(dev)
+    h_d = torch.from_numpy(h.astype(npdt)).to(dev)
+    f_d = torch.empty_like(g_d)
+    mi_d = torch.empty(B, dtype=torch.int32, device=dev)
+
+    def step():
+        plan.deblur(g_d, h_d, f_d, mi_d, None)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    launches_per_step = plan.last_launch_count
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * B * args.steps / (ms / 1e3)
+    clocks = clk.summary()
+
+    # per-step breakdown through the step entry points (same kernels)
+    S = plan.spec_elems
+    ghat = torch.empty((B, S, 2), dtype=tdt, device=dev)
+    dbuf = torch.empty((1, S, 2), dtype=tdt, device=dev)
+    G_d = torch.empty((B, K_MU), dtype=torch.float64, device=dev)
+    steps_ms = {}
+    calls = {
+        "eigenvalues": lambda: plan.eigenvalues(h_d, dbuf),
+        "analysis": lambda: plan.analysis(g_d, ghat),
+        "gcv": lambda: plan.gcv(ghat, dbuf, G_d, mi_d),
+        "filter_synthesis": lambda: plan.filter_synthesis(ghat, dbuf, mi_d, f_d),
+    }
+    for name, fn in calls.items():
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        steps_ms[name] = a.elapsed_time(b) / args.steps
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    g_h = torch.from_numpy(g.astype(npdt)).pin_memory().numpy()
+    h_h = np.ascontiguousarray(h.astype(npdt))
+    f_h = torch.empty(g.shape, dtype=tdt).pin_memory().numpy()
+    mi_h = np.empty(B, dtype=np.int32)
+    plan.deblur_host(g_h, h_h, f_h, mi_h)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.deblur_host(g_h, h_h, f_h, mi_h)
+    barrier()
+    el = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([el], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    esz = np.dtype(npdt).itemsize
+    e2e = {"value": world * B * args.steps / el, "unit": "deblurs/s",
+           "h2d_bytes_per_step": B * N_SIDE * N_SIDE * esz + h.size * esz,
+           "d2h_bytes_per_step": B * N_SIDE * N_SIDE * esz + B * 4}
+
+    # roofline of the dominant kernel (the GCV scan): evaluations of
+    # sigma = 1/(a + mu) per launch over the time of the gcv call
+    peaks, peak_kind = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    evals = B * S * K_MU
+    gcv_s = steps_ms["gcv"] / 1e3
+    achieved = evals / gcv_s / 1e9
+    peak = 152 * 16 * sm_max * 1e6 / 1e9      # one MUFU reciprocal per evaluation, 16/clk/SM
+    roofline = {"bound": "alu", "kernel": "k_gcv_partials", "achieved": achieved, "peak": peak,
+                "unit": "Geval/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"152 SMs x 16 MUFU/clk x {sm_max:.0f} MHz ({peak_kind} clock)"}
+    hbm_bytes = B * N_SIDE * N_SIDE * esz * 2 + h.size * esz
+    hbm = {"algorithmic_bytes_per_step": hbm_bytes,
+           "achieved_gbs": hbm_bytes / (ms / args.steps / 1e3) / 1e9,
+           "peak_gbs": peaks.get("hbm_gbs"), "frac": hbm_bytes / (ms / args.steps / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n_img = 3
+        sec = oracle_seconds_per_image(h, g, mus, n_img)
+        cpu = {"value": 1.0 / sec, "unit": "deblurs/s", "cores": blas_threads(), "kind": "oracle",
+               "sample": f"{n_img} images of the same workload, dense FP64 oracle (separable mode)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "deblurs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch_per_gpu": B, "n": N_SIDE, "n_mu": K_MU,
+                       "l2": "inputs+outputs %.0f MB per step > 129 MB L2 (no flush)" % (2 * B * N_SIDE ** 2 * esz / 1e6)},
+            "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
+            "hbm_roofline": hbm, "steps_ms": steps_ms, "cpu_baseline": cpu, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    plan.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,176 @@
+/*
+ * hobc.h -- C ABI of the GB300 library for spectral Tikhonov deblurring under
+ * high-order (polynomial-preserving) boundary conditions, with the
+ * regularisation parameter chosen by generalized cross validation (GCV).
+ *
+ * Method: M. Donatelli, "Fast transforms for high order boundary conditions"
+ * (arXiv:0906.2704).  Section and equation references below use the paper's
+ * equation labels, e.g. Eq. (eq:Tc).
+ *
+ * Problem statement (Sec. 1, Eq. (eq:mod_cont); Sec. 4, Eq. (eq:mintik)):
+ *   observed signal or image g (n or n0 x n1 samples), PSF mask h of odd size
+ *   centred on its middle entry (g_i = sum_j h_j f_{i-j}), boundary condition of
+ *   polynomial degree 1 or 2, smoothing operator L (identity or Laplacian) and a
+ *   grid of regularisation parameters mu_0..mu_{K-1} > 0.  The library returns
+ *   f_reg = T_X Phi D^{-1} T_X^{-1} g at mu* = argmin_j G(mu_j)
+ *   (Eq. (eq:freg), (eq:mugcv)), the index of mu*, and optionally G(mu_j).
+ *
+ * Conventions shared by every call:
+ *   - All device pointers are caller-owned CUDA device memory on the plan's
+ *     device; host pointers are caller-owned host memory (pinned memory gives
+ *     asynchronous copies).  The library never frees a caller buffer.
+ *   - Real arrays are row-major, element type double (HOBC_FP64) or float
+ *     (HOBC_FP32).  A batch of `batch` problems is stored back to back.
+ *   - Every call is asynchronous on the plan's stream unless stated otherwise;
+ *     errors are returned as hobc_status and never thrown across the ABI.
+ *   - The plan owns its workspace (allocated once in hobc_plan_create) and its
+ *     tables; one plan must not be used from two host threads at once.
+ *
+ * Spectrum layout (the output of hobc_analysis, the input of hobc_synthesis,
+ * and the layout of hobc_eigenvalues):  spectral index t of one axis is column
+ * t of T_X on that axis: t = 0 is the left border vector (p or q), t = 1..n-2
+ * the trigonometric columns in the natural order of the transform, t = n-1 the
+ * right border vector.
+ *   Families SINE and COSINE keep real spectra: one item is n values (1D) or
+ *   n1 x n0 values stored as [t1][t0] (2D, t0 fastest).
+ *   Family FOURIER stores complex values (re, im interleaved) and, because g is
+ *   real, only the half of axis 1 that determines the rest:
+ *   W = floor((n-2)/2) + 3 entries, index c = 0 -> t = 0, c = 1..W-2 -> t = c
+ *   (frequencies 0..floor((n-2)/2)), c = W-1 -> t = n-1.  One item is W values
+ *   (1D) or W1 x n0 values stored as [c][t0] (2D).  hobc_spectrum_size reports
+ *   the per-item element counts.
+ */
+#ifndef HOBC_H
+#define HOBC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HOBC_OK = 0,
+    HOBC_ERR_ARG = 1,          /* null pointer, bad enum, bad size, mu <= 0            */
+    HOBC_ERR_UNSUPPORTED = 2,  /* combination the paper gives no fast algorithm for    */
+    HOBC_ERR_SIZE = 3,         /* PSF too large for the field of view, n out of range  */
+    HOBC_ERR_NONFINITE = 4,    /* non-finite value in the mu grid                      */
+    HOBC_ERR_CUDA = 5,         /* a CUDA runtime call failed; see hobc_last_error      */
+    HOBC_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up                   */
+} hobc_status;
+
+typedef enum {
+    HOBC_FAMILY_AUTO = 0,      /* degree 1 -> SINE; degree 2 -> COSINE if the desc says
+                                  the PSF is symmetric, else FOURIER                     */
+    HOBC_FAMILY_SINE = 1,      /* antireflective, Sec. 2.2, Eq. (eq:ART), (eq:jcf)       */
+    HOBC_FAMILY_COSINE = 2,    /* degree 2, symmetric PSF, Sec. 3.1, Eq. (eq:Tc), (eq:Ac) */
+    HOBC_FAMILY_FOURIER = 3    /* degree 2, any PSF, Sec. 3.2, Eq. (eq:Tf), (eq:Af)      */
+} hobc_family;
+
+typedef enum {
+    HOBC_L_IDENTITY = 0,       /* L = I                                                   */
+    HOBC_L_LAPLACIAN = 1       /* L_X = T_X diag(2 - 2cos theta) T_X^{-1} (Sec. 4, Eq. (eq:L));
+                                  2D: Kronecker sum, eigenvalue s(t0) + s(t1)             */
+} hobc_smoothing;
+
+typedef enum {
+    HOBC_FP64 = 0,             /* all arithmetic and I/O in double                        */
+    HOBC_FP32 = 1              /* transforms, filter and GCV terms in float; boundary 2x2
+                                  solve, eigenvalues and GCV sums in double; float I/O     */
+} hobc_precision;
+
+typedef struct {
+    int ndim;                  /* 1 (signals) or 2 (images)                               */
+    int n[2];                  /* field of view: 1D n[0]; 2D n[0] rows x n[1] columns;
+                                  each in [6, 2048]                                        */
+    int psf[2];                /* PSF mask size (odd): 1D psf[0] = 2m+1; 2D rows x cols;
+                                  needs psf[i] <= n[i] - 2 (Sec. 2.2, Sec. 3)             */
+    int bc_degree;             /* 1 or 2                                                   */
+    hobc_family family;
+    int psf_symmetric;         /* caller asserts h_{-j} = h_j on every axis (used by AUTO) */
+    hobc_smoothing L;
+    hobc_precision prec;
+    int n_mu;                  /* K >= 1 grid points                                       */
+    int batch;                 /* problems per call, >= 1                                  */
+    int psf_per_item;          /* 0: one PSF for the whole batch; 1: one PSF per problem   */
+} hobc_plan_desc;
+
+typedef struct hobc_plan_s hobc_plan;
+
+/* Create a plan.  desc: problem description (copied).  mu_grid_host: K positive
+ * finite doubles (copied).  cuda_stream: a cudaStream_t on the current device,
+ * or NULL for the legacy default stream.  Allocates the plan's device workspace
+ * and tables (cudaMalloc); synchronous.  On error *out is set to NULL. */
+hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_host,
+                             void* cuda_stream, hobc_plan** out);
+
+/* Release the plan and its device memory (synchronises the plan's stream). */
+void hobc_plan_destroy(hobc_plan* plan);
+
+/* The resolved family (HOBC_FAMILY_SINE/COSINE/FOURIER) of a plan. */
+hobc_family hobc_plan_family(const hobc_plan* plan);
+
+/* Per-item element counts: *spec = values in one item's spectrum (complex
+ * values counted once), *spec_is_complex = 1 for FOURIER, *psf = values in one
+ * PSF.  Any output pointer may be NULL. */
+hobc_status hobc_spectrum_size(const hobc_plan* plan, size_t* spec, int* spec_is_complex,
+                               size_t* psf);
+
+/* The whole method on `batch` problems (Sec. 4, Sec. 6):
+ *   g_dev   [batch][n...] real input; psf_dev one PSF or [batch] PSFs, row-major;
+ *   f_dev   [batch][n...] real output (may not alias g_dev);
+ *   mu_index_dev  [batch] int output: grid index of mu* (nullable);
+ *   gcv_dev [batch][K] double output: G(mu_j) of Eq. (eq:mugcv) (nullable).
+ * Ties in G take the smallest index; NaN values of G never win. */
+hobc_status hobc_deblur(hobc_plan* plan, const void* g_dev, const void* psf_dev, void* f_dev,
+                        int* mu_index_dev, double* gcv_dev);
+
+/* hobc_deblur with HOST buffers: copies g and the PSF(s) to the plan's
+ * workspace, runs the method, copies f (and mu index, G if non-NULL) back, and
+ * synchronises the plan's stream before returning. */
+hobc_status hobc_deblur_host(hobc_plan* plan, const void* g_host, const void* psf_host,
+                             void* f_host, int* mu_index_host, double* gcv_host);
+
+/* Step: analysis transform ghat = T_X^{-1} g (Thm. 1 / Eq. (eq:Tx); 2D: tensor
+ * product, Sec. 6), the boundary-polynomial correction included.
+ * g_dev [batch][n...] real; ghat_dev [batch][spectrum] in the spectrum layout. */
+hobc_status hobc_analysis(hobc_plan* plan, const void* g_dev, void* ghat_dev);
+
+/* Step: synthesis y = T_X c (Eq. (eq:ART), (eq:Tc), (eq:Tf); 2D tensor product),
+ * the polynomial add-back included.  c_dev in the spectrum layout (FOURIER:
+ * must be the half of a spectrum with the symmetry of a real image);
+ * y_dev [batch][n...] real. */
+hobc_status hobc_synthesis(hobc_plan* plan, const void* c_dev, void* y_dev);
+
+/* Step: eigenvalues d_t = z(-theta_t) of A_X (Eq. (eq:symbol), (eq:jcf),
+ * (eq:Ac), (eq:Af); 2D: the three-step rule of Sec. 6, i.e. z at the tensor
+ * grid with border indices at angle 0), in the spectrum layout, one per PSF
+ * (npsf = batch if psf_per_item else 1).  Element type: the plan's precision,
+ * complex for FOURIER. */
+hobc_status hobc_eigenvalues(hobc_plan* plan, const void* psf_dev, void* d_dev);
+
+/* Step: GCV scan (Eq. (eq:gcv2), (eq:mugcv)): for every problem and every mu_j,
+ * G = sum |sigma_i ghat_i|^2 / (sum sigma_i)^2, sigma_i = |s_i|^2/(|d_i|^2 + mu_j |s_i|^2),
+ * sums in double; then mu* = argmin.  ghat_dev as from hobc_analysis, d_dev as
+ * from hobc_eigenvalues.  gcv_dev [batch][K] (nullable), mu_index_dev [batch]. */
+hobc_status hobc_gcv(hobc_plan* plan, const void* ghat_dev, const void* d_dev,
+                     double* gcv_dev, int* mu_index_dev);
+
+/* Step: filter at mu* and synthesis, f = T_X diag(conj(d)/(|d|^2 + mu*|s|^2)) ghat
+ * (Eq. (eq:freg)).  mu_index_dev [batch] grid indices. */
+hobc_status hobc_filter_synthesis(hobc_plan* plan, const void* ghat_dev, const void* d_dev,
+                                  const int* mu_index_dev, void* f_dev);
+
+/* Number of kernel launches the last call on this plan issued. */
+int hobc_last_launch_count(const hobc_plan* plan);
+
+/* Human-readable name of a status; text of the last CUDA error seen by the
+ * library on this host thread (empty if none). */
+const char* hobc_status_str(hobc_status s);
+const char* hobc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOBC_H */

@@ -1,0 +1,451 @@
+// C ABI of the library (include/hobc.h): plan creation with the per-axis
+// tables of the high-order boundary-condition transforms, workspace, and the
+// entry points that run the hot path on the plan's stream.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "hobc_internal.h"
+#include "hobc_device.cuh"
+
+using hobc::AxisHost;
+typedef std::complex<double> cd;
+
+namespace hobc {
+
+static thread_local char g_last_error[512] = "";
+
+void set_last_error(const char* what, cudaError_t e) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------- GCV finalize
+
+__global__ void k_gcv_finalize(const double* __restrict__ partials, int nchunks, int K, double* __restrict__ gcv,
+                               int* __restrict__ mu_idx) {
+    __shared__ double sv[256];
+    __shared__ int si[256];
+    const long long item = blockIdx.x;
+    const double* p = partials + item * (long long)nchunks * 2 * K;
+    double best = INFINITY;
+    int bi = 0x7fffffff;
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        double num = 0, den = 0;
+        for (int c = 0; c < nchunks; ++c) {
+            num += p[(long long)c * 2 * K + j];
+            den += p[(long long)c * 2 * K + K + j];
+        }
+        const double G = num / (den * den);
+        if (gcv) gcv[item * K + j] = G;
+        const double key = isnan(G) ? INFINITY : G;
+        if (key < best || (key == best && j < bi)) { best = key; bi = j; }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            const double v2 = sv[threadIdx.x + s];
+            const int i2 = si[threadIdx.x + s];
+            if (v2 < sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
+                sv[threadIdx.x] = v2;
+                si[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mu_idx[item] = si[0] == 0x7fffffff ? 0 : si[0];
+}
+
+hobc_status launch_gcv_finalize(hobc_plan_s* p, double* gcv, int* mu_idx) {
+    k_gcv_finalize<<<p->desc.batch, 256, 0, p->stream>>>(p->partials, p->gcv_chunks, p->K, gcv, mu_idx);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_last_error("k_gcv_finalize", e);
+        return HOBC_ERR_CUDA;
+    }
+    ++p->launches;
+    return HOBC_OK;
+}
+
+// ------------------------------------------------------------------ tables
+
+static void fft_host(std::vector<cd>& a) {   // in-place radix-2, exp(-i ...)
+    const size_t n = a.size();
+    for (size_t i = 1, j = 0; i < n; ++i) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+        for (size_t i = 0; i < n; i += len) {
+            for (size_t k = 0; k < len / 2; ++k) {
+                const double ang = -2.0 * M_PI * (double)k / (double)len;
+                const cd w(cos(ang), sin(ang));
+                const cd u = a[i + k], v = a[i + k + len / 2] * w;
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+            }
+        }
+    }
+}
+
+// exp(-i pi a/b) with the argument reduced exactly (a may be negative).
+static cd expm_ipi(long long a, long long b) {
+    long long r = a % (2 * b);
+    if (r < 0) r += 2 * b;
+    const double ang = M_PI * (double)r / (double)b;
+    return cd(cos(ang), -sin(ang));
+}
+
+// theta/pi of spectral index t as the fraction num/den (border columns: 0).
+static void theta_frac(int fam, int n, int t, long long& num, long long& den) {
+    const int N = n - 2;
+    if (t == 0 || t == n - 1) { num = 0; den = 1; return; }
+    if (fam == hobc::FAM_S) { num = t; den = N + 1; }
+    else if (fam == hobc::FAM_C) { num = t - 1; den = N; }
+    else { num = 2 * (t - 1); den = N; }
+}
+
+// Left border column of T_X: p of Eq. (eq:ART) with unit norm (S); q on the
+// grid of Eq. (eq:points)/(eq:ints) (C) or Eq. (eq:pointn)/(eq:intn) (F).
+static std::vector<double> border_column(int fam, int n) {
+    std::vector<double> v(n);
+    for (int i = 0; i < n; ++i) {
+        if (fam == hobc::FAM_S) {
+            v[i] = 1.0 - (double)i / (double)(n - 1);
+        } else if (fam == hobc::FAM_C) {
+            const double x = (2.0 * i - 1.0) * M_PI / (2.0 * n - 4.0);
+            const double b = (2.0 * n - 3.0) * M_PI / (2.0 * n - 4.0);
+            v[i] = (b - x) * (b - x);
+        } else {
+            const double x = (i - 1.0) * 2.0 * M_PI / (n - 2.0);
+            const double b = 2.0 * M_PI;
+            v[i] = (b - x) * (b - x);
+        }
+    }
+    double nrm = 0;
+    for (double x : v) nrm += x * x;
+    nrm = sqrt(nrm);
+    for (double& x : v) x /= nrm;
+    return v;
+}
+
+template <typename T>
+static void* upload_complex(const std::vector<cd>& h, cudaError_t& err) {
+    std::vector<T> tmp(2 * h.size());
+    for (size_t i = 0; i < h.size(); ++i) { tmp[2 * i] = (T)h[i].real(); tmp[2 * i + 1] = (T)h[i].imag(); }
+    void* d = nullptr;
+    if (err == cudaSuccess) err = cudaMalloc(&d, tmp.size() * sizeof(T));
+    if (err == cudaSuccess) err = cudaMemcpy(d, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return d;
+}
+
+template <typename T>
+static void* upload_real(const std::vector<double>& h, cudaError_t& err) {
+    std::vector<T> tmp(h.begin(), h.end());
+    void* d = nullptr;
+    if (err == cudaSuccess) err = cudaMalloc(&d, tmp.size() * sizeof(T));
+    if (err == cudaSuccess) err = cudaMemcpy(d, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return d;
+}
+
+template <typename T>
+static cudaError_t build_axis(AxisHost& a, int fam, int n, int p, bool half) {
+    memset(&a, 0, sizeof(a));
+    a.fam = fam;
+    a.n = n;
+    a.N = n - 2;
+    a.p = p;
+    const int N = a.N;
+    a.L = fam == hobc::FAM_S ? 2 * (N + 1) : N;
+    if (a.L >= 8 && (a.L & (a.L - 1)) == 0) {
+        a.M = a.L;
+        a.blue = 0;
+    } else {
+        a.M = 8;
+        while (a.M < 2 * a.L - 1) a.M *= 2;
+        a.blue = 1;
+    }
+    a.log2M = 0;
+    while ((1 << a.log2M) < a.M) ++a.log2M;
+    a.tpg = a.M / 8;
+    a.H = fam == hobc::FAM_F ? N / 2 + 1 : N;
+    a.W = (fam == hobc::FAM_F && half) ? a.H + 2 : n;
+
+    cudaError_t err = cudaSuccess;
+    std::vector<cd> tw(a.M);
+    for (int k = 0; k < a.M; ++k) tw[k] = expm_ipi(2LL * k, a.M);
+    a.tw = upload_complex<T>(tw, err);
+    if (a.blue) {
+        std::vector<cd> chirp(a.L), c(a.M, cd(0, 0));
+        for (long long k = 0; k < a.L; ++k) chirp[k] = expm_ipi((k * k) % (2LL * a.L), a.L);
+        for (int m = 0; m < a.L; ++m) c[m] = std::conj(chirp[m]);
+        for (int m = 1; m < a.L; ++m) c[a.M - m] = std::conj(chirp[m]);
+        fft_host(c);
+        for (cd& x : c) x /= (double)a.M;
+        a.chirp = upload_complex<T>(chirp, err);
+        a.bhat = upload_complex<T>(c, err);
+    }
+    if (fam == hobc::FAM_C) {
+        std::vector<cd> post(N);
+        for (int k = 0; k < N; ++k) post[k] = expm_ipi(k, 2LL * N);
+        a.post = upload_complex<T>(post, err);
+    }
+    std::vector<double> q = border_column(fam, n);
+    a.q = upload_real<T>(q, err);
+    a.q1 = q[0];
+    if (fam == hobc::FAM_S) {
+        a.ka = 1.0 / q[0];
+        a.kb = 0.0;
+    } else {
+        const double al = fam == hobc::FAM_C ? q[0] - q[1] : q[0] - q[n - 2];
+        const double be = fam == hobc::FAM_C ? -q[n - 2] : -q[1];
+        const double det = al * al - be * be;
+        a.ka = al / det;
+        a.kb = -be / det;
+    }
+    a.sc = fam == hobc::FAM_F ? 1.0 / sqrt((double)N) : sqrt(2.0 / (N + 1)) / 2.0;
+    a.s0 = sqrt(1.0 / N);
+    a.s1 = sqrt(2.0 / N);
+    a.is0 = sqrt((double)N);
+    a.is1 = sqrt(N / 2.0);
+    a.invN = 1.0 / N;
+    // eigen-exponential table E[t][j] = exp(-i (j - m) theta_t), plus a unit entry
+    const int m = p / 2;
+    std::vector<double> et(2 * ((size_t)a.W * p + 1));
+    for (int ts = 0; ts < a.W; ++ts) {
+        const int t = (fam == hobc::FAM_F && half && ts == a.W - 1) ? n - 1 : ts;
+        long long num, den;
+        theta_frac(fam, n, t, num, den);
+        for (int j = 0; j < p; ++j) {
+            const cd e = expm_ipi((long long)(j - m) * num, den);
+            et[2 * ((size_t)ts * p + j)] = e.real();
+            et[2 * ((size_t)ts * p + j) + 1] = e.imag();
+        }
+    }
+    et[2 * (size_t)a.W * p] = 1.0;
+    et[2 * (size_t)a.W * p + 1] = 0.0;
+    if (err == cudaSuccess) err = cudaMalloc((void**)&a.etab, et.size() * sizeof(double));
+    if (err == cudaSuccess) err = cudaMemcpy(a.etab, et.data(), et.size() * sizeof(double), cudaMemcpyHostToDevice);
+    return err;
+}
+
+static void free_axis(AxisHost& a) {
+    cudaFree(a.tw); cudaFree(a.chirp); cudaFree(a.bhat); cudaFree(a.post); cudaFree(a.q); cudaFree(a.etab);
+    memset(&a, 0, sizeof(a));
+}
+
+}  // namespace hobc
+
+using namespace hobc;
+
+// =================================================================== ABI
+
+extern "C" {
+
+const char* hobc_status_str(hobc_status s) {
+    switch (s) {
+        case HOBC_OK: return "HOBC_OK";
+        case HOBC_ERR_ARG: return "HOBC_ERR_ARG";
+        case HOBC_ERR_UNSUPPORTED: return "HOBC_ERR_UNSUPPORTED";
+        case HOBC_ERR_SIZE: return "HOBC_ERR_SIZE";
+        case HOBC_ERR_NONFINITE: return "HOBC_ERR_NONFINITE";
+        case HOBC_ERR_CUDA: return "HOBC_ERR_CUDA";
+        case HOBC_ERR_TIMEOUT: return "HOBC_ERR_TIMEOUT";
+    }
+    return "HOBC_ERR_UNKNOWN";
+}
+
+const char* hobc_last_error(void) { return g_last_error; }
+
+void hobc_plan_destroy(hobc_plan* p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    else cudaDeviceSynchronize();
+    for (int i = 0; i < 2; ++i) free_axis(p->ax[i]);
+    cudaFree(p->mu); cudaFree(p->muT); cudaFree(p->R); cudaFree(p->G); cudaFree(p->D);
+    cudaFree(p->partials); cudaFree(p->gcv); cudaFree(p->mu_idx);
+    cudaFree(p->g_in); cudaFree(p->f_out); cudaFree(p->psf_in);
+    delete p;
+}
+
+hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_host, void* cuda_stream,
+                             hobc_plan** out) {
+    if (!out) return HOBC_ERR_ARG;
+    *out = nullptr;
+    if (!desc || !mu_grid_host) return HOBC_ERR_ARG;
+    const hobc_plan_desc d = *desc;
+    if (d.ndim != 1 && d.ndim != 2) return HOBC_ERR_ARG;
+    if (d.n_mu < 1 || d.batch < 1) return HOBC_ERR_ARG;
+    if (d.prec != HOBC_FP64 && d.prec != HOBC_FP32) return HOBC_ERR_ARG;
+    if (d.L != HOBC_L_IDENTITY && d.L != HOBC_L_LAPLACIAN) return HOBC_ERR_ARG;
+    if (d.psf_per_item != 0 && d.psf_per_item != 1) return HOBC_ERR_ARG;
+    for (int i = 0; i < d.ndim; ++i) {
+        if (d.n[i] < 6 || d.n[i] > 1024) return HOBC_ERR_SIZE;
+        if (d.psf[i] < 1 || d.psf[i] % 2 == 0 || d.psf[i] > 63) return HOBC_ERR_SIZE;
+        if (d.psf[i] > d.n[i] - 2) return HOBC_ERR_SIZE;       // 2m+1 <= n-2
+    }
+    for (int j = 0; j < d.n_mu; ++j) {
+        if (!std::isfinite(mu_grid_host[j])) return HOBC_ERR_NONFINITE;
+        if (!(mu_grid_host[j] > 0)) return HOBC_ERR_ARG;
+    }
+    int fam = d.family;
+    if (d.bc_degree != 1 && d.bc_degree != 2) return HOBC_ERR_UNSUPPORTED;
+    if (fam == HOBC_FAMILY_AUTO) {
+        if (d.bc_degree == 1) fam = d.psf_symmetric ? HOBC_FAMILY_SINE : -1;
+        else fam = d.psf_symmetric ? HOBC_FAMILY_COSINE : HOBC_FAMILY_FOURIER;
+        if (fam < 0) return HOBC_ERR_UNSUPPORTED;   // antireflective needs a symmetric PSF (Sec. 2.2)
+    }
+    if (fam == HOBC_FAMILY_SINE && d.bc_degree != 1) return HOBC_ERR_UNSUPPORTED;
+    if ((fam == HOBC_FAMILY_COSINE || fam == HOBC_FAMILY_FOURIER) && d.bc_degree != 2) return HOBC_ERR_UNSUPPORTED;
+    if (fam < HOBC_FAMILY_SINE || fam > HOBC_FAMILY_FOURIER) return HOBC_ERR_ARG;
+
+    hobc_plan_s* p = new hobc_plan_s;
+    memset(p, 0, sizeof(*p));
+    p->desc = d;
+    p->fam = fam;
+    p->prec = d.prec;
+    p->esz = d.prec == HOBC_FP64 ? 8 : 4;
+    p->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    p->K = d.n_mu;
+    p->nax = d.ndim;
+    cudaGetDevice(&p->device);
+    cudaError_t err = cudaSuccess;
+    for (int i = 0; i < d.ndim && err == cudaSuccess; ++i) {
+        const bool half = (i == d.ndim - 1);
+        err = d.prec == HOBC_FP64 ? build_axis<double>(p->ax[i], fam, d.n[i], d.psf[i], half)
+                                  : build_axis<float>(p->ax[i], fam, d.n[i], d.psf[i], half);
+    }
+    const AxisHost& last = p->ax[d.ndim - 1];
+    p->spec_elems = d.ndim == 1 ? (size_t)last.W : (size_t)last.W * p->ax[0].n;
+    const size_t ebytes = p->esz * (fam == HOBC_FAMILY_FOURIER ? 2 : 1);
+    p->spec_bytes = p->spec_elems * ebytes;
+    p->img_elems = d.ndim == 1 ? (size_t)d.n[0] : (size_t)d.n[0] * d.n[1];
+    p->psf_elems = d.ndim == 1 ? (size_t)d.psf[0] : (size_t)d.psf[0] * d.psf[1];
+    p->npsf = d.psf_per_item ? d.batch : 1;
+    p->gcv_chunk = (int)std::min<size_t>(p->spec_elems, d.prec == HOBC_FP64 ? 1024 : 2048);
+    p->gcv_chunks = (int)((p->spec_elems + p->gcv_chunk - 1) / p->gcv_chunk);
+    const size_t B = (size_t)d.batch;
+    auto alloc = [&](void** ptr, size_t bytes) {
+        if (err == cudaSuccess && bytes) err = cudaMalloc(ptr, bytes);
+    };
+    alloc((void**)&p->mu, sizeof(double) * p->K);
+    alloc(&p->muT, p->esz * p->K);
+    if (err == cudaSuccess) err = cudaMemcpy(p->mu, mu_grid_host, sizeof(double) * p->K, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) {
+        if (d.prec == HOBC_FP64) {
+            err = cudaMemcpy(p->muT, mu_grid_host, sizeof(double) * p->K, cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> mf(mu_grid_host, mu_grid_host + p->K);
+            err = cudaMemcpy(p->muT, mf.data(), sizeof(float) * p->K, cudaMemcpyHostToDevice);
+        }
+    }
+    if (d.ndim == 2) alloc(&p->R, B * p->spec_bytes);
+    alloc(&p->G, B * p->spec_bytes);
+    alloc(&p->D, (size_t)p->npsf * p->spec_bytes);
+    alloc((void**)&p->partials, B * p->gcv_chunks * 2 * p->K * sizeof(double));
+    alloc((void**)&p->gcv, B * p->K * sizeof(double));
+    alloc((void**)&p->mu_idx, B * sizeof(int));
+    alloc(&p->g_in, B * p->img_elems * p->esz);
+    alloc(&p->f_out, B * p->img_elems * p->esz);
+    alloc(&p->psf_in, (size_t)p->npsf * p->psf_elems * p->esz);
+    if (err != cudaSuccess) {
+        set_last_error("hobc_plan_create", err);
+        hobc_plan_destroy(p);
+        return HOBC_ERR_CUDA;
+    }
+    hobc_status s = d.prec == HOBC_FP64 ? prepare_kernels<double>(p) : prepare_kernels<float>(p);
+    if (s != HOBC_OK) {
+        hobc_plan_destroy(p);
+        return s;
+    }
+    *out = p;
+    return HOBC_OK;
+}
+
+hobc_family hobc_plan_family(const hobc_plan* p) { return p ? (hobc_family)p->fam : HOBC_FAMILY_AUTO; }
+
+hobc_status hobc_spectrum_size(const hobc_plan* p, size_t* spec, int* is_complex, size_t* psf) {
+    if (!p) return HOBC_ERR_ARG;
+    if (spec) *spec = p->spec_elems;
+    if (is_complex) *is_complex = p->fam == HOBC_FAMILY_FOURIER;
+    if (psf) *psf = p->psf_elems;
+    return HOBC_OK;
+}
+
+int hobc_last_launch_count(const hobc_plan* p) { return p ? p->launches : 0; }
+
+#define HOBC_DISPATCH(p, fn, ...) ((p)->prec == HOBC_FP64 ? fn<double>(p, __VA_ARGS__) : fn<float>(p, __VA_ARGS__))
+
+hobc_status hobc_eigenvalues(hobc_plan* p, const void* psf, void* D) {
+    if (!p || !psf || !D) return HOBC_ERR_ARG;
+    p->launches = 0;
+    return HOBC_DISPATCH(p, run_eig, psf, D);
+}
+
+hobc_status hobc_analysis(hobc_plan* p, const void* g, void* ghat) {
+    if (!p || !g || !ghat) return HOBC_ERR_ARG;
+    p->launches = 0;
+    return HOBC_DISPATCH(p, run_analysis, g, ghat);
+}
+
+hobc_status hobc_synthesis(hobc_plan* p, const void* c, void* y) {
+    if (!p || !c || !y) return HOBC_ERR_ARG;
+    p->launches = 0;
+    return HOBC_DISPATCH(p, run_synthesis, c, y);
+}
+
+hobc_status hobc_gcv(hobc_plan* p, const void* ghat, const void* D, double* gcv, int* mu_idx) {
+    if (!p || !ghat || !D || !mu_idx) return HOBC_ERR_ARG;
+    p->launches = 0;
+    return HOBC_DISPATCH(p, run_gcv, ghat, D, gcv, mu_idx);
+}
+
+hobc_status hobc_filter_synthesis(hobc_plan* p, const void* ghat, const void* D, const int* mu_idx, void* f) {
+    if (!p || !ghat || !D || !mu_idx || !f) return HOBC_ERR_ARG;
+    p->launches = 0;
+    return HOBC_DISPATCH(p, run_filter_synthesis, ghat, D, mu_idx, f);
+}
+
+static hobc_status deblur_impl(hobc_plan* p, const void* g, const void* psf, void* f, int* mu_idx, double* gcv) {
+    int* mi = mu_idx ? mu_idx : p->mu_idx;
+    hobc_status s = HOBC_DISPATCH(p, run_eig, psf, p->D);
+    if (s == HOBC_OK) s = HOBC_DISPATCH(p, run_analysis, g, p->G);
+    if (s == HOBC_OK) s = HOBC_DISPATCH(p, run_gcv, p->G, p->D, gcv, mi);
+    if (s == HOBC_OK) s = HOBC_DISPATCH(p, run_filter_synthesis, p->G, p->D, mi, f);
+    return s;
+}
+
+hobc_status hobc_deblur(hobc_plan* p, const void* g, const void* psf, void* f, int* mu_idx, double* gcv) {
+    if (!p || !g || !psf || !f) return HOBC_ERR_ARG;
+    if (g == f) return HOBC_ERR_ARG;
+    p->launches = 0;
+    return deblur_impl(p, g, psf, f, mu_idx, gcv);
+}
+
+hobc_status hobc_deblur_host(hobc_plan* p, const void* g, const void* psf, void* f, int* mu_idx, double* gcv) {
+    if (!p || !g || !psf || !f) return HOBC_ERR_ARG;
+    p->launches = 0;
+    const size_t B = (size_t)p->desc.batch;
+    const size_t gb = B * p->img_elems * p->esz;
+    cudaError_t e = cudaMemcpyAsync(p->g_in, g, gb, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->psf_in, psf, (size_t)p->npsf * p->psf_elems * p->esz, cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) { set_last_error("hobc_deblur_host H2D", e); return HOBC_ERR_CUDA; }
+    hobc_status s = deblur_impl(p, p->g_in, p->psf_in, p->f_out, p->mu_idx, gcv ? p->gcv : nullptr);
+    if (s != HOBC_OK) return s;
+    e = cudaMemcpyAsync(f, p->f_out, gb, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess && mu_idx)
+        e = cudaMemcpyAsync(mu_idx, p->mu_idx, B * sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess && gcv)
+        e = cudaMemcpyAsync(gcv, p->gcv, B * p->K * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) { set_last_error("hobc_deblur_host D2H", e); return HOBC_ERR_CUDA; }
+    return HOBC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,227 @@
+// Device building blocks for the line transforms of the high-order boundary
+// condition method (Donatelli, arXiv:0906.2704):
+//   * complex helpers on float2/double2;
+//   * a shared-memory Stockham FFT of power-of-two length M run by one "group"
+//     of M/8 threads (radix-8 stages, then one radix-4 or radix-2 stage), with
+//     every group of the CTA in lock-step so __syncthreads() can be used;
+//   * Bluestein's chirp-z form for lengths L that are not powers of two
+//     (X_k = b_k sum_j (x_j b_j) conj(b_{k-j}), b_k = exp(-i pi k^2 / L)), so
+//     the awkward orders N = n - 2 of the paper (1022 = 2*7*73 ...) need no
+//     special radices;
+//   * the 2x2 boundary solve that replaces the Sherman-Morrison-Woodbury step
+//     of Thm. 1 (Sec. 3.3), and the angle grids of Eq. (eq:jcf), (eq:Ac), (eq:Af).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hobc {
+
+enum { FAM_S = 1, FAM_C = 2, FAM_F = 3 };   // same values as hobc_family
+
+template <typename T> struct V2;
+template <> struct V2<float> { typedef float2 t; };
+template <> struct V2<double> { typedef double2 t; };
+template <typename T> using C2 = typename V2<T>::t;
+
+template <typename T> __device__ __forceinline__ C2<T> cmk(T x, T y) { C2<T> r; r.x = x; r.y = y; return r; }
+template <typename T> __device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) { return cmk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) { return cmk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+    return cmk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __device__ __forceinline__ C2<T> cconj(C2<T> a) { return cmk<T>(a.x, -a.y); }
+template <typename T> __device__ __forceinline__ C2<T> cscale(C2<T> a, T s) { return cmk<T>(a.x * s, a.y * s); }
+template <typename T> __device__ __forceinline__ T cabs2(C2<T> a) { return a.x * a.x + a.y * a.y; }
+
+// One transform axis: the order-n transform T_X of the paper and the tables of
+// its length-L complex DFT core.  Built on the host (hobc_api.cu), passed by value.
+template <typename T>
+struct Axis {
+    int fam;        // FAM_S / FAM_C / FAM_F
+    int n;          // field-of-view length on this axis
+    int N;          // order of the trigonometric block, n - 2
+    int L;          // length of the complex DFT core: N (C, F) or 2(N+1) (S)
+    int M;          // power-of-two FFT length (== L when L is a power of two >= 8)
+    int log2M;
+    int blue;       // 1: Bluestein (M >= 2L-1), 0: direct
+    int tpg;        // threads per group = M/8
+    int H;          // FOURIER: floor(N/2)+1 stored frequencies; else N
+    int W;          // spectrum entries stored on this axis: n (S, C) or H+2 (F)
+    const C2<T>* tw;      // [M] exp(-2 pi i k / M)
+    const C2<T>* chirp;   // [L] exp(-i pi (k^2 mod 2L) / L)
+    const C2<T>* bhat;    // [M] FFT_M(conj-chirp, wrapped) / M
+    const C2<T>* post;    // COSINE: [N] exp(-i pi k / (2N))
+    const T* q;           // [n] left border column of T_X (p for S, q for C, F)
+    double ka, kb;        // inverse of the 2x2 border system, [[ka, kb], [kb, ka]]
+    T q1;                 // q[0]
+    T sc;                 // F: 1/sqrt(N); S: sqrt(2/(N+1))/2
+    T s0, s1;             // C: DCT-II row scales sqrt(1/N), sqrt(2/N)
+    T is0, is1;           // C: their reciprocals
+    T invN;               // C: 1/N
+};
+
+// ---------------------------------------------------------------- FFT core
+
+template <typename T> __device__ __forceinline__ void dft4(C2<T>& a0, C2<T>& a1, C2<T>& a2, C2<T>& a3) {
+    const C2<T> s02 = cadd<T>(a0, a2), d02 = csub<T>(a0, a2);
+    const C2<T> s13 = cadd<T>(a1, a3), d13 = csub<T>(a1, a3);
+    const C2<T> md13 = cmk<T>(d13.y, -d13.x);          // -i * d13
+    a0 = cadd<T>(s02, s13);
+    a2 = csub<T>(s02, s13);
+    a1 = cadd<T>(d02, md13);
+    a3 = csub<T>(d02, md13);
+}
+
+template <typename T> __device__ __forceinline__ void dft8(C2<T>* v) {
+    C2<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    C2<T> o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<T>(e0, e1, e2, e3);
+    dft4<T>(o0, o1, o2, o3);
+    const T c = (T)0.70710678118654752440;
+    const C2<T> w1 = cmk<T>(c * (o1.x + o1.y), c * (o1.y - o1.x));     // exp(-i pi/4) o1
+    const C2<T> w2 = cmk<T>(o2.y, -o2.x);                             // -i o2
+    const C2<T> w3 = cmk<T>(c * (o3.y - o3.x), -c * (o3.x + o3.y));   // exp(-3i pi/4) o3
+    v[0] = cadd<T>(e0, o0); v[4] = csub<T>(e0, o0);
+    v[1] = cadd<T>(e1, w1); v[5] = csub<T>(e1, w1);
+    v[2] = cadd<T>(e2, w2); v[6] = csub<T>(e2, w2);
+    v[3] = cadd<T>(e3, w3); v[7] = csub<T>(e3, w3);
+}
+
+// One Stockham autosort stage of radix R on buf[0..M): butterfly j reads
+// buf[j + r M/R], twiddles by W_{Ns R}^{r (j mod Ns)}, does an R-point DFT, and
+// writes buf[(j - j mod Ns) R + j mod Ns + r Ns].  Each thread holds 8 values.
+template <int R, typename T>
+__device__ __forceinline__ void fft_stage(C2<T>* buf, int M, int Ns, const C2<T>* __restrict__ tw,
+                                          int t, int tpg) {
+    constexpr int PER = 8 / R;
+    const int nb = M / R;
+    C2<T> v[8];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = t + u * tpg;
+        const int k = j & (Ns - 1);
+        const int step = (M / (Ns * R)) * k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            C2<T> x = buf[j + r * nb];
+            if (r > 0 && Ns > 1) x = cmul<T>(x, tw[r * step]);
+            v[u * R + r] = x;
+        }
+        if (R == 8) dft8<T>(v + u * R);
+        else if (R == 4) dft4<T>(v[u * R], v[u * R + 1], v[u * R + 2], v[u * R + 3]);
+        else {
+            const C2<T> a = v[u * R], b = v[u * R + 1];
+            v[u * R] = cadd<T>(a, b);
+            v[u * R + 1] = csub<T>(a, b);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = t + u * tpg;
+        const int k = j & (Ns - 1);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[base + r * Ns] = v[u * R + r];
+    }
+    __syncthreads();
+}
+
+// Forward power-of-two FFT (exp(-i ...)) of buf[0..M) in place.  Every thread of
+// the CTA must call it (it synchronises the CTA); t in [0, M/8).
+template <typename T>
+__device__ __forceinline__ void group_fft(C2<T>* buf, const Axis<T>& ax, int t) {
+    int Ns = 1, rem = ax.log2M;
+    while (rem >= 3) {
+        fft_stage<8, T>(buf, ax.M, Ns, ax.tw, t, ax.tpg);
+        Ns <<= 3;
+        rem -= 3;
+    }
+    if (rem == 2) fft_stage<4, T>(buf, ax.M, Ns, ax.tw, t, ax.tpg);
+    else if (rem == 1) fft_stage<2, T>(buf, ax.M, Ns, ax.tw, t, ax.tpg);
+}
+
+// Input side of the length-L DFT: value placed at position p of the core.
+template <typename T>
+__device__ __forceinline__ C2<T> dft_in(const Axis<T>& ax, int p, C2<T> x) {
+    return ax.blue ? cmul<T>(x, ax.chirp[p]) : x;
+}
+
+// The length-L DFT of what dft_in placed in buf (positions >= L zero when
+// Bluestein is used).  Leaves buf such that dft_out(k) is output k.
+template <typename T>
+__device__ __forceinline__ void group_dft(C2<T>* buf, const Axis<T>& ax, int t) {
+    group_fft<T>(buf, ax, t);
+    if (ax.blue) {
+        // pointwise product with the transformed chirp, conjugated so the
+        // second forward FFT computes the inverse (1/M folded into bhat)
+        for (int p = t; p < ax.M; p += ax.tpg) buf[p] = cconj<T>(cmul<T>(buf[p], ax.bhat[p]));
+        __syncthreads();
+        group_fft<T>(buf, ax, t);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ C2<T> dft_out(const C2<T>* buf, const Axis<T>& ax, int k) {
+    const C2<T> z = buf[k];
+    return ax.blue ? cmul<T>(cconj<T>(z), ax.chirp[k]) : z;
+}
+
+// Position of interior sample j in the permuted sequence whose DFT gives the
+// DCT-II (even samples forward, odd samples backward).
+__device__ __forceinline__ int pos_C(int j, int N) { return (j & 1) ? (N - 1 - (j >> 1)) : (j >> 1); }
+
+// ------------------------------------------------------------- boundary
+
+// Border coefficients (c_1, c_n) of a line y = T_X c.  Writing T_X with the
+// interior block extended by continuity (Sec. 3, remark) gives, per family,
+//   S: y_1 = p_1 c_1, y_n = p_1 c_n;
+//   C: (q_1 - q_2) c_1 - q_{n-1} c_n = y_1 - y_2,  -q_{n-1} c_1 + (q_1 - q_2) c_n = y_n - y_{n-1};
+//   F: (q_1 - q_{n-1}) c_1 - q_2 c_n = y_1 - y_{n-1},  -q_2 c_1 + (q_1 - q_{n-1}) c_n = y_n - y_2;
+// a symmetric 2x2 system whose inverse [[ka, kb], [kb, ka]] is precomputed in
+// double.  This is the closed form of the Sherman-Morrison-Woodbury inverse of
+// Thm. 1 (the SMW inner products reduce to unit vectors because the border
+// rows repeat interior rows).
+template <typename T>
+__device__ __forceinline__ void border_coeffs(const Axis<T>& ax, double y0, double y1, double ym2,
+                                              double ym1, double& c1, double& cn) {
+    if (ax.fam == FAM_S) {
+        c1 = y0 * ax.ka;
+        cn = ym1 * ax.ka;
+    } else {
+        double r1, r2;
+        if (ax.fam == FAM_C) { r1 = y0 - y1; r2 = ym1 - ym2; }
+        else { r1 = y0 - ym2; r2 = ym1 - y1; }
+        c1 = ax.ka * r1 + ax.kb * r2;
+        cn = ax.kb * r1 + ax.ka * r2;
+    }
+}
+
+// --------------------------------------------------------------- angles
+
+// theta/pi of spectral index t (0..n-1) on an axis (Eq. (eq:jcf), (eq:Ac), (eq:Af)):
+// border columns have angle 0.
+template <typename T>
+__device__ __forceinline__ T theta_over_pi(int fam, int n, int N, int t) {
+    if (t == 0 || t == n - 1) return (T)0;
+    if (fam == FAM_S) return (T)t / (T)(N + 1);
+    if (fam == FAM_C) return (T)(t - 1) / (T)N;
+    return (T)(2 * (t - 1)) / (T)N;
+}
+
+// Spectral index t of stored entry c on an axis (FOURIER stores a half).
+__device__ __forceinline__ int stored_to_t(int fam, int n, int W, int c) {
+    return (fam == FAM_F && c == W - 1) ? n - 1 : c;
+}
+
+// Laplacian eigenvalue s = 2 - 2 cos(theta) = 4 sin^2(theta/2) (Sec. 4), in the
+// form without cancellation near theta = 0.
+__device__ __forceinline__ float sinpi_t(float x) { return sinpif(x); }
+__device__ __forceinline__ double sinpi_t(double x) { return sinpi(x); }
+template <typename T> __device__ __forceinline__ T lap_eig(T frac) {
+    const T sp = sinpi_t(frac * (T)0.5);
+    return (T)4 * sp * sp;
+}
+
+}  // namespace hobc

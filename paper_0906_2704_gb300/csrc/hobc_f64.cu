@@ -1,0 +1,3 @@
+// Double instantiation of the hot-path launch sequences.
+#include "hobc_run.cuh"
+HOBC_INSTANTIATE(double)

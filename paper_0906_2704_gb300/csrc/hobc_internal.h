@@ -1,0 +1,77 @@
+// Host-side plan of the library (see include/hobc.h for the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "../../include/hobc.h"
+
+namespace hobc {
+
+// One transform axis as built on the host; device tables are in the plan's
+// precision (float or double), the eigen-exponential table always in double.
+struct AxisHost {
+    int fam, n, N, L, M, log2M, blue, tpg, H, W;
+    void* tw;       // [M] complex
+    void* chirp;    // [L] complex (Bluestein only)
+    void* bhat;     // [M] complex (Bluestein only)
+    void* post;     // [N] complex (COSINE only)
+    void* q;        // [n] real
+    double ka, kb, q1, sc, s0, s1, is0, is1, invN;
+    int p;          // PSF extent on this axis
+    double2* etab;  // [W][p] exp(-i (j - m) theta_t) for the stored entries t
+};
+
+struct Launch {     // grid/block/shared memory of one line-transform kernel
+    dim3 grid, block;
+    size_t smem;
+};
+
+}  // namespace hobc
+
+struct hobc_plan_s {
+    hobc_plan_desc desc;
+    int fam;                 // resolved family
+    int prec;                // HOBC_FP64 / HOBC_FP32
+    size_t esz;              // bytes of one real element (8 or 4)
+    cudaStream_t stream;
+    int device;
+    int K;
+    double* mu;              // [K] device
+    void* muT;               // [K] device, plan precision
+    hobc::AxisHost ax[2];    // 1D: ax[0] only; 2D: ax[0] rows (axis 0), ax[1] columns (axis 1)
+    int nax;
+    size_t spec_elems;       // stored spectral entries per item
+    size_t spec_bytes;       // bytes per item (complex entries count twice)
+    size_t img_elems;        // real samples per item
+    size_t psf_elems;        // values per PSF
+    int npsf;
+    // workspace
+    void* R;                 // [batch][spec] intermediate of the 2D passes
+    void* G;                 // [batch][spec] spectrum
+    void* D;                 // [npsf][spec] eigenvalues
+    double* partials;        // [batch][chunks][2K]
+    int gcv_chunk, gcv_chunks;
+    double* gcv;             // [batch][K]
+    int* mu_idx;             // [batch]
+    void* g_in;              // [batch][img] host-call staging
+    void* f_out;             // [batch][img]
+    void* psf_in;            // [npsf][psf]
+    int launches;
+};
+
+namespace hobc {
+
+template <typename T> hobc_status run_eig(hobc_plan_s* p, const void* psf, void* D);
+template <typename T> hobc_status run_analysis(hobc_plan_s* p, const void* g, void* ghat);
+template <typename T> hobc_status run_synthesis(hobc_plan_s* p, const void* c, void* y);
+template <typename T> hobc_status run_gcv(hobc_plan_s* p, const void* ghat, const void* D, double* gcv,
+                                          int* mu_idx);
+template <typename T> hobc_status run_filter_synthesis(hobc_plan_s* p, const void* ghat, const void* D,
+                                                       const int* mu_idx, void* f);
+template <typename T> hobc_status prepare_kernels(hobc_plan_s* p);
+
+void set_last_error(const char* what, cudaError_t e);
+hobc_status launch_gcv_finalize(hobc_plan_s* p, double* gcv, int* mu_idx);
+
+}  // namespace hobc

@@ -1,0 +1,574 @@
+// Kernels of the hot path (Donatelli, arXiv:0906.2704), templated on the
+// working precision T (float / double) and the transform family:
+//   k_pair_analysis   T_X^{-1} on pairs of real lines (row passes; real column passes)
+//   k_pair_synthesis  T_X on pairs of real-valued lines, optional fused filter
+//   k_cplx_analysis   T_F^{-1} on complex lines (column pass of the Fourier family)
+//   k_cplx_synthesis  T_F on complex lines, optional fused filter
+//   k_eig             eigenvalues d = z(-theta) on the spectrum layout (FP64 sums)
+//   k_gcv_partials    per-CTA partial GCV sums for every mu of the grid
+//   k_gcv_finalize    G(mu_j) = num/den^2 and the grid argmin, per problem
+// Index conventions are those of include/hobc.h (spectrum layout).
+#pragma once
+
+#include "hobc_device.cuh"
+
+namespace hobc {
+
+template <typename T, bool CPLX> struct ElemT { typedef T t; };
+template <typename T> struct ElemT<T, true> { typedef C2<T> t; };
+
+__device__ __forceinline__ float re_of(float v) { return v; }
+__device__ __forceinline__ double re_of(double v) { return v; }
+__device__ __forceinline__ float re_of(float2 v) { return v.x; }
+__device__ __forceinline__ double re_of(double2 v) { return v.x; }
+__device__ __forceinline__ float abs2_of(float v) { return v * v; }
+__device__ __forceinline__ double abs2_of(double v) { return v * v; }
+__device__ __forceinline__ float abs2_of(float2 v) { return v.x * v.x + v.y * v.y; }
+__device__ __forceinline__ double abs2_of(double2 v) { return v.x * v.x + v.y * v.y; }
+
+// Filter factor Phi_i D_i^{-1} = conj(d_i) / (|d_i|^2 + mu |s_i|^2) (Eq. (eq:freg)) applied to v.
+__device__ __forceinline__ float apply_filter(float v, float d, float s2, float mu) {
+    return v * d / (d * d + mu * s2);
+}
+__device__ __forceinline__ double apply_filter(double v, double d, double s2, double mu) {
+    return v * d / (d * d + mu * s2);
+}
+__device__ __forceinline__ float2 apply_filter(float2 v, float2 d, float s2, float mu) {
+    const float den = d.x * d.x + d.y * d.y + mu * s2;
+    return make_float2((v.x * d.x + v.y * d.y) / den, (v.y * d.x - v.x * d.y) / den);
+}
+__device__ __forceinline__ double2 apply_filter(double2 v, double2 d, double s2, double mu) {
+    const double den = d.x * d.x + d.y * d.y + mu * s2;
+    return make_double2((v.x * d.x + v.y * d.y) / den, (v.y * d.x - v.x * d.y) / den);
+}
+
+// Where the eigenvalues, mu* and smoothing of a filtered element come from.
+struct FilterDesc {
+    const void* D;          // eigenvalues in the spectrum layout
+    long long d_psf_stride; // elements between consecutive PSFs' eigenvalues
+    int psf_per;            // 1: one PSF per problem, 0: shared
+    const int* mu_idx;      // [problems] grid index of mu*
+    const double* mu;       // [K] grid
+    int K;                  // grid size (caller indices are clamped to [0, K))
+    int lap;                // 1: Laplacian smoothing, 0: identity
+    int o_fam, o_n, o_N, o_W;   // 2D: the other axis (axis 1, indexed by line)
+};
+
+// mu* of a problem; an index outside the grid is clamped so it cannot read past it.
+__device__ __forceinline__ double mu_of(const FilterDesc& f, int problem) {
+    const int k = f.mu_idx[problem];
+    return f.mu[k < 0 ? 0 : (k >= f.K ? f.K - 1 : k)];
+}
+
+// 1D (mode 1): problem = line, D offset = psf(line) * stride + pos, s = s(pos).
+// 2D (mode 2): problem = item, D offset = psf(item) * stride + line*lrs + pos*lcs,
+//              s = s0(pos) + s1(line)  (Kronecker-sum Laplacian).
+template <typename T>
+__device__ __forceinline__ T smoothing2(const FilterDesc& f, int mode, const Axis<T>& ax, int line, int pos) {
+    if (!f.lap) return (T)1;
+    const int t = stored_to_t(ax.fam, ax.n, ax.W, pos);
+    T s = lap_eig<T>(theta_over_pi<T>(ax.fam, ax.n, ax.N, t));
+    if (mode == 2) {
+        const int t1 = stored_to_t(f.o_fam, f.o_n, f.o_W, line);
+        s += lap_eig<T>(theta_over_pi<T>(f.o_fam, f.o_n, f.o_N, t1));
+    }
+    return s * s;
+}
+
+// =====================================================================
+// Analysis T_X^{-1} on pairs of real lines.
+// Line r of item i, sample j: in[i*in_item + r*in_rs + j].
+// Output spectral entry c of line r: out[i*out_item + r*out_rs + c*out_cs]
+// (out_rs == 1 means a transposed store, staged so it stays coalesced).
+// grid = (ceil(nlines / 2G), items), block = G * ax.tpg.
+// =====================================================================
+template <typename T, int FAM>
+__global__ void __launch_bounds__(512)
+k_pair_analysis(const T* __restrict__ in, long long in_item, long long in_rs,
+                typename ElemT<T, FAM == FAM_F>::t* __restrict__ out, long long out_item,
+                long long out_rs, long long out_cs, int nlines, Axis<T> ax) {
+    typedef typename ElemT<T, FAM == FAM_F>::t E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = blockDim.x / ax.tpg;
+    const int g = threadIdx.x / ax.tpg;
+    const int t = threadIdx.x - g * ax.tpg;
+    C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.M;
+    E* stage = reinterpret_cast<E*>(reinterpret_cast<C2<T>*>(smem_raw) + (size_t)G * ax.M);
+    const int n = ax.n, N = ax.N, W = ax.W;
+    const long long item = blockIdx.y;
+    const int r0 = blockIdx.x * 2 * G;
+    const int ra = r0 + 2 * g, rb = ra + 1;
+    const bool va = ra < nlines, vb = rb < nlines;
+    const T* ya = in + item * in_item + (long long)(va ? ra : 0) * in_rs;
+    const T* yb = in + item * in_item + (long long)(vb ? rb : 0) * in_rs;
+
+    double c1a = 0, cna = 0, c1b = 0, cnb = 0;
+    if (va) border_coeffs<T>(ax, ya[0], ya[1], ya[n - 2], ya[n - 1], c1a, cna);
+    if (vb) border_coeffs<T>(ax, yb[0], yb[1], yb[n - 2], yb[n - 1], c1b, cnb);
+    const T c1af = (T)c1a, cnaf = (T)cna, c1bf = (T)c1b, cnbf = (T)cnb;
+    const C2<T> zero = cmk<T>(0, 0);
+
+    for (int j = t; j < N; j += ax.tpg) {
+        const T ql = ax.q[1 + j], qr = ax.q[n - 2 - j];
+        const T wa = va ? ya[1 + j] - ql * c1af - qr * cnaf : (T)0;
+        const T wb = vb ? yb[1 + j] - ql * c1bf - qr * cnbf : (T)0;
+        if constexpr (FAM == FAM_F) {
+            buf[j] = dft_in<T>(ax, j, cmk<T>(wa, wb));
+        } else if constexpr (FAM == FAM_C) {
+            const int p = pos_C(j, N);
+            buf[p] = dft_in<T>(ax, p, cmk<T>(wa, wb));
+        } else {   // odd extension of length 2(N+1)
+            buf[1 + j] = dft_in<T>(ax, 1 + j, cmk<T>(wa, wb));
+            const int p2 = ax.L - 1 - j;
+            buf[p2] = dft_in<T>(ax, p2, cmk<T>(-wa, -wb));
+        }
+    }
+    if (FAM == FAM_S && t == 0) { buf[0] = zero; buf[N + 1] = zero; }
+    if (ax.blue)
+        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[p] = zero;
+    __syncthreads();
+    group_dft<T>(buf, ax, t);
+
+    E* sa = stage + (size_t)(2 * g) * W;
+    E* sb = sa + W;
+    if constexpr (FAM == FAM_F) {
+        for (int k = t; k < ax.H; k += ax.tpg) {
+            const C2<T> zk = dft_out<T>(buf, ax, k);
+            const C2<T> zr = cconj<T>(dft_out<T>(buf, ax, k == 0 ? 0 : N - k));
+            const C2<T> s = cadd<T>(zk, zr), d = csub<T>(zk, zr);
+            const T h = (T)0.5 * ax.sc;
+            sa[1 + k] = cmk<T>(s.x * h, s.y * h);
+            sb[1 + k] = cmk<T>(d.y * h, -d.x * h);        // -i (zk - zr) / 2
+        }
+        if (t == 0) {
+            sa[0] = cmk<T>(c1af, 0); sa[W - 1] = cmk<T>(cnaf, 0);
+            sb[0] = cmk<T>(c1bf, 0); sb[W - 1] = cmk<T>(cnbf, 0);
+        }
+    } else if constexpr (FAM == FAM_C) {
+        for (int k = t; k < N; k += ax.tpg) {
+            const C2<T> v = dft_out<T>(buf, ax, k);
+            const C2<T> vr = cconj<T>(dft_out<T>(buf, ax, k == 0 ? 0 : N - k));
+            const C2<T> s = cadd<T>(v, vr), d = csub<T>(v, vr);
+            // Va = s/2, Vb = -i d/2; DCT-II coefficient = scale * Re(post_k * V)
+            const C2<T> ph = ax.post[k];
+            const T sk = (k == 0 ? ax.s0 : ax.s1) * (T)0.5;
+            sa[1 + k] = (T)(sk * (ph.x * s.x - ph.y * s.y));
+            sb[1 + k] = (T)(sk * (ph.x * d.y + ph.y * d.x));
+        }
+        if (t == 0) { sa[0] = c1af; sa[W - 1] = cnaf; sb[0] = c1bf; sb[W - 1] = cnbf; }
+    } else {
+        for (int k = t; k < N; k += ax.tpg) {
+            const C2<T> z = dft_out<T>(buf, ax, k + 1);
+            sa[1 + k] = (T)(-z.y * ax.sc);
+            sb[1 + k] = (T)(z.x * ax.sc);
+        }
+        if (t == 0) { sa[0] = c1af; sa[W - 1] = cnaf; sb[0] = c1bf; sb[W - 1] = cnbf; }
+    }
+    __syncthreads();
+
+    const int rows_here = min(2 * G, nlines - r0);
+    E* o = out + item * out_item + (long long)r0 * out_rs;
+    const int total = rows_here * W;
+    if (out_rs == 1) {
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int c = idx / rows_here, rr = idx - c * rows_here;
+            o[rr + (long long)c * out_cs] = stage[(size_t)rr * W + c];
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int rr = idx / W, c = idx - rr * W;
+            o[(long long)rr * out_rs + (long long)c * out_cs] = stage[(size_t)rr * W + c];
+        }
+    }
+}
+
+// =====================================================================
+// Synthesis T_X on pairs of lines whose result is real.
+// Input spectral entry c of line r: in[i*in_item + r*in_rs + c*in_cs];
+// output sample j of line r: out[i*out_item + r*out_rs + j].
+// FMODE 0: plain; 1: 1D filter (problem = line); 2: 2D filter (problem = item,
+// the line index is the axis-1 stored index).
+// =====================================================================
+template <typename T, int FAM, int FMODE>
+__global__ void __launch_bounds__(512)
+k_pair_synthesis(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in, long long in_item,
+                 long long in_rs, long long in_cs, T* __restrict__ out, long long out_item,
+                 long long out_rs, int nlines, Axis<T> ax, FilterDesc fd) {
+    typedef typename ElemT<T, FAM == FAM_F>::t E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = blockDim.x / ax.tpg;
+    const int g = threadIdx.x / ax.tpg;
+    const int t = threadIdx.x - g * ax.tpg;
+    C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.M;
+    E* stage = reinterpret_cast<E*>(reinterpret_cast<C2<T>*>(smem_raw) + (size_t)G * ax.M);
+    const int n = ax.n, N = ax.N, W = ax.W;
+    const long long item = blockIdx.y;
+    const int r0 = blockIdx.x * 2 * G;
+    const int rows_here = min(2 * G, nlines - r0);
+
+    // gather (and filter) the spectra of this CTA's lines into the stage
+    {
+        const E* ip = in + item * in_item + (long long)r0 * in_rs;
+        const int total = rows_here * W;
+        const E* Dp = reinterpret_cast<const E*>(fd.D);
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            int rr, c;
+            if (in_rs == 1) { c = idx / rows_here; rr = idx - c * rows_here; }
+            else { rr = idx / W; c = idx - rr * W; }
+            const long long off = (long long)rr * in_rs + (long long)c * in_cs;
+            E v = ip[off];
+            if constexpr (FMODE == 1) {
+                const int line = r0 + rr;
+                const E d = Dp[(fd.psf_per ? (long long)line : 0) * fd.d_psf_stride + c];
+                const T mu = (T)mu_of(fd, line);
+                v = apply_filter(v, d, smoothing2<T>(fd, 1, ax, line, c), mu);
+            } else if constexpr (FMODE == 2) {
+                const int line = r0 + rr;
+                const E d = Dp[(fd.psf_per ? item : 0) * fd.d_psf_stride + (long long)line * in_rs + (long long)c * in_cs];
+                const T mu = (T)mu_of(fd, (int)item);
+                v = apply_filter(v, d, smoothing2<T>(fd, 2, ax, line, c), mu);
+            }
+            stage[(size_t)rr * W + c] = v;
+        }
+        for (int idx = total + threadIdx.x; idx < 2 * G * W; idx += blockDim.x) stage[idx] = E();
+    }
+    __syncthreads();
+
+    const E* sa = stage + (size_t)(2 * g) * W;
+    const E* sb = sa + W;
+    const C2<T> zero = cmk<T>(0, 0);
+    if constexpr (FAM == FAM_F) {
+        const int H = ax.H;
+        for (int k = t; k < N; k += ax.tpg) {
+            C2<T> z;
+            if (k < H) {
+                C2<T> a = reinterpret_cast<const C2<T>*>(sa)[1 + k];
+                C2<T> b = reinterpret_cast<const C2<T>*>(sb)[1 + k];
+                if (k == 0 || 2 * k == N) { a.y = 0; b.y = 0; }
+                z = cmk<T>(a.x - b.y, a.y + b.x);                // a + i b
+            } else {
+                const C2<T> a = reinterpret_cast<const C2<T>*>(sa)[1 + N - k];
+                const C2<T> b = reinterpret_cast<const C2<T>*>(sb)[1 + N - k];
+                z = cmk<T>(a.x + b.y, -a.y + b.x);               // conj(a) + i conj(b)
+            }
+            buf[k] = dft_in<T>(ax, k, cconj<T>(z));
+        }
+    } else if constexpr (FAM == FAM_C) {
+        for (int k = t; k < N; k += ax.tpg) {
+            const T isk = k == 0 ? ax.is0 : ax.is1;
+            const T ya = re_of(sa[1 + k]) * isk, yb = re_of(sb[1 + k]) * isk;
+            const T yar = k == 0 ? (T)0 : re_of(sa[1 + N - k]) * ax.is1;
+            const T ybr = k == 0 ? (T)0 : re_of(sb[1 + N - k]) * ax.is1;
+            const C2<T> ph = cconj<T>(ax.post[k]);                  // exp(+i pi k/(2N))
+            const C2<T> v = cmul<T>(ph, cmk<T>(ya + ybr, yb - yar));
+            buf[k] = dft_in<T>(ax, k, cconj<T>(v));
+        }
+    } else {
+        for (int k = t; k < N; k += ax.tpg) {
+            const T a = re_of(sa[1 + k]), b = re_of(sb[1 + k]);
+            buf[1 + k] = dft_in<T>(ax, 1 + k, cmk<T>(a, b));
+            const int p2 = ax.L - 1 - k;
+            buf[p2] = dft_in<T>(ax, p2, cmk<T>(-a, -b));
+        }
+        if (t == 0) { buf[0] = zero; buf[N + 1] = zero; }
+    }
+    if (ax.blue)
+        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[p] = zero;
+    __syncthreads();
+    group_dft<T>(buf, ax, t);
+
+    const int ra = r0 + 2 * g, rb = ra + 1;
+    const bool va = ra < nlines, vb = rb < nlines;
+    const T c1a = re_of(sa[0]), cna = re_of(sa[W - 1]);
+    const T c1b = re_of(sb[0]), cnb = re_of(sb[W - 1]);
+    T* oa = out + item * out_item + (long long)ra * out_rs;
+    T* ob = out + item * out_item + (long long)rb * out_rs;
+    // interior sample j of the trigonometric part, for both lines
+    auto wval = [&](int j, T& wa, T& wb) {
+        if constexpr (FAM == FAM_F) {
+            const C2<T> z = dft_out<T>(buf, ax, j);
+            wa = z.x * ax.sc;
+            wb = -z.y * ax.sc;
+        } else if constexpr (FAM == FAM_C) {
+            const C2<T> z = dft_out<T>(buf, ax, pos_C(j, N));
+            wa = z.x * ax.invN;
+            wb = -z.y * ax.invN;
+        } else {
+            const C2<T> z = dft_out<T>(buf, ax, j + 1);
+            wa = -z.y * ax.sc;
+            wb = z.x * ax.sc;
+        }
+    };
+    for (int j = t; j < N; j += ax.tpg) {
+        T wa, wb;
+        wval(j, wa, wb);
+        const T ql = ax.q[1 + j], qr = ax.q[n - 2 - j];
+        if (va) oa[1 + j] = wa + ql * c1a + qr * cna;
+        if (vb) ob[1 + j] = wb + ql * c1b + qr * cnb;
+    }
+    if (t == 0) {
+        T wa0 = 0, wb0 = 0, wa1 = 0, wb1 = 0;
+        if (FAM != FAM_S) { wval(0, wa0, wb0); wval(N - 1, wa1, wb1); }
+        // C: y_1 = q_1 c_1 + w_1, y_n = q_1 c_n + w_N;  F: y_1 = q_1 c_1 + w_N, y_n = q_1 c_n + w_1
+        const T fa = FAM == FAM_C ? wa0 : wa1, la = FAM == FAM_C ? wa1 : wa0;
+        const T fb = FAM == FAM_C ? wb0 : wb1, lb = FAM == FAM_C ? wb1 : wb0;
+        if (va) { oa[0] = ax.q1 * c1a + fa; oa[n - 1] = ax.q1 * cna + la; }
+        if (vb) { ob[0] = ax.q1 * c1b + fb; ob[n - 1] = ax.q1 * cnb + lb; }
+    }
+}
+
+// =====================================================================
+// Fourier family, complex lines along axis 0 (one line per thread group).
+// Line c of item i: in[i*item_stride + c*n + t].
+// =====================================================================
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_cplx_analysis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long item_stride,
+                int nlines, Axis<T> ax) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = blockDim.x / ax.tpg;
+    const int g = threadIdx.x / ax.tpg;
+    const int t = threadIdx.x - g * ax.tpg;
+    C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.M;
+    const int n = ax.n, N = ax.N;
+    const long long item = blockIdx.y;
+    const int c = blockIdx.x * G + g;
+    const bool valid = c < nlines;
+    const C2<T>* y = in + item * item_stride + (long long)(valid ? c : 0) * n;
+    double c1r = 0, cnr = 0, c1i = 0, cni = 0;
+    if (valid) {
+        const C2<T> y0 = y[0], y1 = y[1], ym2 = y[n - 2], ym1 = y[n - 1];
+        border_coeffs<T>(ax, y0.x, y1.x, ym2.x, ym1.x, c1r, cnr);
+        border_coeffs<T>(ax, y0.y, y1.y, ym2.y, ym1.y, c1i, cni);
+    }
+    const C2<T> c1 = cmk<T>((T)c1r, (T)c1i), cn = cmk<T>((T)cnr, (T)cni);
+    for (int j = t; j < N; j += ax.tpg) {
+        const T ql = ax.q[1 + j], qr = ax.q[n - 2 - j];
+        C2<T> w = cmk<T>(0, 0);
+        if (valid) {
+            const C2<T> v = y[1 + j];
+            w = cmk<T>(v.x - ql * c1.x - qr * cn.x, v.y - ql * c1.y - qr * cn.y);
+        }
+        buf[j] = dft_in<T>(ax, j, w);
+    }
+    if (ax.blue)
+        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[p] = cmk<T>(0, 0);
+    __syncthreads();
+    group_dft<T>(buf, ax, t);
+    if (!valid) return;
+    C2<T>* o = out + item * item_stride + (long long)c * n;
+    for (int k = t; k < N; k += ax.tpg) o[1 + k] = cscale<T>(dft_out<T>(buf, ax, k), ax.sc);
+    if (t == 0) { o[0] = c1; o[n - 1] = cn; }
+}
+
+template <typename T, bool FILTER>
+__global__ void __launch_bounds__(512)
+k_cplx_synthesis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long item_stride,
+                 int nlines, Axis<T> ax, FilterDesc fd) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = blockDim.x / ax.tpg;
+    const int g = threadIdx.x / ax.tpg;
+    const int t = threadIdx.x - g * ax.tpg;
+    C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.M;
+    const int n = ax.n, N = ax.N;
+    const long long item = blockIdx.y;
+    const int c = blockIdx.x * G + g;
+    const bool valid = c < nlines;
+    const C2<T>* x = in + item * item_stride + (long long)(valid ? c : 0) * n;
+    const C2<T>* Dp = reinterpret_cast<const C2<T>*>(fd.D) + (fd.psf_per ? item : 0) * fd.d_psf_stride +
+                      (long long)(valid ? c : 0) * n;
+    T mu = 0;
+    if (FILTER) mu = (T)mu_of(fd, (int)item);
+    auto coef = [&](int pos) -> C2<T> {
+        C2<T> v = x[pos];
+        if constexpr (FILTER) v = apply_filter(v, Dp[pos], smoothing2<T>(fd, 2, ax, c, pos), mu);
+        return v;
+    };
+    for (int k = t; k < N; k += ax.tpg) {
+        const C2<T> v = valid ? coef(1 + k) : cmk<T>(0, 0);
+        buf[k] = dft_in<T>(ax, k, cconj<T>(v));
+    }
+    if (ax.blue)
+        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[p] = cmk<T>(0, 0);
+    __syncthreads();
+    group_dft<T>(buf, ax, t);
+    if (!valid) return;
+    const C2<T> c1 = coef(0), cn = coef(n - 1);
+    C2<T>* o = out + item * item_stride + (long long)c * n;
+    for (int j = t; j < N; j += ax.tpg) {
+        const C2<T> w = cscale<T>(cconj<T>(dft_out<T>(buf, ax, j)), ax.sc);
+        const T ql = ax.q[1 + j], qr = ax.q[n - 2 - j];
+        o[1 + j] = cmk<T>(w.x + ql * c1.x + qr * cn.x, w.y + ql * c1.y + qr * cn.y);
+    }
+    if (t == 0) {
+        const C2<T> w0 = cscale<T>(cconj<T>(dft_out<T>(buf, ax, 0)), ax.sc);
+        const C2<T> wN = cscale<T>(cconj<T>(dft_out<T>(buf, ax, N - 1)), ax.sc);
+        o[0] = cmk<T>(ax.q1 * c1.x + wN.x, ax.q1 * c1.y + wN.y);      // y_1 = q_1 c_1 + w_N
+        o[n - 1] = cmk<T>(ax.q1 * cn.x + w0.x, ax.q1 * cn.y + w0.y);  // y_n = q_1 c_n + w_1
+    }
+}
+
+// =====================================================================
+// Eigenvalues d[c][t0] = sum_{j0,j1} h[j0][j1] E0[t0][j0] E1[c][j1] with
+// E[t][j] = exp(-i (j - m) theta_t)  (Eq. (eq:symbol) at -theta, Sec. 6),
+// accumulated in double.  1D problems use n0 = p0 = 1 and E0 = [[1]].
+// grid = (W1, npsf), block = 256.
+// =====================================================================
+template <typename T, bool CPLX>
+__global__ void k_eig(const T* __restrict__ psf, long long psf_stride, int p0, int p1,
+                      const double2* __restrict__ E0, const double2* __restrict__ E1, int n0,
+                      typename ElemT<T, CPLX>::t* __restrict__ D, long long d_psf_stride) {
+    __shared__ double2 P[64];
+    const int c = blockIdx.x;
+    const long long ip = blockIdx.y;
+    const T* h = psf + ip * psf_stride;
+    for (int j0 = threadIdx.x; j0 < p0; j0 += blockDim.x) {
+        double re = 0, im = 0;
+        for (int j1 = 0; j1 < p1; ++j1) {
+            const double hv = (double)h[j0 * p1 + j1];
+            const double2 e = E1[(long long)c * p1 + j1];
+            re += hv * e.x;
+            im += hv * e.y;
+        }
+        P[j0] = make_double2(re, im);
+    }
+    __syncthreads();
+    typename ElemT<T, CPLX>::t* o = D + ip * d_psf_stride + (long long)c * n0;
+    for (int t0 = threadIdx.x; t0 < n0; t0 += blockDim.x) {
+        double re = 0, im = 0;
+        const double2* e0 = E0 + (long long)t0 * p0;
+        for (int j0 = 0; j0 < p0; ++j0) {
+            const double2 a = P[j0], b = e0[j0];
+            re += a.x * b.x - a.y * b.y;
+            im += a.x * b.y + a.y * b.x;
+        }
+        if constexpr (CPLX) o[t0] = cmk<T>((T)re, (T)im);
+        else o[t0] = (T)re;
+    }
+}
+
+// =====================================================================
+// GCV partial sums (Eq. (eq:gcv2), (eq:mugcv)).  For every stored spectral
+// element: weight w (2 for Fourier-half entries standing for a conjugate
+// pair, else 1), e = w |ghat|^2, a = |d|^2 / |s|^2 (elements with s = 0 have
+// sigma = 0 and are dropped).  For each mu of the grid,
+//   sigma = 1/(a + mu),  num += e sigma^2,  den += w sigma.
+// Each thread takes a pair of grid values and shares one reciprocal between
+// them: r = 1/((a+mu1)(a+mu2)), sigma1 = (a+mu2) r, sigma2 = (a+mu1) r.
+// FP32: terms summed in float over runs of 256 elements, then in double.
+// grid = (chunks, items), block = 256; partials[item][chunk][2K].
+// =====================================================================
+struct GcvGeom {
+    int ndim;
+    int fam;
+    int n0, N0;         // axis 0 (2D only): spectral positions along a line
+    int n1, N1, W1;     // axis of the stored index c (1D: the only axis)
+    int lap;
+    long long S;        // stored elements per item
+    int chunk;          // elements per CTA
+    int K;
+};
+
+template <typename T> struct Pack4;
+template <> struct Pack4<float> { typedef float4 t; };
+template <> struct Pack4<double> { typedef double4 t; };
+
+__device__ __forceinline__ float pair_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double pair_rcp(double x) { return 1.0 / x; }
+
+// largest a kept in FP32 so that (a + mu1)(a + mu2) cannot overflow
+template <typename T> __device__ __forceinline__ T a_cap() { return sizeof(T) == 4 ? (T)1e18 : (T)1e150; }
+
+template <typename T, bool CPLX>
+__global__ void __launch_bounds__(256)
+k_gcv_partials(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
+               long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo,
+               double* __restrict__ partials) {
+    typedef typename Pack4<T>::t P4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    P4* pk = reinterpret_cast<P4*>(smem_raw);
+    const long long item = blockIdx.y;
+    const long long e0 = (long long)blockIdx.x * geo.chunk;
+    const int cnt = (int)min((long long)geo.chunk, geo.S - e0);
+    const typename ElemT<T, CPLX>::t* sp = spec + item * geo.S + e0;
+    const typename ElemT<T, CPLX>::t* dp = D + (psf_per ? item : 0) * d_psf_stride + e0;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const long long e = e0 + i;
+        int c, t0 = 0;
+        if (geo.ndim == 2) { c = (int)(e / geo.n0); t0 = (int)(e - (long long)c * geo.n0); }
+        else c = (int)e;
+        T w = 1;
+        if (CPLX) {
+            const bool self = (c == 0 || c == geo.W1 - 1 || c == 1 || 2 * (c - 1) == geo.N1);
+            w = self ? (T)1 : (T)2;
+        }
+        T s2 = 1;
+        if (geo.lap) {
+            const int t1 = stored_to_t(geo.fam, geo.n1, geo.W1, c);
+            T s = lap_eig<T>(theta_over_pi<T>(geo.fam, geo.n1, geo.N1, t1));
+            if (geo.ndim == 2) s += lap_eig<T>(theta_over_pi<T>(geo.fam, geo.n0, geo.N0, t0));
+            s2 = s * s;
+        }
+        const T lam = abs2_of(dp[i]);
+        const T g2 = abs2_of(sp[i]);
+        P4 v;
+        if (s2 > (T)0) { v.x = min(lam / s2, a_cap<T>()); v.y = w * g2; v.z = w; }
+        else { v.x = (T)1; v.y = (T)0; v.z = (T)0; }
+        v.w = 0;
+        pk[i] = v;
+    }
+    __syncthreads();
+    const int K = geo.K;
+    const int NP = (K + 1) / 2;                 // pairs of grid values
+    int tpm = 1;                                // threads per pair: a power of two <= 32
+    while (tpm * 2 <= 32 && tpm * 2 * NP <= (int)blockDim.x) tpm *= 2;
+    const int ppp = blockDim.x / tpm;
+    const int sub = threadIdx.x % tpm;
+    double* outp = partials + (item * gridDim.x + blockIdx.x) * 2LL * K;
+    for (int base = 0; base < NP; base += ppp) {
+        const int pr = base + threadIdx.x / tpm;
+        const int j1 = 2 * pr, j2 = j1 + 1;
+        const T mu1 = j1 < K ? muT[j1] : (T)1;
+        const T mu2 = j2 < K ? muT[j2] : (T)1;
+        double n1 = 0, d1 = 0, n2 = 0, d2 = 0;
+        const int run = sizeof(T) == 4 ? 256 * tpm : (1 << 30);
+        for (int i0 = sub; i0 < cnt; i0 += run) {
+            const int iend = min(cnt, i0 + run);
+            T fn1 = 0, fd1 = 0, fn2 = 0, fd2 = 0;
+#pragma unroll 4
+            for (int i = i0; i < iend; i += tpm) {
+                const P4 v = pk[i];
+                const T t1 = v.x + mu1, t2 = v.x + mu2;
+                const T r = pair_rcp(t1 * t2);
+                const T s1 = t2 * r, s2 = t1 * r;
+                fd1 += v.z * s1;
+                fd2 += v.z * s2;
+                const T q1 = v.y * s1, q2 = v.y * s2;
+                fn1 += q1 * s1;
+                fn2 += q2 * s2;
+            }
+            n1 += fn1; d1 += fd1; n2 += fn2; d2 += fd2;
+        }
+        for (int off = tpm / 2; off > 0; off >>= 1) {
+            n1 += __shfl_down_sync(0xffffffffu, n1, off, tpm);
+            d1 += __shfl_down_sync(0xffffffffu, d1, off, tpm);
+            n2 += __shfl_down_sync(0xffffffffu, n2, off, tpm);
+            d2 += __shfl_down_sync(0xffffffffu, d2, off, tpm);
+        }
+        if (sub == 0) {
+            if (j1 < K) { outp[j1] = n1; outp[K + j1] = d1; }
+            if (j2 < K) { outp[j2] = n2; outp[K + j2] = d2; }
+        }
+    }
+}
+
+// G(mu_j) = num_j / den_j^2 and the first index of the minimum (NaN never wins).
+// grid = items, block = 256.
+__global__ void k_gcv_finalize(const double* __restrict__ partials, int nchunks, int K,
+                               double* __restrict__ gcv, int* __restrict__ mu_idx);
+
+}  // namespace hobc

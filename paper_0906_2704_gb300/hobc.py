@@ -1,0 +1,213 @@
+"""Python binding of the C ABI in include/hobc.h (ctypes; marshalling only).
+
+Every step of the method runs in the CUDA library ``libhobc.so`` built in this
+package directory by ``paper_0906_2704_gb300.build``.  There is no fallback: if
+the library is missing, importing this module raises.
+
+Device buffers are passed as torch CUDA tensors (or raw integer addresses);
+host buffers for :meth:`Plan.deblur_host` as NumPy arrays.  Shapes and dtypes
+are checked here only to produce clear errors before the C call.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhobc.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "hobc.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_0906_2704_gb300.build`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+FAMILY = {"auto": 0, "sine": 1, "cosine": 2, "fourier": 3}
+FAMILY_NAME = {v: k for k, v in FAMILY.items()}
+SMOOTHING = {"I": 0, "identity": 0, "lap": 1, "laplacian": 1}
+PRECISION = {"fp64": 0, "fp32": 1}
+STATUS = ["HOBC_OK", "HOBC_ERR_ARG", "HOBC_ERR_UNSUPPORTED", "HOBC_ERR_SIZE",
+          "HOBC_ERR_NONFINITE", "HOBC_ERR_CUDA", "HOBC_ERR_TIMEOUT"]
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int),
+        ("n", ctypes.c_int * 2),
+        ("psf", ctypes.c_int * 2),
+        ("bc_degree", ctypes.c_int),
+        ("family", ctypes.c_int),
+        ("psf_symmetric", ctypes.c_int),
+        ("L", ctypes.c_int),
+        ("prec", ctypes.c_int),
+        ("n_mu", ctypes.c_int),
+        ("batch", ctypes.c_int),
+        ("psf_per_item", ctypes.c_int),
+    ]
+
+
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_lib.hobc_plan_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(ctypes.c_double), _vp,
+                                  ctypes.POINTER(_vp)]
+_lib.hobc_plan_create.restype = ctypes.c_int
+_lib.hobc_plan_destroy.argtypes = [_vp]
+_lib.hobc_plan_destroy.restype = None
+_lib.hobc_plan_family.argtypes = [_vp]
+_lib.hobc_plan_family.restype = ctypes.c_int
+_lib.hobc_spectrum_size.argtypes = [_vp, ctypes.POINTER(_sz), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_sz)]
+_lib.hobc_spectrum_size.restype = ctypes.c_int
+for _name, _n in (("hobc_deblur", 6), ("hobc_deblur_host", 6), ("hobc_analysis", 3), ("hobc_synthesis", 3),
+                  ("hobc_eigenvalues", 3), ("hobc_gcv", 5), ("hobc_filter_synthesis", 5)):
+    getattr(_lib, _name).argtypes = [_vp] * _n
+    getattr(_lib, _name).restype = ctypes.c_int
+_lib.hobc_last_launch_count.argtypes = [_vp]
+_lib.hobc_last_launch_count.restype = ctypes.c_int
+_lib.hobc_status_str.argtypes = [ctypes.c_int]
+_lib.hobc_status_str.restype = ctypes.c_char_p
+_lib.hobc_last_error.argtypes = []
+_lib.hobc_last_error.restype = ctypes.c_char_p
+
+
+class HobcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        name = _lib.hobc_status_str(status).decode()
+        detail = _lib.hobc_last_error().decode()
+        super().__init__(f"{what}: {name}" + (f" ({detail})" if detail else ""))
+
+
+def _check(status: int, what: str) -> None:
+    if status != 0:
+        raise HobcError(status, what)
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions declared in include/hobc.h."""
+    with open(HEADER_PATH) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hobc_[a-z_0-9]+)\s*\(", text)))
+
+
+def library() -> ctypes.CDLL:
+    return _lib
+
+
+def _ptr(x) -> int | None:
+    """Device address of a torch tensor (or an int address / None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return x.data_ptr()
+
+
+def _hptr(a) -> int | None:
+    if a is None:
+        return None
+    if not isinstance(a, np.ndarray) or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous NumPy array")
+    return a.ctypes.data
+
+
+class Plan:
+    """A plan of the C ABI: problem geometry, tables and workspace on one GPU."""
+
+    def __init__(self, ndim: int, n, psf, bc_degree: int, mu_grid, L: str = "I",
+                 prec: str = "fp64", family: str = "auto", psf_symmetric: bool = False,
+                 batch: int = 1, psf_per_item: bool = False, stream=None):
+        n = [int(n)] if np.isscalar(n) else [int(v) for v in n]
+        psf = [int(psf)] if np.isscalar(psf) else [int(v) for v in psf]
+        d = PlanDesc()
+        d.ndim = ndim
+        for i in range(2):
+            d.n[i] = n[i] if i < len(n) else 0
+            d.psf[i] = psf[i] if i < len(psf) else 0
+        d.bc_degree = bc_degree
+        d.family = FAMILY[family]
+        d.psf_symmetric = int(bool(psf_symmetric))
+        d.L = SMOOTHING[L]
+        d.prec = PRECISION[prec]
+        mu = np.ascontiguousarray(mu_grid, dtype=np.float64)
+        d.n_mu = len(mu)
+        d.batch = batch
+        d.psf_per_item = int(bool(psf_per_item))
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except ImportError:
+                stream = 0
+        elif not isinstance(stream, int):
+            stream = stream.cuda_stream
+        self._handle = _vp()
+        _check(_lib.hobc_plan_create(ctypes.byref(d), mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     _vp(stream), ctypes.byref(self._handle)), "hobc_plan_create")
+        self.ndim, self.n, self.psf_shape = ndim, tuple(n[:ndim]), tuple(psf[:ndim])
+        self.batch, self.mu_grid, self.prec, self.L = batch, mu, prec, L
+        self.psf_per_item = bool(psf_per_item)
+        self.family = FAMILY_NAME[_lib.hobc_plan_family(self._handle)]
+        spec, cplx, psfn = _sz(), ctypes.c_int(), _sz()
+        _check(_lib.hobc_spectrum_size(self._handle, ctypes.byref(spec), ctypes.byref(cplx), ctypes.byref(psfn)),
+               "hobc_spectrum_size")
+        self.spec_elems, self.spec_complex, self.psf_elems = spec.value, bool(cplx.value), psfn.value
+
+    # geometry helpers -------------------------------------------------------
+    @property
+    def spectrum_shape(self):
+        """Per-item stored spectrum shape (see the spectrum layout in include/hobc.h)."""
+        if self.ndim == 1:
+            return (self.spec_elems,)
+        return (self.spec_elems // self.n[0], self.n[0])
+
+    @property
+    def real_dtype(self):
+        return np.float64 if self.prec == "fp64" else np.float32
+
+    @property
+    def last_launch_count(self) -> int:
+        return _lib.hobc_last_launch_count(self._handle)
+
+    # C ABI calls --------------------------------------------------------------
+    def deblur(self, g, psf, f, mu_index=None, gcv=None) -> None:
+        _check(_lib.hobc_deblur(self._handle, _ptr(g), _ptr(psf), _ptr(f), _ptr(mu_index), _ptr(gcv)),
+               "hobc_deblur")
+
+    def deblur_host(self, g, psf, f, mu_index=None, gcv=None) -> None:
+        _check(_lib.hobc_deblur_host(self._handle, _hptr(g), _hptr(psf), _hptr(f), _hptr(mu_index), _hptr(gcv)),
+               "hobc_deblur_host")
+
+    def analysis(self, g, ghat) -> None:
+        _check(_lib.hobc_analysis(self._handle, _ptr(g), _ptr(ghat)), "hobc_analysis")
+
+    def synthesis(self, c, y) -> None:
+        _check(_lib.hobc_synthesis(self._handle, _ptr(c), _ptr(y)), "hobc_synthesis")
+
+    def eigenvalues(self, psf, d) -> None:
+        _check(_lib.hobc_eigenvalues(self._handle, _ptr(psf), _ptr(d)), "hobc_eigenvalues")
+
+    def gcv(self, ghat, d, gcv, mu_index) -> None:
+        _check(_lib.hobc_gcv(self._handle, _ptr(ghat), _ptr(d), _ptr(gcv), _ptr(mu_index)), "hobc_gcv")
+
+    def filter_synthesis(self, ghat, d, mu_index, f) -> None:
+        _check(_lib.hobc_filter_synthesis(self._handle, _ptr(ghat), _ptr(d), _ptr(mu_index), _ptr(f)),
+               "hobc_filter_synthesis")
+
+    def close(self) -> None:
+        if getattr(self, "_handle", None):
+            _lib.hobc_plan_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,79 @@
+"""The C-ABI library loads, exports every function include/hobc.h declares, and
+rejects bad problem descriptions on the host before touching the GPU.  CPU only:
+no call here reaches a kernel or allocates device memory."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_0906_2704_gb300", "libhobc.so")
+
+
+@pytest.fixture(scope="module")
+def hobc():
+    if not os.path.exists(LIB):
+        from paper_0906_2704_gb300 import build
+        build.build()
+    from paper_0906_2704_gb300 import hobc as mod
+    return mod
+
+
+def test_library_exports_every_declared_function(hobc):
+    names = hobc.declared_functions()
+    assert len(names) >= 14
+    lib = ctypes.CDLL(hobc.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(hobc):
+    lib = hobc.library()
+    for code, name in enumerate(hobc.STATUS):
+        assert lib.hobc_status_str(code).decode() == name
+
+
+def _create(hobc, **kw):
+    args = dict(ndim=1, n=64, psf=5, bc_degree=2, mu_grid=[1e-3, 1e-2], psf_symmetric=True)
+    args.update(kw)
+    return hobc.Plan(**args)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(n=5), "HOBC_ERR_SIZE"),                       # n < 6
+    (dict(n=2048), "HOBC_ERR_SIZE"),                    # n > 1024
+    (dict(psf=4), "HOBC_ERR_SIZE"),                     # even PSF
+    (dict(n=8, psf=7), "HOBC_ERR_SIZE"),                # 2m+1 > n-2
+    (dict(bc_degree=3), "HOBC_ERR_UNSUPPORTED"),
+    (dict(bc_degree=1, psf_symmetric=False), "HOBC_ERR_UNSUPPORTED"),   # antireflective needs symmetry
+    (dict(family="sine", bc_degree=2), "HOBC_ERR_UNSUPPORTED"),
+    (dict(family="fourier", bc_degree=1), "HOBC_ERR_UNSUPPORTED"),
+    (dict(mu_grid=[1e-3, 0.0]), "HOBC_ERR_ARG"),        # mu > 0 (Eq. (eq:mintik))
+    (dict(mu_grid=[1e-3, float("nan")]), "HOBC_ERR_NONFINITE"),
+    (dict(mu_grid=[1e-3, float("inf")]), "HOBC_ERR_NONFINITE"),
+    (dict(batch=0), "HOBC_ERR_ARG"),
+    (dict(ndim=3), "HOBC_ERR_ARG"),
+])
+def test_plan_validation_rejects_bad_descriptions(hobc, kw, status):
+    with pytest.raises(hobc.HobcError) as ei:
+        _create(hobc, **kw)
+    assert hobc.STATUS[ei.value.status] == status
+
+
+def test_null_arguments_rejected(hobc):
+    lib = hobc.library()
+    out = ctypes.c_void_p()
+    assert lib.hobc_plan_create(None, None, None, ctypes.byref(out)) == 1
+    assert lib.hobc_deblur(None, None, None, None, None, None) == 1
+    assert lib.hobc_analysis(None, None, None) == 1
+    assert lib.hobc_gcv(None, None, None, None, None) == 1
+
+
+def test_binding_has_no_cpu_fallback(hobc):
+    """The binding only marshals: it refuses host tensors for device entry points."""
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        hobc._ptr(torch.zeros(4))
+    with pytest.raises(ValueError):
+        hobc._hptr(np.zeros((4, 4))[:, ::2])

@@ -1,0 +1,302 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Seeded inputs at small sizes that span several FFT groups, Bluestein and
+power-of-two lengths, odd and non-square shapes, odd batches (ragged line
+pairs), shared and per-problem PSFs; plus the full-size configurations.
+
+Layer 1 -- each step on identical inputs (the oracle's own values rounded to the
+working precision are given to both sides), element by element, relative to the
+largest reference entry:
+  eigenvalues  FP64 1e-12;  FP32 1e-6 per entry (summed in FP64, stored in FP32)
+  analysis     FP64 1e-10;  FP32 1e-5
+  G(mu_j)      FP64 1e-10;  FP32 1e-5   (relative, every mu)
+  argmin       equal, or an index whose oracle G is within the G tolerance of the minimum
+  filter+synthesis  FP64 1e-10; FP32: C eps log2(M) max(|T| |Phi ghat|)
+Layer 2 -- the whole path from g: FP64 1e-10; FP32 forward-error bounds from the
+arithmetic (reading R13): the analysis error delta = C eps log2(M) max(|T^{-1}||g|)
+is magnified by the filter factor kappa = max|d|/(|d|^2+mu|s|^2) and by |T|.
+C = 8 (a small constant of the FFT error bound).
+"""
+import numpy as np
+import pytest
+
+from oracle import hobc_oracle as O
+from paper_0906_2704_gb300 import synth
+import parity_utils as P
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+from paper_0906_2704_gb300 import hobc  # noqa: E402  (raises if the library is missing)
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+C_FFT = 8.0
+
+
+def _dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=dtype)).cuda()
+
+
+def _spec_dev(a, plan, dt):
+    """Complex layout array -> device tensor (interleaved for the Fourier family)."""
+    if plan.spec_complex:
+        a = np.stack([a.real, a.imag], axis=-1)
+    return _dev(a.real if not plan.spec_complex else a, dt)
+
+
+def _spec_np(t, plan):
+    a = t.cpu().numpy()
+    return a[..., 0] + 1j * a[..., 1] if plan.spec_complex else a
+
+
+def _round(x, dt):
+    """The value a working-precision buffer holds (complex parts rounded separately)."""
+    if np.iscomplexobj(x):
+        return x.real.astype(dt).astype(np.float64) + 1j * x.imag.astype(dt).astype(np.float64)
+    return x.astype(dt).astype(np.float64)
+
+
+def run_case(ndim, fam_name, n, taps, L, prec, batch, psf_per_item=False, K=24, seed=0, mus=None, h0=None,
+             eta=0.01, check_items=None):
+    fam = P.FAM_LETTER[fam_name]
+    dt = np.float64 if prec == "fp64" else np.float32
+    tdt = torch.float64 if prec == "fp64" else torch.float32
+    eps = 2.0 ** -53 if prec == "fp64" else P.EPS32
+    n = (n,) if ndim == 1 else tuple(n)
+    base = P.psf_for(fam, ndim, taps) if h0 is None else h0
+    hs = []
+    for b in range(batch if psf_per_item else 1):
+        h = base ** (1.0 + 0.15 * b) if psf_per_item else base
+        hs.append(_round(h / h.sum(), dt))
+    g, _ = P.problems(ndim, n, hs[0], batch, seed, eta)
+    g = _round(g, dt)
+    mus = synth.mu_grid(K, 1e-6, 1.0) if mus is None else mus
+    K = len(mus)
+    plan = hobc.Plan(ndim, n, hs[0].shape, 1 if fam == "S" else 2, mus, L=L, prec=prec, family=fam_name,
+                     psf_symmetric=fam != "F", batch=batch, psf_per_item=psf_per_item)
+    S = plan.spec_elems
+    cs = (2,) if plan.spec_complex else ()
+    npsf = len(hs)
+    tol = TOL[prec]
+    l2m = P.log2_fft(fam, n)
+    items = range(batch) if check_items is None else check_items
+
+    # ---- oracle answers (FP64) on the rounded inputs
+    orc = [P.oracle_steps(fam, ndim, hs[b if psf_per_item else 0], g[b], L, mus) for b in items]
+
+    # ---- layer 1a: eigenvalues and analysis from the seeded inputs
+    psf_d = _dev(np.stack(hs), dt)
+    d_d = torch.empty((npsf, S) + cs, dtype=tdt, device="cuda")
+    plan.eigenvalues(psf_d, d_d)
+    g_d = _dev(g, dt)
+    gh_d = torch.empty((batch, S) + cs, dtype=tdt, device="cuda")
+    plan.analysis(g_d, gh_d)
+    dg = _spec_np(d_d, plan)
+    gh = _spec_np(gh_d, plan)
+    for i, b in enumerate(items):
+        ghat_o, d_o = orc[i][0], orc[i][1]
+        ref = P.to_layout(fam, ghat_o).reshape(gh[b].shape)
+        err = np.abs(gh[b] - ref).max() / np.abs(ref).max()
+        assert err <= tol, f"analysis item {b}: {err:.3e}"
+        dref = P.to_layout(fam, d_o).reshape(dg[0].shape)
+        dgot = dg[b if psf_per_item else 0]
+        if prec == "fp64":
+            assert np.abs(dgot - dref).max() <= 1e-12 * np.abs(dref).max(), "eigenvalues"
+        else:
+            assert np.all(np.abs(dgot - dref) <= 1e-6 * np.abs(dref) + 1e-37), "eigenvalues"
+
+    # ---- layer 1b: GCV and filter+synthesis on identical (rounded oracle) inputs
+    gin = np.zeros((batch, S) + (() if not plan.spec_complex else ()), dtype=complex if plan.spec_complex else float)
+    din = np.zeros((npsf, S), dtype=gin.dtype)
+    full_in = {}
+    for i, b in enumerate(items):
+        ghat_o, d_o = orc[i][0], orc[i][1]
+        gr, dr = _round(ghat_o, dt), _round(d_o, dt)
+        full_in[b] = (gr, dr)
+        gin[b] = P.to_layout(fam, gr).reshape(-1)
+        din[b if psf_per_item else 0] = P.to_layout(fam, dr).reshape(-1)
+    G_d = torch.empty((batch, K), dtype=torch.float64, device="cuda")
+    mi_d = torch.empty(batch, dtype=torch.int32, device="cuda")
+    gin_d = _spec_dev(gin, plan, dt)
+    din_d = _spec_dev(din, plan, dt)
+    plan.gcv(gin_d, din_d, G_d, mi_d)
+    mi_fix = np.array([orc[list(items).index(b)][4] if b in items else 0 for b in range(batch)], dtype=np.int32)
+    f_d = torch.empty(g.shape, dtype=tdt, device="cuda")
+    plan.filter_synthesis(gin_d, din_d, _dev(mi_fix, np.int32), f_d)
+    G, mi, f = G_d.cpu().numpy(), mi_d.cpu().numpy(), f_d.cpu().numpy()
+    for i, b in enumerate(items):
+        s_o = orc[i][2]
+        gr, dr = full_in[b]
+        Gref = O.gcv_curve(gr, dr, s_o, mus)
+        gerr = np.max(np.abs(G[b] - Gref) / np.abs(Gref))
+        assert gerr <= tol, f"G (identical inputs) item {b}: {gerr:.3e}"
+        k = int(mi[b])
+        kref = O.gcv_argmin(Gref)
+        assert k == kref or Gref[k] <= (1 + tol) * Gref.min(), f"argmin {k} vs {kref}"
+        X = O.filter_factors(dr, s_o, mus[mi_fix[b]]) * gr
+        fref = P.oracle_filtered(fam, ndim, gr, dr, s_o, mus[mi_fix[b]])
+        bound = tol * np.abs(fref).max() if prec == "fp64" else C_FFT * eps * l2m * P.abs_apply(fam, X).max()
+        ferr = np.abs(f[b] - fref).max()
+        assert ferr <= bound, f"filter+synthesis item {b}: {ferr:.3e} > {bound:.3e}"
+
+    # ---- layer 2: the whole path from g (one call, plus the round trip)
+    f2_d = torch.empty(g.shape, dtype=tdt, device="cuda")
+    mi2_d = torch.empty(batch, dtype=torch.int32, device="cuda")
+    G2_d = torch.empty((batch, K), dtype=torch.float64, device="cuda")
+    plan.deblur(g_d, psf_d, f2_d, mi2_d, G2_d)
+    y_d = torch.empty(g.shape, dtype=tdt, device="cuda")
+    plan.synthesis(gh_d, y_d)
+    f2, mi2, G2, y = f2_d.cpu().numpy(), mi2_d.cpu().numpy(), G2_d.cpu().numpy(), y_d.cpu().numpy()
+    for i, b in enumerate(items):
+        ghat_o, d_o, s_o, G_o, k_o = orc[i]
+        delta = C_FFT * eps * l2m * P.abs_apply(fam, g[b], inverse=True).max()   # analysis error bound
+        k = int(mi2[b])
+        if prec == "fp64":
+            assert np.max(np.abs(G2[b] - G_o) / G_o) <= tol, "end-to-end G"
+            assert k == k_o or G_o[k] <= (1 + tol) * G_o.min(), "end-to-end argmin"
+        else:
+            a2 = np.abs(d_o) ** 2
+            gbs = []
+            for j, mu in enumerate(mus):
+                sig = np.abs(s_o) ** 2 / (a2 + mu * np.abs(s_o) ** 2)
+                num = np.sum(sig * sig * np.abs(ghat_o) ** 2)
+                gb = (2 * delta * np.sum(sig * sig * np.abs(ghat_o)) + delta ** 2 * np.sum(sig * sig)) / num + tol
+                gbs.append(gb)
+                assert abs(G2[b, j] - G_o[j]) <= gb * G_o[j], f"end-to-end G mu {j}: bound {gb:.2e}"
+            assert k == k_o or G_o[k] <= (1 + 2 * max(gbs)) * G_o.min(), "end-to-end argmin"
+        fo = P.oracle_filtered(fam, ndim, ghat_o, d_o, s_o, mus[k])
+        if prec == "fp64":
+            bound = tol * np.abs(fo).max()
+            ybound = tol * np.abs(g[b]).max()
+        else:
+            kappa = P.amplification(d_o, s_o, mus[k])
+            X = O.filter_factors(d_o, s_o, mus[k]) * ghat_o
+            bound = (C_FFT * eps * l2m * P.abs_apply(fam, X).max()
+                     + P.abs_norm(fam, n) * kappa * delta)
+            ybound = C_FFT * eps * l2m * P.abs_apply(fam, ghat_o).max() + P.abs_norm(fam, n) * delta
+        ferr = np.abs(f2[b] - fo).max()
+        assert ferr <= bound, f"end-to-end f item {b}: {ferr:.3e} > {bound:.3e}"
+        yerr = np.abs(y[b] - g[b]).max()
+        assert yerr <= ybound, f"round trip item {b}: {yerr:.3e} > {ybound:.3e}"
+    return plan
+
+
+CASES_1D = [(37, 5), (66, 7), (130, 5)]
+CASES_2D = [((19, 34), (5, 5)), ((34, 21), (7, 7)), ((66, 40), (5, 5))]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("L", ["I", "lap"])
+@pytest.mark.parametrize("fam", ["sine", "cosine", "fourier"])
+@pytest.mark.parametrize("n,taps", CASES_1D)
+def test_parity_1d(fam, n, taps, L, prec):
+    run_case(1, fam, n, taps, L, prec, batch=5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("L", ["I", "lap"])
+@pytest.mark.parametrize("fam", ["sine", "cosine", "fourier"])
+@pytest.mark.parametrize("n,taps", CASES_2D)
+def test_parity_2d(fam, n, taps, L, prec):
+    run_case(2, fam, n, taps, L, prec, batch=3)
+
+
+@pytest.mark.parametrize("fam", ["sine", "cosine", "fourier"])
+@pytest.mark.parametrize("ndim", [1, 2])
+def test_parity_per_item_psf(fam, ndim):
+    if ndim == 1:
+        run_case(1, fam, 45, 5, "lap", "fp64", batch=4, psf_per_item=True)
+    else:
+        run_case(2, fam, (23, 30), (5, 5), "I", "fp32", batch=3, psf_per_item=True)
+
+
+def test_identity_psf_closed_form():
+    """h = delta, L = I: f = g/(1+mu*) exactly (d = 1)."""
+    n = 50
+    g = np.random.default_rng(3).standard_normal((4, n))
+    mus = synth.mu_grid(8)
+    for fam, deg in (("sine", 1), ("cosine", 2), ("fourier", 2)):
+        plan = hobc.Plan(1, n, 1, deg, mus, family=fam, psf_symmetric=True, batch=4)
+        f = torch.empty((4, n), dtype=torch.float64, device="cuda")
+        mi = torch.empty(4, dtype=torch.int32, device="cuda")
+        plan.deblur(_dev(g, np.float64), _dev(np.ones(1), np.float64), f, mi)
+        k = mi.cpu().numpy()
+        assert np.allclose(f.cpu().numpy(), g / (1 + mus[k])[:, None], rtol=0, atol=1e-12)
+
+
+def test_zero_input_and_single_mu():
+    """g = 0 gives G = 0 for every mu, mu* = index 0, f = 0; K = 1 works."""
+    for K in (1, 5):
+        mus = synth.mu_grid(K)
+        plan = hobc.Plan(2, (20, 24), (5, 5), 2, mus, L="lap", family="cosine", psf_symmetric=True, batch=2)
+        h = P.psf_for("C", 2, (5, 5))
+        g = torch.zeros((2, 20, 24), dtype=torch.float64, device="cuda")
+        f = torch.full_like(g, 7.0)
+        mi = torch.full((2,), -1, dtype=torch.int32, device="cuda")
+        G = torch.full((2, K), -1.0, dtype=torch.float64, device="cuda")
+        plan.deblur(g, _dev(h, np.float64), f, mi, G)
+        assert torch.all(f == 0) and torch.all(mi == 0) and torch.all(G == 0)
+
+
+def test_minimum_size_and_host_entry_point():
+    """Smallest field of view (n = 6 with a 3-tap PSF) and the host-buffer call."""
+    mus = synth.mu_grid(6, 1e-4, 1.0)
+    for fam, deg in (("sine", 1), ("cosine", 2), ("fourier", 2)):
+        h = np.array([0.25, 0.5, 0.25])
+        g, _ = synth.problem_1d(1, 6, h, 0.01, count=3)
+        plan = hobc.Plan(1, 6, 3, deg, mus, family=fam, psf_symmetric=True, batch=3)
+        f = np.empty_like(g)
+        mi = np.empty(3, dtype=np.int32)
+        G = np.empty((3, 6))
+        plan.deblur_host(g, h, f, mi, G)
+        for b in range(3):
+            fo, Go, ko, _ = O.deblur_1d(P.FAM_LETTER[fam], h, g[b], "I", mus)
+            assert np.allclose(G[b], Go, rtol=1e-10)
+            assert mi[b] == ko
+            assert np.abs(f[b] - fo).max() <= 1e-10 * np.abs(fo).max()
+
+
+def test_caller_mu_index_out_of_range_is_clamped():
+    """A caller-supplied mu index outside the grid is clamped on the device."""
+    mus = synth.mu_grid(4, 1e-3, 1.0)
+    h = P.psf_for("C", 1, 5)
+    g, _ = synth.problem_1d(2, 40, h, 0.01, count=2)
+    plan = hobc.Plan(1, 40, 5, 2, mus, family="cosine", psf_symmetric=True, batch=2)
+    gh = torch.empty((2, plan.spec_elems), dtype=torch.float64, device="cuda")
+    d = torch.empty((1, plan.spec_elems), dtype=torch.float64, device="cuda")
+    plan.analysis(_dev(g, np.float64), gh)
+    plan.eigenvalues(_dev(h, np.float64), d)
+    f_bad = torch.empty((2, 40), dtype=torch.float64, device="cuda")
+    f_ok = torch.empty_like(f_bad)
+    plan.filter_synthesis(gh, d, _dev(np.array([-5, 99], np.int32), np.int32), f_bad)
+    plan.filter_synthesis(gh, d, _dev(np.array([0, 3], np.int32), np.int32), f_ok)
+    assert torch.equal(f_bad, f_ok)
+
+
+# ------------------------------------------------------------ full-size configurations
+
+
+def test_full_size_1d_signals_fp64():
+    """1D: n = 256, symmetric Gaussian sigma 2 (9 taps), antireflective (degree 1), L = I,
+    64 mu in [1e-8, 1], 1% noise, the 65,536-signal batch; 16 sampled signals vs the oracle."""
+    h = synth.gaussian_psf_1d(2.0, 9)
+    mus = synth.mu_grid(64)
+    idx = [0, 1, 777, 4096, 30000, 65535] + list(range(10, 20))
+    run_case(1, "sine", 256, 9, "I", "fp64", batch=65536, mus=mus, h0=h, check_items=idx)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_512_cosine_laplacian(prec):
+    """2D 512 x 512, separable Gaussian 15 x 15 (sigma 2.5), degree 2 (cosine), Laplacian, 256 mu."""
+    h = synth.gaussian_psf_2d_separable(2.5, 15)
+    run_case(2, "cosine", (512, 512), (15, 15), "lap", prec, batch=1, mus=synth.mu_grid(256), h0=h, eta=0.005)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_1024_fourier(prec):
+    """2D 1024 x 1024, rotated anisotropic Gaussian 21 x 21, degree 2 (Fourier), L = I, 256 mu --
+    the benchmark workload, in the benchmark's launch configuration (batch of 2 here)."""
+    h = synth.gaussian_psf_2d_rotated(3.0, 1.5, 30.0, 21, 2.0, -1.0)
+    run_case(2, "fourier", (1024, 1024), (21, 21), "I", prec, batch=2, mus=synth.mu_grid(256), h0=h, eta=0.005,
+             check_items=[1])
