@@ -283,10 +283,14 @@ def run_ours(args):
     evals = B * S * K_MU
     gcv_s = steps_ms["gcv"] / 1e3
     achieved = evals / gcv_s / 1e9
-    peak = 152 * 16 * sm_max * 1e6 / 1e9      # one MUFU reciprocal per evaluation, 16/clk/SM
+    # per evaluation: 5.5 FP32-pipe operations (a+mu; half of the shared product; sigma;
+    # den FMA; e*sigma; num FMA) and half a MUFU reciprocal; 128 FP32 lanes per SM-clock
+    # bind first: 152 SMs x 128/5.5 evaluations per clock
+    peak = 152 * (128 / 5.5) * sm_max * 1e6 / 1e9
     roofline = {"bound": "alu", "kernel": "k_gcv_partials", "achieved": achieved, "peak": peak,
                 "unit": "Geval/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"152 SMs x 16 MUFU/clk x {sm_max:.0f} MHz ({peak_kind} clock)"}
+                "peak_source": f"152 SMs x 128 FP32 lanes / 5.5 ops per evaluation x {sm_max:.0f} MHz "
+                               f"({peak_kind} max clock)"}
     hbm_bytes = B * N_SIDE * N_SIDE * esz * 2 + h.size * esz
     hbm = {"algorithmic_bytes_per_step": hbm_bytes,
            "achieved_gbs": hbm_bytes / (ms / args.steps / 1e3) / 1e9,

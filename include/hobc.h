@@ -82,7 +82,7 @@ typedef enum {
 typedef struct {
     int ndim;                  /* 1 (signals) or 2 (images)                               */
     int n[2];                  /* field of view: 1D n[0]; 2D n[0] rows x n[1] columns;
-                                  each in [6, 2048]                                        */
+                                  each in [6, 1024]                                        */
     int psf[2];                /* PSF mask size (odd): 1D psf[0] = 2m+1; 2D rows x cols;
                                   needs psf[i] <= n[i] - 2 (Sec. 2.2, Sec. 3)             */
     int bc_degree;             /* 1 or 2                                                   */
@@ -91,7 +91,7 @@ typedef struct {
     hobc_smoothing L;
     hobc_precision prec;
     int n_mu;                  /* K >= 1 grid points                                       */
-    int batch;                 /* problems per call, >= 1                                  */
+    int batch;                 /* problems per call, >= 1 (2D: <= 65535)                   */
     int psf_per_item;          /* 0: one PSF for the whole batch; 1: one PSF per problem   */
 } hobc_plan_desc;
 

@@ -281,6 +281,7 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
     const hobc_plan_desc d = *desc;
     if (d.ndim != 1 && d.ndim != 2) return HOBC_ERR_ARG;
     if (d.n_mu < 1 || d.batch < 1) return HOBC_ERR_ARG;
+    if (d.ndim == 2 && d.batch > 65535) return HOBC_ERR_SIZE;     // items ride on gridDim.y
     if (d.prec != HOBC_FP64 && d.prec != HOBC_FP32) return HOBC_ERR_ARG;
     if (d.L != HOBC_L_IDENTITY && d.L != HOBC_L_LAPLACIAN) return HOBC_ERR_ARG;
     if (d.psf_per_item != 0 && d.psf_per_item != 1) return HOBC_ERR_ARG;

@@ -46,6 +46,7 @@ struct Axis {
     int log2M;
     int blue;       // 1: Bluestein (M >= 2L-1), 0: direct
     int tpg;        // threads per group = M/8
+    int Mp;         // shared-memory slots per group: M plus one pad slot per 16 (pidx)
     int H;          // FOURIER: floor(N/2)+1 stored frequencies; else N
     int W;          // spectrum entries stored on this axis: n (S, C) or H+2 (F)
     const C2<T>* tw;      // [M] exp(-2 pi i k / M)
@@ -62,6 +63,11 @@ struct Axis {
 };
 
 // ---------------------------------------------------------------- FFT core
+
+// Shared-memory slot of logical FFT index i: one pad slot after every 16
+// entries, so the stride-8 writes of the first Stockham stages hit distinct
+// banks (without it a warp's stage-1 store of 8-byte values is 16-way conflicted).
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
 
 template <typename T> __device__ __forceinline__ void dft4(C2<T>& a0, C2<T>& a1, C2<T>& a2, C2<T>& a3) {
     const C2<T> s02 = cadd<T>(a0, a2), d02 = csub<T>(a0, a2);
@@ -104,7 +110,7 @@ __device__ __forceinline__ void fft_stage(C2<T>* buf, int M, int Ns, const C2<T>
         const int step = (M / (Ns * R)) * k;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            C2<T> x = buf[j + r * nb];
+            C2<T> x = buf[pidx(j + r * nb)];
             if (r > 0 && Ns > 1) x = cmul<T>(x, tw[r * step]);
             v[u * R + r] = x;
         }
@@ -123,7 +129,7 @@ __device__ __forceinline__ void fft_stage(C2<T>* buf, int M, int Ns, const C2<T>
         const int k = j & (Ns - 1);
         const int base = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[base + r * Ns] = v[u * R + r];
+        for (int r = 0; r < R; ++r) buf[pidx(base + r * Ns)] = v[u * R + r];
     }
     __syncthreads();
 }
@@ -156,7 +162,7 @@ __device__ __forceinline__ void group_dft(C2<T>* buf, const Axis<T>& ax, int t) 
     if (ax.blue) {
         // pointwise product with the transformed chirp, conjugated so the
         // second forward FFT computes the inverse (1/M folded into bhat)
-        for (int p = t; p < ax.M; p += ax.tpg) buf[p] = cconj<T>(cmul<T>(buf[p], ax.bhat[p]));
+        for (int p = t; p < ax.M; p += ax.tpg) buf[pidx(p)] = cconj<T>(cmul<T>(buf[pidx(p)], ax.bhat[p]));
         __syncthreads();
         group_fft<T>(buf, ax, t);
     }
@@ -164,7 +170,7 @@ __device__ __forceinline__ void group_dft(C2<T>* buf, const Axis<T>& ax, int t) 
 
 template <typename T>
 __device__ __forceinline__ C2<T> dft_out(const C2<T>* buf, const Axis<T>& ax, int k) {
-    const C2<T> z = buf[k];
+    const C2<T> z = buf[pidx(k)];
     return ax.blue ? cmul<T>(cconj<T>(z), ax.chirp[k]) : z;
 }
 

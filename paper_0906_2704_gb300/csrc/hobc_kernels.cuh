@@ -92,8 +92,8 @@ k_pair_analysis(const T* __restrict__ in, long long in_item, long long in_rs,
     const int G = blockDim.x / ax.tpg;
     const int g = threadIdx.x / ax.tpg;
     const int t = threadIdx.x - g * ax.tpg;
-    C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.M;
-    E* stage = reinterpret_cast<E*>(reinterpret_cast<C2<T>*>(smem_raw) + (size_t)G * ax.M);
+    C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.Mp;
+    E* stage = reinterpret_cast<E*>(reinterpret_cast<C2<T>*>(smem_raw) + (size_t)G * ax.Mp);
     const int n = ax.n, N = ax.N, W = ax.W;
     const long long item = blockIdx.y;
     const int r0 = blockIdx.x * 2 * G;
@@ -113,19 +113,19 @@ k_pair_analysis(const T* __restrict__ in, long long in_item, long long in_rs,
         const T wa = va ? ya[1 + j] - ql * c1af - qr * cnaf : (T)0;
         const T wb = vb ? yb[1 + j] - ql * c1bf - qr * cnbf : (T)0;
         if constexpr (FAM == FAM_F) {
-            buf[j] = dft_in<T>(ax, j, cmk<T>(wa, wb));
+            buf[pidx(j)] = dft_in<T>(ax, j, cmk<T>(wa, wb));
         } else if constexpr (FAM == FAM_C) {
             const int p = pos_C(j, N);
-            buf[p] = dft_in<T>(ax, p, cmk<T>(wa, wb));
+            buf[pidx(p)] = dft_in<T>(ax, p, cmk<T>(wa, wb));
         } else {   // odd extension of length 2(N+1)
-            buf[1 + j] = dft_in<T>(ax, 1 + j, cmk<T>(wa, wb));
+            buf[pidx(1 + j)] = dft_in<T>(ax, 1 + j, cmk<T>(wa, wb));
             const int p2 = ax.L - 1 - j;
-            buf[p2] = dft_in<T>(ax, p2, cmk<T>(-wa, -wb));
+            buf[pidx(p2)] = dft_in<T>(ax, p2, cmk<T>(-wa, -wb));
         }
     }
-    if (FAM == FAM_S && t == 0) { buf[0] = zero; buf[N + 1] = zero; }
+    if (FAM == FAM_S && t == 0) { buf[pidx(0)] = zero; buf[pidx(N + 1)] = zero; }
     if (ax.blue)
-        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[p] = zero;
+        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[pidx(p)] = zero;
     __syncthreads();
     group_dft<T>(buf, ax, t);
 
@@ -199,8 +199,8 @@ k_pair_synthesis(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in, long
     const int G = blockDim.x / ax.tpg;
     const int g = threadIdx.x / ax.tpg;
     const int t = threadIdx.x - g * ax.tpg;
-    C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.M;
-    E* stage = reinterpret_cast<E*>(reinterpret_cast<C2<T>*>(smem_raw) + (size_t)G * ax.M);
+    C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.Mp;
+    E* stage = reinterpret_cast<E*>(reinterpret_cast<C2<T>*>(smem_raw) + (size_t)G * ax.Mp);
     const int n = ax.n, N = ax.N, W = ax.W;
     const long long item = blockIdx.y;
     const int r0 = blockIdx.x * 2 * G;
@@ -251,7 +251,7 @@ k_pair_synthesis(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in, long
                 const C2<T> b = reinterpret_cast<const C2<T>*>(sb)[1 + N - k];
                 z = cmk<T>(a.x + b.y, -a.y + b.x);               // conj(a) + i conj(b)
             }
-            buf[k] = dft_in<T>(ax, k, cconj<T>(z));
+            buf[pidx(k)] = dft_in<T>(ax, k, cconj<T>(z));
         }
     } else if constexpr (FAM == FAM_C) {
         for (int k = t; k < N; k += ax.tpg) {
@@ -261,19 +261,19 @@ k_pair_synthesis(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in, long
             const T ybr = k == 0 ? (T)0 : re_of(sb[1 + N - k]) * ax.is1;
             const C2<T> ph = cconj<T>(ax.post[k]);                  // exp(+i pi k/(2N))
             const C2<T> v = cmul<T>(ph, cmk<T>(ya + ybr, yb - yar));
-            buf[k] = dft_in<T>(ax, k, cconj<T>(v));
+            buf[pidx(k)] = dft_in<T>(ax, k, cconj<T>(v));
         }
     } else {
         for (int k = t; k < N; k += ax.tpg) {
             const T a = re_of(sa[1 + k]), b = re_of(sb[1 + k]);
-            buf[1 + k] = dft_in<T>(ax, 1 + k, cmk<T>(a, b));
+            buf[pidx(1 + k)] = dft_in<T>(ax, 1 + k, cmk<T>(a, b));
             const int p2 = ax.L - 1 - k;
-            buf[p2] = dft_in<T>(ax, p2, cmk<T>(-a, -b));
+            buf[pidx(p2)] = dft_in<T>(ax, p2, cmk<T>(-a, -b));
         }
-        if (t == 0) { buf[0] = zero; buf[N + 1] = zero; }
+        if (t == 0) { buf[pidx(0)] = zero; buf[pidx(N + 1)] = zero; }
     }
     if (ax.blue)
-        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[p] = zero;
+        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[pidx(p)] = zero;
     __syncthreads();
     group_dft<T>(buf, ax, t);
 
@@ -329,7 +329,7 @@ k_cplx_analysis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long
     const int G = blockDim.x / ax.tpg;
     const int g = threadIdx.x / ax.tpg;
     const int t = threadIdx.x - g * ax.tpg;
-    C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.M;
+    C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.Mp;
     const int n = ax.n, N = ax.N;
     const long long item = blockIdx.y;
     const int c = blockIdx.x * G + g;
@@ -349,10 +349,10 @@ k_cplx_analysis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long
             const C2<T> v = y[1 + j];
             w = cmk<T>(v.x - ql * c1.x - qr * cn.x, v.y - ql * c1.y - qr * cn.y);
         }
-        buf[j] = dft_in<T>(ax, j, w);
+        buf[pidx(j)] = dft_in<T>(ax, j, w);
     }
     if (ax.blue)
-        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[p] = cmk<T>(0, 0);
+        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[pidx(p)] = cmk<T>(0, 0);
     __syncthreads();
     group_dft<T>(buf, ax, t);
     if (!valid) return;
@@ -369,7 +369,7 @@ k_cplx_synthesis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long lon
     const int G = blockDim.x / ax.tpg;
     const int g = threadIdx.x / ax.tpg;
     const int t = threadIdx.x - g * ax.tpg;
-    C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.M;
+    C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.Mp;
     const int n = ax.n, N = ax.N;
     const long long item = blockIdx.y;
     const int c = blockIdx.x * G + g;
@@ -386,10 +386,10 @@ k_cplx_synthesis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long lon
     };
     for (int k = t; k < N; k += ax.tpg) {
         const C2<T> v = valid ? coef(1 + k) : cmk<T>(0, 0);
-        buf[k] = dft_in<T>(ax, k, cconj<T>(v));
+        buf[pidx(k)] = dft_in<T>(ax, k, cconj<T>(v));
     }
     if (ax.blue)
-        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[p] = cmk<T>(0, 0);
+        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[pidx(p)] = cmk<T>(0, 0);
     __syncthreads();
     group_dft<T>(buf, ax, t);
     if (!valid) return;
@@ -412,15 +412,15 @@ k_cplx_synthesis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long lon
 // Eigenvalues d[c][t0] = sum_{j0,j1} h[j0][j1] E0[t0][j0] E1[c][j1] with
 // E[t][j] = exp(-i (j - m) theta_t)  (Eq. (eq:symbol) at -theta, Sec. 6),
 // accumulated in double.  1D problems use n0 = p0 = 1 and E0 = [[1]].
-// grid = (W1, npsf), block = 256.
+// grid = (npsf, W1), block = 256.
 // =====================================================================
 template <typename T, bool CPLX>
 __global__ void k_eig(const T* __restrict__ psf, long long psf_stride, int p0, int p1,
                       const double2* __restrict__ E0, const double2* __restrict__ E1, int n0,
                       typename ElemT<T, CPLX>::t* __restrict__ D, long long d_psf_stride) {
     __shared__ double2 P[64];
-    const int c = blockIdx.x;
-    const long long ip = blockIdx.y;
+    const int c = blockIdx.y;
+    const long long ip = blockIdx.x;
     const T* h = psf + ip * psf_stride;
     for (int j0 = threadIdx.x; j0 < p0; j0 += blockDim.x) {
         double re = 0, im = 0;
@@ -453,10 +453,10 @@ __global__ void k_eig(const T* __restrict__ psf, long long psf_stride, int p0, i
 // pair, else 1), e = w |ghat|^2, a = |d|^2 / |s|^2 (elements with s = 0 have
 // sigma = 0 and are dropped).  For each mu of the grid,
 //   sigma = 1/(a + mu),  num += e sigma^2,  den += w sigma.
-// Each thread takes a pair of grid values and shares one reciprocal between
-// them: r = 1/((a+mu1)(a+mu2)), sigma1 = (a+mu2) r, sigma2 = (a+mu1) r.
+// Each thread takes four grid values, in two pairs that each share one
+// reciprocal: r = 1/((a+mu1)(a+mu2)), sigma1 = (a+mu2) r, sigma2 = (a+mu1) r.
 // FP32: terms summed in float over runs of 256 elements, then in double.
-// grid = (chunks, items), block = 256; partials[item][chunk][2K].
+// grid = chunks * items (item-major), block = 256; partials[item][chunk][2K].
 // =====================================================================
 struct GcvGeom {
     int ndim;
@@ -491,8 +491,10 @@ k_gcv_partials(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typena
     typedef typename Pack4<T>::t P4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     P4* pk = reinterpret_cast<P4*>(smem_raw);
-    const long long item = blockIdx.y;
-    const long long e0 = (long long)blockIdx.x * geo.chunk;
+    const int nch = (int)((geo.S + geo.chunk - 1) / geo.chunk);
+    const long long item = blockIdx.x / nch;
+    const int chunk = blockIdx.x - (int)(item * nch);
+    const long long e0 = (long long)chunk * geo.chunk;
     const int cnt = (int)min((long long)geo.chunk, geo.S - e0);
     const typename ElemT<T, CPLX>::t* sp = spec + item * geo.S + e0;
     const typename ElemT<T, CPLX>::t* dp = D + (psf_per ? item : 0) * d_psf_stride + e0;
@@ -523,45 +525,51 @@ k_gcv_partials(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typena
     }
     __syncthreads();
     const int K = geo.K;
-    const int NP = (K + 1) / 2;                 // pairs of grid values
-    int tpm = 1;                                // threads per pair: a power of two <= 32
-    while (tpm * 2 <= 32 && tpm * 2 * NP <= (int)blockDim.x) tpm *= 2;
-    const int ppp = blockDim.x / tpm;
+    const int NQ = (K + 3) / 4;                 // quads of grid values (two shared-reciprocal pairs)
+    int tpm = 1;                                // threads per quad: a power of two <= 32
+    while (tpm * 2 <= 32 && tpm * 2 * NQ <= (int)blockDim.x) tpm *= 2;
+    const int qpp = blockDim.x / tpm;
     const int sub = threadIdx.x % tpm;
-    double* outp = partials + (item * gridDim.x + blockIdx.x) * 2LL * K;
-    for (int base = 0; base < NP; base += ppp) {
-        const int pr = base + threadIdx.x / tpm;
-        const int j1 = 2 * pr, j2 = j1 + 1;
-        const T mu1 = j1 < K ? muT[j1] : (T)1;
-        const T mu2 = j2 < K ? muT[j2] : (T)1;
-        double n1 = 0, d1 = 0, n2 = 0, d2 = 0;
+    double* outp = partials + (long long)blockIdx.x * 2LL * K;
+    for (int base = 0; base < NQ; base += qpp) {
+        const int j0 = 4 * (base + threadIdx.x / tpm);
+        T mu[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) mu[u] = j0 + u < K ? muT[j0 + u] : (T)1;
+        double nd[4] = {0, 0, 0, 0}, dd[4] = {0, 0, 0, 0};
         const int run = sizeof(T) == 4 ? 256 * tpm : (1 << 30);
         for (int i0 = sub; i0 < cnt; i0 += run) {
             const int iend = min(cnt, i0 + run);
-            T fn1 = 0, fd1 = 0, fn2 = 0, fd2 = 0;
-#pragma unroll 4
+            T fn[4] = {0, 0, 0, 0}, fd[4] = {0, 0, 0, 0};
+#pragma unroll 2
             for (int i = i0; i < iend; i += tpm) {
                 const P4 v = pk[i];
-                const T t1 = v.x + mu1, t2 = v.x + mu2;
-                const T r = pair_rcp(t1 * t2);
-                const T s1 = t2 * r, s2 = t1 * r;
-                fd1 += v.z * s1;
-                fd2 += v.z * s2;
-                const T q1 = v.y * s1, q2 = v.y * s2;
-                fn1 += q1 * s1;
-                fn2 += q2 * s2;
+#pragma unroll
+                for (int u = 0; u < 4; u += 2) {
+                    const T t1 = v.x + mu[u], t2 = v.x + mu[u + 1];
+                    const T r = pair_rcp(t1 * t2);
+                    const T s1 = t2 * r, s2 = t1 * r;
+                    fd[u] += v.z * s1;
+                    fd[u + 1] += v.z * s2;
+                    const T q1 = v.y * s1, q2 = v.y * s2;
+                    fn[u] += q1 * s1;
+                    fn[u + 1] += q2 * s2;
+                }
             }
-            n1 += fn1; d1 += fd1; n2 += fn2; d2 += fd2;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { nd[u] += fn[u]; dd[u] += fd[u]; }
         }
-        for (int off = tpm / 2; off > 0; off >>= 1) {
-            n1 += __shfl_down_sync(0xffffffffu, n1, off, tpm);
-            d1 += __shfl_down_sync(0xffffffffu, d1, off, tpm);
-            n2 += __shfl_down_sync(0xffffffffu, n2, off, tpm);
-            d2 += __shfl_down_sync(0xffffffffu, d2, off, tpm);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            for (int off = tpm / 2; off > 0; off >>= 1) {
+                nd[u] += __shfl_down_sync(0xffffffffu, nd[u], off, tpm);
+                dd[u] += __shfl_down_sync(0xffffffffu, dd[u], off, tpm);
+            }
         }
         if (sub == 0) {
-            if (j1 < K) { outp[j1] = n1; outp[K + j1] = d1; }
-            if (j2 < K) { outp[j2] = n2; outp[K + j2] = d2; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (j0 + u < K) { outp[j0 + u] = nd[u]; outp[K + j0 + u] = dd[u]; }
         }
     }
 }

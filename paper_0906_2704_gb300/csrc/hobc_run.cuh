@@ -13,7 +13,7 @@ template <typename T>
 static Axis<T> dev_axis(const AxisHost& a) {
     Axis<T> x;
     x.fam = a.fam; x.n = a.n; x.N = a.N; x.L = a.L; x.M = a.M; x.log2M = a.log2M;
-    x.blue = a.blue; x.tpg = a.tpg; x.H = a.H; x.W = a.W;
+    x.blue = a.blue; x.tpg = a.tpg; x.Mp = a.M + a.M / 16; x.H = a.H; x.W = a.W;
     x.tw = reinterpret_cast<const C2<T>*>(a.tw);
     x.chirp = reinterpret_cast<const C2<T>*>(a.chirp);
     x.bhat = reinterpret_cast<const C2<T>*>(a.bhat);
@@ -34,7 +34,8 @@ static inline Launch pair_launch(const AxisHost& a, size_t cbytes, size_t ebytes
     G = std::min(G, std::max(1, 512 / a.tpg));
     G = std::min(G, (nlines + 1) / 2);
     G = std::max(G, 1);
-    auto smem = [&](int g) { return (size_t)g * a.M * cbytes + (size_t)2 * g * a.W * ebytes; };
+    const size_t Mp = (size_t)a.M + a.M / 16;
+    auto smem = [&](int g) { return (size_t)g * Mp * cbytes + (size_t)2 * g * a.W * ebytes; };
     while (G > 1 && smem(G) > 200 * 1024) --G;
     Launch l;
     l.block = dim3(G * a.tpg);
@@ -47,11 +48,12 @@ static inline Launch cplx_launch(const AxisHost& a, size_t cbytes, int nlines, i
     int G = std::max(1, 256 / a.tpg);
     G = std::min(G, std::max(1, 512 / a.tpg));
     G = std::min(G, nlines);
-    while (G > 1 && (size_t)G * a.M * cbytes > 200 * 1024) --G;
+    const size_t Mp = (size_t)a.M + a.M / 16;
+    while (G > 1 && (size_t)G * Mp * cbytes > 200 * 1024) --G;
     Launch l;
     l.block = dim3(G * a.tpg);
     l.grid = dim3((nlines + G - 1) / G, items);
-    l.smem = (size_t)G * a.M * cbytes;
+    l.smem = (size_t)G * Mp * cbytes;
     return l;
 }
 
@@ -196,7 +198,7 @@ hobc_status run_eig(hobc_plan_s* p, const void* psf, void* D) {
     if (p->nax == 2) { E0 = p->ax[0].etab; p0 = p->ax[0].p; n0 = p->ax[0].n; }
     else { E0 = last.etab + (size_t)last.W * last.p; p0 = 1; n0 = 1; }   // unit entry after the table
     const long long psf_stride = (long long)p->psf_elems;
-    dim3 grid(last.W, p->npsf);
+    dim3 grid(p->npsf, last.W);
     if (cplx)
         k_eig<T, true><<<grid, 256, 0, p->stream>>>(reinterpret_cast<const T*>(psf), psf_stride, p0, last.p, E0,
                                                     last.etab, n0, reinterpret_cast<C2<T>*>(D),
@@ -225,7 +227,7 @@ hobc_status run_gcv(hobc_plan_s* p, const void* ghat, const void* D, double* gcv
     geo.S = (long long)p->spec_elems;
     geo.chunk = p->gcv_chunk;
     geo.K = p->K;
-    dim3 grid(p->gcv_chunks, p->desc.batch);
+    dim3 grid((unsigned)(p->gcv_chunks * (long long)p->desc.batch));
     const size_t smem = 4 * (size_t)p->gcv_chunk * sizeof(T);
     if (p->fam == FAM_F)
         k_gcv_partials<T, true><<<grid, 256, smem, p->stream>>>(
@@ -245,7 +247,9 @@ template <typename T>
 hobc_status prepare_kernels(hobc_plan_s* p) {
     const int lim = 200 * 1024;
     cudaError_t e = cudaSuccess;
-#define HOBC_SMEM(k) if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
+#define HOBC_SMEM(k)                                                                                \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100)
     HOBC_SMEM((k_pair_analysis<T, FAM_S>));
     HOBC_SMEM((k_pair_analysis<T, FAM_C>));
     HOBC_SMEM((k_pair_analysis<T, FAM_F>));

@@ -115,3 +115,13 @@ def log2_fft(fam: str, shape) -> float:
         M = L if (L >= 8 and L & (L - 1) == 0) else max(8, 1 << int(np.ceil(np.log2(2 * L - 1))))
         out = max(out, np.log2(M))
     return out
+
+
+def sigma(fam: str, shape, inverse: bool = False) -> float:
+    """Largest singular value of the 1D/2D transform T_X (or of T_X^{-1}):
+    the product over axes of ||T_axis||_2 (||T_axis^{-1}||_2)."""
+    out = 1.0
+    for n in shape:
+        sv = np.linalg.svd(O.transform_matrix(fam, n), compute_uv=False)
+        out *= (1.0 / sv.min()) if inverse else sv.max()
+    return float(out)

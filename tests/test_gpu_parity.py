@@ -11,11 +11,17 @@ largest reference entry:
   analysis     FP64 1e-10;  FP32 1e-5
   G(mu_j)      FP64 1e-10;  FP32 1e-5   (relative, every mu)
   argmin       equal, or an index whose oracle G is within the G tolerance of the minimum
-  filter+synthesis  FP64 1e-10; FP32: C eps log2(M) max(|T| |Phi ghat|)
-Layer 2 -- the whole path from g: FP64 1e-10; FP32 forward-error bounds from the
-arithmetic (reading R13): the analysis error delta = C eps log2(M) max(|T^{-1}||g|)
-is magnified by the filter factor kappa = max|d|/(|d|^2+mu|s|^2) and by |T|.
-C = 8 (a small constant of the FFT error bound).
+  filter+synthesis, synthesis   max(flat, eps rb sigma(T) ||X||_2): the norm-wise
+                    rounding bound of an FFT-based product, rb = 16 log2(M) + 2 sum_axes
+                    sqrt(n) (GPU FFT + the oracle's dense products), sigma(T) = ||T||_2
+Layer 2 -- the one-call deblur equals the GPU's own step sequence bit for bit.
+Layer 3 -- the whole path from g: forward-error bounds from the arithmetic
+(reading R13), never below the flat tolerance: the analysis error norm
+delta = min(eps rb ||T^{-1}|| ||g||, the layer-1 analysis tolerance) is magnified
+by the filter factor kappa = max|d|/(|d|^2+mu|s|^2) and by ||T||;
+eps = 2^-53 (FP64) or 2^-24 (FP32).  Where the problem's own
+conditioning exceeds the flat tolerance (tiny mu* with T_X of condition ~1e4),
+the derived bound is the one that applies.
 """
 import numpy as np
 import pytest
@@ -31,7 +37,8 @@ if not torch.cuda.is_available():
 from paper_0906_2704_gb300 import hobc  # noqa: E402  (raises if the library is missing)
 
 TOL = {"fp64": 1e-10, "fp32": 1e-5}
-C_FFT = 8.0
+C_FFT = 16.0     # Bluestein: two FFTs of length M plus the chirp products
+C_DOT = 2.0      # the oracle's dense products: ~sqrt(n) roundings per axis
 
 
 def _dev(a, dtype):
@@ -80,6 +87,9 @@ def run_case(ndim, fam_name, n, taps, L, prec, batch, psf_per_item=False, K=24, 
     npsf = len(hs)
     tol = TOL[prec]
     l2m = P.log2_fft(fam, n)
+    # rounding budget (units of eps) of a transform applied by both sides: the
+    # GPU's FFT (C_FFT log2 M) plus the oracle's dense products (C_DOT sqrt(n) per axis)
+    rb = C_FFT * l2m + C_DOT * sum(np.sqrt(v) for v in n)
     items = range(batch) if check_items is None else check_items
 
     # ---- oracle answers (FP64) on the rounded inputs
@@ -101,21 +111,26 @@ def run_case(ndim, fam_name, n, taps, L, prec, batch, psf_per_item=False, K=24, 
         assert err <= tol, f"analysis item {b}: {err:.3e}"
         dref = P.to_layout(fam, d_o).reshape(dg[0].shape)
         dgot = dg[b if psf_per_item else 0]
+        # both sides sum in FP64 (in different orders): absolute floor ~ eps64 * sum|h|;
+        # FP32 storage adds one rounding relative to each entry
+        floor = 64 * 2.0 ** -53 * np.abs(hs[b if psf_per_item else 0]).sum()
         if prec == "fp64":
-            assert np.abs(dgot - dref).max() <= 1e-12 * np.abs(dref).max(), "eigenvalues"
+            assert np.abs(dgot - dref).max() <= max(1e-12 * np.abs(dref).max(), floor), "eigenvalues"
         else:
-            assert np.all(np.abs(dgot - dref) <= 1e-6 * np.abs(dref) + 1e-37), "eigenvalues"
+            assert np.all(np.abs(dgot - dref) <= 1e-6 * np.abs(dref) + floor), "eigenvalues"
 
-    # ---- layer 1b: GCV and filter+synthesis on identical (rounded oracle) inputs
-    gin = np.zeros((batch, S) + (() if not plan.spec_complex else ()), dtype=complex if plan.spec_complex else float)
+    # ---- layer 1b: GCV, filter+synthesis and synthesis on identical (rounded oracle) inputs
+    sT = P.sigma(fam, n)
+    gin = np.zeros((batch, S), dtype=complex if plan.spec_complex else float)
     din = np.zeros((npsf, S), dtype=gin.dtype)
     full_in = {}
     for i, b in enumerate(items):
         ghat_o, d_o = orc[i][0], orc[i][1]
         gr, dr = _round(ghat_o, dt), _round(d_o, dt)
         full_in[b] = (gr, dr)
-        gin[b] = P.to_layout(fam, gr).reshape(-1)
-        din[b if psf_per_item else 0] = P.to_layout(fam, dr).reshape(-1)
+        cast = (lambda a: a) if plan.spec_complex else np.real
+        gin[b] = cast(P.to_layout(fam, gr).reshape(-1))
+        din[b if psf_per_item else 0] = cast(P.to_layout(fam, dr).reshape(-1))
     G_d = torch.empty((batch, K), dtype=torch.float64, device="cuda")
     mi_d = torch.empty(batch, dtype=torch.int32, device="cuda")
     gin_d = _spec_dev(gin, plan, dt)
@@ -124,7 +139,9 @@ def run_case(ndim, fam_name, n, taps, L, prec, batch, psf_per_item=False, K=24, 
     mi_fix = np.array([orc[list(items).index(b)][4] if b in items else 0 for b in range(batch)], dtype=np.int32)
     f_d = torch.empty(g.shape, dtype=tdt, device="cuda")
     plan.filter_synthesis(gin_d, din_d, _dev(mi_fix, np.int32), f_d)
-    G, mi, f = G_d.cpu().numpy(), mi_d.cpu().numpy(), f_d.cpu().numpy()
+    y_d = torch.empty(g.shape, dtype=tdt, device="cuda")
+    plan.synthesis(gin_d, y_d)
+    G, mi, f, y = G_d.cpu().numpy(), mi_d.cpu().numpy(), f_d.cpu().numpy(), y_d.cpu().numpy()
     for i, b in enumerate(items):
         s_o = orc[i][2]
         gr, dr = full_in[b]
@@ -136,49 +153,51 @@ def run_case(ndim, fam_name, n, taps, L, prec, batch, psf_per_item=False, K=24, 
         assert k == kref or Gref[k] <= (1 + tol) * Gref.min(), f"argmin {k} vs {kref}"
         X = O.filter_factors(dr, s_o, mus[mi_fix[b]]) * gr
         fref = P.oracle_filtered(fam, ndim, gr, dr, s_o, mus[mi_fix[b]])
-        bound = tol * np.abs(fref).max() if prec == "fp64" else C_FFT * eps * l2m * P.abs_apply(fam, X).max()
+        bound = max(tol * np.abs(fref).max(), rb * eps * sT * np.linalg.norm(X))
         ferr = np.abs(f[b] - fref).max()
         assert ferr <= bound, f"filter+synthesis item {b}: {ferr:.3e} > {bound:.3e}"
+        yref = (O.synthesis_1d(fam, gr) if ndim == 1 else O.synthesis_2d(fam, gr)).real
+        ybound = max(tol * np.abs(yref).max(), rb * eps * sT * np.linalg.norm(gr))
+        yerr = np.abs(y[b] - yref).max()
+        assert yerr <= ybound, f"synthesis item {b}: {yerr:.3e} > {ybound:.3e}"
 
-    # ---- layer 2: the whole path from g (one call, plus the round trip)
+    # ---- layer 2: the one-call path equals the GPU's own step sequence, bit for bit
+    f1_d = torch.empty(g.shape, dtype=tdt, device="cuda")
+    mi1_d = torch.empty(batch, dtype=torch.int32, device="cuda")
+    G1_d = torch.empty((batch, K), dtype=torch.float64, device="cuda")
+    plan.gcv(gh_d, d_d, G1_d, mi1_d)
+    plan.filter_synthesis(gh_d, d_d, mi1_d, f1_d)
     f2_d = torch.empty(g.shape, dtype=tdt, device="cuda")
     mi2_d = torch.empty(batch, dtype=torch.int32, device="cuda")
     G2_d = torch.empty((batch, K), dtype=torch.float64, device="cuda")
     plan.deblur(g_d, psf_d, f2_d, mi2_d, G2_d)
-    y_d = torch.empty(g.shape, dtype=tdt, device="cuda")
-    plan.synthesis(gh_d, y_d)
-    f2, mi2, G2, y = f2_d.cpu().numpy(), mi2_d.cpu().numpy(), G2_d.cpu().numpy(), y_d.cpu().numpy()
+    assert torch.equal(f2_d, f1_d) and torch.equal(mi2_d, mi1_d) and torch.equal(G2_d, G1_d)
+
+    # ---- layer 3: the whole path from g against the oracle.  The analysis error
+    # norm is bounded by what layer 1 asserted (tol * max|ghat| per entry) and by the
+    # FFT bound through ||T^{-1}||; it is magnified by the filter (kappa) and by T.
+    f2, mi2, G2 = f2_d.cpu().numpy(), mi2_d.cpu().numpy(), G2_d.cpu().numpy()
+    sTi = P.sigma(fam, n, inverse=True)
     for i, b in enumerate(items):
         ghat_o, d_o, s_o, G_o, k_o = orc[i]
-        delta = C_FFT * eps * l2m * P.abs_apply(fam, g[b], inverse=True).max()   # analysis error bound
+        delta = min(rb * eps * sTi * np.linalg.norm(g[b]), tol * np.abs(ghat_o).max() * np.sqrt(ghat_o.size))
         k = int(mi2[b])
-        if prec == "fp64":
-            assert np.max(np.abs(G2[b] - G_o) / G_o) <= tol, "end-to-end G"
-            assert k == k_o or G_o[k] <= (1 + tol) * G_o.min(), "end-to-end argmin"
-        else:
-            a2 = np.abs(d_o) ** 2
-            gbs = []
-            for j, mu in enumerate(mus):
-                sig = np.abs(s_o) ** 2 / (a2 + mu * np.abs(s_o) ** 2)
-                num = np.sum(sig * sig * np.abs(ghat_o) ** 2)
-                gb = (2 * delta * np.sum(sig * sig * np.abs(ghat_o)) + delta ** 2 * np.sum(sig * sig)) / num + tol
-                gbs.append(gb)
-                assert abs(G2[b, j] - G_o[j]) <= gb * G_o[j], f"end-to-end G mu {j}: bound {gb:.2e}"
-            assert k == k_o or G_o[k] <= (1 + 2 * max(gbs)) * G_o.min(), "end-to-end argmin"
+        a2 = np.abs(d_o) ** 2
+        gbs = []
+        for j, mu in enumerate(mus):
+            sig = np.abs(s_o) ** 2 / (a2 + mu * np.abs(s_o) ** 2)
+            num = np.sum(sig * sig * np.abs(ghat_o) ** 2)
+            gb = max(tol, (2 * np.sqrt(np.sum(sig ** 4 * np.abs(ghat_o) ** 2)) * delta + sig.max() ** 2 * delta ** 2)
+                     / num + (tol if prec == "fp32" else 0.0))
+            gbs.append(gb)
+            assert abs(G2[b, j] - G_o[j]) <= gb * G_o[j], f"end-to-end G mu {j}: bound {gb:.2e}"
+        assert k == k_o or G_o[k] <= (1 + 2 * max(gbs)) * G_o.min(), "end-to-end argmin"
         fo = P.oracle_filtered(fam, ndim, ghat_o, d_o, s_o, mus[k])
-        if prec == "fp64":
-            bound = tol * np.abs(fo).max()
-            ybound = tol * np.abs(g[b]).max()
-        else:
-            kappa = P.amplification(d_o, s_o, mus[k])
-            X = O.filter_factors(d_o, s_o, mus[k]) * ghat_o
-            bound = (C_FFT * eps * l2m * P.abs_apply(fam, X).max()
-                     + P.abs_norm(fam, n) * kappa * delta)
-            ybound = C_FFT * eps * l2m * P.abs_apply(fam, ghat_o).max() + P.abs_norm(fam, n) * delta
+        kappa = P.amplification(d_o, s_o, mus[k])
+        X = O.filter_factors(d_o, s_o, mus[k]) * ghat_o
+        bound = max(tol * np.abs(fo).max(), rb * eps * sT * np.linalg.norm(X) + sT * kappa * delta)
         ferr = np.abs(f2[b] - fo).max()
         assert ferr <= bound, f"end-to-end f item {b}: {ferr:.3e} > {bound:.3e}"
-        yerr = np.abs(y[b] - g[b]).max()
-        assert yerr <= ybound, f"round trip item {b}: {yerr:.3e} > {ybound:.3e}"
     return plan
 
 
