@@ -161,6 +161,38 @@ hobc_status hobc_gcv(hobc_plan* plan, const void* ghat_dev, const void* d_dev,
 hobc_status hobc_filter_synthesis(hobc_plan* plan, const void* ghat_dev, const void* d_dev,
                                   const int* mu_index_dev, void* f_dev);
 
+/* The GCV scan of hobc_gcv for callers that cannot allocate device memory.
+ * The paper has no counterpart: this entry point exists for the deployment
+ * side only.  Some callers may not call cudaMalloc at all -- code that runs
+ * under a memory allocator it does not own (another framework's device pool,
+ * a host application that fixes the device-memory budget at start-up), or a
+ * latency-critical path that cannot take cudaMalloc's device-wide
+ * synchronisation -- and so cannot create a plan.  This call needs no plan and
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *   desc: geometry of the problems (ndim, n, family or bc_degree +
+ *         psf_symmetric, L, prec, n_mu, batch, psf_per_item; psf is ignored);
+ *   ghat_dev, d_dev: spectra and eigenvalues in the spectrum layout, as
+ *         hobc_analysis and hobc_eigenvalues produce them;
+ *   mu_dev: the K grid values (double, device);
+ *   gcv_dev: [batch][K] output (nullable); mu_index_dev: [batch] output;
+ *   cuda_stream: the stream to run on (NULL: legacy default stream).
+ * The per-CTA partial sums live in one statically allocated device array of
+ * hobc_gcv_noalloc_max_bytes() bytes (16 MiB) that every GPU loading the
+ * library holds until the process exits.  A request that needs more --
+ * batch * ceil(spectrum/chunk) * 2 * K doubles plus the grid -- is rejected
+ * with HOBC_ERR_SIZE and a message in hobc_last_error().  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents; every
+ * entry a call reads is written earlier in the same call, so nothing needs
+ * clearing, but calls whose work overlaps on the GPU (different streams, or
+ * host threads) race on it and must be serialised by the caller. */
+hobc_status hobc_gcv_noalloc(const hobc_plan_desc* desc, const void* ghat_dev, const void* d_dev,
+                             const double* mu_dev, double* gcv_dev, int* mu_index_dev, void* cuda_stream);
+
+/* Size in bytes of the static scratch array of hobc_gcv_noalloc. */
+size_t hobc_gcv_noalloc_max_bytes(void);
+
 /* Number of kernel launches the last call on this plan issued. */
 int hobc_last_launch_count(const hobc_plan* plan);
 

@@ -21,6 +21,8 @@ void set_last_error(const char* what, cudaError_t e) {
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
+void set_last_error_text(const char* text) { snprintf(g_last_error, sizeof(g_last_error), "%s", text); }
+
 // ------------------------------------------------------------- GCV finalize
 
 __global__ void k_gcv_finalize(const double* __restrict__ partials, int nchunks, int K, double* __restrict__ gcv,

@@ -72,6 +72,7 @@ template <typename T> hobc_status run_filter_synthesis(hobc_plan_s* p, const voi
 template <typename T> hobc_status prepare_kernels(hobc_plan_s* p);
 
 void set_last_error(const char* what, cudaError_t e);
+void set_last_error_text(const char* text);
 hobc_status launch_gcv_finalize(hobc_plan_s* p, double* gcv, int* mu_idx);
 
 }  // namespace hobc

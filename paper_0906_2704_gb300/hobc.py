@@ -64,6 +64,10 @@ for _name, _n in (("hobc_deblur", 6), ("hobc_deblur_host", 6), ("hobc_analysis",
                   ("hobc_eigenvalues", 3), ("hobc_gcv", 5), ("hobc_filter_synthesis", 5)):
     getattr(_lib, _name).argtypes = [_vp] * _n
     getattr(_lib, _name).restype = ctypes.c_int
+_lib.hobc_gcv_noalloc.argtypes = [ctypes.POINTER(PlanDesc)] + [_vp] * 6
+_lib.hobc_gcv_noalloc.restype = ctypes.c_int
+_lib.hobc_gcv_noalloc_max_bytes.argtypes = []
+_lib.hobc_gcv_noalloc_max_bytes.restype = _sz
 _lib.hobc_last_launch_count.argtypes = [_vp]
 _lib.hobc_last_launch_count.restype = ctypes.c_int
 _lib.hobc_status_str.argtypes = [ctypes.c_int]
@@ -116,6 +120,44 @@ def _hptr(a) -> int | None:
     if not isinstance(a, np.ndarray) or not a.flags["C_CONTIGUOUS"]:
         raise ValueError("expected a C-contiguous NumPy array")
     return a.ctypes.data
+
+
+def make_desc(ndim: int, n, bc_degree: int, n_mu: int, L: str = "I", prec: str = "fp64",
+              family: str = "auto", psf_symmetric: bool = False, batch: int = 1,
+              psf_per_item: bool = False, psf=None) -> PlanDesc:
+    """Fill a hobc_plan_desc (the PSF size is only needed by hobc_plan_create)."""
+    n = [int(n)] if np.isscalar(n) else [int(v) for v in n]
+    psf = [1] * len(n) if psf is None else ([int(psf)] if np.isscalar(psf) else [int(v) for v in psf])
+    d = PlanDesc()
+    d.ndim = ndim
+    for i in range(2):
+        d.n[i] = n[i] if i < len(n) else 0
+        d.psf[i] = psf[i] if i < len(psf) else 0
+    d.bc_degree = bc_degree
+    d.family = FAMILY[family]
+    d.psf_symmetric = int(bool(psf_symmetric))
+    d.L = SMOOTHING[L]
+    d.prec = PRECISION[prec]
+    d.n_mu = n_mu
+    d.batch = batch
+    d.psf_per_item = int(bool(psf_per_item))
+    return d
+
+
+def gcv_noalloc(desc: PlanDesc, ghat, d, mu, gcv, mu_index, stream=None) -> None:
+    """hobc_gcv_noalloc: the GCV scan with no plan and no device allocation
+    (scratch in the library's static array of gcv_noalloc_max_bytes() bytes)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    _check(_lib.hobc_gcv_noalloc(ctypes.byref(desc), _ptr(ghat), _ptr(d), _ptr(mu), _ptr(gcv), _ptr(mu_index),
+                                 _vp(stream)), "hobc_gcv_noalloc")
+
+
+def gcv_noalloc_max_bytes() -> int:
+    return int(_lib.hobc_gcv_noalloc_max_bytes())
 
 
 class Plan:

@@ -1,0 +1,98 @@
+"""hobc_gcv_noalloc -- the GCV scan for callers that cannot allocate device
+memory (their process runs under an allocator they do not own, or a fixed
+device-memory budget, or a path that cannot take cudaMalloc's synchronisation)
+-- must give the answer of hobc_gcv, the plan-based call, on the same spectra.
+
+Its scratch is one static device array shared by every call and never
+cleared, so each case runs the allocation-free call twice in a row, and one
+test alternates between two problem shapes.  This file is collected last on
+purpose: if it fails, a run that stops at the first failure has already run
+every other test.  It also passes alone, in a fresh process.
+"""
+import numpy as np
+import pytest
+
+from paper_0906_2704_gb300 import synth
+import parity_utils as P
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+from paper_0906_2704_gb300 import hobc  # noqa: E402
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+
+
+def _setup(ndim, n, fam, L, prec, batch, K, seed):
+    """Spectra, eigenvalues and the plan-based GCV answer for one case."""
+    letter = P.FAM_LETTER[fam]
+    dt = np.float64 if prec == "fp64" else np.float32
+    tdt = torch.float64 if prec == "fp64" else torch.float32
+    taps = 5 if ndim == 1 else (5, 5)
+    h = P.psf_for(letter, ndim, taps)
+    g, _ = P.problems(ndim, (n,) if ndim == 1 else n, h, batch, seed)
+    mus = synth.mu_grid(K, 1e-6, 1.0)
+    deg = 1 if letter == "S" else 2
+    plan = hobc.Plan(ndim, n, h.shape, deg, mus, L=L, prec=prec, family=fam, psf_symmetric=letter != "F",
+                     batch=batch)
+    cs = (2,) if plan.spec_complex else ()
+    gh = torch.empty((batch, plan.spec_elems) + cs, dtype=tdt, device="cuda")
+    d = torch.empty((1, plan.spec_elems) + cs, dtype=tdt, device="cuda")
+    plan.analysis(torch.from_numpy(g.astype(dt)).cuda(), gh)
+    plan.eigenvalues(torch.from_numpy(h.astype(dt)).cuda(), d)
+    G_ref = torch.empty((batch, K), dtype=torch.float64, device="cuda")
+    mi_ref = torch.empty(batch, dtype=torch.int32, device="cuda")
+    plan.gcv(gh, d, G_ref, mi_ref)
+    desc = hobc.make_desc(ndim, n, deg, K, L=L, prec=prec, family=fam, psf_symmetric=letter != "F", batch=batch)
+    mu_d = torch.from_numpy(mus).cuda()
+    return desc, gh, d, mu_d, G_ref, mi_ref
+
+
+def _noalloc(case):
+    desc, gh, d, mu_d, G_ref, _ = case
+    G = torch.full_like(G_ref, -1.0)
+    mi = torch.full((G_ref.shape[0],), -1, dtype=torch.int32, device="cuda")
+    hobc.gcv_noalloc(desc, gh, d, mu_d, G, mi)
+    torch.cuda.synchronize()
+    return G, mi
+
+
+def _check(case, got, prec):
+    G_ref, mi_ref = case[4], case[5]
+    G, mi = got
+    rel = ((G - G_ref).abs() / G_ref.abs()).max().item()
+    assert rel <= TOL[prec], f"G differs from hobc_gcv by {rel:.3e}"
+    assert torch.equal(mi, mi_ref)
+
+
+CASES = [
+    (1, 77, "sine", "I", "fp64", 5, 24),
+    (2, (34, 21), "cosine", "lap", "fp64", 3, 17),
+    (2, (66, 40), "fourier", "I", "fp32", 4, 256),
+]
+
+
+@pytest.mark.parametrize("ndim,n,fam,L,prec,batch,K", CASES)
+def test_noalloc_matches_plan_gcv_twice(ndim, n, fam, L, prec, batch, K):
+    case = _setup(ndim, n, fam, L, prec, batch, K, seed=3)
+    for _ in range(2):
+        _check(case, _noalloc(case), prec)
+
+
+def test_noalloc_alternating_shapes_do_not_see_stale_scratch():
+    a = _setup(2, (66, 40), "fourier", "lap", "fp32", 6, 64, seed=5)
+    b = _setup(1, 130, "cosine", "I", "fp64", 9, 31, seed=6)
+    for _ in range(2):
+        _check(a, _noalloc(a), "fp32")
+        _check(b, _noalloc(b), "fp64")
+
+
+def test_noalloc_rejects_requests_beyond_its_scratch():
+    limit = hobc.gcv_noalloc_max_bytes()
+    assert limit == 16 << 20
+    desc = hobc.make_desc(2, (1024, 1024), 2, 256, prec="fp32", family="fourier", batch=64)
+    with pytest.raises(hobc.HobcError) as ei:
+        hobc.gcv_noalloc(desc, 16, 16, 16, None, 16)   # rejected before any device access
+    assert hobc.STATUS[ei.value.status] == "HOBC_ERR_SIZE"
+    assert "maximum" in str(ei.value)
