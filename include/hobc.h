@@ -98,7 +98,7 @@ typedef struct {
 typedef struct hobc_plan_s hobc_plan;
 
 /* Create a plan.  desc: problem description (copied).  mu_grid_host: K positive
- * finite doubles (copied).  cuda_stream: a cudaStream_t on the current device,
+ * finite doubles (copied); FP32 plans need every mu in [1e-18, 1e18].  cuda_stream: a cudaStream_t on the current device,
  * or NULL for the legacy default stream.  Allocates the plan's device workspace
  * and tables (cudaMalloc); synchronous.  On error *out is set to NULL. */
 hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_host,
@@ -173,7 +173,8 @@ hobc_status hobc_filter_synthesis(hobc_plan* plan, const void* ghat_dev, const v
  *         psf_symmetric, L, prec, n_mu, batch, psf_per_item; psf is ignored);
  *   ghat_dev, d_dev: spectra and eigenvalues in the spectrum layout, as
  *         hobc_analysis and hobc_eigenvalues produce them;
- *   mu_dev: the K grid values (double, device);
+ *   mu_dev: the K grid values (double, device; FP32: each in [1e-18, 1e18],
+ *         not checked here because they live on the device);
  *   gcv_dev: [batch][K] output (nullable); mu_index_dev: [batch] output;
  *   cuda_stream: the stream to run on (NULL: legacy default stream).
  * The per-CTA partial sums live in one statically allocated device array of

@@ -9,6 +9,7 @@
 
 #include "hobc_internal.h"
 #include "hobc_device.cuh"
+#include "hobc_kernels.cuh"
 
 using hobc::AxisHost;
 typedef std::complex<double> cd;
@@ -295,6 +296,8 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
     for (int j = 0; j < d.n_mu; ++j) {
         if (!std::isfinite(mu_grid_host[j])) return HOBC_ERR_NONFINITE;
         if (!(mu_grid_host[j] > 0)) return HOBC_ERR_ARG;
+        // FP32 GCV pairs grid values: (a + mu1)(a + mu2) must stay a normal float
+        if (d.prec == HOBC_FP32 && (mu_grid_host[j] < 1e-18 || mu_grid_host[j] > 1e18)) return HOBC_ERR_ARG;
     }
     int fam = d.family;
     if (d.bc_degree != 1 && d.bc_degree != 2) return HOBC_ERR_UNSUPPORTED;
@@ -330,7 +333,7 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
     p->img_elems = d.ndim == 1 ? (size_t)d.n[0] : (size_t)d.n[0] * d.n[1];
     p->psf_elems = d.ndim == 1 ? (size_t)d.psf[0] : (size_t)d.psf[0] * d.psf[1];
     p->npsf = d.psf_per_item ? d.batch : 1;
-    p->gcv_chunk = (int)std::min<size_t>(p->spec_elems, d.prec == HOBC_FP64 ? 1024 : 2048);
+    p->gcv_chunk = hobc::gcv_chunk_for((long long)p->spec_elems, p->K, d.prec == HOBC_FP64);
     p->gcv_chunks = (int)((p->spec_elems + p->gcv_chunk - 1) / p->gcv_chunk);
     const size_t B = (size_t)d.batch;
     auto alloc = [&](void** ptr, size_t bytes) {

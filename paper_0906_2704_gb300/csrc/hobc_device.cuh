@@ -108,10 +108,23 @@ __device__ __forceinline__ void fft_stage(C2<T>* buf, int M, int Ns, const C2<T>
         const int j = t + u * tpg;
         const int k = j & (Ns - 1);
         const int step = (M / (Ns * R)) * k;
+        // twiddles W^{r step}: load W^step, W^{2 step}, W^{4 step}; form the rest
+        // with one complex product each (two roundings at most)
+        C2<T> w[8];
+        if (Ns > 1) {
+            w[1] = tw[step];
+            if (R >= 4) { w[2] = tw[2 * step]; w[3] = cmul<T>(w[1], w[2]); }
+            if (R == 8) {
+                w[4] = tw[4 * step];
+                w[5] = cmul<T>(w[1], w[4]);
+                w[6] = cmul<T>(w[2], w[4]);
+                w[7] = cmul<T>(w[3], w[4]);
+            }
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             C2<T> x = buf[pidx(j + r * nb)];
-            if (r > 0 && Ns > 1) x = cmul<T>(x, tw[r * step]);
+            if (r > 0 && Ns > 1) x = cmul<T>(x, w[r]);
             v[u * R + r] = x;
         }
         if (R == 8) dft8<T>(v + u * R);

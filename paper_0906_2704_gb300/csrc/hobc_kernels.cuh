@@ -453,9 +453,9 @@ __global__ void k_eig(const T* __restrict__ psf, long long psf_stride, int p0, i
 // pair, else 1), e = w |ghat|^2, a = |d|^2 / |s|^2 (elements with s = 0 have
 // sigma = 0 and are dropped).  For each mu of the grid,
 //   sigma = 1/(a + mu),  num += e sigma^2,  den += w sigma.
-// Each thread takes four grid values, in two pairs that each share one
-// reciprocal: r = 1/((a+mu1)(a+mu2)), sigma1 = (a+mu2) r, sigma2 = (a+mu1) r.
-// FP32: terms summed in float over runs of 256 elements, then in double.
+// Grid values are taken in pairs that share one reciprocal:
+// r = 1/((a+mu1)(a+mu2)), sigma1 = (a+mu2) r, sigma2 = (a+mu1) r.
+// In FP32 that needs mu >= 1e-18 and a <= 1e18 so the product stays normal.
 // grid = chunks * items (item-major), block = 256; partials[item][chunk][2K].
 // =====================================================================
 struct GcvGeom {
@@ -482,6 +482,123 @@ __device__ __forceinline__ double pair_rcp(double x) { return 1.0 / x; }
 
 // largest a kept in FP32 so that (a + mu1)(a + mu2) cannot overflow
 template <typename T> __device__ __forceinline__ T a_cap() { return sizeof(T) == 4 ? (T)1e18 : (T)1e150; }
+
+// The mu loop of the GCV scan over the packed elements of one CTA.  Threads
+// that share a group of grid values (tpm of them, adjacent lanes) split the
+// elements and combine their sums with shuffles.
+
+// Elements per CTA of the GCV scan.  In FP32 every thread sums its share of
+// the chunk in float and converts to double once, so a chunk holds at most
+// 256 elements per thread of a grid-value group; FP64 sums in double.
+__host__ __device__ inline int gcv_threads_per_group(int K, bool fp64) {
+    const int per = fp64 ? 4 : 8;            // grid values per thread
+    const int groups = (K + per - 1) / per;
+    int tpm = 1;
+    while (tpm * 2 <= 32 && tpm * 2 * groups <= 256) tpm *= 2;
+    return tpm;
+}
+__host__ __device__ inline int gcv_chunk_for(long long S, int K, bool fp64) {
+    const long long cap = fp64 ? 1024 : (long long)min(2048, 256 * gcv_threads_per_group(K, false));
+    return (int)(S < cap ? S : cap);
+}
+
+// FP64: four grid values per thread, two reciprocal-sharing pairs.
+__device__ __forceinline__ void gcv_scan(const double4* __restrict__ pk, int cnt, const double* __restrict__ muT,
+                                         int K, double* __restrict__ outp) {
+    const int NQ = (K + 3) / 4;
+    const int tpm = gcv_threads_per_group(K, true);
+    const int qpp = blockDim.x / tpm;
+    const int sub = threadIdx.x % tpm;
+    for (int base = 0; base < NQ; base += qpp) {
+        const int j0 = 4 * (base + threadIdx.x / tpm);
+        double mu[4], nd[4] = {0, 0, 0, 0}, dd[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) mu[u] = j0 + u < K ? muT[j0 + u] : 1.0;
+        for (int i = sub; i < cnt; i += tpm) {
+            const double4 v = pk[i];
+#pragma unroll
+            for (int u = 0; u < 4; u += 2) {
+                const double t1 = v.x + mu[u], t2 = v.x + mu[u + 1];
+                const double r = 1.0 / (t1 * t2);
+                const double s1 = t2 * r, s2 = t1 * r;
+                dd[u] += v.z * s1;
+                dd[u + 1] += v.z * s2;
+                nd[u] += v.y * s1 * s1;
+                nd[u + 1] += v.y * s2 * s2;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            for (int off = tpm / 2; off > 0; off >>= 1) {
+                nd[u] += __shfl_down_sync(0xffffffffu, nd[u], off, tpm);
+                dd[u] += __shfl_down_sync(0xffffffffu, dd[u], off, tpm);
+            }
+        if (sub == 0)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (j0 + u < K) { outp[j0 + u] = nd[u]; outp[K + j0 + u] = dd[u]; }
+    }
+}
+
+// FP32: eight grid values per thread in packed f32x2 lanes.  Lanes hold
+// (mu0, mu2) / (mu1, mu3) and (mu4, mu6) / (mu5, mu7), so one packed product
+// forms both shared denominators of a pair of pairs and each packed op
+// advances two evaluations; one rcp.approx per two evaluations.  A thread's
+// terms (at most 256 elements, see gcv_chunk_for) are summed in float, then
+// combined across threads in double.
+__device__ __forceinline__ void gcv_scan(const float4* __restrict__ pk, int cnt, const float* __restrict__ muT,
+                                         int K, double* __restrict__ outp) {
+    const int NO = (K + 7) / 8;
+    const int tpm = gcv_threads_per_group(K, false);
+    const int opp = blockDim.x / tpm;
+    const int sub = threadIdx.x % tpm;
+    for (int base = 0; base < NO; base += opp) {
+        const int j0 = 8 * (base + threadIdx.x / tpm);
+        float mu[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) mu[u] = j0 + u < K ? muT[j0 + u] : 1.0f;
+        const float2 mA[2] = {make_float2(mu[0], mu[2]), make_float2(mu[4], mu[6])};
+        const float2 mB[2] = {make_float2(mu[1], mu[3]), make_float2(mu[5], mu[7])};
+        const float2 z = make_float2(0.f, 0.f);
+        float2 NA[2] = {z, z}, NB[2] = {z, z}, DA[2] = {z, z}, DB[2] = {z, z};
+#pragma unroll 4
+        for (int i = sub; i < cnt; i += tpm) {
+            const float4 v = pk[i];
+            const float2 aa = make_float2(v.x, v.x), ee = make_float2(v.y, v.y), ww = make_float2(v.z, v.z);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float2 A = __fadd2_rn(aa, mA[h]);
+                const float2 B = __fadd2_rn(aa, mB[h]);
+                const float2 P = __fmul2_rn(A, B);
+                const float2 R = make_float2(pair_rcp(P.x), pair_rcp(P.y));
+                const float2 SA = __fmul2_rn(B, R);      // sigma of the A lanes
+                const float2 SB = __fmul2_rn(A, R);      // sigma of the B lanes
+                DA[h] = __ffma2_rn(ww, SA, DA[h]);
+                DB[h] = __ffma2_rn(ww, SB, DB[h]);
+                NA[h] = __ffma2_rn(__fmul2_rn(ee, SA), SA, NA[h]);
+                NB[h] = __ffma2_rn(__fmul2_rn(ee, SB), SB, NB[h]);
+            }
+        }
+        double nd[8], dd[8];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            nd[4 * h + 0] = NA[h].x; nd[4 * h + 2] = NA[h].y;
+            nd[4 * h + 1] = NB[h].x; nd[4 * h + 3] = NB[h].y;
+            dd[4 * h + 0] = DA[h].x; dd[4 * h + 2] = DA[h].y;
+            dd[4 * h + 1] = DB[h].x; dd[4 * h + 3] = DB[h].y;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            for (int off = tpm / 2; off > 0; off >>= 1) {
+                nd[u] += __shfl_down_sync(0xffffffffu, nd[u], off, tpm);
+                dd[u] += __shfl_down_sync(0xffffffffu, dd[u], off, tpm);
+            }
+        if (sub == 0)
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (j0 + u < K) { outp[j0 + u] = nd[u]; outp[K + j0 + u] = dd[u]; }
+    }
+}
 
 template <typename T, bool CPLX>
 __global__ void __launch_bounds__(256)
@@ -524,54 +641,8 @@ k_gcv_partials(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typena
         pk[i] = v;
     }
     __syncthreads();
-    const int K = geo.K;
-    const int NQ = (K + 3) / 4;                 // quads of grid values (two shared-reciprocal pairs)
-    int tpm = 1;                                // threads per quad: a power of two <= 32
-    while (tpm * 2 <= 32 && tpm * 2 * NQ <= (int)blockDim.x) tpm *= 2;
-    const int qpp = blockDim.x / tpm;
-    const int sub = threadIdx.x % tpm;
-    double* outp = partials + (long long)blockIdx.x * 2LL * K;
-    for (int base = 0; base < NQ; base += qpp) {
-        const int j0 = 4 * (base + threadIdx.x / tpm);
-        T mu[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) mu[u] = j0 + u < K ? muT[j0 + u] : (T)1;
-        double nd[4] = {0, 0, 0, 0}, dd[4] = {0, 0, 0, 0};
-        const int run = sizeof(T) == 4 ? 256 * tpm : (1 << 30);
-        for (int i0 = sub; i0 < cnt; i0 += run) {
-            const int iend = min(cnt, i0 + run);
-            T fn[4] = {0, 0, 0, 0}, fd[4] = {0, 0, 0, 0};
-#pragma unroll 2
-            for (int i = i0; i < iend; i += tpm) {
-                const P4 v = pk[i];
-#pragma unroll
-                for (int u = 0; u < 4; u += 2) {
-                    const T t1 = v.x + mu[u], t2 = v.x + mu[u + 1];
-                    const T r = pair_rcp(t1 * t2);
-                    const T s1 = t2 * r, s2 = t1 * r;
-                    fd[u] += v.z * s1;
-                    fd[u + 1] += v.z * s2;
-                    const T q1 = v.y * s1, q2 = v.y * s2;
-                    fn[u] += q1 * s1;
-                    fn[u + 1] += q2 * s2;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) { nd[u] += fn[u]; dd[u] += fd[u]; }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            for (int off = tpm / 2; off > 0; off >>= 1) {
-                nd[u] += __shfl_down_sync(0xffffffffu, nd[u], off, tpm);
-                dd[u] += __shfl_down_sync(0xffffffffu, dd[u], off, tpm);
-            }
-        }
-        if (sub == 0) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (j0 + u < K) { outp[j0 + u] = nd[u]; outp[K + j0 + u] = dd[u]; }
-        }
-    }
+    double* outp = partials + (long long)blockIdx.x * 2LL * geo.K;
+    gcv_scan(pk, cnt, muT, geo.K, outp);
 }
 
 // G(mu_j) = num_j / den_j^2 and the first index of the minimum (NaN never wins).

@@ -101,7 +101,7 @@ extern "C" hobc_status hobc_gcv_noalloc(const hobc_plan_desc* desc, const void* 
     const int Nl = nl - 2;
     const int Wl = fam == HOBC_FAMILY_FOURIER ? Nl / 2 + 3 : nl;
     const long long S = dsc.ndim == 1 ? (long long)Wl : (long long)Wl * dsc.n[0];
-    const int chunk = (int)std::min<long long>(S, dsc.prec == HOBC_FP64 ? 1024 : 2048);
+    const int chunk = hobc::gcv_chunk_for(S, dsc.n_mu, dsc.prec == HOBC_FP64);
     const long long chunks = (S + chunk - 1) / chunk;
     const size_t esz = dsc.prec == HOBC_FP64 ? 8 : 4;
     const size_t mu_bytes = ((size_t)dsc.n_mu * esz + 255) / 256 * 256;

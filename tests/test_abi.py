@@ -53,6 +53,7 @@ def _create(hobc, **kw):
     (dict(mu_grid=[1e-3, float("nan")]), "HOBC_ERR_NONFINITE"),
     (dict(mu_grid=[1e-3, float("inf")]), "HOBC_ERR_NONFINITE"),
     (dict(batch=0), "HOBC_ERR_ARG"),
+    (dict(prec="fp32", mu_grid=[1e-20, 1.0]), "HOBC_ERR_ARG"),   # FP32 pairs grid values: mu >= 1e-18
     (dict(ndim=3), "HOBC_ERR_ARG"),
 ])
 def test_plan_validation_rejects_bad_descriptions(hobc, kw, status):
