@@ -17,6 +17,8 @@ Families (per axis):
   'S'  antireflective BC, degree 1 (Sec. 2.2, Eq. (eq:ART), Eq. (eq:jcf))
   'C'  quadratic-preserving, cosine basis, symmetric PSF (Sec. 3.1, Eq. (eq:Tc), (eq:Ac))
   'F'  quadratic-preserving, Fourier basis, any PSF (Sec. 3.2, Eq. (eq:Tf), (eq:Af))
+  'S3' cubic-preserving, sine basis, symmetric PSF: degree 3, which the paper
+      only names (Sec. 1 "quadratic or cubic", Sec. 7); built as reading R6 below.
 Comparison (classical) families, used by the pins:
   'P'  periodic (Sec. 2.1, Eq. (eq:permat));  'R' reflective (Sec. 2.1, Eq. (eq:refm))
 
@@ -29,6 +31,10 @@ DESIGN.md):
   R4  the A_F grid is x_i = (i-2) 2 pi/(n-2) (the text says "circulant of order n-2").
   R8  2D Laplacian = Kronecker sum, s(t0, t1) = s(t0) + s(t1) (5-point stencil).
   R10 argmin ties -> lowest index (smallest mu).
+  R6  degree 3 ('S3'): DST-I of order N = n-4 on x_i = i pi/(N+1), i = -1..N+2,
+      extended oddly (rows i = 0, N+1 are zero, rows i = -1, N+2 are minus rows 1, N);
+      border columns L1 = (x_{N+1}-x)(x_{N+2}-x), L2 = L1 (x_{N+2}-x) and their flips,
+      each of unit norm, with eigenvalue z(0); together they span the cubics.
   GCV with complex spectra uses |sigma_i ghat_i|^2 (Eq. (eq:gcv2) is written for
       real data).
 
@@ -124,6 +130,17 @@ def border_vector(family: str, n: int) -> np.ndarray:
     return qt / np.linalg.norm(qt)
 
 
+def cubic_border_columns(n: int):
+    """L1, L2 of the degree-3 transform (reading R6), unit 2-norm, on the grid
+    x_i = i pi/(N+1), i = -1..N+2 (array index i+1), N = n-4."""
+    N = n - 4
+    x = np.arange(-1, N + 3) * np.pi / (N + 1)
+    xa, xb = np.pi, (N + 2) * np.pi / (N + 1)          # x_{N+1}, x_{N+2}
+    L1 = (xa - x) * (xb - x)
+    L2 = L1 * (xb - x)
+    return L1 / np.linalg.norm(L1), L2 / np.linalg.norm(L2)
+
+
 def extended_grid(family: str, n: int):
     """Grid x_0..x_{n-1} and interval [a, b] of the basis functions (Sec. 3, remark)."""
     N = n - 2
@@ -148,6 +165,7 @@ def eigen_angles(family: str, n: int) -> np.ndarray:
     'S': y_i = (i-1) pi/(n-1), i = 1..n-1, y_n = 0        (Eq. (eq:jcf))
     'C': x_1 = x_n = 0, x_i = (i-2) pi/(n-2)              (Eq. (eq:Ac))
     'F': x_1 = x_n = 0, x_i = (i-2) 2 pi/(n-2)            (Eq. (eq:Af), reading R4)
+    'S3': border columns 1, 2, n-1, n at 0, the others (i-2) pi/(n-3)   (reading R6)
     'P': x_i = 2 (i-1) pi/n                               (Eq. (eq:permat))
     'R': x_i = (i-1) pi/n                                 (Eq. (eq:refm))
     """
@@ -161,6 +179,9 @@ def eigen_angles(family: str, n: int) -> np.ndarray:
     elif family == "F":
         th = (i - 2) * 2 * np.pi / (n - 2)
         th[0] = th[-1] = 0.0
+    elif family == "S3":                                 # reading R6
+        th = (i - 2) * np.pi / (n - 3)
+        th[[0, 1, n - 2, n - 1]] = 0.0
     elif family == "P":
         th = 2 * (i - 1) * np.pi / n
     elif family == "R":
@@ -187,6 +208,17 @@ def transform_matrix(family: str, n: int) -> np.ndarray:
         return dft_matrix(n).conj().T
     if family == "R":
         return dct2_matrix(n).T
+    if family == "S3":                                   # reading R6
+        N = n - 4
+        L1, L2 = cubic_border_columns(n)
+        Q = dst1_matrix(N)
+        T = np.zeros((n, n))
+        T[:, 0], T[:, 1] = L1, L2
+        T[:, n - 2], T[:, n - 1] = L2[::-1], L1[::-1]
+        T[2:N + 2, 2:N + 2] = Q
+        T[0, 2:N + 2] = -Q[0, :]                          # sin at x_{-1} = -sin at x_1
+        T[n - 1, 2:N + 2] = -Q[N - 1, :]                  # sin at x_{N+2} = -sin at x_N
+        return T
     N = n - 2
     v = border_vector(family, n)
     J = flip(n)
@@ -318,6 +350,13 @@ def extension_matrix(family: str, n: int) -> np.ndarray:
     'F': rows 1 and n copy interior rows N and 1 (periodic wrap).
     'S': rows 1 and n are zero (the sine vanishes at x_0 and x_{n-1}).
     """
+    if family == "S3":                                   # odd extension by two samples
+        N = n - 4
+        E = np.zeros((n, N))
+        E[2:N + 2, :] = np.eye(N)
+        E[0, 0] = -1.0
+        E[n - 1, N - 1] = -1.0
+        return E
     N = n - 2
     E = np.zeros((n, N))
     E[1:n - 1, :] = np.eye(N)
@@ -339,23 +378,26 @@ def blur_matrix_bcfree(family: str, h: np.ndarray, n: int) -> np.ndarray:
         the classical BC that the block diagonalises (reflective for 'C',
         periodic for 'F', the odd/tau extension for 'S'): A_X E = E A_N;
     (ii) sampled polynomials of the preserved degree (quadratics for 'C', 'F';
-        linear for 'S') are eigenvectors with eigenvalue z(0) (Sec. 3.1, 3.2, Remark 2).
+        linear for 'S'; cubics for 'S3') are eigenvectors with eigenvalue z(0)
+        (Sec. 3.1, 3.2, Remark 2; reading R6).
     The polynomials are sampled as monomials on the integer grid, deliberately
     unlike the paper's q and p.  A_X = [z0 P_L | E A_N | z0 P_R] B^{-1} with
     B = [P_L | E | P_R].
     """
-    N = n - 2
     E = extension_matrix(family, n)
-    rule = {"C": "reflective", "F": "periodic", "S": "odd"}[family]
+    N = E.shape[1]
+    rule = {"C": "reflective", "F": "periodic", "S": "odd", "S3": "odd"}[family]
     AN = bc_matrix(h, N, rule)
     z0 = float(np.sum(h))
-    t = np.arange(n, dtype=np.float64)
+    t = np.arange(n, dtype=np.float64) / n
     if family == "S":
-        PL, PR = np.ones(n), t          # span{1, x} = linear functions
+        P = [np.ones(n), t]                     # span{1, x} = linear functions
+    elif family == "S3":
+        P = [np.ones(n), t, t * t, t ** 3]      # cubics
     else:
-        PL, PR = t * t, t               # with the constant in range(E): quadratics
-    B = np.column_stack([PL, E, PR])
-    AB = np.column_stack([z0 * PL, E @ AN, z0 * PR])
+        P = [t * t, t]                          # with the constant in range(E): quadratics
+    B = np.column_stack(P + [E])
+    AB = np.column_stack([z0 * v for v in P] + [E @ AN])
     return AB @ np.linalg.inv(B)
 
 

@@ -93,12 +93,13 @@ def test_antireflective_spectral_equals_extension_rule(n, h):
     assert np.abs(O.blur_matrix_spectral("S", h, n) - A).max() < 1e-12
 
 
-@pytest.mark.parametrize("fam", ["S", "C", "F"])
-@pytest.mark.parametrize("n", [8, 13, 24])
+@pytest.mark.parametrize("fam", ["S", "C", "F", "S3"])
+@pytest.mark.parametrize("n", [9, 13, 24])
 def test_high_order_matrix_equals_transform_free_construction(fam, n):
-    """T_X diag(d) T_X^{-1} (Eq. (eq:Ac), (eq:Af)) equals the matrix built with no
-    transform from the classical BC on the interior block and polynomial preservation."""
-    h = _h(fam) if n > 8 or fam != "S" else H_SYM
+    """T_X diag(d) T_X^{-1} (Eq. (eq:Ac), (eq:Af); reading R6 for S3) equals the matrix
+    built with no transform from the classical BC on the interior block and
+    polynomial preservation."""
+    h = _h(fam)
     As = O.blur_matrix_spectral(fam, h, n)
     assert np.abs(As - O.blur_matrix_bcfree(fam, h, n)).max() < 1e-12
     assert np.abs(As.imag).max() < 1e-12          # a real PSF gives a real matrix
@@ -127,7 +128,7 @@ def test_grid_reading_R4_printed_grid_breaks_the_algebra():
 # ---------------------------------------------------- invariants (P3, P4)
 
 
-@pytest.mark.parametrize("fam,deg", [("S", 1), ("C", 2), ("F", 2)])
+@pytest.mark.parametrize("fam,deg", [("S", 1), ("C", 2), ("F", 2), ("S3", 3)])
 def test_polynomials_are_preserved(fam, deg):
     """Sampled polynomials of degree <= deg are eigenvectors with eigenvalue z(0) = 1."""
     n = 20
@@ -139,7 +140,7 @@ def test_polynomials_are_preserved(fam, deg):
     assert np.abs(A @ t ** (deg + 1) - t ** (deg + 1)).max() > 1e-4
 
 
-@pytest.mark.parametrize("fam", ["S", "C", "F"])
+@pytest.mark.parametrize("fam", ["S", "C", "F", "S3"])
 def test_spectrum_equals_dense_eigendecomposition(fam):
     """eig(A_X) is the multiset of d; T_X T_X^{-1} = I."""
     n = 16
@@ -165,18 +166,18 @@ def test_antireflective_laplacian_is_eq_L(n):
     assert np.abs(Ls - L).max() < 1e-12
 
 
-@pytest.mark.parametrize("fam,rule", [("C", "reflective"), ("F", "periodic")])
-def test_high_order_laplacian(fam, rule):
-    """L_X annihilates quadratics (Null(L) = preserved space) and acts on the
-    extended interior as the second difference with the classical BC."""
+@pytest.mark.parametrize("fam,rule,deg", [("C", "reflective", 2), ("F", "periodic", 2), ("S3", "odd", 3)])
+def test_high_order_laplacian(fam, rule, deg):
+    """L_X annihilates the preserved polynomials (Null(L) = preserved space) and acts
+    on the extended interior as the second difference with the classical BC."""
     n = 14
     T = O.transform_matrix(fam, n)
     Ls = T @ np.diag(O.laplacian_angles_1d(fam, n)) @ np.linalg.inv(T)
     t = np.arange(n, dtype=float)
-    for k in range(3):
-        assert np.abs(Ls @ t ** k).max() < 1e-9
+    for k in range(deg + 1):
+        assert np.abs(Ls @ t ** k).max() < 1e-8
     E = O.extension_matrix(fam, n)
-    LN = O.bc_matrix(np.array([-1.0, 2.0, -1.0]), n - 2, rule)
+    LN = O.bc_matrix(np.array([-1.0, 2.0, -1.0]), E.shape[1], rule)
     assert np.abs(Ls @ E - E @ LN).max() < 1e-12
 
 
@@ -191,7 +192,7 @@ def test_rotated_psf_gives_conjugate_eigenvalues(fam):
     assert np.allclose(O.eigenvalues_1d(fam, h[::-1], n), np.conj(O.eigenvalues_1d(fam, h, n)))
 
 
-@pytest.mark.parametrize("fam", ["S", "C", "F"])
+@pytest.mark.parametrize("fam", ["S", "C", "F", "S3"])
 @pytest.mark.parametrize("L", ["I", "lap"])
 @pytest.mark.parametrize("mu", [1e-6, 1e-2, 3.0])
 def test_spectral_filter_equals_reblurred_normal_equations(fam, L, mu):
@@ -209,7 +210,7 @@ def test_spectral_filter_equals_reblurred_normal_equations(fam, L, mu):
 # ------------------------------------------------------------- GCV (P6, P7)
 
 
-@pytest.mark.parametrize("fam", ["S", "C", "F"])
+@pytest.mark.parametrize("fam", ["S", "C", "F", "S3"])
 def test_gcv_trace_identity(fam):
     """trace(I - A R_mu) = sum (1 - Phi_i) exactly."""
     n = 12
@@ -237,13 +238,13 @@ def test_gcv_exact_equals_spectral_for_periodic():
     assert np.allclose(Gs, Ge, rtol=1e-10)
 
 
-@pytest.mark.parametrize("fam", ["S", "C", "F"])
+@pytest.mark.parametrize("fam", ["S", "C", "F", "S3"])
 @pytest.mark.parametrize("L", ["I", "lap"])
 def test_gcv_brute_force_tiny(fam, L):
     """Brute force on n = 10: for each mu, solve the dense normal equations, form
     ||T^{-1}(g - A f)||^2 / trace(I - A R)^2; equals G from the spectral sums, same argmin."""
     n = 10
-    h = _h(fam) if fam != "S" else H_SYM
+    h = _h(fam)
     rng = np.random.default_rng(11)
     g = np.cumsum(rng.standard_normal(n)) + 0.3 * rng.standard_normal(n)
     mus = synth.mu_grid(17, 1e-5, 10.0)
@@ -294,29 +295,30 @@ def test_symbol2_brute_force():
     assert np.allclose(O.symbol2(h, t0, t1), ref, atol=1e-14)
 
 
-@pytest.mark.parametrize("fam,rule", [("F", "periodic"), ("C", "reflective"), ("S", "odd")])
+@pytest.mark.parametrize("fam,rule", [("F", "periodic"), ("C", "reflective"), ("S", "odd"), ("S3", "odd")])
 def test_2d_interior_is_classical_bc_and_biquadratics_preserved(fam, rule):
     """2D A_X (Sec. 6, tensor transform + 2D eigenvalues) acts on the extended interior
     as the 2D classical-BC matrix of the 2D PSF, and preserves tensor products of
     preserved 1D polynomials with eigenvalue 1."""
-    n0, n1 = 9, 11
+    n0, n1 = 10, 11
     h = (synth.gaussian_psf_2d_rotated(1.2, 0.7, 30, 5, 0.4, -0.3) if fam == "F"
          else synth.gaussian_psf_2d_separable(1.0, 5))
     A2 = O.blur_matrix_2d_spectral(fam, h, n0, n1)
-    E = np.kron(O.extension_matrix(fam, n0), O.extension_matrix(fam, n1))
-    assert np.abs(A2 @ E - E @ O.bc_matrix_2d(h, n0 - 2, n1 - 2, rule)).max() < 1e-12
+    E0, E1 = O.extension_matrix(fam, n0), O.extension_matrix(fam, n1)
+    E = np.kron(E0, E1)
+    assert np.abs(A2 @ E - E @ O.bc_matrix_2d(h, E0.shape[1], E1.shape[1], rule)).max() < 1e-12
     t0 = np.arange(n0)[:, None] / 3.0
     t1 = np.arange(n1)[None, :] / 4.0
-    deg = 1 if fam == "S" else 2
-    u = sum(t0 ** a for a in range(deg + 1)) * (2 - t1 + (0.3 * t1 ** 2 if deg == 2 else 0))
+    deg = {"S": 1, "C": 2, "F": 2, "S3": 3}[fam]
+    u = sum(t0 ** a for a in range(deg + 1)) * sum((-0.7 * t1) ** a for a in range(deg + 1))
     assert np.abs(A2 @ u.ravel() - u.ravel()).max() < 1e-10
 
 
-@pytest.mark.parametrize("fam", ["S", "C", "F"])
+@pytest.mark.parametrize("fam", ["S", "C", "F", "S3"])
 @pytest.mark.parametrize("L", ["I", "lap"])
 def test_2d_separable_mode_equals_dense_normal_equations(fam, L):
     """The separable dense 2D method equals the dense (n0 n1)^2 reblurred normal equations."""
-    n0, n1 = 7, 9
+    n0, n1 = 8, 9
     h = (synth.gaussian_psf_2d_rotated(1.0, 0.6, 30, 3, 0.2, -0.1) if fam == "F"
          else synth.gaussian_psf_2d_separable(0.8, 3))
     g = np.random.default_rng(2).standard_normal((n0, n1))
