@@ -30,8 +30,9 @@
  * and the layout of hobc_eigenvalues):  spectral index t of one axis is column
  * t of T_X on that axis: t = 0 is the left border vector (p or q), t = 1..n-2
  * the trigonometric columns in the natural order of the transform, t = n-1 the
- * right border vector.
- *   Families SINE and COSINE keep real spectra: one item is n values (1D) or
+ * right border vector.  SINE_CUBIC has two border columns on each side:
+ * t = 0, 1 (L1, L2) and t = n-2, n-1 (their flips), t = 2..n-3 trigonometric.
+ *   Families SINE, SINE_CUBIC and COSINE keep real spectra: one item is n values (1D) or
  *   n1 x n0 values stored as [t1][t0] (2D, t0 fastest).
  *   Family FOURIER stores complex values (re, im interleaved) and, because g is
  *   real, only the half of axis 1 that determines the rest:
@@ -61,10 +62,13 @@ typedef enum {
 
 typedef enum {
     HOBC_FAMILY_AUTO = 0,      /* degree 1 -> SINE; degree 2 -> COSINE if the desc says
-                                  the PSF is symmetric, else FOURIER                     */
+                                  the PSF is symmetric, else FOURIER; degree 3 -> SINE_CUBIC */
     HOBC_FAMILY_SINE = 1,      /* antireflective, Sec. 2.2, Eq. (eq:ART), (eq:jcf)       */
     HOBC_FAMILY_COSINE = 2,    /* degree 2, symmetric PSF, Sec. 3.1, Eq. (eq:Tc), (eq:Ac) */
-    HOBC_FAMILY_FOURIER = 3    /* degree 2, any PSF, Sec. 3.2, Eq. (eq:Tf), (eq:Af)      */
+    HOBC_FAMILY_FOURIER = 3,   /* degree 2, any PSF, Sec. 3.2, Eq. (eq:Tf), (eq:Af)      */
+    HOBC_FAMILY_SINE_CUBIC = 4 /* degree 3, symmetric PSF: DST-I of order n-4 with four
+                                  border columns spanning the cubics (the paper names
+                                  degree 3 in Sec. 1 and Sec. 7 without a construction) */
 } hobc_family;
 
 typedef enum {
@@ -84,8 +88,9 @@ typedef struct {
     int n[2];                  /* field of view: 1D n[0]; 2D n[0] rows x n[1] columns;
                                   each in [6, 1024]                                        */
     int psf[2];                /* PSF mask size (odd): 1D psf[0] = 2m+1; 2D rows x cols;
-                                  needs psf[i] <= n[i] - 2 (Sec. 2.2, Sec. 3)             */
-    int bc_degree;             /* 1 or 2                                                   */
+                                  needs psf[i] <= n[i] - 2 (Sec. 2.2, Sec. 3), or
+                                  psf[i] <= n[i] - 4 for SINE_CUBIC                       */
+    int bc_degree;             /* 1, 2 or 3                                                */
     hobc_family family;
     int psf_symmetric;         /* caller asserts h_{-j} = h_j on every axis (used by AUTO) */
     hobc_smoothing L;

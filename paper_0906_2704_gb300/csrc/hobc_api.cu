@@ -108,6 +108,11 @@ static cd expm_ipi(long long a, long long b) {
 static void theta_frac(int fam, int n, int t, long long& num, long long& den) {
     const int N = n - 2;
     if (t == 0 || t == n - 1) { num = 0; den = 1; return; }
+    if (fam == hobc::FAM_S3) {                     // N of the cubic family is n - 4
+        if (t == 1 || t == n - 2) { num = 0; den = 1; }
+        else { num = t - 1; den = n - 3; }
+        return;
+    }
     if (fam == hobc::FAM_S) { num = t; den = N + 1; }
     else if (fam == hobc::FAM_C) { num = t - 1; den = N; }
     else { num = 2 * (t - 1); den = N; }
@@ -137,6 +142,49 @@ static std::vector<double> border_column(int fam, int n) {
     return v;
 }
 
+// Border columns L1, L2 of the cubic family on x_a = (a - 1) pi/(N+1),
+// a = 0..n-1, N = n - 4: L1 = (x_{N+1} - x)(x_{N+2} - x), L2 = L1 (x_{N+2} - x),
+// each of unit norm.
+static void cubic_columns(int n, std::vector<double>& L1, std::vector<double>& L2) {
+    const int N = n - 4;
+    const double xa = M_PI, xb = (N + 2) * M_PI / (N + 1);
+    L1.assign(n, 0.0);
+    L2.assign(n, 0.0);
+    double n1 = 0, n2 = 0;
+    for (int a = 0; a < n; ++a) {
+        const double x = (a - 1) * M_PI / (N + 1);
+        L1[a] = (xa - x) * (xb - x);
+        L2[a] = L1[a] * (xb - x);
+        n1 += L1[a] * L1[a];
+        n2 += L2[a] * L2[a];
+    }
+    for (int a = 0; a < n; ++a) { L1[a] /= sqrt(n1); L2[a] /= sqrt(n2); }
+}
+
+// Gauss-Jordan inverse of a 4x4 matrix with partial pivoting; false if singular.
+static bool invert4(const double* A, double* inv) {
+    double m[4][8];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 8; ++j) m[i][j] = j < 4 ? A[4 * i + j] : (j - 4 == i ? 1.0 : 0.0);
+    for (int c = 0; c < 4; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 4; ++r)
+            if (fabs(m[r][c]) > fabs(m[piv][c])) piv = r;
+        if (m[piv][c] == 0.0) return false;
+        for (int j = 0; j < 8; ++j) std::swap(m[c][j], m[piv][j]);
+        const double d = m[c][c];
+        for (int j = 0; j < 8; ++j) m[c][j] /= d;
+        for (int r = 0; r < 4; ++r) {
+            if (r == c) continue;
+            const double f = m[r][c];
+            for (int j = 0; j < 8; ++j) m[r][j] -= f * m[c][j];
+        }
+    }
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) inv[4 * i + j] = m[i][j + 4];
+    return true;
+}
+
 template <typename T>
 static void* upload_complex(const std::vector<cd>& h, cudaError_t& err) {
     std::vector<T> tmp(2 * h.size());
@@ -161,10 +209,10 @@ static cudaError_t build_axis(AxisHost& a, int fam, int n, int p, bool half) {
     memset(&a, 0, sizeof(a));
     a.fam = fam;
     a.n = n;
-    a.N = n - 2;
+    a.N = fam == hobc::FAM_S3 ? n - 4 : n - 2;
     a.p = p;
     const int N = a.N;
-    a.L = fam == hobc::FAM_S ? 2 * (N + 1) : N;
+    a.L = (fam == hobc::FAM_S || fam == hobc::FAM_S3) ? 2 * (N + 1) : N;
     if (a.L >= 8 && (a.L & (a.L - 1)) == 0) {
         a.M = a.L;
         a.blue = 0;
@@ -198,10 +246,30 @@ static cudaError_t build_axis(AxisHost& a, int fam, int n, int p, bool half) {
         for (int k = 0; k < N; ++k) post[k] = expm_ipi(k, 2LL * N);
         a.post = upload_complex<T>(post, err);
     }
-    std::vector<double> q = border_column(fam, n);
+    std::vector<double> q;
+    if (fam == hobc::FAM_S3) {
+        std::vector<double> L2;
+        cubic_columns(n, q, L2);
+        a.q2 = upload_real<T>(L2, err);
+        // rows 0+2, 1, n-2, n-1+n-3 of T restricted to the border columns
+        // (L1, L2, flip L2, flip L1)
+        auto B = [&](int b, int r) {
+            return b == 0 ? q[r] : b == 1 ? L2[r] : b == 2 ? L2[n - 1 - r] : q[n - 1 - r];
+        };
+        double K[16];
+        for (int b = 0; b < 4; ++b) {
+            K[0 * 4 + b] = B(b, 0) + B(b, 2);
+            K[1 * 4 + b] = B(b, 1);
+            K[2 * 4 + b] = B(b, n - 2);
+            K[3 * 4 + b] = B(b, n - 1) + B(b, n - 3);
+        }
+        if (!invert4(K, a.k4) && err == cudaSuccess) err = cudaErrorInvalidValue;
+    } else {
+        q = border_column(fam, n);
+    }
     a.q = upload_real<T>(q, err);
     a.q1 = q[0];
-    if (fam == hobc::FAM_S) {
+    if (fam == hobc::FAM_S || fam == hobc::FAM_S3) {
         a.ka = 1.0 / q[0];
         a.kb = 0.0;
     } else {
@@ -238,7 +306,8 @@ static cudaError_t build_axis(AxisHost& a, int fam, int n, int p, bool half) {
 }
 
 static void free_axis(AxisHost& a) {
-    cudaFree(a.tw); cudaFree(a.chirp); cudaFree(a.bhat); cudaFree(a.post); cudaFree(a.q); cudaFree(a.etab);
+    cudaFree(a.tw); cudaFree(a.chirp); cudaFree(a.bhat); cudaFree(a.post); cudaFree(a.q); cudaFree(a.q2);
+    cudaFree(a.etab);
     memset(&a, 0, sizeof(a));
 }
 
@@ -293,6 +362,10 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
         if (d.psf[i] < 1 || d.psf[i] % 2 == 0 || d.psf[i] > 63) return HOBC_ERR_SIZE;
         if (d.psf[i] > d.n[i] - 2) return HOBC_ERR_SIZE;       // 2m+1 <= n-2
     }
+    const bool cubic = d.family == HOBC_FAMILY_SINE_CUBIC || (d.family == HOBC_FAMILY_AUTO && d.bc_degree == 3);
+    if (cubic)
+        for (int i = 0; i < d.ndim; ++i)
+            if (d.n[i] < 8 || d.psf[i] > d.n[i] - 4) return HOBC_ERR_SIZE;   // 2m+1 <= n-4
     for (int j = 0; j < d.n_mu; ++j) {
         if (!std::isfinite(mu_grid_host[j])) return HOBC_ERR_NONFINITE;
         if (!(mu_grid_host[j] > 0)) return HOBC_ERR_ARG;
@@ -300,15 +373,17 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
         if (d.prec == HOBC_FP32 && (mu_grid_host[j] < 1e-18 || mu_grid_host[j] > 1e18)) return HOBC_ERR_ARG;
     }
     int fam = d.family;
-    if (d.bc_degree != 1 && d.bc_degree != 2) return HOBC_ERR_UNSUPPORTED;
+    if (d.bc_degree < 1 || d.bc_degree > 3) return HOBC_ERR_UNSUPPORTED;
     if (fam == HOBC_FAMILY_AUTO) {
         if (d.bc_degree == 1) fam = d.psf_symmetric ? HOBC_FAMILY_SINE : -1;
-        else fam = d.psf_symmetric ? HOBC_FAMILY_COSINE : HOBC_FAMILY_FOURIER;
-        if (fam < 0) return HOBC_ERR_UNSUPPORTED;   // antireflective needs a symmetric PSF (Sec. 2.2)
+        else if (d.bc_degree == 2) fam = d.psf_symmetric ? HOBC_FAMILY_COSINE : HOBC_FAMILY_FOURIER;
+        else fam = d.psf_symmetric ? HOBC_FAMILY_SINE_CUBIC : -1;
+        if (fam < 0) return HOBC_ERR_UNSUPPORTED;   // sine families need a symmetric PSF (Sec. 2.2)
     }
     if (fam == HOBC_FAMILY_SINE && d.bc_degree != 1) return HOBC_ERR_UNSUPPORTED;
     if ((fam == HOBC_FAMILY_COSINE || fam == HOBC_FAMILY_FOURIER) && d.bc_degree != 2) return HOBC_ERR_UNSUPPORTED;
-    if (fam < HOBC_FAMILY_SINE || fam > HOBC_FAMILY_FOURIER) return HOBC_ERR_ARG;
+    if (fam == HOBC_FAMILY_SINE_CUBIC && d.bc_degree != 3) return HOBC_ERR_UNSUPPORTED;
+    if (fam < HOBC_FAMILY_SINE || fam > HOBC_FAMILY_SINE_CUBIC) return HOBC_ERR_ARG;
 
     hobc_plan_s* p = new hobc_plan_s;
     memset(p, 0, sizeof(*p));

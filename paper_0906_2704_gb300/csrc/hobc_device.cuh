@@ -17,7 +17,7 @@
 
 namespace hobc {
 
-enum { FAM_S = 1, FAM_C = 2, FAM_F = 3 };   // same values as hobc_family
+enum { FAM_S = 1, FAM_C = 2, FAM_F = 3, FAM_S3 = 4 };   // same values as hobc_family
 
 template <typename T> struct V2;
 template <> struct V2<float> { typedef float2 t; };
@@ -40,8 +40,8 @@ template <typename T>
 struct Axis {
     int fam;        // FAM_S / FAM_C / FAM_F
     int n;          // field-of-view length on this axis
-    int N;          // order of the trigonometric block, n - 2
-    int L;          // length of the complex DFT core: N (C, F) or 2(N+1) (S)
+    int N;          // order of the trigonometric block: n - 2 (n - 4 for S3)
+    int L;          // length of the complex DFT core: N (C, F) or 2(N+1) (S, S3)
     int M;          // power-of-two FFT length (== L when L is a power of two >= 8)
     int log2M;
     int blue;       // 1: Bluestein (M >= 2L-1), 0: direct
@@ -53,10 +53,12 @@ struct Axis {
     const C2<T>* chirp;   // [L] exp(-i pi (k^2 mod 2L) / L)
     const C2<T>* bhat;    // [M] FFT_M(conj-chirp, wrapped) / M
     const C2<T>* post;    // COSINE: [N] exp(-i pi k / (2N))
-    const T* q;           // [n] left border column of T_X (p for S, q for C, F)
+    const T* q;           // [n] left border column of T_X (p for S, q for C, F, L1 for S3)
+    const T* q2;          // S3: [n] second left border column L2
     double ka, kb;        // inverse of the 2x2 border system, [[ka, kb], [kb, ka]]
+    double k4[16];        // S3: inverse of the 4x4 border system, row-major
     T q1;                 // q[0]
-    T sc;                 // F: 1/sqrt(N); S: sqrt(2/(N+1))/2
+    T sc;                 // F: 1/sqrt(N); S, S3: sqrt(2/(N+1))/2
     T s0, s1;             // C: DCT-II row scales sqrt(1/N), sqrt(2/N)
     T is0, is1;           // C: their reciprocals
     T invN;               // C: 1/N
@@ -217,6 +219,27 @@ __device__ __forceinline__ void border_coeffs(const Axis<T>& ax, double y0, doub
     }
 }
 
+// S3 (degree 3): y = sum_b c_b B_b + E w with border columns B = (L1, L2, flip L2,
+// flip L1) and the odd extension E (rows 0 and n-1 are minus the first and last
+// interior samples, rows 1 and n-2 are zero).  Rows 0+2, 1, n-2 and n-1+n-3 of
+// y therefore involve only the border coefficients: a 4x4 system whose inverse
+// is precomputed in double.
+template <typename T>
+__device__ __forceinline__ void border_coeffs4(const Axis<T>& ax, double y0, double y1, double y2, double ym3,
+                                               double ym2, double ym1, double* c) {
+    const double r[4] = {y0 + y2, y1, ym2, ym1 + ym3};
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        c[b] = ax.k4[4 * b] * r[0] + ax.k4[4 * b + 1] * r[1] + ax.k4[4 * b + 2] * r[2] + ax.k4[4 * b + 3] * r[3];
+}
+
+// value of sum_b c_b B_b at sample a (S3)
+template <typename T>
+__device__ __forceinline__ T border_sum4(const Axis<T>& ax, const T* c, int a) {
+    const int n = ax.n;
+    return c[0] * ax.q[a] + c[1] * ax.q2[a] + c[2] * ax.q2[n - 1 - a] + c[3] * ax.q[n - 1 - a];
+}
+
 // --------------------------------------------------------------- angles
 
 // theta/pi of spectral index t (0..n-1) on an axis (Eq. (eq:jcf), (eq:Ac), (eq:Af)):
@@ -224,6 +247,7 @@ __device__ __forceinline__ void border_coeffs(const Axis<T>& ax, double y0, doub
 template <typename T>
 __device__ __forceinline__ T theta_over_pi(int fam, int n, int N, int t) {
     if (t == 0 || t == n - 1) return (T)0;
+    if (fam == FAM_S3) return (t == 1 || t == n - 2) ? (T)0 : (T)(t - 1) / (T)(N + 1);
     if (fam == FAM_S) return (T)t / (T)(N + 1);
     if (fam == FAM_C) return (T)(t - 1) / (T)N;
     return (T)(2 * (t - 1)) / (T)N;

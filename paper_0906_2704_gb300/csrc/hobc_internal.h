@@ -17,7 +17,9 @@ struct AxisHost {
     void* bhat;     // [M] complex (Bluestein only)
     void* post;     // [N] complex (COSINE only)
     void* q;        // [n] real
+    void* q2;       // [n] real, S3 only (second border column)
     double ka, kb, q1, sc, s0, s1, is0, is1, invN;
+    double k4[16];  // S3: inverse of the 4x4 border system
     int p;          // PSF extent on this axis
     double2* etab;  // [W][p] exp(-i (j - m) theta_t) for the stored entries t
 };

@@ -102,16 +102,32 @@ k_pair_analysis(const T* __restrict__ in, long long in_item, long long in_rs,
     const T* ya = in + item * in_item + (long long)(va ? ra : 0) * in_rs;
     const T* yb = in + item * in_item + (long long)(vb ? rb : 0) * in_rs;
 
+    constexpr bool CUBIC = (FAM == FAM_S3);
+    constexpr int NB = CUBIC ? 2 : 1;            // border entries on each side
     double c1a = 0, cna = 0, c1b = 0, cnb = 0;
-    if (va) border_coeffs<T>(ax, ya[0], ya[1], ya[n - 2], ya[n - 1], c1a, cna);
-    if (vb) border_coeffs<T>(ax, yb[0], yb[1], yb[n - 2], yb[n - 1], c1b, cnb);
+    double ca4[4] = {0, 0, 0, 0}, cb4[4] = {0, 0, 0, 0};
+    if constexpr (CUBIC) {
+        if (va) border_coeffs4<T>(ax, ya[0], ya[1], ya[2], ya[n - 3], ya[n - 2], ya[n - 1], ca4);
+        if (vb) border_coeffs4<T>(ax, yb[0], yb[1], yb[2], yb[n - 3], yb[n - 2], yb[n - 1], cb4);
+    } else {
+        if (va) border_coeffs<T>(ax, ya[0], ya[1], ya[n - 2], ya[n - 1], c1a, cna);
+        if (vb) border_coeffs<T>(ax, yb[0], yb[1], yb[n - 2], yb[n - 1], c1b, cnb);
+    }
     const T c1af = (T)c1a, cnaf = (T)cna, c1bf = (T)c1b, cnbf = (T)cnb;
+    const T ca4f[4] = {(T)ca4[0], (T)ca4[1], (T)ca4[2], (T)ca4[3]};
+    const T cb4f[4] = {(T)cb4[0], (T)cb4[1], (T)cb4[2], (T)cb4[3]};
     const C2<T> zero = cmk<T>(0, 0);
 
     for (int j = t; j < N; j += ax.tpg) {
-        const T ql = ax.q[1 + j], qr = ax.q[n - 2 - j];
-        const T wa = va ? ya[1 + j] - ql * c1af - qr * cnaf : (T)0;
-        const T wb = vb ? yb[1 + j] - ql * c1bf - qr * cnbf : (T)0;
+        T wa, wb;
+        if constexpr (CUBIC) {
+            wa = va ? ya[2 + j] - border_sum4<T>(ax, ca4f, 2 + j) : (T)0;
+            wb = vb ? yb[2 + j] - border_sum4<T>(ax, cb4f, 2 + j) : (T)0;
+        } else {
+            const T ql = ax.q[1 + j], qr = ax.q[n - 2 - j];
+            wa = va ? ya[1 + j] - ql * c1af - qr * cnaf : (T)0;
+            wb = vb ? yb[1 + j] - ql * c1bf - qr * cnbf : (T)0;
+        }
         if constexpr (FAM == FAM_F) {
             buf[pidx(j)] = dft_in<T>(ax, j, cmk<T>(wa, wb));
         } else if constexpr (FAM == FAM_C) {
@@ -123,7 +139,7 @@ k_pair_analysis(const T* __restrict__ in, long long in_item, long long in_rs,
             buf[pidx(p2)] = dft_in<T>(ax, p2, cmk<T>(-wa, -wb));
         }
     }
-    if (FAM == FAM_S && t == 0) { buf[pidx(0)] = zero; buf[pidx(N + 1)] = zero; }
+    if ((FAM == FAM_S || CUBIC) && t == 0) { buf[pidx(0)] = zero; buf[pidx(N + 1)] = zero; }
     if (ax.blue)
         for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[pidx(p)] = zero;
     __syncthreads();
@@ -159,10 +175,17 @@ k_pair_analysis(const T* __restrict__ in, long long in_item, long long in_rs,
     } else {
         for (int k = t; k < N; k += ax.tpg) {
             const C2<T> z = dft_out<T>(buf, ax, k + 1);
-            sa[1 + k] = (T)(-z.y * ax.sc);
-            sb[1 + k] = (T)(z.x * ax.sc);
+            sa[NB + k] = (T)(-z.y * ax.sc);
+            sb[NB + k] = (T)(z.x * ax.sc);
         }
-        if (t == 0) { sa[0] = c1af; sa[W - 1] = cnaf; sb[0] = c1bf; sb[W - 1] = cnbf; }
+        if (t == 0) {
+            if constexpr (CUBIC) {
+                sa[0] = ca4f[0]; sa[1] = ca4f[1]; sa[W - 2] = ca4f[2]; sa[W - 1] = ca4f[3];
+                sb[0] = cb4f[0]; sb[1] = cb4f[1]; sb[W - 2] = cb4f[2]; sb[W - 1] = cb4f[3];
+            } else {
+                sa[0] = c1af; sa[W - 1] = cnaf; sb[0] = c1bf; sb[W - 1] = cnbf;
+            }
+        }
     }
     __syncthreads();
 
@@ -264,8 +287,9 @@ k_pair_synthesis(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in, long
             buf[pidx(k)] = dft_in<T>(ax, k, cconj<T>(v));
         }
     } else {
+        constexpr int NB = (FAM == FAM_S3) ? 2 : 1;
         for (int k = t; k < N; k += ax.tpg) {
-            const T a = re_of(sa[1 + k]), b = re_of(sb[1 + k]);
+            const T a = re_of(sa[NB + k]), b = re_of(sb[NB + k]);
             buf[pidx(1 + k)] = dft_in<T>(ax, 1 + k, cmk<T>(a, b));
             const int p2 = ax.L - 1 - k;
             buf[pidx(p2)] = dft_in<T>(ax, p2, cmk<T>(-a, -b));
@@ -299,6 +323,32 @@ k_pair_synthesis(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in, long
             wb = z.x * ax.sc;
         }
     };
+    if constexpr (FAM == FAM_S3) {
+        const T c4a[4] = {re_of(sa[0]), re_of(sa[1]), re_of(sa[W - 2]), re_of(sa[W - 1])};
+        const T c4b[4] = {re_of(sb[0]), re_of(sb[1]), re_of(sb[W - 2]), re_of(sb[W - 1])};
+        for (int j = t; j < N; j += ax.tpg) {
+            T wa, wb;
+            wval(j, wa, wb);
+            if (va) oa[2 + j] = wa + border_sum4<T>(ax, c4a, 2 + j);
+            if (vb) ob[2 + j] = wb + border_sum4<T>(ax, c4b, 2 + j);
+        }
+        if (t == 0) {
+            // rows 1 and n-2 carry only the border columns; rows 0 and n-1 also
+            // minus the first / last interior trigonometric sample (odd extension)
+            T wa0, wb0, wa1, wb1;
+            wval(0, wa0, wb0);
+            wval(N - 1, wa1, wb1);
+            if (va) {
+                oa[1] = border_sum4<T>(ax, c4a, 1); oa[n - 2] = border_sum4<T>(ax, c4a, n - 2);
+                oa[0] = border_sum4<T>(ax, c4a, 0) - wa0; oa[n - 1] = border_sum4<T>(ax, c4a, n - 1) - wa1;
+            }
+            if (vb) {
+                ob[1] = border_sum4<T>(ax, c4b, 1); ob[n - 2] = border_sum4<T>(ax, c4b, n - 2);
+                ob[0] = border_sum4<T>(ax, c4b, 0) - wb0; ob[n - 1] = border_sum4<T>(ax, c4b, n - 1) - wb1;
+            }
+        }
+        return;
+    }
     for (int j = t; j < N; j += ax.tpg) {
         T wa, wb;
         wval(j, wa, wb);

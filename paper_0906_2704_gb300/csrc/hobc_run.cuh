@@ -19,7 +19,9 @@ static Axis<T> dev_axis(const AxisHost& a) {
     x.bhat = reinterpret_cast<const C2<T>*>(a.bhat);
     x.post = reinterpret_cast<const C2<T>*>(a.post);
     x.q = reinterpret_cast<const T*>(a.q);
+    x.q2 = reinterpret_cast<const T*>(a.q2);
     x.ka = a.ka; x.kb = a.kb;
+    for (int i = 0; i < 16; ++i) x.k4[i] = a.k4[i];
     x.q1 = (T)a.q1; x.sc = (T)a.sc; x.s0 = (T)a.s0; x.s1 = (T)a.s1;
     x.is0 = (T)a.is0; x.is1 = (T)a.is1; x.invN = (T)a.invN;
     return x;
@@ -133,6 +135,7 @@ hobc_status run_analysis(hobc_plan_s* p, const void* g, void* ghat) {
     const T* gt = reinterpret_cast<const T*>(g);
     switch (p->fam) {
         case FAM_S: return analysis_fam<T, FAM_S>(p, gt, ghat);
+        case FAM_S3: return analysis_fam<T, FAM_S3>(p, gt, ghat);
         case FAM_C: return analysis_fam<T, FAM_C>(p, gt, ghat);
         default: return analysis_fam<T, FAM_F>(p, gt, ghat);
     }
@@ -171,6 +174,7 @@ hobc_status run_synthesis(hobc_plan_s* p, const void* c, void* y) {
     T* yt = reinterpret_cast<T*>(y);
     switch (p->fam) {
         case FAM_S: return synthesis_fam<T, FAM_S, false>(p, c, yt, fd);
+        case FAM_S3: return synthesis_fam<T, FAM_S3, false>(p, c, yt, fd);
         case FAM_C: return synthesis_fam<T, FAM_C, false>(p, c, yt, fd);
         default: return synthesis_fam<T, FAM_F, false>(p, c, yt, fd);
     }
@@ -182,6 +186,7 @@ hobc_status run_filter_synthesis(hobc_plan_s* p, const void* ghat, const void* D
     T* ft = reinterpret_cast<T*>(f);
     switch (p->fam) {
         case FAM_S: return synthesis_fam<T, FAM_S, true>(p, ghat, ft, fd);
+        case FAM_S3: return synthesis_fam<T, FAM_S3, true>(p, ghat, ft, fd);
         case FAM_C: return synthesis_fam<T, FAM_C, true>(p, ghat, ft, fd);
         default: return synthesis_fam<T, FAM_F, true>(p, ghat, ft, fd);
     }
@@ -251,6 +256,10 @@ hobc_status prepare_kernels(hobc_plan_s* p) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100)
     HOBC_SMEM((k_pair_analysis<T, FAM_S>));
+    HOBC_SMEM((k_pair_analysis<T, FAM_S3>));
+    HOBC_SMEM((k_pair_synthesis<T, FAM_S3, 0>));
+    HOBC_SMEM((k_pair_synthesis<T, FAM_S3, 1>));
+    HOBC_SMEM((k_pair_synthesis<T, FAM_S3, 2>));
     HOBC_SMEM((k_pair_analysis<T, FAM_C>));
     HOBC_SMEM((k_pair_analysis<T, FAM_F>));
     HOBC_SMEM((k_pair_synthesis<T, FAM_S, 0>));
