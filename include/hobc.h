@@ -199,6 +199,51 @@ hobc_status hobc_gcv_noalloc(const hobc_plan_desc* desc, const void* ghat_dev, c
 /* Size in bytes of the static scratch array of hobc_gcv_noalloc. */
 size_t hobc_gcv_noalloc_max_bytes(void);
 
+/* ---------------------------------------------------------------------------
+ * Batches of 2D problems of uneven sizes (Sec. 6 for each problem).
+ * Every problem has its own field of view, its own symmetric PSF and its own
+ * boundary-condition degree: 1 -> SINE, 2 -> COSINE, 3 -> SINE_CUBIC.  The
+ * smoothing operator, precision and mu grid are shared.  Problems are stored
+ * back to back: problem i's image occupies elements [img_off[i], img_off[i+1])
+ * (n[0] x n[1], row-major) of the packed g and f buffers, its PSF elements
+ * [psf_off[i], psf_off[i+1]) of the packed PSF buffer (hobc_batch_offsets).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int n[2];                  /* field of view, each in [8, 512] (COSINE: [8, 1024])      */
+    int psf[2];                /* odd PSF size, <= n - 2 (SINE_CUBIC: <= n - 4), <= 63     */
+    int bc_degree;             /* 1, 2 or 3                                                */
+} hobc_batch_item;
+
+typedef struct {
+    int count;                 /* number of problems                                       */
+    hobc_smoothing L;
+    hobc_precision prec;
+    int n_mu;                  /* K >= 1 (FP32: every mu in [1e-18, 1e18])                 */
+} hobc_batch_desc;
+
+typedef struct hobc_batch_s hobc_batch;
+
+/* Build the batch plan: transform tables once per distinct (family, n), work
+ * lists of every pass, workspace.  With a non-NULL stream the whole launch
+ * sequence is captured once into a CUDA graph that hobc_deblur_batched
+ * replays; with the legacy NULL stream the kernels are launched directly.
+ * Synchronous; allocates device memory. */
+hobc_status hobc_batch_create(const hobc_batch_desc* desc, const hobc_batch_item* items_host,
+                              const double* mu_grid_host, void* cuda_stream, hobc_batch** out);
+void hobc_batch_destroy(hobc_batch* batch);
+
+/* Packed-layout offsets (host arrays of count + 1 elements each, nullable). */
+hobc_status hobc_batch_offsets(const hobc_batch* batch, size_t* img_off, size_t* psf_off);
+
+/* Kernel launches per batched deblur (one per pass and family present). */
+int hobc_batch_launch_count(const hobc_batch* batch);
+
+/* The whole method on every problem of the batch: g_dev, f_dev packed images,
+ * psf_dev packed PSFs, mu_index_dev [count] (nullable), gcv_dev [count][K]
+ * (nullable).  Asynchronous on the batch's stream. */
+hobc_status hobc_deblur_batched(hobc_batch* batch, const void* g_dev, const void* psf_dev, void* f_dev,
+                                int* mu_index_dev, double* gcv_dev);
+
 /* Number of kernel launches the last call on this plan issued. */
 int hobc_last_launch_count(const hobc_plan* plan);
 

@@ -205,7 +205,7 @@ static void* upload_real(const std::vector<double>& h, cudaError_t& err) {
 }
 
 template <typename T>
-static cudaError_t build_axis(AxisHost& a, int fam, int n, int p, bool half) {
+cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half) {
     memset(&a, 0, sizeof(a));
     a.fam = fam;
     a.n = n;
@@ -305,6 +305,9 @@ static cudaError_t build_axis(AxisHost& a, int fam, int n, int p, bool half) {
     return err;
 }
 
+template cudaError_t build_axis_host<float>(AxisHost&, int, int, int, bool);
+template cudaError_t build_axis_host<double>(AxisHost&, int, int, int, bool);
+
 static void free_axis(AxisHost& a) {
     cudaFree(a.tw); cudaFree(a.chirp); cudaFree(a.bhat); cudaFree(a.post); cudaFree(a.q); cudaFree(a.q2);
     cudaFree(a.etab);
@@ -398,8 +401,8 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
     cudaError_t err = cudaSuccess;
     for (int i = 0; i < d.ndim && err == cudaSuccess; ++i) {
         const bool half = (i == d.ndim - 1);
-        err = d.prec == HOBC_FP64 ? build_axis<double>(p->ax[i], fam, d.n[i], d.psf[i], half)
-                                  : build_axis<float>(p->ax[i], fam, d.n[i], d.psf[i], half);
+        err = d.prec == HOBC_FP64 ? build_axis_host<double>(p->ax[i], fam, d.n[i], d.psf[i], half)
+                                  : build_axis_host<float>(p->ax[i], fam, d.n[i], d.psf[i], half);
     }
     const AxisHost& last = p->ax[d.ndim - 1];
     p->spec_elems = d.ndim == 1 ? (size_t)last.W : (size_t)last.W * p->ax[0].n;

@@ -1,0 +1,558 @@
+// Batched deblurring of many 2D problems of uneven sizes, each with its own
+// symmetric PSF and boundary-condition degree (1: SINE, 2: COSINE,
+// 3: SINE_CUBIC), in one CUDA-graph launch.
+//
+// The batch plan builds the transform tables once per distinct (family, n),
+// lays the problems out back to back, and turns every pass of the method into
+// a host-built work list: one entry per (problem, block of lines) for the line
+// transforms, per (problem, chunk) for the GCV scan, per (problem, column) for
+// the eigenvalues.  One kernel launch per pass and family walks its list; a
+// CTA reads its entry, takes that problem's axis tables, and runs the same
+// device code as the single-geometry plan (pair_analysis_body,
+// pair_synthesis_body, gcv_partials_body).  Every line kernel runs 256-thread
+// CTAs: an FFT of length M uses M/8 threads per line pair, so a CTA holds
+// 2048/M groups and the shared memory of a CTA is the same for every M.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "hobc_internal.h"
+#include "hobc_kernels.cuh"
+
+namespace hobc {
+
+struct LineWork {           // one CTA of a line pass
+    int item, axis, r0, nlines;
+    long long in_off, out_off;
+    int in_rs, in_cs, out_rs, out_cs;
+    int axis_o;             // the other axis (filter smoothing)
+};
+
+struct ItemDev {            // per-problem geometry on the device
+    int n0, n1, p0, p1, fam;
+    int N0, N1;
+    long long img_off, psf_off;
+};
+
+struct GcvItem {
+    GcvGeom geo;
+    long long spec_off, part_off;
+    int nchunks;
+};
+
+struct BatchIO {            // the caller's buffers of one call (read by the graph)
+    const void* g;
+    const void* psf;
+    void* f;
+    int* mu_idx;
+    double* gcv;
+};
+
+static const int kBatchThreads = 256;
+
+// ------------------------------------------------------------------ kernels
+
+template <typename T, int FAM>
+__global__ void __launch_bounds__(256)
+kb_pair_analysis(const LineWork* __restrict__ work, const Axis<T>* __restrict__ axes, const T* __restrict__ in_fixed,
+                 int in_from_io, const BatchIO* __restrict__ io, T* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const LineWork w = work[blockIdx.x];
+    const T* in = (in_from_io ? reinterpret_cast<const T*>(io->g) : in_fixed) + w.in_off;
+    pair_analysis_body<T, FAM>(in, 0, w.in_rs, out + w.out_off, 0, w.out_rs, w.out_cs, w.nlines, axes[w.axis], 0,
+                               w.r0, smem_raw);
+}
+
+template <typename T, int FAM, int FMODE>
+__global__ void __launch_bounds__(256)
+kb_pair_synthesis(const LineWork* __restrict__ work, const Axis<T>* __restrict__ axes, const T* __restrict__ in,
+                  T* __restrict__ out_fixed, int out_to_io, const BatchIO* __restrict__ io, const T* __restrict__ D,
+                  FilterDesc fd) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const LineWork w = work[blockIdx.x];
+    if (FMODE == 2) {
+        const Axis<T>& ao = axes[w.axis_o];
+        fd.D = D + w.in_off;             // eigenvalues share the spectrum layout
+        fd.d_psf_stride = 0;
+        fd.psf_per = 0;
+        fd.mu_idx = io->mu_idx + w.item;
+        fd.o_fam = ao.fam; fd.o_n = ao.n; fd.o_N = ao.N; fd.o_W = ao.W;
+    }
+    T* out = (out_to_io ? reinterpret_cast<T*>(io->f) : out_fixed) + w.out_off;
+    pair_synthesis_body<T, FAM, FMODE>(in + w.in_off, 0, w.in_rs, w.in_cs, out, 0, w.out_rs, w.nlines, axes[w.axis],
+                                       fd, 0, w.r0, smem_raw);
+}
+
+// Eigenvalues of a symmetric PSF on the real families: d = sum h cos(j0 th0) cos(j1 th1)
+// (Eq. (eq:symbol) at -theta, Sec. 6), partial sums over j1 per column, then a
+// cosine recurrence over j0; FP64.  One CTA per (problem, column).
+template <typename T>
+__global__ void __launch_bounds__(256)
+kb_eig(const int2* __restrict__ work, const ItemDev* __restrict__ items, const BatchIO* __restrict__ io,
+       T* __restrict__ D) {
+    __shared__ double P[64];
+    const int2 w = work[blockIdx.x];
+    const ItemDev it = items[w.x];
+    const int c = w.y;
+    const T* h = reinterpret_cast<const T*>(io->psf) + it.psf_off;
+    const int m0 = it.p0 / 2, m1 = it.p1 / 2;
+    const double f1 = (double)theta_over_pi<double>(it.fam, it.n1, it.N1, c);
+    for (int j0 = threadIdx.x; j0 < it.p0; j0 += blockDim.x) {
+        double acc = 0;
+        for (int j1 = 0; j1 < it.p1; ++j1) acc += (double)h[j0 * it.p1 + j1] * cospi((double)(j1 - m1) * f1);
+        P[j0] = acc;
+    }
+    __syncthreads();
+    T* o = D + it.img_off + (long long)c * it.n0;
+    for (int t0 = threadIdx.x; t0 < it.n0; t0 += blockDim.x) {
+        const double c1 = cospi((double)theta_over_pi<double>(it.fam, it.n0, it.N0, t0));
+        double acc = P[m0];
+        double ck = 1.0, cprev = c1;          // cos(0), cos(-th)
+        for (int k = 1; k <= m0; ++k) {
+            const double cn = 2.0 * c1 * ck - cprev;   // cos(k th) = 2 cos(th) cos((k-1) th) - cos((k-2) th)
+            cprev = ck;
+            ck = cn;
+            acc += (P[m0 + k] + P[m0 - k]) * ck;
+        }
+        o[t0] = (T)acc;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+kb_gcv(const int2* __restrict__ work, const GcvItem* __restrict__ gi, const T* __restrict__ G,
+       const T* __restrict__ D, const T* __restrict__ muT, double* __restrict__ partials) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int2 w = work[blockIdx.x];
+    const GcvItem g = gi[w.x];
+    gcv_partials_body<T, false>(G + g.spec_off, D + g.spec_off, muT, g.geo, (long long)w.y * g.geo.chunk,
+                                partials + g.part_off + (long long)w.y * 2 * g.geo.K, smem_raw);
+}
+
+__global__ void kb_gcv_finalize(const GcvItem* __restrict__ gi, const double* __restrict__ partials,
+                                const BatchIO* __restrict__ io, int K) {
+    __shared__ double sv[256];
+    __shared__ int si[256];
+    const int item = blockIdx.x;
+    const GcvItem g = gi[item];
+    const double* p = partials + g.part_off;
+    double best = INFINITY;
+    int bi = 0x7fffffff;
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        double num = 0, den = 0;
+        for (int c = 0; c < g.nchunks; ++c) {
+            num += p[(long long)c * 2 * K + j];
+            den += p[(long long)c * 2 * K + K + j];
+        }
+        const double Gv = num / (den * den);
+        if (io->gcv) io->gcv[(long long)item * K + j] = Gv;
+        const double key = isnan(Gv) ? INFINITY : Gv;
+        if (key < best || (key == best && j < bi)) { best = key; bi = j; }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            const double v2 = sv[threadIdx.x + s];
+            const int i2 = si[threadIdx.x + s];
+            if (v2 < sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
+                sv[threadIdx.x] = v2;
+                si[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) io->mu_idx[item] = si[0] == 0x7fffffff ? 0 : si[0];
+}
+
+}  // namespace hobc
+
+using namespace hobc;
+
+// ----------------------------------------------------------------- the plan
+
+struct PassList {           // one launch: a family's work list for one pass
+    int fam;
+    LineWork* dev;
+    int count;
+    size_t smem;
+};
+
+struct hobc_batch_s {
+    hobc_batch_desc desc;
+    int count, K, prec;
+    size_t esz;
+    cudaStream_t stream;
+    std::vector<hobc_batch_item> items;
+    std::vector<size_t> img_off, psf_off;
+    std::vector<AxisHost> axes_host;
+    void* axes_dev;
+    ItemDev* items_dev;
+    GcvItem* gcv_items_dev;
+    int2* gcv_work;
+    int gcv_count;
+    int2* eig_work;
+    int eig_count;
+    std::vector<PassList> rowA, colA, colS, rowS;
+    double* mu;
+    void* muT;
+    void *R, *G, *D;
+    double* partials;
+    int* mu_idx_ws;
+    double* gcv_ws;
+    BatchIO* io_dev;
+    cudaGraphExec_t graph;
+    int launches;
+};
+
+namespace {
+
+int family_of(int degree) {
+    return degree == 1 ? FAM_S : degree == 2 ? FAM_C : degree == 3 ? FAM_S3 : -1;
+}
+
+template <typename T>
+hobc_status launch_all(hobc_batch_s* b) {
+    cudaStream_t st = b->stream;
+    const BatchIO* io = b->io_dev;
+    const Axis<T>* axes = reinterpret_cast<const Axis<T>*>(b->axes_dev);
+    T* R = reinterpret_cast<T*>(b->R);
+    T* G = reinterpret_cast<T*>(b->G);
+    T* D = reinterpret_cast<T*>(b->D);
+    int launches = 0;
+    if (b->eig_count) { kb_eig<T><<<b->eig_count, 256, 0, st>>>(b->eig_work, b->items_dev, io, D); ++launches; }
+    for (const PassList& l : b->rowA) {
+        if (!l.count) continue;
+        if (l.fam == FAM_S) kb_pair_analysis<T, FAM_S><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, nullptr, 1, io, R);
+        else if (l.fam == FAM_C) kb_pair_analysis<T, FAM_C><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, nullptr, 1, io, R);
+        else kb_pair_analysis<T, FAM_S3><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, nullptr, 1, io, R);
+        ++launches;
+    }
+    for (const PassList& l : b->colA) {
+        if (!l.count) continue;
+        if (l.fam == FAM_S) kb_pair_analysis<T, FAM_S><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, R, 0, io, G);
+        else if (l.fam == FAM_C) kb_pair_analysis<T, FAM_C><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, R, 0, io, G);
+        else kb_pair_analysis<T, FAM_S3><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, R, 0, io, G);
+        ++launches;
+    }
+    const size_t gsmem = 4 * (size_t)gcv_chunk_for(1LL << 40, b->K, sizeof(T) == 8) * sizeof(T);
+    kb_gcv<T><<<b->gcv_count, 256, gsmem, st>>>(b->gcv_work, b->gcv_items_dev, G, D, reinterpret_cast<const T*>(b->muT),
+                                                b->partials);
+    kb_gcv_finalize<<<b->count, 256, 0, st>>>(b->gcv_items_dev, b->partials, io, b->K);
+    launches += 2;
+    FilterDesc fd;
+    memset(&fd, 0, sizeof(fd));
+    fd.mu = b->mu;
+    fd.K = b->K;
+    fd.lap = b->desc.L == HOBC_L_LAPLACIAN;
+    for (const PassList& l : b->colS) {
+        if (!l.count) continue;
+        if (l.fam == FAM_S) kb_pair_synthesis<T, FAM_S, 2><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, G, R, 0, io, D, fd);
+        else if (l.fam == FAM_C) kb_pair_synthesis<T, FAM_C, 2><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, G, R, 0, io, D, fd);
+        else kb_pair_synthesis<T, FAM_S3, 2><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, G, R, 0, io, D, fd);
+        ++launches;
+    }
+    for (const PassList& l : b->rowS) {
+        if (!l.count) continue;
+        if (l.fam == FAM_S) kb_pair_synthesis<T, FAM_S, 0><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, R, nullptr, 1, io, D, fd);
+        else if (l.fam == FAM_C) kb_pair_synthesis<T, FAM_C, 0><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, R, nullptr, 1, io, D, fd);
+        else kb_pair_synthesis<T, FAM_S3, 0><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, R, nullptr, 1, io, D, fd);
+        ++launches;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { set_last_error("hobc_deblur_batched launch", e); return HOBC_ERR_CUDA; }
+    b->launches = launches;
+    return HOBC_OK;
+}
+
+template <typename T>
+cudaError_t prepare_batched() {
+    const int lim = 200 * 1024;
+    cudaError_t e = cudaSuccess;
+#define HOBC_BSMEM(k) if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
+    HOBC_BSMEM((kb_pair_analysis<T, FAM_S>));
+    HOBC_BSMEM((kb_pair_analysis<T, FAM_C>));
+    HOBC_BSMEM((kb_pair_analysis<T, FAM_S3>));
+    HOBC_BSMEM((kb_pair_synthesis<T, FAM_S, 0>));
+    HOBC_BSMEM((kb_pair_synthesis<T, FAM_C, 0>));
+    HOBC_BSMEM((kb_pair_synthesis<T, FAM_S3, 0>));
+    HOBC_BSMEM((kb_pair_synthesis<T, FAM_S, 2>));
+    HOBC_BSMEM((kb_pair_synthesis<T, FAM_C, 2>));
+    HOBC_BSMEM((kb_pair_synthesis<T, FAM_S3, 2>));
+#undef HOBC_BSMEM
+    return e;
+}
+
+template <typename T>
+Axis<T> to_dev_axis(const AxisHost& a) {
+    Axis<T> x;
+    memset(&x, 0, sizeof(x));
+    x.fam = a.fam; x.n = a.n; x.N = a.N; x.L = a.L; x.M = a.M; x.log2M = a.log2M;
+    x.blue = a.blue; x.tpg = a.tpg; x.Mp = a.M + a.M / 16; x.H = a.H; x.W = a.W;
+    x.tw = reinterpret_cast<const C2<T>*>(a.tw);
+    x.chirp = reinterpret_cast<const C2<T>*>(a.chirp);
+    x.bhat = reinterpret_cast<const C2<T>*>(a.bhat);
+    x.post = reinterpret_cast<const C2<T>*>(a.post);
+    x.q = reinterpret_cast<const T*>(a.q);
+    x.q2 = reinterpret_cast<const T*>(a.q2);
+    x.ka = a.ka; x.kb = a.kb;
+    for (int i = 0; i < 16; ++i) x.k4[i] = a.k4[i];
+    x.q1 = (T)a.q1; x.sc = (T)a.sc; x.s0 = (T)a.s0; x.s1 = (T)a.s1;
+    x.is0 = (T)a.is0; x.is1 = (T)a.is1; x.invN = (T)a.invN;
+    return x;
+}
+
+template <typename T>
+void* upload(const std::vector<T>& v, cudaError_t& err) {
+    void* d = nullptr;
+    if (err == cudaSuccess && !v.empty()) err = cudaMalloc(&d, v.size() * sizeof(T));
+    if (err == cudaSuccess && !v.empty()) err = cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return d;
+}
+
+}  // namespace
+
+extern "C" void hobc_batch_destroy(hobc_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (AxisHost& a : b->axes_host) {
+        cudaFree(a.tw); cudaFree(a.chirp); cudaFree(a.bhat); cudaFree(a.post); cudaFree(a.q); cudaFree(a.q2);
+        cudaFree(a.etab);
+    }
+    for (auto* lists : {&b->rowA, &b->colA, &b->colS, &b->rowS})
+        for (PassList& l : *lists) cudaFree(l.dev);
+    cudaFree(b->axes_dev); cudaFree(b->items_dev); cudaFree(b->gcv_items_dev); cudaFree(b->gcv_work);
+    cudaFree(b->eig_work); cudaFree(b->mu); cudaFree(b->muT); cudaFree(b->R); cudaFree(b->G); cudaFree(b->D);
+    cudaFree(b->partials); cudaFree(b->mu_idx_ws); cudaFree(b->gcv_ws); cudaFree(b->io_dev);
+    delete b;
+}
+
+extern "C" hobc_status hobc_batch_create(const hobc_batch_desc* desc, const hobc_batch_item* items,
+                                         const double* mu_grid_host, void* cuda_stream, hobc_batch** out) {
+    if (!out) return HOBC_ERR_ARG;
+    *out = nullptr;
+    if (!desc || !items || !mu_grid_host) return HOBC_ERR_ARG;
+    const hobc_batch_desc d = *desc;
+    if (d.count < 1 || d.n_mu < 1) return HOBC_ERR_ARG;
+    if (d.prec != HOBC_FP64 && d.prec != HOBC_FP32) return HOBC_ERR_ARG;
+    if (d.L != HOBC_L_IDENTITY && d.L != HOBC_L_LAPLACIAN) return HOBC_ERR_ARG;
+    for (int j = 0; j < d.n_mu; ++j) {
+        if (!std::isfinite(mu_grid_host[j])) return HOBC_ERR_NONFINITE;
+        if (!(mu_grid_host[j] > 0)) return HOBC_ERR_ARG;
+        if (d.prec == HOBC_FP32 && (mu_grid_host[j] < 1e-18 || mu_grid_host[j] > 1e18)) return HOBC_ERR_ARG;
+    }
+    for (int i = 0; i < d.count; ++i) {
+        const hobc_batch_item& it = items[i];
+        const int fam = family_of(it.bc_degree);
+        if (fam < 0) return HOBC_ERR_UNSUPPORTED;
+        const int border = fam == FAM_S3 ? 4 : 2;
+        for (int a = 0; a < 2; ++a) {
+            const int nmax = fam == FAM_C ? 1024 : 512;          // FFT length M <= 2048
+            if (it.n[a] < 8 || it.n[a] > nmax) return HOBC_ERR_SIZE;
+            if (it.psf[a] < 1 || it.psf[a] % 2 == 0 || it.psf[a] > 63) return HOBC_ERR_SIZE;
+            if (it.psf[a] > it.n[a] - border) return HOBC_ERR_SIZE;
+        }
+    }
+    hobc_batch_s* b = new hobc_batch_s();
+    b->desc = d;
+    b->count = d.count;
+    b->K = d.n_mu;
+    b->prec = d.prec;
+    b->esz = d.prec == HOBC_FP64 ? 8 : 4;
+    b->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    b->items.assign(items, items + d.count);
+    cudaError_t err = d.prec == HOBC_FP64 ? prepare_batched<double>() : prepare_batched<float>();
+
+    // distinct axes and offsets
+    std::map<std::pair<int, int>, int> axis_id;
+    auto axis_of = [&](int fam, int n) {
+        auto key = std::make_pair(fam, n);
+        auto itr = axis_id.find(key);
+        if (itr != axis_id.end()) return itr->second;
+        AxisHost a;
+        if (err == cudaSuccess)
+            err = d.prec == HOBC_FP64 ? build_axis_host<double>(a, fam, n, 1, false) : build_axis_host<float>(a, fam, n, 1, false);
+        b->axes_host.push_back(a);
+        const int id = (int)b->axes_host.size() - 1;
+        axis_id[key] = id;
+        return id;
+    };
+    std::vector<ItemDev> idev(d.count);
+    std::vector<int> ax0(d.count), ax1(d.count);
+    b->img_off.assign(d.count + 1, 0);
+    b->psf_off.assign(d.count + 1, 0);
+    for (int i = 0; i < d.count; ++i) {
+        const hobc_batch_item& it = items[i];
+        const int fam = family_of(it.bc_degree);
+        ax0[i] = axis_of(fam, it.n[0]);
+        ax1[i] = axis_of(fam, it.n[1]);
+        b->img_off[i + 1] = b->img_off[i] + (size_t)it.n[0] * it.n[1];
+        b->psf_off[i + 1] = b->psf_off[i] + (size_t)it.psf[0] * it.psf[1];
+        ItemDev& x = idev[i];
+        x.n0 = it.n[0]; x.n1 = it.n[1]; x.p0 = it.psf[0]; x.p1 = it.psf[1]; x.fam = fam;
+        x.N0 = fam == FAM_S3 ? x.n0 - 4 : x.n0 - 2;
+        x.N1 = fam == FAM_S3 ? x.n1 - 4 : x.n1 - 2;
+        x.img_off = (long long)b->img_off[i];
+        x.psf_off = (long long)b->psf_off[i];
+    }
+    if (err == cudaSuccess) {
+        if (d.prec == HOBC_FP64) {
+            std::vector<Axis<double>> v;
+            for (auto& a : b->axes_host) v.push_back(to_dev_axis<double>(a));
+            b->axes_dev = upload(v, err);
+        } else {
+            std::vector<Axis<float>> v;
+            for (auto& a : b->axes_host) v.push_back(to_dev_axis<float>(a));
+            b->axes_dev = upload(v, err);
+        }
+    }
+    b->items_dev = reinterpret_cast<ItemDev*>(upload(idev, err));
+
+    // line work lists: every pass, per family; a CTA covers 2G lines, G = 256/(M/8)
+    const size_t csz = 2 * b->esz;
+    auto build_pass = [&](std::vector<PassList>& lists, int pass) {
+        for (int fam : {FAM_S, FAM_C, FAM_S3}) {
+            std::vector<LineWork> w;
+            size_t smem = 0;
+            for (int i = 0; i < d.count; ++i) {
+                if (idev[i].fam != fam) continue;
+                const int n0 = idev[i].n0, n1 = idev[i].n1;
+                const bool rows = pass == 0 || pass == 3;         // row passes run along axis 1
+                const int ax = rows ? ax1[i] : ax0[i];
+                const AxisHost& a = b->axes_host[ax];
+                const int G = kBatchThreads / a.tpg;
+                const int nl = rows ? n0 : n1;
+                smem = std::max(smem, (size_t)G * (a.M + a.M / 16) * csz + (size_t)2 * G * a.W * b->esz);
+                for (int r0 = 0; r0 < nl; r0 += 2 * G) {
+                    LineWork e;
+                    memset(&e, 0, sizeof(e));
+                    e.item = i; e.axis = ax; e.r0 = r0; e.nlines = nl;
+                    e.in_off = e.out_off = idev[i].img_off;
+                    e.axis_o = ax1[i];
+                    if (pass == 0) { e.in_rs = n1; e.out_rs = 1; e.out_cs = n0; }            // rows -> R[c][r]
+                    else if (pass == 1) { e.in_rs = n0; e.out_rs = n0; e.out_cs = 1; }       // R columns -> G
+                    else if (pass == 2) { e.in_rs = n0; e.in_cs = 1; e.out_rs = n0; }        // G -> R (filter)
+                    else { e.in_rs = 1; e.in_cs = n0; e.out_rs = n1; }                        // R -> f rows
+                    w.push_back(e);
+                }
+            }
+            PassList l;
+            l.fam = fam;
+            l.count = (int)w.size();
+            l.smem = smem;
+            l.dev = reinterpret_cast<LineWork*>(upload(w, err));
+            lists.push_back(l);
+        }
+    };
+    build_pass(b->rowA, 0);
+    build_pass(b->colA, 1);
+    build_pass(b->colS, 2);
+    build_pass(b->rowS, 3);
+
+    // GCV and eigenvalue work
+    std::vector<GcvItem> gi(d.count);
+    std::vector<int2> gw, ew;
+    long long part = 0;
+    for (int i = 0; i < d.count; ++i) {
+        GcvItem& g = gi[i];
+        memset(&g, 0, sizeof(g));
+        const AxisHost& a0 = b->axes_host[ax0[i]];
+        const AxisHost& a1 = b->axes_host[ax1[i]];
+        g.geo.ndim = 2; g.geo.fam = idev[i].fam;
+        g.geo.n0 = a0.n; g.geo.N0 = a0.N; g.geo.n1 = a1.n; g.geo.N1 = a1.N; g.geo.W1 = a1.W;
+        g.geo.lap = d.L == HOBC_L_LAPLACIAN;
+        g.geo.S = (long long)a1.W * a0.n;
+        g.geo.chunk = gcv_chunk_for(g.geo.S, b->K, d.prec == HOBC_FP64);
+        g.geo.K = b->K;
+        g.nchunks = (int)((g.geo.S + g.geo.chunk - 1) / g.geo.chunk);
+        g.spec_off = idev[i].img_off;
+        g.part_off = part;
+        part += (long long)g.nchunks * 2 * b->K;
+        for (int c = 0; c < g.nchunks; ++c) gw.push_back(make_int2(i, c));
+        for (int c = 0; c < idev[i].n1; ++c) ew.push_back(make_int2(i, c));
+    }
+    b->gcv_count = (int)gw.size();
+    b->eig_count = (int)ew.size();
+    b->gcv_items_dev = reinterpret_cast<GcvItem*>(upload(gi, err));
+    b->gcv_work = reinterpret_cast<int2*>(upload(gw, err));
+    b->eig_work = reinterpret_cast<int2*>(upload(ew, err));
+
+    const size_t total = b->img_off[d.count];
+    auto alloc = [&](void** p, size_t bytes) { if (err == cudaSuccess && bytes) err = cudaMalloc(p, bytes); };
+    alloc(&b->R, total * b->esz);
+    alloc(&b->G, total * b->esz);
+    alloc(&b->D, total * b->esz);
+    alloc((void**)&b->partials, (size_t)part * sizeof(double));
+    alloc((void**)&b->mu_idx_ws, (size_t)d.count * sizeof(int));
+    alloc((void**)&b->gcv_ws, (size_t)d.count * b->K * sizeof(double));
+    alloc((void**)&b->io_dev, sizeof(BatchIO));
+    alloc((void**)&b->mu, sizeof(double) * b->K);
+    alloc(&b->muT, b->esz * b->K);
+    if (err == cudaSuccess) err = cudaMemcpy(b->mu, mu_grid_host, sizeof(double) * b->K, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) {
+        if (d.prec == HOBC_FP64) {
+            err = cudaMemcpy(b->muT, mu_grid_host, sizeof(double) * b->K, cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> mf(mu_grid_host, mu_grid_host + b->K);
+            err = cudaMemcpy(b->muT, mf.data(), sizeof(float) * b->K, cudaMemcpyHostToDevice);
+        }
+    }
+    if (err != cudaSuccess) {
+        set_last_error("hobc_batch_create", err);
+        hobc_batch_destroy(b);
+        return HOBC_ERR_CUDA;
+    }
+    // capture the whole launch sequence once (needs a capturable stream)
+    if (b->stream) {
+        cudaGraph_t graph = nullptr;
+        err = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        hobc_status s = HOBC_OK;
+        if (err == cudaSuccess) s = d.prec == HOBC_FP64 ? launch_all<double>(b) : launch_all<float>(b);
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+        if (err == cudaSuccess) err = e2;
+        if (err == cudaSuccess && s == HOBC_OK) err = cudaGraphInstantiate(&b->graph, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (err != cudaSuccess || s != HOBC_OK) {
+            if (err != cudaSuccess) set_last_error("hobc_batch_create: graph capture", err);
+            hobc_batch_destroy(b);
+            return err != cudaSuccess ? HOBC_ERR_CUDA : s;
+        }
+    }
+    *out = b;
+    return HOBC_OK;
+}
+
+extern "C" hobc_status hobc_batch_offsets(const hobc_batch* b, size_t* img_off, size_t* psf_off) {
+    if (!b) return HOBC_ERR_ARG;
+    if (img_off) std::copy(b->img_off.begin(), b->img_off.end(), img_off);
+    if (psf_off) std::copy(b->psf_off.begin(), b->psf_off.end(), psf_off);
+    return HOBC_OK;
+}
+
+extern "C" int hobc_batch_launch_count(const hobc_batch* b) { return b ? b->launches : 0; }
+
+extern "C" hobc_status hobc_deblur_batched(hobc_batch* b, const void* g_dev, const void* psf_dev, void* f_dev,
+                                           int* mu_index_dev, double* gcv_dev) {
+    if (!b || !g_dev || !psf_dev || !f_dev) return HOBC_ERR_ARG;
+    BatchIO io;
+    io.g = g_dev;
+    io.psf = psf_dev;
+    io.f = f_dev;
+    io.mu_idx = mu_index_dev ? mu_index_dev : b->mu_idx_ws;
+    io.gcv = gcv_dev;
+    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    cudaError_t e = cudaMemcpyAsync(b->io_dev, &io, sizeof(io), cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) { set_last_error("hobc_deblur_batched", e); return HOBC_ERR_CUDA; }
+    if (b->graph) {
+        e = cudaGraphLaunch(b->graph, b->stream);
+        if (e != cudaSuccess) { set_last_error("hobc_deblur_batched: graph launch", e); return HOBC_ERR_CUDA; }
+        return HOBC_OK;
+    }
+    return b->prec == HOBC_FP64 ? launch_all<double>(b) : launch_all<float>(b);
+}

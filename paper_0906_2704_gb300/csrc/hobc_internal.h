@@ -73,6 +73,7 @@ template <typename T> hobc_status run_filter_synthesis(hobc_plan_s* p, const voi
                                                        const int* mu_idx, void* f);
 template <typename T> hobc_status prepare_kernels(hobc_plan_s* p);
 
+template <typename T> cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half);
 void set_last_error(const char* what, cudaError_t e);
 void set_last_error_text(const char* text);
 hobc_status launch_gcv_finalize(hobc_plan_s* p, double* gcv, int* mu_idx);

@@ -83,20 +83,18 @@ __device__ __forceinline__ T smoothing2(const FilterDesc& f, int mode, const Axi
 // grid = (ceil(nlines / 2G), items), block = G * ax.tpg.
 // =====================================================================
 template <typename T, int FAM>
-__global__ void __launch_bounds__(512)
-k_pair_analysis(const T* __restrict__ in, long long in_item, long long in_rs,
-                typename ElemT<T, FAM == FAM_F>::t* __restrict__ out, long long out_item,
-                long long out_rs, long long out_cs, int nlines, Axis<T> ax) {
+__device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, long long in_item, long long in_rs,
+                                                   typename ElemT<T, FAM == FAM_F>::t* __restrict__ out,
+                                                   long long out_item, long long out_rs, long long out_cs,
+                                                   int nlines, const Axis<T>& ax, long long item, int r0,
+                                                   unsigned char* smem_raw) {
     typedef typename ElemT<T, FAM == FAM_F>::t E;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = blockDim.x / ax.tpg;
     const int g = threadIdx.x / ax.tpg;
     const int t = threadIdx.x - g * ax.tpg;
     C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.Mp;
     E* stage = reinterpret_cast<E*>(reinterpret_cast<C2<T>*>(smem_raw) + (size_t)G * ax.Mp);
     const int n = ax.n, N = ax.N, W = ax.W;
-    const long long item = blockIdx.y;
-    const int r0 = blockIdx.x * 2 * G;
     const int ra = r0 + 2 * g, rb = ra + 1;
     const bool va = ra < nlines, vb = rb < nlines;
     const T* ya = in + item * in_item + (long long)(va ? ra : 0) * in_rs;
@@ -205,6 +203,17 @@ k_pair_analysis(const T* __restrict__ in, long long in_item, long long in_rs,
     }
 }
 
+template <typename T, int FAM>
+__global__ void __launch_bounds__(512)
+k_pair_analysis(const T* __restrict__ in, long long in_item, long long in_rs,
+                typename ElemT<T, FAM == FAM_F>::t* __restrict__ out, long long out_item,
+                long long out_rs, long long out_cs, int nlines, Axis<T> ax) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = blockDim.x / ax.tpg;
+    pair_analysis_body<T, FAM>(in, in_item, in_rs, out, out_item, out_rs, out_cs, nlines, ax, blockIdx.y,
+                               blockIdx.x * 2 * G, smem_raw);
+}
+
 // =====================================================================
 // Synthesis T_X on pairs of lines whose result is real.
 // Input spectral entry c of line r: in[i*in_item + r*in_rs + c*in_cs];
@@ -213,20 +222,18 @@ k_pair_analysis(const T* __restrict__ in, long long in_item, long long in_rs,
 // the line index is the axis-1 stored index).
 // =====================================================================
 template <typename T, int FAM, int FMODE>
-__global__ void __launch_bounds__(512)
-k_pair_synthesis(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in, long long in_item,
-                 long long in_rs, long long in_cs, T* __restrict__ out, long long out_item,
-                 long long out_rs, int nlines, Axis<T> ax, FilterDesc fd) {
+__device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in,
+                                                    long long in_item, long long in_rs, long long in_cs,
+                                                    T* __restrict__ out, long long out_item, long long out_rs,
+                                                    int nlines, const Axis<T>& ax, const FilterDesc& fd,
+                                                    long long item, int r0, unsigned char* smem_raw) {
     typedef typename ElemT<T, FAM == FAM_F>::t E;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = blockDim.x / ax.tpg;
     const int g = threadIdx.x / ax.tpg;
     const int t = threadIdx.x - g * ax.tpg;
     C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.Mp;
     E* stage = reinterpret_cast<E*>(reinterpret_cast<C2<T>*>(smem_raw) + (size_t)G * ax.Mp);
     const int n = ax.n, N = ax.N, W = ax.W;
-    const long long item = blockIdx.y;
-    const int r0 = blockIdx.x * 2 * G;
     const int rows_here = min(2 * G, nlines - r0);
 
     // gather (and filter) the spectra of this CTA's lines into the stage
@@ -365,6 +372,17 @@ k_pair_synthesis(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in, long
         if (va) { oa[0] = ax.q1 * c1a + fa; oa[n - 1] = ax.q1 * cna + la; }
         if (vb) { ob[0] = ax.q1 * c1b + fb; ob[n - 1] = ax.q1 * cnb + lb; }
     }
+}
+
+template <typename T, int FAM, int FMODE>
+__global__ void __launch_bounds__(512)
+k_pair_synthesis(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in, long long in_item,
+                 long long in_rs, long long in_cs, T* __restrict__ out, long long out_item,
+                 long long out_rs, int nlines, Axis<T> ax, FilterDesc fd) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = blockDim.x / ax.tpg;
+    pair_synthesis_body<T, FAM, FMODE>(in, in_item, in_rs, in_cs, out, out_item, out_rs, nlines, ax, fd,
+                                       blockIdx.y, blockIdx.x * 2 * G, smem_raw);
 }
 
 // =====================================================================
@@ -650,21 +668,18 @@ __device__ __forceinline__ void gcv_scan(const float4* __restrict__ pk, int cnt,
     }
 }
 
+// One CTA's share of the scan: elements [e0, e0 + chunk) of one problem whose
+// spectrum starts at spec_item and eigenvalues at d_item; sums go to outp[2K].
 template <typename T, bool CPLX>
-__global__ void __launch_bounds__(256)
-k_gcv_partials(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
-               long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo,
-               double* __restrict__ partials) {
+__device__ __forceinline__ void gcv_partials_body(const typename ElemT<T, CPLX>::t* __restrict__ spec_item,
+                                                  const typename ElemT<T, CPLX>::t* __restrict__ d_item,
+                                                  const T* __restrict__ muT, const GcvGeom& geo, long long e0,
+                                                  double* __restrict__ outp, unsigned char* smem_raw) {
     typedef typename Pack4<T>::t P4;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     P4* pk = reinterpret_cast<P4*>(smem_raw);
-    const int nch = (int)((geo.S + geo.chunk - 1) / geo.chunk);
-    const long long item = blockIdx.x / nch;
-    const int chunk = blockIdx.x - (int)(item * nch);
-    const long long e0 = (long long)chunk * geo.chunk;
     const int cnt = (int)min((long long)geo.chunk, geo.S - e0);
-    const typename ElemT<T, CPLX>::t* sp = spec + item * geo.S + e0;
-    const typename ElemT<T, CPLX>::t* dp = D + (psf_per ? item : 0) * d_psf_stride + e0;
+    const typename ElemT<T, CPLX>::t* sp = spec_item + e0;
+    const typename ElemT<T, CPLX>::t* dp = d_item + e0;
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
         const long long e = e0 + i;
         int c, t0 = 0;
@@ -691,8 +706,21 @@ k_gcv_partials(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typena
         pk[i] = v;
     }
     __syncthreads();
-    double* outp = partials + (long long)blockIdx.x * 2LL * geo.K;
     gcv_scan(pk, cnt, muT, geo.K, outp);
+}
+
+template <typename T, bool CPLX>
+__global__ void __launch_bounds__(256)
+k_gcv_partials(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
+               long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo,
+               double* __restrict__ partials) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nch = (int)((geo.S + geo.chunk - 1) / geo.chunk);
+    const long long item = blockIdx.x / nch;
+    const int chunk = blockIdx.x - (int)(item * nch);
+    gcv_partials_body<T, CPLX>(spec + item * geo.S, D + (psf_per ? item : 0) * d_psf_stride, muT, geo,
+                               (long long)chunk * geo.chunk, partials + (long long)blockIdx.x * 2LL * geo.K,
+                               smem_raw);
 }
 
 // G(mu_j) = num_j / den_j^2 and the first index of the minimum (NaN never wins).

@@ -68,6 +68,25 @@ _lib.hobc_gcv_noalloc.argtypes = [ctypes.POINTER(PlanDesc)] + [_vp] * 6
 _lib.hobc_gcv_noalloc.restype = ctypes.c_int
 _lib.hobc_gcv_noalloc_max_bytes.argtypes = []
 _lib.hobc_gcv_noalloc_max_bytes.restype = _sz
+class BatchItem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 2), ("psf", ctypes.c_int * 2), ("bc_degree", ctypes.c_int)]
+
+
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("L", ctypes.c_int), ("prec", ctypes.c_int), ("n_mu", ctypes.c_int)]
+
+
+_lib.hobc_batch_create.argtypes = [ctypes.POINTER(BatchDesc), ctypes.POINTER(BatchItem),
+                                   ctypes.POINTER(ctypes.c_double), _vp, ctypes.POINTER(_vp)]
+_lib.hobc_batch_create.restype = ctypes.c_int
+_lib.hobc_batch_destroy.argtypes = [_vp]
+_lib.hobc_batch_destroy.restype = None
+_lib.hobc_batch_offsets.argtypes = [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]
+_lib.hobc_batch_offsets.restype = ctypes.c_int
+_lib.hobc_batch_launch_count.argtypes = [_vp]
+_lib.hobc_batch_launch_count.restype = ctypes.c_int
+_lib.hobc_deblur_batched.argtypes = [_vp] * 6
+_lib.hobc_deblur_batched.restype = ctypes.c_int
 _lib.hobc_last_launch_count.argtypes = [_vp]
 _lib.hobc_last_launch_count.restype = ctypes.c_int
 _lib.hobc_status_str.argtypes = [ctypes.c_int]
@@ -246,6 +265,53 @@ class Plan:
     def close(self) -> None:
         if getattr(self, "_handle", None):
             _lib.hobc_plan_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A batch plan: many 2D problems of uneven sizes, each with its own
+    symmetric PSF and boundary degree (1, 2, 3), deblurred in one call."""
+
+    def __init__(self, items, mu_grid, L: str = "lap", prec: str = "fp64", stream=None):
+        """items: sequence of (n0, n1, psf0, psf1, bc_degree)."""
+        arr = (BatchItem * len(items))()
+        for i, (n0, n1, p0, p1, deg) in enumerate(items):
+            arr[i].n[0], arr[i].n[1], arr[i].psf[0], arr[i].psf[1], arr[i].bc_degree = n0, n1, p0, p1, deg
+        d = BatchDesc()
+        d.count, d.L, d.prec = len(items), SMOOTHING[L], PRECISION[prec]
+        mu = np.ascontiguousarray(mu_grid, dtype=np.float64)
+        d.n_mu = len(mu)
+        if stream is None:
+            stream = 0
+        elif not isinstance(stream, int):
+            stream = stream.cuda_stream
+        self._handle = _vp()
+        _check(_lib.hobc_batch_create(ctypes.byref(d), arr, mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      _vp(stream), ctypes.byref(self._handle)), "hobc_batch_create")
+        self.items, self.mu_grid, self.prec, self.L = list(items), mu, prec, L
+        io = (_sz * (len(items) + 1))()
+        po = (_sz * (len(items) + 1))()
+        _check(_lib.hobc_batch_offsets(self._handle, io, po), "hobc_batch_offsets")
+        self.img_off = np.array(io[:], dtype=np.int64)
+        self.psf_off = np.array(po[:], dtype=np.int64)
+
+    @property
+    def last_launch_count(self) -> int:
+        return _lib.hobc_batch_launch_count(self._handle)
+
+    def deblur(self, g, psf, f, mu_index=None, gcv=None) -> None:
+        _check(_lib.hobc_deblur_batched(self._handle, _ptr(g), _ptr(psf), _ptr(f), _ptr(mu_index), _ptr(gcv)),
+               "hobc_deblur_batched")
+
+    def close(self) -> None:
+        if getattr(self, "_handle", None):
+            _lib.hobc_batch_destroy(self._handle)
             self._handle = None
 
     def __del__(self):

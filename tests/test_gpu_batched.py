@@ -1,0 +1,112 @@
+"""Batched deblurring of 2D problems of uneven sizes, degrees and PSFs
+(hobc_deblur_batched) against the single-geometry plan path -- itself pinned
+to the oracle -- and directly against the oracle's G curve, mu* and f."""
+import numpy as np
+import pytest
+
+from oracle import hobc_oracle as O
+from paper_0906_2704_gb300 import synth
+import parity_utils as P
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+from paper_0906_2704_gb300 import hobc  # noqa: E402
+
+FAM = {1: "sine", 2: "cosine", 3: "sine3"}
+ITEMS = [(16, 20, 5, 3, 1), (33, 33, 7, 7, 2), (40, 28, 5, 5, 3), (9, 12, 3, 3, 1),
+         (66, 31, 9, 5, 2), (25, 64, 5, 9, 3), (18, 18, 1, 1, 2)]
+
+
+def _problems(items, seed):
+    rng = np.random.default_rng(seed)
+    gs, hs = [], []
+    for (n0, n1, p0, p1, deg) in items:
+        h = np.outer(synth.gaussian_psf_1d(rng.uniform(0.7, 1.6), p0), synth.gaussian_psf_1d(rng.uniform(0.7, 1.6), p1))
+        h /= h.sum()
+        g, _ = synth.problem_2d(int(rng.integers(1 << 30)), n0, n1, h, 0.01, count=1)
+        gs.append(g[0])
+        hs.append(h)
+    return gs, hs
+
+
+def _run(batch, gs, hs, dt, K):
+    g = torch.from_numpy(np.concatenate([x.ravel() for x in gs]).astype(dt)).cuda()
+    h = torch.from_numpy(np.concatenate([x.ravel() for x in hs]).astype(dt)).cuda()
+    f = torch.empty_like(g)
+    mi = torch.empty(len(gs), dtype=torch.int32, device="cuda")
+    G = torch.empty((len(gs), K), dtype=torch.float64, device="cuda")
+    batch.deblur(g, h, f, mi, G)
+    torch.cuda.synchronize()
+    return f.cpu().numpy(), mi.cpu().numpy(), G.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("L", ["I", "lap"])
+def test_batched_matches_plan_and_oracle(prec, L):
+    dt = np.float64 if prec == "fp64" else np.float32
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    K = 24
+    mus = synth.mu_grid(K, 1e-6, 1.0)
+    gs, hs = _problems(ITEMS, 11)
+    gs = [x.astype(dt).astype(np.float64) for x in gs]
+    hs = [x.astype(dt).astype(np.float64) for x in hs]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch = hobc.Batch(ITEMS, mus, L=L, prec=prec, stream=stream)
+        f, mi, G = _run(batch, gs, hs, dt, K)
+    assert batch.last_launch_count >= 5
+    for i, (n0, n1, p0, p1, deg) in enumerate(ITEMS):
+        fb = f[batch.img_off[i]:batch.img_off[i + 1]].reshape(n0, n1)
+        # the single-geometry plan path on the same problem
+        plan = hobc.Plan(2, (n0, n1), (p0, p1), deg, mus, L=L, prec=prec, family=FAM[deg], psf_symmetric=True)
+        fp = torch.empty((1, n0, n1), dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda")
+        mp = torch.empty(1, dtype=torch.int32, device="cuda")
+        Gp = torch.empty((1, K), dtype=torch.float64, device="cuda")
+        plan.deblur(torch.from_numpy(gs[i][None].astype(dt)).cuda(), torch.from_numpy(hs[i].astype(dt)).cuda(),
+                    fp, mp, Gp)
+        torch.cuda.synchronize()
+        assert np.max(np.abs(G[i] - Gp.cpu().numpy()[0]) / Gp.cpu().numpy()[0]) <= tol, f"G vs plan, item {i}"
+        assert mi[i] == mp.cpu().numpy()[0], f"mu* vs plan, item {i}"
+        # the two paths differ only in how the eigenvalues are summed (cosine recurrence
+        # here, complex tables there); the difference is magnified by cond(T0) cond(T1)
+        fam = P.FAM_LETTER[FAM[deg]]
+        cond = np.linalg.cond(O.transform_matrix(fam, n0)) * np.linalg.cond(O.transform_matrix(fam, n1))
+        eps = 2.0 ** -53 if prec == "fp64" else 2.0 ** -24
+        fpn = fp.cpu().numpy()[0]
+        ftol = max(1e3 * tol, 64 * eps * cond)
+        assert np.abs(fb - fpn).max() <= ftol * max(1.0, np.abs(fpn).max()), f"f vs plan, item {i}"
+        # the oracle
+        ghat, d, s, Go, ko = P.oracle_steps(fam, 2, hs[i], gs[i], L, mus)
+        if prec == "fp64":
+            gtol = max(1e-8, 1e-14 * cond)
+            assert np.max(np.abs(G[i] - Go) / Go) <= gtol, f"G vs oracle, item {i}"
+            assert mi[i] == ko or Go[mi[i]] <= (1 + gtol) * Go.min(), f"mu* vs oracle, item {i}"
+            fo = P.oracle_filtered(fam, 2, ghat, d, s, mus[mi[i]])
+            assert np.abs(fb - fo).max() <= max(1e-10, 1e-13 * cond) * max(1.0, np.abs(fo).max()), \
+                f"f vs oracle, item {i}"
+
+
+def test_graph_replay_equals_direct_launch_and_repeats():
+    K = 16
+    mus = synth.mu_grid(K, 1e-6, 1.0)
+    gs, hs = _problems(ITEMS, 5)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        graphed = hobc.Batch(ITEMS, mus, L="lap", prec="fp64", stream=stream)
+        a = _run(graphed, gs, hs, np.float64, K)
+        b = _run(graphed, gs, hs, np.float64, K)
+    direct = hobc.Batch(ITEMS, mus, L="lap", prec="fp64", stream=None)
+    c = _run(direct, gs, hs, np.float64, K)
+    for x, y, z in zip(a, b, c):
+        assert np.array_equal(x, y) and np.array_equal(x, z)
+
+
+def test_batched_rejects_bad_items():
+    mus = synth.mu_grid(4)
+    for bad, status in (((16, 16, 5, 5, 4), "HOBC_ERR_UNSUPPORTED"), ((16, 600, 5, 5, 1), "HOBC_ERR_SIZE"),
+                        ((12, 12, 9, 9, 3), "HOBC_ERR_SIZE"), ((12, 12, 4, 3, 2), "HOBC_ERR_SIZE")):
+        with pytest.raises(hobc.HobcError) as ei:
+            hobc.Batch([(20, 20, 3, 3, 2), bad], mus)
+        assert hobc.STATUS[ei.value.status] == status
