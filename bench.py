@@ -343,6 +343,105 @@ def run_ours(args):
     return 0
 
 
+def _timed(step, stream, steps, warmup):
+    """Device time of ``steps`` calls of step() after ``warmup`` untimed ones (ms)."""
+    import torch
+    for _ in range(max(warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(steps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+    return a.elapsed_time(b), clk.summary()
+
+
+def run_other(args):
+    """The other configurations, on one GPU, one JSON line each (not the headline):
+    batched  -- 4096 square problems, side log-uniform in [64, 512], own Gaussian
+                PSF (sigma U[1,4]) and degree in {1,2,3}, Laplacian, 128 mu, 1% noise
+    signals1d -- 65,536 signals n = 256, Gaussian sigma 2 (9 taps), antireflective,
+                L = I, 64 mu in [1e-8, 1], 1% noise
+    cosine512 -- 512 x 512, separable Gaussian 15 x 15 sigma 2.5, degree 2 (cosine),
+                Laplacian, 256 mu, 0.5% noise, batch 32"""
+    import torch
+    from paper_0906_2704_gb300 import hobc, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    prec = args.prec
+    npdt = np.float32 if prec == "fp32" else np.float64
+    stream = torch.cuda.Stream()
+    extra = {}
+    with torch.cuda.stream(stream):
+        if args.workload == "batched":
+            count = args.count
+            items, gs, hs = synth.batch_uneven(7, count)
+            K = 128
+            batch = hobc.Batch(items, synth.mu_grid(K), L="lap", prec=prec, stream=stream)
+            g = torch.from_numpy(np.concatenate([x.ravel() for x in gs]).astype(npdt)).to(dev)
+            h = torch.from_numpy(np.concatenate([x.ravel() for x in hs]).astype(npdt)).to(dev)
+            f = torch.empty_like(g)
+            mi = torch.empty(count, dtype=torch.int32, device=dev)
+            ms, clocks = _timed(lambda: batch.deblur(g, h, f, mi), stream, args.steps, args.warmup)
+            units, unit = count, "images/s"
+            launches = batch.last_launch_count
+            pixels = int(g.numel())
+            extra = {"pixels_per_step": pixels, "pixels_per_s": pixels * args.steps / (ms / 1e3),
+                     "degrees": np.bincount([it[4] for it in items], minlength=4)[1:].tolist(),
+                     "graph": True}
+            cfg = {"workload": f"{count} uneven 2D problems (side log-uniform in [64,512], own Gaussian PSF, "
+                               f"degree 1/2/3, Laplacian, 128 mu, 1% noise), one CUDA-graph launch",
+                   "count": count}
+            io_bytes = 2 * pixels * np.dtype(npdt).itemsize
+        elif args.workload == "signals1d":
+            B, n, K = 65536, 256, 64
+            hh = synth.gaussian_psf_1d(2.0, 9)
+            gg, _ = synth.problem_1d(3, n, hh, 0.01, count=B)
+            plan = hobc.Plan(1, n, 9, 1, synth.mu_grid(K), L="I", prec=prec, family="sine", batch=B, stream=stream)
+            g = torch.from_numpy(gg.astype(npdt)).to(dev)
+            h = torch.from_numpy(hh.astype(npdt)).to(dev)
+            f = torch.empty_like(g)
+            mi = torch.empty(B, dtype=torch.int32, device=dev)
+            ms, clocks = _timed(lambda: plan.deblur(g, h, f, mi), stream, args.steps, args.warmup)
+            units, unit, launches = B, "signals/s", plan.last_launch_count
+            cfg = {"workload": "65536 1D signals n=256, Gaussian sigma 2 (9 taps), antireflective, L=I, 64 mu, 1% noise",
+                   "batch": B}
+            io_bytes = 2 * B * n * np.dtype(npdt).itemsize
+        else:
+            B, n, K = 32, 512, 256
+            hh = synth.gaussian_psf_2d_separable(2.5, 15)
+            clean, _ = synth.problem_2d(4, n, n, hh, 0.0, count=4)
+            rng = np.random.default_rng(5)
+            gg = np.stack([synth.add_noise(rng, clean[i % 4], 0.005) for i in range(B)])
+            plan = hobc.Plan(2, (n, n), (15, 15), 2, synth.mu_grid(K), L="lap", prec=prec, family="cosine",
+                             batch=B, stream=stream)
+            g = torch.from_numpy(gg.astype(npdt)).to(dev)
+            h = torch.from_numpy(hh.astype(npdt)).to(dev)
+            f = torch.empty_like(g)
+            mi = torch.empty(B, dtype=torch.int32, device=dev)
+            ms, clocks = _timed(lambda: plan.deblur(g, h, f, mi), stream, args.steps, args.warmup)
+            units, unit, launches = B, "deblurs/s", plan.last_launch_count
+            cfg = {"workload": "512x512, separable Gaussian 15x15 sigma 2.5, degree 2 (cosine), Laplacian, 256 mu, "
+                               "0.5% noise", "batch": B}
+            io_bytes = 2 * B * n * n * np.dtype(npdt).itemsize
+    peaks, kind = measured_peaks()
+    sec = ms / args.steps / 1e3
+    line = {"metric": f"{args.workload} throughput", "value": units / sec, "unit": unit, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+            "data": "synthetic", "config": cfg, "gpu_launches": launches * args.steps,
+            "hbm_roofline": {"algorithmic_bytes_per_step": io_bytes, "achieved_gbs": io_bytes / sec / 1e9,
+                             "peak_gbs": peaks.get("hbm_gbs"), "frac": io_bytes / sec / 1e9 / peaks.get("hbm_gbs")},
+            "clocks": clocks, **extra}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,9 +451,14 @@ def main():
     ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["fourier1024", "batched", "signals1d", "cosine512"],
+                    default="fourier1024")
+    ap.add_argument("--count", type=int, default=4096, help="problems of the batched workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "fourier1024":
+        return run_other(args)
     return run_ours(args)
 
 

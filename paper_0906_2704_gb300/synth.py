@@ -40,6 +40,7 @@ __all__ = [
     "mu_grid",
     "problem_1d",
     "problem_2d",
+    "batch_uneven",
 ]
 
 
@@ -162,3 +163,30 @@ def problem_2d(seed: int, rows: int, cols: int, h: np.ndarray, eta: float,
         g[i] = add_noise(rng, blur_valid_2d(f_ext, h), eta)
         ft[i] = f_ext[m0:m0 + rows, m1:m1 + cols]
     return g, ft
+
+
+def batch_uneven(seed: int, count: int, n_lo: int = 64, n_hi: int = 512, eta: float = 0.01):
+    """``count`` square problems of uneven sizes (side log-uniform in [n_lo, n_hi]),
+    each with its own isotropic Gaussian PSF (sigma ~ U[1, 4], 2*ceil(3 sigma)+1
+    taps) and boundary degree uniform in {1, 2, 3}.
+
+    Returns (items, g_list, h_list): items are (n, n, taps, taps, degree).
+    """
+    rng = np.random.default_rng(seed)
+    items, gs, hs = [], [], []
+    for _ in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
+        sigma = rng.uniform(1.0, 4.0)
+        taps = 2 * int(np.ceil(3 * sigma)) + 1
+        deg = int(rng.integers(1, 4))
+        h1 = gaussian_psf_1d(sigma, taps)
+        h = np.outer(h1, h1)
+        m = taps // 2
+        f_ext = image_2d(rng, n + 2 * m, n + 2 * m)
+        # separable PSF: the valid 2D convolution is two valid 1D convolutions
+        tmp = np.apply_along_axis(lambda v: np.convolve(v, h1, mode="valid"), 1, f_ext)
+        gc = np.apply_along_axis(lambda v: np.convolve(v, h1, mode="valid"), 0, tmp)
+        gs.append(add_noise(rng, gc, eta))
+        hs.append(h)
+        items.append((n, n, taps, taps, deg))
+    return items, gs, hs
