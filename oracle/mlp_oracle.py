@@ -1,0 +1,111 @@
+"""FP64 CPU oracle for the learned-mu extension (not part of the paper).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests and the benchmark's CPU leg,
+never by the product path; it shares no code with the CUDA kernels.
+
+The extension predicts log10(mu) of the GCV choice from two radial spectra
+and falls back to the full GCV scan when the prediction is poor.  Everything
+below is written from its plain definition:
+
+  features (per problem, 2 x B bins): spectral entry (t0, t1) has normalised
+    frequency f_a = theta_a / pi on each axis (the angle grid of the family,
+    border columns at 0), folded into [0, 1] as min(f, 2 - f) for the Fourier
+    family, and radius rho = sqrt((f0^2 + f1^2) / 2);
+    bin b = min(B-1, floor(B rho)).  Feature b is log10 of the mean |ghat|^2
+    over the entries of bin b, feature B + b the same for |d|^2 (1e-30 is
+    added before the log; an empty bin gives log10(1e-30)).
+  network: x (128) -> GELU(W1 x + b1) (256) -> GELU(W2 h1 + b2) (256) -> w3 . h2 + b3,
+    GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2; inputs are standardised
+    with per-feature mean and scale stored with the weights.
+  loss: mean squared error of the prediction against the label.
+  optimiser: AdamW (decoupled weight decay, bias-corrected moments).
+
+parity status: pinned by tests/test_mlp_oracle.py (finite differences, a
+closed-form single-layer case, the features of a constant spectrum).
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.special import erf
+
+from . import hobc_oracle as O
+
+NBINS = 64
+
+
+def radial_bins(family: str, n0: int, n1: int, nbins: int = NBINS) -> np.ndarray:
+    """Bin index of every spectral entry (t0, t1) of an n0 x n1 problem."""
+    f0 = O.eigen_angles(family, n0) / np.pi
+    f1 = O.eigen_angles(family, n1) / np.pi
+    f0, f1 = np.minimum(f0, 2.0 - f0), np.minimum(f1, 2.0 - f1)
+    rho = np.sqrt((f0[:, None] ** 2 + f1[None, :] ** 2) / 2.0)
+    return np.minimum(nbins - 1, np.floor(nbins * rho)).astype(int)
+
+
+def features(family: str, ghat: np.ndarray, d: np.ndarray, nbins: int = NBINS) -> np.ndarray:
+    """The 2 x nbins radial log-spectra of one 2D problem (full spectra)."""
+    b = radial_bins(family, ghat.shape[0], ghat.shape[1], nbins).ravel()
+    cnt = np.bincount(b, minlength=nbins).astype(float)
+    sg = np.bincount(b, weights=np.abs(ghat.ravel()) ** 2, minlength=nbins)
+    sd = np.bincount(b, weights=np.abs(d.ravel()) ** 2, minlength=nbins)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        mg = np.where(cnt > 0, sg / np.maximum(cnt, 1), 0.0)
+        md = np.where(cnt > 0, sd / np.maximum(cnt, 1), 0.0)
+    return np.concatenate([np.log10(mg + 1e-30), np.log10(md + 1e-30)])
+
+
+def gelu(z):
+    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+
+
+def gelu_grad(z):
+    return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
+
+
+def init_params(rng: np.random.Generator, n_in=2 * NBINS, n_hidden=256):
+    """Scaled-normal initial weights (a plain He-style choice)."""
+    return {
+        "W1": rng.standard_normal((n_hidden, n_in)) * np.sqrt(2.0 / n_in),
+        "b1": np.zeros(n_hidden),
+        "W2": rng.standard_normal((n_hidden, n_hidden)) * np.sqrt(2.0 / n_hidden),
+        "b2": np.zeros(n_hidden),
+        "w3": rng.standard_normal(n_hidden) * np.sqrt(1.0 / n_hidden),
+        "b3": np.zeros(1),
+    }
+
+
+def forward(p, X):
+    """Prediction for a batch X [B, n_in] (already standardised); returns (y, cache)."""
+    z1 = X @ p["W1"].T + p["b1"]
+    h1 = gelu(z1)
+    z2 = h1 @ p["W2"].T + p["b2"]
+    h2 = gelu(z2)
+    y = h2 @ p["w3"] + p["b3"][0]
+    return y, (X, z1, h1, z2, h2)
+
+
+def loss_and_grads(p, X, t):
+    """Mean squared error and its gradient with respect to every parameter."""
+    y, (X, z1, h1, z2, h2) = forward(p, X)
+    B = X.shape[0]
+    r = y - t
+    loss = float(np.mean(r * r))
+    dy = 2.0 * r / B
+    g = {"w3": h2.T @ dy, "b3": np.array([dy.sum()])}
+    dz2 = np.outer(dy, p["w3"]) * gelu_grad(z2)
+    g["W2"] = dz2.T @ h1
+    g["b2"] = dz2.sum(axis=0)
+    dz1 = (dz2 @ p["W2"]) * gelu_grad(z1)
+    g["W1"] = dz1.T @ X
+    g["b1"] = dz1.sum(axis=0)
+    return loss, g
+
+
+def adamw_step(p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=1e-4):
+    """One AdamW update in place (step counts from 1)."""
+    for k in p:
+        m[k] = beta1 * m[k] + (1 - beta1) * g[k]
+        v[k] = beta2 * v[k] + (1 - beta2) * g[k] * g[k]
+        mh = m[k] / (1 - beta1 ** step)
+        vh = v[k] / (1 - beta2 ** step)
+        p[k] = p[k] - lr * (mh / (np.sqrt(vh) + eps) + wd * p[k])
