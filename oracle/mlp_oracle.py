@@ -16,7 +16,9 @@ below is written from its plain definition:
     added before the log; an empty bin gives log10(1e-30)).
   network: x (128) -> GELU(W1 x + b1) (256) -> GELU(W2 h1 + b2) (256) -> w3 . h2 + b3,
     GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2; inputs are standardised
-    with per-feature mean and scale stored with the weights.
+    with per-feature mean and scale stored with the weights.  The GPU uses the
+    weight matrices in bfloat16: a parity check rounds them with bf16_round.
+  choice: learned_choice, the bracket test that keeps or rejects the prediction.
   loss: mean squared error of the prediction against the label.
   optimiser: AdamW (decoupled weight decay, bias-corrected moments).
 
@@ -33,13 +35,48 @@ from . import hobc_oracle as O
 NBINS = 64
 
 
+def angle_fraction(family: str, n: int):
+    """theta_t / pi of every column t as exact integers a_t / q, folded into
+    [0, 1] for the Fourier family (min(f, 2 - f)); border columns give 0."""
+    t = np.arange(n, dtype=np.int64)
+    if family == "S":
+        q = n - 1
+        a = t.copy()
+        a[-1] = 0
+    elif family == "C":
+        q = n - 2
+        a = t - 1
+        a[[0, -1]] = 0
+    elif family == "F":
+        q = n - 2
+        a = 2 * (t - 1)
+        a[[0, -1]] = 0
+        a = np.minimum(a, 2 * q - a)
+    elif family == "S3":
+        q = n - 3
+        a = t - 1
+        a[[0, 1, n - 2, n - 1]] = 0
+    else:
+        raise ValueError(family)
+    return a, q
+
+
 def radial_bins(family: str, n0: int, n1: int, nbins: int = NBINS) -> np.ndarray:
-    """Bin index of every spectral entry (t0, t1) of an n0 x n1 problem."""
-    f0 = O.eigen_angles(family, n0) / np.pi
-    f1 = O.eigen_angles(family, n1) / np.pi
-    f0, f1 = np.minimum(f0, 2.0 - f0), np.minimum(f1, 2.0 - f1)
-    rho = np.sqrt((f0[:, None] ** 2 + f1[None, :] ** 2) / 2.0)
-    return np.minimum(nbins - 1, np.floor(nbins * rho)).astype(int)
+    """Bin index floor(nbins * rho) of every spectral entry (t0, t1), clamped to
+    nbins - 1, with rho^2 = (f0^2 + f1^2) / 2 and f = a / q from angle_fraction.
+
+    The floor is taken in exact arithmetic: many entries sit exactly on a bin
+    edge (f0 = f1 = 1/2, say), where a rounded rho would fall either way.
+    nbins^2 rho^2 = X / Y with X = nbins^2 (a0^2 q1^2 + a1^2 q0^2), Y = 2 q0^2 q1^2,
+    and floor(sqrt(X / Y)) = isqrt(X // Y).
+    """
+    a0, q0 = angle_fraction(family, n0)
+    a1, q1 = angle_fraction(family, n1)
+    X = nbins * nbins * (a0[:, None] ** 2 * q1 * q1 + a1[None, :] ** 2 * q0 * q0)
+    Y = 2 * q0 * q0 * q1 * q1
+    v = X // Y                                     # exact, at most nbins^2
+    b = np.floor(np.sqrt(v.astype(np.float64))).astype(int)   # exact for v <= 2^52
+    return np.minimum(nbins - 1, b)
 
 
 def features(family: str, ghat: np.ndarray, d: np.ndarray, nbins: int = NBINS) -> np.ndarray:
@@ -52,6 +89,15 @@ def features(family: str, ghat: np.ndarray, d: np.ndarray, nbins: int = NBINS) -
         mg = np.where(cnt > 0, sg / np.maximum(cnt, 1), 0.0)
         md = np.where(cnt > 0, sd / np.maximum(cnt, 1), 0.0)
     return np.concatenate([np.log10(mg + 1e-30), np.log10(md + 1e-30)])
+
+
+def bf16_round(x) -> np.ndarray:
+    """Round to the nearest bfloat16 (ties to even), via float32: bfloat16 keeps
+    the top 16 bits of the IEEE float32 pattern.  Finite inputs only."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 def gelu(z):
@@ -99,6 +145,38 @@ def loss_and_grads(p, X, t):
     g["W1"] = dz1.T @ X
     g["b1"] = dz1.sum(axis=0)
     return loss, g
+
+
+def learned_choice(G_at, grid: np.ndarray, y: float, width: int = 9, tol: float = 1.05):
+    """mu* of the learned path for one problem and whether it fell back.
+
+    G_at(mus) returns the GCV functional at an array of mu values.
+    mu_hat = 10^y with y clamped to the grid's log10 range (NaN -> grid start);
+    the bracket is the min(width, K) consecutive grid values around the grid
+    value nearest to mu_hat in log10 (first on ties), shifted inside the grid.
+    mu_hat is kept unless G(mu_hat) > tol * (bracket minimum of G) (or is NaN)
+    or the bracket minimum (first index) is on an edge of the bracket that is
+    not an end of the grid; then mu* is the full-grid GCV argmin (first index).
+    """
+    K = len(grid)
+    lg = np.log10(grid)
+    l = lg[0] if np.isnan(y) else min(max(float(y), lg[0]), lg[-1])
+    mu_hat = 10.0 ** l
+    kn = int(np.argmin(np.abs(lg - l)))
+    span = min(width, K)
+    k0 = max(0, min(kn - span // 2, K - span))
+    Gb = G_at(np.concatenate([[mu_hat], grid[k0:k0 + span]]))
+    inner = np.where(np.isnan(Gb[1:]), np.inf, Gb[1:])
+    am = int(np.argmin(inner))
+    mn = inner[am]
+    kmin = k0 + am
+    edge = (am == 0 and kmin > 0) or (am == span - 1 and kmin < K - 1)
+    worse = not (Gb[0] <= tol * mn)
+    if edge or worse:
+        Gf = G_at(grid)
+        Gf = np.where(np.isnan(Gf), np.inf, Gf)
+        return float(grid[int(np.argmin(Gf))]), True
+    return float(mu_hat), False
 
 
 def adamw_step(p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=1e-4):

@@ -83,3 +83,79 @@ def test_features_of_constant_spectra():
     assert np.allclose(f[:M.NBINS][~full], -30.0)
     # border columns sit at frequency 0: bin 0 holds the four corner products
     assert b.reshape(n0, n1)[0, 0] == 0 and b.reshape(n0, n1)[-1, -1] == 0
+
+
+@pytest.mark.parametrize("fam", ["S", "C", "F", "S3"])
+@pytest.mark.parametrize("n", [8, 13, 66])
+def test_angle_fraction_matches_eigen_angles(fam, n):
+    """a/q * pi is the oracle's angle grid (folded into [0, pi] for F)."""
+    from oracle import hobc_oracle as O
+    a, q = M.angle_fraction(fam, n)
+    th = O.eigen_angles(fam, n)
+    if fam == "F":
+        th = np.minimum(th, 2 * np.pi - th)
+    assert np.allclose(a / q * np.pi, th, rtol=0, atol=1e-14)
+    assert a.dtype.kind == "i" and np.all((a >= 0) & (a <= q))
+
+
+def test_exact_bins_on_and_off_edges():
+    """floor(64 rho) in exact arithmetic: f0 = f1 = 1/2 lands exactly on edge 32;
+    elsewhere the exact bins equal a float computation except within rounding
+    distance of an edge."""
+    b = M.radial_bins("C", 10, 10)          # q = 8: t = 5 gives a = 4, f = 1/2
+    assert b[5, 5] == 32 and b[0, 0] == 0 and b[9, 9] == 0
+    assert b[8, 8] == 56                     # f0 = f1 = 7/8: 64 rho = 56 exactly
+    assert b[2, 8] == 40 and b[8, 2] == 40   # f = 1/8, 7/8: rho^2 = 50/128, 64 rho = 40
+    for fam, n0, n1 in [("C", 34, 50), ("F", 66, 40), ("S", 21, 30), ("S3", 30, 19)]:
+        from oracle import hobc_oracle as O
+        f0 = O.eigen_angles(fam, n0) / np.pi
+        f1 = O.eigen_angles(fam, n1) / np.pi
+        f0, f1 = np.minimum(f0, 2 - f0), np.minimum(f1, 2 - f1)
+        r = 64 * np.sqrt((f0[:, None] ** 2 + f1[None, :] ** 2) / 2)
+        fl = np.minimum(63, np.floor(r)).astype(int)
+        ex = M.radial_bins(fam, n0, n1)
+        far = np.abs(r - np.round(r)) > 1e-9
+        assert np.array_equal(ex[far], fl[far])
+        assert np.all(np.abs(ex - fl) <= 1)
+
+
+def test_bf16_round():
+    one = np.float32(1.0)
+    ulp = 2.0 ** -7                          # bfloat16 spacing at 1
+    assert M.bf16_round(1.0) == 1.0
+    assert M.bf16_round(1.0 + ulp) == 1.0 + ulp
+    assert M.bf16_round(1.0 + ulp / 2) == 1.0                 # tie -> even
+    assert M.bf16_round(1.0 + 3 * ulp / 2) == 1.0 + 2 * ulp   # tie -> even
+    assert M.bf16_round(1.0 + 0.6 * ulp) == 1.0 + ulp
+    assert M.bf16_round(-3.0) == -3.0 and M.bf16_round(0.0) == 0.0
+    x = np.random.default_rng(0).standard_normal(1000)
+    r = M.bf16_round(x)
+    assert np.all(np.abs(r - x) <= np.abs(x) * 2.0 ** -8 * (1 + 1e-6))
+    del one
+
+
+def _bowl(c):
+    """G(mu) = (log10 mu - c)^2 + 1: a GCV-like curve with its minimum at 10^c."""
+    return lambda mus: (np.log10(np.asarray(mus, dtype=float)) - c) ** 2 + 1.0
+
+
+def test_learned_choice_cases():
+    grid = 10.0 ** np.linspace(-8, 0, 81)    # spacing 0.1 in log10
+    c = -4.0                                  # on the grid (index 40)
+    G = _bowl(c)
+    mu, fb = M.learned_choice(G, grid, c)
+    assert not fb and np.isclose(mu, 1e-4)
+    mu, fb = M.learned_choice(G, grid, c + 0.2)   # G = 1.04 <= 1.05 * 1
+    assert not fb and np.isclose(mu, 10 ** (c + 0.2))
+    mu, fb = M.learned_choice(G, grid, c + 0.3)   # G = 1.09 > 1.05, minimum inside
+    assert fb and np.isclose(mu, 1e-4)
+    mu, fb = M.learned_choice(G, grid, c + 3.0)   # minimum far outside the bracket
+    assert fb and np.isclose(mu, 1e-4)
+    mu, fb = M.learned_choice(G, grid, np.nan)    # NaN -> grid start, minimum outside
+    assert fb and np.isclose(mu, 1e-4)
+    Gend = _bowl(0.0)                             # minimum at the grid's last value
+    mu, fb = M.learned_choice(Gend, grid, 5.0)    # clamped to 1: edge is the grid end
+    assert not fb and np.isclose(mu, 1.0)
+    small = 10.0 ** np.linspace(-2, 0, 5)         # K = 5 < 9: the bracket is the grid
+    mu, fb = M.learned_choice(_bowl(-1.0), small, -1.0)
+    assert not fb and np.isclose(mu, 0.1)
