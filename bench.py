@@ -442,6 +442,138 @@ def run_other(args):
     return 0
 
 
+def _learned_chunk(seed: int, count: int, n: int, taps: int, truth: bool):
+    """One worker's share of the learned-mu problems (float32 to keep transfers small)."""
+    from paper_0906_2704_gb300 import synth
+    g, ft, h, eta = synth.learned_set(seed, count, n, taps)
+    return g.astype(np.float32), (ft.astype(np.float32) if truth else None), h.astype(np.float32), eta
+
+
+def _learned_data(pool, seed: int, count: int, n: int, taps: int, truth: bool, per: int = 64):
+    jobs = [(seed * 100003 + i, min(per, count - i * per), n, taps, truth) for i in range((count + per - 1) // per)]
+    parts = pool.starmap(_learned_chunk, jobs)
+    g = np.concatenate([p[0] for p in parts])
+    ft = np.concatenate([p[1] for p in parts]) if truth else None
+    h = np.concatenate([p[2] for p in parts])
+    eta = np.concatenate([p[3] for p in parts])
+    return g, ft, h, eta
+
+
+def run_learned(args):
+    """Learned choice of mu against the full GCV scan, at equal relative error.
+
+    Problems: images as in the other 2D workloads blurred by out-of-focus disks
+    (radius U[1.5, 5], 11 x 11 PSF array, one per image), noise log-uniform in
+    [1e-3, 3e-2]; degree 2 (cosine family), Laplacian, 256 mu in [1e-8, 1], FP32.
+    The network is trained here (outside the timed region) on GCV labels of
+    ``--train`` problems at 256^2 and timed on 1024 other problems at 256^2
+    (plus a 1024^2 pass of 64 problems)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    n, taps, K = 256, 11, 256
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(min(16, cores)) as pool:      # before the first GPU call
+        gtr, _, htr, _ = _learned_data(pool, 1, args.train, n, taps, False)
+        gte, fte, hte, etate = _learned_data(pool, 2, 1024, n, taps, True)
+        gbig, fbig, hbig, _ = _learned_data(pool, 3, 64, 1024, taps, True, per=4)
+    t_data = time.time() - t0
+    import torch
+    from paper_0906_2704_gb300 import hobc, learned, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    mus = synth.mu_grid(K)
+    B = 512
+    plan = hobc.Plan(2, (n, n), (taps, taps), 2, mus, L="lap", prec="fp32", family="cosine", psf_symmetric=True,
+                     batch=B, psf_per_item=True, stream=stream)
+    # ---- training (not timed)
+    t1 = time.time()
+    Xs, ts = [], []
+    for s in range(0, len(gtr) - B + 1, B):
+        X, t, _ = learned.features_and_labels(plan, torch.from_numpy(gtr[s:s + B]).to(dev),
+                                              torch.from_numpy(htr[s:s + B]).to(dev))
+        Xs.append(X)
+        ts.append(t)
+    Xtr, ttr = torch.cat(Xs), torch.cat(ts)
+    net = learned.init_network(Xtr, 256, seed=0, stream=stream.cuda_stream)
+    hist = learned.fit(net, Xtr, ttr, epochs=args.epochs, batch=256, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.time() - t1
+    # ---- inference: learned vs full scan on the same 1024 test problems
+    g_d = torch.from_numpy(gte).to(dev)
+    h_d = torch.from_numpy(hte).to(dev)
+    f_l = torch.empty_like(g_d)
+    f_g = torch.empty_like(g_d)
+    mu_l = torch.empty(len(gte), dtype=torch.float64, device=dev)
+    fb_l = torch.empty(len(gte), dtype=torch.int32, device=dev)
+    mi_g = torch.empty(len(gte), dtype=torch.int32, device=dev)
+    chunks = [slice(s, s + B) for s in range(0, len(gte), B)]
+
+    def step_learned():
+        for c in chunks:
+            plan.deblur_learned(net, g_d[c], h_d[c], f_l[c], mu_l[c], fb_l[c])
+
+    def step_gcv():
+        for c in chunks:
+            plan.deblur(g_d[c], h_d[c], f_g[c], mi_g[c])
+
+    ms_l, clk_l = _timed(step_learned, stream, args.steps, args.warmup)
+    launches = plan.last_launch_count * len(chunks)
+    ms_g, clk_g = _timed(step_gcv, stream, args.steps, args.warmup)
+
+    def rre(f, ft):
+        d = (f.astype(np.float64) - ft).reshape(len(ft), -1)
+        return np.linalg.norm(d, axis=1) / np.linalg.norm(ft.reshape(len(ft), -1), axis=1)
+
+    r_l, r_g = rre(f_l.cpu().numpy(), fte), rre(f_g.cpu().numpy(), fte)
+    fb = fb_l.cpu().numpy()
+    lab = np.log10(mus)[mi_g.cpu().numpy()]
+    pred_err = np.abs(np.log10(mu_l.cpu().numpy()) - lab)
+    # ---- the same network on 64 problems at 1024^2 (a size it was not trained on)
+    Bb = 16
+    plan_b = hobc.Plan(2, (1024, 1024), (taps, taps), 2, mus, L="lap", prec="fp32", family="cosine",
+                       psf_symmetric=True, batch=Bb, psf_per_item=True, stream=stream)
+    gb_d, hb_d = torch.from_numpy(gbig).to(dev), torch.from_numpy(hbig).to(dev)
+    fb_lb, fb_gb = torch.empty_like(gb_d), torch.empty_like(gb_d)
+    fbb = torch.empty(len(gbig), dtype=torch.int32, device=dev)
+    mib = torch.empty(len(gbig), dtype=torch.int32, device=dev)
+    cb = [slice(s, s + Bb) for s in range(0, len(gbig), Bb)]
+    ms_lb, _ = _timed(lambda: [plan_b.deblur_learned(net, gb_d[c], hb_d[c], fb_lb[c], None, fbb[c]) for c in cb],
+                      stream, max(1, args.steps // 2), 3)
+    ms_gb, _ = _timed(lambda: [plan_b.deblur(gb_d[c], hb_d[c], fb_gb[c], mib[c]) for c in cb],
+                      stream, max(1, args.steps // 2), 3)
+    rb_l, rb_g = rre(fb_lb.cpu().numpy(), fbig), rre(fb_gb.cpu().numpy(), fbig)
+    sec_l, sec_g = ms_l / args.steps / 1e3, ms_g / args.steps / 1e3
+    peaks, _ = measured_peaks()
+    io_bytes = 2 * gte.size * 4
+    line = {"metric": "learned-mu deblurs/s at equal relative error (256x256, cosine family, disk PSF)",
+            "value": len(gte) / sec_l, "unit": "images/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_l / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "1024 problems 256x256, disk PSF r~U[1.5,5] (11x11), noise log-U[1e-3,3e-2], "
+                                   "degree 2 (cosine), Laplacian, 256 mu in [1e-8,1], learned mu with bracket "
+                                   "check; inputs 268 MB (> L2)", "batch": B, "train_problems": int(len(gtr))},
+            "gcv_scan": {"value": len(gte) / sec_g, "unit": "images/s", "ms_per_step": ms_g / args.steps},
+            "speedup_vs_gcv_scan": sec_g / sec_l,
+            "rre": {"learned_mean": float(r_l.mean()), "gcv_mean": float(r_g.mean()),
+                    "ratio": float(r_l.mean() / r_g.mean()),
+                    "worst_item_ratio": float(np.max(r_l / r_g))},
+            "fallback_rate": float(fb.mean()),
+            "log10_mu_abs_err_vs_gcv": {"median": float(np.median(pred_err)), "p90": float(np.quantile(pred_err, 0.9))},
+            "train": {"seconds": t_train, "data_seconds": t_data, "epochs": args.epochs,
+                      "loss_first": hist[0], "loss_last": hist[-1]},
+            "at_1024": {"images": int(len(gbig)), "learned_images_per_s": len(gbig) / (ms_lb / max(1, args.steps // 2) / 1e3),
+                        "gcv_images_per_s": len(gbig) / (ms_gb / max(1, args.steps // 2) / 1e3),
+                        "fallback_rate": float(fbb.cpu().numpy().mean()),
+                        "rre_ratio": float(rb_l.mean() / rb_g.mean())},
+            "gpu_launches": launches * args.steps,
+            "hbm_roofline": {"algorithmic_bytes_per_step": io_bytes, "achieved_gbs": io_bytes / sec_l / 1e9,
+                             "peak_gbs": peaks.get("hbm_gbs"), "frac": io_bytes / sec_l / 1e9 / peaks.get("hbm_gbs")},
+            "clocks": clk_l, "clocks_gcv_scan": clk_g}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -451,12 +583,16 @@ def main():
     ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["fourier1024", "batched", "signals1d", "cosine512"],
+    ap.add_argument("--workload", choices=["fourier1024", "batched", "signals1d", "cosine512", "learned"],
                     default="fourier1024")
+    ap.add_argument("--train", type=int, default=8192, help="training problems of the learned workload")
+    ap.add_argument("--epochs", type=int, default=60, help="training epochs of the learned workload")
     ap.add_argument("--count", type=int, default=4096, help="problems of the batched workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "learned":
+        return run_learned(args)
     if args.workload != "fourier1024":
         return run_other(args)
     return run_ours(args)

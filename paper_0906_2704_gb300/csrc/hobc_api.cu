@@ -345,6 +345,7 @@ void hobc_plan_destroy(hobc_plan* p) {
     cudaFree(p->mu); cudaFree(p->muT); cudaFree(p->R); cudaFree(p->G); cudaFree(p->D);
     cudaFree(p->partials); cudaFree(p->gcv); cudaFree(p->mu_idx);
     cudaFree(p->g_in); cudaFree(p->f_out); cudaFree(p->psf_in);
+    free_learned_ws(p);
     delete p;
 }
 

@@ -60,6 +60,21 @@ struct hobc_plan_s {
     void* f_out;             // [batch][img]
     void* psf_in;            // [npsf][psf]
     int launches;
+    // learned-mu workspace, allocated on first use (hobc_learned.cu)
+    double* feat_partials;   // [batch][feature chunks][3 * bins]
+    float* feat;             // [batch][2 * bins]
+    float* mlp_y;            // [batch] predicted log10(mu)
+    void* bracket_mu;        // [batch][J] plan precision
+    double* mu_hat;          // [batch]
+    int* bracket_k0;         // [batch]
+    double* bracket_partials;// [batch][chunks][2J]
+    double* bracket_G;       // [batch][J]
+    int* bracket_idx;        // [batch]
+    double* mu_val;          // [batch] mu* used by the filter
+    int* fell_back;          // [batch]
+    double* log_grid;        // [K] log10 of the mu grid (host-computed)
+    unsigned char* bin_tab;  // [spec] radial bin (bits 0-5) and pair weight flag (bit 6)
+    int grid_ascending;      // 1 if the mu grid is strictly increasing
 };
 
 namespace hobc {
@@ -71,7 +86,10 @@ template <typename T> hobc_status run_gcv(hobc_plan_s* p, const void* ghat, cons
                                           int* mu_idx);
 template <typename T> hobc_status run_filter_synthesis(hobc_plan_s* p, const void* ghat, const void* D,
                                                        const int* mu_idx, void* f);
+template <typename T> hobc_status run_filter_synthesis_mu(hobc_plan_s* p, const void* ghat, const void* D,
+                                                          const double* mu_val, void* f);
 template <typename T> hobc_status prepare_kernels(hobc_plan_s* p);
+void free_learned_ws(hobc_plan_s* p);
 
 template <typename T> cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half);
 void set_last_error(const char* what, cudaError_t e);

@@ -52,10 +52,12 @@ struct FilterDesc {
     int K;                  // grid size (caller indices are clamped to [0, K))
     int lap;                // 1: Laplacian smoothing, 0: identity
     int o_fam, o_n, o_N, o_W;   // 2D: the other axis (axis 1, indexed by line)
+    const double* mu_val;   // [problems] mu* itself; when set it replaces mu_idx / mu
 };
 
 // mu* of a problem; an index outside the grid is clamped so it cannot read past it.
 __device__ __forceinline__ double mu_of(const FilterDesc& f, int problem) {
+    if (f.mu_val) return f.mu_val[problem];
     const int k = f.mu_idx[problem];
     return f.mu[k < 0 ? 0 : (k >= f.K ? f.K - 1 : k)];
 }
@@ -480,6 +482,10 @@ k_cplx_synthesis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long lon
 // Eigenvalues d[c][t0] = sum_{j0,j1} h[j0][j1] E0[t0][j0] E1[c][j1] with
 // E[t][j] = exp(-i (j - m) theta_t)  (Eq. (eq:symbol) at -theta, Sec. 6),
 // accumulated in double.  1D problems use n0 = p0 = 1 and E0 = [[1]].
+// The row stage P_k = sum_j1 h[m0 + k][j1] E1[c][j1] is combined over tap
+// offsets +-k:  P_k e^{-ik th} + P_{-k} e^{ik th} = A_k cos(k th) - i B_k sin(k th),
+// A_k = P_k + P_{-k}, B_k = P_k - P_{-k}, so the real part costs two products
+// per k (four with the imaginary part) instead of eight.
 // grid = (npsf, W1), block = 256.
 // =====================================================================
 template <typename T, bool CPLX>
@@ -487,9 +493,11 @@ __global__ void k_eig(const T* __restrict__ psf, long long psf_stride, int p0, i
                       const double2* __restrict__ E0, const double2* __restrict__ E1, int n0,
                       typename ElemT<T, CPLX>::t* __restrict__ D, long long d_psf_stride) {
     __shared__ double2 P[64];
+    __shared__ double2 A[32], Bk[32];
     const int c = blockIdx.y;
     const long long ip = blockIdx.x;
     const T* h = psf + ip * psf_stride;
+    const int m0 = p0 / 2;
     for (int j0 = threadIdx.x; j0 < p0; j0 += blockDim.x) {
         double re = 0, im = 0;
         for (int j1 = 0; j1 < p1; ++j1) {
@@ -501,14 +509,21 @@ __global__ void k_eig(const T* __restrict__ psf, long long psf_stride, int p0, i
         P[j0] = make_double2(re, im);
     }
     __syncthreads();
+    for (int k = 1 + threadIdx.x; k <= m0; k += blockDim.x) {
+        const double2 pp = P[m0 + k], pm = P[m0 - k];
+        A[k] = make_double2(pp.x + pm.x, pp.y + pm.y);
+        Bk[k] = make_double2(pp.x - pm.x, pp.y - pm.y);
+    }
+    __syncthreads();
     typename ElemT<T, CPLX>::t* o = D + ip * d_psf_stride + (long long)c * n0;
     for (int t0 = threadIdx.x; t0 < n0; t0 += blockDim.x) {
-        double re = 0, im = 0;
-        const double2* e0 = E0 + (long long)t0 * p0;
-        for (int j0 = 0; j0 < p0; ++j0) {
-            const double2 a = P[j0], b = e0[j0];
-            re += a.x * b.x - a.y * b.y;
-            im += a.x * b.y + a.y * b.x;
+        double re = P[m0].x, im = P[m0].y;
+        const double2* e0 = E0 + (long long)t0 * p0 + m0;
+        for (int k = 1; k <= m0; ++k) {
+            const double2 e = e0[k];          // (cos k th, -sin k th)
+            const double2 a = A[k], b = Bk[k];
+            re += a.x * e.x - b.y * e.y;
+            if constexpr (CPLX) im += a.y * e.x + b.x * e.y;
         }
         if constexpr (CPLX) o[t0] = cmk<T>((T)re, (T)im);
         else o[t0] = (T)re;
@@ -668,6 +683,37 @@ __device__ __forceinline__ void gcv_scan(const float4* __restrict__ pk, int cnt,
     }
 }
 
+// The GCV terms of stored element e of a problem: x = a = |d|^2 / s^2 (capped),
+// y = w |ghat|^2, z = w, with w = 2 for a Fourier entry that stands for a
+// conjugate pair; an entry with s = 0 contributes nothing.
+template <typename T, bool CPLX>
+__device__ __forceinline__ typename Pack4<T>::t gcv_term(const typename ElemT<T, CPLX>::t& spv,
+                                                         const typename ElemT<T, CPLX>::t& dpv, const GcvGeom& geo,
+                                                         long long e) {
+    int c, t0 = 0;
+    if (geo.ndim == 2) { c = (int)(e / geo.n0); t0 = (int)(e - (long long)c * geo.n0); }
+    else c = (int)e;
+    T w = 1;
+    if (CPLX) {
+        const bool self = (c == 0 || c == geo.W1 - 1 || c == 1 || 2 * (c - 1) == geo.N1);
+        w = self ? (T)1 : (T)2;
+    }
+    T s2 = 1;
+    if (geo.lap) {
+        const int t1 = stored_to_t(geo.fam, geo.n1, geo.W1, c);
+        T s = lap_eig<T>(theta_over_pi<T>(geo.fam, geo.n1, geo.N1, t1));
+        if (geo.ndim == 2) s += lap_eig<T>(theta_over_pi<T>(geo.fam, geo.n0, geo.N0, t0));
+        s2 = s * s;
+    }
+    const T lam = abs2_of(dpv);
+    const T g2 = abs2_of(spv);
+    typename Pack4<T>::t v;
+    if (s2 > (T)0) { v.x = min(lam / s2, a_cap<T>()); v.y = w * g2; v.z = w; }
+    else { v.x = (T)1; v.y = (T)0; v.z = (T)0; }
+    v.w = 0;
+    return v;
+}
+
 // One CTA's share of the scan: elements [e0, e0 + chunk) of one problem whose
 // spectrum starts at spec_item and eigenvalues at d_item; sums go to outp[2K].
 template <typename T, bool CPLX>
@@ -680,31 +726,7 @@ __device__ __forceinline__ void gcv_partials_body(const typename ElemT<T, CPLX>:
     const int cnt = (int)min((long long)geo.chunk, geo.S - e0);
     const typename ElemT<T, CPLX>::t* sp = spec_item + e0;
     const typename ElemT<T, CPLX>::t* dp = d_item + e0;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const long long e = e0 + i;
-        int c, t0 = 0;
-        if (geo.ndim == 2) { c = (int)(e / geo.n0); t0 = (int)(e - (long long)c * geo.n0); }
-        else c = (int)e;
-        T w = 1;
-        if (CPLX) {
-            const bool self = (c == 0 || c == geo.W1 - 1 || c == 1 || 2 * (c - 1) == geo.N1);
-            w = self ? (T)1 : (T)2;
-        }
-        T s2 = 1;
-        if (geo.lap) {
-            const int t1 = stored_to_t(geo.fam, geo.n1, geo.W1, c);
-            T s = lap_eig<T>(theta_over_pi<T>(geo.fam, geo.n1, geo.N1, t1));
-            if (geo.ndim == 2) s += lap_eig<T>(theta_over_pi<T>(geo.fam, geo.n0, geo.N0, t0));
-            s2 = s * s;
-        }
-        const T lam = abs2_of(dp[i]);
-        const T g2 = abs2_of(sp[i]);
-        P4 v;
-        if (s2 > (T)0) { v.x = min(lam / s2, a_cap<T>()); v.y = w * g2; v.z = w; }
-        else { v.x = (T)1; v.y = (T)0; v.z = (T)0; }
-        v.w = 0;
-        pk[i] = v;
-    }
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) pk[i] = gcv_term<T, CPLX>(sp[i], dp[i], geo, e0 + i);
     __syncthreads();
     gcv_scan(pk, cnt, muT, geo.K, outp);
 }

@@ -102,6 +102,7 @@ static inline FilterDesc make_filter(const hobc_plan_s* p, const void* D, const 
     f.lap = p->desc.L == HOBC_L_LAPLACIAN;
     const AxisHost& o = p->ax[p->nax - 1];
     f.o_fam = o.fam; f.o_n = o.n; f.o_N = o.N; f.o_W = o.W;
+    f.mu_val = nullptr;
     return f;
 }
 
@@ -183,6 +184,20 @@ hobc_status run_synthesis(hobc_plan_s* p, const void* c, void* y) {
 template <typename T>
 hobc_status run_filter_synthesis(hobc_plan_s* p, const void* ghat, const void* D, const int* mu_idx, void* f) {
     FilterDesc fd = make_filter(p, D, mu_idx);
+    T* ft = reinterpret_cast<T*>(f);
+    switch (p->fam) {
+        case FAM_S: return synthesis_fam<T, FAM_S, true>(p, ghat, ft, fd);
+        case FAM_S3: return synthesis_fam<T, FAM_S3, true>(p, ghat, ft, fd);
+        case FAM_C: return synthesis_fam<T, FAM_C, true>(p, ghat, ft, fd);
+        default: return synthesis_fam<T, FAM_F, true>(p, ghat, ft, fd);
+    }
+}
+
+// The same with mu* given per problem as a value rather than a grid index.
+template <typename T>
+hobc_status run_filter_synthesis_mu(hobc_plan_s* p, const void* ghat, const void* D, const double* mu_val, void* f) {
+    FilterDesc fd = make_filter(p, D, nullptr);
+    fd.mu_val = mu_val;
     T* ft = reinterpret_cast<T*>(f);
     switch (p->fam) {
         case FAM_S: return synthesis_fam<T, FAM_S, true>(p, ghat, ft, fd);
@@ -292,4 +307,6 @@ hobc_status prepare_kernels(hobc_plan_s* p) {
     template hobc_status hobc::run_gcv<T>(hobc_plan_s*, const void*, const void*, double*, int*);            \
     template hobc_status hobc::run_filter_synthesis<T>(hobc_plan_s*, const void*, const void*, const int*,   \
                                                        void*);                                               \
+    template hobc_status hobc::run_filter_synthesis_mu<T>(hobc_plan_s*, const void*, const void*,             \
+                                                          const double*, void*);                             \
     template hobc_status hobc::prepare_kernels<T>(hobc_plan_s*);

@@ -1,4 +1,5 @@
-"""Python binding of the C ABI in include/hobc.h (ctypes; marshalling only).
+"""Python binding of the C ABI in include/hobc.h and include/hobc_learned.h
+(ctypes; marshalling only).
 
 Every step of the method runs in the CUDA library ``libhobc.so`` built in this
 package directory by ``paper_0906_2704_gb300.build``.  There is no fallback: if
@@ -19,6 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhobc.so")
 HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "hobc.h")
+HEADER_PATHS = [HEADER_PATH, os.path.join(os.path.dirname(_HERE), "include", "hobc_learned.h")]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_0906_2704_gb300.build`")
@@ -93,6 +95,32 @@ _lib.hobc_status_str.argtypes = [ctypes.c_int]
 _lib.hobc_status_str.restype = ctypes.c_char_p
 _lib.hobc_last_error.argtypes = []
 _lib.hobc_last_error.restype = ctypes.c_char_p
+_lib.hobc_features.argtypes = [_vp] * 4
+_lib.hobc_features.restype = ctypes.c_int
+_lib.hobc_deblur_learned.argtypes = [_vp] * 7
+_lib.hobc_deblur_learned.restype = ctypes.c_int
+_lib.hobc_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp]
+_lib.hobc_mlp_create.restype = ctypes.c_int
+_lib.hobc_mlp_destroy.argtypes = [_vp]
+_lib.hobc_mlp_destroy.restype = None
+_lib.hobc_mlp_param_count.argtypes = [_vp]
+_lib.hobc_mlp_param_count.restype = ctypes.c_int
+_lib.hobc_mlp_last_launch_count.argtypes = [_vp]
+_lib.hobc_mlp_last_launch_count.restype = ctypes.c_int
+for _name in ("hobc_mlp_set_params", "hobc_mlp_get_params"):
+    getattr(_lib, _name).argtypes = [_vp, _vp]
+    getattr(_lib, _name).restype = ctypes.c_int
+for _name in ("hobc_mlp_save", "hobc_mlp_load"):
+    getattr(_lib, _name).argtypes = [_vp, ctypes.c_char_p]
+    getattr(_lib, _name).restype = ctypes.c_int
+_lib.hobc_mlp_forward.argtypes = [_vp, _vp, ctypes.c_int, _vp]
+_lib.hobc_mlp_forward.restype = ctypes.c_int
+_lib.hobc_mlp_gradients.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]
+_lib.hobc_mlp_gradients.restype = ctypes.c_int
+_lib.hobc_mlp_train_step.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_float, ctypes.c_float, _vp]
+_lib.hobc_mlp_train_step.restype = ctypes.c_int
+
+FEATURE_BINS = 64
 
 
 class HobcError(RuntimeError):
@@ -109,9 +137,11 @@ def _check(status: int, what: str) -> None:
 
 
 def declared_functions() -> list[str]:
-    """Names of the functions declared in include/hobc.h."""
-    with open(HEADER_PATH) as fh:
-        text = fh.read()
+    """Names of the functions declared in include/hobc.h and include/hobc_learned.h."""
+    text = ""
+    for path in HEADER_PATHS:
+        with open(path) as fh:
+            text += fh.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(hobc_[a-z_0-9]+)\s*\(", text)))
 
@@ -262,6 +292,13 @@ class Plan:
         _check(_lib.hobc_filter_synthesis(self._handle, _ptr(ghat), _ptr(d), _ptr(mu_index), _ptr(f)),
                "hobc_filter_synthesis")
 
+    def features(self, ghat, d, x) -> None:
+        _check(_lib.hobc_features(self._handle, _ptr(ghat), _ptr(d), _ptr(x)), "hobc_features")
+
+    def deblur_learned(self, net: "MLP", g, psf, f, mu=None, fell_back=None) -> None:
+        _check(_lib.hobc_deblur_learned(self._handle, net._handle, _ptr(g), _ptr(psf), _ptr(f), _ptr(mu),
+                                        _ptr(fell_back)), "hobc_deblur_learned")
+
     def close(self) -> None:
         if getattr(self, "_handle", None):
             _lib.hobc_plan_destroy(self._handle)
@@ -319,3 +356,80 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class MLP:
+    """The mu-predicting network of include/hobc_learned.h on one GPU."""
+
+    def __init__(self, n_in: int = 2 * FEATURE_BINS, n_hidden: int = 256, stream=None):
+        if stream is None:
+            stream = 0
+        elif not isinstance(stream, int):
+            stream = stream.cuda_stream
+        self._handle = _vp()
+        _check(_lib.hobc_mlp_create(n_in, n_hidden, _vp(stream), ctypes.byref(self._handle)), "hobc_mlp_create")
+        self.n_in, self.n_hidden = n_in, n_hidden
+        self.param_count = _lib.hobc_mlp_param_count(self._handle)
+
+    @property
+    def last_launch_count(self) -> int:
+        return _lib.hobc_mlp_last_launch_count(self._handle)
+
+    def set_params(self, flat) -> None:
+        """flat: float32 host array of param_count + 2 n_in values (parameters, mean, scale)."""
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        if a.size != self.param_count + 2 * self.n_in:
+            raise ValueError("wrong parameter vector length")
+        _check(_lib.hobc_mlp_set_params(self._handle, a.ctypes.data), "hobc_mlp_set_params")
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.param_count + 2 * self.n_in, dtype=np.float32)
+        _check(_lib.hobc_mlp_get_params(self._handle, a.ctypes.data), "hobc_mlp_get_params")
+        return a
+
+    def forward(self, x, y) -> None:
+        _check(_lib.hobc_mlp_forward(self._handle, _ptr(x), int(x.shape[0]), _ptr(y)), "hobc_mlp_forward")
+
+    def gradients(self, x, t, grad=None, loss=None) -> None:
+        _check(_lib.hobc_mlp_gradients(self._handle, _ptr(x), _ptr(t), int(x.shape[0]), _ptr(grad), _ptr(loss)),
+               "hobc_mlp_gradients")
+
+    def train_step(self, x, t, lr: float, weight_decay: float = 1e-4, loss=None) -> None:
+        _check(_lib.hobc_mlp_train_step(self._handle, _ptr(x), _ptr(t), int(x.shape[0]), lr, weight_decay,
+                                        _ptr(loss)), "hobc_mlp_train_step")
+
+    def save(self, path: str) -> None:
+        _check(_lib.hobc_mlp_save(self._handle, path.encode()), "hobc_mlp_save")
+
+    def load(self, path: str) -> None:
+        _check(_lib.hobc_mlp_load(self._handle, path.encode()), "hobc_mlp_load")
+
+    def close(self) -> None:
+        if getattr(self, "_handle", None):
+            _lib.hobc_mlp_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pack_params(p: dict, mean, scale) -> np.ndarray:
+    """Flat float32 vector (W1, b1, W2, b2, w3, b3, mean, scale) in the ABI's layout."""
+    parts = [p["W1"], p["b1"], p["W2"], p["b2"], p["w3"], p["b3"], mean, scale]
+    return np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in parts]).astype(np.float32)
+
+
+def unpack_params(flat, n_in: int, n_hidden: int):
+    """Inverse of pack_params: (params dict, mean, scale) as float64 arrays."""
+    flat = np.asarray(flat, dtype=np.float64)
+    sizes = [("W1", (n_hidden, n_in)), ("b1", (n_hidden,)), ("W2", (n_hidden, n_hidden)), ("b2", (n_hidden,)),
+             ("w3", (n_hidden,)), ("b3", (1,))]
+    out, o = {}, 0
+    for k, shp in sizes:
+        cnt = int(np.prod(shp))
+        out[k] = flat[o:o + cnt].reshape(shp)
+        o += cnt
+    return out, flat[o:o + n_in], flat[o + n_in:o + 2 * n_in]

@@ -23,6 +23,11 @@ paper's own signals and images exist only as figures, so these stand in):
     plus a linear ramp, the image experiments of Sec. 6.1.
   * ``gaussian_psf_1d``, ``gaussian_psf_2d_separable``,
     ``gaussian_psf_2d_rotated`` -- Gaussian blurs (symmetric and nonsymmetric).
+  * ``disk_psf`` -- out-of-focus blur (a uniform disk), as in the image
+    experiments of Sec. 6.1; symmetric in each axis.
+  * ``learned_set`` -- the training / inference problems of the learned choice
+    of mu: images as above, disk PSFs of radius U[1.5, 5], noise level
+    log-uniform in [1e-3, 3e-2].
 """
 from __future__ import annotations
 
@@ -41,6 +46,8 @@ __all__ = [
     "problem_1d",
     "problem_2d",
     "batch_uneven",
+    "disk_psf",
+    "learned_set",
 ]
 
 
@@ -190,3 +197,39 @@ def batch_uneven(seed: int, count: int, n_lo: int = 64, n_hi: int = 512, eta: fl
         hs.append(h)
         items.append((n, n, taps, taps, deg))
     return items, gs, hs
+
+
+def disk_psf(radius: float) -> np.ndarray:
+    """Uniform disk of the given radius on a (2 ceil(radius) + 1)^2 grid:
+    h[r, c] = 1 where (r - m)^2 + (c - m)^2 <= radius^2, normalised to sum 1."""
+    m = int(np.ceil(radius))
+    j = np.arange(-m, m + 1, dtype=np.float64)
+    h = ((j[:, None] ** 2 + j[None, :] ** 2) <= radius * radius).astype(np.float64)
+    return h / h.sum()
+
+
+def learned_set(seed: int, count: int, n: int, taps: int = 11, r_lo: float = 1.5, r_hi: float = 5.0,
+                eta_lo: float = 1e-3, eta_hi: float = 3e-2):
+    """``count`` n x n problems for the learned choice of mu, each with its own
+    disk PSF (radius U[r_lo, r_hi], embedded centred in a taps x taps array so
+    that one plan serves all) and noise level (log-uniform in [eta_lo, eta_hi]).
+
+    Returns (g[count, n, n], f_true[count, n, n], h[count, taps, taps], eta[count]).
+    """
+    rng = np.random.default_rng(seed)
+    m = taps // 2
+    g = np.empty((count, n, n))
+    ft = np.empty((count, n, n))
+    hs = np.zeros((count, taps, taps))
+    etas = np.empty(count)
+    for i in range(count):
+        r = rng.uniform(r_lo, min(r_hi, m))
+        d = disk_psf(r)
+        k = d.shape[0] // 2
+        hs[i, m - k:m + k + 1, m - k:m + k + 1] = d
+        eta = float(np.exp(rng.uniform(np.log(eta_lo), np.log(eta_hi))))
+        f_ext = image_2d(rng, n + 2 * m, n + 2 * m)
+        g[i] = add_noise(rng, blur_valid_2d(f_ext, hs[i]), eta)
+        ft[i] = f_ext[m:m + n, m:m + n]
+        etas[i] = eta
+    return g, ft, hs, etas

@@ -81,3 +81,27 @@ def test_binding_has_no_cpu_fallback(hobc):
         hobc._ptr(torch.zeros(4))
     with pytest.raises(ValueError):
         hobc._hptr(np.zeros((4, 4))[:, ::2])
+
+
+def test_learned_entry_points_reject_bad_arguments_on_the_host(hobc):
+    """The learned-mu calls of include/hobc_learned.h check their arguments
+    before any CUDA call (no device needed)."""
+    lib = hobc.library()
+    out = ctypes.c_void_p()
+    arg = hobc.STATUS.index("HOBC_ERR_ARG")
+    assert lib.hobc_mlp_create(0, 16, None, ctypes.byref(out)) == arg
+    assert lib.hobc_mlp_create(128, 0, None, ctypes.byref(out)) == arg
+    assert lib.hobc_mlp_create(5000, 16, None, ctypes.byref(out)) == arg
+    assert lib.hobc_mlp_create(128, 16, None, None) == arg
+    assert lib.hobc_mlp_param_count(None) == 0
+    assert lib.hobc_mlp_last_launch_count(None) == 0
+    assert lib.hobc_mlp_set_params(None, None) == arg
+    assert lib.hobc_mlp_get_params(None, None) == arg
+    assert lib.hobc_mlp_forward(None, None, 1, None) == arg
+    assert lib.hobc_mlp_gradients(None, None, None, 1, None, None) == arg
+    assert lib.hobc_mlp_train_step(None, None, None, 1, 1e-3, 0.0, None) == arg
+    assert lib.hobc_mlp_save(None, b"x") == arg
+    assert lib.hobc_mlp_load(None, b"x") == arg
+    assert lib.hobc_features(None, None, None, None) == arg
+    assert lib.hobc_deblur_learned(None, None, None, None, None, None, None) == arg
+    lib.hobc_mlp_destroy(None)
