@@ -275,6 +275,27 @@ def run_ours(args):
         torch.cuda.synchronize()
         steps_ms[name] = a.elapsed_time(b) / args.steps
 
+    # the binned choice of mu (histogram localises, exact G decides) on the same batch
+    f_b = torch.empty_like(g_d)
+    mi_b = torch.empty(B, dtype=torch.int32, device=dev)
+    fb_b = torch.empty(B, dtype=torch.int32, device=dev)
+    ms_b, clk_b = _timed(lambda: plan.deblur_binned(g_d, h_d, f_b, mi_b, fb_b), stream, args.steps, args.warmup)
+    binned_launches = plan.last_launch_count
+    ms_b = max_over_ranks(ms_b, dist, dev)
+
+    def rre(f):
+        d = (f.cpu().numpy().astype(np.float64) - ft).reshape(B, -1)
+        return np.linalg.norm(d, axis=1) / np.linalg.norm(ft.reshape(B, -1), axis=1)
+
+    plan.deblur(g_d, h_d, f_d, mi_d, None)
+    r_full, r_bin = rre(f_d), rre(f_b)
+    binned = {"value": whole_job_rate(world, B, args.steps, ms_b / 1e3), "unit": "deblurs/s",
+              "ms_per_step": ms_b / args.steps, "gpu_launches": binned_launches * args.steps,
+              "fallback_rate": float(fb_b.float().mean()),
+              "index_agreement_with_full_scan": float((mi_b == mi_d).float().mean()),
+              "rre_mean": {"full_scan": float(r_full.mean()), "binned": float(r_bin.mean())},
+              "clocks": clk_b}
+
     # end to end through the host-buffer entry point (pinned host memory)
     g_h = torch.from_numpy(g.astype(npdt)).pin_memory().numpy()
     h_h = np.ascontiguousarray(h.astype(npdt))
@@ -334,6 +355,7 @@ def run_ours(args):
                        "l2": "inputs+outputs %.0f MB per step > 129 MB L2 (no flush)" % (2 * B * N_SIDE ** 2 * esz / 1e6)},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
             "hbm_roofline": hbm, "steps_ms": steps_ms, "cpu_baseline": cpu, "clocks": clocks,
+            "binned_mu": binned,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -517,15 +539,25 @@ def run_learned(args):
         for c in chunks:
             plan.deblur(g_d[c], h_d[c], f_g[c], mi_g[c])
 
+    f_b = torch.empty_like(g_d)
+    mi_b = torch.empty(len(gte), dtype=torch.int32, device=dev)
+    fb_b = torch.empty(len(gte), dtype=torch.int32, device=dev)
+
+    def step_binned():
+        for c in chunks:
+            plan.deblur_binned(g_d[c], h_d[c], f_b[c], mi_b[c], fb_b[c])
+
     ms_l, clk_l = _timed(step_learned, stream, args.steps, args.warmup)
     launches = plan.last_launch_count * len(chunks)
     ms_g, clk_g = _timed(step_gcv, stream, args.steps, args.warmup)
+    ms_b, clk_b = _timed(step_binned, stream, args.steps, args.warmup)
 
     def rre(f, ft):
         d = (f.astype(np.float64) - ft).reshape(len(ft), -1)
         return np.linalg.norm(d, axis=1) / np.linalg.norm(ft.reshape(len(ft), -1), axis=1)
 
     r_l, r_g = rre(f_l.cpu().numpy(), fte), rre(f_g.cpu().numpy(), fte)
+    r_b = rre(f_b.cpu().numpy(), fte)
     fb = fb_l.cpu().numpy()
     lab = np.log10(mus)[mi_g.cpu().numpy()]
     pred_err = np.abs(np.log10(mu_l.cpu().numpy()) - lab)
@@ -542,7 +574,12 @@ def run_learned(args):
                       stream, max(1, args.steps // 2), 3)
     ms_gb, _ = _timed(lambda: [plan_b.deblur(gb_d[c], hb_d[c], fb_gb[c], mib[c]) for c in cb],
                       stream, max(1, args.steps // 2), 3)
+    fb_bb = torch.empty_like(gb_d)
+    mib_b = torch.empty(len(gbig), dtype=torch.int32, device=dev)
+    ms_bb, _ = _timed(lambda: [plan_b.deblur_binned(gb_d[c], hb_d[c], fb_bb[c], mib_b[c]) for c in cb],
+                      stream, max(1, args.steps // 2), 3)
     rb_l, rb_g = rre(fb_lb.cpu().numpy(), fbig), rre(fb_gb.cpu().numpy(), fbig)
+    rb_b = rre(fb_bb.cpu().numpy(), fbig)
     sec_l, sec_g = ms_l / args.steps / 1e3, ms_g / args.steps / 1e3
     peaks, _ = measured_peaks()
     io_bytes = 2 * gte.size * 4
@@ -559,13 +596,22 @@ def run_learned(args):
                     "ratio": float(r_l.mean() / r_g.mean()),
                     "worst_item_ratio": float(np.max(r_l / r_g))},
             "fallback_rate": float(fb.mean()),
+            "binned_mu": {"value": len(gte) / (ms_b / args.steps / 1e3), "unit": "images/s",
+                          "fallback_rate": float(fb_b.float().mean()),
+                          "index_agreement_with_full_scan": float((mi_b == mi_g).float().mean()),
+                          "rre_ratio": float(r_b.mean() / r_g.mean()), "clocks": clk_b},
+            "rre_median": {"learned": float(np.median(r_l)), "gcv": float(np.median(r_g)),
+                           "binned": float(np.median(r_b))},
             "log10_mu_abs_err_vs_gcv": {"median": float(np.median(pred_err)), "p90": float(np.quantile(pred_err, 0.9))},
             "train": {"seconds": t_train, "data_seconds": t_data, "epochs": args.epochs,
                       "loss_first": hist[0], "loss_last": hist[-1]},
             "at_1024": {"images": int(len(gbig)), "learned_images_per_s": len(gbig) / (ms_lb / max(1, args.steps // 2) / 1e3),
                         "gcv_images_per_s": len(gbig) / (ms_gb / max(1, args.steps // 2) / 1e3),
                         "fallback_rate": float(fbb.cpu().numpy().mean()),
-                        "rre_ratio": float(rb_l.mean() / rb_g.mean())},
+                        "rre_ratio": float(rb_l.mean() / rb_g.mean()),
+                        "binned_images_per_s": len(gbig) / (ms_bb / max(1, args.steps // 2) / 1e3),
+                        "binned_index_agreement": float((mib_b == mib).float().mean()),
+                        "binned_rre_ratio": float(rb_b.mean() / rb_g.mean())},
             "gpu_launches": launches * args.steps,
             "hbm_roofline": {"algorithmic_bytes_per_step": io_bytes, "achieved_gbs": io_bytes / sec_l / 1e9,
                              "peak_gbs": peaks.get("hbm_gbs"), "frac": io_bytes / sec_l / 1e9 / peaks.get("hbm_gbs")},

@@ -74,6 +74,9 @@ struct hobc_plan_s {
     int* fell_back;          // [batch]
     double* log_grid;        // [K] log10 of the mu grid (host-computed)
     unsigned char* bin_tab;  // [spec] radial bin (bits 0-5) and pair weight flag (bit 6)
+    double* ahist_partials;  // [batch][chunks][3][128] histogram over log10 a of the binned choice
+    void* a_edges;           // [129] bin edges, plan precision
+    int* k_hat;              // [batch] argmin of the binned G
     int grid_ascending;      // 1 if the mu grid is strictly increasing
 };
 

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <vector>
 
+#include "../../include/hobc_binned.h"
 #include "../../include/hobc_learned.h"
 #include "hobc_internal.h"
 #include "hobc_kernels.cuh"
@@ -24,7 +25,7 @@ constexpr int kBins = 64;            // radial bins per spectrum
 constexpr int kFeat = 2 * kBins;     // network inputs
 static_assert(kBins == 64, "k_features gives each lane of a warp two bins");
 constexpr int kJ = 10;               // bracket width: mu_hat and up to 9 grid values
-constexpr int kBracketChunk = 4096;  // spectral entries per bracket-scan CTA
+constexpr int kBracketChunk = 16384; // spectral entries per bracket-scan CTA
 
 // ------------------------------------------------------------ features
 
@@ -420,6 +421,27 @@ k_gcv_bracket(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typenam
     }
 }
 
+// G at the kJ bracket values of every problem from the per-CTA sums: twelve
+// groups of 20 threads split the chunks, then combine in group order.
+// grid = items, block = 256; G [item][kJ].
+__global__ void k_bracket_finalize(const double* __restrict__ partials, int nchunks, double* __restrict__ G) {
+    constexpr int V = 2 * kJ, NG = 256 / V;
+    __shared__ double acc[NG][V];
+    const int item = blockIdx.x;
+    const int g = threadIdx.x / V, v = threadIdx.x % V;
+    if (g < NG) {
+        double a = 0;
+        for (int c = g; c < nchunks; c += NG) a += partials[((long long)item * nchunks + c) * V + v];
+        acc[g][v] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < kJ) {
+        double num = 0, den = 0;
+        for (int q = 0; q < NG; ++q) { num += acc[q][threadIdx.x]; den += acc[q][kJ + threadIdx.x]; }
+        G[(long long)item * kJ + threadIdx.x] = num / (den * den);
+    }
+}
+
 template <typename T, bool CPLX>
 __global__ void __launch_bounds__(256)
 k_gcv_masked(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
@@ -436,7 +458,8 @@ k_gcv_masked(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename
 
 // argmin over the full grid for the problems that fell back; mu_val = grid[argmin]
 __global__ void k_masked_finalize(const double* __restrict__ partials, int nchunks, int K, const int* __restrict__ mask,
-                                  const double* __restrict__ grid, double* __restrict__ mu_val) {
+                                  const double* __restrict__ grid, double* __restrict__ mu_val,
+                                  int* __restrict__ mu_idx) {
     __shared__ double sv[256];
     __shared__ int si[256];
     const int item = blockIdx.x;
@@ -467,18 +490,220 @@ __global__ void k_masked_finalize(const double* __restrict__ partials, int nchun
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) mu_val[item] = grid[si[0] == 0x7fffffff ? 0 : si[0]];
+    if (threadIdx.x == 0) {
+        const int k = si[0] == 0x7fffffff ? 0 : si[0];
+        if (mu_val) mu_val[item] = grid[k];
+        if (mu_idx) mu_idx[item] = k;
+    }
+}
+
+// ------------------------------------------------------------- binned choice
+
+constexpr int kABins = 128;          // bins of log10 a over [1e-12, 1e4)
+constexpr int kAChunk = 16384;       // spectral entries per histogram CTA (2048 per warp)
+constexpr double kALo = -12.0, kAHi = 4.0;
+
+// Per-CTA histogram of the GCV terms over a = |d|^2/|s|^2: per bin the weight
+// W, the energy E = w |ghat|^2 and A = w a.  An entry's bin is the number of
+// interior edges <= a (end bins take everything outside); entries with s = 0
+// are left out.  Same deterministic warp reduction as k_features.
+// grid = items x ceil(S / geo.chunk), block = 256; partials [CTA][3][kABins].
+template <typename T, bool CPLX>
+__global__ void __launch_bounds__(256)
+k_ahist(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
+        long long d_psf_stride, int psf_per, GcvGeom geo, const T* __restrict__ edges,
+        double* __restrict__ partials) {
+    __shared__ float ws[8][3][kABins];
+    __shared__ T ed[kABins + 1];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    for (int k = threadIdx.x; k <= kABins; k += blockDim.x) ed[k] = edges[k];
+    for (int k = lane; k < 3 * kABins; k += 32) ws[warp][k / kABins][k % kABins] = 0.f;
+    __syncthreads();
+    const int nch = (int)((geo.S + geo.chunk - 1) / geo.chunk);
+    const long long item = blockIdx.x / nch;
+    const int ci = blockIdx.x - (int)(item * nch);
+    const long long e0 = (long long)ci * geo.chunk;
+    const int cnt = (int)min((long long)geo.chunk, geo.S - e0);
+    const typename ElemT<T, CPLX>::t* sp = spec + item * geo.S + e0;
+    const typename ElemT<T, CPLX>::t* dp = D + (psf_per ? item : 0) * d_psf_stride + e0;
+    const int per_warp = (cnt + 7) / 8;
+    const int w0 = warp * per_warp, w1 = min(cnt, w0 + per_warp);
+    for (int base = w0; base < w1; base += 32) {
+        const int i = base + lane;
+        bool valid = i < w1;
+        int key = -1 - lane;
+        float vc = 0.f, vg = 0.f, va = 0.f;
+        if (valid) {
+            const typename Pack4<T>::t v = gcv_term<T, CPLX>(sp[i], dp[i], geo, e0 + i);
+            valid = v.z > (T)0;
+            if (valid) {
+                int lo = 1, hi = kABins;                // first interior edge > a
+                while (lo < hi) {
+                    const int mid = (lo + hi) / 2;
+                    if (ed[mid] <= v.x) lo = mid + 1; else hi = mid;
+                }
+                key = lo - 1;
+                vc = (float)v.z;
+                vg = (float)v.y;
+                va = (float)(v.z * v.x);
+            }
+        }
+        const int prev = __shfl_up_sync(FULL, key, 1);
+        const bool head = lane == 0 || prev != key;
+        const unsigned heads = __ballot_sync(FULL, head);
+        const int run = __popc(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int r = __shfl_up_sync(FULL, run, d);
+            const float a = __shfl_up_sync(FULL, vc, d);
+            const float b = __shfl_up_sync(FULL, vg, d);
+            const float c = __shfl_up_sync(FULL, va, d);
+            if (lane >= d && r == run) { vc += a; vg += b; va += c; }
+        }
+        const int next = __shfl_down_sync(FULL, run, 1);
+        const bool tail = valid && (lane == 31 || next != run);
+        const unsigned tails = __ballot_sync(FULL, tail);
+        if (tail) {
+            const unsigned same = __match_any_sync(tails, key);
+            const int rank = __popc(same & ((1u << lane) - 1u));
+            const int rounds = __reduce_max_sync(tails, (unsigned)__popc(same));
+            for (int r = 0; r < rounds; ++r) {
+                if (rank == r) {
+                    ws[warp][0][key] += vc;
+                    ws[warp][1][key] += vg;
+                    ws[warp][2][key] += va;
+                }
+                __syncwarp(tails);
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    double* o = partials + (long long)blockIdx.x * 3 * kABins;
+    for (int k = threadIdx.x; k < 3 * kABins; k += blockDim.x) {
+        double acc = 0;
+        for (int v = 0; v < 8; ++v) acc += ws[v][k / kABins][k % kABins];
+        o[k] = acc;
+    }
+}
+
+// Per problem: the bin sums over all chunks, G_bin(mu_j) for every grid value
+// (normalised energies and weights, FP32 terms, 1/(abar + mu) with abar + mu
+// kept >= 1e-18), its first minimiser k_hat (NaN never wins), and the bracket
+// of min(9, K) grid values around k_hat as the list of the exact scan.
+// grid = items, block = 256.
+template <typename T>
+__global__ void k_binned_khat(const double* __restrict__ partials, int nchunks, const double* __restrict__ grid, int K,
+                              int* __restrict__ k_hat, int* __restrict__ k0_out, T* __restrict__ lists) {
+    __shared__ float sa[kABins], se[kABins], sw[kABins];
+    __shared__ double rmax[kABins], rsum[kABins];
+    __shared__ float sv[256];
+    __shared__ int si[256];
+    const int item = blockIdx.x;
+    __shared__ double sum3[3 * kABins];
+    const double* p = partials + (long long)item * nchunks * 3 * kABins;
+    for (int k = threadIdx.x; k < 3 * kABins; k += blockDim.x) {   // chunk sums, four loads in flight
+        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        int c = 0;
+        for (; c + 4 <= nchunks; c += 4) {
+            a0 += p[(long long)c * 3 * kABins + k];
+            a1 += p[(long long)(c + 1) * 3 * kABins + k];
+            a2 += p[(long long)(c + 2) * 3 * kABins + k];
+            a3 += p[(long long)(c + 3) * 3 * kABins + k];
+        }
+        for (; c < nchunks; ++c) a0 += p[(long long)c * 3 * kABins + k];
+        sum3[k] = (a0 + a1) + (a2 + a3);
+    }
+    __syncthreads();
+    const double W = threadIdx.x < kABins ? sum3[threadIdx.x] : 0.0;
+    const double E = threadIdx.x < kABins ? sum3[kABins + threadIdx.x] : 0.0;
+    const double A = threadIdx.x < kABins ? sum3[2 * kABins + threadIdx.x] : 0.0;
+    if (threadIdx.x < kABins) {
+        rmax[threadIdx.x] = E;
+        rsum[threadIdx.x] = W;
+    }
+    __syncthreads();
+    for (int st = kABins / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) {
+            rmax[threadIdx.x] = fmax(rmax[threadIdx.x], rmax[threadIdx.x + st]);
+            rsum[threadIdx.x] += rsum[threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    const double emax = rmax[0] > 0 ? rmax[0] : 1.0, wtot = rsum[0] > 0 ? rsum[0] : 1.0;
+    if (threadIdx.x < kABins) {
+        const int b = threadIdx.x;
+        sa[b] = W > 0 ? (float)(A / W) : 1.f;
+        se[b] = (float)(E / emax);
+        sw[b] = (float)(W / wtot);
+    }
+    __syncthreads();
+    float best = INFINITY;
+    int bi = 0x7fffffff;
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        const float mu = (float)grid[j];
+        float num = 0.f, den = 0.f;
+        for (int b = 0; b < kABins; ++b) {
+            const float r = __frcp_rn(fmaxf(sa[b] + mu, 1e-18f));
+            den = fmaf(sw[b], r, den);
+            num = fmaf(se[b] * r, r, num);
+        }
+        const float G = (float)((double)num / ((double)den * (double)den));
+        const float key = isnan(G) ? INFINITY : G;
+        if (key < best || (key == best && j < bi)) { best = key; bi = j; }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) {
+            if (sv[threadIdx.x + st] < sv[threadIdx.x] ||
+                (sv[threadIdx.x + st] == sv[threadIdx.x] && si[threadIdx.x + st] < si[threadIdx.x])) {
+                sv[threadIdx.x] = sv[threadIdx.x + st];
+                si[threadIdx.x] = si[threadIdx.x + st];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int kh = si[0] == 0x7fffffff ? 0 : si[0];
+        const int span = min(kJ - 1, K);
+        const int k0 = max(0, min(kh - span / 2, K - span));
+        k_hat[item] = kh;
+        k0_out[item] = k0;
+        T* o = lists + (long long)item * kJ;
+        for (int j = 0; j < kJ; ++j) o[j] = (T)grid[k0 + min(j, span - 1)];
+    }
+}
+
+// The exact G on the bracket: its first minimiser is mu* unless it lies on a
+// bracket edge that is not an end of the grid (then the problem falls back).
+__global__ void k_binned_decide(const double* __restrict__ Gb, int K, const int* __restrict__ k0,
+                                int* __restrict__ mu_idx, int* __restrict__ fell_back, int B) {
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= B) return;
+    const int span = min(kJ - 1, K);
+    const double* g = Gb + (long long)item * kJ;
+    double mn = INFINITY;
+    int am = 0;
+    for (int j = 0; j < span; ++j)
+        if (g[j] < mn) { mn = g[j]; am = j; }
+    const int kmin = k0[item] + am;
+    const bool edge = (am == 0 && kmin > 0) || (am == span - 1 && kmin < K - 1);
+    fell_back[item] = edge ? 1 : 0;
+    mu_idx[item] = kmin;
 }
 
 void free_learned_ws(hobc_plan_s* p) {
     void* ps[] = {p->feat_partials, p->feat, p->mlp_y, p->bracket_mu, p->mu_hat, p->bracket_k0,
                   p->bracket_partials, p->bracket_G, p->bracket_idx, p->mu_val, p->fell_back, p->log_grid,
-                  p->bin_tab};
+                  p->bin_tab, p->ahist_partials, p->a_edges, p->k_hat};
     for (void* q : ps) cudaFree(q);
     p->feat_partials = nullptr; p->feat = nullptr; p->mlp_y = nullptr; p->bracket_mu = nullptr;
     p->mu_hat = nullptr; p->bracket_k0 = nullptr; p->bracket_partials = nullptr; p->bracket_G = nullptr;
     p->bracket_idx = nullptr; p->mu_val = nullptr; p->fell_back = nullptr; p->log_grid = nullptr;
-    p->bin_tab = nullptr;
+    p->bin_tab = nullptr; p->ahist_partials = nullptr; p->a_edges = nullptr; p->k_hat = nullptr;
 }
 
 }  // namespace hobc
@@ -760,20 +985,22 @@ namespace {
 
 constexpr int kFeatChunk = 2048;     // spectral entries per features CTA
 
-int bracket_size(const hobc_plan_s* p) { return 1 + std::min(9, p->K); }
+int bracket_size(const hobc_plan_s* p) { return 1 + std::min(kJ - 1, p->K); }
 
 cudaError_t ensure_learned_ws(hobc_plan_s* p) {
     if (p->log_grid) return cudaSuccess;
     const size_t B = (size_t)p->desc.batch;
     const size_t S = p->spec_elems;
-    const int J = bracket_size(p);
     const size_t fch = (S + kFeatChunk - 1) / kFeatChunk;
     const size_t bch = (S + kBracketChunk - 1) / kBracketChunk;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** ptr, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(ptr, bytes); };
-    alloc((void**)&p->feat_partials, B * fch * 3 * kBins * sizeof(double));
-    alloc((void**)&p->feat, B * kFeat * sizeof(float));
-    alloc((void**)&p->mlp_y, B * sizeof(float));
+    if (p->nax == 2) {            // features of the learned choice (2D only)
+        alloc((void**)&p->feat_partials, B * fch * 3 * kBins * sizeof(double));
+        alloc((void**)&p->feat, B * kFeat * sizeof(float));
+        alloc((void**)&p->mlp_y, B * sizeof(float));
+        alloc((void**)&p->bin_tab, S);
+    }
     alloc(&p->bracket_mu, B * kJ * p->esz);
     alloc((void**)&p->mu_hat, B * sizeof(double));
     alloc((void**)&p->bracket_k0, B * sizeof(int));
@@ -781,8 +1008,21 @@ cudaError_t ensure_learned_ws(hobc_plan_s* p) {
     alloc((void**)&p->bracket_G, B * kJ * sizeof(double));
     alloc((void**)&p->bracket_idx, B * sizeof(int));
     alloc((void**)&p->mu_val, B * sizeof(double));
-    alloc((void**)&p->bin_tab, S);
+    alloc((void**)&p->fell_back, B * sizeof(int));
+    alloc((void**)&p->ahist_partials, B * ((S + kAChunk - 1) / kAChunk) * 3 * kABins * sizeof(double));
+    alloc(&p->a_edges, (kABins + 1) * p->esz);
+    alloc((void**)&p->k_hat, B * sizeof(int));
     alloc((void**)&p->log_grid, (size_t)p->K * sizeof(double));
+    if (e == cudaSuccess) {       // the histogram's bin edges 10^(lo + b (hi - lo) / nb), in plan precision
+        std::vector<double> ed(kABins + 1);
+        for (int b = 0; b <= kABins; ++b) ed[b] = std::pow(10.0, kALo + (b * (kAHi - kALo)) / kABins);
+        if (p->prec == HOBC_FP64) {
+            e = cudaMemcpy(p->a_edges, ed.data(), ed.size() * sizeof(double), cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> ef(ed.begin(), ed.end());
+            e = cudaMemcpy(p->a_edges, ef.data(), ef.size() * sizeof(float), cudaMemcpyHostToDevice);
+        }
+    }
     if (e == cudaSuccess && p->nax == 2) {
         GcvGeom geo;
         memset(&geo, 0, sizeof(geo));
@@ -863,7 +1103,7 @@ hobc_status run_learned(hobc_plan_s* p, hobc_mlp_s* q, const void* g, const void
         k_gcv_bracket<T, false><<<gridJ, 256, 0, p->stream>>>(
             reinterpret_cast<const T*>(p->G), reinterpret_cast<const T*>(p->D), (long long)p->spec_elems,
             p->desc.psf_per_item, lists, geo, p->bracket_partials);
-    k_gcv_finalize<<<B, 256, 0, p->stream>>>(p->bracket_partials, nchJ, kJ, p->bracket_G, p->bracket_idx);
+    k_bracket_finalize<<<B, 256, 0, p->stream>>>(p->bracket_partials, nchJ, p->bracket_G);
     double* mu_val = mu_out ? mu_out : p->mu_val;
     int* fb = fb_out ? fb_out : p->fell_back;
     k_bracket_decide<<<(B + 127) / 128, 128, 0, p->stream>>>(p->bracket_G, J, p->bracket_k0, K, p->mu_hat, mu_val, fb, B);
@@ -880,11 +1120,82 @@ hobc_status run_learned(hobc_plan_s* p, hobc_mlp_s* q, const void* g, const void
         k_gcv_masked<T, false><<<gridK, 256, smemK, p->stream>>>(
             reinterpret_cast<const T*>(p->G), reinterpret_cast<const T*>(p->D), (long long)p->spec_elems,
             p->desc.psf_per_item, reinterpret_cast<const T*>(p->muT), geo, fb, p->partials);
-    k_masked_finalize<<<B, 256, 0, p->stream>>>(p->partials, p->gcv_chunks, K, fb, p->mu, mu_val);
+    k_masked_finalize<<<B, 256, 0, p->stream>>>(p->partials, p->gcv_chunks, K, fb, p->mu, mu_val, nullptr);
     p->launches += 6;
     s = check("hobc_deblur_learned");
     if (s != HOBC_OK) return s;
     return run_filter_synthesis_mu<T>(p, p->G, p->D, mu_val, f);
+}
+
+template <typename T>
+GcvGeom spectrum_geo(const hobc_plan_s* p) {
+    GcvGeom geo;
+    memset(&geo, 0, sizeof(geo));
+    const AxisHost& last = p->ax[p->nax - 1];
+    geo.ndim = p->nax; geo.fam = p->fam; geo.n0 = p->ax[0].n; geo.N0 = p->ax[0].N;
+    geo.n1 = last.n; geo.N1 = last.N; geo.W1 = last.W; geo.lap = p->desc.L == HOBC_L_LAPLACIAN;
+    geo.S = (long long)p->spec_elems;
+    return geo;
+}
+
+// The binned choice on a plan's spectra: histogram, k_hat, exact G on the
+// bracket, decision, and the masked full scan for the problems that fell back.
+template <typename T>
+hobc_status run_gcv_binned(hobc_plan_s* p, const void* ghat, const void* D, int* mu_idx, int* fb, int* khat) {
+    const int B = p->desc.batch, K = p->K;
+    const bool cplx = p->fam == HOBC_FAMILY_FOURIER;
+    typedef C2<T> CT;
+    GcvGeom geo = spectrum_geo<T>(p);
+    geo.chunk = kAChunk;
+    const int nch = (int)((geo.S + kAChunk - 1) / kAChunk);
+    const unsigned gridA = (unsigned)(nch * (long long)B);
+    const T* edges = reinterpret_cast<const T*>(p->a_edges);
+    if (cplx)
+        k_ahist<T, true><<<gridA, 256, 0, p->stream>>>(reinterpret_cast<const CT*>(ghat), reinterpret_cast<const CT*>(D),
+                                                        geo.S, p->desc.psf_per_item, geo, edges, p->ahist_partials);
+    else
+        k_ahist<T, false><<<gridA, 256, 0, p->stream>>>(reinterpret_cast<const T*>(ghat), reinterpret_cast<const T*>(D),
+                                                         geo.S, p->desc.psf_per_item, geo, edges, p->ahist_partials);
+    T* lists = reinterpret_cast<T*>(p->bracket_mu);
+    k_binned_khat<T><<<B, 256, 0, p->stream>>>(p->ahist_partials, nch, p->mu, K, khat, p->bracket_k0, lists);
+    geo.K = kJ;
+    geo.chunk = kBracketChunk;
+    const int nchJ = (int)((geo.S + kBracketChunk - 1) / kBracketChunk);
+    const unsigned gridJ = (unsigned)(nchJ * (long long)B);
+    if (cplx)
+        k_gcv_bracket<T, true><<<gridJ, 256, 0, p->stream>>>(reinterpret_cast<const CT*>(ghat),
+                                                              reinterpret_cast<const CT*>(D), geo.S,
+                                                              p->desc.psf_per_item, lists, geo, p->bracket_partials);
+    else
+        k_gcv_bracket<T, false><<<gridJ, 256, 0, p->stream>>>(reinterpret_cast<const T*>(ghat),
+                                                               reinterpret_cast<const T*>(D), geo.S,
+                                                               p->desc.psf_per_item, lists, geo, p->bracket_partials);
+    k_bracket_finalize<<<B, 256, 0, p->stream>>>(p->bracket_partials, nchJ, p->bracket_G);
+    k_binned_decide<<<(B + 127) / 128, 128, 0, p->stream>>>(p->bracket_G, K, p->bracket_k0, mu_idx, fb, B);
+    geo.K = K;
+    geo.chunk = p->gcv_chunk;
+    const size_t smemK = 4 * (size_t)geo.chunk * sizeof(T);
+    const unsigned gridK = (unsigned)(p->gcv_chunks * (long long)B);
+    if (cplx)
+        k_gcv_masked<T, true><<<gridK, 256, smemK, p->stream>>>(
+            reinterpret_cast<const CT*>(ghat), reinterpret_cast<const CT*>(D), geo.S, p->desc.psf_per_item,
+            reinterpret_cast<const T*>(p->muT), geo, fb, p->partials);
+    else
+        k_gcv_masked<T, false><<<gridK, 256, smemK, p->stream>>>(
+            reinterpret_cast<const T*>(ghat), reinterpret_cast<const T*>(D), geo.S, p->desc.psf_per_item,
+            reinterpret_cast<const T*>(p->muT), geo, fb, p->partials);
+    k_masked_finalize<<<B, 256, 0, p->stream>>>(p->partials, p->gcv_chunks, K, fb, p->mu, nullptr, mu_idx);
+    p->launches += 8;
+    return check("hobc_gcv_binned");
+}
+
+template <typename T>
+hobc_status run_deblur_binned(hobc_plan_s* p, const void* g, const void* psf, void* f, int* mu_idx, int* fb) {
+    hobc_status s = run_eig<T>(p, psf, p->D);
+    if (s == HOBC_OK) s = run_analysis<T>(p, g, p->G);
+    if (s == HOBC_OK) s = run_gcv_binned<T>(p, p->G, p->D, mu_idx, fb, p->k_hat);
+    if (s == HOBC_OK) s = run_filter_synthesis<T>(p, p->G, p->D, mu_idx, f);
+    return s;
 }
 
 }  // namespace
@@ -914,6 +1225,38 @@ hobc_status hobc_deblur_learned(hobc_plan* p, hobc_mlp* q, const void* g_dev, co
     p->launches = 0;
     return p->prec == HOBC_FP64 ? run_learned<double>(p, q, g_dev, psf_dev, f_dev, mu_dev, fell_back_dev)
                                 : run_learned<float>(p, q, g_dev, psf_dev, f_dev, mu_dev, fell_back_dev);
+}
+
+hobc_status hobc_gcv_binned(hobc_plan* p, const void* ghat_dev, const void* d_dev, int* mu_index_dev,
+                            int* fell_back_dev, int* k_hat_dev) {
+    if (!p || !ghat_dev || !d_dev || !mu_index_dev) return HOBC_ERR_ARG;
+    cudaError_t e = ensure_learned_ws(p);
+    if (e != cudaSuccess) { set_last_error("hobc_gcv_binned", e); return HOBC_ERR_CUDA; }
+    if (!p->grid_ascending) {
+        set_last_error_text("hobc_gcv_binned: the mu grid must be strictly increasing");
+        return HOBC_ERR_ARG;
+    }
+    p->launches = 0;
+    int* fb = fell_back_dev ? fell_back_dev : p->fell_back;
+    int* kh = k_hat_dev ? k_hat_dev : p->k_hat;
+    return p->prec == HOBC_FP64 ? run_gcv_binned<double>(p, ghat_dev, d_dev, mu_index_dev, fb, kh)
+                                : run_gcv_binned<float>(p, ghat_dev, d_dev, mu_index_dev, fb, kh);
+}
+
+hobc_status hobc_deblur_binned(hobc_plan* p, const void* g_dev, const void* psf_dev, void* f_dev, int* mu_index_dev,
+                               int* fell_back_dev) {
+    if (!p || !g_dev || !psf_dev || !f_dev) return HOBC_ERR_ARG;
+    cudaError_t e = ensure_learned_ws(p);
+    if (e != cudaSuccess) { set_last_error("hobc_deblur_binned", e); return HOBC_ERR_CUDA; }
+    if (!p->grid_ascending) {
+        set_last_error_text("hobc_deblur_binned: the mu grid must be strictly increasing");
+        return HOBC_ERR_ARG;
+    }
+    p->launches = 0;
+    int* mi = mu_index_dev ? mu_index_dev : p->mu_idx;
+    int* fb = fell_back_dev ? fell_back_dev : p->fell_back;
+    return p->prec == HOBC_FP64 ? run_deblur_binned<double>(p, g_dev, psf_dev, f_dev, mi, fb)
+                                : run_deblur_binned<float>(p, g_dev, psf_dev, f_dev, mi, fb);
 }
 
 }  // extern "C"

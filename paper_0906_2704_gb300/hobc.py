@@ -1,5 +1,5 @@
-"""Python binding of the C ABI in include/hobc.h and include/hobc_learned.h
-(ctypes; marshalling only).
+"""Python binding of the C ABI in include/hobc.h, include/hobc_learned.h and
+include/hobc_binned.h (ctypes; marshalling only).
 
 Every step of the method runs in the CUDA library ``libhobc.so`` built in this
 package directory by ``paper_0906_2704_gb300.build``.  There is no fallback: if
@@ -20,7 +20,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhobc.so")
 HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "hobc.h")
-HEADER_PATHS = [HEADER_PATH, os.path.join(os.path.dirname(_HERE), "include", "hobc_learned.h")]
+HEADER_PATHS = [HEADER_PATH, os.path.join(os.path.dirname(_HERE), "include", "hobc_learned.h"),
+                os.path.join(os.path.dirname(_HERE), "include", "hobc_binned.h")]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_0906_2704_gb300.build`")
@@ -95,6 +96,10 @@ _lib.hobc_status_str.argtypes = [ctypes.c_int]
 _lib.hobc_status_str.restype = ctypes.c_char_p
 _lib.hobc_last_error.argtypes = []
 _lib.hobc_last_error.restype = ctypes.c_char_p
+_lib.hobc_gcv_binned.argtypes = [_vp] * 6
+_lib.hobc_gcv_binned.restype = ctypes.c_int
+_lib.hobc_deblur_binned.argtypes = [_vp] * 6
+_lib.hobc_deblur_binned.restype = ctypes.c_int
 _lib.hobc_features.argtypes = [_vp] * 4
 _lib.hobc_features.restype = ctypes.c_int
 _lib.hobc_deblur_learned.argtypes = [_vp] * 7
@@ -291,6 +296,14 @@ class Plan:
     def filter_synthesis(self, ghat, d, mu_index, f) -> None:
         _check(_lib.hobc_filter_synthesis(self._handle, _ptr(ghat), _ptr(d), _ptr(mu_index), _ptr(f)),
                "hobc_filter_synthesis")
+
+    def gcv_binned(self, ghat, d, mu_index, fell_back=None, k_hat=None) -> None:
+        _check(_lib.hobc_gcv_binned(self._handle, _ptr(ghat), _ptr(d), _ptr(mu_index), _ptr(fell_back), _ptr(k_hat)),
+               "hobc_gcv_binned")
+
+    def deblur_binned(self, g, psf, f, mu_index=None, fell_back=None) -> None:
+        _check(_lib.hobc_deblur_binned(self._handle, _ptr(g), _ptr(psf), _ptr(f), _ptr(mu_index), _ptr(fell_back)),
+               "hobc_deblur_binned")
 
     def features(self, ghat, d, x) -> None:
         _check(_lib.hobc_features(self._handle, _ptr(ghat), _ptr(d), _ptr(x)), "hobc_features")

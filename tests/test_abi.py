@@ -104,4 +104,6 @@ def test_learned_entry_points_reject_bad_arguments_on_the_host(hobc):
     assert lib.hobc_mlp_load(None, b"x") == arg
     assert lib.hobc_features(None, None, None, None) == arg
     assert lib.hobc_deblur_learned(None, None, None, None, None, None, None) == arg
+    assert lib.hobc_gcv_binned(None, None, None, None, None, None) == arg
+    assert lib.hobc_deblur_binned(None, None, None, None, None, None) == arg
     lib.hobc_mlp_destroy(None)
