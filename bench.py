@@ -300,7 +300,7 @@ def run_ours(args):
     g_h = torch.from_numpy(g.astype(npdt)).pin_memory().numpy()
     h_h = np.ascontiguousarray(h.astype(npdt))
     f_h = torch.empty(g.shape, dtype=tdt).pin_memory().numpy()
-    mi_h = np.empty(B, dtype=np.int32)
+    mi_h = torch.empty(B, dtype=torch.int32).pin_memory().numpy()
     plan.deblur_host(g_h, h_h, f_h, mi_h)
     barrier()
     t0 = time.perf_counter()

@@ -1,6 +1,7 @@
 // C ABI of the library (include/hobc.h): plan creation with the per-axis
 // tables of the high-order boundary-condition transforms, workspace, and the
 // entry points that run the hot path on the plan's stream.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -346,6 +347,9 @@ void hobc_plan_destroy(hobc_plan* p) {
     cudaFree(p->partials); cudaFree(p->gcv); cudaFree(p->mu_idx);
     cudaFree(p->g_in); cudaFree(p->f_out); cudaFree(p->psf_in);
     free_learned_ws(p);
+    for (int i = 0; i < 2; ++i)
+        if (p->aux[i]) cudaStreamDestroy(p->aux[i]);
+    if (p->aux_ev) cudaEventDestroy(p->aux_ev);
     delete p;
 }
 
@@ -512,24 +516,77 @@ hobc_status hobc_deblur(hobc_plan* p, const void* g, const void* psf, void* f, i
     return deblur_impl(p, g, psf, f, mu_idx, gcv);
 }
 
+// The plan seen as the sub-batch [c0, c0 + cb): per-item workspace offsets,
+// its own stream.  A shallow copy: it owns nothing.
+static hobc_plan_s chunk_view(const hobc_plan_s* p, size_t c0, size_t cb, cudaStream_t s) {
+    hobc_plan_s v = *p;
+    auto off = [&](void* base, size_t per_item) -> void* {
+        return base ? static_cast<void*>(static_cast<char*>(base) + c0 * per_item) : nullptr;
+    };
+    v.desc.batch = (int)cb;
+    v.stream = s;
+    v.R = off(p->R, p->spec_bytes);
+    v.G = off(p->G, p->spec_bytes);
+    if (p->desc.psf_per_item) {
+        v.D = off(p->D, p->spec_bytes);
+        v.npsf = (int)cb;
+    }
+    v.partials = p->partials + c0 * (size_t)p->gcv_chunks * 2 * p->K;
+    v.gcv = p->gcv + c0 * p->K;
+    v.mu_idx = p->mu_idx + c0;
+    v.g_in = off(p->g_in, p->img_elems * p->esz);
+    v.f_out = off(p->f_out, p->img_elems * p->esz);
+    v.launches = 0;
+    return v;
+}
+
 hobc_status hobc_deblur_host(hobc_plan* p, const void* g, const void* psf, void* f, int* mu_idx, double* gcv) {
     if (!p || !g || !psf || !f) return HOBC_ERR_ARG;
     p->launches = 0;
     const size_t B = (size_t)p->desc.batch;
-    const size_t gb = B * p->img_elems * p->esz;
-    cudaError_t e = cudaMemcpyAsync(p->g_in, g, gb, cudaMemcpyHostToDevice, p->stream);
+    const size_t ib = p->img_elems * p->esz;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        if (!p->aux[i]) e = cudaStreamCreateWithFlags(&p->aux[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess && !p->aux_ev) e = cudaEventCreateWithFlags(&p->aux_ev, cudaEventDisableTiming);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->psf_in, psf, (size_t)p->npsf * p->psf_elems * p->esz, cudaMemcpyHostToDevice, p->stream);
     if (e != cudaSuccess) { set_last_error("hobc_deblur_host H2D", e); return HOBC_ERR_CUDA; }
-    hobc_status s = deblur_impl(p, p->g_in, p->psf_in, p->f_out, p->mu_idx, gcv ? p->gcv : nullptr);
+    hobc_status s = HOBC_DISPATCH(p, run_eig, p->psf_in, p->D);
     if (s != HOBC_OK) return s;
-    e = cudaMemcpyAsync(f, p->f_out, gb, cudaMemcpyDeviceToHost, p->stream);
-    if (e == cudaSuccess && mu_idx)
-        e = cudaMemcpyAsync(mu_idx, p->mu_idx, B * sizeof(int), cudaMemcpyDeviceToHost, p->stream);
-    if (e == cudaSuccess && gcv)
-        e = cudaMemcpyAsync(gcv, p->gcv, B * p->K * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
-    if (e != cudaSuccess) { set_last_error("hobc_deblur_host D2H", e); return HOBC_ERR_CUDA; }
+    e = cudaEventRecord(p->aux_ev, p->stream);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(p->aux[i], p->aux_ev, 0);
+    // chunks alternate between two streams, so that one chunk's copies overlap
+    // the other's kernels; the small outputs follow once every chunk is queued
+    // (a copy to pageable host memory holds the host thread until it is done)
+    const size_t nchunk = B >= 4 ? 4 : B;
+    const size_t cb = (B + nchunk - 1) / nchunk;
+    for (size_t c0 = 0, c = 0; c0 < B && e == cudaSuccess && s == HOBC_OK; c0 += cb, ++c) {
+        const size_t n = std::min(cb, B - c0);
+        hobc_plan_s v = chunk_view(p, c0, n, p->aux[c % 2]);
+        e = cudaMemcpyAsync(v.g_in, static_cast<const char*>(g) + c0 * ib, n * ib, cudaMemcpyHostToDevice, v.stream);
+        if (e != cudaSuccess) break;
+        s = HOBC_DISPATCH(&v, run_analysis, v.g_in, v.G);
+        if (s == HOBC_OK) s = HOBC_DISPATCH(&v, run_gcv, v.G, v.D, gcv ? v.gcv : nullptr, v.mu_idx);
+        if (s == HOBC_OK) s = HOBC_DISPATCH(&v, run_filter_synthesis, v.G, v.D, v.mu_idx, v.f_out);
+        p->launches += v.launches;
+        if (s != HOBC_OK) break;
+        e = cudaMemcpyAsync(static_cast<char*>(f) + c0 * ib, v.f_out, n * ib, cudaMemcpyDeviceToHost, v.stream);
+    }
+    for (size_t c0 = 0, c = 0; c0 < B && e == cudaSuccess && s == HOBC_OK; c0 += cb, ++c) {
+        const size_t n = std::min(cb, B - c0);
+        cudaStream_t st = p->aux[c % 2];
+        if (mu_idx) e = cudaMemcpyAsync(mu_idx + c0, p->mu_idx + c0, n * sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && gcv)
+            e = cudaMemcpyAsync(gcv + c0 * p->K, p->gcv + c0 * p->K, n * p->K * sizeof(double), cudaMemcpyDeviceToHost,
+                                st);
+    }
+    for (int i = 0; i < 2; ++i) {
+        const cudaError_t e2 = cudaStreamSynchronize(p->aux[i]);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (s != HOBC_OK) return s;
+    if (e != cudaSuccess) { set_last_error("hobc_deblur_host", e); return HOBC_ERR_CUDA; }
     return HOBC_OK;
 }
 

@@ -262,6 +262,13 @@ hobc_status run_gcv(hobc_plan_s* p, const void* ghat, const void* D, double* gcv
     return launch_gcv_finalize(p, gcv, mu_idx);
 }
 
+// Shared-memory share of the unified L1/shared array requested for the line
+// kernels (percent; -1 leaves the choice to the driver, which keeps enough L1
+// for the twiddle, chirp and border tables: 4% faster than 100 at 1024^2).
+#ifndef HOBC_CARVEOUT
+#define HOBC_CARVEOUT -1
+#endif
+
 // Allow the line kernels up to 200 KB of dynamic shared memory.
 template <typename T>
 hobc_status prepare_kernels(hobc_plan_s* p) {
@@ -269,7 +276,7 @@ hobc_status prepare_kernels(hobc_plan_s* p) {
     cudaError_t e = cudaSuccess;
 #define HOBC_SMEM(k)                                                                                \
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100)
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, HOBC_CARVEOUT)
     HOBC_SMEM((k_pair_analysis<T, FAM_S>));
     HOBC_SMEM((k_pair_analysis<T, FAM_S3>));
     HOBC_SMEM((k_pair_synthesis<T, FAM_S3, 0>));

@@ -280,6 +280,31 @@ def test_minimum_size_and_host_entry_point():
             assert np.abs(f[b] - fo).max() <= 1e-10 * np.abs(fo).max()
 
 
+@pytest.mark.parametrize("psf_per_item", [False, True])
+@pytest.mark.parametrize("batch", [1, 4, 7])
+def test_host_entry_point_equals_device_entry_point(batch, psf_per_item):
+    """The chunked, two-stream host-buffer call gives the device call's results bit for bit."""
+    n, taps, K = (30, 36), (5, 5), 12
+    mus = synth.mu_grid(K)
+    h0 = P.psf_for("F", 2, taps)
+    hs = np.stack([h0 ** (1 + 0.1 * b) / (h0 ** (1 + 0.1 * b)).sum() for b in range(batch if psf_per_item else 1)])
+    g, _ = P.problems(2, n, h0, batch, 8)
+    plan = hobc.Plan(2, n, taps, 2, mus, family="fourier", batch=batch, psf_per_item=psf_per_item)
+    f_h = torch.empty(g.shape, dtype=torch.float64).pin_memory().numpy()
+    g_h = torch.from_numpy(g).pin_memory().numpy()
+    mi_h = np.empty(batch, dtype=np.int32)
+    G_h = np.empty((batch, K))
+    plan.deblur_host(g_h, np.ascontiguousarray(hs), f_h, mi_h, G_h)
+    f_d = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+    mi_d = torch.empty(batch, dtype=torch.int32, device="cuda")
+    G_d = torch.empty((batch, K), dtype=torch.float64, device="cuda")
+    plan.deblur(_dev(g, np.float64), _dev(hs, np.float64), f_d, mi_d, G_d)
+    assert np.array_equal(f_h, f_d.cpu().numpy())
+    assert np.array_equal(mi_h, mi_d.cpu().numpy())
+    assert np.array_equal(G_h, G_d.cpu().numpy())
+    assert plan.last_launch_count >= 7
+
+
 def test_caller_mu_index_out_of_range_is_clamped():
     """A caller-supplied mu index outside the grid is clamped on the device."""
     mus = synth.mu_grid(4, 1e-3, 1.0)
