@@ -115,9 +115,10 @@ __device__ __forceinline__ void fft_stage(C2<T>* buf, int M, int Ns, const C2<T>
         C2<T> w[8];
         if (Ns > 1) {
             w[1] = tw[step];
-            if (R >= 4) { w[2] = tw[2 * step]; w[3] = cmul<T>(w[1], w[2]); }
+            if (R >= 4) w[2] = tw[2 * step];
+            if (R == 8) w[4] = tw[4 * step];
+            if (R >= 4) w[3] = cmul<T>(w[1], w[2]);
             if (R == 8) {
-                w[4] = tw[4 * step];
                 w[5] = cmul<T>(w[1], w[4]);
                 w[6] = cmul<T>(w[2], w[4]);
                 w[7] = cmul<T>(w[3], w[4]);

@@ -12,6 +12,14 @@
 
 #include "hobc_device.cuh"
 
+// Minimum resident 512-thread blocks per SM asked of the FP32 line kernels
+// (caps their registers at 65536 / (512 x this)).  The transforms are latency
+// bound: 3 (40 registers, a few spilled bytes) runs the 1024^2 passes 7%
+// faster than the unconstrained 60 registers.
+#ifndef HOBC_LINE_MINB
+#define HOBC_LINE_MINB 3
+#endif
+
 namespace hobc {
 
 template <typename T, bool CPLX> struct ElemT { typedef T t; };
@@ -206,7 +214,7 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
 }
 
 template <typename T, int FAM>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? HOBC_LINE_MINB : 1)
 k_pair_analysis(const T* __restrict__ in, long long in_item, long long in_rs,
                 typename ElemT<T, FAM == FAM_F>::t* __restrict__ out, long long out_item,
                 long long out_rs, long long out_cs, int nlines, Axis<T> ax) {
@@ -377,7 +385,7 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM 
 }
 
 template <typename T, int FAM, int FMODE>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? HOBC_LINE_MINB : 1)
 k_pair_synthesis(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in, long long in_item,
                  long long in_rs, long long in_cs, T* __restrict__ out, long long out_item,
                  long long out_rs, int nlines, Axis<T> ax, FilterDesc fd) {
@@ -392,7 +400,7 @@ k_pair_synthesis(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in, long
 // Line c of item i: in[i*item_stride + c*n + t].
 // =====================================================================
 template <typename T>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? HOBC_LINE_MINB : 1)
 k_cplx_analysis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long item_stride,
                 int nlines, Axis<T> ax) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -432,7 +440,7 @@ k_cplx_analysis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long
 }
 
 template <typename T, bool FILTER>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? HOBC_LINE_MINB : 1)
 k_cplx_synthesis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long item_stride,
                  int nlines, Axis<T> ax, FilterDesc fd) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
