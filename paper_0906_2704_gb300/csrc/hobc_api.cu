@@ -36,11 +36,8 @@ __global__ void k_gcv_finalize(const double* __restrict__ partials, int nchunks,
     double best = INFINITY;
     int bi = 0x7fffffff;
     for (int j = threadIdx.x; j < K; j += blockDim.x) {
-        double num = 0, den = 0;
-        for (int c = 0; c < nchunks; ++c) {
-            num += p[(long long)c * 2 * K + j];
-            den += p[(long long)c * 2 * K + K + j];
-        }
+        double num, den;
+        sum_chunks(p, nchunks, K, j, num, den);
         const double G = num / (den * den);
         if (gcv) gcv[item * K + j] = G;
         const double key = isnan(G) ? INFINITY : G;

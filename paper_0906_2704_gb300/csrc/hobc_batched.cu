@@ -142,11 +142,8 @@ __global__ void kb_gcv_finalize(const GcvItem* __restrict__ gi, const double* __
     double best = INFINITY;
     int bi = 0x7fffffff;
     for (int j = threadIdx.x; j < K; j += blockDim.x) {
-        double num = 0, den = 0;
-        for (int c = 0; c < g.nchunks; ++c) {
-            num += p[(long long)c * 2 * K + j];
-            den += p[(long long)c * 2 * K + K + j];
-        }
+        double num, den;
+        sum_chunks(p, g.nchunks, K, j, num, den);
         const double Gv = num / (den * den);
         if (io->gcv) io->gcv[(long long)item * K + j] = Gv;
         const double key = isnan(Gv) ? INFINITY : Gv;

@@ -753,6 +753,19 @@ k_gcv_partials(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typena
                                smem_raw);
 }
 
+// Sum over the chunks of one problem of the per-CTA partial sums of grid value
+// j (numerator at j, denominator at K + j of each chunk's 2K block), in chunk
+// order.  (Splitting it into four interleaved accumulators measured slower.)
+__device__ __forceinline__ void sum_chunks(const double* __restrict__ p, int nchunks, int K, int j, double& num,
+                                           double& den) {
+    num = 0;
+    den = 0;
+    for (int c = 0; c < nchunks; ++c) {
+        num += p[(long long)c * 2 * K + j];
+        den += p[(long long)c * 2 * K + K + j];
+    }
+}
+
 // G(mu_j) = num_j / den_j^2 and the first index of the minimum (NaN never wins).
 // grid = items, block = 256.
 __global__ void k_gcv_finalize(const double* __restrict__ partials, int nchunks, int K,

@@ -468,11 +468,8 @@ __global__ void k_masked_finalize(const double* __restrict__ partials, int nchun
     double best = INFINITY;
     int bi = 0x7fffffff;
     for (int j = threadIdx.x; j < K; j += blockDim.x) {
-        double num = 0, den = 0;
-        for (int c = 0; c < nchunks; ++c) {
-            num += p[(long long)c * 2 * K + j];
-            den += p[(long long)c * 2 * K + K + j];
-        }
+        double num, den;
+        sum_chunks(p, nchunks, K, j, num, den);
         const double Gv = num / (den * den);
         const double key = isnan(Gv) ? INFINITY : Gv;
         if (key < best || (key == best && j < bi)) { best = key; bi = j; }
@@ -538,12 +535,15 @@ k_ahist(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename Elem
             const typename Pack4<T>::t v = gcv_term<T, CPLX>(sp[i], dp[i], geo, e0 + i);
             valid = v.z > (T)0;
             if (valid) {
-                int lo = 1, hi = kABins;                // first interior edge > a
-                while (lo < hi) {
-                    const int mid = (lo + hi) / 2;
-                    if (ed[mid] <= v.x) lo = mid + 1; else hi = mid;
-                }
-                key = lo - 1;
+                // estimate the bin from log10 a, then settle it exactly against the
+                // edges: the bin is the number of interior edges <= a
+                float la = __log2f((float)v.x) * 0.30102999566f;
+                la = fminf(fmaxf(la, (float)kALo - 1.f), (float)kAHi + 1.f);
+                int b = (int)floorf((la - (float)kALo) * (float)(kABins / (kAHi - kALo)));
+                b = min(max(b, 0), kABins - 1);
+                while (b > 0 && v.x < ed[b]) --b;
+                while (b < kABins - 1 && v.x >= ed[b + 1]) ++b;
+                key = b;
                 vc = (float)v.z;
                 vg = (float)v.y;
                 va = (float)(v.z * v.x);
