@@ -21,7 +21,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhobc.so")
 HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "hobc.h")
 HEADER_PATHS = [HEADER_PATH, os.path.join(os.path.dirname(_HERE), "include", "hobc_learned.h"),
-                os.path.join(os.path.dirname(_HERE), "include", "hobc_binned.h")]
+                os.path.join(os.path.dirname(_HERE), "include", "hobc_binned.h"),
+                os.path.join(os.path.dirname(_HERE), "include", "hobc_tc.h")]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_0906_2704_gb300.build`")
@@ -96,6 +97,25 @@ _lib.hobc_status_str.argtypes = [ctypes.c_int]
 _lib.hobc_status_str.restype = ctypes.c_char_p
 _lib.hobc_last_error.argtypes = []
 _lib.hobc_last_error.restype = ctypes.c_char_p
+class TcOperand(ctypes.Structure):
+    _fields_ = [("hi", _vp), ("lo", _vp), ("ld", ctypes.c_longlong), ("batch_stride", ctypes.c_longlong)]
+
+
+class TcOutput(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("f32", _vp), ("hi", _vp), ("lo", _vp), ("ld", ctypes.c_longlong),
+                ("batch_stride", ctypes.c_longlong), ("rows", ctypes.c_int), ("cols", ctypes.c_int)]
+
+
+TC_OUT = {"f32": 0, "f32_t": 1, "split": 2, "split_t": 3}
+_lib.hobc_tc_gemm.argtypes = [ctypes.POINTER(TcOperand), ctypes.POINTER(TcOperand), ctypes.c_int, ctypes.c_int,
+                              ctypes.c_int, ctypes.c_int, ctypes.POINTER(TcOutput), _vp, _vp]
+_lib.hobc_tc_gemm.restype = ctypes.c_int
+_lib.hobc_tc_split.argtypes = [_vp, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                               ctypes.c_longlong, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _vp]
+_lib.hobc_tc_split.restype = ctypes.c_int
+for _name in ("hobc_tc_tile_m", "hobc_tc_tile_n", "hobc_tc_tile_k"):
+    getattr(_lib, _name).argtypes = []
+    getattr(_lib, _name).restype = ctypes.c_int
 _lib.hobc_gcv_binned.argtypes = [_vp] * 6
 _lib.hobc_gcv_binned.restype = ctypes.c_int
 _lib.hobc_deblur_binned.argtypes = [_vp] * 6
@@ -208,6 +228,30 @@ def gcv_noalloc(desc: PlanDesc, ghat, d, mu, gcv, mu_index, stream=None) -> None
         stream = stream.cuda_stream
     _check(_lib.hobc_gcv_noalloc(ctypes.byref(desc), _ptr(ghat), _ptr(d), _ptr(mu), _ptr(gcv), _ptr(mu_index),
                                  _vp(stream)), "hobc_gcv_noalloc")
+
+
+def tc_tiles():
+    """(tile_m, tile_n, tile_k) of the tensor-core GEMM."""
+    return _lib.hobc_tc_tile_m(), _lib.hobc_tc_tile_n(), _lib.hobc_tc_tile_k()
+
+
+def tc_gemm(a_hi, a_lo, a_ld, b_hi, b_lo, b_ld, m, n, k, out, mode="f32", out_lo=None, out_ld=None,
+            batch=1, a_bs=0, b_bs=0, out_bs=0, err=None, stream=None) -> None:
+    """C = A . B^T on the tensor cores (include/hobc_tc.h); device tensors."""
+    A = TcOperand(_ptr(a_hi), _ptr(a_lo), a_ld, a_bs)
+    B = TcOperand(_ptr(b_hi), _ptr(b_lo), b_ld, b_bs)
+    md = TC_OUT[mode]
+    O = TcOutput(md, _ptr(out) if md < 2 else None, _ptr(out) if md >= 2 else None, _ptr(out_lo),
+                 out_ld if out_ld is not None else (n if md in (0, 2) else m), out_bs, m, n)
+    st = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(_lib.hobc_tc_gemm(ctypes.byref(A), ctypes.byref(B), m, n, k, batch, ctypes.byref(O), _ptr(err),
+                             _vp(st)), "hobc_tc_gemm")
+
+
+def tc_split(src, src_ld, src_bs, rows, cols, hi, lo, ld, bs, rows_padded, batch=1, stream=None) -> None:
+    st = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(_lib.hobc_tc_split(_ptr(src), src_ld, src_bs, rows, cols, _ptr(hi), _ptr(lo), ld, bs, rows_padded,
+                              batch, _vp(st)), "hobc_tc_split")
 
 
 def gcv_noalloc_max_bytes() -> int:
