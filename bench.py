@@ -396,7 +396,7 @@ def run_other(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     prec = args.prec
-    npdt = np.float32 if prec == "fp32" else np.float64
+    npdt = np.float64 if prec == "fp64" else np.float32
     stream = torch.cuda.Stream()
     extra = {}
     with torch.cuda.stream(stream):
@@ -435,7 +435,8 @@ def run_other(args):
                    "batch": B}
             io_bytes = 2 * B * n * np.dtype(npdt).itemsize
         else:
-            B, n, K = 32, 512, 256
+            n = 1024 if args.workload == "cosine1024" else 512
+            B, K = (16 if n == 1024 else 32), 256
             hh = synth.gaussian_psf_2d_separable(2.5, 15)
             clean, _ = synth.problem_2d(4, n, n, hh, 0.0, count=4)
             rng = np.random.default_rng(5)
@@ -447,15 +448,34 @@ def run_other(args):
             f = torch.empty_like(g)
             mi = torch.empty(B, dtype=torch.int32, device=dev)
             ms, clocks = _timed(lambda: plan.deblur(g, h, f, mi), stream, args.steps, args.warmup)
+            plan.status()
             units, unit, launches = B, "deblurs/s", plan.last_launch_count
-            cfg = {"workload": "512x512, separable Gaussian 15x15 sigma 2.5, degree 2 (cosine), Laplacian, 256 mu, "
+            cfg = {"workload": f"{n}x{n}, separable Gaussian 15x15 sigma 2.5, degree 2 (cosine), Laplacian, 256 mu, "
                                "0.5% noise", "batch": B}
             io_bytes = 2 * B * n * n * np.dtype(npdt).itemsize
+            # the transform passes alone (analysis + synthesis), and for the dense mode their tensor-core rate
+            S = plan.spec_elems
+            gh = torch.empty((B, S), dtype=g.dtype, device=dev)
+            ms_a, _ = _timed(lambda: plan.analysis(g, gh), stream, args.steps, 2)
+            ms_s, _ = _timed(lambda: plan.synthesis(gh, f), stream, args.steps, 2)
+            extra = {"transform_ms_per_step": {"analysis": ms_a / args.steps, "synthesis": ms_s / args.steps}}
+            if prec == "split_bf16":
+                # 4 passes x 3 split products x 2 n^3 (the padded tile shape is what the tensor cores run)
+                tm, tn, tk = hobc.tc_tiles()
+                npad = [-(-n // t) * t for t in (tm, tn, tk)]
+                flops = 4 * 3 * 2.0 * npad[0] * npad[1] * npad[2] * B
+                t_s = (ms_a + ms_s) / args.steps / 1e3
+                pk = measured_peaks()[0].get("bf16_tflops")
+                extra["roofline"] = {"bound": "tensor", "kernel": "k_gemm_split (4 passes)",
+                                     "achieved": flops / t_s / 1e12, "peak": pk, "unit": "TFLOP/s",
+                                     "frac": flops / t_s / 1e12 / pk if pk else None, "traffic": None,
+                                     "flops_per_step": flops}
     peaks, kind = measured_peaks()
     sec = ms / args.steps / 1e3
     line = {"metric": f"{args.workload} throughput", "value": units / sec, "unit": unit, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp64": "f64", "split_bf16": "bf16x3 (split) / f32"}[prec],
             "data": "synthetic", "config": cfg, "gpu_launches": launches * args.steps,
             "hbm_roofline": {"algorithmic_bytes_per_step": io_bytes, "achieved_gbs": io_bytes / sec / 1e9,
                              "peak_gbs": peaks.get("hbm_gbs"), "frac": io_bytes / sec / 1e9 / peaks.get("hbm_gbs")},
@@ -626,10 +646,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--prec", choices=["fp32", "fp64", "split_bf16"], default="fp32")
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["fourier1024", "batched", "signals1d", "cosine512", "learned"],
+    ap.add_argument("--workload", choices=["fourier1024", "batched", "signals1d", "cosine512", "cosine1024",
+                                           "learned"],
                     default="fourier1024")
     ap.add_argument("--train", type=int, default=8192, help="training problems of the learned workload")
     ap.add_argument("--epochs", type=int, default=60, help="training epochs of the learned workload")

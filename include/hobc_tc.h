@@ -65,6 +65,11 @@ hobc_status hobc_tc_split(const float* src, long long src_ld, long long src_batc
                           void* hi, void* lo, long long ld, long long batch_stride, int rows_padded, int batch,
                           void* cuda_stream);
 
+/* Synchronise the plan's stream and report whether a bounded tensor-core wait
+ * of an HOBC_SPLIT_BF16 plan gave up since the last call (HOBC_ERR_TIMEOUT,
+ * flag cleared); HOBC_OK otherwise and for other precisions. */
+hobc_status hobc_plan_status(hobc_plan* plan);
+
 #ifdef __cplusplus
 }
 #endif

@@ -344,6 +344,7 @@ void hobc_plan_destroy(hobc_plan* p) {
     cudaFree(p->partials); cudaFree(p->gcv); cudaFree(p->mu_idx);
     cudaFree(p->g_in); cudaFree(p->f_out); cudaFree(p->psf_in);
     free_learned_ws(p);
+    dense_free(p);
     for (int i = 0; i < 2; ++i)
         if (p->aux[i]) cudaStreamDestroy(p->aux[i]);
     if (p->aux_ev) cudaEventDestroy(p->aux_ev);
@@ -359,7 +360,7 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
     if (d.ndim != 1 && d.ndim != 2) return HOBC_ERR_ARG;
     if (d.n_mu < 1 || d.batch < 1) return HOBC_ERR_ARG;
     if (d.ndim == 2 && d.batch > 65535) return HOBC_ERR_SIZE;     // items ride on gridDim.y
-    if (d.prec != HOBC_FP64 && d.prec != HOBC_FP32) return HOBC_ERR_ARG;
+    if (d.prec != HOBC_FP64 && d.prec != HOBC_FP32 && d.prec != HOBC_SPLIT_BF16) return HOBC_ERR_ARG;
     if (d.L != HOBC_L_IDENTITY && d.L != HOBC_L_LAPLACIAN) return HOBC_ERR_ARG;
     if (d.psf_per_item != 0 && d.psf_per_item != 1) return HOBC_ERR_ARG;
     for (int i = 0; i < d.ndim; ++i) {
@@ -375,7 +376,7 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
         if (!std::isfinite(mu_grid_host[j])) return HOBC_ERR_NONFINITE;
         if (!(mu_grid_host[j] > 0)) return HOBC_ERR_ARG;
         // FP32 GCV pairs grid values: (a + mu1)(a + mu2) must stay a normal float
-        if (d.prec == HOBC_FP32 && (mu_grid_host[j] < 1e-18 || mu_grid_host[j] > 1e18)) return HOBC_ERR_ARG;
+        if (d.prec != HOBC_FP64 && (mu_grid_host[j] < 1e-18 || mu_grid_host[j] > 1e18)) return HOBC_ERR_ARG;
     }
     int fam = d.family;
     if (d.bc_degree < 1 || d.bc_degree > 3) return HOBC_ERR_UNSUPPORTED;
@@ -389,6 +390,7 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
     if ((fam == HOBC_FAMILY_COSINE || fam == HOBC_FAMILY_FOURIER) && d.bc_degree != 2) return HOBC_ERR_UNSUPPORTED;
     if (fam == HOBC_FAMILY_SINE_CUBIC && d.bc_degree != 3) return HOBC_ERR_UNSUPPORTED;
     if (fam < HOBC_FAMILY_SINE || fam > HOBC_FAMILY_SINE_CUBIC) return HOBC_ERR_ARG;
+    if (d.prec == HOBC_SPLIT_BF16 && fam == HOBC_FAMILY_FOURIER) return HOBC_ERR_UNSUPPORTED;   // complex T_F
 
     hobc_plan_s* p = new hobc_plan_s;
     memset(p, 0, sizeof(*p));
@@ -445,6 +447,7 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
         return HOBC_ERR_CUDA;
     }
     hobc_status s = d.prec == HOBC_FP64 ? prepare_kernels<double>(p) : prepare_kernels<float>(p);
+    if (s == HOBC_OK && d.prec == HOBC_SPLIT_BF16) s = dense_prepare(p);
     if (s != HOBC_OK) {
         hobc_plan_destroy(p);
         return s;
@@ -533,6 +536,7 @@ static hobc_plan_s chunk_view(const hobc_plan_s* p, size_t c0, size_t cb, cudaSt
     v.mu_idx = p->mu_idx + c0;
     v.g_in = off(p->g_in, p->img_elems * p->esz);
     v.f_out = off(p->f_out, p->img_elems * p->esz);
+    v.item0 = p->item0 + c0;
     v.launches = 0;
     return v;
 }

@@ -80,6 +80,8 @@ struct hobc_plan_s {
     cudaStream_t aux[2];     // host-buffer pipeline streams (created on first use)
     cudaEvent_t aux_ev;
     int grid_ascending;      // 1 if the mu grid is strictly increasing
+    struct hobc_dense_s* dense;   // HOBC_SPLIT_BF16: matrices and operand workspace (hobc_tc.cu)
+    size_t item0;            // first problem of this view of the plan (0 for the plan itself)
 };
 
 namespace hobc {
@@ -95,6 +97,12 @@ template <typename T> hobc_status run_filter_synthesis_mu(hobc_plan_s* p, const 
                                                           const double* mu_val, void* f);
 template <typename T> hobc_status prepare_kernels(hobc_plan_s* p);
 void free_learned_ws(hobc_plan_s* p);
+hobc_status dense_prepare(hobc_plan_s* p);
+void dense_free(hobc_plan_s* p);
+hobc_status dense_analysis(hobc_plan_s* p, const void* g, void* ghat);
+hobc_status dense_synthesis(hobc_plan_s* p, const void* c, void* y);
+hobc_status dense_filter_synthesis(hobc_plan_s* p, const void* ghat, const void* D, const int* mu_idx,
+                                   const double* mu_val, void* f);
 
 template <typename T> cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half);
 void set_last_error(const char* what, cudaError_t e);

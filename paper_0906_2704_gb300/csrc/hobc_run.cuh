@@ -133,6 +133,7 @@ static hobc_status analysis_fam(hobc_plan_s* p, const T* g, void* ghat) {
 
 template <typename T>
 hobc_status run_analysis(hobc_plan_s* p, const void* g, void* ghat) {
+    if (sizeof(T) == 4 && p->prec == HOBC_SPLIT_BF16) return dense_analysis(p, g, ghat);
     const T* gt = reinterpret_cast<const T*>(g);
     switch (p->fam) {
         case FAM_S: return analysis_fam<T, FAM_S>(p, gt, ghat);
@@ -171,6 +172,7 @@ static hobc_status synthesis_fam(hobc_plan_s* p, const void* c, T* y, const Filt
 
 template <typename T>
 hobc_status run_synthesis(hobc_plan_s* p, const void* c, void* y) {
+    if (sizeof(T) == 4 && p->prec == HOBC_SPLIT_BF16) return dense_synthesis(p, c, y);
     FilterDesc fd = make_filter(p, nullptr, nullptr);
     T* yt = reinterpret_cast<T*>(y);
     switch (p->fam) {
@@ -183,6 +185,7 @@ hobc_status run_synthesis(hobc_plan_s* p, const void* c, void* y) {
 
 template <typename T>
 hobc_status run_filter_synthesis(hobc_plan_s* p, const void* ghat, const void* D, const int* mu_idx, void* f) {
+    if (sizeof(T) == 4 && p->prec == HOBC_SPLIT_BF16) return dense_filter_synthesis(p, ghat, D, mu_idx, nullptr, f);
     FilterDesc fd = make_filter(p, D, mu_idx);
     T* ft = reinterpret_cast<T*>(f);
     switch (p->fam) {
@@ -196,6 +199,7 @@ hobc_status run_filter_synthesis(hobc_plan_s* p, const void* ghat, const void* D
 // The same with mu* given per problem as a value rather than a grid index.
 template <typename T>
 hobc_status run_filter_synthesis_mu(hobc_plan_s* p, const void* ghat, const void* D, const double* mu_val, void* f) {
+    if (sizeof(T) == 4 && p->prec == HOBC_SPLIT_BF16) return dense_filter_synthesis(p, ghat, D, nullptr, mu_val, f);
     FilterDesc fd = make_filter(p, D, nullptr);
     fd.mu_val = mu_val;
     T* ft = reinterpret_cast<T*>(f);

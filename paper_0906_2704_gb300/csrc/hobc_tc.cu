@@ -4,13 +4,14 @@
 // operands K-major in HBM and each operand held as a pair of bfloat16 arrays
 // (hi = bf16(x), lo = bf16(x - hi)); the three products hi.hi + hi.lo + lo.hi
 // accumulate in FP32 in tensor memory, which keeps about 16 significant bits
-// of every product.  One CTA (four warps) computes a 128 x 256 tile: all
-// threads stage K-slices of 64 into shared memory with cp.async in the
-// no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix), one
-// thread issues tcgen05.mma and commits to an mbarrier per stage, and the
-// four warps read their 32 accumulator lanes back with tcgen05.ld for the
-// epilogue.  Every mbarrier wait is bounded; a wait that gives up sets an
-// error word that the host reads.
+// of every product.  One CTA (four warps) computes a 128 x 128 tile with a
+// warp-specialised three-stage pipeline: one thread issues TMA loads of
+// 64-wide K slices (128-byte swizzled shared memory, completion counted in
+// bytes on a per-stage mbarrier), one thread issues tcgen05.mma and commits
+// each stage back to the producer, and the four warps read their 32
+// accumulator lanes back with tcgen05.ld for the epilogue.  Every mbarrier
+// wait is bounded; a wait that gives up sets an error word that the host reads.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -20,34 +21,37 @@
 
 #include "../../include/hobc_tc.h"
 #include "hobc_internal.h"
+#include "hobc_kernels.cuh"
 
 namespace hobc {
 namespace tc {
 
 constexpr int BM = 128;          // tile rows (accumulator lanes)
-constexpr int BN = 256;          // tile columns (accumulator columns)
-constexpr int BK = 64;           // K per stage (eight 16-byte core-matrix columns)
-constexpr int STAGES = 2;
+constexpr int BN = 128;          // tile columns (accumulator columns)
+constexpr int BK = 64;           // K per stage: one 128-byte swizzled row per operand row
+constexpr int STAGES = 3;
 constexpr int THREADS = 128;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;     // A hi, A lo, B hi, B lo
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;    // + barriers and the TMEM slot
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 1024;   // + alignment slack, barriers, TMEM slot
 constexpr unsigned WAIT_LIMIT = 1u << 22;                  // try_wait polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Shared-memory matrix descriptor, no swizzle: start address, the byte
-// distance between core matrices adjacent in K (leading) and in M/N (stride).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lead, uint32_t stride) {
+// Shared-memory matrix descriptor of a K-major tile in the 128-byte swizzled
+// layout TMA writes: rows of 128 bytes, 8-row groups 1024 bytes apart (the
+// stride field); the leading field is not used by this layout.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lead >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((stride >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1u << 46;     // descriptor version of this architecture family
-    return d;                    // base offset 0, swizzle none
+    d |= (uint64_t)1u << 16;                     // leading byte offset (unused): 16 bytes
+    d |= (uint64_t)(1024u >> 4) << 32;           // stride byte offset: 1024
+    d |= (uint64_t)1u << 46;                     // descriptor version of this architecture family
+    d |= (uint64_t)2u << 61;                     // layout: 128-byte swizzle
+    return d;
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
@@ -88,30 +92,21 @@ __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
+__device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
 }
 
-// Rows [0, R) x K-slice [k0, k0 + 64) of a K-major bf16 matrix (leading
-// dimension ld elements) into the core-matrix layout: row r, 16-byte column c
-// at ((r / 8) * 8 + c) * 128 + (r % 8) * 16.  Thread i copies the i-th 16 bytes
-// of that layout, so a warp's shared-memory stores are contiguous and its
-// global reads are 64 contiguous bytes from each of 8 rows.
-template <int R>
-__device__ __forceinline__ void stage_tile(uint32_t sbase, const __nv_bfloat16* __restrict__ g, long long ld,
-                                           int k0) {
-#pragma unroll 4
-    for (int i = threadIdx.x; i < R * 8; i += THREADS) {
-        const int grp = i >> 6, c = (i >> 3) & 7, rr = i & 7;
-        cp_async16(sbase + (uint32_t)(i << 4), g + (long long)(grp * 8 + rr) * ld + k0 + c * 8);
-    }
+// 2D TMA load of box (x = K offset, y = row) into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load(uint32_t sdst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(sdst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
 }
 
-struct Operand {                 // one split operand: hi and lo arrays, K-major
-    const __nv_bfloat16* hi;
-    const __nv_bfloat16* lo;
-    long long ld;                // elements between rows
-    long long batch_stride;      // elements between problems (0: shared)
+struct Maps {                    // tensor maps of the four operand arrays
+    CUtensorMap a_hi, a_lo, b_hi, b_lo;
 };
 
 struct Output {
@@ -130,28 +125,35 @@ __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo
     lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-// C tile (blockIdx.x: N tile, blockIdx.y: M tile, blockIdx.z: problem).
+// C tile (blockIdx.x: N tile, blockIdx.y: M tile, blockIdx.z: problem).  Rows of
+// problem z start at z * a_rpp (A) and z * b_rpp (B) in the maps' row space.
 __global__ void __launch_bounds__(THREADS, 1)
-k_gemm_split(Operand A, Operand B, int KT, Output out, int* __restrict__ err) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + STAGES * STAGE_BYTES + 64);
+k_gemm_split(const __grid_constant__ Maps maps, int a_rpp, int b_rpp, int KT, Output out, int* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    // 128-byte swizzled tiles want 1024-byte alignment
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = empty + STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    int* progress = reinterpret_cast<int*>(tmem_slot + 1);         // [0] stages loaded, [1] stages consumed
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const long long z = blockIdx.z;
+    const int z = blockIdx.z;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const __nv_bfloat16* Ahi = A.hi + z * A.batch_stride + (long long)m0 * A.ld;
-    const __nv_bfloat16* Alo = A.lo + z * A.batch_stride + (long long)m0 * A.ld;
-    const __nv_bfloat16* Bhi = B.hi + z * B.batch_stride + (long long)n0 * B.ld;
-    const __nv_bfloat16* Blo = B.lo + z * B.batch_stride + (long long)n0 * B.ld;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(BN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[s])), "r"(1));
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[s])), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(done)), "r"(1));
+        progress[0] = 0;
+        progress[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
         asm volatile("fence.proxy.async.shared::cta;");
     }
@@ -159,51 +161,55 @@ k_gemm_split(Operand A, Operand B, int KT, Output out, int* __restrict__ err) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = instr_desc(BM, BN);
     bool ok = true;
 
-    for (int kt = 0; kt < KT; ++kt) {
-        const int s = kt % STAGES;
-        unsigned char* st = smem + s * STAGE_BYTES;
-        if (kt >= STAGES) {      // the MMAs of tile kt - STAGES read this stage
-            if (!wait_bounded(&bars[s], (uint32_t)((kt / STAGES - 1) & 1))) ok = false;
+    if (threadIdx.x == 0) {                      // producer: TMA loads of every K slice
+        const int ya = z * a_rpp + m0, yb = z * b_rpp + n0;
+        int kt = 0;
+        for (; kt < KT; ++kt) {
+            const int s = kt % STAGES;
+            if (kt >= STAGES && !wait_bounded(&empty[s], (uint32_t)((kt / STAGES - 1) & 1))) { ok = false; break; }
+            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+            expect_tx(&full[s], STAGE_BYTES);
+            tma_load(sa, &maps.a_hi, kt * BK, ya, &full[s]);
+            tma_load(sa + A_BYTES, &maps.a_lo, kt * BK, ya, &full[s]);
+            tma_load(sa + 2 * A_BYTES, &maps.b_hi, kt * BK, yb, &full[s]);
+            tma_load(sa + 2 * A_BYTES + B_BYTES, &maps.b_lo, kt * BK, yb, &full[s]);
         }
-        ok = __syncthreads_and(ok) != 0;
-        if (!ok) break;
-        const uint32_t sa = smem_u32(st);
-        stage_tile<BM>(sa, Ahi, A.ld, kt * BK);
-        stage_tile<BM>(sa + A_BYTES, Alo, A.ld, kt * BK);
-        stage_tile<BN>(sa + 2 * A_BYTES, Bhi, B.ld, kt * BK);
-        stage_tile<BN>(sa + 2 * A_BYTES + B_BYTES, Blo, B.ld, kt * BK);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        progress[0] = kt;
+    } else if (threadIdx.x == 32) {              // MMA issuer
+        const uint32_t idesc = instr_desc(BM, BN);
+        int kt = 0;
+        for (; kt < KT; ++kt) {
+            const int s = kt % STAGES;
+            if (!wait_bounded(&full[s], (uint32_t)((kt / STAGES) & 1))) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
             const uint32_t a_hi = sa, a_lo = sa + A_BYTES, b_hi = sa + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint32_t ko = kk * 256;     // two core matrices of K per MMA
-                const uint64_t dah = smem_desc(a_hi + ko, 128, 1024), dal = smem_desc(a_lo + ko, 128, 1024);
-                const uint64_t dbh = smem_desc(b_hi + ko, 128, 1024), dbl = smem_desc(b_lo + ko, 128, 1024);
+                const uint32_t ko = kk * 32;             // 16 bf16 of K inside the 128-byte row
+                const uint64_t dah = smem_desc_sw128(a_hi + ko), dal = smem_desc_sw128(a_lo + ko);
+                const uint64_t dbh = smem_desc_sw128(b_hi + ko), dbl = smem_desc_sw128(b_lo + ko);
                 mma(tmem, dah, dbh, idesc, (kt | kk) ? 1u : 0u);
                 mma(tmem, dah, dbl, idesc, 1u);
                 mma(tmem, dal, dbh, idesc, 1u);
             }
-            commit(&bars[s]);
+            commit(&empty[s]);
         }
-        __syncthreads();
+        progress[1] = kt;
+        if (ok) commit(done);
     }
-    // all MMAs issued so far complete in order: wait for the last commit
-    if (ok && KT > 0) {
-        const int last = KT - 1;
-        if (!wait_bounded(&bars[last % STAGES], (uint32_t)((last / STAGES) & 1))) ok = false;
+    // epilogue: every warp waits for the last MMA, then reads its 32 lanes
+    const bool all_ok = __syncthreads_and(ok) != 0;
+    bool have = false;
+    if (all_ok) have = wait_bounded(done, 0);
+    if (!have && lane == 0) atomicOr(err, 1);
+    if (threadIdx.x == 0 && !all_ok) {           // let loads still in flight land before the CTA exits
+        for (int kt = progress[1]; kt < progress[0]; ++kt) wait_bounded(&full[kt % STAGES], (uint32_t)((kt / STAGES) & 1));
     }
-    if (!ok && lane == 0) atomicOr(err, 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
-
-    if (ok) {
+    if (__syncthreads_and(have)) {
         const int row = m0 + warp * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
         for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -222,14 +228,15 @@ k_gemm_split(Operand A, Operand B, int KT, Output out, int* __restrict__ err) {
                     const int col = n0 + c0 + j;
                     if (col >= out.cols) break;
                     const float v = __uint_as_float(r[j]);
+                    const long long zb = (long long)z * out.batch_stride;
                     if (out.mode == HOBC_TC_OUT_F32) {
-                        out.f32[z * out.batch_stride + (long long)row * out.ld + col] = v;
+                        out.f32[zb + (long long)row * out.ld + col] = v;
                     } else if (out.mode == HOBC_TC_OUT_F32_T) {
-                        out.f32[z * out.batch_stride + (long long)col * out.ld + row] = v;
+                        out.f32[zb + (long long)col * out.ld + row] = v;
                     } else if (out.mode == HOBC_TC_OUT_SPLIT) {
-                        split_store(out.hi, out.lo, z * out.batch_stride + (long long)row * out.ld + col, v);
+                        split_store(out.hi, out.lo, zb + (long long)row * out.ld + col, v);
                     } else {
-                        split_store(out.hi, out.lo, z * out.batch_stride + (long long)col * out.ld + row, v);
+                        split_store(out.hi, out.lo, zb + (long long)col * out.ld + row, v);
                     }
                 }
             }
@@ -258,10 +265,334 @@ __global__ void k_split(const float* __restrict__ src, long long src_ld, long lo
     }
 }
 
+// src holds a matrix transposed (FP64, src[c][r] at c * src_ld + r); write
+// rows r < rows, columns c < cols of its transpose as a split operand.
+__global__ void k_split_f64_t(const double* __restrict__ src, long long src_ld, int rows, int cols,
+                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long long ld) {
+    const long long total = (long long)rows * cols;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / cols), c = (int)(i - (long long)r * cols);
+        const double v = src[(long long)c * src_ld + r];
+        const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+        hi[(long long)r * ld + c] = h;
+        lo[(long long)r * ld + c] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+    }
+}
+
+// Filter (Eq. (eq:freg)) of the spectrum and split into the A operand of the
+// first synthesis pass.  2D: spectrum [item][t1][t0] -> rows t1, columns t0;
+// 1D: [item][t] -> row item, column t.  fd.D null: no filter (plain synthesis).
+__global__ void k_filter_split(const float* __restrict__ spec, long long S, int nrows, int ncols, int ndim,
+                               Axis<float> ax0, FilterDesc fd, int items, __nv_bfloat16* __restrict__ hi,
+                               __nv_bfloat16* __restrict__ lo, long long ld, long long bs) {
+    const long long per = (long long)nrows * ncols;
+    const long long total = per * items;
+    const float* D = static_cast<const float*>(fd.D);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long item = i / per, e = i - item * per;
+        const int r = (int)(e / ncols), c = (int)(e - (long long)r * ncols);
+        float v = spec[item * S + e];
+        if (D) {
+            const int problem = (int)item;
+            const float d = D[(fd.psf_per ? item : 0) * fd.d_psf_stride + e];
+            const float s2 = smoothing2<float>(fd, ndim == 2 ? 2 : 1, ax0, ndim == 2 ? r : problem, c);
+            v = apply_filter(v, d, s2, (float)mu_of(fd, problem));
+        }
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const long long o = ndim == 2 ? item * bs + (long long)r * ld + c : (item) * ld + c;
+        hi[o] = h;
+        lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+// ------------------------------------------------------------ tensor maps
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiled g_encode = nullptr;
+
+hobc_status encode_maps() {
+    if (g_encode) return HOBC_OK;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+        set_last_error_text("hobc_tc_gemm: cuTensorMapEncodeTiled is not available");
+        return HOBC_ERR_CUDA;
+    }
+    g_encode = reinterpret_cast<EncodeTiled>(fn);
+    return HOBC_OK;
+}
+
+// Rows x K bf16 array (row stride ld elements) read in boxes of 64 K x box_rows,
+// 128-byte swizzled; reads outside the array return zeros.
+hobc_status make_map(CUtensorMap* map, const void* base, long long k, long long ld, long long rows, int box_rows) {
+    const cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        char msg[96];
+        snprintf(msg, sizeof(msg), "hobc_tc_gemm: cuTensorMapEncodeTiled failed (%d)", (int)r);
+        set_last_error_text(msg);
+        return HOBC_ERR_ARG;
+    }
+    return HOBC_OK;
+}
+
 }  // namespace tc
 }  // namespace hobc
 
 using namespace hobc;
+
+// ===================================================== dense plan (HOBC_SPLIT_BF16)
+
+struct hobc_dense_s {
+    int nax;
+    int n[2];
+    long long kp[2];                       // padded K per axis
+    // split matrices: 2D 0 = T1^{-1} (B), 1 = T0^{-1} (A), 2 = T0 (B), 3 = T1 (A);
+    //                 1D 0 = T^{-1} (B), 2 = T (B)
+    __nv_bfloat16* m_hi[4];
+    __nv_bfloat16* m_lo[4];
+    long long m_ld[4];
+    // operand workspace: 0 = g (A), 1 = row-pass output (B), 2 = filtered spectrum (A), 3 = column-synthesis output (B)
+    __nv_bfloat16* w_hi[4];
+    __nv_bfloat16* w_lo[4];
+    long long w_ld[4], w_bs[4];
+    int* err;
+};
+
+namespace {
+
+long long pad_to(long long x, long long t) { return (x + t - 1) / t * t; }
+
+hobc_status gemm(hobc_plan_s* p, const __nv_bfloat16* ah, const __nv_bfloat16* al, long long ald, long long abs_,
+                 const __nv_bfloat16* bh, const __nv_bfloat16* bl, long long bld, long long bbs, int m, int n, long long k,
+                 int batch, int mode, float* f32, __nv_bfloat16* oh, __nv_bfloat16* ol, long long old_, long long obs) {
+    hobc_tc_operand A{ah, al, ald, abs_};
+    hobc_tc_operand B{bh, bl, bld, bbs};
+    hobc_tc_output O{mode, f32, oh, ol, old_, obs, m, n};
+    hobc_status s = hobc_tc_gemm(&A, &B, m, n, (int)k, batch, &O, p->dense->err, p->stream);
+    if (s == HOBC_OK) ++p->launches;
+    return s;
+}
+
+Axis<float> axis0(const hobc_plan_s* p) {
+    Axis<float> a;
+    memset(&a, 0, sizeof(a));
+    a.fam = p->ax[0].fam; a.n = p->ax[0].n; a.N = p->ax[0].N; a.W = p->ax[0].W;
+    return a;
+}
+
+FilterDesc filter_desc(const hobc_plan_s* p, const void* D, const int* mu_idx, const double* mu_val) {
+    FilterDesc f;
+    memset(&f, 0, sizeof(f));
+    f.D = D;
+    f.d_psf_stride = (long long)p->spec_elems;
+    f.psf_per = p->desc.psf_per_item;
+    f.mu_idx = mu_idx;
+    f.mu = p->mu;
+    f.K = p->K;
+    f.lap = p->desc.L == HOBC_L_LAPLACIAN;
+    const AxisHost& o = p->ax[p->nax - 1];
+    f.o_fam = o.fam; f.o_n = o.n; f.o_N = o.N; f.o_W = o.W;
+    f.mu_val = mu_val;
+    return f;
+}
+
+hobc_status check(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { set_last_error(what, e); return HOBC_ERR_CUDA; }
+    return HOBC_OK;
+}
+
+// Synthesis from the split operand already in workspace 2 (rows of the filtered spectrum).
+hobc_status dense_synthesis_from_x(hobc_plan_s* p, float* y) {
+    hobc_dense_s* d = p->dense;
+    const int B = p->desc.batch;
+    const size_t z0 = p->item0;
+    if (d->nax == 1) {
+        const int n = d->n[0];
+        return gemm(p, d->w_hi[2] + z0 * d->w_ld[2], d->w_lo[2] + z0 * d->w_ld[2], d->w_ld[2], 0, d->m_hi[2],
+                    d->m_lo[2], d->m_ld[2], 0, B, n, d->kp[0], 1, HOBC_TC_OUT_F32, y, nullptr, nullptr, n, 0);
+    }
+    const int n0 = d->n[0], n1 = d->n[1];
+    // columns: Y[t1][r] = sum_t0 X[t1][t0] T0[r][t0], stored transposed (rows r)
+    hobc_status s = gemm(p, d->w_hi[2] + z0 * d->w_bs[2], d->w_lo[2] + z0 * d->w_bs[2], d->w_ld[2], d->w_bs[2],
+                         d->m_hi[2], d->m_lo[2], d->m_ld[2], 0, n1, n0, d->kp[0], B, HOBC_TC_OUT_SPLIT_T, nullptr,
+                         d->w_hi[3] + z0 * d->w_bs[3], d->w_lo[3] + z0 * d->w_bs[3], d->w_ld[3], d->w_bs[3]);
+    if (s != HOBC_OK) return s;
+    // rows: f[r][j] = sum_t1 T1[j][t1] Y[t1][r], computed as C[j][r] and stored transposed
+    return gemm(p, d->m_hi[3], d->m_lo[3], d->m_ld[3], 0, d->w_hi[3] + z0 * d->w_bs[3], d->w_lo[3] + z0 * d->w_bs[3],
+                d->w_ld[3], d->w_bs[3], n1, n0, d->kp[1], B, HOBC_TC_OUT_F32_T, y, nullptr, nullptr, n1,
+                (long long)n0 * n1);
+}
+
+}  // namespace
+
+namespace hobc {
+
+void dense_free(hobc_plan_s* p) {
+    hobc_dense_s* d = p->dense;
+    if (!d) return;
+    for (int i = 0; i < 4; ++i) {
+        cudaFree(d->m_hi[i]); cudaFree(d->m_lo[i]); cudaFree(d->w_hi[i]); cudaFree(d->w_lo[i]);
+    }
+    cudaFree(d->err);
+    delete d;
+    p->dense = nullptr;
+}
+
+hobc_status dense_prepare(hobc_plan_s* p) {
+    hobc_dense_s* d = new hobc_dense_s();
+    p->dense = d;
+    d->nax = p->nax;
+    const int B = p->desc.batch;
+    for (int a = 0; a < p->nax; ++a) {
+        d->n[a] = p->ax[a].n;
+        d->kp[a] = pad_to(d->n[a], tc::BK);
+    }
+    cudaError_t e = cudaSuccess;
+    auto alloc2 = [&](__nv_bfloat16** hi, __nv_bfloat16** lo, size_t elems) {
+        if (e == cudaSuccess) e = cudaMalloc((void**)hi, elems * 2);
+        if (e == cudaSuccess) e = cudaMalloc((void**)lo, elems * 2);
+        if (e == cudaSuccess) e = cudaMemset(*hi, 0, elems * 2);
+        if (e == cudaSuccess) e = cudaMemset(*lo, 0, elems * 2);
+    };
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(d->err, 0, sizeof(int));
+    // the matrices: T_X and T_X^{-1} of each axis from the FP64 path applied to identities
+    int mi[2][2];                      // matrix slot of (axis, inverse?)
+    if (p->nax == 2) { mi[1][1] = 0; mi[0][1] = 1; mi[0][0] = 2; mi[1][0] = 3; }
+    else { mi[0][1] = 0; mi[0][0] = 2; }
+    for (int a = 0; a < p->nax && e == cudaSuccess; ++a) {
+        const int n = d->n[a];
+        const long long kp = d->kp[a];
+        for (int inv = 0; inv < 2 && e == cudaSuccess; ++inv) {
+            const int slot = mi[a][inv];
+            const bool as_a = p->nax == 2 && (slot == 1 || slot == 3);
+            const long long rows = pad_to(n, as_a ? tc::BM : tc::BN);
+            d->m_ld[slot] = kp;
+            alloc2(&d->m_hi[slot], &d->m_lo[slot], (size_t)rows * kp);
+        }
+    }
+    // operand workspace
+    if (p->nax == 2) {
+        const long long n0 = d->n[0], n1 = d->n[1];
+        const long long rows[4] = {pad_to(n0, tc::BM), pad_to(n1, tc::BN), pad_to(n1, tc::BM), pad_to(n0, tc::BN)};
+        const long long lds[4] = {d->kp[1], d->kp[0], d->kp[0], d->kp[1]};
+        for (int w = 0; w < 4; ++w) {
+            d->w_ld[w] = lds[w];
+            d->w_bs[w] = rows[w] * lds[w];
+            alloc2(&d->w_hi[w], &d->w_lo[w], (size_t)B * rows[w] * lds[w]);
+        }
+    } else {
+        const long long rows = pad_to(B, tc::BM) + tc::BM;   // a chunk's last tile may run past the batch
+        for (int w : {0, 2}) {
+            d->w_ld[w] = d->kp[0];
+            d->w_bs[w] = 0;
+            alloc2(&d->w_hi[w], &d->w_lo[w], (size_t)rows * d->kp[0]);
+        }
+    }
+    if (e != cudaSuccess) { set_last_error("hobc_plan_create (dense)", e); return HOBC_ERR_CUDA; }
+    // build T and T^{-1}
+    for (int a = 0; a < p->nax; ++a) {
+        const int n = d->n[a];
+        hobc_plan_desc q;
+        memset(&q, 0, sizeof(q));
+        q.ndim = 1; q.n[0] = n; q.psf[0] = 1; q.family = (hobc_family)p->fam; q.psf_symmetric = 1;
+        q.bc_degree = p->fam == HOBC_FAMILY_SINE ? 1 : (p->fam == HOBC_FAMILY_COSINE ? 2 : 3);
+        q.L = HOBC_L_IDENTITY; q.prec = HOBC_FP64; q.n_mu = 1; q.batch = n; q.psf_per_item = 0;
+        const double one = 1.0;
+        hobc_plan* ip = nullptr;
+        hobc_status s = hobc_plan_create(&q, &one, p->stream, &ip);
+        if (s != HOBC_OK) return s;
+        double *I = nullptr, *out = nullptr;
+        e = cudaMalloc((void**)&I, (size_t)n * n * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&out, (size_t)n * n * sizeof(double));
+        if (e == cudaSuccess) {
+            std::vector<double> eye((size_t)n * n, 0.0);
+            for (int i = 0; i < n; ++i) eye[(size_t)i * n + i] = 1.0;
+            e = cudaMemcpy(I, eye.data(), eye.size() * sizeof(double), cudaMemcpyHostToDevice);
+        }
+        for (int inv = 1; inv >= 0 && e == cudaSuccess && s == HOBC_OK; --inv) {
+            // analysis of e_j gives row j = column j of T^{-1}; synthesis of e_t gives column t of T
+            s = inv ? hobc_analysis(ip, I, out) : hobc_synthesis(ip, I, out);
+            if (s != HOBC_OK) break;
+            const int slot = mi[a][inv];
+            tc::k_split_f64_t<<<256, 256, 0, p->stream>>>(out, n, n, n, d->m_hi[slot], d->m_lo[slot], d->m_ld[slot]);
+            e = cudaStreamSynchronize(p->stream);
+        }
+        cudaFree(I);
+        cudaFree(out);
+        hobc_plan_destroy(ip);
+        if (s != HOBC_OK) return s;
+        if (e != cudaSuccess) { set_last_error("hobc_plan_create (dense)", e); return HOBC_ERR_CUDA; }
+    }
+    return HOBC_OK;
+}
+
+hobc_status dense_analysis(hobc_plan_s* p, const void* g, void* ghat) {
+    hobc_dense_s* d = p->dense;
+    const int B = p->desc.batch;
+    const size_t z0 = p->item0;
+    const float* gf = static_cast<const float*>(g);
+    float* out = static_cast<float*>(ghat);
+    if (d->nax == 1) {
+        const int n = d->n[0];
+        hobc_status s = hobc_tc_split(gf, n, 0, B, n, d->w_hi[0] + z0 * d->w_ld[0], d->w_lo[0] + z0 * d->w_ld[0],
+                                      d->w_ld[0], 0, B, 1, p->stream);
+        if (s != HOBC_OK) return s;
+        ++p->launches;
+        return gemm(p, d->w_hi[0] + z0 * d->w_ld[0], d->w_lo[0] + z0 * d->w_ld[0], d->w_ld[0], 0, d->m_hi[0],
+                    d->m_lo[0], d->m_ld[0], 0, B, n, d->kp[0], 1, HOBC_TC_OUT_F32, out, nullptr, nullptr, n, 0);
+    }
+    const int n0 = d->n[0], n1 = d->n[1];
+    hobc_status s = hobc_tc_split(gf, n1, (long long)n0 * n1, n0, n1, d->w_hi[0] + z0 * d->w_bs[0],
+                                  d->w_lo[0] + z0 * d->w_bs[0], d->w_ld[0], d->w_bs[0], n0, B, p->stream);
+    if (s != HOBC_OK) return s;
+    ++p->launches;
+    // rows: R[t1][r] = sum_j T1^{-1}[t1][j] g[r][j], computed as C[r][t1] and stored transposed
+    s = gemm(p, d->w_hi[0] + z0 * d->w_bs[0], d->w_lo[0] + z0 * d->w_bs[0], d->w_ld[0], d->w_bs[0], d->m_hi[0],
+             d->m_lo[0], d->m_ld[0], 0, n0, n1, d->kp[1], B, HOBC_TC_OUT_SPLIT_T, nullptr,
+             d->w_hi[1] + z0 * d->w_bs[1], d->w_lo[1] + z0 * d->w_bs[1], d->w_ld[1], d->w_bs[1]);
+    if (s != HOBC_OK) return s;
+    // columns: ghat[t1][t0] = sum_r T0^{-1}[t0][r] R[t1][r], computed as C[t0][t1] and stored transposed
+    return gemm(p, d->m_hi[1], d->m_lo[1], d->m_ld[1], 0, d->w_hi[1] + z0 * d->w_bs[1], d->w_lo[1] + z0 * d->w_bs[1],
+                d->w_ld[1], d->w_bs[1], n0, n1, d->kp[0], B, HOBC_TC_OUT_F32_T, out, nullptr, nullptr, n0,
+                (long long)n0 * n1);
+}
+
+hobc_status dense_filter_synthesis(hobc_plan_s* p, const void* ghat, const void* D, const int* mu_idx,
+                                   const double* mu_val, void* f) {
+    hobc_dense_s* d = p->dense;
+    const int B = p->desc.batch;
+    const size_t z0 = p->item0;
+    const FilterDesc fd = filter_desc(p, D, mu_idx, mu_val);
+    const int rows = d->nax == 2 ? d->n[1] : 1, cols = d->nax == 2 ? d->n[0] : d->n[0];
+    __nv_bfloat16* xh = d->w_hi[2] + z0 * (d->nax == 2 ? d->w_bs[2] : d->w_ld[2]);
+    __nv_bfloat16* xl = d->w_lo[2] + z0 * (d->nax == 2 ? d->w_bs[2] : d->w_ld[2]);
+    tc::k_filter_split<<<1024, 256, 0, p->stream>>>(static_cast<const float*>(ghat), (long long)p->spec_elems, rows,
+                                                     cols, d->nax, axis0(p), fd, B, xh, xl, d->w_ld[2], d->w_bs[2]);
+    hobc_status s = check("k_filter_split");
+    if (s != HOBC_OK) return s;
+    ++p->launches;
+    return dense_synthesis_from_x(p, static_cast<float*>(f));
+}
+
+hobc_status dense_synthesis(hobc_plan_s* p, const void* c, void* y) {
+    return dense_filter_synthesis(p, c, nullptr, nullptr, nullptr, y);
+}
+
+}  // namespace hobc
+
 
 extern "C" {
 
@@ -287,23 +618,48 @@ hobc_status hobc_tc_gemm(const hobc_tc_operand* a, const hobc_tc_operand* b, int
     if (!a->hi || !a->lo || !b->hi || !b->lo) return HOBC_ERR_ARG;
     if (a->ld % 8 || b->ld % 8 || a->ld < k || b->ld < k) return HOBC_ERR_ARG;     // 16-byte rows
     if (k % tc::BK) return HOBC_ERR_ARG;                                             // padded K
+    if (a->batch_stride % a->ld || b->batch_stride % b->ld) return HOBC_ERR_ARG;     // whole rows per problem
     if (out->mode < HOBC_TC_OUT_F32 || out->mode > HOBC_TC_OUT_SPLIT_T) return HOBC_ERR_ARG;
     const bool split = out->mode == HOBC_TC_OUT_SPLIT || out->mode == HOBC_TC_OUT_SPLIT_T;
     if (split ? (!out->hi || !out->lo) : !out->f32) return HOBC_ERR_ARG;
+    const long long mp = (m + tc::BM - 1) / tc::BM * tc::BM, np = (n + tc::BN - 1) / tc::BN * tc::BN;
+    const long long a_rpp = a->batch_stride / a->ld, b_rpp = b->batch_stride / b->ld;
+    if ((a_rpp && a_rpp < mp) || (b_rpp && b_rpp < np)) return HOBC_ERR_ARG;     // padded rows per problem
+    if (a_rpp * (batch - 1) + mp > INT32_MAX || b_rpp * (batch - 1) + np > INT32_MAX) return HOBC_ERR_SIZE;
+    hobc_status s = tc::encode_maps();
+    if (s != HOBC_OK) return s;
+    tc::Maps maps;
+    s = tc::make_map(&maps.a_hi, a->hi, k, a->ld, a_rpp * (batch - 1) + mp, tc::BM);
+    if (s == HOBC_OK) s = tc::make_map(&maps.a_lo, a->lo, k, a->ld, a_rpp * (batch - 1) + mp, tc::BM);
+    if (s == HOBC_OK) s = tc::make_map(&maps.b_hi, b->hi, k, b->ld, b_rpp * (batch - 1) + np, tc::BN);
+    if (s == HOBC_OK) s = tc::make_map(&maps.b_lo, b->lo, k, b->ld, b_rpp * (batch - 1) + np, tc::BN);
+    if (s != HOBC_OK) return s;
     cudaError_t e = cudaFuncSetAttribute(tc::k_gemm_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          tc::SMEM_BYTES);
     if (e != cudaSuccess) { set_last_error("hobc_tc_gemm", e); return HOBC_ERR_CUDA; }
-    tc::Operand A{static_cast<const __nv_bfloat16*>(a->hi), static_cast<const __nv_bfloat16*>(a->lo), a->ld,
-                  a->batch_stride};
-    tc::Operand B{static_cast<const __nv_bfloat16*>(b->hi), static_cast<const __nv_bfloat16*>(b->lo), b->ld,
-                  b->batch_stride};
     tc::Output O{out->mode, out->f32, static_cast<__nv_bfloat16*>(out->hi), static_cast<__nv_bfloat16*>(out->lo),
                  out->ld, out->batch_stride, out->rows, out->cols};
-    dim3 grid((unsigned)((n + tc::BN - 1) / tc::BN), (unsigned)((m + tc::BM - 1) / tc::BM), (unsigned)batch);
+    dim3 grid((unsigned)(np / tc::BN), (unsigned)(mp / tc::BM), (unsigned)batch);
     tc::k_gemm_split<<<grid, tc::THREADS, tc::SMEM_BYTES, reinterpret_cast<cudaStream_t>(cuda_stream)>>>(
-        A, B, k / tc::BK, O, err_dev);
+        maps, (int)a_rpp, (int)b_rpp, k / tc::BK, O, err_dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_last_error("hobc_tc_gemm", e); return HOBC_ERR_CUDA; }
+    return HOBC_OK;
+}
+
+hobc_status hobc_plan_status(hobc_plan* p) {
+    if (!p) return HOBC_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) { set_last_error("hobc_plan_status", e); return HOBC_ERR_CUDA; }
+    if (!p->dense) return HOBC_OK;
+    int flag = 0;
+    e = cudaMemcpy(&flag, p->dense->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && flag) e = cudaMemset(p->dense->err, 0, sizeof(int));
+    if (e != cudaSuccess) { set_last_error("hobc_plan_status", e); return HOBC_ERR_CUDA; }
+    if (flag) {
+        set_last_error_text("a tensor-core pipeline wait gave up; the affected tiles were not written");
+        return HOBC_ERR_TIMEOUT;
+    }
     return HOBC_OK;
 }
 

@@ -32,7 +32,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 FAMILY = {"auto": 0, "sine": 1, "cosine": 2, "fourier": 3, "sine3": 4}
 FAMILY_NAME = {v: k for k, v in FAMILY.items()}
 SMOOTHING = {"I": 0, "identity": 0, "lap": 1, "laplacian": 1}
-PRECISION = {"fp64": 0, "fp32": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "split_bf16": 2}
 STATUS = ["HOBC_OK", "HOBC_ERR_ARG", "HOBC_ERR_UNSUPPORTED", "HOBC_ERR_SIZE",
           "HOBC_ERR_NONFINITE", "HOBC_ERR_CUDA", "HOBC_ERR_TIMEOUT"]
 
@@ -116,6 +116,8 @@ _lib.hobc_tc_split.restype = ctypes.c_int
 for _name in ("hobc_tc_tile_m", "hobc_tc_tile_n", "hobc_tc_tile_k"):
     getattr(_lib, _name).argtypes = []
     getattr(_lib, _name).restype = ctypes.c_int
+_lib.hobc_plan_status.argtypes = [_vp]
+_lib.hobc_plan_status.restype = ctypes.c_int
 _lib.hobc_gcv_binned.argtypes = [_vp] * 6
 _lib.hobc_gcv_binned.restype = ctypes.c_int
 _lib.hobc_deblur_binned.argtypes = [_vp] * 6
@@ -311,6 +313,10 @@ class Plan:
     @property
     def real_dtype(self):
         return np.float64 if self.prec == "fp64" else np.float32
+
+    def status(self) -> None:
+        """Synchronise and raise if a bounded tensor-core wait gave up (split_bf16 plans)."""
+        _check(_lib.hobc_plan_status(self._handle), "hobc_plan_status")
 
     @property
     def last_launch_count(self) -> int:
