@@ -5,8 +5,8 @@
 // (hi = bf16(x), lo = bf16(x - hi)); the three products hi.hi + hi.lo + lo.hi
 // accumulate in FP32 in tensor memory, which keeps about 16 significant bits
 // of every product.  One CTA (four warps) computes a 128 x 128 tile with a
-// warp-specialised three-stage pipeline: one thread issues TMA loads of
-// 64-wide K slices (128-byte swizzled shared memory, completion counted in
+// warp-specialised three-stage pipeline (two CTAs per SM): one thread issues
+// TMA loads of 32-wide K slices (64-byte swizzled shared memory, completion counted in
 // bytes on a per-stage mbarrier), one thread issues tcgen05.mma and commits
 // each stage back to the producer, and the four warps read their 32
 // accumulator lanes back with tcgen05.ld for the epilogue.  Every mbarrier
@@ -28,29 +28,30 @@ namespace tc {
 
 constexpr int BM = 128;          // tile rows (accumulator lanes)
 constexpr int BN = 128;          // tile columns (accumulator columns)
-constexpr int BK = 64;           // K per stage: one 128-byte swizzled row per operand row
+constexpr int BK = 32;           // K per stage: one 64-byte swizzled row per operand row
 constexpr int STAGES = 3;
 constexpr int THREADS = 128;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;     // A hi, A lo, B hi, B lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 1024;   // + alignment slack, barriers, TMEM slot
+constexpr int CTAS_PER_SM = 2;   // one CTA's prologue and epilogue overlap the other's main loop
 constexpr unsigned WAIT_LIMIT = 1u << 22;                  // try_wait polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Shared-memory matrix descriptor of a K-major tile in the 128-byte swizzled
-// layout TMA writes: rows of 128 bytes, 8-row groups 1024 bytes apart (the
+// Shared-memory matrix descriptor of a K-major tile in the 64-byte swizzled
+// layout TMA writes: rows of 64 bytes, 8-row groups 512 bytes apart (the
 // stride field); the leading field is not used by this layout.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)1u << 16;                     // leading byte offset (unused): 16 bytes
-    d |= (uint64_t)(1024u >> 4) << 32;           // stride byte offset: 1024
+    d |= (uint64_t)(512u >> 4) << 32;            // stride byte offset: 512
     d |= (uint64_t)1u << 46;                     // descriptor version of this architecture family
-    d |= (uint64_t)2u << 61;                     // layout: 128-byte swizzle
+    d |= (uint64_t)4u << 61;                     // layout: 64-byte swizzle
     return d;
 }
 
@@ -127,10 +128,10 @@ __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo
 
 // C tile (blockIdx.x: N tile, blockIdx.y: M tile, blockIdx.z: problem).  Rows of
 // problem z start at z * a_rpp (A) and z * b_rpp (B) in the maps' row space.
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
 k_gemm_split(const __grid_constant__ Maps maps, int a_rpp, int b_rpp, int KT, Output out, int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
-    // 128-byte swizzled tiles want 1024-byte alignment
+    // swizzled tiles want 1024-byte alignment
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
@@ -188,9 +189,9 @@ k_gemm_split(const __grid_constant__ Maps maps, int a_rpp, int b_rpp, int KT, Ou
             const uint32_t a_hi = sa, a_lo = sa + A_BYTES, b_hi = sa + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint32_t ko = kk * 32;             // 16 bf16 of K inside the 128-byte row
-                const uint64_t dah = smem_desc_sw128(a_hi + ko), dal = smem_desc_sw128(a_lo + ko);
-                const uint64_t dbh = smem_desc_sw128(b_hi + ko), dbl = smem_desc_sw128(b_lo + ko);
+                const uint32_t ko = kk * 32;             // 16 bf16 of K inside the 64-byte row
+                const uint64_t dah = smem_desc_sw64(a_hi + ko), dal = smem_desc_sw64(a_lo + ko);
+                const uint64_t dbh = smem_desc_sw64(b_hi + ko), dbl = smem_desc_sw64(b_lo + ko);
                 mma(tmem, dah, dbh, idesc, (kt | kk) ? 1u : 0u);
                 mma(tmem, dah, dbl, idesc, 1u);
                 mma(tmem, dal, dbh, idesc, 1u);
@@ -327,15 +328,15 @@ hobc_status encode_maps() {
     return HOBC_OK;
 }
 
-// Rows x K bf16 array (row stride ld elements) read in boxes of 64 K x box_rows,
-// 128-byte swizzled; reads outside the array return zeros.
+// Rows x K bf16 array (row stride ld elements) read in boxes of BK x box_rows,
+// 64-byte swizzled; reads outside the array return zeros.
 hobc_status make_map(CUtensorMap* map, const void* base, long long k, long long ld, long long rows, int box_rows) {
     const cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
     const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         char msg[96];
