@@ -459,6 +459,12 @@ def run_other(args):
             ms_a, _ = _timed(lambda: plan.analysis(g, gh), stream, args.steps, 2)
             ms_s, _ = _timed(lambda: plan.synthesis(gh, f), stream, args.steps, 2)
             extra = {"transform_ms_per_step": {"analysis": ms_a / args.steps, "synthesis": ms_s / args.steps}}
+            f_b = torch.empty_like(g)
+            mi_b = torch.empty(B, dtype=torch.int32, device=dev)
+            ms_b, _ = _timed(lambda: plan.deblur_binned(g, h, f_b, mi_b), stream, args.steps, 2)
+            plan.status()
+            extra["binned_mu"] = {"value": B / (ms_b / args.steps / 1e3), "unit": "deblurs/s",
+                                  "index_agreement_with_full_scan": float((mi_b == mi).float().mean())}
             if prec == "split_bf16":
                 # 4 passes x 3 split products x 2 n^3 (the padded tile shape is what the tensor cores run)
                 tm, tn, tk = hobc.tc_tiles()
