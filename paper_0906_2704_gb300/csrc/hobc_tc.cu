@@ -4,7 +4,7 @@
 // operands K-major in HBM and each operand held as a pair of bfloat16 arrays
 // (hi = bf16(x), lo = bf16(x - hi)); the three products hi.hi + hi.lo + lo.hi
 // accumulate in FP32 in tensor memory, which keeps about 16 significant bits
-// of every product.  One CTA (four warps) computes a 128 x 128 tile with a
+// of every product.  A persistent CTA per SM computes 128 x 256 tiles with a
 // warp-specialised three-stage pipeline (two CTAs per SM): one thread issues
 // TMA loads of 32-wide K slices (64-byte swizzled shared memory, completion counted in
 // bytes on a per-stage mbarrier), one thread issues tcgen05.mma and commits
@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -27,15 +28,15 @@ namespace hobc {
 namespace tc {
 
 constexpr int BM = 128;          // tile rows (accumulator lanes)
-constexpr int BN = 128;          // tile columns (accumulator columns)
+constexpr int BN = 256;          // tile columns (accumulator columns)
 constexpr int BK = 32;           // K per stage: one 64-byte swizzled row per operand row
-constexpr int STAGES = 3;
-constexpr int THREADS = 128;
+constexpr int STAGES = 4;
+constexpr int THREADS = 192;     // warp 0: TMA producer, warp 1: MMA issuer, warps 2-5: epilogue
+constexpr int ACC = 2;           // accumulators in tensor memory (epilogue of one tile overlaps the next)
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;     // A hi, A lo, B hi, B lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 1024;   // + alignment slack, barriers, TMEM slot
-constexpr int CTAS_PER_SM = 2;   // one CTA's prologue and epilogue overlap the other's main loop
 constexpr unsigned WAIT_LIMIT = 1u << 22;                  // try_wait polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -126,25 +127,28 @@ __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo
     lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-// C tile (blockIdx.x: N tile, blockIdx.y: M tile, blockIdx.z: problem).  Rows of
-// problem z start at z * a_rpp (A) and z * b_rpp (B) in the maps' row space.
-__global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
-k_gemm_split(const __grid_constant__ Maps maps, int a_rpp, int b_rpp, int KT, Output out, int* __restrict__ err) {
+// Persistent: CTA c takes tiles c, c + gridDim.x, ... of the ntn x ntm x batch
+// tiles (N tile fastest).  Rows of problem z start at z * a_rpp (A) and
+// z * b_rpp (B) in the maps' row space.  Stage barriers full/empty pace the
+// producer and the MMA thread; accumulator barriers tfull/tempty pace the
+// MMA thread and the four epilogue warps.
+__global__ void __launch_bounds__(THREADS, 1)
+k_gemm_split(const __grid_constant__ Maps maps, int a_rpp, int b_rpp, int KT, int ntn, int ntm, int ntiles,
+             Output out, int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     // swizzled tiles want 1024-byte alignment
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* done = empty + STAGES;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    uint64_t* tfull = empty + STAGES;
+    uint64_t* tempty = tfull + ACC;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + ACC);
     int* progress = reinterpret_cast<int*>(tmem_slot + 1);         // [0] stages loaded, [1] stages consumed
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int z = blockIdx.z;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(BN));
+                     "r"(ACC * BN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (threadIdx.x == 32) {
@@ -152,7 +156,10 @@ k_gemm_split(const __grid_constant__ Maps maps, int a_rpp, int b_rpp, int KT, Ou
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(1));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[s])), "r"(1));
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(done)), "r"(1));
+        for (int a = 0; a < ACC; ++a) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tfull[a])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tempty[a])), "r"(4));
+        }
         progress[0] = 0;
         progress[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -164,88 +171,106 @@ k_gemm_split(const __grid_constant__ Maps maps, int a_rpp, int b_rpp, int KT, Ou
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
 
-    if (threadIdx.x == 0) {                      // producer: TMA loads of every K slice
-        const int ya = z * a_rpp + m0, yb = z * b_rpp + n0;
-        int kt = 0;
-        for (; kt < KT; ++kt) {
-            const int s = kt % STAGES;
-            if (kt >= STAGES && !wait_bounded(&empty[s], (uint32_t)((kt / STAGES - 1) & 1))) { ok = false; break; }
-            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-            expect_tx(&full[s], STAGE_BYTES);
-            tma_load(sa, &maps.a_hi, kt * BK, ya, &full[s]);
-            tma_load(sa + A_BYTES, &maps.a_lo, kt * BK, ya, &full[s]);
-            tma_load(sa + 2 * A_BYTES, &maps.b_hi, kt * BK, yb, &full[s]);
-            tma_load(sa + 2 * A_BYTES + B_BYTES, &maps.b_lo, kt * BK, yb, &full[s]);
+    if (threadIdx.x == 0) {                      // producer: TMA loads of every K slice of every tile
+        int it = 0;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int nt = t % ntn, rest = t / ntn, mt = rest % ntm, z = rest / ntm;
+            const int ya = z * a_rpp + mt * BM, yb = z * b_rpp + nt * BN;
+            for (int kt = 0; kt < KT; ++kt, ++it) {
+                const int s = it % STAGES;
+                if (it >= STAGES && !wait_bounded(&empty[s], (uint32_t)((it / STAGES - 1) & 1))) { ok = false; break; }
+                const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                expect_tx(&full[s], STAGE_BYTES);
+                tma_load(sa, &maps.a_hi, kt * BK, ya, &full[s]);
+                tma_load(sa + A_BYTES, &maps.a_lo, kt * BK, ya, &full[s]);
+                tma_load(sa + 2 * A_BYTES, &maps.b_hi, kt * BK, yb, &full[s]);
+                tma_load(sa + 2 * A_BYTES + B_BYTES, &maps.b_lo, kt * BK, yb, &full[s]);
+            }
         }
-        progress[0] = kt;
+        progress[0] = it;
     } else if (threadIdx.x == 32) {              // MMA issuer
         const uint32_t idesc = instr_desc(BM, BN);
-        int kt = 0;
-        for (; kt < KT; ++kt) {
-            const int s = kt % STAGES;
-            if (!wait_bounded(&full[s], (uint32_t)((kt / STAGES) & 1))) { ok = false; break; }
+        int it = 0, tc_ = 0;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tc_) {
+            const int a = tc_ % ACC;
+            if (tc_ >= ACC && !wait_bounded(&tempty[a], (uint32_t)((tc_ / ACC - 1) & 1))) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-            const uint32_t a_hi = sa, a_lo = sa + A_BYTES, b_hi = sa + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
+            const uint32_t acc = tmem + (uint32_t)(a * BN);
+            for (int kt = 0; kt < KT; ++kt, ++it) {
+                const int s = it % STAGES;
+                if (!wait_bounded(&full[s], (uint32_t)((it / STAGES) & 1))) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                const uint32_t a_hi = sa, a_lo = sa + A_BYTES, b_hi = sa + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint32_t ko = kk * 32;             // 16 bf16 of K inside the 64-byte row
-                const uint64_t dah = smem_desc_sw64(a_hi + ko), dal = smem_desc_sw64(a_lo + ko);
-                const uint64_t dbh = smem_desc_sw64(b_hi + ko), dbl = smem_desc_sw64(b_lo + ko);
-                mma(tmem, dah, dbh, idesc, (kt | kk) ? 1u : 0u);
-                mma(tmem, dah, dbl, idesc, 1u);
-                mma(tmem, dal, dbh, idesc, 1u);
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    const uint32_t ko = kk * 32;         // 16 bf16 of K inside the 64-byte row
+                    const uint64_t dah = smem_desc_sw64(a_hi + ko), dal = smem_desc_sw64(a_lo + ko);
+                    const uint64_t dbh = smem_desc_sw64(b_hi + ko), dbl = smem_desc_sw64(b_lo + ko);
+                    mma(acc, dah, dbh, idesc, (kt | kk) ? 1u : 0u);
+                    mma(acc, dah, dbl, idesc, 1u);
+                    mma(acc, dal, dbh, idesc, 1u);
+                }
+                commit(&empty[s]);
             }
-            commit(&empty[s]);
+            if (!ok) break;
+            commit(&tfull[a]);
         }
-        progress[1] = kt;
-        if (ok) commit(done);
-    }
-    // epilogue: every warp waits for the last MMA, then reads its 32 lanes
-    const bool all_ok = __syncthreads_and(ok) != 0;
-    bool have = false;
-    if (all_ok) have = wait_bounded(done, 0);
-    if (!have && lane == 0) atomicOr(err, 1);
-    if (threadIdx.x == 0 && !all_ok) {           // let loads still in flight land before the CTA exits
-        for (int kt = progress[1]; kt < progress[0]; ++kt) wait_bounded(&full[kt % STAGES], (uint32_t)((kt / STAGES) & 1));
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (__syncthreads_and(have)) {
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            uint32_t r[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                "%13, %14, %15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(lane_base + (uint32_t)c0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < out.rows) {
+        progress[1] = it;
+    } else if (warp >= 2) {                      // epilogue: accumulator lanes of quarter warp % 4
+        const int q = warp % 4;
+        int tc_ = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tc_) {
+            const int a = tc_ % ACC;
+            if (!wait_bounded(&tfull[a], (uint32_t)((tc_ / ACC) & 1))) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int nt = t % ntn, rest = t / ntn, mt = rest % ntm, z = rest / ntm;
+            const int row = mt * BM + q * 32 + lane, n0 = nt * BN;
+            const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN);
+            const long long zb = (long long)z * out.batch_stride;
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                uint32_t r[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15}, [%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(base + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < out.rows) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + c0 + j;
-                    if (col >= out.cols) break;
-                    const float v = __uint_as_float(r[j]);
-                    const long long zb = (long long)z * out.batch_stride;
-                    if (out.mode == HOBC_TC_OUT_F32) {
-                        out.f32[zb + (long long)row * out.ld + col] = v;
-                    } else if (out.mode == HOBC_TC_OUT_F32_T) {
-                        out.f32[zb + (long long)col * out.ld + row] = v;
-                    } else if (out.mode == HOBC_TC_OUT_SPLIT) {
-                        split_store(out.hi, out.lo, zb + (long long)row * out.ld + col, v);
-                    } else {
-                        split_store(out.hi, out.lo, zb + (long long)col * out.ld + row, v);
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = n0 + c0 + j;
+                        if (col >= out.cols) break;
+                        const float v = __uint_as_float(r[j]);
+                        if (out.mode == HOBC_TC_OUT_F32) {
+                            out.f32[zb + (long long)row * out.ld + col] = v;
+                        } else if (out.mode == HOBC_TC_OUT_F32_T) {
+                            out.f32[zb + (long long)col * out.ld + row] = v;
+                        } else if (out.mode == HOBC_TC_OUT_SPLIT) {
+                            split_store(out.hi, out.lo, zb + (long long)row * out.ld + col, v);
+                        } else {
+                            split_store(out.hi, out.lo, zb + (long long)col * out.ld + row, v);
+                        }
                     }
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[a])) : "memory");
         }
+    }
+    if (!ok && lane == 0) atomicOr(err, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {                      // let loads still in flight land before the CTA exits
+        for (int it = progress[1]; it < progress[0]; ++it)
+            wait_bounded(&full[it % STAGES], (uint32_t)((it / STAGES) & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ACC * BN));
 }
 
 // x -> (bf16(x), bf16(x - bf16(x))) into a zero-padded K-major layout: source
@@ -640,9 +665,19 @@ hobc_status hobc_tc_gemm(const hobc_tc_operand* a, const hobc_tc_operand* b, int
     if (e != cudaSuccess) { set_last_error("hobc_tc_gemm", e); return HOBC_ERR_CUDA; }
     tc::Output O{out->mode, out->f32, static_cast<__nv_bfloat16*>(out->hi), static_cast<__nv_bfloat16*>(out->lo),
                  out->ld, out->batch_stride, out->rows, out->cols};
-    dim3 grid((unsigned)(np / tc::BN), (unsigned)(mp / tc::BM), (unsigned)batch);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    const int ntn = (int)(np / tc::BN), ntm = (int)(mp / tc::BM);
+    const long long ntiles = (long long)ntn * ntm * batch;
+    if (ntiles > INT32_MAX) return HOBC_ERR_SIZE;
+    const unsigned grid = (unsigned)std::min<long long>(ntiles, sms);
     tc::k_gemm_split<<<grid, tc::THREADS, tc::SMEM_BYTES, reinterpret_cast<cudaStream_t>(cuda_stream)>>>(
-        maps, (int)a_rpp, (int)b_rpp, k / tc::BK, O, err_dev);
+        maps, (int)a_rpp, (int)b_rpp, k / tc::BK, ntn, ntm, (int)ntiles, O, err_dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_last_error("hobc_tc_gemm", e); return HOBC_ERR_CUDA; }
     return HOBC_OK;
