@@ -103,6 +103,13 @@ def dft_matrix(N: int) -> np.ndarray:
     return np.exp(-2j * np.pi * np.outer(k, k) / N) / np.sqrt(N)
 
 
+def hartley_matrix(n: int) -> np.ndarray:
+    """H[k, j] = (cos(2 pi k j / n) + sin(2 pi k j / n)) / sqrt(n)."""
+    k = np.arange(n)
+    a = 2.0 * np.pi * np.outer(k, k) / n
+    return (np.cos(a) + np.sin(a)) / np.sqrt(n)
+
+
 def flip(n: int) -> np.ndarray:
     """Flip matrix J, J_{i, n+1-i} = 1."""
     return np.eye(n)[::-1]
@@ -167,6 +174,7 @@ def eigen_angles(family: str, n: int) -> np.ndarray:
     'F': x_1 = x_n = 0, x_i = (i-2) 2 pi/(n-2)            (Eq. (eq:Af), reading R4)
     'S3': border columns 1, 2, n-1, n at 0, the others (i-2) pi/(n-3)   (reading R6)
     'P': x_i = 2 (i-1) pi/n                               (Eq. (eq:permat))
+    'PH': as 'P' (periodic conditions in the Hartley basis)
     'R': x_i = (i-1) pi/n                                 (Eq. (eq:refm))
     """
     i = np.arange(1, n + 1, dtype=np.float64)
@@ -182,7 +190,7 @@ def eigen_angles(family: str, n: int) -> np.ndarray:
     elif family == "S3":                                 # reading R6
         th = (i - 2) * np.pi / (n - 3)
         th[[0, 1, n - 2, n - 1]] = 0.0
-    elif family == "P":
+    elif family in ("P", "PH"):
         th = 2 * (i - 1) * np.pi / n
     elif family == "R":
         th = (i - 1) * np.pi / n
@@ -203,9 +211,14 @@ def transform_matrix(family: str, n: int) -> np.ndarray:
     'C': Eq. (eq:Tc)   T_C = [q | c_a^T; C^T; c_b^T | Jq]
     'F': Eq. (eq:Tf)   T_F = [q | c_a^T; F^H; c_b^T | Jq]
     'P': F^H (Eq. (eq:permat)),  'R': C^T (Eq. (eq:refm)) -- classical cases.
+    'PH': the Hartley matrix H (real, orthonormal, H = H^{-1}): for a symmetric
+          PSF the circulant of the periodic conditions has real eigenvalues with
+          z(theta_k) = z(theta_{n-k}), so H diagonalises it as F^H does.
     """
     if family == "P":
         return dft_matrix(n).conj().T
+    if family == "PH":
+        return hartley_matrix(n)
     if family == "R":
         return dct2_matrix(n).T
     if family == "S3":                                   # reading R6
