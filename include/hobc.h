@@ -66,9 +66,16 @@ typedef enum {
     HOBC_FAMILY_SINE = 1,      /* antireflective, Sec. 2.2, Eq. (eq:ART), (eq:jcf)       */
     HOBC_FAMILY_COSINE = 2,    /* degree 2, symmetric PSF, Sec. 3.1, Eq. (eq:Tc), (eq:Ac) */
     HOBC_FAMILY_FOURIER = 3,   /* degree 2, any PSF, Sec. 3.2, Eq. (eq:Tf), (eq:Af)      */
-    HOBC_FAMILY_SINE_CUBIC = 4 /* degree 3, symmetric PSF: DST-I of order n-4 with four
+    HOBC_FAMILY_SINE_CUBIC = 4, /* degree 3, symmetric PSF: DST-I of order n-4 with four
                                   border columns spanning the cubics (the paper names
                                   degree 3 in Sec. 1 and Sec. 7 without a construction) */
+    HOBC_FAMILY_REFLECTIVE = 5, /* classical reflective conditions (Sec. 2, Eq. (eq:refm)):
+                                  T = C^T, the orthonormal DCT-II of order n, theta_k =
+                                  k pi / n; bc_degree 0, symmetric PSF, HOBC_SPLIT_BF16 only */
+    HOBC_FAMILY_PERIODIC = 6    /* classical periodic conditions (Sec. 2, Eq. (eq:permat)) in
+                                  the real Hartley basis (for a symmetric PSF it
+                                  diagonalises the circulant as F^H does), theta_k =
+                                  2 pi k / n; bc_degree 0, symmetric PSF, HOBC_SPLIT_BF16 only */
 } hobc_family;
 
 typedef enum {
@@ -95,7 +102,7 @@ typedef struct {
     int psf[2];                /* PSF mask size (odd): 1D psf[0] = 2m+1; 2D rows x cols;
                                   needs psf[i] <= n[i] - 2 (Sec. 2.2, Sec. 3), or
                                   psf[i] <= n[i] - 4 for SINE_CUBIC                       */
-    int bc_degree;             /* 1, 2 or 3                                                */
+    int bc_degree;             /* 1, 2 or 3 (0 with the REFLECTIVE / PERIODIC families)    */
     hobc_family family;
     int psf_symmetric;         /* caller asserts h_{-j} = h_j on every axis (used by AUTO) */
     hobc_smoothing L;

@@ -105,6 +105,8 @@ static cd expm_ipi(long long a, long long b) {
 // theta/pi of spectral index t as the fraction num/den (border columns: 0).
 static void theta_frac(int fam, int n, int t, long long& num, long long& den) {
     const int N = n - 2;
+    if (fam == hobc::FAM_R) { num = t; den = n; return; }          // comparison families: no border columns
+    if (fam == hobc::FAM_PH) { num = 2LL * t; den = n; return; }
     if (t == 0 || t == n - 1) { num = 0; den = 1; return; }
     if (fam == hobc::FAM_S3) {                     // N of the cubic family is n - 4
         if (t == 1 || t == n - 2) { num = 0; den = 1; }
@@ -207,8 +209,14 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half) {
     memset(&a, 0, sizeof(a));
     a.fam = fam;
     a.n = n;
-    a.N = fam == hobc::FAM_S3 ? n - 4 : n - 2;
     a.p = p;
+    cudaError_t err = cudaSuccess;
+    if (fam == hobc::FAM_R || fam == hobc::FAM_PH) {
+        // the classical comparison conditions run only in the dense mode: no
+        // FFT or border tables, only the grid and the eigen-exponential table
+        a.N = n; a.L = n; a.M = 8; a.log2M = 3; a.tpg = 1; a.H = n; a.W = n;
+    } else {
+    a.N = fam == hobc::FAM_S3 ? n - 4 : n - 2;
     const int N = a.N;
     a.L = (fam == hobc::FAM_S || fam == hobc::FAM_S3) ? 2 * (N + 1) : N;
     if (a.L >= 8 && (a.L & (a.L - 1)) == 0) {
@@ -225,7 +233,6 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half) {
     a.H = fam == hobc::FAM_F ? N / 2 + 1 : N;
     a.W = (fam == hobc::FAM_F && half) ? a.H + 2 : n;
 
-    cudaError_t err = cudaSuccess;
     std::vector<cd> tw(a.M);
     for (int k = 0; k < a.M; ++k) tw[k] = expm_ipi(2LL * k, a.M);
     a.tw = upload_complex<T>(tw, err);
@@ -283,6 +290,7 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half) {
     a.is0 = sqrt((double)N);
     a.is1 = sqrt(N / 2.0);
     a.invN = 1.0 / N;
+    }
     // eigen-exponential table E[t][j] = exp(-i (j - m) theta_t), plus a unit entry
     const int m = p / 2;
     std::vector<double> et(2 * ((size_t)a.W * p + 1));
@@ -379,6 +387,11 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
         if (d.prec != HOBC_FP64 && (mu_grid_host[j] < 1e-18 || mu_grid_host[j] > 1e18)) return HOBC_ERR_ARG;
     }
     int fam = d.family;
+    const bool comparison = fam == HOBC_FAMILY_REFLECTIVE || fam == HOBC_FAMILY_PERIODIC;
+    if (comparison) {
+        // classical conditions (Sec. 2): constants preserved, symmetric PSF, dense mode only
+        if (d.bc_degree != 0 || !d.psf_symmetric || d.prec != HOBC_SPLIT_BF16) return HOBC_ERR_UNSUPPORTED;
+    } else {
     if (d.bc_degree < 1 || d.bc_degree > 3) return HOBC_ERR_UNSUPPORTED;
     if (fam == HOBC_FAMILY_AUTO) {
         if (d.bc_degree == 1) fam = d.psf_symmetric ? HOBC_FAMILY_SINE : -1;
@@ -390,6 +403,7 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
     if ((fam == HOBC_FAMILY_COSINE || fam == HOBC_FAMILY_FOURIER) && d.bc_degree != 2) return HOBC_ERR_UNSUPPORTED;
     if (fam == HOBC_FAMILY_SINE_CUBIC && d.bc_degree != 3) return HOBC_ERR_UNSUPPORTED;
     if (fam < HOBC_FAMILY_SINE || fam > HOBC_FAMILY_SINE_CUBIC) return HOBC_ERR_ARG;
+    }
     if (d.prec == HOBC_SPLIT_BF16 && fam == HOBC_FAMILY_FOURIER) return HOBC_ERR_UNSUPPORTED;   // complex T_F
 
     hobc_plan_s* p = new hobc_plan_s;

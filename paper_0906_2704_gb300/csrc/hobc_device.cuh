@@ -17,7 +17,7 @@
 
 namespace hobc {
 
-enum { FAM_S = 1, FAM_C = 2, FAM_F = 3, FAM_S3 = 4 };   // same values as hobc_family
+enum { FAM_S = 1, FAM_C = 2, FAM_F = 3, FAM_S3 = 4, FAM_R = 5, FAM_PH = 6 };   // same values as hobc_family
 
 template <typename T> struct V2;
 template <> struct V2<float> { typedef float2 t; };
@@ -247,6 +247,8 @@ __device__ __forceinline__ T border_sum4(const Axis<T>& ax, const T* c, int a) {
 // border columns have angle 0.
 template <typename T>
 __device__ __forceinline__ T theta_over_pi(int fam, int n, int N, int t) {
+    if (fam == FAM_R) return (T)t / (T)n;                 // reflective (Eq. (eq:refm)): no border columns
+    if (fam == FAM_PH) return (T)(2 * t) / (T)n;          // periodic (Eq. (eq:permat))
     if (t == 0 || t == n - 1) return (T)0;
     if (fam == FAM_S3) return (t == 1 || t == n - 2) ? (T)0 : (T)(t - 1) / (T)(N + 1);
     if (fam == FAM_S) return (T)t / (T)(N + 1);

@@ -1204,7 +1204,7 @@ extern "C" {
 
 hobc_status hobc_features(hobc_plan* p, const void* ghat_dev, const void* d_dev, float* x_dev) {
     if (!p || !ghat_dev || !d_dev || !x_dev) return HOBC_ERR_ARG;
-    if (p->nax != 2) return HOBC_ERR_UNSUPPORTED;
+    if (p->nax != 2 || p->fam == HOBC_FAMILY_REFLECTIVE || p->fam == HOBC_FAMILY_PERIODIC) return HOBC_ERR_UNSUPPORTED;
     cudaError_t e = ensure_learned_ws(p);
     if (e != cudaSuccess) { set_last_error("hobc_features", e); return HOBC_ERR_CUDA; }
     p->launches = 0;
@@ -1215,7 +1215,8 @@ hobc_status hobc_features(hobc_plan* p, const void* ghat_dev, const void* d_dev,
 hobc_status hobc_deblur_learned(hobc_plan* p, hobc_mlp* q, const void* g_dev, const void* psf_dev, void* f_dev,
                                 double* mu_dev, int* fell_back_dev) {
     if (!p || !q || !g_dev || !psf_dev || !f_dev) return HOBC_ERR_ARG;
-    if (p->nax != 2 || q->nin != kFeat) return HOBC_ERR_UNSUPPORTED;
+    if (p->nax != 2 || q->nin != kFeat || p->fam == HOBC_FAMILY_REFLECTIVE || p->fam == HOBC_FAMILY_PERIODIC)
+        return HOBC_ERR_UNSUPPORTED;
     cudaError_t e = ensure_learned_ws(p);
     if (e != cudaSuccess) { set_last_error("hobc_deblur_learned", e); return HOBC_ERR_CUDA; }
     if (!p->grid_ascending) {

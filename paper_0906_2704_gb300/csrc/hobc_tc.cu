@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -529,6 +530,44 @@ hobc_status dense_prepare(hobc_plan_s* p) {
     }
     if (e != cudaSuccess) { set_last_error("hobc_plan_create (dense)", e); return HOBC_ERR_CUDA; }
     // build T and T^{-1}
+    if (p->fam == HOBC_FAMILY_REFLECTIVE || p->fam == HOBC_FAMILY_PERIODIC) {
+        // the classical conditions: orthonormal C (T^{-1} = C, T = C^T) or the
+        // symmetric Hartley matrix (T = T^{-1} = H), written straight from their definitions
+        for (int a = 0; a < p->nax; ++a) {
+            const int n = d->n[a];
+            std::vector<double> X((size_t)n * n);          // X[k][j]
+            for (int k = 0; k < n; ++k)
+                for (int j = 0; j < n; ++j) {
+                    if (p->fam == HOBC_FAMILY_REFLECTIVE) {
+                        const double sc = std::sqrt((k == 0 ? 1.0 : 2.0) / n);
+                        X[(size_t)k * n + j] = sc * std::cos(M_PI * k * (2.0 * j + 1.0) / (2.0 * n));
+                    } else {
+                        const long long r = (long long)k * j % n;
+                        const double ang = 2.0 * M_PI * (double)r / n;
+                        X[(size_t)k * n + j] = (std::cos(ang) + std::sin(ang)) / std::sqrt((double)n);
+                    }
+                }
+            double* dev = nullptr;
+            e = cudaMalloc((void**)&dev, X.size() * sizeof(double));
+            for (int inv = 1; inv >= 0 && e == cudaSuccess; --inv) {
+                // k_split_f64_t writes the transpose of what it reads: feed it the
+                // transpose of the wanted matrix (T^{-1} = X, T = X^T)
+                std::vector<double> src((size_t)n * n);
+                for (int r = 0; r < n; ++r)
+                    for (int c = 0; c < n; ++c)
+                        src[(size_t)c * n + r] = inv ? X[(size_t)r * n + c] : X[(size_t)c * n + r];
+                e = cudaMemcpy(dev, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) break;
+                const int slot = mi[a][inv];
+                tc::k_split_f64_t<<<256, 256, 0, p->stream>>>(dev, n, n, n, d->m_hi[slot], d->m_lo[slot],
+                                                               d->m_ld[slot]);
+                e = cudaStreamSynchronize(p->stream);
+            }
+            cudaFree(dev);
+            if (e != cudaSuccess) { set_last_error("hobc_plan_create (dense)", e); return HOBC_ERR_CUDA; }
+        }
+        return HOBC_OK;
+    }
     for (int a = 0; a < p->nax; ++a) {
         const int n = d->n[a];
         hobc_plan_desc q;

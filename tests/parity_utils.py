@@ -8,7 +8,7 @@ import numpy as np
 from oracle import hobc_oracle as O
 from paper_0906_2704_gb300 import synth
 
-FAM_LETTER = {"sine": "S", "cosine": "C", "fourier": "F", "sine3": "S3"}
+FAM_LETTER = {"sine": "S", "cosine": "C", "fourier": "F", "sine3": "S3", "reflective": "R", "periodic": "PH"}
 EPS32 = 2.0 ** -24
 
 

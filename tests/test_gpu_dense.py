@@ -26,7 +26,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 from paper_0906_2704_gb300 import hobc  # noqa: E402
 
-DEG = {"sine": 1, "cosine": 2, "sine3": 3}
+DEG = {"sine": 1, "cosine": 2, "sine3": 3, "reflective": 0, "periodic": 0}
 EPS = 2.0 ** -11
 
 
@@ -56,7 +56,7 @@ def _status(plan):
 
 
 @pytest.mark.parametrize("L", ["I", "lap"])
-@pytest.mark.parametrize("fam", ["sine", "cosine", "sine3"])
+@pytest.mark.parametrize("fam", ["sine", "cosine", "sine3", "reflective", "periodic"])
 @pytest.mark.parametrize("ndim,n,taps", [(1, 70, 5), (1, 130, 7), (2, (40, 52), (5, 5)), (2, (66, 34), (7, 7))])
 def test_dense_steps_match_oracle(ndim, n, taps, fam, L):
     F, n, h, g, mus, plan = _case(ndim, fam, n, taps, L)
@@ -82,7 +82,7 @@ def test_dense_steps_match_oracle(ndim, n, taps, fam, L):
         assert np.all(np.abs(y[b] - yref) <= ybound), f"synthesis item {b}"
 
 
-@pytest.mark.parametrize("fam", ["sine", "cosine", "sine3"])
+@pytest.mark.parametrize("fam", ["sine", "cosine", "sine3", "reflective", "periodic"])
 @pytest.mark.parametrize("ndim,n,taps", [(1, 90, 5), (2, (48, 40), (5, 5))])
 def test_dense_deblur_matches_oracle(ndim, n, taps, fam):
     F, n, h, g, mus, plan = _case(ndim, fam, n, taps, "lap", batch=4, K=32, seed=3)
@@ -119,6 +119,16 @@ def test_dense_host_call_equals_device_call(ndim, n, taps):
     plan.deblur(_dev(g), _dev(h), f_d, mi_d)
     _status(plan)
     assert np.array_equal(f_h, f_d.cpu().numpy()) and np.array_equal(mi_h, mi_d.cpu().numpy())
+
+
+def test_comparison_families_need_the_dense_mode_and_degree_zero():
+    for prec in ("fp32", "fp64"):
+        with pytest.raises(hobc.HobcError):
+            hobc.Plan(2, (32, 32), (5, 5), 0, synth.mu_grid(8), prec=prec, family="reflective", psf_symmetric=True)
+    with pytest.raises(hobc.HobcError):
+        hobc.Plan(2, (32, 32), (5, 5), 2, synth.mu_grid(8), prec="split_bf16", family="periodic", psf_symmetric=True)
+    with pytest.raises(hobc.HobcError):
+        hobc.Plan(2, (32, 32), (5, 5), 0, synth.mu_grid(8), prec="split_bf16", family="periodic")
 
 
 def test_dense_mode_rejects_the_fourier_family():
