@@ -753,6 +753,132 @@ k_gcv_partials(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typena
                                smem_raw);
 }
 
+// ---------------------------------------------------------------------
+// GCV for many small problems (1D plans): a group of TPI adjacent threads owns
+// one problem and each of its threads PER grid values (8 in FP32, 4 in FP64);
+// the problem's entries pass through shared memory in tiles (32 KB per CTA), every
+// thread sweeps all of them for its values, so the sums need no cross-thread
+// reduction: G(mu_j) = num/den^2 and the first minimiser (NaN never wins)
+// come out of the same kernel.  FP32 per-thread sums are folded into FP64
+// every 256 entries.  grid = ceil(items / (256 / TPI)), block = 256.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ void eval_group(const float4 v, const float2 (&mA)[2], const float2 (&mB)[2],
+                                           float2 (&NA)[2], float2 (&NB)[2], float2 (&DA)[2], float2 (&DB)[2]) {
+    const float2 aa = make_float2(v.x, v.x), ee = make_float2(v.y, v.y), ww = make_float2(v.z, v.z);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float2 A = __fadd2_rn(aa, mA[h]);
+        const float2 B = __fadd2_rn(aa, mB[h]);
+        const float2 P = __fmul2_rn(A, B);
+        const float2 R = make_float2(pair_rcp(P.x), pair_rcp(P.y));
+        const float2 SA = __fmul2_rn(B, R);
+        const float2 SB = __fmul2_rn(A, R);
+        DA[h] = __ffma2_rn(ww, SA, DA[h]);
+        DB[h] = __ffma2_rn(ww, SB, DB[h]);
+        NA[h] = __ffma2_rn(__fmul2_rn(ee, SA), SA, NA[h]);
+        NB[h] = __ffma2_rn(__fmul2_rn(ee, SB), SB, NB[h]);
+    }
+}
+
+template <typename T, bool CPLX, int TPI>
+__global__ void __launch_bounds__(256)
+k_gcv_items(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
+            long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo, int items,
+            double* __restrict__ gcv, int* __restrict__ mu_idx) {
+    typedef typename Pack4<T>::t P4;
+    constexpr int IPC = 256 / TPI;                       // problems per CTA
+    constexpr int PER = sizeof(T) == 4 ? 8 : 4;          // grid values per thread
+    constexpr int GT_RAW = 32768 / (IPC * (int)sizeof(P4));
+    constexpr int GT_TILE = GT_RAW > 32 ? 32 : GT_RAW;   // entries per problem and tile
+    __shared__ P4 tile[IPC][GT_TILE];
+    const int slot = threadIdx.x / TPI, sub = threadIdx.x % TPI;
+    const long long item0 = (long long)blockIdx.x * IPC;
+    const long long item = item0 + slot;
+    const int K = geo.K;
+    const int j0 = sub * PER;
+    T mu[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) mu[u] = j0 + u < K ? muT[j0 + u] : (T)1;
+    double nd[PER], dd[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) { nd[u] = 0; dd[u] = 0; }
+    // FP32: packed lanes as in the grid scan; FP64: pairs sharing one reciprocal
+    float2 NA[2] = {}, NB[2] = {}, DA[2] = {}, DB[2] = {};
+    float2 mA[2], mB[2];
+    if constexpr (sizeof(T) == 4) {
+        mA[0] = make_float2((float)mu[0], (float)mu[2]); mA[1] = make_float2((float)mu[4], (float)mu[6]);
+        mB[0] = make_float2((float)mu[1], (float)mu[3]); mB[1] = make_float2((float)mu[5], (float)mu[7]);
+    }
+    int since_fold = 0;
+    for (long long e0 = 0; e0 < geo.S; e0 += GT_TILE) {
+        const int cnt = (int)min((long long)GT_TILE, geo.S - e0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < IPC * GT_TILE; i += blockDim.x) {
+            const int it = i / GT_TILE, k = i - it * GT_TILE;
+            const long long itm = item0 + it;
+            P4 v;
+            v.x = (T)1; v.y = (T)0; v.z = (T)0; v.w = (T)0;
+            if (itm < items && k < cnt)
+                v = gcv_term<T, CPLX>(spec[itm * geo.S + e0 + k], D[(psf_per ? itm : 0) * d_psf_stride + e0 + k], geo,
+                                      e0 + k);
+            tile[it][k] = v;
+        }
+        __syncthreads();
+        if (item < items) {
+            if constexpr (sizeof(T) == 4) {
+#pragma unroll 4
+                for (int k = 0; k < cnt; ++k) eval_group(tile[slot][k], mA, mB, NA, NB, DA, DB);
+                since_fold += cnt;
+                if (since_fold >= 256 || e0 + GT_TILE >= geo.S) {        // fold into FP64
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        nd[4 * h + 0] += NA[h].x; nd[4 * h + 2] += NA[h].y;
+                        nd[4 * h + 1] += NB[h].x; nd[4 * h + 3] += NB[h].y;
+                        dd[4 * h + 0] += DA[h].x; dd[4 * h + 2] += DA[h].y;
+                        dd[4 * h + 1] += DB[h].x; dd[4 * h + 3] += DB[h].y;
+                        NA[h] = make_float2(0.f, 0.f); NB[h] = NA[h]; DA[h] = NA[h]; DB[h] = NA[h];
+                    }
+                    since_fold = 0;
+                }
+            } else {
+                for (int k = 0; k < cnt; ++k) {
+                    const P4 v = tile[slot][k];
+#pragma unroll
+                    for (int u = 0; u < PER; u += 2) {
+                        const double t1 = v.x + mu[u], t2 = v.x + mu[u + 1];
+                        const double r = 1.0 / (t1 * t2);
+                        const double s1 = t2 * r, s2 = t1 * r;
+                        dd[u] += v.z * s1;
+                        dd[u + 1] += v.z * s2;
+                        nd[u] += v.y * s1 * s1;
+                        nd[u + 1] += v.y * s2 * s2;
+                    }
+                }
+            }
+        }
+    }
+    // G at this thread's grid values, then the first minimiser across the problem's threads
+    double best = INFINITY;
+    int bi = 0x7fffffff;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = j0 + u;
+        if (item < items && j < K) {
+            const double Gv = nd[u] / (dd[u] * dd[u]);
+            if (gcv) gcv[item * K + j] = Gv;
+            const double key = isnan(Gv) ? INFINITY : Gv;
+            if (key < best) { best = key; bi = j; }
+        }
+    }
+#pragma unroll
+    for (int off = TPI / 2; off > 0; off >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, off, TPI);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off, TPI);
+        if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (sub == 0 && item < items) mu_idx[item] = bi == 0x7fffffff ? 0 : bi;
+}
+
 // Sum over the chunks of one problem of the per-CTA partial sums of grid value
 // j (numerator at j, denominator at K + j of each chunk's 2K block), in chunk
 // order.  (Splitting it into four interleaved accumulators measured slower.)

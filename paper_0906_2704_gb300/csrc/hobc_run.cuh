@@ -251,6 +251,31 @@ hobc_status run_gcv(hobc_plan_s* p, const void* ghat, const void* D, double* gcv
     geo.S = (long long)p->spec_elems;
     geo.chunk = p->gcv_chunk;
     geo.K = p->K;
+    if (p->nax == 1) {
+        // many small spectra: one thread group per problem, no partial sums
+        const int per = sizeof(T) == 4 ? 8 : 4;
+        int tpi = 1;
+        while (tpi * per < p->K) tpi *= 2;
+        if (tpi <= 32) {
+            const int B = p->desc.batch;
+            const unsigned grid = (unsigned)((B + 256 / tpi - 1) / (256 / tpi));
+            typedef typename ElemT<T, true>::t CT;
+#define HOBC_ITEMS(TPI_)                                                                                   \
+    if (tpi == TPI_) {                                                                                     \
+        if (p->fam == FAM_F)                                                                               \
+            k_gcv_items<T, true, TPI_><<<grid, 256, 0, p->stream>>>(                                        \
+                reinterpret_cast<const CT*>(ghat), reinterpret_cast<const CT*>(D), (long long)p->spec_elems, \
+                p->desc.psf_per_item, reinterpret_cast<const T*>(p->muT), geo, B, gcv, mu_idx);            \
+        else                                                                                               \
+            k_gcv_items<T, false, TPI_><<<grid, 256, 0, p->stream>>>(                                       \
+                reinterpret_cast<const T*>(ghat), reinterpret_cast<const T*>(D), (long long)p->spec_elems,  \
+                p->desc.psf_per_item, reinterpret_cast<const T*>(p->muT), geo, B, gcv, mu_idx);            \
+    }
+            HOBC_ITEMS(1) HOBC_ITEMS(2) HOBC_ITEMS(4) HOBC_ITEMS(8) HOBC_ITEMS(16) HOBC_ITEMS(32)
+#undef HOBC_ITEMS
+            return check_launch(p, "k_gcv_items");
+        }
+    }
     dim3 grid((unsigned)(p->gcv_chunks * (long long)p->desc.batch));
     const size_t smem = 4 * (size_t)p->gcv_chunk * sizeof(T);
     if (p->fam == FAM_F)
