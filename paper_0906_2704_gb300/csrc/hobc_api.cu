@@ -95,7 +95,7 @@ static void fft_host(std::vector<cd>& a) {   // in-place radix-2, exp(-i ...)
 }
 
 // exp(-i pi a/b) with the argument reduced exactly (a may be negative).
-static cd expm_ipi(long long a, long long b) {
+cd expm_ipi(long long a, long long b) {
     long long r = a % (2 * b);
     if (r < 0) r += 2 * b;
     const double ang = M_PI * (double)r / (double)b;
@@ -103,7 +103,7 @@ static cd expm_ipi(long long a, long long b) {
 }
 
 // theta/pi of spectral index t as the fraction num/den (border columns: 0).
-static void theta_frac(int fam, int n, int t, long long& num, long long& den) {
+void theta_frac(int fam, int n, int t, long long& num, long long& den) {
     const int N = n - 2;
     if (fam == hobc::FAM_R) { num = t; den = n; return; }          // comparison families: no border columns
     if (fam == hobc::FAM_PH) { num = 2LL * t; den = n; return; }

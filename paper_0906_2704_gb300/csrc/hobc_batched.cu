@@ -35,6 +35,7 @@ struct ItemDev {            // per-problem geometry on the device
     int n0, n1, p0, p1, fam;
     int N0, N1;
     long long img_off, psf_off;
+    long long cos0, cos1;   // cosine tables of the two axes: cos(k theta_t) at base + k n + t
 };
 
 struct GcvItem {
@@ -87,36 +88,33 @@ kb_pair_synthesis(const LineWork* __restrict__ work, const Axis<T>* __restrict__
 }
 
 // Eigenvalues of a symmetric PSF on the real families: d = sum h cos(j0 th0) cos(j1 th1)
-// (Eq. (eq:symbol) at -theta, Sec. 6), partial sums over j1 per column, then a
-// cosine recurrence over j0; FP64.  One CTA per (problem, column).
+// (Eq. (eq:symbol) at -theta, Sec. 6): partial sums over j1 for the column,
+// then the sum over j0 for every entry, tap offsets +-k folded; the cosines
+// cos(k theta_t) come from per-axis tables built on the host with the
+// argument reduced exactly; FP64 sums.  One CTA per (problem, column).
 template <typename T>
 __global__ void __launch_bounds__(256)
 kb_eig(const int2* __restrict__ work, const ItemDev* __restrict__ items, const BatchIO* __restrict__ io,
-       T* __restrict__ D) {
+       const double* __restrict__ costab, T* __restrict__ D) {
     __shared__ double P[64];
     const int2 w = work[blockIdx.x];
     const ItemDev it = items[w.x];
     const int c = w.y;
     const T* h = reinterpret_cast<const T*>(io->psf) + it.psf_off;
     const int m0 = it.p0 / 2, m1 = it.p1 / 2;
-    const double f1 = (double)theta_over_pi<double>(it.fam, it.n1, it.N1, c);
+    const double* c1t = costab + it.cos1 + c;             // cos(k theta_c) at c1t[k n1]
     for (int j0 = threadIdx.x; j0 < it.p0; j0 += blockDim.x) {
-        double acc = 0;
-        for (int j1 = 0; j1 < it.p1; ++j1) acc += (double)h[j0 * it.p1 + j1] * cospi((double)(j1 - m1) * f1);
+        const T* hr = h + j0 * it.p1;
+        double acc = (double)hr[m1];
+        for (int k = 1; k <= m1; ++k) acc += ((double)hr[m1 + k] + (double)hr[m1 - k]) * c1t[(long long)k * it.n1];
         P[j0] = acc;
     }
     __syncthreads();
     T* o = D + it.img_off + (long long)c * it.n0;
+    const double* c0t = costab + it.cos0;
     for (int t0 = threadIdx.x; t0 < it.n0; t0 += blockDim.x) {
-        const double c1 = cospi((double)theta_over_pi<double>(it.fam, it.n0, it.N0, t0));
         double acc = P[m0];
-        double ck = 1.0, cprev = c1;          // cos(0), cos(-th)
-        for (int k = 1; k <= m0; ++k) {
-            const double cn = 2.0 * c1 * ck - cprev;   // cos(k th) = 2 cos(th) cos((k-1) th) - cos((k-2) th)
-            cprev = ck;
-            ck = cn;
-            acc += (P[m0 + k] + P[m0 - k]) * ck;
-        }
+        for (int k = 1; k <= m0; ++k) acc += (P[m0 + k] + P[m0 - k]) * c0t[(long long)k * it.n0 + t0];
         o[t0] = (T)acc;
     }
 }
@@ -202,6 +200,7 @@ struct hobc_batch_s {
     int* mu_idx_ws;
     double* gcv_ws;
     BatchIO* io_dev;
+    double* costab;          // per-axis tables cos(k theta_t), k <= the largest PSF half-width
     cudaGraphExec_t graph;
     int launches;
 };
@@ -221,7 +220,7 @@ hobc_status launch_all(hobc_batch_s* b) {
     T* G = reinterpret_cast<T*>(b->G);
     T* D = reinterpret_cast<T*>(b->D);
     int launches = 0;
-    if (b->eig_count) { kb_eig<T><<<b->eig_count, 256, 0, st>>>(b->eig_work, b->items_dev, io, D); ++launches; }
+    if (b->eig_count) { kb_eig<T><<<b->eig_count, 256, 0, st>>>(b->eig_work, b->items_dev, io, b->costab, D); ++launches; }
     for (const PassList& l : b->rowA) {
         if (!l.count) continue;
         if (l.fam == FAM_S) kb_pair_analysis<T, FAM_S><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, nullptr, 1, io, R);
@@ -325,6 +324,7 @@ extern "C" void hobc_batch_destroy(hobc_batch* b) {
     for (auto* lists : {&b->rowA, &b->colA, &b->colS, &b->rowS})
         for (PassList& l : *lists) cudaFree(l.dev);
     cudaFree(b->axes_dev); cudaFree(b->items_dev); cudaFree(b->gcv_items_dev); cudaFree(b->gcv_work);
+    cudaFree(b->costab);
     cudaFree(b->eig_work); cudaFree(b->mu); cudaFree(b->muT); cudaFree(b->R); cudaFree(b->G); cudaFree(b->D);
     cudaFree(b->partials); cudaFree(b->mu_idx_ws); cudaFree(b->gcv_ws); cudaFree(b->io_dev);
     delete b;
@@ -397,6 +397,31 @@ extern "C" hobc_status hobc_batch_create(const hobc_batch_desc* desc, const hobc
         x.N1 = fam == FAM_S3 ? x.n1 - 4 : x.n1 - 2;
         x.img_off = (long long)b->img_off[i];
         x.psf_off = (long long)b->psf_off[i];
+    }
+    // cosine tables of every distinct axis: cos(k theta_t) for k <= the largest half-width
+    {
+        int kc = 1;
+        for (int i = 0; i < d.count; ++i) kc = std::max(kc, std::max(items[i].psf[0], items[i].psf[1]) / 2 + 1);
+        std::vector<long long> base(b->axes_host.size());
+        long long total_cos = 0;
+        for (size_t a = 0; a < b->axes_host.size(); ++a) {
+            base[a] = total_cos;
+            total_cos += (long long)kc * b->axes_host[a].n;
+        }
+        std::vector<double> tab((size_t)total_cos);
+        for (size_t a = 0; a < b->axes_host.size(); ++a) {
+            const AxisHost& ah = b->axes_host[a];
+            for (int t = 0; t < ah.n; ++t) {
+                long long num, den;
+                theta_frac(ah.fam, ah.n, t, num, den);
+                for (int k = 0; k < kc; ++k) tab[(size_t)(base[a] + (long long)k * ah.n + t)] = expm_ipi(k * num, den).real();
+            }
+        }
+        for (int i = 0; i < d.count; ++i) {
+            idev[i].cos0 = base[ax0[i]];
+            idev[i].cos1 = base[ax1[i]];
+        }
+        b->costab = reinterpret_cast<double*>(upload(tab, err));
     }
     if (err == cudaSuccess) {
         if (d.prec == HOBC_FP64) {

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <complex>
+
 #include "../../include/hobc.h"
 
 namespace hobc {
@@ -105,6 +107,10 @@ hobc_status dense_filter_synthesis(hobc_plan_s* p, const void* ghat, const void*
                                    const double* mu_val, void* f);
 
 template <typename T> cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half);
+// exp(-i pi a / b) with the argument reduced exactly; theta_t / pi of spectral
+// index t of a family's axis as the fraction num / den (hobc_api.cu)
+std::complex<double> expm_ipi(long long a, long long b);
+void theta_frac(int fam, int n, int t, long long& num, long long& den);
 void set_last_error(const char* what, cudaError_t e);
 void set_last_error_text(const char* text);
 hobc_status launch_gcv_finalize(hobc_plan_s* p, double* gcv, int* mu_idx);
