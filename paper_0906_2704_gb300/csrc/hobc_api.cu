@@ -8,6 +8,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "hobc_internal.h"
 #include "hobc_device.cuh"
 #include "hobc_kernels.cuh"
@@ -27,42 +29,96 @@ void set_last_error_text(const char* text) { snprintf(g_last_error, sizeof(g_las
 
 // ------------------------------------------------------------- GCV finalize
 
-__global__ void k_gcv_finalize(const double* __restrict__ partials, int nchunks, int K, double* __restrict__ gcv,
-                               int* __restrict__ mu_idx) {
-    __shared__ double sv[256];
-    __shared__ int si[256];
-    const long long item = blockIdx.x;
+// One cluster of nblk CTAs per problem.  A CTA owns the grid values
+// j = rank*32 + lane (+ nblk*32 per further stripe); its 8 warps sum the chunk
+// partials c = warp, warp + 8, ... of those values in double, the 8 slice sums
+// are added in slice order, and G = num / den^2 is formed.  Each CTA keeps its
+// first minimum (NaN never wins) in shared memory, and rank 0 combines the
+// cluster's minima through distributed shared memory.  The order of every sum
+// is fixed, so results do not depend on scheduling.
+constexpr int kFinJ = 32, kFinSlices = 8, kFinMaxCluster = 8;
+
+__global__ void __launch_bounds__(kFinJ * kFinSlices)
+k_gcv_finalize(const double* __restrict__ partials, int nchunks, int K, double* __restrict__ gcv,
+               int* __restrict__ mu_idx) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int nblk = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    __shared__ double sn[kFinSlices][kFinJ], sd[kFinSlices][kFinJ];
+    __shared__ double best_v;
+    __shared__ int best_i;
+    const long long item = blockIdx.x / nblk;
     const double* p = partials + item * (long long)nchunks * 2 * K;
+    const int lane = threadIdx.x % kFinJ, slice = threadIdx.x / kFinJ;
     double best = INFINITY;
     int bi = 0x7fffffff;
-    for (int j = threadIdx.x; j < K; j += blockDim.x) {
-        double num, den;
-        sum_chunks(p, nchunks, K, j, num, den);
-        const double G = num / (den * den);
-        if (gcv) gcv[item * K + j] = G;
-        const double key = isnan(G) ? INFINITY : G;
-        if (key < best || (key == best && j < bi)) { best = key; bi = j; }
-    }
-    sv[threadIdx.x] = best;
-    si[threadIdx.x] = bi;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) {
-            const double v2 = sv[threadIdx.x + s];
-            const int i2 = si[threadIdx.x + s];
-            if (v2 < sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
-                sv[threadIdx.x] = v2;
-                si[threadIdx.x] = i2;
+    for (int jb = rank * kFinJ; jb < K; jb += nblk * kFinJ) {
+        const int j = jb + lane;
+        double num = 0, den = 0;
+        if (j < K)
+            for (int c = slice; c < nchunks; c += kFinSlices) {
+                num += p[(long long)c * 2 * K + j];
+                den += p[(long long)c * 2 * K + K + j];
             }
+        sn[slice][lane] = num;
+        sd[slice][lane] = den;
+        __syncthreads();
+        if (slice == 0 && j < K) {
+            num = 0;
+            den = 0;
+#pragma unroll
+            for (int s = 0; s < kFinSlices; ++s) { num += sn[s][lane]; den += sd[s][lane]; }
+            const double G = num / (den * den);
+            if (gcv) gcv[item * K + j] = G;
+            const double key = isnan(G) ? INFINITY : G;
+            if (key < best || (key == best && j < bi)) { best = key; bi = j; }
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) mu_idx[item] = si[0] == 0x7fffffff ? 0 : si[0];
+    if (slice == 0) {
+        for (int off = 16; off > 0; off >>= 1) {
+            const double v2 = __shfl_down_sync(0xffffffffu, best, off);
+            const int i2 = __shfl_down_sync(0xffffffffu, bi, off);
+            if (v2 < best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+        }
+        if (lane == 0) { best_v = best; best_i = bi; }
+    }
+    cluster.sync();
+    if (rank == 0 && threadIdx.x == 0) {
+        double v = INFINITY;
+        int i = 0x7fffffff;
+        for (int r = 0; r < nblk; ++r) {
+            const double v2 = *cluster.map_shared_rank(&best_v, r);
+            const int i2 = *cluster.map_shared_rank(&best_i, r);
+            if (v2 < v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+        }
+        mu_idx[item] = i == 0x7fffffff ? 0 : i;
+    }
+    cluster.sync();      // the other CTAs' shared memory stays valid until rank 0 has read it
+}
+
+cudaError_t launch_gcv_finalize_raw(const double* partials, int nchunks, int K, int batch, double* gcv,
+                                    int* mu_idx, cudaStream_t st) {
+    const int nblk = std::min(kFinMaxCluster, (K + kFinJ - 1) / kFinJ);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((long long)batch * nblk));
+    cfg.blockDim = dim3(kFinJ * kFinSlices);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)nblk;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_gcv_finalize, partials, nchunks, K, gcv, mu_idx);
 }
 
 hobc_status launch_gcv_finalize(hobc_plan_s* p, double* gcv, int* mu_idx) {
-    k_gcv_finalize<<<p->desc.batch, 256, 0, p->stream>>>(p->partials, p->gcv_chunks, p->K, gcv, mu_idx);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_gcv_finalize_raw(p->partials, p->gcv_chunks, p->K, p->desc.batch, gcv, mu_idx, p->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_last_error("k_gcv_finalize", e);
         return HOBC_ERR_CUDA;

@@ -114,5 +114,9 @@ void theta_frac(int fam, int n, int t, long long& num, long long& den);
 void set_last_error(const char* what, cudaError_t e);
 void set_last_error_text(const char* text);
 hobc_status launch_gcv_finalize(hobc_plan_s* p, double* gcv, int* mu_idx);
+// G(mu_j) and the grid argmin of each problem from its chunk partials: one
+// cluster of up to 8 CTAs per problem (hobc_api.cu)
+cudaError_t launch_gcv_finalize_raw(const double* partials, int nchunks, int K, int batch, double* gcv,
+                                    int* mu_idx, cudaStream_t st);
 
 }  // namespace hobc

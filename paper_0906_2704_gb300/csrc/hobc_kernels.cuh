@@ -635,8 +635,11 @@ __device__ __forceinline__ void gcv_scan(const double4* __restrict__ pk, int cnt
 // (mu0, mu2) / (mu1, mu3) and (mu4, mu6) / (mu5, mu7), so one packed product
 // forms both shared denominators of a pair of pairs and each packed op
 // advances two evaluations; one rcp.approx per two evaluations.  A thread's
-// terms (at most 256 elements, see gcv_chunk_for) are summed in float, then
-// combined across threads in double.
+// terms (at most 256 elements, see gcv_chunk_for) are summed in float and the
+// tpm threads of a group (at most 32) combined in float by a shuffle tree, at
+// most 256 + 5 roundings per sum; each grid value's CTA sum is then converted
+// to double once (FP64 runs at a small fraction of the FP32 rate on this part,
+// so the combine stays off the FP64 pipe).
 __device__ __forceinline__ void gcv_scan(const float4* __restrict__ pk, int cnt, const float* __restrict__ muT,
                                          int K, double* __restrict__ outp) {
     const int NO = (K + 7) / 8;
@@ -670,24 +673,24 @@ __device__ __forceinline__ void gcv_scan(const float4* __restrict__ pk, int cnt,
                 NB[h] = __ffma2_rn(__fmul2_rn(ee, SB), SB, NB[h]);
             }
         }
-        double nd[8], dd[8];
+        float nf[8], df[8];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            nd[4 * h + 0] = NA[h].x; nd[4 * h + 2] = NA[h].y;
-            nd[4 * h + 1] = NB[h].x; nd[4 * h + 3] = NB[h].y;
-            dd[4 * h + 0] = DA[h].x; dd[4 * h + 2] = DA[h].y;
-            dd[4 * h + 1] = DB[h].x; dd[4 * h + 3] = DB[h].y;
+            nf[4 * h + 0] = NA[h].x; nf[4 * h + 2] = NA[h].y;
+            nf[4 * h + 1] = NB[h].x; nf[4 * h + 3] = NB[h].y;
+            df[4 * h + 0] = DA[h].x; df[4 * h + 2] = DA[h].y;
+            df[4 * h + 1] = DB[h].x; df[4 * h + 3] = DB[h].y;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u)
             for (int off = tpm / 2; off > 0; off >>= 1) {
-                nd[u] += __shfl_down_sync(0xffffffffu, nd[u], off, tpm);
-                dd[u] += __shfl_down_sync(0xffffffffu, dd[u], off, tpm);
+                nf[u] += __shfl_down_sync(0xffffffffu, nf[u], off, tpm);
+                df[u] += __shfl_down_sync(0xffffffffu, df[u], off, tpm);
             }
         if (sub == 0)
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-                if (j0 + u < K) { outp[j0 + u] = nd[u]; outp[K + j0 + u] = dd[u]; }
+                if (j0 + u < K) { outp[j0 + u] = (double)nf[u]; outp[K + j0 + u] = (double)df[u]; }
     }
 }
 
@@ -893,7 +896,7 @@ __device__ __forceinline__ void sum_chunks(const double* __restrict__ p, int nch
 }
 
 // G(mu_j) = num_j / den_j^2 and the first index of the minimum (NaN never wins).
-// grid = items, block = 256.
+// Launched as one thread-block cluster per problem (launch_gcv_finalize_raw).
 __global__ void k_gcv_finalize(const double* __restrict__ partials, int nchunks, int K,
                                double* __restrict__ gcv, int* __restrict__ mu_idx);
 

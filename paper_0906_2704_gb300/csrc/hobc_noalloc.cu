@@ -65,8 +65,8 @@ hobc_status launch(const hobc::GcvGeom& geo, int cplx, int batch, int chunks, co
         k_gcv_partials<T, false><<<grid, 256, smem, st>>>(reinterpret_cast<const T*>(ghat),
                                                            reinterpret_cast<const T*>(d), d_psf_stride, psf_per,
                                                            muT, geo, partials);
-    k_gcv_finalize<<<batch, 256, 0, st>>>(partials, chunks, geo.K, gcv, mu_idx);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_gcv_finalize_raw(partials, chunks, geo.K, batch, gcv, mu_idx, st);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) { set_last_error("hobc_gcv_noalloc launch", e); return HOBC_ERR_CUDA; }
     return HOBC_OK;
 }
