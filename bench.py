@@ -287,8 +287,29 @@ def run_ours(args):
         d = (f.cpu().numpy().astype(np.float64) - ft).reshape(B, -1)
         return np.linalg.norm(d, axis=1) / np.linalg.norm(ft.reshape(B, -1), axis=1)
 
+    # the grid argmin refined over continuous mu (5 rounds of 9 points in its bracket)
+    f_r = torch.empty_like(g_d)
+    mi_r = torch.empty(B, dtype=torch.int32, device=dev)
+    mu_r = torch.empty(B, dtype=torch.float64, device=dev)
+    ms_r, clk_r = _timed(lambda: plan.deblur_refined(g_d, h_d, f_r, mi_r, mu_r), stream, args.steps, args.warmup)
+    refined_launches = plan.last_launch_count
+    ms_r = max_over_ranks(ms_r, dist, dev)
+    G_grid = torch.empty((B, K_MU), dtype=torch.float64, device=dev)
+    G_ref = torch.empty(B, dtype=torch.float64, device=dev)
+    plan.gcv(ghat, dbuf, G_grid, mi_d)
+    plan.gcv_refine(ghat, dbuf, mi_d, mu_r, G_ref)
+    g_min = G_grid.min(dim=1).values
+
     plan.deblur(g_d, h_d, f_d, mi_d, None)
     r_full, r_bin = rre(f_d), rre(f_b)
+    r_ref = rre(f_r)
+    refined = {"value": whole_job_rate(world, B, args.steps, ms_r / 1e3), "unit": "deblurs/s",
+               "ms_per_step": ms_r / args.steps, "gpu_launches": refined_launches * args.steps,
+               "G_ratio_to_grid_min": {"mean": float((G_ref / g_min).mean()), "max": float((G_ref / g_min).max())},
+               "mu_ratio_to_grid": {"min": float((mu_r / torch.from_numpy(mus).to(dev)[mi_d.long()]).min()),
+                                    "max": float((mu_r / torch.from_numpy(mus).to(dev)[mi_d.long()]).max())},
+               "rre_mean": {"full_scan": float(r_full.mean()), "refined": float(r_ref.mean())},
+               "clocks": clk_r}
     binned = {"value": whole_job_rate(world, B, args.steps, ms_b / 1e3), "unit": "deblurs/s",
               "ms_per_step": ms_b / args.steps, "gpu_launches": binned_launches * args.steps,
               "fallback_rate": float(fb_b.float().mean()),
@@ -355,7 +376,7 @@ def run_ours(args):
                        "l2": "inputs+outputs %.0f MB per step > 129 MB L2 (no flush)" % (2 * B * N_SIDE ** 2 * esz / 1e6)},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
             "hbm_roofline": hbm, "steps_ms": steps_ms, "cpu_baseline": cpu, "clocks": clocks,
-            "binned_mu": binned,
+            "binned_mu": binned, "refined_mu": refined,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

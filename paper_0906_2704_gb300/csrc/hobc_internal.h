@@ -79,6 +79,7 @@ struct hobc_plan_s {
     double* ahist_partials;  // [batch][chunks][3][128] histogram over log10 a of the binned choice
     void* a_edges;           // [129] bin edges, plan precision
     int* k_hat;              // [batch] argmin of the binned G
+    double* refine_state;    // [batch][4] lo, mid, hi (log10 mu) and the incumbent mu of the refinement
     cudaStream_t aux[2];     // host-buffer pipeline streams (created on first use)
     cudaEvent_t aux_ev;
     int grid_ascending;      // 1 if the mu grid is strictly increasing

@@ -702,8 +702,12 @@ __device__ __forceinline__ typename Pack4<T>::t gcv_term(const typename ElemT<T,
                                                          const typename ElemT<T, CPLX>::t& dpv, const GcvGeom& geo,
                                                          long long e) {
     int c, t0 = 0;
-    if (geo.ndim == 2) { c = (int)(e / geo.n0); t0 = (int)(e - (long long)c * geo.n0); }
-    else c = (int)e;
+    if (geo.ndim == 2) {             // e < S <= 1024 x 1024: 32-bit division
+        c = (int)((unsigned)e / (unsigned)geo.n0);
+        t0 = (int)e - c * geo.n0;
+    } else {
+        c = (int)e;
+    }
     T w = 1;
     if (CPLX) {
         const bool self = (c == 0 || c == geo.W1 - 1 || c == 1 || 2 * (c - 1) == geo.N1);

@@ -6,6 +6,8 @@
 // minimum sits on its edge.  Everything runs in the kernels below: features,
 // the network's forward and backward passes (tiled FP32-accumulating GEMMs
 // with BF16 weights), AdamW, the bracket scan and the masked full scan.
+// The same bracket scan serves the binned choice of mu (include/hobc_binned.h)
+// and the continuous refinement of mu* (include/hobc_refine.h).
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -16,6 +18,7 @@
 
 #include "../../include/hobc_binned.h"
 #include "../../include/hobc_learned.h"
+#include "../../include/hobc_refine.h"
 #include "hobc_internal.h"
 #include "hobc_kernels.cuh"
 
@@ -25,7 +28,8 @@ constexpr int kBins = 64;            // radial bins per spectrum
 constexpr int kFeat = 2 * kBins;     // network inputs
 static_assert(kBins == 64, "k_features gives each lane of a warp two bins");
 constexpr int kJ = 10;               // bracket width: mu_hat and up to 9 grid values
-constexpr int kBracketChunk = 16384; // spectral entries per bracket-scan CTA
+constexpr int kBracketChunk = 4096;  // spectral entries per bracket-scan CTA
+constexpr int kBracketU = 4;         // entries per thread whose loads are issued together
 
 // ------------------------------------------------------------ features
 
@@ -372,7 +376,8 @@ __global__ void k_bracket_decide(const double* __restrict__ Gb, int J, const int
 
 // G's sums at the kJ bracket values of every problem: each thread takes its
 // elements' terms once and accumulates all kJ values (reciprocals shared by
-// pairs, as in the grid scan); sums per thread in T, across threads in double.
+// pairs, as in the grid scan); sums per thread and per warp in T, across
+// warps in double.
 // grid = items x ceil(S / kBracketChunk), block = 256; partials [CTA][2 kJ].
 template <typename T, bool CPLX>
 __global__ void __launch_bounds__(256)
@@ -390,28 +395,45 @@ k_gcv_bracket(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typenam
     T mu[kJ], nd[kJ], dd[kJ];
 #pragma unroll
     for (int j = 0; j < kJ; ++j) { mu[j] = lists[item * kJ + j]; nd[j] = 0; dd[j] = 0; }
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const typename Pack4<T>::t v = gcv_term<T, CPLX>(sp[i], dp[i], geo, e0 + i);
+    // kBracketU entries per thread and step, all loads issued before the math:
+    // with ten evaluations per entry the pass is bound by load latency
+    typedef typename ElemT<T, CPLX>::t E;
+    for (int i0 = threadIdx.x; i0 < cnt; i0 += kBracketU * blockDim.x) {
+        E sv[kBracketU], dv[kBracketU];
 #pragma unroll
-        for (int j = 0; j < kJ; j += 2) {
-            const T t1 = v.x + mu[j], t2 = v.x + mu[j + 1];
-            const T r = pair_rcp(t1 * t2);
-            const T s1 = t2 * r, s2 = t1 * r;
-            dd[j] += v.z * s1;
-            dd[j + 1] += v.z * s2;
-            nd[j] += v.y * s1 * s1;
-            nd[j + 1] += v.y * s2 * s2;
+        for (int u = 0; u < kBracketU; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < cnt) { sv[u] = sp[i]; dv[u] = dp[i]; }
+        }
+#pragma unroll
+        for (int u = 0; u < kBracketU; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i >= cnt) break;
+            const typename Pack4<T>::t v = gcv_term<T, CPLX>(sv[u], dv[u], geo, e0 + i);
+#pragma unroll
+            for (int j = 0; j < kJ; j += 2) {
+                const T t1 = v.x + mu[j], t2 = v.x + mu[j + 1];
+                const T r = pair_rcp(t1 * t2);
+                const T s1 = t2 * r, s2 = t1 * r;
+                dd[j] += v.z * s1;
+                dd[j + 1] += v.z * s2;
+                nd[j] += v.y * s1 * s1;
+                nd[j + 1] += v.y * s2 * s2;
+            }
         }
     }
+    // warp sums in the working precision (a thread holds at most
+    // kBracketChunk / 256 entries, so at most 16 + 5 roundings in FP32), one
+    // conversion per warp: FP64 runs at a small fraction of the FP32 rate
     const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
 #pragma unroll
     for (int j = 0; j < kJ; ++j) {
-        double a = nd[j], b = dd[j];
+        T a = nd[j], b = dd[j];
         for (int off = 16; off > 0; off >>= 1) {
             a += __shfl_down_sync(0xffffffffu, a, off);
             b += __shfl_down_sync(0xffffffffu, b, off);
         }
-        if (lane == 0) { red[warp][j] = a; red[warp][kJ + j] = b; }
+        if (lane == 0) { red[warp][j] = (double)a; red[warp][kJ + j] = (double)b; }
     }
     __syncthreads();
     if (threadIdx.x < 2 * kJ) {
@@ -440,6 +462,76 @@ __global__ void k_bracket_finalize(const double* __restrict__ partials, int nchu
         for (int q = 0; q < NG; ++q) { num += acc[q][threadIdx.x]; den += acc[q][kJ + threadIdx.x]; }
         G[(long long)item * kJ + threadIdx.x] = num / (den * den);
     }
+}
+
+// ------------------------------------------- continuous refinement of mu*
+// Eq. (eq:mugcv) minimises G over mu > 0; the grid argmin k only brackets the
+// minimiser.  Per problem the search keeps lo, mid, hi in log10 mu and the
+// incumbent mu (the value G was evaluated at).  Every round evaluates G at
+// nine points, four equal log10 steps from lo to mid and four from mid to hi
+// (point 4 is the incumbent, point 9 of the kJ slots repeats point 8), moves
+// mid to the first minimiser j (NaN never wins; all NaN keeps the incumbent)
+// and lo, hi to its neighbours.  Rounds shrink the bracket about four times.
+constexpr int kRefinePoints = 9;
+constexpr int kRefineRounds = 5;
+static_assert(kRefinePoints <= kJ, "a round's points fit the bracket scan's slots");
+
+__device__ __forceinline__ double refine_point(double lo, double mid, double hi, int j) {
+    constexpr int half = kRefinePoints / 2;
+    return j <= half ? lo + (mid - lo) * j / half : mid + (hi - mid) * (j - half) / half;
+}
+
+template <typename T>
+__device__ __forceinline__ void refine_lists(double lo, double mid, double hi, double mid_mu, T* o) {
+    for (int j = 0; j < kRefinePoints; ++j)
+        o[j] = j == kRefinePoints / 2 ? (T)mid_mu : (T)pow(10.0, refine_point(lo, mid, hi, j));
+    for (int j = kRefinePoints; j < kJ; ++j) o[j] = o[kRefinePoints - 1];
+}
+
+// Round 0 around the grid argmin: st[item] = (lo, mid, hi, incumbent mu).
+template <typename T>
+__global__ void k_refine_init(const int* __restrict__ mu_idx, const double* __restrict__ grid,
+                              const double* __restrict__ lg, int K, double* __restrict__ st, T* __restrict__ lists,
+                              int B) {
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= B) return;
+    const int k = min(max(mu_idx[item], 0), K - 1);
+    const double lo = lg[max(k - 1, 0)], mid = lg[k], hi = lg[min(k + 1, K - 1)];
+    const double mid_mu = (double)(T)grid[k];
+    double* q = st + 4LL * item;
+    q[0] = lo; q[1] = mid; q[2] = hi; q[3] = mid_mu;
+    refine_lists<T>(lo, mid, hi, mid_mu, lists + (long long)item * kJ);
+}
+
+// After a round's G: the next round's bracket and points, or (last round) mu*
+// and G(mu*).
+template <typename T>
+__global__ void k_refine_step(const double* __restrict__ Gb, double* __restrict__ st, T* __restrict__ lists,
+                              int last, double* __restrict__ mu_out, double* __restrict__ G_out, int B) {
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= B) return;
+    const double* g = Gb + (long long)item * kJ;
+    int jm = kRefinePoints / 2;
+    double best = INFINITY;
+    bool any = false;
+    for (int j = 0; j < kRefinePoints; ++j) {
+        if (isnan(g[j])) continue;
+        if (!any || g[j] < best) { best = g[j]; jm = j; any = true; }
+    }
+    double* q = st + 4LL * item;
+    const double lo = q[0], mid = q[1], hi = q[2];
+    T* o = lists + (long long)item * kJ;
+    const double mu_j = (double)o[jm];
+    if (last) {
+        mu_out[item] = mu_j;
+        if (G_out) G_out[item] = g[jm];
+        return;
+    }
+    const double nlo = refine_point(lo, mid, hi, max(jm - 1, 0));
+    const double nmid = refine_point(lo, mid, hi, jm);
+    const double nhi = refine_point(lo, mid, hi, min(jm + 1, kRefinePoints - 1));
+    q[0] = nlo; q[1] = nmid; q[2] = nhi; q[3] = mu_j;
+    refine_lists<T>(nlo, nmid, nhi, mu_j, o);
 }
 
 template <typename T, bool CPLX>
@@ -698,8 +790,9 @@ __global__ void k_binned_decide(const double* __restrict__ Gb, int K, const int*
 void free_learned_ws(hobc_plan_s* p) {
     void* ps[] = {p->feat_partials, p->feat, p->mlp_y, p->bracket_mu, p->mu_hat, p->bracket_k0,
                   p->bracket_partials, p->bracket_G, p->bracket_idx, p->mu_val, p->fell_back, p->log_grid,
-                  p->bin_tab, p->ahist_partials, p->a_edges, p->k_hat};
+                  p->bin_tab, p->ahist_partials, p->a_edges, p->k_hat, p->refine_state};
     for (void* q : ps) cudaFree(q);
+    p->refine_state = nullptr;
     p->feat_partials = nullptr; p->feat = nullptr; p->mlp_y = nullptr; p->bracket_mu = nullptr;
     p->mu_hat = nullptr; p->bracket_k0 = nullptr; p->bracket_partials = nullptr; p->bracket_G = nullptr;
     p->bracket_idx = nullptr; p->mu_val = nullptr; p->fell_back = nullptr; p->log_grid = nullptr;
@@ -1012,6 +1105,7 @@ cudaError_t ensure_learned_ws(hobc_plan_s* p) {
     alloc((void**)&p->ahist_partials, B * ((S + kAChunk - 1) / kAChunk) * 3 * kABins * sizeof(double));
     alloc(&p->a_edges, (kABins + 1) * p->esz);
     alloc((void**)&p->k_hat, B * sizeof(int));
+    alloc((void**)&p->refine_state, B * 4 * sizeof(double));
     alloc((void**)&p->log_grid, (size_t)p->K * sizeof(double));
     if (e == cudaSuccess) {       // the histogram's bin edges 10^(lo + b (hi - lo) / nb), in plan precision
         std::vector<double> ed(kABins + 1);
@@ -1189,6 +1283,52 @@ hobc_status run_gcv_binned(hobc_plan_s* p, const void* ghat, const void* D, int*
     return check("hobc_gcv_binned");
 }
 
+// The refinement on a plan's spectra from the grid argmin mu_idx: one init
+// launch, then per round the bracket scan, its finalize and the step.
+template <typename T>
+hobc_status run_gcv_refine(hobc_plan_s* p, const void* ghat, const void* D, const int* mu_idx, double* mu_out,
+                           double* G_out) {
+    const int B = p->desc.batch, K = p->K;
+    const bool cplx = p->fam == HOBC_FAMILY_FOURIER;
+    typedef C2<T> CT;
+    T* lists = reinterpret_cast<T*>(p->bracket_mu);
+    const unsigned gridB = (unsigned)((B + 127) / 128);
+    k_refine_init<T><<<gridB, 128, 0, p->stream>>>(mu_idx, p->mu, p->log_grid, K, p->refine_state, lists, B);
+    GcvGeom geo = spectrum_geo<T>(p);
+    geo.K = kJ;
+    geo.chunk = kBracketChunk;
+    const int nchJ = (int)((geo.S + kBracketChunk - 1) / kBracketChunk);
+    const unsigned gridJ = (unsigned)(nchJ * (long long)B);
+    for (int r = 0; r < kRefineRounds; ++r) {
+        if (cplx)
+            k_gcv_bracket<T, true><<<gridJ, 256, 0, p->stream>>>(reinterpret_cast<const CT*>(ghat),
+                                                                  reinterpret_cast<const CT*>(D), geo.S,
+                                                                  p->desc.psf_per_item, lists, geo,
+                                                                  p->bracket_partials);
+        else
+            k_gcv_bracket<T, false><<<gridJ, 256, 0, p->stream>>>(reinterpret_cast<const T*>(ghat),
+                                                                   reinterpret_cast<const T*>(D), geo.S,
+                                                                   p->desc.psf_per_item, lists, geo,
+                                                                   p->bracket_partials);
+        k_bracket_finalize<<<B, 256, 0, p->stream>>>(p->bracket_partials, nchJ, p->bracket_G);
+        k_refine_step<T><<<gridB, 128, 0, p->stream>>>(p->bracket_G, p->refine_state, lists,
+                                                        r == kRefineRounds - 1, mu_out, G_out, B);
+    }
+    p->launches += 1 + 3 * kRefineRounds;
+    return check("hobc_gcv_refine");
+}
+
+template <typename T>
+hobc_status run_deblur_refined(hobc_plan_s* p, const void* g, const void* psf, void* f, int* mu_idx,
+                               double* mu_out) {
+    hobc_status s = run_eig<T>(p, psf, p->D);
+    if (s == HOBC_OK) s = run_analysis<T>(p, g, p->G);
+    if (s == HOBC_OK) s = run_gcv<T>(p, p->G, p->D, nullptr, mu_idx);
+    if (s == HOBC_OK) s = run_gcv_refine<T>(p, p->G, p->D, mu_idx, mu_out, nullptr);
+    if (s == HOBC_OK) s = run_filter_synthesis_mu<T>(p, p->G, p->D, mu_out, f);
+    return s;
+}
+
 template <typename T>
 hobc_status run_deblur_binned(hobc_plan_s* p, const void* g, const void* psf, void* f, int* mu_idx, int* fb) {
     hobc_status s = run_eig<T>(p, psf, p->D);
@@ -1258,6 +1398,45 @@ hobc_status hobc_deblur_binned(hobc_plan* p, const void* g_dev, const void* psf_
     int* fb = fell_back_dev ? fell_back_dev : p->fell_back;
     return p->prec == HOBC_FP64 ? run_deblur_binned<double>(p, g_dev, psf_dev, f_dev, mi, fb)
                                 : run_deblur_binned<float>(p, g_dev, psf_dev, f_dev, mi, fb);
+}
+
+hobc_status hobc_gcv_refine(hobc_plan* p, const void* ghat_dev, const void* d_dev, const int* mu_index_dev,
+                            double* mu_dev, double* gcv_dev) {
+    if (!p || !ghat_dev || !d_dev || !mu_index_dev || !mu_dev) return HOBC_ERR_ARG;
+    cudaError_t e = ensure_learned_ws(p);
+    if (e != cudaSuccess) { set_last_error("hobc_gcv_refine", e); return HOBC_ERR_CUDA; }
+    if (!p->grid_ascending) {
+        set_last_error_text("hobc_gcv_refine: the mu grid must be strictly increasing");
+        return HOBC_ERR_ARG;
+    }
+    p->launches = 0;
+    return p->prec == HOBC_FP64 ? run_gcv_refine<double>(p, ghat_dev, d_dev, mu_index_dev, mu_dev, gcv_dev)
+                                : run_gcv_refine<float>(p, ghat_dev, d_dev, mu_index_dev, mu_dev, gcv_dev);
+}
+
+hobc_status hobc_filter_synthesis_mu(hobc_plan* p, const void* ghat_dev, const void* d_dev, const double* mu_dev,
+                                     void* f_dev) {
+    if (!p || !ghat_dev || !d_dev || !mu_dev || !f_dev) return HOBC_ERR_ARG;
+    p->launches = 0;
+    hobc_status s = p->prec == HOBC_FP64 ? run_filter_synthesis_mu<double>(p, ghat_dev, d_dev, mu_dev, f_dev)
+                                         : run_filter_synthesis_mu<float>(p, ghat_dev, d_dev, mu_dev, f_dev);
+    return s == HOBC_OK ? check("hobc_filter_synthesis_mu") : s;
+}
+
+hobc_status hobc_deblur_refined(hobc_plan* p, const void* g_dev, const void* psf_dev, void* f_dev, int* mu_index_dev,
+                                double* mu_dev) {
+    if (!p || !g_dev || !psf_dev || !f_dev) return HOBC_ERR_ARG;
+    cudaError_t e = ensure_learned_ws(p);
+    if (e != cudaSuccess) { set_last_error("hobc_deblur_refined", e); return HOBC_ERR_CUDA; }
+    if (!p->grid_ascending) {
+        set_last_error_text("hobc_deblur_refined: the mu grid must be strictly increasing");
+        return HOBC_ERR_ARG;
+    }
+    p->launches = 0;
+    int* mi = mu_index_dev ? mu_index_dev : p->mu_idx;
+    double* mu = mu_dev ? mu_dev : p->mu_val;
+    return p->prec == HOBC_FP64 ? run_deblur_refined<double>(p, g_dev, psf_dev, f_dev, mi, mu)
+                                : run_deblur_refined<float>(p, g_dev, psf_dev, f_dev, mi, mu);
 }
 
 }  // extern "C"

@@ -22,7 +22,8 @@ LIB_PATH = os.path.join(_HERE, "libhobc.so")
 HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "hobc.h")
 HEADER_PATHS = [HEADER_PATH, os.path.join(os.path.dirname(_HERE), "include", "hobc_learned.h"),
                 os.path.join(os.path.dirname(_HERE), "include", "hobc_binned.h"),
-                os.path.join(os.path.dirname(_HERE), "include", "hobc_tc.h")]
+                os.path.join(os.path.dirname(_HERE), "include", "hobc_tc.h"),
+                os.path.join(os.path.dirname(_HERE), "include", "hobc_refine.h")]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_0906_2704_gb300.build`")
@@ -122,6 +123,12 @@ _lib.hobc_gcv_binned.argtypes = [_vp] * 6
 _lib.hobc_gcv_binned.restype = ctypes.c_int
 _lib.hobc_deblur_binned.argtypes = [_vp] * 6
 _lib.hobc_deblur_binned.restype = ctypes.c_int
+_lib.hobc_gcv_refine.argtypes = [_vp] * 6
+_lib.hobc_gcv_refine.restype = ctypes.c_int
+_lib.hobc_deblur_refined.argtypes = [_vp] * 6
+_lib.hobc_deblur_refined.restype = ctypes.c_int
+_lib.hobc_filter_synthesis_mu.argtypes = [_vp] * 5
+_lib.hobc_filter_synthesis_mu.restype = ctypes.c_int
 _lib.hobc_features.argtypes = [_vp] * 4
 _lib.hobc_features.restype = ctypes.c_int
 _lib.hobc_deblur_learned.argtypes = [_vp] * 7
@@ -354,6 +361,20 @@ class Plan:
     def deblur_binned(self, g, psf, f, mu_index=None, fell_back=None) -> None:
         _check(_lib.hobc_deblur_binned(self._handle, _ptr(g), _ptr(psf), _ptr(f), _ptr(mu_index), _ptr(fell_back)),
                "hobc_deblur_binned")
+
+    def gcv_refine(self, ghat, d, mu_index, mu, gcv=None) -> None:
+        """Refined mu* (double, per problem) from the grid argmin mu_index; gcv: G at mu*."""
+        _check(_lib.hobc_gcv_refine(self._handle, _ptr(ghat), _ptr(d), _ptr(mu_index), _ptr(mu), _ptr(gcv)),
+               "hobc_gcv_refine")
+
+    def filter_synthesis_mu(self, ghat, d, mu, f) -> None:
+        """Filter at mu[item] (double, device) and synthesis."""
+        _check(_lib.hobc_filter_synthesis_mu(self._handle, _ptr(ghat), _ptr(d), _ptr(mu), _ptr(f)),
+               "hobc_filter_synthesis_mu")
+
+    def deblur_refined(self, g, psf, f, mu_index=None, mu=None) -> None:
+        _check(_lib.hobc_deblur_refined(self._handle, _ptr(g), _ptr(psf), _ptr(f), _ptr(mu_index), _ptr(mu)),
+               "hobc_deblur_refined")
 
     def features(self, ghat, d, x) -> None:
         _check(_lib.hobc_features(self._handle, _ptr(ghat), _ptr(d), _ptr(x)), "hobc_features")

@@ -106,4 +106,7 @@ def test_learned_entry_points_reject_bad_arguments_on_the_host(hobc):
     assert lib.hobc_deblur_learned(None, None, None, None, None, None, None) == arg
     assert lib.hobc_gcv_binned(None, None, None, None, None, None) == arg
     assert lib.hobc_deblur_binned(None, None, None, None, None, None) == arg
+    assert lib.hobc_gcv_refine(None, None, None, None, None, None) == arg
+    assert lib.hobc_deblur_refined(None, None, None, None, None, None) == arg
+    assert lib.hobc_filter_synthesis_mu(None, None, None, None, None) == arg
     lib.hobc_mlp_destroy(None)
