@@ -459,9 +459,10 @@ def run_other(args):
             n = 1024 if args.workload == "cosine1024" else 512
             B, K = (16 if n == 1024 else 32), 256
             hh = synth.gaussian_psf_2d_separable(2.5, 15)
-            clean, _ = synth.problem_2d(4, n, n, hh, 0.0, count=4)
+            clean, truth = synth.problem_2d(4, n, n, hh, 0.0, count=4)
             rng = np.random.default_rng(5)
             gg = np.stack([synth.add_noise(rng, clean[i % 4], 0.005) for i in range(B)])
+            ftrue = np.stack([truth[i % 4] for i in range(B)])
             plan = hobc.Plan(2, (n, n), (15, 15), 2, synth.mu_grid(K), L="lap", prec=prec, family="cosine",
                              batch=B, stream=stream)
             g = torch.from_numpy(gg.astype(npdt)).to(dev)
@@ -486,6 +487,24 @@ def run_other(args):
             plan.status()
             extra["binned_mu"] = {"value": B / (ms_b / args.steps / 1e3), "unit": "deblurs/s",
                                   "index_agreement_with_full_scan": float((mi_b == mi).float().mean())}
+            # the exact GCV functional of Eq. (eq:gcv) (T_X kept in the numerator)
+            f_x = torch.empty_like(g)
+            mi_x = torch.empty(B, dtype=torch.int32, device=dev)
+            ms_x, _ = _timed(lambda: plan.deblur_exact(g, h, f_x, mi_x), stream, args.steps, 2)
+            x_launches = plan.last_launch_count
+            plan.deblur(g, h, f, mi)
+            plan.status()
+
+            def rre(t):
+                dlt = (t.cpu().numpy().astype(np.float64) - ftrue).reshape(B, -1)
+                return np.linalg.norm(dlt, axis=1) / np.linalg.norm(ftrue.reshape(B, -1), axis=1)
+            grid = synth.mu_grid(K)
+            extra["exact_gcv"] = {"value": B / (ms_x / args.steps / 1e3), "unit": "deblurs/s",
+                                  "ms_per_step": ms_x / args.steps, "gpu_launches": x_launches * args.steps,
+                                  "index_agreement_with_approximation": float((mi_x == mi).float().mean()),
+                                  "mu": {"approximate_median": float(np.median(grid[mi.cpu().numpy()])),
+                                         "exact_median": float(np.median(grid[mi_x.cpu().numpy()]))},
+                                  "rre_mean": {"approximate": float(rre(f).mean()), "exact": float(rre(f_x).mean())}}
             if prec == "split_bf16":
                 # 4 passes x 3 split products x 2 n^3 (the padded tile shape is what the tensor cores run)
                 tm, tn, tk = hobc.tc_tiles()
@@ -669,7 +688,8 @@ def run_learned(args):
 
 def run_bccompare(args):
     """The paper's comparison of boundary conditions (its 2D out-of-focus experiment) on
-    synthetic images: RRE at the RRE-optimal grid mu and at the GCV mu for periodic,
+    synthetic images: RRE at the RRE-optimal grid mu, at the GCV mu (the paper's
+    approximation, Eq. (eq:gcv2)) and at the exact-GCV mu (Eq. (eq:gcv)) for periodic,
     reflective, antireflective (degree 1), degree-2 (cosine) and degree-3 conditions.
     Images as in the other 2D workloads, out-of-focus (disk) PSF of radius 3.3 in a
     9 x 9 array, 0.1% noise, L = I (the paper's setting) and the Laplacian, 64 mu."""
@@ -721,9 +741,14 @@ def run_bccompare(args):
             plan.gcv(G, D, torch.empty((B, K), dtype=torch.float64, device=dev), mi)
             plan.status()
             kg = mi.cpu().numpy()
+            # the exact functional of Eq. (eq:gcv): T_X kept in the numerator
+            plan.gcv_exact(G, D, None, mi)
+            plan.status()
+            kx = mi.cpu().numpy()
             table[fam] = {"rre_opt": float(rre.min(axis=0).mean()), "rre_gcv": float(rre[kg, np.arange(B)].mean()),
-                          "mu_gcv_median": float(np.median(mus[kg])), "engine": prec,
-                          "deblurs_per_s": B / (ms / args.steps / 1e3)}
+                          "rre_gcv_exact": float(rre[kx, np.arange(B)].mean()),
+                          "mu_gcv_median": float(np.median(mus[kg])), "mu_gcv_exact_median": float(np.median(mus[kx])),
+                          "engine": prec, "deblurs_per_s": B / (ms / args.steps / 1e3)}
         tables[L] = table
     table = tables["I"]
     line = {"metric": "RRE at mu_opt / mu_GCV by boundary condition (2D out-of-focus blur, 0.1% noise, L=I)",

@@ -1,0 +1,60 @@
+/*
+ * The exact GCV functional of Eq. (eq:gcv), as an option beside the paper's
+ * approximation (Eq. (eq:gcv2)).  With A = T_X D T_X^{-1} and the reblurred
+ * filter of Eq. (eq:freg), g - A f_mu = T_X (I - Phi_mu) ghat, so
+ *
+ *   G_ex(mu) = ||T_X (sigma . ghat)||^2 / (sum_i sigma_i)^2,
+ *   sigma_i = |s_i|^2 / (|d_i|^2 + mu |s_i|^2),
+ *
+ * the approximate functional with T_X kept in the numerator (both divided by
+ * mu^2).  The paper drops T_X because it is close to orthogonal; it is not
+ * for large n (T_C at n = 1024 has condition ~2e4), which is where the two
+ * functionals part.  Each axis's T_a is split by rows: the interior rows are
+ * X_a^T W_a with X_a^T orthonormal and W_a = [bhat_L | I | bhat_R] (bhat the
+ * transformed interior parts of the k border columns per side), the 2k
+ * extension rows are V_a.  In 2D (T = T_0 (x) T_1 acting as T_0 P T_1^T on the
+ * spectrum P = sigma . ghat):
+ *
+ *   ||T P||^2 = ||W0 P W1^T||^2 + ||V0 P W1^T||^2 + ||W0 P V1^T||^2 + ||V0 P V1^T||^2,
+ *
+ * every term a sum of squares, so rounding is amplified by cond(T), not
+ * cond(T)^2.  Per (entry, mu) this costs 1 + 2k reciprocals and about 4k(k+1)
+ * products beside the approximation's terms.  Real families only (sine and
+ * cosine: k = 1, degree 3: k = 2; the classical reflective and periodic
+ * conditions of HOBC_SPLIT_BF16 plans have orthogonal T, k = 0, and G_ex
+ * equals the approximation).  The Fourier family returns
+ * HOBC_ERR_UNSUPPORTED: its complex T_F on a half spectrum couples each stored
+ * row with its conjugate partner.
+ *
+ * Conventions are those of hobc.h: device pointers, calls asynchronous on the
+ * plan's stream, errors as hobc_status with hobc_last_error() for CUDA
+ * failures.  The first call on a plan builds the row splits (FP64 transforms
+ * of the identity, synchronous) and, for 2D plans, allocates the per-line
+ * sums (batch x ((3 + 2k) n_1 + n_0) x K values of the plan's precision).
+ */
+#ifndef HOBC_EXACT_H
+#define HOBC_EXACT_H
+
+#include "hobc.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Step: G_ex on every grid value and its first minimiser (NaN never wins),
+ * from spectra laid out as hobc_analysis / hobc_eigenvalues write them.
+ * gcv_dev [batch][K] (nullable), mu_index_dev [batch].  Sums per line in the
+ * plan's precision, across lines in FP64. */
+hobc_status hobc_gcv_exact(hobc_plan* plan, const void* ghat_dev, const void* d_dev, double* gcv_dev,
+                           int* mu_index_dev);
+
+/* The whole method with mu* chosen by G_ex: eigenvalues, analysis,
+ * hobc_gcv_exact, filter + synthesis at the grid value mu*. */
+hobc_status hobc_deblur_exact(hobc_plan* plan, const void* g_dev, const void* psf_dev, void* f_dev,
+                              int* mu_index_dev, double* gcv_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOBC_EXACT_H */

@@ -409,6 +409,7 @@ void hobc_plan_destroy(hobc_plan* p) {
     cudaFree(p->g_in); cudaFree(p->f_out); cudaFree(p->psf_in);
     free_learned_ws(p);
     dense_free(p);
+    exact_free(p);
     for (int i = 0; i < 2; ++i)
         if (p->aux[i]) cudaStreamDestroy(p->aux[i]);
     if (p->aux_ev) cudaEventDestroy(p->aux_ev);

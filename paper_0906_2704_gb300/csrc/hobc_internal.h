@@ -84,6 +84,7 @@ struct hobc_plan_s {
     cudaEvent_t aux_ev;
     int grid_ascending;      // 1 if the mu grid is strictly increasing
     struct hobc_dense_s* dense;   // HOBC_SPLIT_BF16: matrices and operand workspace (hobc_tc.cu)
+    struct hobc_exact_s* exact;   // exact GCV: Gram factors and line sums, allocated on first use (hobc_exact.cu)
     size_t item0;            // first problem of this view of the plan (0 for the plan itself)
 };
 
@@ -115,6 +116,7 @@ void theta_frac(int fam, int n, int t, long long& num, long long& den);
 void set_last_error(const char* what, cudaError_t e);
 void set_last_error_text(const char* text);
 hobc_status launch_gcv_finalize(hobc_plan_s* p, double* gcv, int* mu_idx);
+void exact_free(hobc_plan_s* p);
 // G(mu_j) and the grid argmin of each problem from its chunk partials: one
 // cluster of up to 8 CTAs per problem (hobc_api.cu)
 cudaError_t launch_gcv_finalize_raw(const double* partials, int nchunks, int K, int batch, double* gcv,

@@ -23,7 +23,8 @@ HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "hobc.h")
 HEADER_PATHS = [HEADER_PATH, os.path.join(os.path.dirname(_HERE), "include", "hobc_learned.h"),
                 os.path.join(os.path.dirname(_HERE), "include", "hobc_binned.h"),
                 os.path.join(os.path.dirname(_HERE), "include", "hobc_tc.h"),
-                os.path.join(os.path.dirname(_HERE), "include", "hobc_refine.h")]
+                os.path.join(os.path.dirname(_HERE), "include", "hobc_refine.h"),
+                os.path.join(os.path.dirname(_HERE), "include", "hobc_exact.h")]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_0906_2704_gb300.build`")
@@ -129,6 +130,10 @@ _lib.hobc_deblur_refined.argtypes = [_vp] * 6
 _lib.hobc_deblur_refined.restype = ctypes.c_int
 _lib.hobc_filter_synthesis_mu.argtypes = [_vp] * 5
 _lib.hobc_filter_synthesis_mu.restype = ctypes.c_int
+_lib.hobc_gcv_exact.argtypes = [_vp] * 5
+_lib.hobc_gcv_exact.restype = ctypes.c_int
+_lib.hobc_deblur_exact.argtypes = [_vp] * 6
+_lib.hobc_deblur_exact.restype = ctypes.c_int
 _lib.hobc_features.argtypes = [_vp] * 4
 _lib.hobc_features.restype = ctypes.c_int
 _lib.hobc_deblur_learned.argtypes = [_vp] * 7
@@ -371,6 +376,14 @@ class Plan:
         """Filter at mu[item] (double, device) and synthesis."""
         _check(_lib.hobc_filter_synthesis_mu(self._handle, _ptr(ghat), _ptr(d), _ptr(mu), _ptr(f)),
                "hobc_filter_synthesis_mu")
+
+    def gcv_exact(self, ghat, d, gcv, mu_index) -> None:
+        """The exact GCV functional of Eq. (eq:gcv) on the grid and its argmin."""
+        _check(_lib.hobc_gcv_exact(self._handle, _ptr(ghat), _ptr(d), _ptr(gcv), _ptr(mu_index)), "hobc_gcv_exact")
+
+    def deblur_exact(self, g, psf, f, mu_index=None, gcv=None) -> None:
+        _check(_lib.hobc_deblur_exact(self._handle, _ptr(g), _ptr(psf), _ptr(f), _ptr(mu_index), _ptr(gcv)),
+               "hobc_deblur_exact")
 
     def deblur_refined(self, g, psf, f, mu_index=None, mu=None) -> None:
         _check(_lib.hobc_deblur_refined(self._handle, _ptr(g), _ptr(psf), _ptr(f), _ptr(mu_index), _ptr(mu)),

@@ -109,4 +109,6 @@ def test_learned_entry_points_reject_bad_arguments_on_the_host(hobc):
     assert lib.hobc_gcv_refine(None, None, None, None, None, None) == arg
     assert lib.hobc_deblur_refined(None, None, None, None, None, None) == arg
     assert lib.hobc_filter_synthesis_mu(None, None, None, None, None) == arg
+    assert lib.hobc_gcv_exact(None, None, None, None, None) == arg
+    assert lib.hobc_deblur_exact(None, None, None, None, None, None) == arg
     lib.hobc_mlp_destroy(None)
