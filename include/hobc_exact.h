@@ -7,10 +7,10 @@
  *   sigma_i = |s_i|^2 / (|d_i|^2 + mu |s_i|^2),
  *
  * the approximate functional with T_X kept in the numerator (both divided by
- * mu^2).  The paper drops T_X because it is close to orthogonal; it is not
+ * mu^2).  The paper drops T_X because it is close to unitary; it is not
  * for large n (T_C at n = 1024 has condition ~2e4), which is where the two
  * functionals part.  Each axis's T_a is split by rows: the interior rows are
- * X_a^T W_a with X_a^T orthonormal and W_a = [bhat_L | I | bhat_R] (bhat the
+ * X_a^H W_a with X_a^H unitary and W_a = [bhat_L | I | bhat_R] (bhat the
  * transformed interior parts of the k border columns per side), the 2k
  * extension rows are V_a.  In 2D (T = T_0 (x) T_1 acting as T_0 P T_1^T on the
  * spectrum P = sigma . ghat):
@@ -19,18 +19,20 @@
  *
  * every term a sum of squares, so rounding is amplified by cond(T), not
  * cond(T)^2.  Per (entry, mu) this costs 1 + 2k reciprocals and about 4k(k+1)
- * products beside the approximation's terms.  Real families only (sine and
- * cosine: k = 1, degree 3: k = 2; the classical reflective and periodic
- * conditions of HOBC_SPLIT_BF16 plans have orthogonal T, k = 0, and G_ex
- * equals the approximation).  The Fourier family returns
- * HOBC_ERR_UNSUPPORTED: its complex T_F on a half spectrum couples each stored
- * row with its conjugate partner.
+ * products beside the approximation's terms (complex for the Fourier
+ * family).  Every family: sine, cosine and Fourier k = 1, degree 3 k = 2; the
+ * classical reflective and periodic conditions of HOBC_SPLIT_BF16 plans have
+ * orthogonal T, k = 0, and G_ex equals the approximation.  The Fourier family
+ * stores half of the last axis: a full column of the other half is the
+ * conjugate of a stored column with its rows mapped t -> -t, so column sums
+ * carry the pair weight 2 and the row sums add the partner entries.
  *
  * Conventions are those of hobc.h: device pointers, calls asynchronous on the
  * plan's stream, errors as hobc_status with hobc_last_error() for CUDA
  * failures.  The first call on a plan builds the row splits (FP64 transforms
  * of the identity, synchronous) and, for 2D plans, allocates the per-line
- * sums (batch x ((3 + 2k) n_1 + n_0) x K values of the plan's precision).
+ * sums (batch x ((3 + 2k c) W_1 + n_0) x K values of the plan's precision;
+ * W_1 the stored columns, c = 2 for the Fourier family, else 1).
  */
 #ifndef HOBC_EXACT_H
 #define HOBC_EXACT_H

@@ -1,16 +1,21 @@
-// The exact GCV functional of Eq. (eq:gcv) for the real families
-// (include/hobc_exact.h).  Per plan, once: T_a of each axis from the FP64
-// synthesis of the identity, split by rows on the host (FP64): the interior
-// rows are X_a^T W_a with X_a^T orthonormal and W_a = [bhat_L | I | bhat_R],
-// the 2k extension rows (at the border indices) are V_a.  Then
+// The exact GCV functional of Eq. (eq:gcv) (include/hobc_exact.h).  Per plan,
+// once: T_a of each axis from the FP64 synthesis path, split by rows on the
+// host (FP64): the interior rows are X_a^H W_a with X_a^H unitary and
+// W_a = [bhat_L | I | bhat_R], the 2k extension rows (at the border indices)
+// are V_a.  Then
 //   ||T_0 P T_1^T||^2 = ||W0 P W1^T||^2 + ||V0 P W1^T||^2 + ||W0 P V1^T||^2
 //                       + ||V0 P V1^T||^2,
 // every term a sum of squares (no cancellation between large terms, which
-// the Gram form |P|^2 + P^T (T^T T - I) P suffers: T_C at n = 1024 has
-// condition ~2e4).  Per call: one CTA per spectral column, one per spectral
-// row, an FP64 reduction and the argmin; 1D plans one CTA per problem.
+// the Gram form |P|^2 + P^H (T^H T - I) P suffers: T_C at n = 1024 has
+// condition ~2e4).  Per call: one CTA per stored spectral column, one per
+// spectral row, an FP64 reduction and the argmin; 1D plans one CTA per
+// problem.  The Fourier family stores half of the last axis: a full column of
+// the other half is the conjugate of a stored column with its rows mapped
+// t -> -t, so column sums carry the pair weight 2, and row sums and
+// V0 P V1^T add the partner entries explicitly.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -19,14 +24,17 @@
 #include "hobc_internal.h"
 #include "hobc_kernels.cuh"
 
+typedef std::complex<double> cdx;
+
 struct hobc_exact_s {
-    int k;                 // border vectors per side (1: sine and cosine, 2: degree 3, 0: orthogonal T)
+    int k;                 // border vectors per side (1: degrees 1 and 2, 2: degree 3, 0: orthogonal T)
+    int cplx;              // Fourier family: complex T and a half spectrum on the last axis
     int N[2];              // interior length n_a - 2k
     int bidx[2][4];        // border indices of each axis: 0..k-1, n-k..n-1
-    void* bhat[2];         // [2k][N_a] plan precision: X_a times the interior part of each border column
+    void* bhat[2];         // [2k][N_a] plan precision (complex for the Fourier family)
     void* V[2];            // [2k][n_a] plan precision: the extension rows of T_a
-    double* Vd[2];         // [2k][n_a] FP64 copy of V_a (the V_0 P V_1^T term)
-    void* col_out;         // [batch][n_1][3 + 2k][K]: |W0 P W1^T col|^2, |V0 P W1^T col|^2, sum sigma, V0 P col
+    void* Vd[2];           // [2k][n_a] FP64 copy of V_a (the V_0 P V_1^T term)
+    void* col_out;         // [batch][stored columns][3 + 2k (x2 complex)][K]
     void* row_out;         // [batch][n_0][K]: |W0 P V1^T row|^2
     double* G;             // [batch][K] when the caller passes no curve
 };
@@ -35,27 +43,74 @@ namespace hobc {
 
 constexpr int kExKMax = 2;             // border vectors per side at most (degree 3)
 constexpr int kExB = 2 * kExKMax;
-constexpr int kExSlots = 8;            // reduction: line slices per grid value
+constexpr int kExSlots = 4;            // reduction: line slices per grid value
+
+// ------------------------------------------------- real or complex entries
+__device__ __forceinline__ float xm(float a, float b) { return a * b; }
+__device__ __forceinline__ double xm(double a, double b) { return a * b; }
+__device__ __forceinline__ float2 xm(float2 a, float2 b) { return cmul<float>(a, b); }
+__device__ __forceinline__ double2 xm(double2 a, double2 b) { return cmul<double>(a, b); }
+__device__ __forceinline__ float xa(float a, float b) { return a + b; }
+__device__ __forceinline__ double xa(double a, double b) { return a + b; }
+__device__ __forceinline__ float2 xa(float2 a, float2 b) { return cadd<float>(a, b); }
+__device__ __forceinline__ double2 xa(double2 a, double2 b) { return cadd<double>(a, b); }
+__device__ __forceinline__ float xc(float a) { return a; }
+__device__ __forceinline__ double xc(double a) { return a; }
+__device__ __forceinline__ float2 xc(float2 a) { return cconj<float>(a); }
+__device__ __forceinline__ double2 xc(double2 a) { return cconj<double>(a); }
+__device__ __forceinline__ float xs(float a, float s) { return a * s; }
+__device__ __forceinline__ double xs(double a, double s) { return a * s; }
+__device__ __forceinline__ float2 xs(float2 a, float s) { return cscale<float>(a, s); }
+__device__ __forceinline__ double2 xs(double2 a, double s) { return cscale<double>(a, s); }
+template <typename E> __device__ __forceinline__ E xz();
+template <> __device__ __forceinline__ float xz<float>() { return 0.f; }
+template <> __device__ __forceinline__ double xz<double>() { return 0.0; }
+template <> __device__ __forceinline__ float2 xz<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 xz<double2>() { return make_double2(0.0, 0.0); }
+
+// Fourier half spectrum along an axis of n (N = n - 2): spectral index of a
+// stored entry, whether it stands alone (no conjugate partner), and t -> -t.
+__device__ __forceinline__ int hx_t(int c, int n, int W) { return c == W - 1 ? n - 1 : c; }
+__device__ __forceinline__ bool hx_self(int c, int n, int W) { return c == 0 || c == W - 1 || c == 1 || 2 * (c - 1) == n - 2; }
+__device__ __forceinline__ int hx_neg(int t, int n) {
+    const int N = n - 2;
+    return (t == 0 || t == n - 1) ? t : 1 + (N - (t - 1)) % N;
+}
 
 namespace {
 
-// Column t of T_X of one axis (T[i * n + t]) from the FP64 synthesis of e_t.
-hobc_status axis_matrix(int fam, int n, cudaStream_t st, std::vector<double>& T) {
+// Column t of T_X of one axis (T[i * n + t]) from the FP64 synthesis path.
+// Real families: synthesis of e_t.  Fourier family (real signals from half
+// spectra): a unit at stored bin c gives T[:, t] + T[:, -t] = 2 Re T[:, t] and
+// an imaginary unit gives -2 Im T[:, t]; borders and self-conjugate bins are
+// real columns; T[:, -t] = conj T[:, t].
+hobc_status axis_matrix(int fam, int n, cudaStream_t st, std::vector<cdx>& T) {
+    const bool F = fam == HOBC_FAMILY_FOURIER;
+    const int N = n - 2;
+    const int W = F ? N / 2 + 3 : n;
+    const int items = F ? 2 * W : n;
     hobc_plan_desc q;
     memset(&q, 0, sizeof(q));
     q.ndim = 1; q.n[0] = n; q.psf[0] = 1; q.family = (hobc_family)fam; q.psf_symmetric = 1;
-    q.bc_degree = fam == HOBC_FAMILY_SINE ? 1 : (fam == HOBC_FAMILY_COSINE ? 2 : 3);
-    q.L = HOBC_L_IDENTITY; q.prec = HOBC_FP64; q.n_mu = 1; q.batch = n; q.psf_per_item = 0;
+    q.bc_degree = fam == HOBC_FAMILY_SINE ? 1 : (fam == HOBC_FAMILY_SINE_CUBIC ? 3 : 2);
+    q.L = HOBC_L_IDENTITY; q.prec = HOBC_FP64; q.n_mu = 1; q.batch = items; q.psf_per_item = 0;
     const double one = 1.0;
     hobc_plan* ip = nullptr;
     hobc_status s = hobc_plan_create(&q, &one, st, &ip);
     if (s != HOBC_OK) return s;
+    const size_t in_per = F ? 2 * (size_t)W : (size_t)n;        // doubles per input item
+    std::vector<double> in((size_t)items * in_per, 0.0), Y((size_t)items * n);
+    if (F)
+        for (int c = 0; c < W; ++c) {
+            in[(size_t)(2 * c) * in_per + 2 * c] = 1.0;          // real unit at stored c
+            in[(size_t)(2 * c + 1) * in_per + 2 * c + 1] = 1.0;  // imaginary unit at stored c
+        }
+    else
+        for (int t = 0; t < n; ++t) in[(size_t)t * in_per + t] = 1.0;
     double *I = nullptr, *out = nullptr;
-    cudaError_t e = cudaMalloc((void**)&I, (size_t)n * n * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&out, (size_t)n * n * sizeof(double));
-    std::vector<double> eye((size_t)n * n, 0.0), Y((size_t)n * n);
-    for (int i = 0; i < n; ++i) eye[(size_t)i * n + i] = 1.0;
-    if (e == cudaSuccess) e = cudaMemcpy(I, eye.data(), eye.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMalloc((void**)&I, in.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&out, Y.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(I, in.data(), in.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) s = hobc_synthesis(ip, I, out);
     if (e == cudaSuccess && s == HOBC_OK) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && s == HOBC_OK) e = cudaMemcpy(Y.data(), out, Y.size() * sizeof(double), cudaMemcpyDeviceToHost);
@@ -64,35 +119,54 @@ hobc_status axis_matrix(int fam, int n, cudaStream_t st, std::vector<double>& T)
     hobc_plan_destroy(ip);
     if (s != HOBC_OK) return s;
     if (e != cudaSuccess) { set_last_error("hobc_gcv_exact (transform matrix)", e); return HOBC_ERR_CUDA; }
-    T.assign((size_t)n * n, 0.0);
-    for (int t = 0; t < n; ++t)                 // row t of the output is T e_t
-        for (int i = 0; i < n; ++i) T[(size_t)i * n + t] = Y[(size_t)t * n + i];
+    T.assign((size_t)n * n, cdx(0, 0));
+    if (!F) {
+        for (int t = 0; t < n; ++t)
+            for (int i = 0; i < n; ++i) T[(size_t)i * n + t] = Y[(size_t)t * n + i];
+        return HOBC_OK;
+    }
+    for (int c = 0; c < W; ++c) {
+        const int t = c == W - 1 ? n - 1 : c;
+        const bool self = c == 0 || c == W - 1 || c == 1 || 2 * (c - 1) == N;
+        const double* yr = &Y[(size_t)(2 * c) * n];
+        const double* yi = &Y[(size_t)(2 * c + 1) * n];
+        if (self) {
+            for (int i = 0; i < n; ++i) T[(size_t)i * n + t] = yr[i];
+        } else {
+            const int tn = 1 + (N - (t - 1)) % N;
+            for (int i = 0; i < n; ++i) {
+                const cdx v(0.5 * yr[i], -0.5 * yi[i]);
+                T[(size_t)i * n + t] = v;
+                T[(size_t)i * n + tn] = std::conj(v);
+            }
+        }
+    }
     return HOBC_OK;
 }
 
 // The row split of T (k border indices per side): interior rows k..n-k-1 are
-// X^T [bhat_L | I | bhat_R] with X^T = T[interior][interior] orthonormal, and
-// the extension rows (the border indices) are V.  Checks the orthonormality.
-hobc_status split_rows(const std::vector<double>& T, int n, int k, std::vector<double>& bhat, std::vector<double>& V) {
+// X^H [bhat_L | I | bhat_R] with X^H = T[interior][interior] unitary, and the
+// extension rows (the border indices) are V.  Checks the unitarity.
+hobc_status split_rows(const std::vector<cdx>& T, int n, int k, std::vector<cdx>& bhat, std::vector<cdx>& V) {
     const int N = n - 2 * k;
     double dev = 0;
-    for (int i = 0; i < N; ++i)                 // rows of X^T: X^T X = I
+    for (int i = 0; i < N; ++i)                 // rows of X^H are orthonormal
         for (int j = i; j < N; ++j) {
-            double acc = 0;
-            for (int m = 0; m < N; ++m) acc += T[(size_t)(k + i) * n + k + m] * T[(size_t)(k + j) * n + k + m];
-            dev = std::max(dev, std::fabs(acc - (i == j ? 1.0 : 0.0)));
+            cdx acc(0, 0);
+            for (int m = 0; m < N; ++m) acc += T[(size_t)(k + i) * n + k + m] * std::conj(T[(size_t)(k + j) * n + k + m]);
+            dev = std::max(dev, std::abs(acc - cdx(i == j ? 1.0 : 0.0, 0.0)));
         }
     if (dev > 1e-10) {
-        set_last_error_text("hobc_gcv_exact: the interior block of T is not orthonormal");
+        set_last_error_text("hobc_gcv_exact: the interior block of T is not unitary");
         return HOBC_ERR_UNSUPPORTED;
     }
-    bhat.assign((size_t)std::max(2 * k * N, 1), 0.0);
-    V.assign((size_t)std::max(2 * k * n, 1), 0.0);
+    bhat.assign((size_t)std::max(2 * k * N, 1), cdx(0, 0));
+    V.assign((size_t)std::max(2 * k * n, 1), cdx(0, 0));
     for (int b = 0; b < 2 * k; ++b) {
         const int col = b < k ? b : n - 2 * k + b;
-        for (int i = 0; i < N; ++i) {           // (X t_int)[i] = sum_m X^T[m][i] T[k + m][col]
-            double acc = 0;
-            for (int m = 0; m < N; ++m) acc += T[(size_t)(k + m) * n + k + i] * T[(size_t)(k + m) * n + col];
+        for (int i = 0; i < N; ++i) {           // (X t_int)[i] = sum_m conj(X^H[m][i]) T[k + m][col]
+            cdx acc(0, 0);
+            for (int m = 0; m < N; ++m) acc += std::conj(T[(size_t)(k + m) * n + k + i]) * T[(size_t)(k + m) * n + col];
             bhat[(size_t)b * N + i] = acc;
         }
         for (int a = 0; a < n; ++a) V[(size_t)b * n + a] = T[(size_t)col * n + a];
@@ -100,8 +174,13 @@ hobc_status split_rows(const std::vector<double>& T, int n, int k, std::vector<d
     return HOBC_OK;
 }
 
-template <typename T> cudaError_t upload(void** dst, const std::vector<double>& v) {
-    std::vector<T> w(v.begin(), v.end());
+// Device copy in the plan's precision: real parts only, or (re, im) pairs.
+template <typename T> cudaError_t upload(void** dst, const std::vector<cdx>& v, bool cplx) {
+    std::vector<T> w(v.size() * (cplx ? 2 : 1));
+    for (size_t i = 0; i < v.size(); ++i) {
+        if (cplx) { w[2 * i] = (T)v[i].real(); w[2 * i + 1] = (T)v[i].imag(); }
+        else w[i] = (T)v[i].real();
+    }
     cudaError_t e = cudaMalloc(dst, w.size() * sizeof(T));
     if (e == cudaSuccess) e = cudaMemcpy(*dst, w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice);
     return e;
@@ -121,106 +200,119 @@ GcvGeom exact_geo(const hobc_plan_s* p) {
 struct ExAxis {            // one axis's split, as the kernels see it
     const void* bhat;
     const void* V;
-    int n, N;
-    int bidx[kExB];
+    int n, N, W;           // W: stored entries along the axis (half spectrum on the Fourier family's last axis)
+    int bidx[kExB];        // border spectral indices
+    int bcol[kExB];        // their stored positions
 };
 
 }  // namespace
 
-// a and ghat of stored entry e into shared memory: entries with s = 0 carry
-// a = inf (sigma = 0, so they drop out as in the approximation).
-template <typename T>
-__device__ __forceinline__ void ex_stage(const T* sp, const T* dp, const GcvGeom& geo, long long e, T& a, T& g) {
-    const typename Pack4<T>::t v = gcv_term<T, false>(sp[e], dp[e], geo, e);
+// a and ghat of stored entry e: entries with s = 0 carry a = inf (sigma = 0,
+// so they drop out as in the approximation).
+template <typename T, bool CPLX>
+__device__ __forceinline__ void ex_stage(const typename ElemT<T, CPLX>::t* sp, const typename ElemT<T, CPLX>::t* dp,
+                                         const GcvGeom& geo, long long e, T& a, typename ElemT<T, CPLX>::t& g) {
+    typedef typename ElemT<T, CPLX>::t E;
+    const typename Pack4<T>::t v = gcv_term<T, CPLX>(sp[e], dp[e], geo, e);
     const bool live = v.z > (T)0;
     a = live ? v.x : (T)INFINITY;
-    g = live ? sp[e] : (T)0;
+    g = live ? sp[e] : xz<E>();
 }
 
-// 2D, one CTA per spectral column c (entries c n0 + a), one grid value per
-// thread.  Also stages the border columns.  For an interior column j = c - k:
-//   ww = sum_i (W0 P W1^T)[i][j]^2,  vw = sum_r (V0 P W1^T)[r][j]^2;
-// for every column: den = sum sigma and the projections (V0 P)[r][c].
-// grid = (n1, items), block = 256; dynamic shared memory 2 (1 + 2k) n0 sizeof(T).
-template <typename T>
+// 2D, one CTA per stored spectral column c (entries c n0 + a), one grid value
+// per thread, with the border columns staged.  For an interior column
+// (spectral index t, j = t - k):
+//   ww = sum_i |(W0 P W1^T)[i][j]|^2,  vw = sum_r |(V0 P W1^T)[r][j]|^2;
+// for every column: den = sum sigma and the projections (V0 P)[r][c].  The
+// sums carry the column's pair weight (2 for a stored Fourier column that
+// stands for a conjugate pair).
+// grid = (stored columns, items), block <= 256;
+// dynamic shared memory (1 + 2k) n0 (sizeof(T) + sizeof(E)).
+template <typename T, bool CPLX>
 __global__ void __launch_bounds__(256)
-k_ex_cols(const T* __restrict__ spec, const T* __restrict__ D, long long d_psf_stride, int psf_per,
-          const T* __restrict__ muT, GcvGeom geo, ExAxis A0, ExAxis A1, int k, T* __restrict__ out) {
+k_ex_cols(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
+          long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo, ExAxis A0, ExAxis A1, int k,
+          T* __restrict__ out) {
+    typedef typename ElemT<T, CPLX>::t E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n0 = A0.n, n1 = A1.n, nb = 2 * k;
-    T* sa = reinterpret_cast<T*>(smem_raw);     // [1 + nb][n0]
-    T* sg = sa + (size_t)(1 + nb) * n0;
+    E* sg = reinterpret_cast<E*>(smem_raw);                      // [1 + nb][n0]
+    T* sa = reinterpret_cast<T*>(sg + (size_t)(1 + nb) * n0);     // [1 + nb][n0]
     const int c = blockIdx.x;
     const long long item = blockIdx.y;
-    const T* sp = spec + item * geo.S;
-    const T* dp = D + (psf_per ? item : 0) * d_psf_stride;
+    const E* sp = spec + item * geo.S;
+    const E* dp = D + (psf_per ? item : 0) * d_psf_stride;
     for (int s = 0; s <= nb; ++s) {
-        const int col = s == 0 ? c : A1.bidx[s - 1];
+        const int col = s == 0 ? c : A1.bcol[s - 1];
         for (int a = threadIdx.x; a < n0; a += blockDim.x)
-            ex_stage<T>(sp, dp, geo, (long long)col * n0 + a, sa[s * n0 + a], sg[s * n0 + a]);
+            ex_stage<T, CPLX>(sp, dp, geo, (long long)col * n0 + a, sa[s * n0 + a], sg[s * n0 + a]);
     }
     __syncthreads();
-    const T* b0 = reinterpret_cast<const T*>(A0.bhat);
-    const T* b1 = reinterpret_cast<const T*>(A1.bhat);
-    const T* V0 = reinterpret_cast<const T*>(A0.V);
-    const bool inter = c >= k && c < n1 - k;
-    const int jj = c - k;
-    T beta[kExB];
+    const E* b0 = reinterpret_cast<const E*>(A0.bhat);
+    const E* b1 = reinterpret_cast<const E*>(A1.bhat);
+    const E* V0 = reinterpret_cast<const E*>(A0.V);
+    const int t = CPLX ? hx_t(c, n1, A1.W) : c;
+    const T wgt = (CPLX && !hx_self(c, n1, A1.W)) ? (T)2 : (T)1;
+    const bool inter = t >= k && t < n1 - k;
+    const int jj = t - k;
+    E beta[kExB];
 #pragma unroll
-    for (int bl = 0; bl < kExB; ++bl) beta[bl] = (inter && bl < nb) ? b1[(size_t)bl * A1.N + jj] : (T)0;
+    for (int bl = 0; bl < kExB; ++bl) beta[bl] = (inter && bl < nb) ? b1[(size_t)bl * A1.N + jj] : xz<E>();
     const int K = geo.K;
-    const int nval = 3 + nb;
-    T* o = out + (item * n1 + c) * (long long)nval * K;
+    const int nval = 3 + nb * (CPLX ? 2 : 1);
+    T* o = out + (item * A1.W + c) * (long long)nval * K;
     for (int jb = 0; jb < K; jb += blockDim.x) {
         const int j = jb + threadIdx.x;
         const T mu = j < K ? muT[j] : (T)1;
-        T gam[kExB];                            // P[bk][c] + sum_bl P[bk][bl] bhat1[bl][jj]
+        E gam[kExB];                            // P[bk][t] + sum_bl P[bk][bl] bhat1[bl][jj]
 #pragma unroll
         for (int bk = 0; bk < kExB; ++bk) {
-            gam[bk] = 0;
+            gam[bk] = xz<E>();
             if (bk < nb) {
                 const int ar = A0.bidx[bk];
-                T gv = pair_rcp(sa[ar] + mu) * sg[ar];
+                E gv = xs(sg[ar], pair_rcp(sa[ar] + mu));
 #pragma unroll
                 for (int bl = 0; bl < kExB; ++bl)
-                    if (bl < nb) gv += pair_rcp(sa[(1 + bl) * n0 + ar] + mu) * sg[(1 + bl) * n0 + ar] * beta[bl];
+                    if (bl < nb)
+                        gv = xa(gv, xm(xs(sg[(1 + bl) * n0 + ar], pair_rcp(sa[(1 + bl) * n0 + ar] + mu)), beta[bl]));
                 gam[bk] = gv;
             }
         }
-        T ww = 0, den = 0, s[kExB], sb[kExB][kExB];
+        T ww = 0, den = 0;
+        E s[kExB], sb[kExB][kExB];
 #pragma unroll
         for (int r = 0; r < kExB; ++r) {
-            s[r] = 0;
+            s[r] = xz<E>();
 #pragma unroll
-            for (int bl = 0; bl < kExB; ++bl) sb[r][bl] = 0;
+            for (int bl = 0; bl < kExB; ++bl) sb[r][bl] = xz<E>();
         }
         for (int a = 0; a < n0; ++a) {
             const T s0 = pair_rcp(sa[a] + mu);
-            const T P0 = s0 * sg[a];
+            const E P0 = xs(sg[a], s0);
             den += s0;
-            T Pb[kExB];
+            E Pb[kExB];
 #pragma unroll
             for (int bl = 0; bl < kExB; ++bl)
-                Pb[bl] = bl < nb ? pair_rcp(sa[(1 + bl) * n0 + a] + mu) * sg[(1 + bl) * n0 + a] : (T)0;
+                Pb[bl] = bl < nb ? xs(sg[(1 + bl) * n0 + a], pair_rcp(sa[(1 + bl) * n0 + a] + mu)) : xz<E>();
 #pragma unroll
             for (int r = 0; r < kExB; ++r)
                 if (r < nb) {
-                    const T v = __ldg(V0 + (size_t)r * n0 + a);
-                    s[r] += v * P0;
+                    const E v = V0[(size_t)r * n0 + a];
+                    s[r] = xa(s[r], xm(v, P0));
 #pragma unroll
                     for (int bl = 0; bl < kExB; ++bl)
-                        if (bl < nb) sb[r][bl] += v * Pb[bl];
+                        if (bl < nb) sb[r][bl] = xa(sb[r][bl], xm(v, Pb[bl]));
                 }
             if (inter && a >= k && a < n0 - k) {
                 const int i = a - k;
-                T w = P0;
+                E w = P0;
 #pragma unroll
                 for (int bl = 0; bl < kExB; ++bl)
-                    if (bl < nb) w += Pb[bl] * beta[bl];
+                    if (bl < nb) w = xa(w, xm(Pb[bl], beta[bl]));
 #pragma unroll
                 for (int bk = 0; bk < kExB; ++bk)
-                    if (bk < nb) w += __ldg(b0 + (size_t)bk * A0.N + i) * gam[bk];
-                ww += w * w;
+                    if (bk < nb) w = xa(w, xm(b0[(size_t)bk * A0.N + i], gam[bk]));
+                ww += abs2_of(w);
             }
         }
         T vw = 0;
@@ -228,33 +320,45 @@ k_ex_cols(const T* __restrict__ spec, const T* __restrict__ D, long long d_psf_s
 #pragma unroll
             for (int r = 0; r < kExB; ++r)
                 if (r < nb) {
-                    T v = s[r];
+                    E v = s[r];
 #pragma unroll
                     for (int bl = 0; bl < kExB; ++bl)
-                        if (bl < nb) v += sb[r][bl] * beta[bl];
-                    vw += v * v;
+                        if (bl < nb) v = xa(v, xm(sb[r][bl], beta[bl]));
+                    vw += abs2_of(v);
                 }
         if (j < K) {
-            o[j] = ww;
-            o[K + j] = vw;
-            o[2 * K + j] = den;
+            o[j] = wgt * ww;
+            o[K + j] = wgt * vw;
+            o[2 * K + j] = wgt * den;
 #pragma unroll
             for (int r = 0; r < kExB; ++r)
-                if (r < nb) o[(3 + r) * K + j] = s[r];
+                if (r < nb) {
+                    if constexpr (CPLX) {
+                        o[(3 + 2 * r) * K + j] = s[r].x;
+                        o[(4 + 2 * r) * K + j] = s[r].y;
+                    } else {
+                        o[(3 + r) * K + j] = s[r];
+                    }
+                }
         }
     }
 }
 
 // 2D, one CTA per spectral row a (entries c n0 + a), one grid value per
-// thread, with the border rows staged: for an interior row i = a - k,
-// wv = sum_r (W0 P V1^T)[i][r]^2 (0 on border rows).
-// grid = (n0, items), block = 256; dynamic shared memory 2 (1 + 2k) n1 sizeof(T).
-template <typename T>
+// thread, with the border rows (and, for the Fourier family, the partner row
+// -a) staged: for an interior row i = a - k, wv = sum_r |(W0 P V1^T)[i][r]|^2
+// (0 on border rows).  A stored Fourier column c that stands for a pair adds
+// its partner, P[a][-t] = conj(P[-a][t]), at V1's column -t.
+// grid = (n0, items), block <= 256;
+// dynamic shared memory (2 + 2k) W1 (sizeof(T) + sizeof(E)).
+template <typename T, bool CPLX>
 __global__ void __launch_bounds__(256)
-k_ex_rows(const T* __restrict__ spec, const T* __restrict__ D, long long d_psf_stride, int psf_per,
-          const T* __restrict__ muT, GcvGeom geo, ExAxis A0, ExAxis A1, int k, T* __restrict__ out) {
+k_ex_rows(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
+          long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo, ExAxis A0, ExAxis A1, int k,
+          T* __restrict__ out) {
+    typedef typename ElemT<T, CPLX>::t E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n0 = A0.n, n1 = A1.n, nb = 2 * k;
+    const int n0 = A0.n, n1 = A1.n, W1 = A1.W, nb = 2 * k;
     const int a = blockIdx.x;
     const long long item = blockIdx.y;
     const int K = geo.K;
@@ -263,90 +367,123 @@ k_ex_rows(const T* __restrict__ spec, const T* __restrict__ D, long long d_psf_s
         for (int j = threadIdx.x; j < K; j += blockDim.x) o[j] = 0;
         return;
     }
-    T* sa = reinterpret_cast<T*>(smem_raw);     // [1 + nb][n1]
-    T* sg = sa + (size_t)(1 + nb) * n1;
-    const T* sp = spec + item * geo.S;
-    const T* dp = D + (psf_per ? item : 0) * d_psf_stride;
-    for (int s = 0; s <= nb; ++s) {
-        const int row = s == 0 ? a : A0.bidx[s - 1];
-        for (int c = threadIdx.x; c < n1; c += blockDim.x)
-            ex_stage<T>(sp, dp, geo, (long long)c * n0 + row, sa[s * n1 + c], sg[s * n1 + c]);
+    const int ns = 2 + nb;                                        // own, borders, partner
+    E* sg = reinterpret_cast<E*>(smem_raw);                      // [ns][W1]
+    T* sa = reinterpret_cast<T*>(sg + (size_t)ns * W1);          // [ns][W1]
+    const E* sp = spec + item * geo.S;
+    const E* dp = D + (psf_per ? item : 0) * d_psf_stride;
+    for (int s = 0; s < ns; ++s) {
+        const int row = s == 0 ? a : (s <= nb ? A0.bidx[s - 1] : (CPLX ? hx_neg(a, n0) : a));
+        for (int c = threadIdx.x; c < W1; c += blockDim.x)
+            ex_stage<T, CPLX>(sp, dp, geo, (long long)c * n0 + row, sa[s * W1 + c], sg[s * W1 + c]);
     }
     __syncthreads();
-    const T* b0 = reinterpret_cast<const T*>(A0.bhat);
-    const T* V1 = reinterpret_cast<const T*>(A1.V);
+    const E* b0 = reinterpret_cast<const E*>(A0.bhat);
+    const E* V1 = reinterpret_cast<const E*>(A1.V);
     const int i = a - k;
-    T alpha[kExB];
+    E alpha[kExB];
 #pragma unroll
-    for (int bk = 0; bk < kExB; ++bk) alpha[bk] = bk < nb ? b0[(size_t)bk * A0.N + i] : (T)0;
+    for (int bk = 0; bk < kExB; ++bk) alpha[bk] = bk < nb ? b0[(size_t)bk * A0.N + i] : xz<E>();
     for (int jb = 0; jb < K; jb += blockDim.x) {
         const int j = jb + threadIdx.x;
         const T mu = j < K ? muT[j] : (T)1;
-        T u[kExB], ub[kExB][kExB];
+        E u[kExB], ub[kExB][kExB];
 #pragma unroll
         for (int r = 0; r < kExB; ++r) {
-            u[r] = 0;
+            u[r] = xz<E>();
 #pragma unroll
-            for (int bk = 0; bk < kExB; ++bk) ub[r][bk] = 0;
+            for (int bk = 0; bk < kExB; ++bk) ub[r][bk] = xz<E>();
         }
-        for (int c = 0; c < n1; ++c) {
-            const T P0 = pair_rcp(sa[c] + mu) * sg[c];
-            T Pb[kExB];
+        for (int c = 0; c < W1; ++c) {
+            const int t = CPLX ? hx_t(c, n1, W1) : c;
+            const E P0 = xs(sg[c], pair_rcp(sa[c] + mu));
+            E Pb[kExB];
 #pragma unroll
             for (int bk = 0; bk < kExB; ++bk)
-                Pb[bk] = bk < nb ? pair_rcp(sa[(1 + bk) * n1 + c] + mu) * sg[(1 + bk) * n1 + c] : (T)0;
+                Pb[bk] = bk < nb ? xs(sg[(1 + bk) * W1 + c], pair_rcp(sa[(1 + bk) * W1 + c] + mu)) : xz<E>();
 #pragma unroll
             for (int r = 0; r < kExB; ++r)
                 if (r < nb) {
-                    const T v = __ldg(V1 + (size_t)r * n1 + c);
-                    u[r] += v * P0;
+                    const E v = V1[(size_t)r * n1 + t];
+                    u[r] = xa(u[r], xm(v, P0));
 #pragma unroll
                     for (int bk = 0; bk < kExB; ++bk)
-                        if (bk < nb) ub[r][bk] += v * Pb[bk];
+                        if (bk < nb) ub[r][bk] = xa(ub[r][bk], xm(v, Pb[bk]));
                 }
+            if constexpr (CPLX) {
+                if (!hx_self(c, n1, W1)) {
+                    const int tn = hx_neg(t, n1);
+                    const E Pp = xc(xs(sg[(1 + nb) * W1 + c], pair_rcp(sa[(1 + nb) * W1 + c] + mu)));
+#pragma unroll
+                    for (int r = 0; r < kExB; ++r)
+                        if (r < nb) {
+                            const E v = V1[(size_t)r * n1 + tn];
+                            u[r] = xa(u[r], xm(v, Pp));
+#pragma unroll
+                            for (int bk = 0; bk < kExB; ++bk)     // border rows are their own partners
+                                if (bk < nb) ub[r][bk] = xa(ub[r][bk], xm(v, xc(Pb[bk])));
+                        }
+                }
+            }
         }
         T wv = 0;
 #pragma unroll
         for (int r = 0; r < kExB; ++r)
             if (r < nb) {
-                T v = u[r];
+                E v = u[r];
 #pragma unroll
                 for (int bk = 0; bk < kExB; ++bk)
-                    if (bk < nb) v += alpha[bk] * ub[r][bk];
-                wv += v * v;
+                    if (bk < nb) v = xa(v, xm(alpha[bk], ub[r][bk]));
+                wv += abs2_of(v);
             }
         if (j < K) o[j] = wv;
     }
 }
 
 // 2D: G_ex from the line sums.  Slot s of grid value j (lane) sums, in FP64,
-// the columns and rows = s mod kExSlots and its share of
-// (V0 P V1^T)[r][r'] = sum_c (V0 P)[r][c] V1[r'][c]; slot 0 adds the slots in
-// order.  num = ww + vw + wv + |V0 P V1^T|^2, G = num / den^2.
+// the stored columns and rows = s mod kExSlots and its share of
+// (V0 P V1^T)[r][r'] = sum over full columns of (V0 P)[r][t] V1[r'][t] (a
+// stored Fourier column that stands for a pair adds conj((V0 P)[r][c]) at
+// V1's column -t); slot 0 adds the slots in order.
+// num = ww + vw + wv + |V0 P V1^T|^2, G = num / den^2.
 // grid = (items, ceil(K / 32)), block = (32, kExSlots).
-template <typename T>
+template <typename T, bool CPLX>
 __global__ void __launch_bounds__(32 * kExSlots)
-k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, int n0, int n1, int k,
+k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, int n0, int n1, int W1, int k,
             const double* __restrict__ V1d, int K, double* __restrict__ G) {
     __shared__ double part[4][kExSlots][32];
-    __shared__ double vv[kExSlots][kExB * kExB][32];
+    __shared__ double vre[kExSlots][kExB * kExB][32], vim[kExSlots][kExB * kExB][32];
     const int lane = threadIdx.x, s = threadIdx.y;
     const int j = blockIdx.y * 32 + lane;
     const long long item = blockIdx.x;
-    const int nb = 2 * k, nval = 3 + nb;
-    double ww = 0, vw = 0, den = 0, wv = 0, m[kExB * kExB];
+    const int nb = 2 * k, nval = 3 + nb * (CPLX ? 2 : 1);
+    double ww = 0, vw = 0, den = 0, wv = 0, mr[kExB * kExB], mi[kExB * kExB];
 #pragma unroll
-    for (int q = 0; q < kExB * kExB; ++q) m[q] = 0;
+    for (int q = 0; q < kExB * kExB; ++q) { mr[q] = 0; mi[q] = 0; }
     if (j < K) {
-        const T* co = col_out + item * (long long)n1 * nval * K;
-        for (int c = s; c < n1; c += kExSlots) {
+        const T* co = col_out + item * (long long)W1 * nval * K;
+        for (int c = s; c < W1; c += kExSlots) {
             const T* oc = co + (long long)c * nval * K;
             ww += (double)oc[j];
             vw += (double)oc[K + j];
             den += (double)oc[2 * K + j];
+            const int t = CPLX ? hx_t(c, n1, W1) : c;
+            const bool pair = CPLX && !hx_self(c, n1, W1);
+            const int tn = pair ? hx_neg(t, n1) : t;
             for (int r = 0; r < nb; ++r) {
-                const double sv = (double)oc[(3 + r) * K + j];
-                for (int rr = 0; rr < nb; ++rr) m[r * kExB + rr] += sv * V1d[(size_t)rr * n1 + c];
+                const double sr = CPLX ? (double)oc[(3 + 2 * r) * K + j] : (double)oc[(3 + r) * K + j];
+                const double si = CPLX ? (double)oc[(4 + 2 * r) * K + j] : 0.0;
+                for (int rr = 0; rr < nb; ++rr) {
+                    const double vr = CPLX ? V1d[2 * ((size_t)rr * n1 + t)] : V1d[(size_t)rr * n1 + t];
+                    const double vi = CPLX ? V1d[2 * ((size_t)rr * n1 + t) + 1] : 0.0;
+                    mr[r * kExB + rr] += sr * vr - si * vi;
+                    mi[r * kExB + rr] += sr * vi + si * vr;
+                    if (pair) {                 // conj(s) at column -t
+                        const double pr = V1d[2 * ((size_t)rr * n1 + tn)], pim = V1d[2 * ((size_t)rr * n1 + tn) + 1];
+                        mr[r * kExB + rr] += sr * pr + si * pim;
+                        mi[r * kExB + rr] += sr * pim - si * pr;
+                    }
+                }
             }
         }
         const T* ro = row_out + item * (long long)n0 * K;
@@ -354,7 +491,7 @@ k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, int n0
     }
     part[0][s][lane] = ww; part[1][s][lane] = vw; part[2][s][lane] = den; part[3][s][lane] = wv;
 #pragma unroll
-    for (int q = 0; q < kExB * kExB; ++q) vv[s][q][lane] = m[q];
+    for (int q = 0; q < kExB * kExB; ++q) { vre[s][q][lane] = mr[q]; vim[s][q][lane] = mi[q]; }
     __syncthreads();
     if (s != 0 || j >= K) return;
     ww = vw = den = wv = 0;
@@ -363,61 +500,71 @@ k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, int n0
     }
     double vsq = 0;
     for (int q = 0; q < kExB * kExB; ++q) {
-        double acc = 0;
-        for (int t = 0; t < kExSlots; ++t) acc += vv[t][q][lane];
-        vsq += acc * acc;
+        double ar = 0, ai = 0;
+        for (int t = 0; t < kExSlots; ++t) { ar += vre[t][q][lane]; ai += vim[t][q][lane]; }
+        vsq += ar * ar + ai * ai;
     }
     G[item * K + j] = (ww + vw + wv + vsq) / (den * den);
 }
 
 // 1D: one CTA per problem, one grid value per thread:
-// num = sum_i (W P)[i]^2 + sum_r (V P)[r]^2, G = num / (sum sigma)^2.
-// grid = items, block = 256; dynamic shared memory 2 n sizeof(T).
-template <typename T>
+// num = sum_i |(W P)[i]|^2 + sum_r |(V P)[r]|^2, G = num / (sum sigma)^2 (Fourier
+// half spectrum: pair weights on the first two sums, partner entries in V P).
+// grid = items, block <= 256; dynamic shared memory W (sizeof(T) + sizeof(E)).
+template <typename T, bool CPLX>
 __global__ void __launch_bounds__(256)
-k_ex_1d(const T* __restrict__ spec, const T* __restrict__ D, long long d_psf_stride, int psf_per,
-        const T* __restrict__ muT, GcvGeom geo, ExAxis A0, int k, double* __restrict__ G) {
+k_ex_1d(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
+        long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo, ExAxis A0, int k,
+        double* __restrict__ G) {
+    typedef typename ElemT<T, CPLX>::t E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n = A0.n, nb = 2 * k;
-    T* sa = reinterpret_cast<T*>(smem_raw);
-    T* sg = sa + n;
+    const int n = A0.n, W = A0.W, nb = 2 * k;
+    E* sg = reinterpret_cast<E*>(smem_raw);
+    T* sa = reinterpret_cast<T*>(sg + W);
     const long long item = blockIdx.x;
-    const T* sp = spec + item * geo.S;
-    const T* dp = D + (psf_per ? item : 0) * d_psf_stride;
-    for (int a = threadIdx.x; a < n; a += blockDim.x) ex_stage<T>(sp, dp, geo, a, sa[a], sg[a]);
+    const E* sp = spec + item * geo.S;
+    const E* dp = D + (psf_per ? item : 0) * d_psf_stride;
+    for (int c = threadIdx.x; c < W; c += blockDim.x) ex_stage<T, CPLX>(sp, dp, geo, c, sa[c], sg[c]);
     __syncthreads();
-    const T* b0 = reinterpret_cast<const T*>(A0.bhat);
-    const T* V0 = reinterpret_cast<const T*>(A0.V);
+    const E* b0 = reinterpret_cast<const E*>(A0.bhat);
+    const E* V0 = reinterpret_cast<const E*>(A0.V);
     const int K = geo.K;
     for (int jb = 0; jb < K; jb += blockDim.x) {
         const int j = jb + threadIdx.x;
         const T mu = j < K ? muT[j] : (T)1;
-        T pb[kExB];
+        E pb[kExB];
 #pragma unroll
         for (int b = 0; b < kExB; ++b)
-            pb[b] = b < nb ? pair_rcp(sa[A0.bidx[b]] + mu) * sg[A0.bidx[b]] : (T)0;
-        T ww = 0, den = 0, s[kExB];
+            pb[b] = b < nb ? xs(sg[A0.bcol[b]], pair_rcp(sa[A0.bcol[b]] + mu)) : xz<E>();
+        T ww = 0, den = 0;
+        E s[kExB];
 #pragma unroll
-        for (int r = 0; r < kExB; ++r) s[r] = 0;
-        for (int a = 0; a < n; ++a) {
-            const T s0 = pair_rcp(sa[a] + mu);
-            const T P0 = s0 * sg[a];
-            den += s0;
+        for (int r = 0; r < kExB; ++r) s[r] = xz<E>();
+        for (int c = 0; c < W; ++c) {
+            const int t = CPLX ? hx_t(c, n, W) : c;
+            const bool pair = CPLX && !hx_self(c, n, W);
+            const T wg = pair ? (T)2 : (T)1;
+            const T s0 = pair_rcp(sa[c] + mu);
+            const E P0 = xs(sg[c], s0);
+            den += wg * s0;
 #pragma unroll
             for (int r = 0; r < kExB; ++r)
-                if (r < nb) s[r] += __ldg(V0 + (size_t)r * n + a) * P0;
-            if (a >= k && a < n - k) {
-                T w = P0;
+                if (r < nb) {
+                    s[r] = xa(s[r], xm(V0[(size_t)r * n + t], P0));
+                    if (pair) s[r] = xa(s[r], xm(V0[(size_t)r * n + hx_neg(t, n)], xc(P0)));
+                }
+            if (t >= k && t < n - k) {
+                E w = P0;
 #pragma unroll
                 for (int b = 0; b < kExB; ++b)
-                    if (b < nb) w += __ldg(b0 + (size_t)b * A0.N + (a - k)) * pb[b];
-                ww += w * w;
+                    if (b < nb) w = xa(w, xm(b0[(size_t)b * A0.N + (t - k)], pb[b]));
+                ww += wg * abs2_of(w);
             }
         }
         T vsq = 0;
 #pragma unroll
         for (int r = 0; r < kExB; ++r)
-            if (r < nb) vsq += s[r] * s[r];
+            if (r < nb) vsq += abs2_of(s[r]);
         if (j < K) G[item * K + j] = ((double)ww + (double)vsq) / ((double)den * (double)den);
     }
 }
@@ -465,7 +612,7 @@ void exact_free(hobc_plan_s* p) {
 namespace {
 
 int border_count(int fam) {
-    if (fam == HOBC_FAMILY_SINE || fam == HOBC_FAMILY_COSINE) return 1;
+    if (fam == HOBC_FAMILY_SINE || fam == HOBC_FAMILY_COSINE || fam == HOBC_FAMILY_FOURIER) return 1;
     if (fam == HOBC_FAMILY_SINE_CUBIC) return 2;
     if (fam == HOBC_FAMILY_REFLECTIVE || fam == HOBC_FAMILY_PERIODIC) return 0;   // T orthogonal
     return -1;
@@ -476,33 +623,35 @@ hobc_status ensure_exact(hobc_plan_s* p) {
     if (p->exact) return HOBC_OK;
     const int k = border_count(p->fam);
     if (k < 0) {
-        set_last_error_text("hobc_gcv_exact: real families only (the Fourier family's T_F is complex)");
+        set_last_error_text("hobc_gcv_exact: unsupported family");
         return HOBC_ERR_UNSUPPORTED;
     }
     hobc_exact_s* x = new hobc_exact_s();
     p->exact = x;
     x->k = k;
+    x->cplx = p->fam == HOBC_FAMILY_FOURIER;
     const bool fp64 = p->prec == HOBC_FP64;
     cudaError_t e = cudaSuccess;
     for (int a = 0; a < p->nax; ++a) {
         const int n = p->ax[a].n;
         x->N[a] = n - 2 * k;
         for (int b = 0; b < 2 * k; ++b) x->bidx[a][b] = b < k ? b : n - 2 * k + b;
-        std::vector<double> bhat(1, 0.0), V(1, 0.0);
+        std::vector<cdx> bhat(1, cdx(0, 0)), V(1, cdx(0, 0));
         if (k > 0) {
-            std::vector<double> Tm;
+            std::vector<cdx> Tm;
             hobc_status s = axis_matrix(p->fam, n, p->stream, Tm);
             if (s == HOBC_OK) s = split_rows(Tm, n, k, bhat, V);
             if (s != HOBC_OK) { exact_free(p); return s; }
         }
-        if (e == cudaSuccess) e = fp64 ? upload<double>(&x->bhat[a], bhat) : upload<float>(&x->bhat[a], bhat);
-        if (e == cudaSuccess) e = fp64 ? upload<double>(&x->V[a], V) : upload<float>(&x->V[a], V);
-        if (e == cudaSuccess) e = upload<double>((void**)&x->Vd[a], V);
+        if (e == cudaSuccess) e = fp64 ? upload<double>(&x->bhat[a], bhat, x->cplx) : upload<float>(&x->bhat[a], bhat, x->cplx);
+        if (e == cudaSuccess) e = fp64 ? upload<double>(&x->V[a], V, x->cplx) : upload<float>(&x->V[a], V, x->cplx);
+        if (e == cudaSuccess) e = upload<double>(&x->Vd[a], V, x->cplx);
     }
     const size_t B = (size_t)p->desc.batch, K = (size_t)p->K;
     if (p->nax == 2) {
-        const size_t n0 = (size_t)p->ax[0].n, n1 = (size_t)p->ax[1].n;
-        if (e == cudaSuccess) e = cudaMalloc(&x->col_out, B * n1 * (3 + 2 * k) * K * p->esz);
+        const size_t n0 = (size_t)p->ax[0].n, W1 = (size_t)p->ax[1].W;
+        const size_t nval = 3 + 2 * (size_t)k * (x->cplx ? 2 : 1);
+        if (e == cudaSuccess) e = cudaMalloc(&x->col_out, B * W1 * nval * K * p->esz);
         if (e == cudaSuccess) e = cudaMalloc(&x->row_out, B * n0 * K * p->esz);
     }
     if (e == cudaSuccess) e = cudaMalloc((void**)&x->G, B * K * sizeof(double));
@@ -521,42 +670,48 @@ ExAxis ex_axis(const hobc_exact_s* x, const hobc_plan_s* p, int a) {
     A.V = x->V[a];
     A.n = p->ax[a].n;
     A.N = x->N[a];
-    for (int b = 0; b < 2 * x->k; ++b) A.bidx[b] = x->bidx[a][b];
+    A.W = p->ax[a].W;
+    for (int b = 0; b < 2 * x->k; ++b) {
+        A.bidx[b] = x->bidx[a][b];
+        A.bcol[b] = (x->cplx && a == p->nax - 1 && A.bidx[b] == A.n - 1) ? A.W - 1 : A.bidx[b];
+    }
     return A;
 }
 
-template <typename T>
+template <typename T, bool CPLX>
 hobc_status run_gcv_exact(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx) {
+    typedef typename ElemT<T, CPLX>::t E;
     hobc_exact_s* x = p->exact;
     GcvGeom geo = exact_geo(p);
     const int B = p->desc.batch, K = p->K, k = x->k;
-    const T* sp = reinterpret_cast<const T*>(ghat);
-    const T* dp = reinterpret_cast<const T*>(D);
+    const E* sp = reinterpret_cast<const E*>(ghat);
+    const E* dp = reinterpret_cast<const E*>(D);
     const T* muT = reinterpret_cast<const T*>(p->muT);
     const long long dps = (long long)p->spec_elems;
     double* Gout = gcv ? gcv : x->G;
     const int threads = std::min(256, (K + 31) / 32 * 32);
+    const size_t el = sizeof(T) + sizeof(E);
     cudaError_t e = cudaSuccess;
     if (p->nax == 1) {
-        const int n = p->ax[0].n;
-        k_ex_1d<T><<<B, threads, 2 * (size_t)n * sizeof(T), p->stream>>>(sp, dp, dps, p->desc.psf_per_item, muT, geo,
-                                                                          ex_axis(x, p, 0), k, Gout);
+        const ExAxis A0 = ex_axis(x, p, 0);
+        k_ex_1d<T, CPLX><<<B, threads, (size_t)A0.W * el, p->stream>>>(sp, dp, dps, p->desc.psf_per_item, muT, geo, A0,
+                                                                      k, Gout);
         p->launches += 1;
     } else {
-        const int n0 = p->ax[0].n, n1 = p->ax[1].n;
-        const size_t sc = 2 * (size_t)(1 + 2 * k) * n0 * sizeof(T), sr = 2 * (size_t)(1 + 2 * k) * n1 * sizeof(T);
-        e = cudaFuncSetAttribute(k_ex_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_ex_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
-        if (e != cudaSuccess) { set_last_error("hobc_gcv_exact", e); return HOBC_ERR_CUDA; }
         const ExAxis A0 = ex_axis(x, p, 0), A1 = ex_axis(x, p, 1);
-        k_ex_cols<T><<<dim3((unsigned)n1, (unsigned)B), threads, sc, p->stream>>>(
+        const int n0 = A0.n, n1 = A1.n, W1 = A1.W;
+        const size_t sc = (size_t)(1 + 2 * k) * n0 * el, sr = (size_t)(2 + 2 * k) * W1 * el;
+        e = cudaFuncSetAttribute(k_ex_cols<T, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_ex_rows<T, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
+        if (e != cudaSuccess) { set_last_error("hobc_gcv_exact", e); return HOBC_ERR_CUDA; }
+        k_ex_cols<T, CPLX><<<dim3((unsigned)W1, (unsigned)B), threads, sc, p->stream>>>(
             sp, dp, dps, p->desc.psf_per_item, muT, geo, A0, A1, k, reinterpret_cast<T*>(x->col_out));
-        k_ex_rows<T><<<dim3((unsigned)n0, (unsigned)B), threads, sr, p->stream>>>(
+        k_ex_rows<T, CPLX><<<dim3((unsigned)n0, (unsigned)B), threads, sr, p->stream>>>(
             sp, dp, dps, p->desc.psf_per_item, muT, geo, A0, A1, k, reinterpret_cast<T*>(x->row_out));
-        k_ex_reduce<T><<<dim3((unsigned)B, (unsigned)((K + 31) / 32)), dim3(32, kExSlots), 0, p->stream>>>(
-            reinterpret_cast<const T*>(x->col_out), reinterpret_cast<const T*>(x->row_out), n0, n1, k, x->Vd[1], K,
-            Gout);
+        k_ex_reduce<T, CPLX><<<dim3((unsigned)B, (unsigned)((K + 31) / 32)), dim3(32, kExSlots), 0, p->stream>>>(
+            reinterpret_cast<const T*>(x->col_out), reinterpret_cast<const T*>(x->row_out), n0, n1, W1, k,
+            reinterpret_cast<const double*>(x->Vd[1]), K, Gout);
         p->launches += 3;
     }
     k_ex_argmin<<<B, 256, 0, p->stream>>>(Gout, K, mu_idx);
@@ -567,8 +722,10 @@ hobc_status run_gcv_exact(hobc_plan_s* p, const void* ghat, const void* D, doubl
 }
 
 hobc_status gcv_exact_dispatch(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx) {
-    return p->prec == HOBC_FP64 ? run_gcv_exact<double>(p, ghat, D, gcv, mu_idx)
-                                : run_gcv_exact<float>(p, ghat, D, gcv, mu_idx);
+    const bool F = p->exact->cplx;
+    if (p->prec == HOBC_FP64)
+        return F ? run_gcv_exact<double, true>(p, ghat, D, gcv, mu_idx) : run_gcv_exact<double, false>(p, ghat, D, gcv, mu_idx);
+    return F ? run_gcv_exact<float, true>(p, ghat, D, gcv, mu_idx) : run_gcv_exact<float, false>(p, ghat, D, gcv, mu_idx);
 }
 
 }  // namespace

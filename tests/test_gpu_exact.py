@@ -28,7 +28,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 from paper_0906_2704_gb300 import hobc  # noqa: E402
 
-DEG = {"sine": 1, "cosine": 2, "sine3": 3}
+DEG = {"sine": 1, "cosine": 2, "fourier": 2, "sine3": 3}
 
 
 def _dev(a, dtype):
@@ -36,7 +36,16 @@ def _dev(a, dtype):
 
 
 def _round(x, dt):
+    if np.iscomplexobj(x):
+        return x.real.astype(dt).astype(np.float64) + 1j * x.imag.astype(dt).astype(np.float64)
     return x.astype(dt).astype(np.float64)
+
+
+def _spec(a, dt, cplx):
+    """Stored-layout spectra -> device tensor (interleaved pairs for the Fourier family)."""
+    if cplx:
+        return _dev(np.stack([a.real, a.imag], axis=-1), dt)
+    return _dev(a.real, dt)
 
 
 def _bound(F, n, gr, dr, s, mus, prec):
@@ -69,29 +78,31 @@ def _case(ndim, fam, prec, L, K=40, batch=3, seed=2):
     h = _round(h / h.sum(), dt)
     g, ft = P.problems(ndim, n, h, batch, seed, 0.01)
     g = _round(g, dt)
-    plan = hobc.Plan(ndim, n, h.shape, DEG[fam], mus, L=L, prec=prec, family=fam, psf_symmetric=True, batch=batch)
+    plan = hobc.Plan(ndim, n, h.shape, DEG[fam], mus, L=L, prec=prec, family=fam, psf_symmetric=F != "F",
+                     batch=batch)
     return F, dt, mus, n, h, g, ft, plan
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("L", ["I", "lap"])
-@pytest.mark.parametrize("fam", ["sine", "cosine", "sine3"])
+@pytest.mark.parametrize("fam", ["sine", "cosine", "fourier", "sine3"])
 @pytest.mark.parametrize("ndim", [1, 2])
 def test_exact_curve_matches_oracle_on_identical_inputs(ndim, fam, L, prec):
     F, dt, mus, n, h, g, _, plan = _case(ndim, fam, prec, L)
     batch, K = g.shape[0], len(mus)
-    gin = np.zeros((batch, plan.spec_elems))
-    din = np.zeros((1, plan.spec_elems))
+    cplx = plan.spec_complex
+    gin = np.zeros((batch, plan.spec_elems), dtype=complex)
+    din = np.zeros((1, plan.spec_elems), dtype=complex)
     full = []
     for b in range(batch):
         ghat, d, s, _, _ = P.oracle_steps(F, ndim, h, g[b], L, mus)
-        gr, dr = _round(ghat.real, dt), _round(d.real, dt)
+        gr, dr = _round(ghat if cplx else ghat.real, dt), _round(d if cplx else d.real, dt)
         full.append((gr, dr, s))
         gin[b] = P.to_layout(F, gr).reshape(-1)
         din[0] = P.to_layout(F, dr).reshape(-1)
     G_d = torch.empty((batch, K), dtype=torch.float64, device="cuda")
     mi_d = torch.empty(batch, dtype=torch.int32, device="cuda")
-    plan.gcv_exact(_dev(gin, dt), _dev(din, dt), G_d, mi_d)
+    plan.gcv_exact(_spec(gin, dt, cplx), _spec(din, dt, cplx), G_d, mi_d)
     G, mi = G_d.cpu().numpy(), mi_d.cpu().numpy()
     for b, (gr, dr, s) in enumerate(full):
         Go = X.gcv_exact_curve(F, gr, dr, s, mus)
@@ -103,7 +114,7 @@ def test_exact_curve_matches_oracle_on_identical_inputs(ndim, fam, L, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("fam", ["sine", "cosine"])
+@pytest.mark.parametrize("fam", ["sine", "cosine", "fourier"])
 def test_deblur_exact_composes_the_steps(fam, prec):
     F, dt, mus, n, h, g, _, plan = _case(2, fam, prec, "lap", batch=4, seed=7)
     batch = g.shape[0]
@@ -113,8 +124,9 @@ def test_deblur_exact_composes_the_steps(fam, prec):
     m1 = torch.empty(batch, dtype=torch.int32, device="cuda")
     G1 = torch.empty((batch, len(mus)), dtype=torch.float64, device="cuda")
     plan.deblur_exact(g_d, h_d, f1, m1, G1)
-    gh = torch.empty((batch, plan.spec_elems), dtype=tdt, device="cuda")
-    dd = torch.empty((1, plan.spec_elems), dtype=tdt, device="cuda")
+    cs = (2,) if plan.spec_complex else ()
+    gh = torch.empty((batch, plan.spec_elems) + cs, dtype=tdt, device="cuda")
+    dd = torch.empty((1, plan.spec_elems) + cs, dtype=tdt, device="cuda")
     plan.analysis(g_d, gh)
     plan.eigenvalues(h_d, dd)
     G2 = torch.empty_like(G1)
@@ -145,15 +157,6 @@ def test_orthogonal_conditions_give_the_approximate_functional():
         assert torch.allclose(Gx, Ga, rtol=2e-5, atol=0), fam
 
 
-def test_fourier_family_is_unsupported():
-    plan = hobc.Plan(2, (32, 32), (5, 5), 2, synth.mu_grid(8), prec="fp64", family="fourier")
-    t = torch.zeros(plan.spec_elems * 2, dtype=torch.float64, device="cuda")
-    mi = torch.zeros(1, dtype=torch.int32, device="cuda")
-    with pytest.raises(hobc.HobcError) as e:
-        plan.gcv_exact(t, t, None, mi)
-    assert e.value.status == hobc.STATUS.index("HOBC_ERR_UNSUPPORTED")
-
-
 def test_full_size_1024_cosine_fp32_at_sampled_mu():
     """The dense-workload shape (1024 x 1024, cosine family, Laplacian, 256 mu) on
     identical inputs: G_ex at five grid values against the oracle's dense
@@ -175,5 +178,29 @@ def test_full_size_1024_cosine_fp32_at_sampled_mu():
     js = [0, 40, 85, 170, 255]
     Go = X.gcv_exact_curve("C", ghat, d, s, mus[js])
     bound = _bound("C", n, ghat, d, s, mus[js], "fp32")
+    rel = np.abs(G_d.cpu().numpy()[0, js] - Go) / Go
+    assert np.all(rel <= bound), f"{rel} > {bound}"
+
+
+def test_full_size_1024_fourier_fp32_at_sampled_mu():
+    """The bench's headline shape (1024 x 1024, Fourier family, nonsymmetric rotated
+    Gaussian, L = I, 256 mu) on identical inputs: G_ex at three grid values against
+    the oracle's dense complex evaluation there (half spectrum on the GPU)."""
+    n = (1024, 1024)
+    h = synth.gaussian_psf_2d_rotated(3.0, 1.5, 30.0, 21, 2.0, -1.0).astype(np.float32).astype(np.float64)
+    g, _ = synth.problem_2d(12, n[0], n[1], h, 0.005, count=1)
+    g = g[0].astype(np.float32).astype(np.float64)
+    mus = synth.mu_grid(256)
+    plan = hobc.Plan(2, n, h.shape, 2, mus, L="I", prec="fp32", family="fourier", batch=1)
+    ghat = _round(O.analysis_2d("F", g), np.float32)
+    d = _round(O.eigenvalues_2d("F", h, n[0], n[1]), np.float32)
+    s = O.smoothing_2d("F", n[0], n[1], "I")
+    G_d = torch.empty((1, 256), dtype=torch.float64, device="cuda")
+    mi = torch.empty(1, dtype=torch.int32, device="cuda")
+    plan.gcv_exact(_spec(P.to_layout("F", ghat).reshape(1, -1), np.float32, True),
+                   _spec(P.to_layout("F", d).reshape(1, -1), np.float32, True), G_d, mi)
+    js = [0, 128, 255]
+    Go = X.gcv_exact_curve("F", ghat, d, s, mus[js])
+    bound = _bound("F", n, ghat, d, s, mus[js], "fp32")
     rel = np.abs(G_d.cpu().numpy()[0, js] - Go) / Go
     assert np.all(rel <= bound), f"{rel} > {bound}"
