@@ -34,8 +34,8 @@ struct hobc_exact_s {
     void* bhat[2];         // [2k][N_a] plan precision (complex for the Fourier family)
     void* V[2];            // [2k][n_a] plan precision: the extension rows of T_a
     void* Vd[2];           // [2k][n_a] FP64 copy of V_a (the V_0 P V_1^T term)
-    void* col_out;         // [batch][stored columns][3 + 2k (x2 complex)][K]
-    void* row_out;         // [batch][n_0][K]: |W0 P V1^T row|^2
+    void* col_out;         // [batch][stored columns][2 + 2k (x2 complex)][K]: ww, den, (V0 P)[r][c]
+    void* row_out;         // [batch][n_0][2k (x2 complex)][K]: (P V1^T)[a][r]
     double* G;             // [batch][K] when the caller passes no curve
 };
 
@@ -44,6 +44,7 @@ namespace hobc {
 constexpr int kExKMax = 2;             // border vectors per side at most (degree 3)
 constexpr int kExB = 2 * kExKMax;
 constexpr int kExSlots = 4;            // reduction: line slices per grid value
+constexpr int kExCB = 4;               // stored columns per CTA of the column pass
 
 // ------------------------------------------------- real or complex entries
 __device__ __forceinline__ float xm(float a, float b) { return a * b; }
@@ -219,15 +220,15 @@ __device__ __forceinline__ void ex_stage(const typename ElemT<T, CPLX>::t* sp, c
     g = live ? sp[e] : xz<E>();
 }
 
-// 2D, one CTA per stored spectral column c (entries c n0 + a), one grid value
-// per thread, with the border columns staged.  For an interior column
-// (spectral index t, j = t - k):
-//   ww = sum_i |(W0 P W1^T)[i][j]|^2,  vw = sum_r |(V0 P W1^T)[r][j]|^2;
-// for every column: den = sum sigma and the projections (V0 P)[r][c].  The
-// sums carry the column's pair weight (2 for a stored Fourier column that
-// stands for a conjugate pair).
-// grid = (stored columns, items), block <= 256;
-// dynamic shared memory (1 + 2k) n0 (sizeof(T) + sizeof(E)).
+// 2D, one CTA per kExCB consecutive stored spectral columns (entries
+// c n0 + a), one grid value per thread, with the border columns staged once
+// for all of them.  Per column (spectral index t): for an interior column
+// (j = t - k), ww = sum_i |(W0 P W1^T)[i][j]|^2; for every column, den =
+// sum sigma and the projections (V0 P)[r][c].  ww and den carry the column's
+// pair weight (2 for a stored Fourier column that stands for a conjugate
+// pair).  The V0 P W1^T term is formed from the projections in k_ex_reduce.
+// grid = (ceil(stored columns / kExCB), items), block <= 256;
+// dynamic shared memory (kExCB + 2k) n0 (sizeof(T) + sizeof(E)).
 template <typename T, bool CPLX>
 __global__ void __launch_bounds__(256)
 k_ex_cols(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
@@ -235,122 +236,127 @@ k_ex_cols(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
           T* __restrict__ out) {
     typedef typename ElemT<T, CPLX>::t E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n0 = A0.n, n1 = A1.n, nb = 2 * k;
-    E* sg = reinterpret_cast<E*>(smem_raw);                      // [1 + nb][n0]
-    T* sa = reinterpret_cast<T*>(sg + (size_t)(1 + nb) * n0);     // [1 + nb][n0]
-    const int c = blockIdx.x;
+    __shared__ E sbeta[kExCB][kExB];
+    const int n0 = A0.n, n1 = A1.n, W1 = A1.W, nb = 2 * k, ns = kExCB + nb;
+    E* sg = reinterpret_cast<E*>(smem_raw);                      // [ns][n0]
+    T* sa = reinterpret_cast<T*>(sg + (size_t)ns * n0);          // [ns][n0]
+    const int c0 = blockIdx.x * kExCB;
     const long long item = blockIdx.y;
     const E* sp = spec + item * geo.S;
     const E* dp = D + (psf_per ? item : 0) * d_psf_stride;
-    for (int s = 0; s <= nb; ++s) {
-        const int col = s == 0 ? c : A1.bcol[s - 1];
+    for (int s = 0; s < ns; ++s) {
+        const int col = s < kExCB ? min(c0 + s, W1 - 1) : A1.bcol[s - kExCB];
         for (int a = threadIdx.x; a < n0; a += blockDim.x)
             ex_stage<T, CPLX>(sp, dp, geo, (long long)col * n0 + a, sa[s * n0 + a], sg[s * n0 + a]);
     }
+    const E* b1 = reinterpret_cast<const E*>(A1.bhat);
+    if (threadIdx.x < kExCB * kExB) {
+        const int q = threadIdx.x / kExB, bl = threadIdx.x % kExB;
+        const int t = CPLX ? hx_t(min(c0 + q, W1 - 1), n1, W1) : min(c0 + q, W1 - 1);
+        sbeta[q][bl] = (bl < nb && t >= k && t < n1 - k) ? b1[(size_t)bl * A1.N + (t - k)] : xz<E>();
+    }
     __syncthreads();
     const E* b0 = reinterpret_cast<const E*>(A0.bhat);
-    const E* b1 = reinterpret_cast<const E*>(A1.bhat);
     const E* V0 = reinterpret_cast<const E*>(A0.V);
-    const int t = CPLX ? hx_t(c, n1, A1.W) : c;
-    const T wgt = (CPLX && !hx_self(c, n1, A1.W)) ? (T)2 : (T)1;
-    const bool inter = t >= k && t < n1 - k;
-    const int jj = t - k;
-    E beta[kExB];
+    int tq[kExCB];
+    bool inter[kExCB];
 #pragma unroll
-    for (int bl = 0; bl < kExB; ++bl) beta[bl] = (inter && bl < nb) ? b1[(size_t)bl * A1.N + jj] : xz<E>();
+    for (int q = 0; q < kExCB; ++q) {
+        const int cq = min(c0 + q, W1 - 1);
+        tq[q] = CPLX ? hx_t(cq, n1, W1) : cq;
+        inter[q] = c0 + q < W1 && tq[q] >= k && tq[q] < n1 - k;
+    }
     const int K = geo.K;
-    const int nval = 3 + nb * (CPLX ? 2 : 1);
-    T* o = out + (item * A1.W + c) * (long long)nval * K;
+    const int nval = 2 + nb * (CPLX ? 2 : 1);
     for (int jb = 0; jb < K; jb += blockDim.x) {
         const int j = jb + threadIdx.x;
         const T mu = j < K ? muT[j] : (T)1;
-        E gam[kExB];                            // P[bk][t] + sum_bl P[bk][bl] bhat1[bl][jj]
+        E gam[kExCB][kExB];                    // P[bk][t] + sum_bl P[bk][bl] bhat1[bl][j(t)]
 #pragma unroll
         for (int bk = 0; bk < kExB; ++bk) {
-            gam[bk] = xz<E>();
-            if (bk < nb) {
-                const int ar = A0.bidx[bk];
-                E gv = xs(sg[ar], pair_rcp(sa[ar] + mu));
-#pragma unroll
-                for (int bl = 0; bl < kExB; ++bl)
-                    if (bl < nb)
-                        gv = xa(gv, xm(xs(sg[(1 + bl) * n0 + ar], pair_rcp(sa[(1 + bl) * n0 + ar] + mu)), beta[bl]));
-                gam[bk] = gv;
-            }
-        }
-        T ww = 0, den = 0;
-        E s[kExB], sb[kExB][kExB];
-#pragma unroll
-        for (int r = 0; r < kExB; ++r) {
-            s[r] = xz<E>();
-#pragma unroll
-            for (int bl = 0; bl < kExB; ++bl) sb[r][bl] = xz<E>();
-        }
-        for (int a = 0; a < n0; ++a) {
-            const T s0 = pair_rcp(sa[a] + mu);
-            const E P0 = xs(sg[a], s0);
-            den += s0;
-            E Pb[kExB];
+            E corner[kExB];
+            const int ar = bk < nb ? A0.bidx[bk] : 0;
 #pragma unroll
             for (int bl = 0; bl < kExB; ++bl)
-                Pb[bl] = bl < nb ? xs(sg[(1 + bl) * n0 + a], pair_rcp(sa[(1 + bl) * n0 + a] + mu)) : xz<E>();
+                corner[bl] = (bk < nb && bl < nb)
+                                 ? xs(sg[(kExCB + bl) * n0 + ar], pair_rcp(sa[(kExCB + bl) * n0 + ar] + mu)) : xz<E>();
 #pragma unroll
-            for (int r = 0; r < kExB; ++r)
-                if (r < nb) {
-                    const E v = V0[(size_t)r * n0 + a];
-                    s[r] = xa(s[r], xm(v, P0));
+            for (int q = 0; q < kExCB; ++q) {
+                E gv = xz<E>();
+                if (bk < nb) {
+                    gv = xs(sg[q * n0 + ar], pair_rcp(sa[q * n0 + ar] + mu));
 #pragma unroll
                     for (int bl = 0; bl < kExB; ++bl)
-                        if (bl < nb) sb[r][bl] = xa(sb[r][bl], xm(v, Pb[bl]));
+                        if (bl < nb) gv = xa(gv, xm(corner[bl], sbeta[q][bl]));
                 }
-            if (inter && a >= k && a < n0 - k) {
-                const int i = a - k;
-                E w = P0;
-#pragma unroll
-                for (int bl = 0; bl < kExB; ++bl)
-                    if (bl < nb) w = xa(w, xm(Pb[bl], beta[bl]));
-#pragma unroll
-                for (int bk = 0; bk < kExB; ++bk)
-                    if (bk < nb) w = xa(w, xm(b0[(size_t)bk * A0.N + i], gam[bk]));
-                ww += abs2_of(w);
+                gam[q][bk] = gv;
             }
         }
-        T vw = 0;
-        if (inter)
+        T ww[kExCB], den[kExCB];
+        E s[kExCB][kExB];
 #pragma unroll
-            for (int r = 0; r < kExB; ++r)
-                if (r < nb) {
-                    E v = s[r];
+        for (int q = 0; q < kExCB; ++q) {
+            ww[q] = 0;
+            den[q] = 0;
 #pragma unroll
-                    for (int bl = 0; bl < kExB; ++bl)
-                        if (bl < nb) v = xa(v, xm(sb[r][bl], beta[bl]));
-                    vw += abs2_of(v);
-                }
-        if (j < K) {
-            o[j] = wgt * ww;
-            o[K + j] = wgt * vw;
-            o[2 * K + j] = wgt * den;
-#pragma unroll
-            for (int r = 0; r < kExB; ++r)
-                if (r < nb) {
-                    if constexpr (CPLX) {
-                        o[(3 + 2 * r) * K + j] = s[r].x;
-                        o[(4 + 2 * r) * K + j] = s[r].y;
-                    } else {
-                        o[(3 + r) * K + j] = s[r];
-                    }
-                }
+            for (int r = 0; r < kExB; ++r) s[q][r] = xz<E>();
         }
+        for (int a = 0; a < n0; ++a) {
+            E Pb[kExB], v0[kExB], bb[kExB];
+#pragma unroll
+            for (int b = 0; b < kExB; ++b) {
+                Pb[b] = b < nb ? xs(sg[(kExCB + b) * n0 + a], pair_rcp(sa[(kExCB + b) * n0 + a] + mu)) : xz<E>();
+                v0[b] = b < nb ? V0[(size_t)b * n0 + a] : xz<E>();
+            }
+            const bool ai = a >= k && a < n0 - k;
+#pragma unroll
+            for (int b = 0; b < kExB; ++b) bb[b] = (ai && b < nb) ? b0[(size_t)b * A0.N + (a - k)] : xz<E>();
+#pragma unroll
+            for (int q = 0; q < kExCB; ++q) {
+                const T s0 = pair_rcp(sa[q * n0 + a] + mu);
+                const E P0 = xs(sg[q * n0 + a], s0);
+                den[q] += s0;
+#pragma unroll
+                for (int r = 0; r < kExB; ++r)
+                    if (r < nb) s[q][r] = xa(s[q][r], xm(v0[r], P0));
+                if (inter[q] && ai) {
+                    E w = P0;
+#pragma unroll
+                    for (int b = 0; b < kExB; ++b)
+                        if (b < nb) w = xa(xa(w, xm(Pb[b], sbeta[q][b])), xm(bb[b], gam[q][b]));
+                    ww[q] += abs2_of(w);
+                }
+            }
+        }
+        if (j < K)
+#pragma unroll
+            for (int q = 0; q < kExCB; ++q) {
+                const int c = c0 + q;
+                if (c >= W1) continue;
+                const T wgt = (CPLX && !hx_self(c, n1, W1)) ? (T)2 : (T)1;
+                T* o = out + (item * W1 + c) * (long long)nval * K;
+                o[j] = wgt * ww[q];
+                o[K + j] = wgt * den[q];
+#pragma unroll
+                for (int r = 0; r < kExB; ++r)
+                    if (r < nb) {
+                        if constexpr (CPLX) {
+                            o[(2 + 2 * r) * K + j] = s[q][r].x;
+                            o[(3 + 2 * r) * K + j] = s[q][r].y;
+                        } else {
+                            o[(2 + r) * K + j] = s[q][r];
+                        }
+                    }
+            }
     }
 }
 
 // 2D, one CTA per spectral row a (entries c n0 + a), one grid value per
-// thread, with the border rows (and, for the Fourier family, the partner row
-// -a) staged: for an interior row i = a - k, wv = sum_r |(W0 P V1^T)[i][r]|^2
-// (0 on border rows).  A stored Fourier column c that stands for a pair adds
-// its partner, P[a][-t] = conj(P[-a][t]), at V1's column -t.
-// grid = (n0, items), block <= 256;
-// dynamic shared memory (2 + 2k) W1 (sizeof(T) + sizeof(E)).
+// thread: the projections u_r = (P V1^T)[a][r] over the full row.  A stored
+// Fourier column c that stands for a pair adds its partner,
+// P[a][-t] = conj(P[-a][t]), at V1's column -t (the partner row -a is staged).
+// The W0 P V1^T term is formed from the projections in k_ex_reduce.
+// grid = (n0, items), block <= 256; dynamic shared memory 2 W1 (sizeof(T) + sizeof(E)).
 template <typename T, bool CPLX>
 __global__ void __launch_bounds__(256)
 k_ex_rows(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
@@ -362,132 +368,141 @@ k_ex_rows(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
     const int a = blockIdx.x;
     const long long item = blockIdx.y;
     const int K = geo.K;
-    T* o = out + (item * n0 + a) * (long long)K;
-    if (!(a >= k && a < n0 - k)) {
-        for (int j = threadIdx.x; j < K; j += blockDim.x) o[j] = 0;
-        return;
-    }
-    const int ns = 2 + nb;                                        // own, borders, partner
+    const int nval = nb * (CPLX ? 2 : 1);
+    const int ns = CPLX ? 2 : 1;                                  // the row and its partner
     E* sg = reinterpret_cast<E*>(smem_raw);                      // [ns][W1]
     T* sa = reinterpret_cast<T*>(sg + (size_t)ns * W1);          // [ns][W1]
     const E* sp = spec + item * geo.S;
     const E* dp = D + (psf_per ? item : 0) * d_psf_stride;
     for (int s = 0; s < ns; ++s) {
-        const int row = s == 0 ? a : (s <= nb ? A0.bidx[s - 1] : (CPLX ? hx_neg(a, n0) : a));
+        const int row = s == 0 ? a : hx_neg(a, n0);
         for (int c = threadIdx.x; c < W1; c += blockDim.x)
             ex_stage<T, CPLX>(sp, dp, geo, (long long)c * n0 + row, sa[s * W1 + c], sg[s * W1 + c]);
     }
     __syncthreads();
-    const E* b0 = reinterpret_cast<const E*>(A0.bhat);
     const E* V1 = reinterpret_cast<const E*>(A1.V);
-    const int i = a - k;
-    E alpha[kExB];
-#pragma unroll
-    for (int bk = 0; bk < kExB; ++bk) alpha[bk] = bk < nb ? b0[(size_t)bk * A0.N + i] : xz<E>();
+    T* o = out + (item * n0 + a) * (long long)nval * K;
     for (int jb = 0; jb < K; jb += blockDim.x) {
         const int j = jb + threadIdx.x;
         const T mu = j < K ? muT[j] : (T)1;
-        E u[kExB], ub[kExB][kExB];
+        E u[kExB];
 #pragma unroll
-        for (int r = 0; r < kExB; ++r) {
-            u[r] = xz<E>();
-#pragma unroll
-            for (int bk = 0; bk < kExB; ++bk) ub[r][bk] = xz<E>();
-        }
+        for (int r = 0; r < kExB; ++r) u[r] = xz<E>();
         for (int c = 0; c < W1; ++c) {
             const int t = CPLX ? hx_t(c, n1, W1) : c;
             const E P0 = xs(sg[c], pair_rcp(sa[c] + mu));
-            E Pb[kExB];
-#pragma unroll
-            for (int bk = 0; bk < kExB; ++bk)
-                Pb[bk] = bk < nb ? xs(sg[(1 + bk) * W1 + c], pair_rcp(sa[(1 + bk) * W1 + c] + mu)) : xz<E>();
 #pragma unroll
             for (int r = 0; r < kExB; ++r)
-                if (r < nb) {
-                    const E v = V1[(size_t)r * n1 + t];
-                    u[r] = xa(u[r], xm(v, P0));
-#pragma unroll
-                    for (int bk = 0; bk < kExB; ++bk)
-                        if (bk < nb) ub[r][bk] = xa(ub[r][bk], xm(v, Pb[bk]));
-                }
+                if (r < nb) u[r] = xa(u[r], xm(V1[(size_t)r * n1 + t], P0));
             if constexpr (CPLX) {
                 if (!hx_self(c, n1, W1)) {
                     const int tn = hx_neg(t, n1);
-                    const E Pp = xc(xs(sg[(1 + nb) * W1 + c], pair_rcp(sa[(1 + nb) * W1 + c] + mu)));
+                    const E Pp = xc(xs(sg[W1 + c], pair_rcp(sa[W1 + c] + mu)));
 #pragma unroll
                     for (int r = 0; r < kExB; ++r)
-                        if (r < nb) {
-                            const E v = V1[(size_t)r * n1 + tn];
-                            u[r] = xa(u[r], xm(v, Pp));
-#pragma unroll
-                            for (int bk = 0; bk < kExB; ++bk)     // border rows are their own partners
-                                if (bk < nb) ub[r][bk] = xa(ub[r][bk], xm(v, xc(Pb[bk])));
-                        }
+                        if (r < nb) u[r] = xa(u[r], xm(V1[(size_t)r * n1 + tn], Pp));
                 }
             }
         }
-        T wv = 0;
+        if (j < K)
 #pragma unroll
-        for (int r = 0; r < kExB; ++r)
-            if (r < nb) {
-                E v = u[r];
-#pragma unroll
-                for (int bk = 0; bk < kExB; ++bk)
-                    if (bk < nb) v = xa(v, xm(alpha[bk], ub[r][bk]));
-                wv += abs2_of(v);
-            }
-        if (j < K) o[j] = wv;
+            for (int r = 0; r < kExB; ++r)
+                if (r < nb) {
+                    if constexpr (CPLX) {
+                        o[(2 * r) * K + j] = u[r].x;
+                        o[(2 * r + 1) * K + j] = u[r].y;
+                    } else {
+                        o[r * K + j] = u[r];
+                    }
+                }
     }
 }
 
-// 2D: G_ex from the line sums.  Slot s of grid value j (lane) sums, in FP64,
-// the stored columns and rows = s mod kExSlots and its share of
-// (V0 P V1^T)[r][r'] = sum over full columns of (V0 P)[r][t] V1[r'][t] (a
-// stored Fourier column that stands for a pair adds conj((V0 P)[r][c]) at
-// V1's column -t); slot 0 adds the slots in order.
-// num = ww + vw + wv + |V0 P V1^T|^2, G = num / den^2.
+// 2D: G_ex from the line sums.  Slot s of grid value j (lane) covers the
+// stored columns and rows = s mod kExSlots: the column sums ww and den, the
+// column terms |(V0 P W1^T)[r][j]|^2 = |(V0 P)[r][c] + sum_bl (V0 P)[r][bl]
+// bhat1[bl][j]|^2 (pair-weighted), the row terms |(W0 P V1^T)[i][r]|^2 =
+// |u_r(a) + sum_bk bhat0[bk][i] u_r(bk)|^2, and its share of (V0 P V1^T)[r][r']
+// = sum over full columns of (V0 P)[r][t] V1[r'][t] (a stored Fourier column
+// that stands for a pair adds conj((V0 P)[r][c]) at V1's column -t).  Line
+// terms in the working precision, sums in FP64; slot 0 adds the slots in
+// order.  num = ww + vw + wv + |V0 P V1^T|^2, G = num / den^2.
 // grid = (items, ceil(K / 32)), block = (32, kExSlots).
 template <typename T, bool CPLX>
 __global__ void __launch_bounds__(32 * kExSlots)
-k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, int n0, int n1, int W1, int k,
+k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, ExAxis A0, ExAxis A1, int k,
             const double* __restrict__ V1d, int K, double* __restrict__ G) {
+    typedef typename ElemT<T, CPLX>::t E;
     __shared__ double part[4][kExSlots][32];
     __shared__ double vre[kExSlots][kExB * kExB][32], vim[kExSlots][kExB * kExB][32];
     const int lane = threadIdx.x, s = threadIdx.y;
     const int j = blockIdx.y * 32 + lane;
     const long long item = blockIdx.x;
-    const int nb = 2 * k, nval = 3 + nb * (CPLX ? 2 : 1);
+    const int n0 = A0.n, n1 = A1.n, W1 = A1.W, nb = 2 * k;
+    const int cv = nb * (CPLX ? 2 : 1), ncol = 2 + cv;
+    const E* b0 = reinterpret_cast<const E*>(A0.bhat);
+    const E* b1 = reinterpret_cast<const E*>(A1.bhat);
     double ww = 0, vw = 0, den = 0, wv = 0, mr[kExB * kExB], mi[kExB * kExB];
 #pragma unroll
     for (int q = 0; q < kExB * kExB; ++q) { mr[q] = 0; mi[q] = 0; }
+    auto ld = [&](const T* base, int idx) -> E {          // projection idx of a line's output
+        if constexpr (CPLX) { E v; v.x = base[(2 * idx) * K + j]; v.y = base[(2 * idx + 1) * K + j]; return v; }
+        else return base[idx * K + j];
+    };
     if (j < K) {
-        const T* co = col_out + item * (long long)W1 * nval * K;
+        const T* co = col_out + item * (long long)W1 * ncol * K;
+        const T* ro = row_out + item * (long long)n0 * cv * K;
+        E sB[kExB][kExB], uB[kExB][kExB];      // projections of the border columns / rows
+#pragma unroll
+        for (int b = 0; b < kExB; ++b)
+#pragma unroll
+            for (int r = 0; r < kExB; ++r) {
+                sB[b][r] = (b < nb && r < nb) ? ld(co + (long long)A1.bcol[b] * ncol * K + 2 * K, r) : xz<E>();
+                uB[b][r] = (b < nb && r < nb) ? ld(ro + (long long)A0.bidx[b] * cv * K, r) : xz<E>();
+            }
         for (int c = s; c < W1; c += kExSlots) {
-            const T* oc = co + (long long)c * nval * K;
+            const T* oc = co + (long long)c * ncol * K;
             ww += (double)oc[j];
-            vw += (double)oc[K + j];
-            den += (double)oc[2 * K + j];
+            den += (double)oc[K + j];
             const int t = CPLX ? hx_t(c, n1, W1) : c;
             const bool pair = CPLX && !hx_self(c, n1, W1);
-            const int tn = pair ? hx_neg(t, n1) : t;
+            const bool inter = t >= k && t < n1 - k;
+            T term = 0;
             for (int r = 0; r < nb; ++r) {
-                const double sr = CPLX ? (double)oc[(3 + 2 * r) * K + j] : (double)oc[(3 + r) * K + j];
-                const double si = CPLX ? (double)oc[(4 + 2 * r) * K + j] : 0.0;
+                const E sr = ld(oc + 2 * K, r);
+                if (inter) {
+                    E v = sr;
+                    for (int b = 0; b < nb; ++b) v = xa(v, xm(sB[b][r], b1[(size_t)b * A1.N + (t - k)]));
+                    term += abs2_of(v);
+                }
+                double sre, sim;
+                if constexpr (CPLX) { sre = sr.x; sim = sr.y; } else { sre = sr; sim = 0.0; }
                 for (int rr = 0; rr < nb; ++rr) {
                     const double vr = CPLX ? V1d[2 * ((size_t)rr * n1 + t)] : V1d[(size_t)rr * n1 + t];
                     const double vi = CPLX ? V1d[2 * ((size_t)rr * n1 + t) + 1] : 0.0;
-                    mr[r * kExB + rr] += sr * vr - si * vi;
-                    mi[r * kExB + rr] += sr * vi + si * vr;
+                    mr[r * kExB + rr] += sre * vr - sim * vi;
+                    mi[r * kExB + rr] += sre * vi + sim * vr;
                     if (pair) {                 // conj(s) at column -t
+                        const int tn = hx_neg(t, n1);
                         const double pr = V1d[2 * ((size_t)rr * n1 + tn)], pim = V1d[2 * ((size_t)rr * n1 + tn) + 1];
-                        mr[r * kExB + rr] += sr * pr + si * pim;
-                        mi[r * kExB + rr] += sr * pim - si * pr;
+                        mr[r * kExB + rr] += sre * pr + sim * pim;
+                        mi[r * kExB + rr] += sre * pim - sim * pr;
                     }
                 }
             }
+            vw += (pair ? 2.0 : 1.0) * (double)term;
         }
-        const T* ro = row_out + item * (long long)n0 * K;
-        for (int a = s; a < n0; a += kExSlots) wv += (double)ro[(long long)a * K + j];
+        for (int a = s; a < n0; a += kExSlots) {
+            if (a < k || a >= n0 - k) continue;
+            const T* orow = ro + (long long)a * cv * K;
+            T term = 0;
+            for (int r = 0; r < nb; ++r) {
+                E v = ld(orow, r);
+                for (int b = 0; b < nb; ++b) v = xa(v, xm(b0[(size_t)b * A0.N + (a - k)], uB[b][r]));
+                term += abs2_of(v);
+            }
+            wv += (double)term;
+        }
     }
     part[0][s][lane] = ww; part[1][s][lane] = vw; part[2][s][lane] = den; part[3][s][lane] = wv;
 #pragma unroll
@@ -650,9 +665,9 @@ hobc_status ensure_exact(hobc_plan_s* p) {
     const size_t B = (size_t)p->desc.batch, K = (size_t)p->K;
     if (p->nax == 2) {
         const size_t n0 = (size_t)p->ax[0].n, W1 = (size_t)p->ax[1].W;
-        const size_t nval = 3 + 2 * (size_t)k * (x->cplx ? 2 : 1);
-        if (e == cudaSuccess) e = cudaMalloc(&x->col_out, B * W1 * nval * K * p->esz);
-        if (e == cudaSuccess) e = cudaMalloc(&x->row_out, B * n0 * K * p->esz);
+        const size_t cv = 2 * (size_t)k * (x->cplx ? 2 : 1);
+        if (e == cudaSuccess) e = cudaMalloc(&x->col_out, B * W1 * (2 + cv) * K * p->esz);
+        if (e == cudaSuccess) e = cudaMalloc(&x->row_out, B * n0 * std::max(cv, (size_t)1) * K * p->esz);
     }
     if (e == cudaSuccess) e = cudaMalloc((void**)&x->G, B * K * sizeof(double));
     if (e != cudaSuccess) {
@@ -699,18 +714,19 @@ hobc_status run_gcv_exact(hobc_plan_s* p, const void* ghat, const void* D, doubl
         p->launches += 1;
     } else {
         const ExAxis A0 = ex_axis(x, p, 0), A1 = ex_axis(x, p, 1);
-        const int n0 = A0.n, n1 = A1.n, W1 = A1.W;
-        const size_t sc = (size_t)(1 + 2 * k) * n0 * el, sr = (size_t)(2 + 2 * k) * W1 * el;
+        const int n0 = A0.n, W1 = A1.W;
+        const size_t sc = (size_t)(kExCB + 2 * k) * n0 * el, sr = (size_t)(CPLX ? 2 : 1) * W1 * el;
         e = cudaFuncSetAttribute(k_ex_cols<T, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_ex_rows<T, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
         if (e != cudaSuccess) { set_last_error("hobc_gcv_exact", e); return HOBC_ERR_CUDA; }
-        k_ex_cols<T, CPLX><<<dim3((unsigned)W1, (unsigned)B), threads, sc, p->stream>>>(
+        k_ex_cols<T, CPLX><<<dim3((unsigned)((W1 + kExCB - 1) / kExCB), (unsigned)B), threads, sc, p->stream>>>(
             sp, dp, dps, p->desc.psf_per_item, muT, geo, A0, A1, k, reinterpret_cast<T*>(x->col_out));
-        k_ex_rows<T, CPLX><<<dim3((unsigned)n0, (unsigned)B), threads, sr, p->stream>>>(
-            sp, dp, dps, p->desc.psf_per_item, muT, geo, A0, A1, k, reinterpret_cast<T*>(x->row_out));
+        if (k > 0)
+            k_ex_rows<T, CPLX><<<dim3((unsigned)n0, (unsigned)B), threads, sr, p->stream>>>(
+                sp, dp, dps, p->desc.psf_per_item, muT, geo, A0, A1, k, reinterpret_cast<T*>(x->row_out));
         k_ex_reduce<T, CPLX><<<dim3((unsigned)B, (unsigned)((K + 31) / 32)), dim3(32, kExSlots), 0, p->stream>>>(
-            reinterpret_cast<const T*>(x->col_out), reinterpret_cast<const T*>(x->row_out), n0, n1, W1, k,
+            reinterpret_cast<const T*>(x->col_out), reinterpret_cast<const T*>(x->row_out), A0, A1, k,
             reinterpret_cast<const double*>(x->Vd[1]), K, Gout);
         p->launches += 3;
     }
