@@ -229,15 +229,16 @@ __device__ __forceinline__ void ex_stage(const typename ElemT<T, CPLX>::t* sp, c
 // pair).  The V0 P W1^T term is formed from the projections in k_ex_reduce.
 // grid = (ceil(stored columns / kExCB), items), block <= 256;
 // dynamic shared memory (kExCB + 2k) n0 (sizeof(T) + sizeof(E)).
-template <typename T, bool CPLX>
+template <typename T, bool CPLX, int NB>
 __global__ void __launch_bounds__(256)
 k_ex_cols(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
-          long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo, ExAxis A0, ExAxis A1, int k,
+          long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo, ExAxis A0, ExAxis A1,
           T* __restrict__ out) {
     typedef typename ElemT<T, CPLX>::t E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ E sbeta[kExCB][kExB];
-    const int n0 = A0.n, n1 = A1.n, W1 = A1.W, nb = 2 * k, ns = kExCB + nb;
+    constexpr int nb = NB, k = NB / 2, NB1 = NB > 0 ? NB : 1, ns = kExCB + NB;
+    __shared__ E sbeta[kExCB][NB1];
+    const int n0 = A0.n, n1 = A1.n, W1 = A1.W;
     E* sg = reinterpret_cast<E*>(smem_raw);                      // [ns][n0]
     T* sa = reinterpret_cast<T*>(sg + (size_t)ns * n0);          // [ns][n0]
     const int c0 = blockIdx.x * kExCB;
@@ -250,8 +251,8 @@ k_ex_cols(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
             ex_stage<T, CPLX>(sp, dp, geo, (long long)col * n0 + a, sa[s * n0 + a], sg[s * n0 + a]);
     }
     const E* b1 = reinterpret_cast<const E*>(A1.bhat);
-    if (threadIdx.x < kExCB * kExB) {
-        const int q = threadIdx.x / kExB, bl = threadIdx.x % kExB;
+    if (threadIdx.x < kExCB * NB1) {
+        const int q = threadIdx.x / NB1, bl = threadIdx.x % NB1;
         const int t = CPLX ? hx_t(min(c0 + q, W1 - 1), n1, W1) : min(c0 + q, W1 - 1);
         sbeta[q][bl] = (bl < nb && t >= k && t < n1 - k) ? b1[(size_t)bl * A1.N + (t - k)] : xz<E>();
     }
@@ -271,13 +272,13 @@ k_ex_cols(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
     for (int jb = 0; jb < K; jb += blockDim.x) {
         const int j = jb + threadIdx.x;
         const T mu = j < K ? muT[j] : (T)1;
-        E gam[kExCB][kExB];                    // P[bk][t] + sum_bl P[bk][bl] bhat1[bl][j(t)]
+        E gam[kExCB][NB1];                    // P[bk][t] + sum_bl P[bk][bl] bhat1[bl][j(t)]
 #pragma unroll
-        for (int bk = 0; bk < kExB; ++bk) {
-            E corner[kExB];
+        for (int bk = 0; bk < NB; ++bk) {
+            E corner[NB1];
             const int ar = bk < nb ? A0.bidx[bk] : 0;
 #pragma unroll
-            for (int bl = 0; bl < kExB; ++bl)
+            for (int bl = 0; bl < NB; ++bl)
                 corner[bl] = (bk < nb && bl < nb)
                                  ? xs(sg[(kExCB + bl) * n0 + ar], pair_rcp(sa[(kExCB + bl) * n0 + ar] + mu)) : xz<E>();
 #pragma unroll
@@ -286,43 +287,43 @@ k_ex_cols(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
                 if (bk < nb) {
                     gv = xs(sg[q * n0 + ar], pair_rcp(sa[q * n0 + ar] + mu));
 #pragma unroll
-                    for (int bl = 0; bl < kExB; ++bl)
+                    for (int bl = 0; bl < NB; ++bl)
                         if (bl < nb) gv = xa(gv, xm(corner[bl], sbeta[q][bl]));
                 }
                 gam[q][bk] = gv;
             }
         }
         T ww[kExCB], den[kExCB];
-        E s[kExCB][kExB];
+        E s[kExCB][NB1];
 #pragma unroll
         for (int q = 0; q < kExCB; ++q) {
             ww[q] = 0;
             den[q] = 0;
 #pragma unroll
-            for (int r = 0; r < kExB; ++r) s[q][r] = xz<E>();
+            for (int r = 0; r < NB; ++r) s[q][r] = xz<E>();
         }
         for (int a = 0; a < n0; ++a) {
-            E Pb[kExB], v0[kExB], bb[kExB];
+            E Pb[NB1], v0[NB1], bb[NB1];
 #pragma unroll
-            for (int b = 0; b < kExB; ++b) {
+            for (int b = 0; b < NB; ++b) {
                 Pb[b] = b < nb ? xs(sg[(kExCB + b) * n0 + a], pair_rcp(sa[(kExCB + b) * n0 + a] + mu)) : xz<E>();
                 v0[b] = b < nb ? V0[(size_t)b * n0 + a] : xz<E>();
             }
             const bool ai = a >= k && a < n0 - k;
 #pragma unroll
-            for (int b = 0; b < kExB; ++b) bb[b] = (ai && b < nb) ? b0[(size_t)b * A0.N + (a - k)] : xz<E>();
+            for (int b = 0; b < NB; ++b) bb[b] = (ai && b < nb) ? b0[(size_t)b * A0.N + (a - k)] : xz<E>();
 #pragma unroll
             for (int q = 0; q < kExCB; ++q) {
                 const T s0 = pair_rcp(sa[q * n0 + a] + mu);
                 const E P0 = xs(sg[q * n0 + a], s0);
                 den[q] += s0;
 #pragma unroll
-                for (int r = 0; r < kExB; ++r)
+                for (int r = 0; r < NB; ++r)
                     if (r < nb) s[q][r] = xa(s[q][r], xm(v0[r], P0));
                 if (inter[q] && ai) {
                     E w = P0;
 #pragma unroll
-                    for (int b = 0; b < kExB; ++b)
+                    for (int b = 0; b < NB; ++b)
                         if (b < nb) w = xa(xa(w, xm(Pb[b], sbeta[q][b])), xm(bb[b], gam[q][b]));
                     ww[q] += abs2_of(w);
                 }
@@ -338,7 +339,7 @@ k_ex_cols(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
                 o[j] = wgt * ww[q];
                 o[K + j] = wgt * den[q];
 #pragma unroll
-                for (int r = 0; r < kExB; ++r)
+                for (int r = 0; r < NB; ++r)
                     if (r < nb) {
                         if constexpr (CPLX) {
                             o[(2 + 2 * r) * K + j] = s[q][r].x;
@@ -357,14 +358,15 @@ k_ex_cols(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
 // P[a][-t] = conj(P[-a][t]), at V1's column -t (the partner row -a is staged).
 // The W0 P V1^T term is formed from the projections in k_ex_reduce.
 // grid = (n0, items), block <= 256; dynamic shared memory 2 W1 (sizeof(T) + sizeof(E)).
-template <typename T, bool CPLX>
+template <typename T, bool CPLX, int NB>
 __global__ void __launch_bounds__(256)
 k_ex_rows(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
-          long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo, ExAxis A0, ExAxis A1, int k,
+          long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo, ExAxis A0, ExAxis A1,
           T* __restrict__ out) {
     typedef typename ElemT<T, CPLX>::t E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n0 = A0.n, n1 = A1.n, W1 = A1.W, nb = 2 * k;
+    constexpr int nb = NB, k = NB / 2, NB1 = NB > 0 ? NB : 1;
+    const int n0 = A0.n, n1 = A1.n, W1 = A1.W;
     const int a = blockIdx.x;
     const long long item = blockIdx.y;
     const int K = geo.K;
@@ -385,28 +387,28 @@ k_ex_rows(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
     for (int jb = 0; jb < K; jb += blockDim.x) {
         const int j = jb + threadIdx.x;
         const T mu = j < K ? muT[j] : (T)1;
-        E u[kExB];
+        E u[NB1];
 #pragma unroll
-        for (int r = 0; r < kExB; ++r) u[r] = xz<E>();
+        for (int r = 0; r < NB; ++r) u[r] = xz<E>();
         for (int c = 0; c < W1; ++c) {
             const int t = CPLX ? hx_t(c, n1, W1) : c;
             const E P0 = xs(sg[c], pair_rcp(sa[c] + mu));
 #pragma unroll
-            for (int r = 0; r < kExB; ++r)
+            for (int r = 0; r < NB; ++r)
                 if (r < nb) u[r] = xa(u[r], xm(V1[(size_t)r * n1 + t], P0));
             if constexpr (CPLX) {
                 if (!hx_self(c, n1, W1)) {
                     const int tn = hx_neg(t, n1);
                     const E Pp = xc(xs(sg[W1 + c], pair_rcp(sa[W1 + c] + mu)));
 #pragma unroll
-                    for (int r = 0; r < kExB; ++r)
+                    for (int r = 0; r < NB; ++r)
                         if (r < nb) u[r] = xa(u[r], xm(V1[(size_t)r * n1 + tn], Pp));
                 }
             }
         }
         if (j < K)
 #pragma unroll
-            for (int r = 0; r < kExB; ++r)
+            for (int r = 0; r < NB; ++r)
                 if (r < nb) {
                     if constexpr (CPLX) {
                         o[(2 * r) * K + j] = u[r].x;
@@ -428,23 +430,24 @@ k_ex_rows(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
 // terms in the working precision, sums in FP64; slot 0 adds the slots in
 // order.  num = ww + vw + wv + |V0 P V1^T|^2, G = num / den^2.
 // grid = (items, ceil(K / 32)), block = (32, kExSlots).
-template <typename T, bool CPLX>
+template <typename T, bool CPLX, int NB>
 __global__ void __launch_bounds__(32 * kExSlots)
-k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, ExAxis A0, ExAxis A1, int k,
+k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, ExAxis A0, ExAxis A1,
             const double* __restrict__ V1d, int K, double* __restrict__ G) {
     typedef typename ElemT<T, CPLX>::t E;
+    constexpr int nb = NB, k = NB / 2, NB1 = NB > 0 ? NB : 1;
     __shared__ double part[4][kExSlots][32];
-    __shared__ double vre[kExSlots][kExB * kExB][32], vim[kExSlots][kExB * kExB][32];
+    __shared__ double vre[kExSlots][NB1 * NB1][32], vim[kExSlots][NB1 * NB1][32];
     const int lane = threadIdx.x, s = threadIdx.y;
     const int j = blockIdx.y * 32 + lane;
     const long long item = blockIdx.x;
-    const int n0 = A0.n, n1 = A1.n, W1 = A1.W, nb = 2 * k;
+    const int n0 = A0.n, n1 = A1.n, W1 = A1.W;
     const int cv = nb * (CPLX ? 2 : 1), ncol = 2 + cv;
     const E* b0 = reinterpret_cast<const E*>(A0.bhat);
     const E* b1 = reinterpret_cast<const E*>(A1.bhat);
-    double ww = 0, vw = 0, den = 0, wv = 0, mr[kExB * kExB], mi[kExB * kExB];
+    double ww = 0, vw = 0, den = 0, wv = 0, mr[NB1 * NB1], mi[NB1 * NB1];
 #pragma unroll
-    for (int q = 0; q < kExB * kExB; ++q) { mr[q] = 0; mi[q] = 0; }
+    for (int q = 0; q < NB1 * NB1; ++q) { mr[q] = 0; mi[q] = 0; }
     auto ld = [&](const T* base, int idx) -> E {          // projection idx of a line's output
         if constexpr (CPLX) { E v; v.x = base[(2 * idx) * K + j]; v.y = base[(2 * idx + 1) * K + j]; return v; }
         else return base[idx * K + j];
@@ -452,11 +455,11 @@ k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, ExAxis
     if (j < K) {
         const T* co = col_out + item * (long long)W1 * ncol * K;
         const T* ro = row_out + item * (long long)n0 * cv * K;
-        E sB[kExB][kExB], uB[kExB][kExB];      // projections of the border columns / rows
+        E sB[NB1][NB1], uB[NB1][NB1];      // projections of the border columns / rows
 #pragma unroll
-        for (int b = 0; b < kExB; ++b)
+        for (int b = 0; b < NB; ++b)
 #pragma unroll
-            for (int r = 0; r < kExB; ++r) {
+            for (int r = 0; r < NB; ++r) {
                 sB[b][r] = (b < nb && r < nb) ? ld(co + (long long)A1.bcol[b] * ncol * K + 2 * K, r) : xz<E>();
                 uB[b][r] = (b < nb && r < nb) ? ld(ro + (long long)A0.bidx[b] * cv * K, r) : xz<E>();
             }
@@ -480,13 +483,13 @@ k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, ExAxis
                 for (int rr = 0; rr < nb; ++rr) {
                     const double vr = CPLX ? V1d[2 * ((size_t)rr * n1 + t)] : V1d[(size_t)rr * n1 + t];
                     const double vi = CPLX ? V1d[2 * ((size_t)rr * n1 + t) + 1] : 0.0;
-                    mr[r * kExB + rr] += sre * vr - sim * vi;
-                    mi[r * kExB + rr] += sre * vi + sim * vr;
+                    mr[r * NB1 + rr] += sre * vr - sim * vi;
+                    mi[r * NB1 + rr] += sre * vi + sim * vr;
                     if (pair) {                 // conj(s) at column -t
                         const int tn = hx_neg(t, n1);
                         const double pr = V1d[2 * ((size_t)rr * n1 + tn)], pim = V1d[2 * ((size_t)rr * n1 + tn) + 1];
-                        mr[r * kExB + rr] += sre * pr + sim * pim;
-                        mi[r * kExB + rr] += sre * pim - sim * pr;
+                        mr[r * NB1 + rr] += sre * pr + sim * pim;
+                        mi[r * NB1 + rr] += sre * pim - sim * pr;
                     }
                 }
             }
@@ -506,7 +509,7 @@ k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, ExAxis
     }
     part[0][s][lane] = ww; part[1][s][lane] = vw; part[2][s][lane] = den; part[3][s][lane] = wv;
 #pragma unroll
-    for (int q = 0; q < kExB * kExB; ++q) { vre[s][q][lane] = mr[q]; vim[s][q][lane] = mi[q]; }
+    for (int q = 0; q < NB1 * NB1; ++q) { vre[s][q][lane] = mr[q]; vim[s][q][lane] = mi[q]; }
     __syncthreads();
     if (s != 0 || j >= K) return;
     ww = vw = den = wv = 0;
@@ -514,7 +517,7 @@ k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, ExAxis
         ww += part[0][q][lane]; vw += part[1][q][lane]; den += part[2][q][lane]; wv += part[3][q][lane];
     }
     double vsq = 0;
-    for (int q = 0; q < kExB * kExB; ++q) {
+    for (int q = 0; q < NB1 * NB1; ++q) {
         double ar = 0, ai = 0;
         for (int t = 0; t < kExSlots; ++t) { ar += vre[t][q][lane]; ai += vim[t][q][lane]; }
         vsq += ar * ar + ai * ai;
@@ -526,14 +529,15 @@ k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, ExAxis
 // num = sum_i |(W P)[i]|^2 + sum_r |(V P)[r]|^2, G = num / (sum sigma)^2 (Fourier
 // half spectrum: pair weights on the first two sums, partner entries in V P).
 // grid = items, block <= 256; dynamic shared memory W (sizeof(T) + sizeof(E)).
-template <typename T, bool CPLX>
+template <typename T, bool CPLX, int NB>
 __global__ void __launch_bounds__(256)
 k_ex_1d(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
-        long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo, ExAxis A0, int k,
+        long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo, ExAxis A0,
         double* __restrict__ G) {
     typedef typename ElemT<T, CPLX>::t E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n = A0.n, W = A0.W, nb = 2 * k;
+    constexpr int nb = NB, k = NB / 2, NB1 = NB > 0 ? NB : 1;
+    const int n = A0.n, W = A0.W;
     E* sg = reinterpret_cast<E*>(smem_raw);
     T* sa = reinterpret_cast<T*>(sg + W);
     const long long item = blockIdx.x;
@@ -547,14 +551,14 @@ k_ex_1d(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename Elem
     for (int jb = 0; jb < K; jb += blockDim.x) {
         const int j = jb + threadIdx.x;
         const T mu = j < K ? muT[j] : (T)1;
-        E pb[kExB];
+        E pb[NB1];
 #pragma unroll
-        for (int b = 0; b < kExB; ++b)
+        for (int b = 0; b < NB; ++b)
             pb[b] = b < nb ? xs(sg[A0.bcol[b]], pair_rcp(sa[A0.bcol[b]] + mu)) : xz<E>();
         T ww = 0, den = 0;
-        E s[kExB];
+        E s[NB1];
 #pragma unroll
-        for (int r = 0; r < kExB; ++r) s[r] = xz<E>();
+        for (int r = 0; r < NB; ++r) s[r] = xz<E>();
         for (int c = 0; c < W; ++c) {
             const int t = CPLX ? hx_t(c, n, W) : c;
             const bool pair = CPLX && !hx_self(c, n, W);
@@ -563,7 +567,7 @@ k_ex_1d(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename Elem
             const E P0 = xs(sg[c], s0);
             den += wg * s0;
 #pragma unroll
-            for (int r = 0; r < kExB; ++r)
+            for (int r = 0; r < NB; ++r)
                 if (r < nb) {
                     s[r] = xa(s[r], xm(V0[(size_t)r * n + t], P0));
                     if (pair) s[r] = xa(s[r], xm(V0[(size_t)r * n + hx_neg(t, n)], xc(P0)));
@@ -571,14 +575,14 @@ k_ex_1d(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename Elem
             if (t >= k && t < n - k) {
                 E w = P0;
 #pragma unroll
-                for (int b = 0; b < kExB; ++b)
+                for (int b = 0; b < NB; ++b)
                     if (b < nb) w = xa(w, xm(b0[(size_t)b * A0.N + (t - k)], pb[b]));
                 ww += wg * abs2_of(w);
             }
         }
         T vsq = 0;
 #pragma unroll
-        for (int r = 0; r < kExB; ++r)
+        for (int r = 0; r < NB; ++r)
             if (r < nb) vsq += abs2_of(s[r]);
         if (j < K) G[item * K + j] = ((double)ww + (double)vsq) / ((double)den * (double)den);
     }
@@ -693,12 +697,13 @@ ExAxis ex_axis(const hobc_exact_s* x, const hobc_plan_s* p, int a) {
     return A;
 }
 
-template <typename T, bool CPLX>
+template <typename T, bool CPLX, int NB>
 hobc_status run_gcv_exact(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx) {
     typedef typename ElemT<T, CPLX>::t E;
     hobc_exact_s* x = p->exact;
     GcvGeom geo = exact_geo(p);
-    const int B = p->desc.batch, K = p->K, k = x->k;
+    const int B = p->desc.batch, K = p->K;
+    constexpr int k = NB / 2;
     const E* sp = reinterpret_cast<const E*>(ghat);
     const E* dp = reinterpret_cast<const E*>(D);
     const T* muT = reinterpret_cast<const T*>(p->muT);
@@ -709,26 +714,26 @@ hobc_status run_gcv_exact(hobc_plan_s* p, const void* ghat, const void* D, doubl
     cudaError_t e = cudaSuccess;
     if (p->nax == 1) {
         const ExAxis A0 = ex_axis(x, p, 0);
-        k_ex_1d<T, CPLX><<<B, threads, (size_t)A0.W * el, p->stream>>>(sp, dp, dps, p->desc.psf_per_item, muT, geo, A0,
-                                                                      k, Gout);
+        k_ex_1d<T, CPLX, NB><<<B, threads, (size_t)A0.W * el, p->stream>>>(sp, dp, dps, p->desc.psf_per_item, muT,
+                                                                          geo, A0, Gout);
         p->launches += 1;
     } else {
         const ExAxis A0 = ex_axis(x, p, 0), A1 = ex_axis(x, p, 1);
         const int n0 = A0.n, W1 = A1.W;
         const size_t sc = (size_t)(kExCB + 2 * k) * n0 * el, sr = (size_t)(CPLX ? 2 : 1) * W1 * el;
-        e = cudaFuncSetAttribute(k_ex_cols<T, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+        e = cudaFuncSetAttribute(k_ex_cols<T, CPLX, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_ex_rows<T, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
+            e = cudaFuncSetAttribute(k_ex_rows<T, CPLX, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
         if (e != cudaSuccess) { set_last_error("hobc_gcv_exact", e); return HOBC_ERR_CUDA; }
-        k_ex_cols<T, CPLX><<<dim3((unsigned)((W1 + kExCB - 1) / kExCB), (unsigned)B), threads, sc, p->stream>>>(
-            sp, dp, dps, p->desc.psf_per_item, muT, geo, A0, A1, k, reinterpret_cast<T*>(x->col_out));
-        if (k > 0)
-            k_ex_rows<T, CPLX><<<dim3((unsigned)n0, (unsigned)B), threads, sr, p->stream>>>(
-                sp, dp, dps, p->desc.psf_per_item, muT, geo, A0, A1, k, reinterpret_cast<T*>(x->row_out));
-        k_ex_reduce<T, CPLX><<<dim3((unsigned)B, (unsigned)((K + 31) / 32)), dim3(32, kExSlots), 0, p->stream>>>(
-            reinterpret_cast<const T*>(x->col_out), reinterpret_cast<const T*>(x->row_out), A0, A1, k,
+        k_ex_cols<T, CPLX, NB><<<dim3((unsigned)((W1 + kExCB - 1) / kExCB), (unsigned)B), threads, sc, p->stream>>>(
+            sp, dp, dps, p->desc.psf_per_item, muT, geo, A0, A1, reinterpret_cast<T*>(x->col_out));
+        if (NB > 0)
+            k_ex_rows<T, CPLX, NB><<<dim3((unsigned)n0, (unsigned)B), threads, sr, p->stream>>>(
+                sp, dp, dps, p->desc.psf_per_item, muT, geo, A0, A1, reinterpret_cast<T*>(x->row_out));
+        k_ex_reduce<T, CPLX, NB><<<dim3((unsigned)B, (unsigned)((K + 31) / 32)), dim3(32, kExSlots), 0, p->stream>>>(
+            reinterpret_cast<const T*>(x->col_out), reinterpret_cast<const T*>(x->row_out), A0, A1,
             reinterpret_cast<const double*>(x->Vd[1]), K, Gout);
-        p->launches += 3;
+        p->launches += NB > 0 ? 3 : 2;
     }
     k_ex_argmin<<<B, 256, 0, p->stream>>>(Gout, K, mu_idx);
     p->launches += 1;
@@ -737,11 +742,21 @@ hobc_status run_gcv_exact(hobc_plan_s* p, const void* ghat, const void* D, doubl
     return HOBC_OK;
 }
 
+// Border vectors per axis: 2 (sine, cosine, Fourier), 4 (degree 3), 0 (orthogonal T).
+template <typename T>
+hobc_status gcv_exact_real(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx) {
+    switch (p->exact->k) {
+        case 0: return run_gcv_exact<T, false, 0>(p, ghat, D, gcv, mu_idx);
+        case 2: return run_gcv_exact<T, false, 4>(p, ghat, D, gcv, mu_idx);
+        default: return run_gcv_exact<T, false, 2>(p, ghat, D, gcv, mu_idx);
+    }
+}
+
 hobc_status gcv_exact_dispatch(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx) {
     const bool F = p->exact->cplx;
     if (p->prec == HOBC_FP64)
-        return F ? run_gcv_exact<double, true>(p, ghat, D, gcv, mu_idx) : run_gcv_exact<double, false>(p, ghat, D, gcv, mu_idx);
-    return F ? run_gcv_exact<float, true>(p, ghat, D, gcv, mu_idx) : run_gcv_exact<float, false>(p, ghat, D, gcv, mu_idx);
+        return F ? run_gcv_exact<double, true, 2>(p, ghat, D, gcv, mu_idx) : gcv_exact_real<double>(p, ghat, D, gcv, mu_idx);
+    return F ? run_gcv_exact<float, true, 2>(p, ghat, D, gcv, mu_idx) : gcv_exact_real<float>(p, ghat, D, gcv, mu_idx);
 }
 
 }  // namespace
