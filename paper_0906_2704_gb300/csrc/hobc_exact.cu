@@ -352,12 +352,15 @@ k_ex_cols(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
     }
 }
 
-// 2D, one CTA per spectral row a (entries c n0 + a), one grid value per
-// thread: the projections u_r = (P V1^T)[a][r] over the full row.  A stored
-// Fourier column c that stands for a pair adds its partner,
-// P[a][-t] = conj(P[-a][t]), at V1's column -t (the partner row -a is staged).
-// The W0 P V1^T term is formed from the projections in k_ex_reduce.
-// grid = (n0, items), block <= 256; dynamic shared memory 2 W1 (sizeof(T) + sizeof(E)).
+// 2D, the projections u_r = (P V1^T)[a][r] of every spectral row a over the
+// full row, one grid value per thread.  Real families: one CTA per row.
+// Fourier family: one CTA per row pair (a, -a) (a row that is its own
+// partner alone), grid.x = the W0 = N0/2 + 3 representatives a of the pairs;
+// a stored column c that stands for a conjugate pair adds the partner entry
+// P[a][-t] = conj(P[-a][t]) at V1's column -t, so the two staged rows give
+// both rows' sums from one reciprocal per stored entry.  The W0 P V1^T term
+// is formed from the projections in k_ex_reduce.
+// dynamic shared memory (1 or 2) W1 (sizeof(T) + sizeof(E)).
 template <typename T, bool CPLX, int NB>
 __global__ void __launch_bounds__(256)
 k_ex_rows(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
@@ -365,58 +368,71 @@ k_ex_rows(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
           T* __restrict__ out) {
     typedef typename ElemT<T, CPLX>::t E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int nb = NB, k = NB / 2, NB1 = NB > 0 ? NB : 1;
+    constexpr int nb = NB, NB1 = NB > 0 ? NB : 1;
     const int n0 = A0.n, n1 = A1.n, W1 = A1.W;
-    const int a = blockIdx.x;
+    const int a = CPLX ? hx_t(blockIdx.x, n0, (n0 - 2) / 2 + 3) : (int)blockIdx.x;
+    const int ap = CPLX ? hx_neg(a, n0) : a;                      // partner row
+    const bool two = ap != a;
     const long long item = blockIdx.y;
     const int K = geo.K;
     const int nval = nb * (CPLX ? 2 : 1);
-    const int ns = CPLX ? 2 : 1;                                  // the row and its partner
+    const int ns = CPLX ? 2 : 1;
     E* sg = reinterpret_cast<E*>(smem_raw);                      // [ns][W1]
     T* sa = reinterpret_cast<T*>(sg + (size_t)ns * W1);          // [ns][W1]
     const E* sp = spec + item * geo.S;
     const E* dp = D + (psf_per ? item : 0) * d_psf_stride;
     for (int s = 0; s < ns; ++s) {
-        const int row = s == 0 ? a : hx_neg(a, n0);
+        const int row = s == 0 ? a : ap;
         for (int c = threadIdx.x; c < W1; c += blockDim.x)
             ex_stage<T, CPLX>(sp, dp, geo, (long long)c * n0 + row, sa[s * W1 + c], sg[s * W1 + c]);
     }
     __syncthreads();
     const E* V1 = reinterpret_cast<const E*>(A1.V);
     T* o = out + (item * n0 + a) * (long long)nval * K;
+    T* op = out + (item * n0 + ap) * (long long)nval * K;
     for (int jb = 0; jb < K; jb += blockDim.x) {
         const int j = jb + threadIdx.x;
         const T mu = j < K ? muT[j] : (T)1;
-        E u[NB1];
+        E u[NB1], up[NB1];
 #pragma unroll
-        for (int r = 0; r < NB; ++r) u[r] = xz<E>();
+        for (int r = 0; r < NB1; ++r) { u[r] = xz<E>(); up[r] = xz<E>(); }
         for (int c = 0; c < W1; ++c) {
             const int t = CPLX ? hx_t(c, n1, W1) : c;
             const E P0 = xs(sg[c], pair_rcp(sa[c] + mu));
-#pragma unroll
-            for (int r = 0; r < NB; ++r)
-                if (r < nb) u[r] = xa(u[r], xm(V1[(size_t)r * n1 + t], P0));
             if constexpr (CPLX) {
-                if (!hx_self(c, n1, W1)) {
-                    const int tn = hx_neg(t, n1);
-                    const E Pp = xc(xs(sg[W1 + c], pair_rcp(sa[W1 + c] + mu)));
+                const E Pq = two ? xs(sg[W1 + c], pair_rcp(sa[W1 + c] + mu)) : P0;   // row -a
+                const bool pair = !hx_self(c, n1, W1);
+                const int tn = hx_neg(t, n1);
 #pragma unroll
-                    for (int r = 0; r < NB; ++r)
-                        if (r < nb) u[r] = xa(u[r], xm(V1[(size_t)r * n1 + tn], Pp));
+                for (int r = 0; r < NB; ++r) {
+                    const E v = V1[(size_t)r * n1 + t];
+                    u[r] = xa(u[r], xm(v, P0));
+                    up[r] = xa(up[r], xm(v, Pq));
+                    if (pair) {
+                        const E vn = V1[(size_t)r * n1 + tn];
+                        u[r] = xa(u[r], xm(vn, xc(Pq)));
+                        up[r] = xa(up[r], xm(vn, xc(P0)));
+                    }
                 }
+            } else {
+#pragma unroll
+                for (int r = 0; r < NB; ++r) u[r] = xa(u[r], xm(V1[(size_t)r * n1 + t], P0));
             }
         }
         if (j < K)
 #pragma unroll
-            for (int r = 0; r < NB; ++r)
-                if (r < nb) {
-                    if constexpr (CPLX) {
-                        o[(2 * r) * K + j] = u[r].x;
-                        o[(2 * r + 1) * K + j] = u[r].y;
-                    } else {
-                        o[r * K + j] = u[r];
+            for (int r = 0; r < NB; ++r) {
+                if constexpr (CPLX) {
+                    o[(2 * r) * K + j] = u[r].x;
+                    o[(2 * r + 1) * K + j] = u[r].y;
+                    if (two) {
+                        op[(2 * r) * K + j] = up[r].x;
+                        op[(2 * r + 1) * K + j] = up[r].y;
                     }
+                } else {
+                    o[r * K + j] = u[r];
                 }
+            }
     }
 }
 
@@ -728,7 +744,8 @@ hobc_status run_gcv_exact(hobc_plan_s* p, const void* ghat, const void* D, doubl
         k_ex_cols<T, CPLX, NB><<<dim3((unsigned)((W1 + kExCB - 1) / kExCB), (unsigned)B), threads, sc, p->stream>>>(
             sp, dp, dps, p->desc.psf_per_item, muT, geo, A0, A1, reinterpret_cast<T*>(x->col_out));
         if (NB > 0)
-            k_ex_rows<T, CPLX, NB><<<dim3((unsigned)n0, (unsigned)B), threads, sr, p->stream>>>(
+            k_ex_rows<T, CPLX, NB><<<dim3((unsigned)(CPLX ? (n0 - 2) / 2 + 3 : n0), (unsigned)B), threads, sr,
+                                     p->stream>>>(
                 sp, dp, dps, p->desc.psf_per_item, muT, geo, A0, A1, reinterpret_cast<T*>(x->row_out));
         k_ex_reduce<T, CPLX, NB><<<dim3((unsigned)B, (unsigned)((K + 31) / 32)), dim3(32, kExSlots), 0, p->stream>>>(
             reinterpret_cast<const T*>(x->col_out), reinterpret_cast<const T*>(x->row_out), A0, A1,
