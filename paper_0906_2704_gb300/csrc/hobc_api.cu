@@ -370,7 +370,7 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half) {
 template cudaError_t build_axis_host<float>(AxisHost&, int, int, int, bool);
 template cudaError_t build_axis_host<double>(AxisHost&, int, int, int, bool);
 
-static void free_axis(AxisHost& a) {
+void free_axis(AxisHost& a) {
     cudaFree(a.tw); cudaFree(a.chirp); cudaFree(a.bhat); cudaFree(a.post); cudaFree(a.q); cudaFree(a.q2);
     cudaFree(a.etab);
     memset(&a, 0, sizeof(a));

@@ -7,6 +7,7 @@
 #include <complex>
 
 #include "../../include/hobc.h"
+#include "../../include/hobc_volume.h"
 
 namespace hobc {
 
@@ -88,6 +89,28 @@ struct hobc_plan_s {
     size_t item0;            // first problem of this view of the plan (0 for the plan itself)
 };
 
+// A 3D plan (include/hobc_volume.h): 2D passes over the slices, a transpose
+// and a pass along axis 0 (hobc_volume.cu, hobc_volume.cuh).
+struct hobc_volume_s {
+    hobc_volume_desc desc;
+    int fam;                 // resolved family
+    int prec;
+    size_t esz;              // bytes of one stored spectral entry
+    cudaStream_t stream;
+    int K, npsf;
+    hobc_plan* slice;        // 2D plan of the (n1, n2) slices, batch x n0 problems (its G is a workspace)
+    hobc::AxisHost az;       // axis 0: complex lines for the Fourier family
+    size_t S2, S3;           // stored entries of a slice and of a volume
+    void* X;                 // [batch][S3] axis-0 lines
+    void* G;                 // [batch][S3] spectrum (hobc_volume_deblur)
+    void* D;                 // [npsf][S3] eigenvalues (hobc_volume_deblur)
+    void* D2;                // [npsf p0][S2] eigenvalues of the PSF's slices
+    double* partials;        // [batch][chunks][2K]
+    int chunk, chunks;
+    int* mu_idx;             // [batch]
+    int launches;
+};
+
 namespace hobc {
 
 template <typename T> hobc_status run_eig(hobc_plan_s* p, const void* psf, void* D);
@@ -109,6 +132,14 @@ hobc_status dense_filter_synthesis(hobc_plan_s* p, const void* ghat, const void*
                                    const double* mu_val, void* f);
 
 template <typename T> cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half);
+void free_axis(AxisHost& a);
+// 3D launch sequences (hobc_volume.cuh); D == nullptr: plain synthesis
+template <typename T> hobc_status run3_analysis(hobc_volume_s* q, const void* g, void* ghat);
+template <typename T> hobc_status run3_synthesis(hobc_volume_s* q, const void* c, void* y, const void* D,
+                                                 const int* mu_idx);
+template <typename T> hobc_status run3_eig(hobc_volume_s* q, const void* psf, void* D);
+template <typename T> hobc_status run3_gcv(hobc_volume_s* q, const void* ghat, const void* D, double* gcv,
+                                           int* mu_idx);
 // exp(-i pi a / b) with the argument reduced exactly; theta_t / pi of spectral
 // index t of a family's axis as the fraction num / den (hobc_api.cu)
 std::complex<double> expm_ipi(long long a, long long b);

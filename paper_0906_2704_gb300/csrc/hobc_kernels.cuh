@@ -558,7 +558,8 @@ struct GcvGeom {
     long long S;        // stored elements per item
     int chunk;          // elements per CTA
     int K;
-};
+    int nz, Nz;         // 3D only: the leading axis, innermost in the volume spectrum
+};                      // (entry e = (c n0 + t0) nz + tz)
 
 template <typename T> struct Pack4;
 template <> struct Pack4<float> { typedef float4 t; };
@@ -694,6 +695,31 @@ __device__ __forceinline__ void gcv_scan(const float4* __restrict__ pk, int cnt,
     }
 }
 
+// |s|^2 of stored element e (1 for L = I; the Laplacian's Kronecker sum, Eq.
+// (eq:L) and reading R8, on 2 or 3 axes) and its stored index c along the last
+// axis.
+template <typename T>
+__device__ __forceinline__ T lap_s2(const GcvGeom& geo, long long e, int& c) {
+    int t0 = 0, tz = 0;
+    if (geo.ndim == 2) {             // e < S <= 1024 x 1024: 32-bit division
+        c = (int)((unsigned)e / (unsigned)geo.n0);
+        t0 = (int)e - c * geo.n0;
+    } else if (geo.ndim == 3) {      // volume spectrum: e = (c n0 + t0) nz + tz
+        const long long e2 = e / geo.nz;
+        tz = (int)(e - e2 * geo.nz);
+        c = (int)(e2 / geo.n0);
+        t0 = (int)(e2 - (long long)c * geo.n0);
+    } else {
+        c = (int)e;
+    }
+    if (!geo.lap) return (T)1;
+    const int t1 = stored_to_t(geo.fam, geo.n1, geo.W1, c);
+    T s = lap_eig<T>(theta_over_pi<T>(geo.fam, geo.n1, geo.N1, t1));
+    if (geo.ndim >= 2) s += lap_eig<T>(theta_over_pi<T>(geo.fam, geo.n0, geo.N0, t0));
+    if (geo.ndim == 3) s += lap_eig<T>(theta_over_pi<T>(geo.fam, geo.nz, geo.Nz, tz));
+    return s * s;
+}
+
 // The GCV terms of stored element e of a problem: x = a = |d|^2 / s^2 (capped),
 // y = w |ghat|^2, z = w, with w = 2 for a Fourier entry that stands for a
 // conjugate pair; an entry with s = 0 contributes nothing.
@@ -701,24 +727,12 @@ template <typename T, bool CPLX>
 __device__ __forceinline__ typename Pack4<T>::t gcv_term(const typename ElemT<T, CPLX>::t& spv,
                                                          const typename ElemT<T, CPLX>::t& dpv, const GcvGeom& geo,
                                                          long long e) {
-    int c, t0 = 0;
-    if (geo.ndim == 2) {             // e < S <= 1024 x 1024: 32-bit division
-        c = (int)((unsigned)e / (unsigned)geo.n0);
-        t0 = (int)e - c * geo.n0;
-    } else {
-        c = (int)e;
-    }
+    int c;
+    const T s2 = lap_s2<T>(geo, e, c);
     T w = 1;
     if (CPLX) {
         const bool self = (c == 0 || c == geo.W1 - 1 || c == 1 || 2 * (c - 1) == geo.N1);
         w = self ? (T)1 : (T)2;
-    }
-    T s2 = 1;
-    if (geo.lap) {
-        const int t1 = stored_to_t(geo.fam, geo.n1, geo.W1, c);
-        T s = lap_eig<T>(theta_over_pi<T>(geo.fam, geo.n1, geo.N1, t1));
-        if (geo.ndim == 2) s += lap_eig<T>(theta_over_pi<T>(geo.fam, geo.n0, geo.N0, t0));
-        s2 = s * s;
     }
     const T lam = abs2_of(dpv);
     const T g2 = abs2_of(spv);

@@ -336,6 +336,8 @@ hobc_status prepare_kernels(hobc_plan_s* p) {
 
 }  // namespace hobc
 
+#include "hobc_volume.cuh"
+
 #define HOBC_INSTANTIATE(T)                                                                                  \
     template hobc_status hobc::run_eig<T>(hobc_plan_s*, const void*, void*);                                 \
     template hobc_status hobc::run_analysis<T>(hobc_plan_s*, const void*, void*);                            \
@@ -345,4 +347,8 @@ hobc_status prepare_kernels(hobc_plan_s* p) {
                                                        void*);                                               \
     template hobc_status hobc::run_filter_synthesis_mu<T>(hobc_plan_s*, const void*, const void*,             \
                                                           const double*, void*);                             \
-    template hobc_status hobc::prepare_kernels<T>(hobc_plan_s*);
+    template hobc_status hobc::prepare_kernels<T>(hobc_plan_s*);                                             \
+    template hobc_status hobc::run3_analysis<T>(hobc_volume_s*, const void*, void*);                         \
+    template hobc_status hobc::run3_synthesis<T>(hobc_volume_s*, const void*, void*, const void*, const int*); \
+    template hobc_status hobc::run3_eig<T>(hobc_volume_s*, const void*, void*);                              \
+    template hobc_status hobc::run3_gcv<T>(hobc_volume_s*, const void*, const void*, double*, int*);

@@ -24,7 +24,8 @@ HEADER_PATHS = [HEADER_PATH, os.path.join(os.path.dirname(_HERE), "include", "ho
                 os.path.join(os.path.dirname(_HERE), "include", "hobc_binned.h"),
                 os.path.join(os.path.dirname(_HERE), "include", "hobc_tc.h"),
                 os.path.join(os.path.dirname(_HERE), "include", "hobc_refine.h"),
-                os.path.join(os.path.dirname(_HERE), "include", "hobc_exact.h")]
+                os.path.join(os.path.dirname(_HERE), "include", "hobc_exact.h"),
+                os.path.join(os.path.dirname(_HERE), "include", "hobc_volume.h")]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_0906_2704_gb300.build`")
@@ -399,6 +400,110 @@ class Plan:
     def close(self) -> None:
         if getattr(self, "_handle", None):
             _lib.hobc_plan_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class VolumeDesc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int * 3),
+        ("psf", ctypes.c_int * 3),
+        ("bc_degree", ctypes.c_int),
+        ("family", ctypes.c_int),
+        ("psf_symmetric", ctypes.c_int),
+        ("L", ctypes.c_int),
+        ("prec", ctypes.c_int),
+        ("n_mu", ctypes.c_int),
+        ("batch", ctypes.c_int),
+        ("psf_per_item", ctypes.c_int),
+    ]
+
+
+_lib.hobc_volume_create.argtypes = [ctypes.POINTER(VolumeDesc), ctypes.POINTER(ctypes.c_double), _vp,
+                                    ctypes.POINTER(_vp)]
+_lib.hobc_volume_create.restype = ctypes.c_int
+_lib.hobc_volume_destroy.argtypes = [_vp]
+_lib.hobc_volume_destroy.restype = None
+_lib.hobc_volume_spectrum_size.argtypes = [_vp, ctypes.POINTER(_sz), ctypes.POINTER(ctypes.c_int)]
+_lib.hobc_volume_spectrum_size.restype = ctypes.c_int
+for _name, _n in (("hobc_volume_analysis", 3), ("hobc_volume_synthesis", 3), ("hobc_volume_eigenvalues", 3),
+                  ("hobc_volume_gcv", 5), ("hobc_volume_filter_synthesis", 5), ("hobc_volume_deblur", 6)):
+    getattr(_lib, _name).argtypes = [_vp] * _n
+    getattr(_lib, _name).restype = ctypes.c_int
+_lib.hobc_volume_launch_count.argtypes = [_vp]
+_lib.hobc_volume_launch_count.restype = ctypes.c_int
+
+
+class Volume:
+    """A plan for 3D arrays [n0][n1][n2] (Sec. 6): tensor-product transforms,
+    3D symbol eigenvalues, GCV and filter per spectral entry."""
+
+    def __init__(self, n, psf, bc_degree: int, mu_grid, L: str = "I", prec: str = "fp64", family: str = "auto",
+                 psf_symmetric: bool = False, batch: int = 1, psf_per_item: bool = False, stream=None):
+        d = VolumeDesc()
+        for i in range(3):
+            d.n[i] = int(n[i])
+            d.psf[i] = int(psf[i])
+        d.bc_degree = int(bc_degree)
+        d.family = FAMILY[family]
+        d.psf_symmetric = int(psf_symmetric)
+        d.L = SMOOTHING[L]
+        d.prec = PRECISION[prec]
+        mus = np.ascontiguousarray(mu_grid, dtype=np.float64)
+        d.n_mu = len(mus)
+        d.batch = int(batch)
+        d.psf_per_item = int(psf_per_item)
+        self.desc = d
+        self.mu_grid = mus
+        h = _vp()
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except ImportError:
+                stream = 0
+        elif not isinstance(stream, int):
+            stream = stream.cuda_stream
+        _check(_lib.hobc_volume_create(ctypes.byref(d), mus.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       _vp(stream), ctypes.byref(h)), "hobc_volume_create")
+        self._handle = h
+        spec, cplx = _sz(), ctypes.c_int()
+        _check(_lib.hobc_volume_spectrum_size(h, ctypes.byref(spec), ctypes.byref(cplx)), "hobc_volume_spectrum_size")
+        self.spec_elems = int(spec.value)
+        self.spec_complex = bool(cplx.value)
+
+    @property
+    def last_launch_count(self) -> int:
+        return _lib.hobc_volume_launch_count(self._handle)
+
+    def analysis(self, g, ghat) -> None:
+        _check(_lib.hobc_volume_analysis(self._handle, _ptr(g), _ptr(ghat)), "hobc_volume_analysis")
+
+    def synthesis(self, c, y) -> None:
+        _check(_lib.hobc_volume_synthesis(self._handle, _ptr(c), _ptr(y)), "hobc_volume_synthesis")
+
+    def eigenvalues(self, psf, d) -> None:
+        _check(_lib.hobc_volume_eigenvalues(self._handle, _ptr(psf), _ptr(d)), "hobc_volume_eigenvalues")
+
+    def gcv(self, ghat, d, gcv, mu_index) -> None:
+        _check(_lib.hobc_volume_gcv(self._handle, _ptr(ghat), _ptr(d), _ptr(gcv), _ptr(mu_index)), "hobc_volume_gcv")
+
+    def filter_synthesis(self, ghat, d, mu_index, f) -> None:
+        _check(_lib.hobc_volume_filter_synthesis(self._handle, _ptr(ghat), _ptr(d), _ptr(mu_index), _ptr(f)),
+               "hobc_volume_filter_synthesis")
+
+    def deblur(self, g, psf, f, mu_index=None, gcv=None) -> None:
+        _check(_lib.hobc_volume_deblur(self._handle, _ptr(g), _ptr(psf), _ptr(f), _ptr(mu_index), _ptr(gcv)),
+               "hobc_volume_deblur")
+
+    def close(self) -> None:
+        if getattr(self, "_handle", None):
+            _lib.hobc_volume_destroy(self._handle)
             self._handle = None
 
     def __del__(self):

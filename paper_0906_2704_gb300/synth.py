@@ -138,6 +138,49 @@ def add_noise(rng: np.random.Generator, g: np.ndarray, eta: float) -> np.ndarray
     return g + eta * np.linalg.norm(g) / np.linalg.norm(e) * e
 
 
+def gaussian_psf_3d(sigmas, taps, offsets=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Product of three 1D Gaussians exp(-((j - o_a)/sigma_a)^2 / 2) on masks of the
+    given odd sizes (nonsymmetric when an offset is nonzero), normalised to sum 1."""
+    axes = []
+    for s, p, o in zip(sigmas, taps, offsets):
+        if p % 2 != 1:
+            raise ValueError("PSF size must be odd")
+        j = np.arange(-(p // 2), p // 2 + 1, dtype=np.float64)
+        axes.append(np.exp(-0.5 * ((j - o) / s) ** 2))
+    h = np.einsum("i,j,k->ijk", *axes)
+    return h / h.sum()
+
+
+def volume_3d(rng: np.random.Generator, n0: int, n1: int, n2: int, pieces: int = 12) -> np.ndarray:
+    """Sum of ``pieces`` random degree-<=2 polynomials on random boxes plus a linear ramp."""
+    z, y, x = np.meshgrid(np.linspace(0, 1, n0), np.linspace(0, 1, n1), np.linspace(0, 1, n2), indexing="ij")
+    a = rng.uniform(-1.0, 1.0, size=4)
+    f = a[0] + a[1] * x + a[2] * y + a[3] * z
+    for _ in range(pieces):
+        lo = [int(rng.integers(0, m)) for m in (n0, n1, n2)]
+        hi = [min(m, l0 + 1 + int(rng.integers(0, m))) for l0, m in zip(lo, (n0, n1, n2))]
+        sl = tuple(slice(l0, h0) for l0, h0 in zip(lo, hi))
+        k = rng.uniform(-1.0, 1.0, size=7)
+        xs, ys, zs = x[sl], y[sl], z[sl]
+        f[sl] += k[0] + k[1] * xs + k[2] * ys + k[3] * zs + k[4] * xs * ys + k[5] * zs * zs + k[6] * xs * xs
+    return f
+
+
+def problem_3d(seed: int, n0: int, n1: int, n2: int, h: np.ndarray, eta: float, count: int = 1):
+    """``count`` seeded 3D problems: the valid part of the blurred extended volume
+    plus noise (the 3D form of the data model).  Returns (g[count, n0, n1, n2], f_true)."""
+    from scipy.signal import fftconvolve
+    rng = np.random.default_rng(seed)
+    m = [p // 2 for p in h.shape]
+    g = np.empty((count, n0, n1, n2))
+    ft = np.empty_like(g)
+    for i in range(count):
+        f_ext = volume_3d(rng, n0 + 2 * m[0], n1 + 2 * m[1], n2 + 2 * m[2])
+        g[i] = add_noise(rng, fftconvolve(f_ext, h, mode="valid"), eta)
+        ft[i] = f_ext[m[0]:m[0] + n0, m[1]:m[1] + n1, m[2]:m[2] + n2]
+    return g, ft
+
+
 def mu_grid(k: int, lo: float = 1e-8, hi: float = 1.0) -> np.ndarray:
     """k log-spaced regularisation parameters, endpoints included."""
     if k == 1:

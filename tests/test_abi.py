@@ -110,5 +110,10 @@ def test_learned_entry_points_reject_bad_arguments_on_the_host(hobc):
     assert lib.hobc_deblur_refined(None, None, None, None, None, None) == arg
     assert lib.hobc_filter_synthesis_mu(None, None, None, None, None) == arg
     assert lib.hobc_gcv_exact(None, None, None, None, None) == arg
+    assert lib.hobc_volume_create(None, None, None, None) == arg
+    assert lib.hobc_volume_deblur(None, None, None, None, None, None) == arg
+    assert lib.hobc_volume_analysis(None, None, None) == arg
+    assert lib.hobc_volume_launch_count(None) == 0
+    lib.hobc_volume_destroy(None)
     assert lib.hobc_deblur_exact(None, None, None, None, None, None) == arg
     lib.hobc_mlp_destroy(None)
