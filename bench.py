@@ -425,6 +425,8 @@ def run_other(args):
                 PSF (sigma U[1,4]) and degree in {1,2,3}, Laplacian, 128 mu, 1% noise
     signals1d -- 65,536 signals n = 256, Gaussian sigma 2 (9 taps), antireflective,
                 L = I, 64 mu in [1e-8, 1], 1% noise
+    volume128 -- 8 volumes 128^3, separable Gaussian 9^3 sigma 1.5, degree 2 (cosine),
+                Laplacian, 128 mu, 1% noise (the tensor-product transform of Sec. 6)
     cosine512 -- 512 x 512, separable Gaussian 15 x 15 sigma 2.5, degree 2 (cosine),
                 Laplacian, 256 mu, 0.5% noise, batch 32"""
     import torch
@@ -470,6 +472,26 @@ def run_other(args):
             cfg = {"workload": "65536 1D signals n=256, Gaussian sigma 2 (9 taps), antireflective, L=I, 64 mu, 1% noise",
                    "batch": B}
             io_bytes = 2 * B * n * np.dtype(npdt).itemsize
+        elif args.workload == "volume128":
+            n, B, K = 128, 8, 128
+            hh = synth.gaussian_psf_3d((1.5, 1.5, 1.5), (9, 9, 9))
+            gg, _ = synth.problem_3d(9, n, n, n, hh, 0.01, count=B)
+            vol = hobc.Volume((n, n, n), hh.shape, 2, synth.mu_grid(K), L="lap", prec=prec, family="cosine",
+                              psf_symmetric=True, batch=B, stream=stream)
+            g = torch.from_numpy(gg.astype(npdt)).to(dev)
+            h = torch.from_numpy(hh.astype(npdt)).to(dev)
+            f = torch.empty_like(g)
+            mi = torch.empty(B, dtype=torch.int32, device=dev)
+            ms, clocks = _timed(lambda: vol.deblur(g, h, f, mi), stream, args.steps, args.warmup)
+            units, unit, launches = B, "volumes/s", vol.last_launch_count
+            cfg = {"workload": f"{B} volumes {n}^3, separable Gaussian 9^3 sigma 1.5, degree 2 (cosine), Laplacian, "
+                               f"{K} mu, 1% noise", "batch": B}
+            io_bytes = 2 * B * n ** 3 * np.dtype(npdt).itemsize
+            S = vol.spec_elems
+            gh = torch.empty((B, S), dtype=g.dtype, device=dev)
+            ms_a, _ = _timed(lambda: vol.analysis(g, gh), stream, args.steps, 2)
+            ms_s, _ = _timed(lambda: vol.synthesis(gh, f), stream, args.steps, 2)
+            extra = {"transform_ms_per_step": {"analysis": ms_a / args.steps, "synthesis": ms_s / args.steps}}
         else:
             n = 1024 if args.workload == "cosine1024" else 512
             B, K = (16 if n == 1024 else 32), 256
@@ -789,7 +811,7 @@ def main():
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["fourier1024", "batched", "signals1d", "cosine512", "cosine1024",
-                                           "learned", "bccompare"],
+                                           "learned", "bccompare", "volume128"],
                     default="fourier1024")
     ap.add_argument("--train", type=int, default=8192, help="training problems of the learned workload")
     ap.add_argument("--epochs", type=int, default=60, help="training epochs of the learned workload")

@@ -37,28 +37,30 @@ k_vol_transpose(const E* __restrict__ in, E* __restrict__ out, int R, long long 
 // (-theta_t0, -theta_t1, -theta_t2) is sum_j0 exp(-i (j0 - m0) theta_t0)
 // d2_j0(t1, t2), with d2_j0 the 2D eigenvalues of slice j0 (FP64 sums; real
 // families keep the real part, the imaginary one cancels for a PSF symmetric
-// along axis 0).  grid = (ceil(S2 / 256), PSFs), block = 256.
+// along axis 0).  One CTA per slice entry e2 (its p0 slice values staged in
+// shared memory), threads over t0, so each CTA writes nz consecutive entries.
+// grid = (S2, PSFs), block = min(nz, 256) rounded to a warp.
 template <typename T, bool CPLX>
-__global__ void k_vol_eig(const typename ElemT<T, CPLX>::t* __restrict__ D2, int p0, long long S2,
-                          const double2* __restrict__ Ez, int nz, typename ElemT<T, CPLX>::t* __restrict__ D3,
-                          long long S3) {
+__global__ void __launch_bounds__(256)
+k_vol_eig(const typename ElemT<T, CPLX>::t* __restrict__ D2, int p0, long long S2, const double2* __restrict__ Ez,
+          int nz, typename ElemT<T, CPLX>::t* __restrict__ D3, long long S3) {
     typedef typename ElemT<T, CPLX>::t E;
-    const long long e2 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e2 >= S2) return;
+    __shared__ double2 v[64];
+    const long long e2 = blockIdx.x;
     const long long ip = blockIdx.y;
-    const E* d2 = D2 + ip * p0 * S2 + e2;
+    for (int j = threadIdx.x; j < p0; j += blockDim.x) {
+        const E d = D2[(ip * p0 + j) * S2 + e2];
+        if constexpr (CPLX) v[j] = make_double2((double)d.x, (double)d.y);
+        else v[j] = make_double2((double)d, 0.0);
+    }
+    __syncthreads();
     E* o = D3 + ip * S3 + e2 * nz;
-    for (int tz = 0; tz < nz; ++tz) {
+    for (int tz = threadIdx.x; tz < nz; tz += blockDim.x) {
         double re = 0, im = 0;
         for (int j = 0; j < p0; ++j) {
             const double2 e = Ez[(long long)tz * p0 + j];
-            const E v = d2[(long long)j * S2];
-            if constexpr (CPLX) {
-                re += e.x * (double)v.x - e.y * (double)v.y;
-                im += e.x * (double)v.y + e.y * (double)v.x;
-            } else {
-                re += e.x * (double)v;
-            }
+            re += e.x * v[j].x - e.y * v[j].y;
+            im += e.x * v[j].y + e.y * v[j].x;
         }
         if constexpr (CPLX) o[tz] = cmk<T>((T)re, (T)im);
         else o[tz] = (T)re;
@@ -186,16 +188,17 @@ hobc_status run3_eig(hobc_volume_s* q, const void* psf, void* D) {
     const long long S2 = (long long)q->S2, S3 = (long long)q->S3;
     const long long slice_psf = (long long)a1.p * a2.p;
     const dim3 g2((unsigned)(q->npsf * p0), (unsigned)a2.W);
-    const dim3 g3((unsigned)((S2 + 255) / 256), (unsigned)q->npsf);
+    const dim3 g3((unsigned)S2, (unsigned)q->npsf);
+    const int b3 = std::min(256, (q->az.n + 31) / 32 * 32);
     if (q->fam == FAM_F) {
         k_eig<T, true><<<g2, 256, 0, q->stream>>>(reinterpret_cast<const T*>(psf), slice_psf, a1.p, a2.p, a1.etab,
                                                   a2.etab, a1.n, reinterpret_cast<C2<T>*>(q->D2), S2);
-        k_vol_eig<T, true><<<g3, 256, 0, q->stream>>>(reinterpret_cast<const C2<T>*>(q->D2), p0, S2, q->az.etab,
+        k_vol_eig<T, true><<<g3, b3, 0, q->stream>>>(reinterpret_cast<const C2<T>*>(q->D2), p0, S2, q->az.etab,
                                                       q->az.n, reinterpret_cast<C2<T>*>(D), S3);
     } else {
         k_eig<T, false><<<g2, 256, 0, q->stream>>>(reinterpret_cast<const T*>(psf), slice_psf, a1.p, a2.p, a1.etab,
                                                    a2.etab, a1.n, reinterpret_cast<T*>(q->D2), S2);
-        k_vol_eig<T, false><<<g3, 256, 0, q->stream>>>(reinterpret_cast<const T*>(q->D2), p0, S2, q->az.etab,
+        k_vol_eig<T, false><<<g3, b3, 0, q->stream>>>(reinterpret_cast<const T*>(q->D2), p0, S2, q->az.etab,
                                                        q->az.n, reinterpret_cast<T*>(D), S3);
     }
     hobc_status s = check_launch(sl, "k_eig");
