@@ -144,10 +144,12 @@ hobc_status hobc_deblur(hobc_plan* plan, const void* g_dev, const void* psf_dev,
 
 /* hobc_deblur with HOST buffers: copies g and the PSF(s) to the plan's
  * workspace, runs the method, copies f (and mu index, G if non-NULL) back, and
- * returns when all of it has finished.  The batch runs as up to four chunks on
- * two internal streams (created on the first call, ordered after the plan's
- * stream), so the copies of one chunk overlap the kernels of another; copies
- * overlap only when the host buffers are page-locked. */
+ * returns when all of it has finished.  The batch runs as up to eight chunks:
+ * their uploads back to back on an internal stream, each chunk's kernels on the
+ * plan's stream once its upload is done, each download on a second internal
+ * stream once its kernels are done (streams created on the first call), so the
+ * copies overlap the kernels of other chunks; copies overlap only when the host
+ * buffers are page-locked. */
 hobc_status hobc_deblur_host(hobc_plan* plan, const void* g_host, const void* psf_host,
                              void* f_host, int* mu_index_host, double* gcv_host);
 

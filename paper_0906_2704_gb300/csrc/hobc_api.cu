@@ -413,6 +413,10 @@ void hobc_plan_destroy(hobc_plan* p) {
     for (int i = 0; i < 2; ++i)
         if (p->aux[i]) cudaStreamDestroy(p->aux[i]);
     if (p->aux_ev) cudaEventDestroy(p->aux_ev);
+    for (int i = 0; i < 8; ++i) {
+        if (p->ev_up[i]) cudaEventDestroy(p->ev_up[i]);
+        if (p->ev_done[i]) cudaEventDestroy(p->ev_done[i]);
+    }
     delete p;
 }
 
@@ -612,6 +616,8 @@ static hobc_plan_s chunk_view(const hobc_plan_s* p, size_t c0, size_t cb, cudaSt
     return v;
 }
 
+static const size_t kHostChunks = 8;   // chunks of the host-buffer pipeline (events per chunk in the plan)
+
 hobc_status hobc_deblur_host(hobc_plan* p, const void* g, const void* psf, void* f, int* mu_idx, double* gcv) {
     if (!p || !g || !psf || !f) return HOBC_ERR_ARG;
     p->launches = 0;
@@ -621,40 +627,59 @@ hobc_status hobc_deblur_host(hobc_plan* p, const void* g, const void* psf, void*
     for (int i = 0; i < 2 && e == cudaSuccess; ++i)
         if (!p->aux[i]) e = cudaStreamCreateWithFlags(&p->aux[i], cudaStreamNonBlocking);
     if (e == cudaSuccess && !p->aux_ev) e = cudaEventCreateWithFlags(&p->aux_ev, cudaEventDisableTiming);
+    // the uploads wait for earlier work on the plan's stream (the workspace is
+    // free), not for the eigenvalues queued next
+    if (e == cudaSuccess) e = cudaEventRecord(p->aux_ev, p->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux[0], p->aux_ev, 0);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->psf_in, psf, (size_t)p->npsf * p->psf_elems * p->esz, cudaMemcpyHostToDevice, p->stream);
     if (e != cudaSuccess) { set_last_error("hobc_deblur_host H2D", e); return HOBC_ERR_CUDA; }
     hobc_status s = HOBC_DISPATCH(p, run_eig, p->psf_in, p->D);
     if (s != HOBC_OK) return s;
-    e = cudaEventRecord(p->aux_ev, p->stream);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(p->aux[i], p->aux_ev, 0);
-    // chunks alternate between two streams, so that one chunk's copies overlap
-    // the other's kernels; the small outputs follow once every chunk is queued
-    // (a copy to pageable host memory holds the host thread until it is done)
-    const size_t nchunk = B >= 4 ? 4 : B;
+    // three-stage pipeline over chunks of the batch: every upload back to back
+    // on aux[0], each chunk's kernels in order on the plan's stream once its
+    // upload is done, each download on aux[1] once its kernels are done; only
+    // the first upload and the last download are not overlapped
+    const size_t nchunk = B >= kHostChunks ? kHostChunks : B;
     const size_t cb = (B + nchunk - 1) / nchunk;
+    for (size_t i = 0; i < nchunk && e == cudaSuccess; ++i) {
+        if (!p->ev_up[i]) e = cudaEventCreateWithFlags(&p->ev_up[i], cudaEventDisableTiming);
+        if (e == cudaSuccess && !p->ev_done[i]) e = cudaEventCreateWithFlags(&p->ev_done[i], cudaEventDisableTiming);
+    }
+    for (size_t c0 = 0, c = 0; c0 < B && e == cudaSuccess; c0 += cb, ++c) {
+        const size_t n = std::min(cb, B - c0);
+        e = cudaMemcpyAsync(static_cast<char*>(p->g_in) + c0 * ib, static_cast<const char*>(g) + c0 * ib, n * ib,
+                            cudaMemcpyHostToDevice, p->aux[0]);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_up[c], p->aux[0]);
+    }
     for (size_t c0 = 0, c = 0; c0 < B && e == cudaSuccess && s == HOBC_OK; c0 += cb, ++c) {
         const size_t n = std::min(cb, B - c0);
-        hobc_plan_s v = chunk_view(p, c0, n, p->aux[c % 2]);
-        e = cudaMemcpyAsync(v.g_in, static_cast<const char*>(g) + c0 * ib, n * ib, cudaMemcpyHostToDevice, v.stream);
+        e = cudaStreamWaitEvent(p->stream, p->ev_up[c], 0);
         if (e != cudaSuccess) break;
+        hobc_plan_s v = chunk_view(p, c0, n, p->stream);
         s = HOBC_DISPATCH(&v, run_analysis, v.g_in, v.G);
         if (s == HOBC_OK) s = HOBC_DISPATCH(&v, run_gcv, v.G, v.D, gcv ? v.gcv : nullptr, v.mu_idx);
         if (s == HOBC_OK) s = HOBC_DISPATCH(&v, run_filter_synthesis, v.G, v.D, v.mu_idx, v.f_out);
         p->launches += v.launches;
         if (s != HOBC_OK) break;
-        e = cudaMemcpyAsync(static_cast<char*>(f) + c0 * ib, v.f_out, n * ib, cudaMemcpyDeviceToHost, v.stream);
+        e = cudaEventRecord(p->ev_done[c], p->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux[1], p->ev_done[c], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(static_cast<char*>(f) + c0 * ib, v.f_out, n * ib, cudaMemcpyDeviceToHost, p->aux[1]);
     }
-    for (size_t c0 = 0, c = 0; c0 < B && e == cudaSuccess && s == HOBC_OK; c0 += cb, ++c) {
-        const size_t n = std::min(cb, B - c0);
-        cudaStream_t st = p->aux[c % 2];
-        if (mu_idx) e = cudaMemcpyAsync(mu_idx + c0, p->mu_idx + c0, n * sizeof(int), cudaMemcpyDeviceToHost, st);
+    // the small outputs follow once every chunk is queued (a copy to pageable
+    // host memory holds the host thread until it is done)
+    if (e == cudaSuccess && s == HOBC_OK) {
+        if (mu_idx) e = cudaMemcpyAsync(mu_idx, p->mu_idx, B * sizeof(int), cudaMemcpyDeviceToHost, p->aux[1]);
         if (e == cudaSuccess && gcv)
-            e = cudaMemcpyAsync(gcv + c0 * p->K, p->gcv + c0 * p->K, n * p->K * sizeof(double), cudaMemcpyDeviceToHost,
-                                st);
+            e = cudaMemcpyAsync(gcv, p->gcv, B * p->K * sizeof(double), cudaMemcpyDeviceToHost, p->aux[1]);
     }
     for (int i = 0; i < 2; ++i) {
         const cudaError_t e2 = cudaStreamSynchronize(p->aux[i]);
+        if (e == cudaSuccess) e = e2;
+    }
+    {
+        const cudaError_t e2 = cudaStreamSynchronize(p->stream);
         if (e == cudaSuccess) e = e2;
     }
     if (s != HOBC_OK) return s;

@@ -81,8 +81,10 @@ struct hobc_plan_s {
     void* a_edges;           // [129] bin edges, plan precision
     int* k_hat;              // [batch] argmin of the binned G
     double* refine_state;    // [batch][4] lo, mid, hi (log10 mu) and the incumbent mu of the refinement
-    cudaStream_t aux[2];     // host-buffer pipeline streams (created on first use)
+    cudaStream_t aux[2];     // host-buffer pipeline: upload and download streams (created on first use)
     cudaEvent_t aux_ev;
+    cudaEvent_t ev_up[8];    // per chunk of the host-buffer pipeline: upload done, kernels done
+    cudaEvent_t ev_done[8];
     int grid_ascending;      // 1 if the mu grid is strictly increasing
     struct hobc_dense_s* dense;   // HOBC_SPLIT_BF16: matrices and operand workspace (hobc_tc.cu)
     struct hobc_exact_s* exact;   // exact GCV: Gram factors and line sums, allocated on first use (hobc_exact.cu)
