@@ -204,3 +204,28 @@ def test_full_size_1024_fourier_fp32_at_sampled_mu():
     bound = _bound("F", n, ghat, d, s, mus[js], "fp32")
     rel = np.abs(G_d.cpu().numpy()[0, js] - Go) / Go
     assert np.all(rel <= bound), f"{rel} > {bound}"
+
+
+@pytest.mark.parametrize("fam,n", [("sine", 6), ("cosine", 6), ("fourier", 6), ("sine3", 8)])
+def test_exact_smallest_field_of_view_and_single_mu(fam, n):
+    """n = 6 (8 for degree 3) in 1D and 2D, K = 1 and K = 3: the curve against the oracle."""
+    F = P.FAM_LETTER[fam]
+    h = np.array([0.25, 0.5, 0.25])
+    for K in (1, 3):
+        mus = synth.mu_grid(K, 1e-3, 1.0)
+        g, _ = synth.problem_1d(2, n, h, 0.01)
+        plan = hobc.Plan(1, n, 3, DEG[fam], mus, family=fam, psf_symmetric=True, batch=1)
+        G = torch.empty((1, K), dtype=torch.float64, device="cuda")
+        f = torch.empty((1, n), dtype=torch.float64, device="cuda")
+        plan.deblur_exact(_dev(g, np.float64), _dev(h, np.float64), f, None, G)
+        ghat, d, s = O.analysis_1d(F, g[0]), O.eigenvalues_1d(F, h, n), O.smoothing_1d(F, n, "I")
+        assert np.allclose(G.cpu().numpy()[0], X.gcv_exact_curve(F, ghat, d, s, mus), rtol=1e-10, atol=0)
+        h2 = np.outer(h, h)
+        g2, _ = synth.problem_2d(3, n, n + 1, h2, 0.01)
+        plan2 = hobc.Plan(2, (n, n + 1), (3, 3), DEG[fam], mus, family=fam, psf_symmetric=True, batch=1)
+        G2 = torch.empty((1, K), dtype=torch.float64, device="cuda")
+        f2 = torch.empty((1, n, n + 1), dtype=torch.float64, device="cuda")
+        plan2.deblur_exact(_dev(g2, np.float64), _dev(h2, np.float64), f2, None, G2)
+        gh2 = O.analysis_2d(F, g2[0])
+        d2, s2 = O.eigenvalues_2d(F, h2, n, n + 1), O.smoothing_2d(F, n, n + 1, "I")
+        assert np.allclose(G2.cpu().numpy()[0], X.gcv_exact_curve(F, gh2, d2, s2, mus), rtol=1e-9, atol=0)

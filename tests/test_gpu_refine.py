@@ -177,3 +177,19 @@ def test_refine_rejects_a_decreasing_grid():
     mu = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(hobc.HobcError, match="increasing"):
         plan.gcv_refine(t, t, mi, mu)
+
+
+def test_refine_single_grid_value_keeps_it():
+    """K = 1: the bracket collapses to the grid value; mu* is that value up to the rounding of
+    10^(log10 mu) in the working precision."""
+    mus = np.array([2e-3])
+    h = np.array([0.25, 0.5, 0.25])
+    g, _ = synth.problem_1d(1, 40, h, 0.01, count=2)
+    for prec, dt in (("fp64", np.float64), ("fp32", np.float32)):
+        plan = hobc.Plan(1, 40, 3, 2, mus, prec=prec, family="cosine", psf_symmetric=True, batch=2)
+        f = torch.empty((2, 40), dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda")
+        mu = torch.empty(2, dtype=torch.float64, device="cuda")
+        mi = torch.empty(2, dtype=torch.int32, device="cuda")
+        plan.deblur_refined(_dev(g, dt), _dev(h, dt), f, mi, mu)
+        assert np.all(mi.cpu().numpy() == 0)
+        assert np.allclose(mu.cpu().numpy(), 2e-3, rtol=4 * float(np.finfo(dt).eps), atol=0)

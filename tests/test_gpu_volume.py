@@ -185,3 +185,21 @@ def test_volume_rejects_what_it_does_not_support():
     with pytest.raises(hobc.HobcError) as e:
         hobc.Volume((1024, 8, 8), (3, 3, 3), 2, mus, family="cosine", psf_symmetric=True, batch=64)
     assert e.value.status == hobc.STATUS.index("HOBC_ERR_SIZE")
+
+
+@pytest.mark.parametrize("fam", ["sine", "cosine", "fourier"])
+def test_volume_smallest_field_of_view_and_single_mu(fam):
+    """6 x 6 x 7 volumes, a 3-tap PSF per axis, K = 1: the whole path against the oracle."""
+    F = P.FAM_LETTER[fam]
+    n = (6, 6, 7)
+    h = synth.gaussian_psf_3d((0.8, 0.9, 0.7), (3, 3, 3), (0.2, 0.0, -0.1) if F == "F" else (0, 0, 0))
+    g, _ = synth.problem_3d(5, *n, h, 0.01, count=1)
+    mus = np.array([3e-3])
+    plan = hobc.Volume(n, h.shape, DEG[fam], mus, L="lap", prec="fp64", family=fam, psf_symmetric=F != "F")
+    f = torch.empty((1,) + n, dtype=torch.float64, device="cuda")
+    G = torch.empty((1, 1), dtype=torch.float64, device="cuda")
+    mi = torch.empty(1, dtype=torch.int32, device="cuda")
+    plan.deblur(_dev(g, np.float64), _dev(h, np.float64), f, mi, G)
+    fo, Go, ko, _ = V.deblur_3d(F, h, g[0], "lap", mus)
+    assert int(mi[0]) == 0 and abs(G[0, 0].item() - Go[0]) <= 1e-10 * Go[0]
+    assert np.abs(f[0].cpu().numpy() - fo).max() <= 1e-9 * np.abs(fo).max()
