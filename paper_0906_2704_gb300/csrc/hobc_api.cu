@@ -289,8 +289,19 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half) {
     a.H = fam == hobc::FAM_F ? N / 2 + 1 : N;
     a.W = (fam == hobc::FAM_F && half) ? a.H + 2 : n;
 
-    std::vector<cd> tw(a.M);
-    for (int k = 0; k < a.M; ++k) tw[k] = expm_ipi(2LL * k, a.M);
+    // per-stage twiddle tables in the order group_fft runs the stages: radix 8
+    // while three or more bits remain, then radix 4 or 2; a stage with Ns > 1
+    // stores W_{Ns R}^{pw k} = W_M^{pw (M / (Ns R)) k} for pw = 1, 2, 4 (those < R), k < Ns
+    std::vector<cd> tw;
+    for (int Ns = 1, rem = a.log2M; rem > 0;) {
+        const int R = rem >= 3 ? 8 : (1 << rem);
+        if (Ns > 1)
+            for (int pw = 1; pw < R; pw *= 2)
+                for (int k = 0; k < Ns; ++k) tw.push_back(expm_ipi(2LL * pw * (a.M / (Ns * R)) * k, a.M));
+        Ns *= R;
+        rem -= R == 8 ? 3 : R == 4 ? 2 : 1;
+    }
+    if (tw.empty()) tw.push_back(cd(1, 0));
     a.tw = upload_complex<T>(tw, err);
     if (a.blue) {
         std::vector<cd> chirp(a.L), c(a.M, cd(0, 0));

@@ -49,7 +49,7 @@ struct Axis {
     int Mp;         // shared-memory slots per group: M plus one pad slot per 16 (pidx)
     int H;          // FOURIER: floor(N/2)+1 stored frequencies; else N
     int W;          // spectrum entries stored on this axis: n (S, C) or H+2 (F)
-    const C2<T>* tw;      // [M] exp(-2 pi i k / M)
+    const C2<T>* tw;      // per-stage twiddle tables of the FFT, concatenated (< M entries)
     const C2<T>* chirp;   // [L] exp(-i pi (k^2 mod 2L) / L)
     const C2<T>* bhat;    // [M] FFT_M(conj-chirp, wrapped) / M
     const C2<T>* post;    // COSINE: [N] exp(-i pi k / (2N))
@@ -99,8 +99,17 @@ template <typename T> __device__ __forceinline__ void dft8(C2<T>* v) {
 // One Stockham autosort stage of radix R on buf[0..M): butterfly j reads
 // buf[j + r M/R], twiddles by W_{Ns R}^{r (j mod Ns)}, does an R-point DFT, and
 // writes buf[(j - j mod Ns) R + j mod Ns + r Ns].  Each thread holds 8 values.
-template <int R, typename T>
-__device__ __forceinline__ void fft_stage(C2<T>* buf, int M, int Ns, const C2<T>* __restrict__ tw,
+// tws is this stage's twiddle table, laid out [power][k] (powers 1, 2, 4 of
+// W_{Ns R}^k, k < Ns) so a warp's loads are contiguous; the other powers are
+// formed with one complex product each (two roundings at most).
+// FIRST marks the stage with Ns = 1 (no twiddles); it reads positions < lim_in
+// only (the rest are zero: the Bluestein padding) and, with PRE, multiplies
+// each value read by pre[] and conjugates it (the chirp product between the
+// two Bluestein FFTs).  Writes at positions >= lim_out are dropped (outputs
+// nobody reads).
+template <int R, bool FIRST, bool PRE, typename T>
+__device__ __forceinline__ void fft_stage(C2<T>* buf, int M, int Ns, const C2<T>* __restrict__ tws,
+                                          const C2<T>* __restrict__ pre, int lim_in, int lim_out,
                                           int t, int tpg) {
     constexpr int PER = 8 / R;
     const int nb = M / R;
@@ -108,15 +117,12 @@ __device__ __forceinline__ void fft_stage(C2<T>* buf, int M, int Ns, const C2<T>
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int j = t + u * tpg;
-        const int k = j & (Ns - 1);
-        const int step = (M / (Ns * R)) * k;
-        // twiddles W^{r step}: load W^step, W^{2 step}, W^{4 step}; form the rest
-        // with one complex product each (two roundings at most)
+        const int k = FIRST ? 0 : (j & (Ns - 1));
         C2<T> w[8];
-        if (Ns > 1) {
-            w[1] = tw[step];
-            if (R >= 4) w[2] = tw[2 * step];
-            if (R == 8) w[4] = tw[4 * step];
+        if (!FIRST) {
+            w[1] = tws[k];
+            if (R >= 4) w[2] = tws[Ns + k];
+            if (R == 8) w[4] = tws[2 * Ns + k];
             if (R >= 4) w[3] = cmul<T>(w[1], w[2]);
             if (R == 8) {
                 w[5] = cmul<T>(w[1], w[4]);
@@ -126,8 +132,18 @@ __device__ __forceinline__ void fft_stage(C2<T>* buf, int M, int Ns, const C2<T>
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            C2<T> x = buf[pidx(j + r * nb)];
-            if (r > 0 && Ns > 1) x = cmul<T>(x, w[r]);
+            const int p = j + r * nb;
+            C2<T> x;
+            if (FIRST) {
+                x = cmk<T>(0, 0);
+                if (p < lim_in) {
+                    x = buf[pidx(p)];
+                    if (PRE) x = cconj<T>(cmul<T>(x, pre[p]));
+                }
+            } else {
+                x = buf[pidx(p)];
+                if (r > 0) x = cmul<T>(x, w[r]);
+            }
             v[u * R + r] = x;
         }
         if (R == 8) dft8<T>(v + u * R);
@@ -142,26 +158,34 @@ __device__ __forceinline__ void fft_stage(C2<T>* buf, int M, int Ns, const C2<T>
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int j = t + u * tpg;
-        const int k = j & (Ns - 1);
+        const int k = FIRST ? 0 : (j & (Ns - 1));
         const int base = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[pidx(base + r * Ns)] = v[u * R + r];
+        for (int r = 0; r < R; ++r)
+            if (base + r * Ns < lim_out) buf[pidx(base + r * Ns)] = v[u * R + r];
     }
     __syncthreads();
 }
 
 // Forward power-of-two FFT (exp(-i ...)) of buf[0..M) in place.  Every thread of
-// the CTA must call it (it synchronises the CTA); t in [0, M/8).
-template <typename T>
-__device__ __forceinline__ void group_fft(C2<T>* buf, const Axis<T>& ax, int t) {
-    int Ns = 1, rem = ax.log2M;
+// the CTA must call it (it synchronises the CTA); t in [0, M/8).  The first
+// stage (radix 8: M >= 8) reads positions < lim_in (the rest are zero) and,
+// with PRE, applies the pre[] product; the last stage writes positions < lim_out only.
+template <bool PRE, typename T>
+__device__ __forceinline__ void group_fft(C2<T>* buf, const Axis<T>& ax, int t, const C2<T>* pre, int lim_in,
+                                          int lim_out) {
+    const int M = ax.M;
+    int rem = ax.log2M - 3;
+    fft_stage<8, true, PRE, T>(buf, M, 1, nullptr, pre, lim_in, rem == 0 ? lim_out : M, t, ax.tpg);
+    int Ns = 8, off = 0;
     while (rem >= 3) {
-        fft_stage<8, T>(buf, ax.M, Ns, ax.tw, t, ax.tpg);
-        Ns <<= 3;
         rem -= 3;
+        fft_stage<8, false, false, T>(buf, M, Ns, ax.tw + off, nullptr, M, rem == 0 ? lim_out : M, t, ax.tpg);
+        off += 3 * Ns;
+        Ns <<= 3;
     }
-    if (rem == 2) fft_stage<4, T>(buf, ax.M, Ns, ax.tw, t, ax.tpg);
-    else if (rem == 1) fft_stage<2, T>(buf, ax.M, Ns, ax.tw, t, ax.tpg);
+    if (rem == 2) fft_stage<4, false, false, T>(buf, M, Ns, ax.tw + off, nullptr, M, lim_out, t, ax.tpg);
+    else if (rem == 1) fft_stage<2, false, false, T>(buf, M, Ns, ax.tw + off, nullptr, M, lim_out, t, ax.tpg);
 }
 
 // Input side of the length-L DFT: value placed at position p of the core.
@@ -170,17 +194,19 @@ __device__ __forceinline__ C2<T> dft_in(const Axis<T>& ax, int p, C2<T> x) {
     return ax.blue ? cmul<T>(x, ax.chirp[p]) : x;
 }
 
-// The length-L DFT of what dft_in placed in buf (positions >= L zero when
-// Bluestein is used).  Leaves buf such that dft_out(k) is output k.
+// The length-L DFT of what dft_in placed in buf[0..L) (nothing needs to be
+// stored at positions >= L: the first stage reads them as zero).  Leaves buf
+// such that dft_out(k), k < L, is output k; positions >= L are left undefined.
 template <typename T>
 __device__ __forceinline__ void group_dft(C2<T>* buf, const Axis<T>& ax, int t) {
-    group_fft<T>(buf, ax, t);
     if (ax.blue) {
+        group_fft<false, T>(buf, ax, t, nullptr, ax.L, ax.M);
         // pointwise product with the transformed chirp, conjugated so the
-        // second forward FFT computes the inverse (1/M folded into bhat)
-        for (int p = t; p < ax.M; p += ax.tpg) buf[pidx(p)] = cconj<T>(cmul<T>(buf[pidx(p)], ax.bhat[p]));
-        __syncthreads();
-        group_fft<T>(buf, ax, t);
+        // second forward FFT computes the inverse (1/M folded into bhat),
+        // applied as the second FFT's first stage reads
+        group_fft<true, T>(buf, ax, t, ax.bhat, ax.M, ax.L);
+    } else {
+        group_fft<false, T>(buf, ax, t, nullptr, ax.M, ax.M);
     }
 }
 

@@ -148,8 +148,6 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
         }
     }
     if ((FAM == FAM_S || CUBIC) && t == 0) { buf[pidx(0)] = zero; buf[pidx(N + 1)] = zero; }
-    if (ax.blue)
-        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[pidx(p)] = zero;
     __syncthreads();
     group_dft<T>(buf, ax, t);
 
@@ -313,8 +311,6 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM 
         }
         if (t == 0) { buf[pidx(0)] = zero; buf[pidx(N + 1)] = zero; }
     }
-    if (ax.blue)
-        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[pidx(p)] = zero;
     __syncthreads();
     group_dft<T>(buf, ax, t);
 
@@ -429,8 +425,6 @@ k_cplx_analysis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long
         }
         buf[pidx(j)] = dft_in<T>(ax, j, w);
     }
-    if (ax.blue)
-        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[pidx(p)] = cmk<T>(0, 0);
     __syncthreads();
     group_dft<T>(buf, ax, t);
     if (!valid) return;
@@ -466,8 +460,6 @@ k_cplx_synthesis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long lon
         const C2<T> v = valid ? coef(1 + k) : cmk<T>(0, 0);
         buf[pidx(k)] = dft_in<T>(ax, k, cconj<T>(v));
     }
-    if (ax.blue)
-        for (int p = ax.L + t; p < ax.M; p += ax.tpg) buf[pidx(p)] = cmk<T>(0, 0);
     __syncthreads();
     group_dft<T>(buf, ax, t);
     if (!valid) return;
