@@ -288,7 +288,7 @@ Axis<T> to_dev_axis(const AxisHost& a) {
     Axis<T> x;
     memset(&x, 0, sizeof(x));
     x.fam = a.fam; x.n = a.n; x.N = a.N; x.L = a.L; x.M = a.M; x.log2M = a.log2M;
-    x.blue = a.blue; x.tpg = a.tpg; x.Mp = a.M + a.M / 16; x.H = a.H; x.W = a.W;
+    x.blue = a.blue; x.tpg = a.tpg; x.Mp = group_slots(a.M); x.H = a.H; x.W = a.W;
     x.tw = reinterpret_cast<const C2<T>*>(a.tw);
     x.chirp = reinterpret_cast<const C2<T>*>(a.chirp);
     x.bhat = reinterpret_cast<const C2<T>*>(a.bhat);
@@ -450,7 +450,7 @@ extern "C" hobc_status hobc_batch_create(const hobc_batch_desc* desc, const hobc
                 const AxisHost& a = b->axes_host[ax];
                 const int G = kBatchThreads / a.tpg;
                 const int nl = rows ? n0 : n1;
-                smem = std::max(smem, (size_t)G * (a.M + a.M / 16) * csz + (size_t)2 * G * a.W * b->esz);
+                smem = std::max(smem, (size_t)G * group_slots(a.M) * csz + (size_t)2 * G * a.W * b->esz);
                 for (int r0 = 0; r0 < nl; r0 += 2 * G) {
                     LineWork e;
                     memset(&e, 0, sizeof(e));

@@ -46,7 +46,7 @@ struct Axis {
     int log2M;
     int blue;       // 1: Bluestein (M >= 2L-1), 0: direct
     int tpg;        // threads per group = M/8
-    int Mp;         // shared-memory slots per group: M plus one pad slot per 16 (pidx)
+    int Mp;         // shared-memory slots per group: group_slots(M)
     int H;          // FOURIER: floor(N/2)+1 stored frequencies; else N
     int W;          // spectrum entries stored on this axis: n (S, C) or H+2 (F)
     const C2<T>* tw;      // per-stage twiddle tables of the FFT, concatenated (< M entries)
@@ -70,6 +70,11 @@ struct Axis {
 // entries, so the stride-8 writes of the first Stockham stages hit distinct
 // banks (without it a warp's stage-1 store of 8-byte values is 16-way conflicted).
 __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+
+// Shared-memory slots of one group: the padded FFT buffer (pidx(M-1) <
+// M + M/16) and four spare complex slots after it, where the line's border
+// coefficients are left for every thread of the group.
+__host__ __device__ __forceinline__ int group_slots(int M) { return M + M / 16 + 4; }
 
 template <typename T> __device__ __forceinline__ void dft4(C2<T>& a0, C2<T>& a1, C2<T>& a2, C2<T>& a3) {
     const C2<T> s02 = cadd<T>(a0, a2), d02 = csub<T>(a0, a2);
@@ -231,19 +236,17 @@ __device__ __forceinline__ int pos_C(int j, int N) { return (j & 1) ? (N - 1 - (
 // double.  This is the closed form of the Sherman-Morrison-Woodbury inverse of
 // Thm. 1 (the SMW inner products reduce to unit vectors because the border
 // rows repeat interior rows).
+// One coefficient per call (which = 0: c_1, 1: c_n), so the threads of a
+// group can share the work: the FP64 pipe of this part is narrow, and every
+// warp repeating the same double operations costs more than a barrier.
 template <typename T>
-__device__ __forceinline__ void border_coeffs(const Axis<T>& ax, double y0, double y1, double ym2,
-                                              double ym1, double& c1, double& cn) {
-    if (ax.fam == FAM_S) {
-        c1 = y0 * ax.ka;
-        cn = ym1 * ax.ka;
-    } else {
-        double r1, r2;
-        if (ax.fam == FAM_C) { r1 = y0 - y1; r2 = ym1 - ym2; }
-        else { r1 = y0 - ym2; r2 = ym1 - y1; }
-        c1 = ax.ka * r1 + ax.kb * r2;
-        cn = ax.kb * r1 + ax.ka * r2;
-    }
+__device__ __forceinline__ double border_coeff(const Axis<T>& ax, double y0, double y1, double ym2, double ym1,
+                                               int which) {
+    if (ax.fam == FAM_S) return (which ? ym1 : y0) * ax.ka;
+    double r1, r2;
+    if (ax.fam == FAM_C) { r1 = y0 - y1; r2 = ym1 - ym2; }
+    else { r1 = y0 - ym2; r2 = ym1 - y1; }
+    return which ? ax.kb * r1 + ax.ka * r2 : ax.ka * r1 + ax.kb * r2;
 }
 
 // S3 (degree 3): y = sum_b c_b B_b + E w with border columns B = (L1, L2, flip L2,
@@ -252,12 +255,10 @@ __device__ __forceinline__ void border_coeffs(const Axis<T>& ax, double y0, doub
 // y therefore involve only the border coefficients: a 4x4 system whose inverse
 // is precomputed in double.
 template <typename T>
-__device__ __forceinline__ void border_coeffs4(const Axis<T>& ax, double y0, double y1, double y2, double ym3,
-                                               double ym2, double ym1, double* c) {
+__device__ __forceinline__ double border_coeff4(const Axis<T>& ax, double y0, double y1, double y2, double ym3,
+                                                double ym2, double ym1, int b) {
     const double r[4] = {y0 + y2, y1, ym2, ym1 + ym3};
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-        c[b] = ax.k4[4 * b] * r[0] + ax.k4[4 * b + 1] * r[1] + ax.k4[4 * b + 2] * r[2] + ax.k4[4 * b + 3] * r[3];
+    return ax.k4[4 * b] * r[0] + ax.k4[4 * b + 1] * r[1] + ax.k4[4 * b + 2] * r[2] + ax.k4[4 * b + 3] * r[3];
 }
 
 // value of sum_b c_b B_b at sample a (S3)

@@ -112,18 +112,25 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
 
     constexpr bool CUBIC = (FAM == FAM_S3);
     constexpr int NB = CUBIC ? 2 : 1;            // border entries on each side
-    double c1a = 0, cna = 0, c1b = 0, cnb = 0;
-    double ca4[4] = {0, 0, 0, 0}, cb4[4] = {0, 0, 0, 0};
-    if constexpr (CUBIC) {
-        if (va) border_coeffs4<T>(ax, ya[0], ya[1], ya[2], ya[n - 3], ya[n - 2], ya[n - 1], ca4);
-        if (vb) border_coeffs4<T>(ax, yb[0], yb[1], yb[2], yb[n - 3], yb[n - 2], yb[n - 1], cb4);
-    } else {
-        if (va) border_coeffs<T>(ax, ya[0], ya[1], ya[n - 2], ya[n - 1], c1a, cna);
-        if (vb) border_coeffs<T>(ax, yb[0], yb[1], yb[n - 2], yb[n - 1], c1b, cnb);
+    // border coefficients of both lines, one per thread: (c_1, c_n) of line a
+    // then of line b, or the four S3 coefficients of each
+    T* xs = reinterpret_cast<T*>(buf + ax.M + ax.M / 16);
+    for (int l = t; l < 4 * NB; l += ax.tpg) {
+        const int side = CUBIC ? l >> 2 : l >> 1;
+        const T* y = side ? yb : ya;
+        double c = 0;
+        if (side ? vb : va) {
+            if constexpr (CUBIC) c = border_coeff4<T>(ax, y[0], y[1], y[2], y[n - 3], y[n - 2], y[n - 1], l & 3);
+            else c = border_coeff<T>(ax, y[0], y[1], y[n - 2], y[n - 1], l & 1);
+        }
+        xs[l] = (T)c;
     }
-    const T c1af = (T)c1a, cnaf = (T)cna, c1bf = (T)c1b, cnbf = (T)cnb;
-    const T ca4f[4] = {(T)ca4[0], (T)ca4[1], (T)ca4[2], (T)ca4[3]};
-    const T cb4f[4] = {(T)cb4[0], (T)cb4[1], (T)cb4[2], (T)cb4[3]};
+    __syncthreads();
+    const T c1af = xs[0], cnaf = xs[1], c1bf = xs[2], cnbf = xs[3];
+    T ca4f[4] = {0, 0, 0, 0}, cb4f[4] = {0, 0, 0, 0};
+    if constexpr (CUBIC)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) { ca4f[b] = xs[b]; cb4f[b] = xs[4 + b]; }
     const C2<T> zero = cmk<T>(0, 0);
 
     for (int j = t; j < N; j += ax.tpg) {
@@ -249,6 +256,8 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM 
         const E* ip = in + item * in_item + (long long)r0 * in_rs;
         const int total = rows_here * W;
         const E* Dp = reinterpret_cast<const E*>(fd.D);
+        T mu_item = 0;                      // 2D filter: one mu per item, read once
+        if constexpr (FMODE == 2) mu_item = (T)mu_of(fd, (int)item);
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             int rr, c;
             if (in_rs == 1) { c = idx / rows_here; rr = idx - c * rows_here; }
@@ -263,8 +272,7 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM 
             } else if constexpr (FMODE == 2) {
                 const int line = r0 + rr;
                 const E d = Dp[(fd.psf_per ? item : 0) * fd.d_psf_stride + (long long)line * in_rs + (long long)c * in_cs];
-                const T mu = (T)mu_of(fd, (int)item);
-                v = apply_filter(v, d, smoothing2<T>(fd, 2, ax, line, c), mu);
+                v = apply_filter(v, d, smoothing2<T>(fd, 2, ax, line, c), mu_item);
             }
             stage[(size_t)rr * W + c] = v;
         }
@@ -409,13 +417,20 @@ k_cplx_analysis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long
     const int c = blockIdx.x * G + g;
     const bool valid = c < nlines;
     const C2<T>* y = in + item * item_stride + (long long)(valid ? c : 0) * n;
-    double c1r = 0, cnr = 0, c1i = 0, cni = 0;
-    if (valid) {
-        const C2<T> y0 = y[0], y1 = y[1], ym2 = y[n - 2], ym1 = y[n - 1];
-        border_coeffs<T>(ax, y0.x, y1.x, ym2.x, ym1.x, c1r, cnr);
-        border_coeffs<T>(ax, y0.y, y1.y, ym2.y, ym1.y, c1i, cni);
+    // border coefficients, one per thread: c_1 and c_n of the real part, then
+    // of the imaginary part
+    T* xs = reinterpret_cast<T*>(buf + ax.M + ax.M / 16);
+    for (int l = t; l < 4; l += ax.tpg) {
+        double c = 0;
+        if (valid) {
+            const C2<T> y0 = y[0], y1 = y[1], ym2 = y[n - 2], ym1 = y[n - 1];
+            c = l < 2 ? border_coeff<T>(ax, y0.x, y1.x, ym2.x, ym1.x, l & 1)
+                      : border_coeff<T>(ax, y0.y, y1.y, ym2.y, ym1.y, l & 1);
+        }
+        xs[l] = (T)c;
     }
-    const C2<T> c1 = cmk<T>((T)c1r, (T)c1i), cn = cmk<T>((T)cnr, (T)cni);
+    __syncthreads();
+    const C2<T> c1 = cmk<T>(xs[0], xs[2]), cn = cmk<T>(xs[1], xs[3]);
     for (int j = t; j < N; j += ax.tpg) {
         const T ql = ax.q[1 + j], qr = ax.q[n - 2 - j];
         C2<T> w = cmk<T>(0, 0);

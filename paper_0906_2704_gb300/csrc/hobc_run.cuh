@@ -13,7 +13,7 @@ template <typename T>
 static Axis<T> dev_axis(const AxisHost& a) {
     Axis<T> x;
     x.fam = a.fam; x.n = a.n; x.N = a.N; x.L = a.L; x.M = a.M; x.log2M = a.log2M;
-    x.blue = a.blue; x.tpg = a.tpg; x.Mp = a.M + a.M / 16; x.H = a.H; x.W = a.W;
+    x.blue = a.blue; x.tpg = a.tpg; x.Mp = group_slots(a.M); x.H = a.H; x.W = a.W;
     x.tw = reinterpret_cast<const C2<T>*>(a.tw);
     x.chirp = reinterpret_cast<const C2<T>*>(a.chirp);
     x.bhat = reinterpret_cast<const C2<T>*>(a.bhat);
@@ -36,7 +36,7 @@ static inline Launch pair_launch(const AxisHost& a, size_t cbytes, size_t ebytes
     G = std::min(G, std::max(1, 512 / a.tpg));
     G = std::min(G, (nlines + 1) / 2);
     G = std::max(G, 1);
-    const size_t Mp = (size_t)a.M + a.M / 16;
+    const size_t Mp = (size_t)group_slots(a.M);
     auto smem = [&](int g) { return (size_t)g * Mp * cbytes + (size_t)2 * g * a.W * ebytes; };
     while (G > 1 && smem(G) > 200 * 1024) --G;
     Launch l;
@@ -50,7 +50,7 @@ static inline Launch cplx_launch(const AxisHost& a, size_t cbytes, int nlines, i
     int G = std::max(1, 256 / a.tpg);
     G = std::min(G, std::max(1, 512 / a.tpg));
     G = std::min(G, nlines);
-    const size_t Mp = (size_t)a.M + a.M / 16;
+    const size_t Mp = (size_t)group_slots(a.M);
     while (G > 1 && (size_t)G * Mp * cbytes > 200 * 1024) --G;
     Launch l;
     l.block = dim3(G * a.tpg);
