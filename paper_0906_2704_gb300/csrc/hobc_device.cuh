@@ -172,6 +172,96 @@ __device__ __forceinline__ void fft_stage(C2<T>* buf, int M, int Ns, const C2<T>
     __syncthreads();
 }
 
+// The same stage with the sub-length NS fixed at compile time, for M >= 128
+// (so nb = M/R and tpg = M/8 are multiples of 16).  Shared-memory slots then
+// follow from one pidx per butterfly: pidx(j + r nb) = pidx(j) + r (nb + nb/16)
+// because nb is a multiple of 16, and pidx(base + r NS) = pidx(base) + pidx(r NS)
+// because the low four bits of base and r NS never carry (NS = 1: base = 8j;
+// NS = 8: base mod 16 = j mod 8; NS >= 64: r NS mod 16 = 0).  IN: 0 plain
+// reads, 1 reads at positions >= lim_in taken as zero, 2 the pre[] product;
+// OUTLIM: writes at positions >= lim_out dropped.
+template <int R, int NS, int IN, bool OUTLIM, typename T>
+__device__ __forceinline__ void fft_stage_ct(C2<T>* buf, int nb, const C2<T>* __restrict__ tws,
+                                             const C2<T>* __restrict__ pre, int lim_in, int lim_out, int t,
+                                             int tpg) {
+    constexpr int PER = 8 / R;
+    const int rstep = nb + (nb >> 4);
+    const int pt = pidx(t), tstep = tpg + (tpg >> 4);
+    C2<T> v[8];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = t + u * tpg;
+        const int pj = pt + u * tstep;
+        const int k = j & (NS - 1);
+        C2<T> w[8];
+        if (NS > 1) {
+            w[1] = tws[k];
+            if (R >= 4) w[2] = tws[NS + k];
+            if (R == 8) w[4] = tws[2 * NS + k];
+            if (R >= 4) w[3] = cmul<T>(w[1], w[2]);
+            if (R == 8) {
+                w[5] = cmul<T>(w[1], w[4]);
+                w[6] = cmul<T>(w[2], w[4]);
+                w[7] = cmul<T>(w[3], w[4]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            C2<T> x;
+            if (IN == 1) {
+                x = cmk<T>(0, 0);
+                if (j + r * nb < lim_in) x = buf[pj + r * rstep];
+            } else {
+                x = buf[pj + r * rstep];
+                if (IN == 2) x = cconj<T>(cmul<T>(x, pre[j + r * nb]));
+            }
+            if (NS > 1 && r > 0) x = cmul<T>(x, w[r]);
+            v[u * R + r] = x;
+        }
+        if (R == 8) dft8<T>(v + u * R);
+        else if (R == 4) dft4<T>(v[u * R], v[u * R + 1], v[u * R + 2], v[u * R + 3]);
+        else {
+            const C2<T> a = v[u * R], b = v[u * R + 1];
+            v[u * R] = cadd<T>(a, b);
+            v[u * R + 1] = csub<T>(a, b);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = t + u * tpg;
+        const int k = j & (NS - 1);
+        const int base = (j - k) * R + k;
+        const int pb = pidx(base);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (!OUTLIM || base + r * NS < lim_out) buf[pb + r * NS + ((r * NS) >> 4)] = v[u * R + r];
+    }
+    __syncthreads();
+}
+
+// Stages of 128 <= M <= 4096 with every sub-length fixed at compile time:
+// radix 8 at NS = 1 and 8, then radix 8, 4 or 2 at NS = 64 and, for M >= 1024,
+// at NS = 512 (twiddle tables at offsets 0, 24 and 216, as the host lays them out).
+template <int IN, bool OUTLIM, typename T>
+__device__ __forceinline__ void group_fft_ct(C2<T>* buf, const Axis<T>& ax, int t, const C2<T>* pre, int lim_in,
+                                             int lim_out) {
+    const int M = ax.M, L2 = ax.log2M, tpg = ax.tpg;
+    fft_stage_ct<8, 1, IN, false, T>(buf, M / 8, nullptr, pre, lim_in, lim_out, t, tpg);
+    fft_stage_ct<8, 8, 0, false, T>(buf, M / 8, ax.tw, nullptr, M, M, t, tpg);
+    const C2<T>* tw64 = ax.tw + 24;
+    if (L2 == 7) fft_stage_ct<2, 64, 0, OUTLIM, T>(buf, M / 2, tw64, nullptr, M, lim_out, t, tpg);
+    else if (L2 == 8) fft_stage_ct<4, 64, 0, OUTLIM, T>(buf, M / 4, tw64, nullptr, M, lim_out, t, tpg);
+    else if (L2 == 9) fft_stage_ct<8, 64, 0, OUTLIM, T>(buf, M / 8, tw64, nullptr, M, lim_out, t, tpg);
+    else {
+        fft_stage_ct<8, 64, 0, false, T>(buf, M / 8, tw64, nullptr, M, M, t, tpg);
+        const C2<T>* tw512 = ax.tw + 216;
+        if (L2 == 10) fft_stage_ct<2, 512, 0, OUTLIM, T>(buf, M / 2, tw512, nullptr, M, lim_out, t, tpg);
+        else if (L2 == 11) fft_stage_ct<4, 512, 0, OUTLIM, T>(buf, M / 4, tw512, nullptr, M, lim_out, t, tpg);
+        else fft_stage_ct<8, 512, 0, OUTLIM, T>(buf, M / 8, tw512, nullptr, M, lim_out, t, tpg);
+    }
+}
+
 // Forward power-of-two FFT (exp(-i ...)) of buf[0..M) in place.  Every thread of
 // the CTA must call it (it synchronises the CTA); t in [0, M/8).  The first
 // stage (radix 8: M >= 8) reads positions < lim_in (the rest are zero) and,
@@ -204,12 +294,20 @@ __device__ __forceinline__ C2<T> dft_in(const Axis<T>& ax, int p, C2<T> x) {
 // such that dft_out(k), k < L, is output k; positions >= L are left undefined.
 template <typename T>
 __device__ __forceinline__ void group_dft(C2<T>* buf, const Axis<T>& ax, int t) {
+    const bool ct = ax.log2M >= 7 && ax.log2M <= 12;
     if (ax.blue) {
-        group_fft<false, T>(buf, ax, t, nullptr, ax.L, ax.M);
-        // pointwise product with the transformed chirp, conjugated so the
-        // second forward FFT computes the inverse (1/M folded into bhat),
-        // applied as the second FFT's first stage reads
-        group_fft<true, T>(buf, ax, t, ax.bhat, ax.M, ax.L);
+        // the second FFT's first stage applies the pointwise product with the
+        // transformed chirp, conjugated so the second forward FFT computes the
+        // inverse (1/M folded into bhat); only outputs k < L are kept
+        if (ct) {
+            group_fft_ct<1, false, T>(buf, ax, t, nullptr, ax.L, ax.M);
+            group_fft_ct<2, true, T>(buf, ax, t, ax.bhat, ax.M, ax.L);
+        } else {
+            group_fft<false, T>(buf, ax, t, nullptr, ax.L, ax.M);
+            group_fft<true, T>(buf, ax, t, ax.bhat, ax.M, ax.L);
+        }
+    } else if (ct) {
+        group_fft_ct<0, false, T>(buf, ax, t, nullptr, ax.M, ax.M);
     } else {
         group_fft<false, T>(buf, ax, t, nullptr, ax.M, ax.M);
     }
