@@ -285,21 +285,27 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half) {
     }
     a.log2M = 0;
     while ((1 << a.log2M) < a.M) ++a.log2M;
-    a.tpg = a.M / 8;
+    a.tpg = hobc::fft_r16(a.M) ? a.M / 16 : a.M / 8;
     a.H = fam == hobc::FAM_F ? N / 2 + 1 : N;
     a.W = (fam == hobc::FAM_F && half) ? a.H + 2 : n;
 
-    // per-stage twiddle tables in the order group_fft runs the stages: radix 8
-    // while three or more bits remain, then radix 4 or 2; a stage with Ns > 1
-    // stores W_{Ns R}^{pw k} = W_M^{pw (M / (Ns R)) k} for pw = 1, 2, 4 (those < R), k < Ns
+    // per-stage twiddle tables in the order the FFT runs its stages: radix 16
+    // while four or more bits remain (fft_r16) or radix 8 while three remain,
+    // then one smaller radix; a stage with Ns > 1 stores W_{Ns R}^{pw k} =
+    // W_M^{pw (M / (Ns R)) k}, k < Ns, for pw = 1, 2, 3, 4, 8, 12 (radix 16)
+    // or pw = 1, 2, 4 (those < R)
     std::vector<cd> tw;
+    const int rmax = hobc::fft_r16(a.M) ? 16 : 8;
     for (int Ns = 1, rem = a.log2M; rem > 0;) {
-        const int R = rem >= 3 ? 8 : (1 << rem);
+        const int R = (1 << rem) >= rmax ? rmax : (1 << rem);
+        std::vector<int> pws;
+        if (R == 16) pws = {1, 2, 3, 4, 8, 12};
+        else for (int pw = 1; pw < R; pw *= 2) pws.push_back(pw);
         if (Ns > 1)
-            for (int pw = 1; pw < R; pw *= 2)
+            for (int pw : pws)
                 for (int k = 0; k < Ns; ++k) tw.push_back(expm_ipi(2LL * pw * (a.M / (Ns * R)) * k, a.M));
         Ns *= R;
-        rem -= R == 8 ? 3 : R == 4 ? 2 : 1;
+        rem -= R == 16 ? 4 : R == 8 ? 3 : R == 4 ? 2 : 1;
     }
     if (tw.empty()) tw.push_back(cd(1, 0));
     a.tw = upload_complex<T>(tw, err);

@@ -2,8 +2,9 @@
 // condition method (Donatelli, arXiv:0906.2704):
 //   * complex helpers on float2/double2;
 //   * a shared-memory Stockham FFT of power-of-two length M run by one "group"
-//     of M/8 threads (radix-8 stages, then one radix-4 or radix-2 stage), with
-//     every group of the CTA in lock-step so __syncthreads() can be used;
+//     of threads, every group of the CTA in lock-step so __syncthreads() can be
+//     used: M/16 threads holding 16 values each for M >= 256 (radix-16 stages,
+//     then one smaller radix), M/8 threads holding 8 values below (radix 8);
 //   * Bluestein's chirp-z form for lengths L that are not powers of two
 //     (X_k = b_k sum_j (x_j b_j) conj(b_{k-j}), b_k = exp(-i pi k^2 / L)), so
 //     the awkward orders N = n - 2 of the paper (1022 = 2*7*73 ...) need no
@@ -45,7 +46,7 @@ struct Axis {
     int M;          // power-of-two FFT length (== L when L is a power of two >= 8)
     int log2M;
     int blue;       // 1: Bluestein (M >= 2L-1), 0: direct
-    int tpg;        // threads per group = M/8
+    int tpg;        // threads per group: M/16 when fft_r16(M), else M/8
     int Mp;         // shared-memory slots per group: group_slots(M)
     int H;          // FOURIER: floor(N/2)+1 stored frequencies; else N
     int W;          // spectrum entries stored on this axis: n (S, C) or H+2 (F)
@@ -262,6 +263,134 @@ __device__ __forceinline__ void group_fft_ct(C2<T>* buf, const Axis<T>& ax, int 
     }
 }
 
+// 16-point DFT in registers, split as r = r1 + 4 r2 and k = s + 4 k1:
+// X_{s + 4 k1} = sum_{r1} W4^{r1 k1} [W16^{r1 s} sum_{r2} W4^{r2 s} x_{r1 + 4 r2}]:
+// four DFT4s over r2, the nine non-trivial W16 factors, four DFT4s over r1.
+template <typename T> __device__ __forceinline__ void dft16(C2<T>* v) {
+#pragma unroll
+    for (int r1 = 0; r1 < 4; ++r1) dft4<T>(v[r1], v[r1 + 4], v[r1 + 8], v[r1 + 12]);
+    const T c1 = (T)0.92387953251128675613;     // cos(pi/8)
+    const T s1 = (T)0.38268343236508977173;     // sin(pi/8)
+    const T c2 = (T)0.70710678118654752440;     // cos(pi/4)
+    // y[r1][s] sits in v[r1 + 4 s]; multiply by W16^{r1 s} = exp(-2 pi i r1 s / 16)
+    v[5] = cmul<T>(v[5], cmk<T>(c1, -s1));                          // W^1
+    v[9] = cmk<T>(c2 * (v[9].x + v[9].y), c2 * (v[9].y - v[9].x));  // W^2
+    v[13] = cmul<T>(v[13], cmk<T>(s1, -c1));                        // W^3
+    v[6] = cmk<T>(c2 * (v[6].x + v[6].y), c2 * (v[6].y - v[6].x));  // W^2
+    v[10] = cmk<T>(v[10].y, -v[10].x);                              // W^4 = -i
+    v[14] = cmk<T>(c2 * (v[14].y - v[14].x), -c2 * (v[14].x + v[14].y));   // W^6
+    v[7] = cmul<T>(v[7], cmk<T>(s1, -c1));                          // W^3
+    v[11] = cmk<T>(c2 * (v[11].y - v[11].x), -c2 * (v[11].x + v[11].y));   // W^6
+    v[15] = cmul<T>(v[15], cmk<T>(-c1, s1));                        // W^9
+#pragma unroll
+    for (int s = 0; s < 4; ++s) dft4<T>(v[4 * s], v[4 * s + 1], v[4 * s + 2], v[4 * s + 3]);
+    // X_q now sits in v[dft16_slot(q)] (q = s + 4 k1 in v[4 s + k1])
+}
+__host__ __device__ __forceinline__ constexpr int dft16_slot(int q) { return 4 * (q & 3) + (q >> 2); }
+
+// FFT lengths M >= 256 run with 16 values per thread (radix-16 stages, M/16
+// threads per group), smaller ones with 8 (radix-8 stages, M/8 threads).
+__host__ __device__ __forceinline__ bool fft_r16(int M) { return M >= 256; }
+
+// A stage of the 16-values-per-thread FFT: PER = 16/R butterflies of radix R
+// per thread, the sub-length NS fixed at compile time, slot arithmetic as in
+// fft_stage_ct (nb = M/R and tpg = M/16 are multiples of 16; NS is 1, 16 or 256).
+// Radix-16 twiddles W_{16 NS}^{r k}: powers 1, 2, 3, 4, 8, 12 are loaded and
+// the rest formed with one complex product (W^{a + 4 b} = W^a W^{4 b}).
+template <int R, int NS, int IN, bool OUTLIM, typename T>
+__device__ __forceinline__ void fft_stage16(C2<T>* buf, int nb, const C2<T>* __restrict__ tws,
+                                            const C2<T>* __restrict__ pre, int lim_in, int lim_out, int t,
+                                            int tpg) {
+    constexpr int PER = 16 / R;
+    const int rstep = nb + (nb >> 4);
+    const int pt = pidx(t), tstep = tpg + (tpg >> 4);
+    C2<T> v[16];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = t + u * tpg;
+        const int pj = pt + u * tstep;
+        const int k = j & (NS - 1);
+        C2<T> wl[4], wh[4], w8[8];
+        if (NS > 1) {
+            if (R == 16) {
+                wl[1] = tws[k]; wl[2] = tws[NS + k]; wl[3] = tws[2 * NS + k];
+                wh[1] = tws[3 * NS + k]; wh[2] = tws[4 * NS + k]; wh[3] = tws[5 * NS + k];
+            } else {
+                w8[1] = tws[k];
+                if (R >= 4) w8[2] = tws[NS + k];
+                if (R == 8) w8[4] = tws[2 * NS + k];
+                if (R >= 4) w8[3] = cmul<T>(w8[1], w8[2]);
+                if (R == 8) {
+                    w8[5] = cmul<T>(w8[1], w8[4]);
+                    w8[6] = cmul<T>(w8[2], w8[4]);
+                    w8[7] = cmul<T>(w8[3], w8[4]);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            C2<T> x;
+            if (IN == 1) {
+                x = cmk<T>(0, 0);
+                if (j + r * nb < lim_in) x = buf[pj + r * rstep];
+            } else {
+                x = buf[pj + r * rstep];
+                if (IN == 2) x = cconj<T>(cmul<T>(x, pre[j + r * nb]));
+            }
+            if (NS > 1 && r > 0) {
+                if (R == 16) {
+                    const int lo = r & 3, hi = r >> 2;
+                    const C2<T> w = lo == 0 ? wh[hi] : (hi == 0 ? wl[lo] : cmul<T>(wl[lo], wh[hi]));
+                    x = cmul<T>(x, w);
+                } else {
+                    x = cmul<T>(x, w8[r]);
+                }
+            }
+            v[u * R + r] = x;
+        }
+        if (R == 16) dft16<T>(v);
+        else if (R == 8) dft8<T>(v + u * R);
+        else if (R == 4) dft4<T>(v[u * R], v[u * R + 1], v[u * R + 2], v[u * R + 3]);
+        else {
+            const C2<T> a = v[u * R], b = v[u * R + 1];
+            v[u * R] = cadd<T>(a, b);
+            v[u * R + 1] = csub<T>(a, b);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = t + u * tpg;
+        const int k = j & (NS - 1);
+        const int base = (j - k) * R + k;
+        const int pb = pidx(base);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (!OUTLIM || base + r * NS < lim_out)
+                buf[pb + r * NS + ((r * NS) >> 4)] = v[R == 16 ? dft16_slot(r) : u * R + r];
+    }
+    __syncthreads();
+}
+
+// Stages of 256 <= M <= 4096: radix 16 at NS = 1 and 16, then radix 2, 4, 8
+// or 16 at NS = 256 for M >= 512 (twiddle tables at offsets 0 and 96).
+template <int IN, bool OUTLIM, typename T>
+__device__ __forceinline__ void group_fft16(C2<T>* buf, const Axis<T>& ax, int t, const C2<T>* pre, int lim_in,
+                                            int lim_out) {
+    const int M = ax.M, L2 = ax.log2M, tpg = ax.tpg;
+    fft_stage16<16, 1, IN, false, T>(buf, M / 16, nullptr, pre, lim_in, lim_out, t, tpg);
+    if (L2 == 8) {
+        fft_stage16<16, 16, 0, OUTLIM, T>(buf, M / 16, ax.tw, nullptr, M, lim_out, t, tpg);
+        return;
+    }
+    fft_stage16<16, 16, 0, false, T>(buf, M / 16, ax.tw, nullptr, M, M, t, tpg);
+    const C2<T>* tw256 = ax.tw + 96;
+    if (L2 == 9) fft_stage16<2, 256, 0, OUTLIM, T>(buf, M / 2, tw256, nullptr, M, lim_out, t, tpg);
+    else if (L2 == 10) fft_stage16<4, 256, 0, OUTLIM, T>(buf, M / 4, tw256, nullptr, M, lim_out, t, tpg);
+    else if (L2 == 11) fft_stage16<8, 256, 0, OUTLIM, T>(buf, M / 8, tw256, nullptr, M, lim_out, t, tpg);
+    else fft_stage16<16, 256, 0, OUTLIM, T>(buf, M / 16, tw256, nullptr, M, lim_out, t, tpg);
+}
+
 // Forward power-of-two FFT (exp(-i ...)) of buf[0..M) in place.  Every thread of
 // the CTA must call it (it synchronises the CTA); t in [0, M/8).  The first
 // stage (radix 8: M >= 8) reads positions < lim_in (the rest are zero) and,
@@ -294,18 +423,24 @@ __device__ __forceinline__ C2<T> dft_in(const Axis<T>& ax, int p, C2<T> x) {
 // such that dft_out(k), k < L, is output k; positions >= L are left undefined.
 template <typename T>
 __device__ __forceinline__ void group_dft(C2<T>* buf, const Axis<T>& ax, int t) {
+    const bool r16 = fft_r16(ax.M) && ax.log2M <= 12;
     const bool ct = ax.log2M >= 7 && ax.log2M <= 12;
     if (ax.blue) {
         // the second FFT's first stage applies the pointwise product with the
         // transformed chirp, conjugated so the second forward FFT computes the
         // inverse (1/M folded into bhat); only outputs k < L are kept
-        if (ct) {
+        if (r16) {
+            group_fft16<1, false, T>(buf, ax, t, nullptr, ax.L, ax.M);
+            group_fft16<2, true, T>(buf, ax, t, ax.bhat, ax.M, ax.L);
+        } else if (ct) {
             group_fft_ct<1, false, T>(buf, ax, t, nullptr, ax.L, ax.M);
             group_fft_ct<2, true, T>(buf, ax, t, ax.bhat, ax.M, ax.L);
         } else {
             group_fft<false, T>(buf, ax, t, nullptr, ax.L, ax.M);
             group_fft<true, T>(buf, ax, t, ax.bhat, ax.M, ax.L);
         }
+    } else if (r16) {
+        group_fft16<0, false, T>(buf, ax, t, nullptr, ax.M, ax.M);
     } else if (ct) {
         group_fft_ct<0, false, T>(buf, ax, t, nullptr, ax.M, ax.M);
     } else {

@@ -13,12 +13,12 @@
 #include "hobc_device.cuh"
 
 // Minimum resident 512-thread blocks per SM asked of the FP32 line kernels
-// (caps their registers at 65536 / (512 x this)).  The transforms are latency
-// bound: 3 (40 registers, a few spilled bytes) runs the 1024^2 passes 7%
-// faster than the unconstrained 60 registers.
-#ifndef HOBC_LINE_MINB
-#define HOBC_LINE_MINB 3
+// (caps their registers at 65536 / (512 x this)): 2 gives the 64 registers
+// that the 16 values per thread of the radix-16 FFT stages need.
+#ifndef HOBC_LINE_REGS
+#define HOBC_LINE_REGS 64
 #endif
+#define HOBC_LINE_BOUNDS __maxnreg__(sizeof(T) == 4 ? HOBC_LINE_REGS : 128)
 
 namespace hobc {
 
@@ -170,8 +170,8 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
             sb[1 + k] = cmk<T>(d.y * h, -d.x * h);        // -i (zk - zr) / 2
         }
         if (t == 0) {
-            sa[0] = cmk<T>(c1af, 0); sa[W - 1] = cmk<T>(cnaf, 0);
-            sb[0] = cmk<T>(c1bf, 0); sb[W - 1] = cmk<T>(cnbf, 0);
+            sa[0] = cmk<T>(xs[0], 0); sa[W - 1] = cmk<T>(xs[1], 0);
+            sb[0] = cmk<T>(xs[2], 0); sb[W - 1] = cmk<T>(xs[3], 0);
         }
     } else if constexpr (FAM == FAM_C) {
         for (int k = t; k < N; k += ax.tpg) {
@@ -184,7 +184,7 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
             sa[1 + k] = (T)(sk * (ph.x * s.x - ph.y * s.y));
             sb[1 + k] = (T)(sk * (ph.x * d.y + ph.y * d.x));
         }
-        if (t == 0) { sa[0] = c1af; sa[W - 1] = cnaf; sb[0] = c1bf; sb[W - 1] = cnbf; }
+        if (t == 0) { sa[0] = xs[0]; sa[W - 1] = xs[1]; sb[0] = xs[2]; sb[W - 1] = xs[3]; }
     } else {
         for (int k = t; k < N; k += ax.tpg) {
             const C2<T> z = dft_out<T>(buf, ax, k + 1);
@@ -193,10 +193,10 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
         }
         if (t == 0) {
             if constexpr (CUBIC) {
-                sa[0] = ca4f[0]; sa[1] = ca4f[1]; sa[W - 2] = ca4f[2]; sa[W - 1] = ca4f[3];
-                sb[0] = cb4f[0]; sb[1] = cb4f[1]; sb[W - 2] = cb4f[2]; sb[W - 1] = cb4f[3];
+                sa[0] = xs[0]; sa[1] = xs[1]; sa[W - 2] = xs[2]; sa[W - 1] = xs[3];
+                sb[0] = xs[4]; sb[1] = xs[5]; sb[W - 2] = xs[6]; sb[W - 1] = xs[7];
             } else {
-                sa[0] = c1af; sa[W - 1] = cnaf; sb[0] = c1bf; sb[W - 1] = cnbf;
+                sa[0] = xs[0]; sa[W - 1] = xs[1]; sb[0] = xs[2]; sb[W - 1] = xs[3];
             }
         }
     }
@@ -219,7 +219,7 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
 }
 
 template <typename T, int FAM>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? HOBC_LINE_MINB : 1)
+__global__ void HOBC_LINE_BOUNDS
 k_pair_analysis(const T* __restrict__ in, long long in_item, long long in_rs,
                 typename ElemT<T, FAM == FAM_F>::t* __restrict__ out, long long out_item,
                 long long out_rs, long long out_cs, int nlines, Axis<T> ax) {
@@ -389,7 +389,7 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM 
 }
 
 template <typename T, int FAM, int FMODE>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? HOBC_LINE_MINB : 1)
+__global__ void HOBC_LINE_BOUNDS
 k_pair_synthesis(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in, long long in_item,
                  long long in_rs, long long in_cs, T* __restrict__ out, long long out_item,
                  long long out_rs, int nlines, Axis<T> ax, FilterDesc fd) {
@@ -404,7 +404,7 @@ k_pair_synthesis(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in, long
 // Line c of item i: in[i*item_stride + c*n + t].
 // =====================================================================
 template <typename T>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? HOBC_LINE_MINB : 1)
+__global__ void HOBC_LINE_BOUNDS
 k_cplx_analysis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long item_stride,
                 int nlines, Axis<T> ax) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -445,11 +445,11 @@ k_cplx_analysis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long
     if (!valid) return;
     C2<T>* o = out + item * item_stride + (long long)c * n;
     for (int k = t; k < N; k += ax.tpg) o[1 + k] = cscale<T>(dft_out<T>(buf, ax, k), ax.sc);
-    if (t == 0) { o[0] = c1; o[n - 1] = cn; }
+    if (t == 0) { o[0] = cmk<T>(xs[0], xs[2]); o[n - 1] = cmk<T>(xs[1], xs[3]); }   // xs outlives the FFT
 }
 
 template <typename T, bool FILTER>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? HOBC_LINE_MINB : 1)
+__global__ void HOBC_LINE_BOUNDS
 k_cplx_synthesis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long item_stride,
                  int nlines, Axis<T> ax, FilterDesc fd) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
