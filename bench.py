@@ -360,14 +360,14 @@ def run_ours(args):
     # den FMA; e*sigma; num FMA) and half a MUFU reciprocal; 128 FP32 lanes per SM-clock
     # bind first: 152 SMs x 128/5.5 evaluations per clock
     peak = 152 * (128 / 5.5) * sm_max * 1e6 / 1e9
-    # DRAM traffic of one k_gcv_partials launch: ncu on the 2-image case read 12.654 MB
-    # (two spectra of 4.2107 MB plus the shared eigenvalues, no re-reads), so a launch
-    # over B images moves B spectra plus one eigenvalue array
+    # DRAM traffic of one k_gcv_partials launch: ncu on the 8-image case read 37.92 MB and
+    # wrote 0.002 MB (eight spectra of 4.2107 MB plus the shared eigenvalues, no re-reads),
+    # so a launch over B images moves B spectra plus one eigenvalue array
     spec_bytes = S * 2 * esz_of(prec)
     traffic = B * spec_bytes + spec_bytes if prec == "fp32" else None
     roofline = {"bound": "alu", "kernel": "k_gcv_partials", "achieved": achieved, "peak": peak,
                 "unit": "Geval/s", "frac": achieved / peak, "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read+write of a 2-image launch (12.654 MB), scaled per image",
+                "traffic_source": "ncu dram__bytes_read+write of an 8-image launch (37.92 MB), scaled per image",
                 "peak_source": f"152 SMs x 128 FP32 lanes / 5.5 ops per evaluation x {sm_max:.0f} MHz "
                                f"({peak_kind} max clock)"}
     hbm_bytes = B * N_SIDE * N_SIDE * esz * 2 + h.size * esz
