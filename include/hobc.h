@@ -144,7 +144,7 @@ hobc_status hobc_deblur(hobc_plan* plan, const void* g_dev, const void* psf_dev,
 
 /* hobc_deblur with HOST buffers: copies g and the PSF(s) to the plan's
  * workspace, runs the method, copies f (and mu index, G if non-NULL) back, and
- * returns when all of it has finished.  The batch runs as up to eight chunks:
+ * returns when all of it has finished.  The batch runs as up to four chunks:
  * their uploads back to back on an internal stream, each chunk's kernels on the
  * plan's stream once its upload is done, each download on a second internal
  * stream once its kernels are done (streams created on the first call), so the
