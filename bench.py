@@ -339,9 +339,12 @@ def run_ours(args):
     mi_h = torch.empty(B, dtype=torch.int32).pin_memory().numpy()
     plan.deblur_host(g_h, h_h, f_h, mi_h)
     barrier()
+    # consecutive calls overlap (each step's uploads run during the previous
+    # step's kernels); every step's copies are inside the timed region
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        plan.deblur_host(g_h, h_h, f_h, mi_h)
+        plan.deblur_host_async(g_h, h_h, f_h, mi_h)
+    plan.wait()
     barrier()
     el = max_over_ranks(time.perf_counter() - t0, dist, dev)
     esz = np.dtype(npdt).itemsize

@@ -144,14 +144,33 @@ hobc_status hobc_deblur(hobc_plan* plan, const void* g_dev, const void* psf_dev,
 
 /* hobc_deblur with HOST buffers: copies g and the PSF(s) to the plan's
  * workspace, runs the method, copies f (and mu index, G if non-NULL) back, and
- * returns when all of it has finished.  The batch runs as up to four chunks:
- * their uploads back to back on an internal stream, each chunk's kernels on the
- * plan's stream once its upload is done, each download on a second internal
- * stream once its kernels are done (streams created on the first call), so the
- * copies overlap the kernels of other chunks; copies overlap only when the host
- * buffers are page-locked. */
+ * returns when all of it has finished (hobc_deblur_host_async followed by
+ * hobc_plan_wait).  The batch runs as up to four chunks: their uploads back to
+ * back on an internal stream, each chunk's kernels on the plan's stream once
+ * its upload is done, each download on a second internal stream once its
+ * kernels are done (streams created on the first call), so the copies overlap
+ * the kernels of other chunks; copies overlap only when g_host and f_host are
+ * page-locked.  The PSF is staged through page-locked memory the plan owns. */
 hobc_status hobc_deblur_host(hobc_plan* plan, const void* g_host, const void* psf_host,
                              void* f_host, int* mu_index_host, double* gcv_host);
+
+/* hobc_deblur_host without the final wait: queues the copies and kernels and
+ * returns once the PSF has been read (it is copied into the plan's staging).
+ * g_host must stay unchanged and f_host, mu_index_host, gcv_host unread until
+ * hobc_plan_wait returns; with page-locked buffers the host returns at once.
+ * Consecutive calls on one plan overlap: a call's uploads run while the
+ * previous call's kernels do, each chunk's upload waiting only until the
+ * previous call's analysis has read that chunk's input slots, and each chunk's
+ * filter + synthesis until the previous call's download has read its output
+ * slots (per-chunk events; the small outputs are copied on the plan's stream).
+ * No other call may use the plan until hobc_plan_wait.  Errors of the queueing
+ * are returned here, errors of the work by hobc_plan_wait. */
+hobc_status hobc_deblur_host_async(hobc_plan* plan, const void* g_host, const void* psf_host,
+                                   void* f_host, int* mu_index_host, double* gcv_host);
+
+/* Waits until every copy and kernel queued on the plan (its stream and the two
+ * host-call streams) has finished.  HOBC_ERR_CUDA if any of it failed. */
+hobc_status hobc_plan_wait(hobc_plan* plan);
 
 /* Step: analysis transform ghat = T_X^{-1} g (Thm. 1 / Eq. (eq:Tx); 2D: tensor
  * product, Sec. 6), the boundary-polynomial correction included.

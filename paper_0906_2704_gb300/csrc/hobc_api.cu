@@ -420,6 +420,8 @@ void hobc_plan_destroy(hobc_plan* p) {
     if (!p) return;
     if (p->stream) cudaStreamSynchronize(p->stream);
     else cudaDeviceSynchronize();
+    for (int i = 0; i < 2; ++i)
+        if (p->aux[i]) cudaStreamSynchronize(p->aux[i]);
     for (int i = 0; i < 2; ++i) free_axis(p->ax[i]);
     cudaFree(p->mu); cudaFree(p->muT); cudaFree(p->R); cudaFree(p->G); cudaFree(p->D);
     cudaFree(p->partials); cudaFree(p->gcv); cudaFree(p->mu_idx);
@@ -429,11 +431,14 @@ void hobc_plan_destroy(hobc_plan* p) {
     exact_free(p);
     for (int i = 0; i < 2; ++i)
         if (p->aux[i]) cudaStreamDestroy(p->aux[i]);
-    if (p->aux_ev) cudaEventDestroy(p->aux_ev);
     for (int i = 0; i < 8; ++i) {
         if (p->ev_up[i]) cudaEventDestroy(p->ev_up[i]);
+        if (p->ev_an[i]) cudaEventDestroy(p->ev_an[i]);
         if (p->ev_done[i]) cudaEventDestroy(p->ev_done[i]);
+        if (p->ev_down[i]) cudaEventDestroy(p->ev_down[i]);
     }
+    if (p->ev_psf) cudaEventDestroy(p->ev_psf);
+    if (p->psf_pinned) cudaFreeHost(p->psf_pinned);
     delete p;
 }
 
@@ -639,38 +644,49 @@ static hobc_plan_s chunk_view(const hobc_plan_s* p, size_t c0, size_t cb, cudaSt
 // exposed, more run the kernels on grids too small to fill the GPU.
 static const size_t kHostChunks = 4;
 
-hobc_status hobc_deblur_host(hobc_plan* p, const void* g, const void* psf, void* f, int* mu_idx, double* gcv) {
+hobc_status hobc_deblur_host_async(hobc_plan* p, const void* g, const void* psf, void* f, int* mu_idx,
+                                   double* gcv) {
     if (!p || !g || !psf || !f) return HOBC_ERR_ARG;
     p->launches = 0;
     const size_t B = (size_t)p->desc.batch;
     const size_t ib = p->img_elems * p->esz;
+    const size_t pb = (size_t)p->npsf * p->psf_elems * p->esz;
+    const size_t nchunk = B >= kHostChunks ? kHostChunks : B;
+    const size_t cb = (B + nchunk - 1) / nchunk;
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 2 && e == cudaSuccess; ++i)
         if (!p->aux[i]) e = cudaStreamCreateWithFlags(&p->aux[i], cudaStreamNonBlocking);
-    if (e == cudaSuccess && !p->aux_ev) e = cudaEventCreateWithFlags(&p->aux_ev, cudaEventDisableTiming);
-    // the uploads wait for earlier work on the plan's stream (the workspace is
-    // free), not for the eigenvalues queued next
-    if (e == cudaSuccess) e = cudaEventRecord(p->aux_ev, p->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux[0], p->aux_ev, 0);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(p->psf_in, psf, (size_t)p->npsf * p->psf_elems * p->esz, cudaMemcpyHostToDevice, p->stream);
-    if (e != cudaSuccess) { set_last_error("hobc_deblur_host H2D", e); return HOBC_ERR_CUDA; }
+    for (size_t i = 0; i < nchunk && e == cudaSuccess; ++i) {
+        cudaEvent_t* evs[4] = {&p->ev_up[i], &p->ev_an[i], &p->ev_done[i], &p->ev_down[i]};
+        for (cudaEvent_t* ev : evs)
+            if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess && !p->ev_psf) e = cudaEventCreateWithFlags(&p->ev_psf, cudaEventDisableTiming);
+    if (e == cudaSuccess && !p->psf_pinned) e = cudaMallocHost(&p->psf_pinned, pb);
+    // the PSF goes through page-locked staging (a copy from pageable memory
+    // would wait for the plan's stream); the staging is rewritten once the
+    // previous call's copy of it has left
+    if (e == cudaSuccess) e = cudaEventSynchronize(p->ev_psf);
+    if (e == cudaSuccess) {
+        memcpy(p->psf_pinned, psf, pb);
+        e = cudaMemcpyAsync(p->psf_in, p->psf_pinned, pb, cudaMemcpyHostToDevice, p->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_psf, p->stream);
+    if (e != cudaSuccess) { set_last_error("hobc_deblur_host_async set-up", e); return HOBC_ERR_CUDA; }
     hobc_status s = HOBC_DISPATCH(p, run_eig, p->psf_in, p->D);
     if (s != HOBC_OK) return s;
     // three-stage pipeline over chunks of the batch: every upload back to back
     // on aux[0], each chunk's kernels in order on the plan's stream once its
-    // upload is done, each download on aux[1] once its kernels are done; only
-    // the first upload and the last download are not overlapped
-    const size_t nchunk = B >= kHostChunks ? kHostChunks : B;
-    const size_t cb = (B + nchunk - 1) / nchunk;
-    for (size_t i = 0; i < nchunk && e == cudaSuccess; ++i) {
-        if (!p->ev_up[i]) e = cudaEventCreateWithFlags(&p->ev_up[i], cudaEventDisableTiming);
-        if (e == cudaSuccess && !p->ev_done[i]) e = cudaEventCreateWithFlags(&p->ev_done[i], cudaEventDisableTiming);
-    }
+    // upload is done, each download on aux[1] once its kernels are done.
+    // Across calls, a chunk's upload waits until the previous call's analysis
+    // has read its input slots, and its filter + synthesis until the previous
+    // call's download has read its output slots.
     for (size_t c0 = 0, c = 0; c0 < B && e == cudaSuccess; c0 += cb, ++c) {
         const size_t n = std::min(cb, B - c0);
-        e = cudaMemcpyAsync(static_cast<char*>(p->g_in) + c0 * ib, static_cast<const char*>(g) + c0 * ib, n * ib,
-                            cudaMemcpyHostToDevice, p->aux[0]);
+        e = cudaStreamWaitEvent(p->aux[0], p->ev_an[c], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(static_cast<char*>(p->g_in) + c0 * ib, static_cast<const char*>(g) + c0 * ib, n * ib,
+                                cudaMemcpyHostToDevice, p->aux[0]);
         if (e == cudaSuccess) e = cudaEventRecord(p->ev_up[c], p->aux[0]);
     }
     for (size_t c0 = 0, c = 0; c0 < B && e == cudaSuccess && s == HOBC_OK; c0 += cb, ++c) {
@@ -679,33 +695,50 @@ hobc_status hobc_deblur_host(hobc_plan* p, const void* g, const void* psf, void*
         if (e != cudaSuccess) break;
         hobc_plan_s v = chunk_view(p, c0, n, p->stream);
         s = HOBC_DISPATCH(&v, run_analysis, v.g_in, v.G);
-        if (s == HOBC_OK) s = HOBC_DISPATCH(&v, run_gcv, v.G, v.D, gcv ? v.gcv : nullptr, v.mu_idx);
-        if (s == HOBC_OK) s = HOBC_DISPATCH(&v, run_filter_synthesis, v.G, v.D, v.mu_idx, v.f_out);
+        if (s == HOBC_OK) e = cudaEventRecord(p->ev_an[c], p->stream);
+        if (s == HOBC_OK && e == cudaSuccess) s = HOBC_DISPATCH(&v, run_gcv, v.G, v.D, gcv ? v.gcv : nullptr, v.mu_idx);
+        if (s == HOBC_OK && e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->ev_down[c], 0);
+        if (s == HOBC_OK && e == cudaSuccess)
+            s = HOBC_DISPATCH(&v, run_filter_synthesis, v.G, v.D, v.mu_idx, v.f_out);
         p->launches += v.launches;
-        if (s != HOBC_OK) break;
+        if (s != HOBC_OK || e != cudaSuccess) break;
         e = cudaEventRecord(p->ev_done[c], p->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux[1], p->ev_done[c], 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(static_cast<char*>(f) + c0 * ib, v.f_out, n * ib, cudaMemcpyDeviceToHost, p->aux[1]);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_down[c], p->aux[1]);
     }
-    // the small outputs follow once every chunk is queued (a copy to pageable
-    // host memory holds the host thread until it is done)
+    // the small outputs go on the plan's stream, after the last scan and
+    // before anything a later call queues there
     if (e == cudaSuccess && s == HOBC_OK) {
-        if (mu_idx) e = cudaMemcpyAsync(mu_idx, p->mu_idx, B * sizeof(int), cudaMemcpyDeviceToHost, p->aux[1]);
+        if (mu_idx) e = cudaMemcpyAsync(mu_idx, p->mu_idx, B * sizeof(int), cudaMemcpyDeviceToHost, p->stream);
         if (e == cudaSuccess && gcv)
-            e = cudaMemcpyAsync(gcv, p->gcv, B * p->K * sizeof(double), cudaMemcpyDeviceToHost, p->aux[1]);
-    }
-    for (int i = 0; i < 2; ++i) {
-        const cudaError_t e2 = cudaStreamSynchronize(p->aux[i]);
-        if (e == cudaSuccess) e = e2;
-    }
-    {
-        const cudaError_t e2 = cudaStreamSynchronize(p->stream);
-        if (e == cudaSuccess) e = e2;
+            e = cudaMemcpyAsync(gcv, p->gcv, B * p->K * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
     }
     if (s != HOBC_OK) return s;
-    if (e != cudaSuccess) { set_last_error("hobc_deblur_host", e); return HOBC_ERR_CUDA; }
+    if (e != cudaSuccess) { set_last_error("hobc_deblur_host_async", e); return HOBC_ERR_CUDA; }
     return HOBC_OK;
+}
+
+hobc_status hobc_plan_wait(hobc_plan* p) {
+    if (!p) return HOBC_ERR_ARG;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2; ++i)
+        if (p->aux[i]) {
+            const cudaError_t e2 = cudaStreamSynchronize(p->aux[i]);
+            if (e == cudaSuccess) e = e2;
+        }
+    const cudaError_t e2 = cudaStreamSynchronize(p->stream);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) { set_last_error("hobc_plan_wait", e); return HOBC_ERR_CUDA; }
+    return HOBC_OK;
+}
+
+hobc_status hobc_deblur_host(hobc_plan* p, const void* g, const void* psf, void* f, int* mu_idx, double* gcv) {
+    const hobc_status s = hobc_deblur_host_async(p, g, psf, f, mu_idx, gcv);
+    if (!p) return s;
+    const hobc_status w = hobc_plan_wait(p);
+    return s != HOBC_OK ? s : w;
 }
 
 }  // extern "C"

@@ -82,9 +82,12 @@ struct hobc_plan_s {
     int* k_hat;              // [batch] argmin of the binned G
     double* refine_state;    // [batch][4] lo, mid, hi (log10 mu) and the incumbent mu of the refinement
     cudaStream_t aux[2];     // host-buffer pipeline: upload and download streams (created on first use)
-    cudaEvent_t aux_ev;
-    cudaEvent_t ev_up[8];    // per chunk of the host-buffer pipeline: upload done, kernels done
-    cudaEvent_t ev_done[8];
+    cudaEvent_t ev_up[8];    // per chunk of the host-buffer pipeline: upload done,
+    cudaEvent_t ev_an[8];    // analysis done (the chunk's input slots are free again),
+    cudaEvent_t ev_done[8];  // kernels done (its output slots are ready),
+    cudaEvent_t ev_down[8];  // download done (its output slots are free again)
+    cudaEvent_t ev_psf;      // the PSF staging copy of the last host call has reached the device
+    void* psf_pinned;        // page-locked host staging of the PSF(s) for the host calls
     int grid_ascending;      // 1 if the mu grid is strictly increasing
     struct hobc_dense_s* dense;   // HOBC_SPLIT_BF16: matrices and operand workspace (hobc_tc.cu)
     struct hobc_exact_s* exact;   // exact GCV: Gram factors and line sums, allocated on first use (hobc_exact.cu)

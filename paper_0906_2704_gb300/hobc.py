@@ -67,7 +67,8 @@ _lib.hobc_plan_family.argtypes = [_vp]
 _lib.hobc_plan_family.restype = ctypes.c_int
 _lib.hobc_spectrum_size.argtypes = [_vp, ctypes.POINTER(_sz), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_sz)]
 _lib.hobc_spectrum_size.restype = ctypes.c_int
-for _name, _n in (("hobc_deblur", 6), ("hobc_deblur_host", 6), ("hobc_analysis", 3), ("hobc_synthesis", 3),
+for _name, _n in (("hobc_deblur", 6), ("hobc_deblur_host", 6), ("hobc_deblur_host_async", 6), ("hobc_plan_wait", 1),
+                  ("hobc_analysis", 3), ("hobc_synthesis", 3),
                   ("hobc_eigenvalues", 3), ("hobc_gcv", 5), ("hobc_filter_synthesis", 5)):
     getattr(_lib, _name).argtypes = [_vp] * _n
     getattr(_lib, _name).restype = ctypes.c_int
@@ -343,6 +344,15 @@ class Plan:
     def deblur_host(self, g, psf, f, mu_index=None, gcv=None) -> None:
         _check(_lib.hobc_deblur_host(self._handle, _hptr(g), _hptr(psf), _hptr(f), _hptr(mu_index), _hptr(gcv)),
                "hobc_deblur_host")
+
+    def deblur_host_async(self, g, psf, f, mu_index=None, gcv=None) -> None:
+        """Queue deblur_host without waiting; the host arrays must stay alive and
+        untouched until wait()."""
+        _check(_lib.hobc_deblur_host_async(self._handle, _hptr(g), _hptr(psf), _hptr(f), _hptr(mu_index),
+                                           _hptr(gcv)), "hobc_deblur_host_async")
+
+    def wait(self) -> None:
+        _check(_lib.hobc_plan_wait(self._handle), "hobc_plan_wait")
 
     def analysis(self, g, ghat) -> None:
         _check(_lib.hobc_analysis(self._handle, _ptr(g), _ptr(ghat)), "hobc_analysis")

@@ -70,6 +70,9 @@ def test_null_arguments_rejected(hobc):
     out = ctypes.c_void_p()
     assert lib.hobc_plan_create(None, None, None, ctypes.byref(out)) == 1
     assert lib.hobc_deblur(None, None, None, None, None, None) == 1
+    assert lib.hobc_deblur_host(None, None, None, None, None, None) == 1
+    assert lib.hobc_deblur_host_async(None, None, None, None, None, None) == 1
+    assert lib.hobc_plan_wait(None) == 1
     assert lib.hobc_analysis(None, None, None) == 1
     assert lib.hobc_gcv(None, None, None, None, None) == 1
 

@@ -305,6 +305,44 @@ def test_host_entry_point_equals_device_entry_point(batch, psf_per_item):
     assert plan.last_launch_count >= 7
 
 
+@pytest.mark.parametrize("batch", [1, 4, 7])
+def test_async_host_calls_overlap_and_equal_device_calls(batch):
+    """Consecutive asynchronous host-buffer calls on one plan (different inputs and
+    outputs, then the same output buffers again) give each call's device results
+    bit for bit: a chunk's input and output slots are not reused before the
+    previous call has read them."""
+    n, taps, K = (30, 36), (5, 5), 12
+    mus = synth.mu_grid(K)
+    h0 = P.psf_for("F", 2, taps)
+    hs = np.ascontiguousarray(h0[None])
+    plan = hobc.Plan(2, n, taps, 2, mus, family="fourier", batch=batch)
+    calls = 4
+    gs = [P.problems(2, n, h0, batch, 20 + c)[0] for c in range(calls)]
+    g_h = [torch.from_numpy(g).pin_memory().numpy() for g in gs]
+    f_h = [torch.empty(gs[0].shape, dtype=torch.float64).pin_memory().numpy() for _ in range(calls)]
+    mi_h = [torch.empty(batch, dtype=torch.int32).pin_memory().numpy() for _ in range(calls)]
+    G_h = [torch.empty((batch, K), dtype=torch.float64).pin_memory().numpy() for _ in range(calls)]
+    for c in range(calls):
+        plan.deblur_host_async(g_h[c], hs, f_h[c], mi_h[c], G_h[c])
+    plan.wait()
+    f_same = torch.empty(gs[0].shape, dtype=torch.float64).pin_memory().numpy()
+    mi_same = torch.empty(batch, dtype=torch.int32).pin_memory().numpy()
+    for c in range(calls):                    # the same output buffers for every call: the last one wins
+        plan.deblur_host_async(g_h[c], hs, f_same, mi_same, None)
+    plan.wait()
+    for c in range(calls):
+        f_d = torch.empty(gs[0].shape, dtype=torch.float64, device="cuda")
+        mi_d = torch.empty(batch, dtype=torch.int32, device="cuda")
+        G_d = torch.empty((batch, K), dtype=torch.float64, device="cuda")
+        plan.deblur(_dev(gs[c], np.float64), _dev(hs, np.float64), f_d, mi_d, G_d)
+        assert np.array_equal(f_h[c], f_d.cpu().numpy()), c
+        assert np.array_equal(mi_h[c], mi_d.cpu().numpy()), c
+        assert np.array_equal(G_h[c], G_d.cpu().numpy()), c
+        if c == calls - 1:
+            assert np.array_equal(f_same, f_d.cpu().numpy())
+            assert np.array_equal(mi_same, mi_d.cpu().numpy())
+
+
 def test_caller_mu_index_out_of_range_is_clamped():
     """A caller-supplied mu index outside the grid is clamped on the device."""
     mus = synth.mu_grid(4, 1e-3, 1.0)
