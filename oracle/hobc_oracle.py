@@ -19,6 +19,9 @@ Families (per axis):
   'F'  quadratic-preserving, Fourier basis, any PSF (Sec. 3.2, Eq. (eq:Tf), (eq:Af))
   'S3' cubic-preserving, sine basis, symmetric PSF: degree 3, which the paper
       only names (Sec. 1 "quadratic or cubic", Sec. 7); built as reading R6 below.
+  'C4' quartic-preserving, cosine basis, symmetric PSF: degree 4, the cosine
+      family with two border columns per side (Sec. 7 names higher orders);
+      built as reading R16 below.
 Comparison (classical) families, used by the pins:
   'P'  periodic (Sec. 2.1, Eq. (eq:permat));  'R' reflective (Sec. 2.1, Eq. (eq:refm))
 
@@ -35,6 +38,15 @@ DESIGN.md):
       extended oddly (rows i = 0, N+1 are zero, rows i = -1, N+2 are minus rows 1, N);
       border columns L1 = (x_{N+1}-x)(x_{N+2}-x), L2 = L1 (x_{N+2}-x) and their flips,
       each of unit norm, with eigenvalue z(0); together they span the cubics.
+  R16 degree 4 ('C4'): the construction of Sec. 3.1 with two border columns per
+      side: DCT-II of order N = n-4 on the grid x_i = (2i-3) pi/(2N), i = 0..n-1
+      (x_2..x_{n-3} the DCT-II samples, two points added at each end by
+      continuity, so rows 0, 1 repeat rows 3, 2 and rows n-2, n-1 repeat rows
+      n-3, n-4: half-sample reflection), interval [a, b] = [x_0, x_{n-1}];
+      border columns Q1 = (b-x)^2 and Q2 = (b-x)^4 and their flips (x-a)^2,
+      (x-a)^4, each of unit norm, with eigenvalue z(0); with the cosine of
+      frequency 0 they span the quartics.  Interior eigenvalues are those of the
+      reflective matrix of order n-4 (angles (t-2) pi/N).
   GCV with complex spectra uses |sigma_i ghat_i|^2 (Eq. (eq:gcv2) is written for
       real data).
 
@@ -148,6 +160,22 @@ def cubic_border_columns(n: int):
     return L1 / np.linalg.norm(L1), L2 / np.linalg.norm(L2)
 
 
+def quartic_grid(n: int):
+    """Grid x_0..x_{n-1} and interval [a, b] of the degree-4 transform (reading R16):
+    x_i = (2i - 3) pi / (2N), N = n - 4."""
+    N = n - 4
+    x = (2 * np.arange(n) - 3) * np.pi / (2 * N)
+    return x, x[0], x[-1]
+
+
+def quartic_border_columns(n: int):
+    """Q1 = (b-x)^2, Q2 = (b-x)^4 of the degree-4 transform (reading R16), unit 2-norm."""
+    x, a, b = quartic_grid(n)
+    Q1 = (b - x) ** 2
+    Q2 = (b - x) ** 4
+    return Q1 / np.linalg.norm(Q1), Q2 / np.linalg.norm(Q2)
+
+
 def extended_grid(family: str, n: int):
     """Grid x_0..x_{n-1} and interval [a, b] of the basis functions (Sec. 3, remark)."""
     N = n - 2
@@ -173,6 +201,7 @@ def eigen_angles(family: str, n: int) -> np.ndarray:
     'C': x_1 = x_n = 0, x_i = (i-2) pi/(n-2)              (Eq. (eq:Ac))
     'F': x_1 = x_n = 0, x_i = (i-2) 2 pi/(n-2)            (Eq. (eq:Af), reading R4)
     'S3': border columns 1, 2, n-1, n at 0, the others (i-2) pi/(n-3)   (reading R6)
+    'C4': border columns 1, 2, n-1, n at 0, the others (i-3) pi/(n-4)   (reading R16)
     'P': x_i = 2 (i-1) pi/n                               (Eq. (eq:permat))
     'PH': as 'P' (periodic conditions in the Hartley basis)
     'R': x_i = (i-1) pi/n                                 (Eq. (eq:refm))
@@ -189,6 +218,9 @@ def eigen_angles(family: str, n: int) -> np.ndarray:
         th[0] = th[-1] = 0.0
     elif family == "S3":                                 # reading R6
         th = (i - 2) * np.pi / (n - 3)
+        th[[0, 1, n - 2, n - 1]] = 0.0
+    elif family == "C4":                                 # reading R16
+        th = (i - 3) * np.pi / (n - 4)
         th[[0, 1, n - 2, n - 1]] = 0.0
     elif family in ("P", "PH"):
         th = 2 * (i - 1) * np.pi / n
@@ -221,6 +253,17 @@ def transform_matrix(family: str, n: int) -> np.ndarray:
         return hartley_matrix(n)
     if family == "R":
         return dct2_matrix(n).T
+    if family == "C4":                                   # reading R16
+        N = n - 4
+        Q1, Q2 = quartic_border_columns(n)
+        x, a, b = quartic_grid(n)
+        j = np.arange(N)
+        scale = np.sqrt((2.0 - (j == 0)) / N)
+        T = np.zeros((n, n))
+        T[:, 0], T[:, 1] = Q1, Q2
+        T[:, n - 2], T[:, n - 1] = Q2[::-1], Q1[::-1]
+        T[:, 2:N + 2] = scale[None, :] * np.cos(np.outer(x, j))   # cos(j x) on the extended grid
+        return T
     if family == "S3":                                   # reading R6
         N = n - 4
         L1, L2 = cubic_border_columns(n)
@@ -370,6 +413,13 @@ def extension_matrix(family: str, n: int) -> np.ndarray:
         E[0, 0] = -1.0
         E[n - 1, N - 1] = -1.0
         return E
+    if family == "C4":                                   # half-sample reflection by two samples
+        N = n - 4
+        E = np.zeros((n, N))
+        E[2:N + 2, :] = np.eye(N)
+        E[0, 1] = E[1, 0] = 1.0
+        E[n - 2, N - 1] = E[n - 1, N - 2] = 1.0
+        return E
     N = n - 2
     E = np.zeros((n, N))
     E[1:n - 1, :] = np.eye(N)
@@ -391,15 +441,15 @@ def blur_matrix_bcfree(family: str, h: np.ndarray, n: int) -> np.ndarray:
         the classical BC that the block diagonalises (reflective for 'C',
         periodic for 'F', the odd/tau extension for 'S'): A_X E = E A_N;
     (ii) sampled polynomials of the preserved degree (quadratics for 'C', 'F';
-        linear for 'S'; cubics for 'S3') are eigenvectors with eigenvalue z(0)
-        (Sec. 3.1, 3.2, Remark 2; reading R6).
+        linear for 'S'; cubics for 'S3'; quartics for 'C4') are eigenvectors with
+        eigenvalue z(0) (Sec. 3.1, 3.2, Remark 2; readings R6, R16).
     The polynomials are sampled as monomials on the integer grid, deliberately
     unlike the paper's q and p.  A_X = [z0 P_L | E A_N | z0 P_R] B^{-1} with
     B = [P_L | E | P_R].
     """
     E = extension_matrix(family, n)
     N = E.shape[1]
-    rule = {"C": "reflective", "F": "periodic", "S": "odd", "S3": "odd"}[family]
+    rule = {"C": "reflective", "F": "periodic", "S": "odd", "S3": "odd", "C4": "reflective"}[family]
     AN = bc_matrix(h, N, rule)
     z0 = float(np.sum(h))
     t = np.arange(n, dtype=np.float64) / n
@@ -407,6 +457,8 @@ def blur_matrix_bcfree(family: str, h: np.ndarray, n: int) -> np.ndarray:
         P = [np.ones(n), t]                     # span{1, x} = linear functions
     elif family == "S3":
         P = [np.ones(n), t, t * t, t ** 3]      # cubics
+    elif family == "C4":
+        P = [t, t * t, t ** 3, t ** 4]          # with the constant in range(E): quartics
     else:
         P = [t * t, t]                          # with the constant in range(E): quadratics
     B = np.column_stack(P + [E])
