@@ -30,9 +30,10 @@
  * and the layout of hobc_eigenvalues):  spectral index t of one axis is column
  * t of T_X on that axis: t = 0 is the left border vector (p or q), t = 1..n-2
  * the trigonometric columns in the natural order of the transform, t = n-1 the
- * right border vector.  SINE_CUBIC has two border columns on each side:
- * t = 0, 1 (L1, L2) and t = n-2, n-1 (their flips), t = 2..n-3 trigonometric.
- *   Families SINE, SINE_CUBIC and COSINE keep real spectra: one item is n values (1D) or
+ * right border vector.  SINE_CUBIC and COSINE_QUARTIC have two border columns
+ * on each side: t = 0, 1 (L1, L2 or Q1, Q2) and t = n-2, n-1 (their flips),
+ * t = 2..n-3 trigonometric.
+ *   Families SINE, SINE_CUBIC, COSINE and COSINE_QUARTIC keep real spectra: one item is n values (1D) or
  *   n1 x n0 values stored as [t1][t0] (2D, t0 fastest).
  *   Family FOURIER stores complex values (re, im interleaved) and, because g is
  *   real, only the half of axis 1 that determines the rest:
@@ -62,7 +63,8 @@ typedef enum {
 
 typedef enum {
     HOBC_FAMILY_AUTO = 0,      /* degree 1 -> SINE; degree 2 -> COSINE if the desc says
-                                  the PSF is symmetric, else FOURIER; degree 3 -> SINE_CUBIC */
+                                  the PSF is symmetric, else FOURIER; degree 3 -> SINE_CUBIC;
+                                  degree 4 -> COSINE_QUARTIC                               */
     HOBC_FAMILY_SINE = 1,      /* antireflective, Sec. 2.2, Eq. (eq:ART), (eq:jcf)       */
     HOBC_FAMILY_COSINE = 2,    /* degree 2, symmetric PSF, Sec. 3.1, Eq. (eq:Tc), (eq:Ac) */
     HOBC_FAMILY_FOURIER = 3,   /* degree 2, any PSF, Sec. 3.2, Eq. (eq:Tf), (eq:Af)      */
@@ -72,10 +74,19 @@ typedef enum {
     HOBC_FAMILY_REFLECTIVE = 5, /* classical reflective conditions (Sec. 2, Eq. (eq:refm)):
                                   T = C^T, the orthonormal DCT-II of order n, theta_k =
                                   k pi / n; bc_degree 0, symmetric PSF, HOBC_SPLIT_BF16 only */
-    HOBC_FAMILY_PERIODIC = 6    /* classical periodic conditions (Sec. 2, Eq. (eq:permat)) in
+    HOBC_FAMILY_PERIODIC = 6,   /* classical periodic conditions (Sec. 2, Eq. (eq:permat)) in
                                   the real Hartley basis (for a symmetric PSF it
                                   diagonalises the circulant as F^H does), theta_k =
                                   2 pi k / n; bc_degree 0, symmetric PSF, HOBC_SPLIT_BF16 only */
+    HOBC_FAMILY_COSINE_QUARTIC = 7 /* degree 4, symmetric PSF: the construction of Sec. 3.1
+                                  with two border columns per side, DCT-II of order n-4 on
+                                  x_a = (2a-3) pi/(2(n-4)), border columns (b-x)^2, (b-x)^4
+                                  and their flips spanning the quartics with the constant;
+                                  the paper names higher orders in Sec. 7 without a
+                                  construction.  cond(T) grows like n^3.5 (1e8 at n = 256):
+                                  FP32 is meaningful only for small n.  Plain method
+                                  (plans, steps, host call, binned / refined / learned mu);
+                                  not in the dense, exact-GCV, batched or 3D paths        */
 } hobc_family;
 
 typedef enum {
@@ -101,8 +112,9 @@ typedef struct {
                                   each in [6, 1024]                                        */
     int psf[2];                /* PSF mask size (odd): 1D psf[0] = 2m+1; 2D rows x cols;
                                   needs psf[i] <= n[i] - 2 (Sec. 2.2, Sec. 3), or
-                                  psf[i] <= n[i] - 4 for SINE_CUBIC                       */
-    int bc_degree;             /* 1, 2 or 3 (0 with the REFLECTIVE / PERIODIC families)    */
+                                  psf[i] <= n[i] - 4 (and n[i] >= 8) for SINE_CUBIC and
+                                  COSINE_QUARTIC                                          */
+    int bc_degree;             /* 1, 2, 3 or 4 (0 with the REFLECTIVE / PERIODIC families) */
     hobc_family family;
     int psf_symmetric;         /* caller asserts h_{-j} = h_j on every axis (used by AUTO) */
     hobc_smoothing L;

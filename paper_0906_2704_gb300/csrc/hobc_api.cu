@@ -169,6 +169,11 @@ void theta_frac(int fam, int n, int t, long long& num, long long& den) {
         else { num = t - 1; den = n - 3; }
         return;
     }
+    if (fam == hobc::FAM_C4) {                     // degree 4: DCT-II of order n - 4
+        if (t == 1 || t == n - 2) { num = 0; den = 1; }
+        else { num = t - 2; den = n - 4; }
+        return;
+    }
     if (fam == hobc::FAM_S) { num = t; den = N + 1; }
     else if (fam == hobc::FAM_C) { num = t - 1; den = N; }
     else { num = 2 * (t - 1); den = N; }
@@ -215,6 +220,26 @@ static void cubic_columns(int n, std::vector<double>& L1, std::vector<double>& L
         n2 += L2[a] * L2[a];
     }
     for (int a = 0; a < n; ++a) { L1[a] /= sqrt(n1); L2[a] /= sqrt(n2); }
+}
+
+// Border columns Q1, Q2 of the degree-4 cosine family on x_a = (2a - 3) pi/(2N),
+// a = 0..n-1, N = n - 4, b = x_{n-1}: Q1 = (b - x)^2, Q2 = (b - x)^4, each of
+// unit norm.
+static void quartic_columns(int n, std::vector<double>& Q1, std::vector<double>& Q2) {
+    const int N = n - 4;
+    const double b = (2.0 * (n - 1) - 3.0) * M_PI / (2.0 * N);
+    Q1.assign(n, 0.0);
+    Q2.assign(n, 0.0);
+    double n1 = 0, n2 = 0;
+    for (int a = 0; a < n; ++a) {
+        const double x = (2.0 * a - 3.0) * M_PI / (2.0 * N);
+        const double u = (b - x) * (b - x);
+        Q1[a] = u;
+        Q2[a] = u * u;
+        n1 += Q1[a] * Q1[a];
+        n2 += Q2[a] * Q2[a];
+    }
+    for (int a = 0; a < n; ++a) { Q1[a] /= sqrt(n1); Q2[a] /= sqrt(n2); }
 }
 
 // Gauss-Jordan inverse of a 4x4 matrix with partial pivoting; false if singular.
@@ -272,7 +297,7 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half) {
         // FFT or border tables, only the grid and the eigen-exponential table
         a.N = n; a.L = n; a.M = 8; a.log2M = 3; a.tpg = 1; a.H = n; a.W = n;
     } else {
-    a.N = fam == hobc::FAM_S3 ? n - 4 : n - 2;
+    a.N = (fam == hobc::FAM_S3 || fam == hobc::FAM_C4) ? n - 4 : n - 2;
     const int N = a.N;
     a.L = (fam == hobc::FAM_S || fam == hobc::FAM_S3) ? 2 * (N + 1) : N;
     if (a.L >= 8 && (a.L & (a.L - 1)) == 0) {
@@ -319,7 +344,7 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half) {
         a.chirp = upload_complex<T>(chirp, err);
         a.bhat = upload_complex<T>(c, err);
     }
-    if (fam == hobc::FAM_C) {
+    if (fam == hobc::FAM_C || fam == hobc::FAM_C4) {
         std::vector<cd> post(N);
         for (int k = 0; k < N; ++k) post[k] = expm_ipi(k, 2LL * N);
         a.post = upload_complex<T>(post, err);
@@ -342,12 +367,33 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half) {
             K[3 * 4 + b] = B(b, n - 1) + B(b, n - 3);
         }
         if (!invert4(K, a.k4) && err == cudaSuccess) err = cudaErrorInvalidValue;
+    } else if (fam == hobc::FAM_C4) {
+        std::vector<double> Q2;
+        quartic_columns(n, q, Q2);
+        a.q2 = upload_real<T>(Q2, err);
+        // rows 0-3, 1-2, (n-2)-(n-3), (n-1)-(n-4) of T restricted to the border
+        // columns (Q1, Q2, flip Q2, flip Q1): the half-sample reflection cancels
+        // the cosine columns in these differences
+        auto B = [&](int b, int r) {
+            return b == 0 ? q[r] : b == 1 ? Q2[r] : b == 2 ? Q2[n - 1 - r] : q[n - 1 - r];
+        };
+        double K[16];
+        for (int b = 0; b < 4; ++b) {
+            K[0 * 4 + b] = B(b, 0) - B(b, 3);
+            K[1 * 4 + b] = B(b, 1) - B(b, 2);
+            K[2 * 4 + b] = B(b, n - 2) - B(b, n - 3);
+            K[3 * 4 + b] = B(b, n - 1) - B(b, n - 4);
+        }
+        if (!invert4(K, a.k4) && err == cudaSuccess) err = cudaErrorInvalidValue;
     } else {
         q = border_column(fam, n);
     }
     a.q = upload_real<T>(q, err);
     a.q1 = q[0];
-    if (fam == hobc::FAM_S || fam == hobc::FAM_S3) {
+    if (fam == hobc::FAM_C4) {               // the 4x4 solve replaces the 2x2 one
+        a.ka = 0.0;
+        a.kb = 0.0;
+    } else if (fam == hobc::FAM_S || fam == hobc::FAM_S3) {
         a.ka = 1.0 / q[0];
         a.kb = 0.0;
     } else {
@@ -459,7 +505,8 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
         if (d.psf[i] < 1 || d.psf[i] % 2 == 0 || d.psf[i] > 63) return HOBC_ERR_SIZE;
         if (d.psf[i] > d.n[i] - 2) return HOBC_ERR_SIZE;       // 2m+1 <= n-2
     }
-    const bool cubic = d.family == HOBC_FAMILY_SINE_CUBIC || (d.family == HOBC_FAMILY_AUTO && d.bc_degree == 3);
+    const bool cubic = d.family == HOBC_FAMILY_SINE_CUBIC || d.family == HOBC_FAMILY_COSINE_QUARTIC ||
+                       (d.family == HOBC_FAMILY_AUTO && (d.bc_degree == 3 || d.bc_degree == 4));
     if (cubic)
         for (int i = 0; i < d.ndim; ++i)
             if (d.n[i] < 8 || d.psf[i] > d.n[i] - 4) return HOBC_ERR_SIZE;   // 2m+1 <= n-4
@@ -475,19 +522,24 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
         // classical conditions (Sec. 2): constants preserved, symmetric PSF, dense mode only
         if (d.bc_degree != 0 || !d.psf_symmetric || d.prec != HOBC_SPLIT_BF16) return HOBC_ERR_UNSUPPORTED;
     } else {
-    if (d.bc_degree < 1 || d.bc_degree > 3) return HOBC_ERR_UNSUPPORTED;
+    if (d.bc_degree < 1 || d.bc_degree > 4) return HOBC_ERR_UNSUPPORTED;
     if (fam == HOBC_FAMILY_AUTO) {
         if (d.bc_degree == 1) fam = d.psf_symmetric ? HOBC_FAMILY_SINE : -1;
         else if (d.bc_degree == 2) fam = d.psf_symmetric ? HOBC_FAMILY_COSINE : HOBC_FAMILY_FOURIER;
-        else fam = d.psf_symmetric ? HOBC_FAMILY_SINE_CUBIC : -1;
+        else if (d.bc_degree == 3) fam = d.psf_symmetric ? HOBC_FAMILY_SINE_CUBIC : -1;
+        else fam = d.psf_symmetric ? HOBC_FAMILY_COSINE_QUARTIC : -1;
         if (fam < 0) return HOBC_ERR_UNSUPPORTED;   // sine families need a symmetric PSF (Sec. 2.2)
     }
     if (fam == HOBC_FAMILY_SINE && d.bc_degree != 1) return HOBC_ERR_UNSUPPORTED;
     if ((fam == HOBC_FAMILY_COSINE || fam == HOBC_FAMILY_FOURIER) && d.bc_degree != 2) return HOBC_ERR_UNSUPPORTED;
     if (fam == HOBC_FAMILY_SINE_CUBIC && d.bc_degree != 3) return HOBC_ERR_UNSUPPORTED;
-    if (fam < HOBC_FAMILY_SINE || fam > HOBC_FAMILY_SINE_CUBIC) return HOBC_ERR_ARG;
+    if (fam == HOBC_FAMILY_COSINE_QUARTIC && (d.bc_degree != 4 || !d.psf_symmetric)) return HOBC_ERR_UNSUPPORTED;
+    if (fam != HOBC_FAMILY_COSINE_QUARTIC && (fam < HOBC_FAMILY_SINE || fam > HOBC_FAMILY_SINE_CUBIC))
+        return HOBC_ERR_ARG;
     }
     if (d.prec == HOBC_SPLIT_BF16 && fam == HOBC_FAMILY_FOURIER) return HOBC_ERR_UNSUPPORTED;   // complex T_F
+    // degree 4 runs on the FFT path only (the dense engine has no matrices for it)
+    if (d.prec == HOBC_SPLIT_BF16 && fam == HOBC_FAMILY_COSINE_QUARTIC) return HOBC_ERR_UNSUPPORTED;
 
     hobc_plan_s* p = new hobc_plan_s;
     memset(p, 0, sizeof(*p));

@@ -10,8 +10,8 @@
 // CTA reads its entry, takes that problem's axis tables, and runs the same
 // device code as the single-geometry plan (pair_analysis_body,
 // pair_synthesis_body, gcv_partials_body).  Every line kernel runs 256-thread
-// CTAs: an FFT of length M uses M/8 threads per line pair, so a CTA holds
-// 2048/M groups and the shared memory of a CTA is the same for every M.
+// CTAs: an FFT of length M uses tpg threads per line pair (M/16 for M >= 256,
+// M/8 below), so a CTA holds 256/tpg groups.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -436,7 +436,7 @@ extern "C" hobc_status hobc_batch_create(const hobc_batch_desc* desc, const hobc
     }
     b->items_dev = reinterpret_cast<ItemDev*>(upload(idev, err));
 
-    // line work lists: every pass, per family; a CTA covers 2G lines, G = 256/(M/8)
+    // line work lists: every pass, per family; a CTA covers 2G lines, G = 256/tpg
     const size_t csz = 2 * b->esz;
     auto build_pass = [&](std::vector<PassList>& lists, int pass) {
         for (int fam : {FAM_S, FAM_C, FAM_S3}) {

@@ -18,7 +18,7 @@
 
 namespace hobc {
 
-enum { FAM_S = 1, FAM_C = 2, FAM_F = 3, FAM_S3 = 4, FAM_R = 5, FAM_PH = 6 };   // same values as hobc_family
+enum { FAM_S = 1, FAM_C = 2, FAM_F = 3, FAM_S3 = 4, FAM_R = 5, FAM_PH = 6, FAM_C4 = 7 };   // same values as hobc_family
 
 template <typename T> struct V2;
 template <> struct V2<float> { typedef float2 t; };
@@ -482,19 +482,27 @@ __device__ __forceinline__ double border_coeff(const Axis<T>& ax, double y0, dou
     return which ? ax.kb * r1 + ax.ka * r2 : ax.ka * r1 + ax.kb * r2;
 }
 
-// S3 (degree 3): y = sum_b c_b B_b + E w with border columns B = (L1, L2, flip L2,
-// flip L1) and the odd extension E (rows 0 and n-1 are minus the first and last
-// interior samples, rows 1 and n-2 are zero).  Rows 0+2, 1, n-2 and n-1+n-3 of
-// y therefore involve only the border coefficients: a 4x4 system whose inverse
-// is precomputed in double.
+// Families with two border columns on each side (S3: degree 3; C4: degree 4):
+// y = sum_b c_b B_b + E w with border columns B = (B1, B2, flip B2, flip B1).
+// S3's odd extension E has rows 0 and n-1 equal to minus the first and last
+// interior samples and rows 1 and n-2 zero; C4's half-sample reflection has
+// rows 0, 1 equal to interior rows 1, 0 (rows 3, 2 of y) and rows n-2, n-1
+// equal to rows n-3, n-4.  Four row combinations of y therefore involve only
+// the border coefficients (S3: rows 0+2, 1, n-2, n-1+n-3; C4: rows 0-3, 1-2,
+// n-2-(n-3), n-1-(n-4)): a 4x4 system whose inverse is precomputed in double.
+// y[0..3] are the first four samples, ym[0..3] the last four (ym[3] = y_{n-1}).
 template <typename T>
-__device__ __forceinline__ double border_coeff4(const Axis<T>& ax, double y0, double y1, double y2, double ym3,
-                                                double ym2, double ym1, int b) {
-    const double r[4] = {y0 + y2, y1, ym2, ym1 + ym3};
+__device__ __forceinline__ double border_coeff4(const Axis<T>& ax, const double* y, const double* ym, int b) {
+    double r[4];
+    if (ax.fam == FAM_C4) {
+        r[0] = y[0] - y[3]; r[1] = y[1] - y[2]; r[2] = ym[2] - ym[1]; r[3] = ym[3] - ym[0];
+    } else {
+        r[0] = y[0] + y[2]; r[1] = y[1]; r[2] = ym[2]; r[3] = ym[3] + ym[1];
+    }
     return ax.k4[4 * b] * r[0] + ax.k4[4 * b + 1] * r[1] + ax.k4[4 * b + 2] * r[2] + ax.k4[4 * b + 3] * r[3];
 }
 
-// value of sum_b c_b B_b at sample a (S3)
+// value of sum_b c_b B_b at sample a (S3, C4)
 template <typename T>
 __device__ __forceinline__ T border_sum4(const Axis<T>& ax, const T* c, int a) {
     const int n = ax.n;
@@ -511,6 +519,7 @@ __device__ __forceinline__ T theta_over_pi(int fam, int n, int N, int t) {
     if (fam == FAM_PH) return (T)(2 * t) / (T)n;          // periodic (Eq. (eq:permat))
     if (t == 0 || t == n - 1) return (T)0;
     if (fam == FAM_S3) return (t == 1 || t == n - 2) ? (T)0 : (T)(t - 1) / (T)(N + 1);
+    if (fam == FAM_C4) return (t == 1 || t == n - 2) ? (T)0 : (T)(t - 2) / (T)N;
     if (fam == FAM_S) return (T)t / (T)(N + 1);
     if (fam == FAM_C) return (T)(t - 1) / (T)N;
     return (T)(2 * (t - 1)) / (T)N;

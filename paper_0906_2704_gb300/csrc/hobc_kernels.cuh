@@ -111,31 +111,38 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
     const T* yb = in + item * in_item + (long long)(vb ? rb : 0) * in_rs;
 
     constexpr bool CUBIC = (FAM == FAM_S3);
-    constexpr int NB = CUBIC ? 2 : 1;            // border entries on each side
+    constexpr bool K2 = (FAM == FAM_S3 || FAM == FAM_C4);   // two border columns on each side
+    constexpr bool DCT = (FAM == FAM_C || FAM == FAM_C4);
+    constexpr int NB = K2 ? 2 : 1;               // border entries on each side
     // border coefficients of both lines, one per thread: (c_1, c_n) of line a
-    // then of line b, or the four S3 coefficients of each
+    // then of line b, or the four coefficients of each (S3, C4)
     T* xs = reinterpret_cast<T*>(buf + ax.M + ax.M / 16);
     for (int l = t; l < 4 * NB; l += ax.tpg) {
-        const int side = CUBIC ? l >> 2 : l >> 1;
+        const int side = K2 ? l >> 2 : l >> 1;
         const T* y = side ? yb : ya;
         double c = 0;
         if (side ? vb : va) {
-            if constexpr (CUBIC) c = border_coeff4<T>(ax, y[0], y[1], y[2], y[n - 3], y[n - 2], y[n - 1], l & 3);
-            else c = border_coeff<T>(ax, y[0], y[1], y[n - 2], y[n - 1], l & 1);
+            if constexpr (K2) {
+                const double y4[4] = {y[0], y[1], y[2], y[3]};
+                const double ym4[4] = {y[n - 4], y[n - 3], y[n - 2], y[n - 1]};
+                c = border_coeff4<T>(ax, y4, ym4, l & 3);
+            } else {
+                c = border_coeff<T>(ax, y[0], y[1], y[n - 2], y[n - 1], l & 1);
+            }
         }
         xs[l] = (T)c;
     }
     __syncthreads();
     const T c1af = xs[0], cnaf = xs[1], c1bf = xs[2], cnbf = xs[3];
     T ca4f[4] = {0, 0, 0, 0}, cb4f[4] = {0, 0, 0, 0};
-    if constexpr (CUBIC)
+    if constexpr (K2)
 #pragma unroll
         for (int b = 0; b < 4; ++b) { ca4f[b] = xs[b]; cb4f[b] = xs[4 + b]; }
     const C2<T> zero = cmk<T>(0, 0);
 
     for (int j = t; j < N; j += ax.tpg) {
         T wa, wb;
-        if constexpr (CUBIC) {
+        if constexpr (K2) {
             wa = va ? ya[2 + j] - border_sum4<T>(ax, ca4f, 2 + j) : (T)0;
             wb = vb ? yb[2 + j] - border_sum4<T>(ax, cb4f, 2 + j) : (T)0;
         } else {
@@ -145,7 +152,7 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
         }
         if constexpr (FAM == FAM_F) {
             buf[pidx(j)] = dft_in<T>(ax, j, cmk<T>(wa, wb));
-        } else if constexpr (FAM == FAM_C) {
+        } else if constexpr (DCT) {
             const int p = pos_C(j, N);
             buf[pidx(p)] = dft_in<T>(ax, p, cmk<T>(wa, wb));
         } else {   // odd extension of length 2(N+1)
@@ -173,7 +180,7 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
             sa[0] = cmk<T>(xs[0], 0); sa[W - 1] = cmk<T>(xs[1], 0);
             sb[0] = cmk<T>(xs[2], 0); sb[W - 1] = cmk<T>(xs[3], 0);
         }
-    } else if constexpr (FAM == FAM_C) {
+    } else if constexpr (DCT) {
         for (int k = t; k < N; k += ax.tpg) {
             const C2<T> v = dft_out<T>(buf, ax, k);
             const C2<T> vr = cconj<T>(dft_out<T>(buf, ax, k == 0 ? 0 : N - k));
@@ -181,10 +188,17 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
             // Va = s/2, Vb = -i d/2; DCT-II coefficient = scale * Re(post_k * V)
             const C2<T> ph = ax.post[k];
             const T sk = (k == 0 ? ax.s0 : ax.s1) * (T)0.5;
-            sa[1 + k] = (T)(sk * (ph.x * s.x - ph.y * s.y));
-            sb[1 + k] = (T)(sk * (ph.x * d.y + ph.y * d.x));
+            sa[NB + k] = (T)(sk * (ph.x * s.x - ph.y * s.y));
+            sb[NB + k] = (T)(sk * (ph.x * d.y + ph.y * d.x));
         }
-        if (t == 0) { sa[0] = xs[0]; sa[W - 1] = xs[1]; sb[0] = xs[2]; sb[W - 1] = xs[3]; }
+        if (t == 0) {
+            if constexpr (K2) {
+                sa[0] = xs[0]; sa[1] = xs[1]; sa[W - 2] = xs[2]; sa[W - 1] = xs[3];
+                sb[0] = xs[4]; sb[1] = xs[5]; sb[W - 2] = xs[6]; sb[W - 1] = xs[7];
+            } else {
+                sa[0] = xs[0]; sa[W - 1] = xs[1]; sb[0] = xs[2]; sb[W - 1] = xs[3];
+            }
+        }
     } else {
         for (int k = t; k < N; k += ax.tpg) {
             const C2<T> z = dft_out<T>(buf, ax, k + 1);
@@ -299,12 +313,13 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM 
             }
             buf[pidx(k)] = dft_in<T>(ax, k, cconj<T>(z));
         }
-    } else if constexpr (FAM == FAM_C) {
+    } else if constexpr (FAM == FAM_C || FAM == FAM_C4) {
+        constexpr int NB = (FAM == FAM_C4) ? 2 : 1;
         for (int k = t; k < N; k += ax.tpg) {
             const T isk = k == 0 ? ax.is0 : ax.is1;
-            const T ya = re_of(sa[1 + k]) * isk, yb = re_of(sb[1 + k]) * isk;
-            const T yar = k == 0 ? (T)0 : re_of(sa[1 + N - k]) * ax.is1;
-            const T ybr = k == 0 ? (T)0 : re_of(sb[1 + N - k]) * ax.is1;
+            const T ya = re_of(sa[NB + k]) * isk, yb = re_of(sb[NB + k]) * isk;
+            const T yar = k == 0 ? (T)0 : re_of(sa[NB + N - k]) * ax.is1;
+            const T ybr = k == 0 ? (T)0 : re_of(sb[NB + N - k]) * ax.is1;
             const C2<T> ph = cconj<T>(ax.post[k]);                  // exp(+i pi k/(2N))
             const C2<T> v = cmul<T>(ph, cmk<T>(ya + ybr, yb - yar));
             buf[pidx(k)] = dft_in<T>(ax, k, cconj<T>(v));
@@ -334,7 +349,7 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM 
             const C2<T> z = dft_out<T>(buf, ax, j);
             wa = z.x * ax.sc;
             wb = -z.y * ax.sc;
-        } else if constexpr (FAM == FAM_C) {
+        } else if constexpr (FAM == FAM_C || FAM == FAM_C4) {
             const C2<T> z = dft_out<T>(buf, ax, pos_C(j, N));
             wa = z.x * ax.invN;
             wb = -z.y * ax.invN;
@@ -344,7 +359,7 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM 
             wb = z.x * ax.sc;
         }
     };
-    if constexpr (FAM == FAM_S3) {
+    if constexpr (FAM == FAM_S3 || FAM == FAM_C4) {
         const T c4a[4] = {re_of(sa[0]), re_of(sa[1]), re_of(sa[W - 2]), re_of(sa[W - 1])};
         const T c4b[4] = {re_of(sb[0]), re_of(sb[1]), re_of(sb[W - 2]), re_of(sb[W - 1])};
         for (int j = t; j < N; j += ax.tpg) {
@@ -353,7 +368,23 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM 
             if (va) oa[2 + j] = wa + border_sum4<T>(ax, c4a, 2 + j);
             if (vb) ob[2 + j] = wb + border_sum4<T>(ax, c4b, 2 + j);
         }
-        if (t == 0) {
+        if (FAM == FAM_C4 && t == 0) {
+            // half-sample reflection: rows 0, 1 add interior samples 1, 0 and
+            // rows n-2, n-1 interior samples N-1, N-2
+            T w0a, w0b, w1a, w1b, wNa, wNb, wMa, wMb;
+            wval(0, w0a, w0b);
+            wval(1, w1a, w1b);
+            wval(N - 1, wNa, wNb);
+            wval(N - 2, wMa, wMb);
+            if (va) {
+                oa[0] = border_sum4<T>(ax, c4a, 0) + w1a; oa[1] = border_sum4<T>(ax, c4a, 1) + w0a;
+                oa[n - 2] = border_sum4<T>(ax, c4a, n - 2) + wNa; oa[n - 1] = border_sum4<T>(ax, c4a, n - 1) + wMa;
+            }
+            if (vb) {
+                ob[0] = border_sum4<T>(ax, c4b, 0) + w1b; ob[1] = border_sum4<T>(ax, c4b, 1) + w0b;
+                ob[n - 2] = border_sum4<T>(ax, c4b, n - 2) + wNb; ob[n - 1] = border_sum4<T>(ax, c4b, n - 1) + wMb;
+            }
+        } else if (t == 0) {
             // rows 1 and n-2 carry only the border columns; rows 0 and n-1 also
             // minus the first / last interior trigonometric sample (odd extension)
             T wa0, wb0, wa1, wb1;

@@ -37,8 +37,9 @@ constexpr int kBracketU = 4;         // entries per thread whose loads are issue
 // Fourier family's angles run over [0, 2 pi)); border columns have a = 0.
 __device__ __forceinline__ void angle_fraction(int fam, int n, int t, long long& a, long long& q) {
     if (fam == FAM_S) { q = n - 1; a = (t == n - 1) ? 0 : t; return; }
-    const bool border = t == 0 || t == n - 1 || (fam == FAM_S3 && (t == 1 || t == n - 2));
+    const bool border = t == 0 || t == n - 1 || ((fam == FAM_S3 || fam == FAM_C4) && (t == 1 || t == n - 2));
     if (fam == FAM_S3) { q = n - 3; a = border ? 0 : t - 1; return; }
+    if (fam == FAM_C4) { q = n - 4; a = border ? 0 : t - 2; return; }
     q = n - 2;
     if (border) { a = 0; return; }
     a = (fam == FAM_F) ? 2LL * (t - 1) : (long long)(t - 1);

@@ -92,14 +92,17 @@ extern "C" hobc_status hobc_gcv_noalloc(const hobc_plan_desc* desc, const void* 
         if (dsc.bc_degree == 1) fam = dsc.psf_symmetric ? HOBC_FAMILY_SINE : -1;
         else if (dsc.bc_degree == 2) fam = dsc.psf_symmetric ? HOBC_FAMILY_COSINE : HOBC_FAMILY_FOURIER;
         else if (dsc.bc_degree == 3) fam = dsc.psf_symmetric ? HOBC_FAMILY_SINE_CUBIC : -1;
+        else if (dsc.bc_degree == 4) fam = dsc.psf_symmetric ? HOBC_FAMILY_COSINE_QUARTIC : -1;
         else fam = -1;
         if (fam < 0) return HOBC_ERR_UNSUPPORTED;
     }
-    if (fam < HOBC_FAMILY_SINE || fam > HOBC_FAMILY_SINE_CUBIC) return HOBC_ERR_ARG;
+    if (fam != HOBC_FAMILY_COSINE_QUARTIC && (fam < HOBC_FAMILY_SINE || fam > HOBC_FAMILY_SINE_CUBIC))
+        return HOBC_ERR_ARG;
+    const bool two_borders = fam == HOBC_FAMILY_SINE_CUBIC || fam == HOBC_FAMILY_COSINE_QUARTIC;
 
     // geometry of the stored spectrum (include/hobc.h, "Spectrum layout")
     const int nl = dsc.n[dsc.ndim - 1];
-    const int Nl = fam == HOBC_FAMILY_SINE_CUBIC ? nl - 4 : nl - 2;
+    const int Nl = two_borders ? nl - 4 : nl - 2;
     const int Wl = fam == HOBC_FAMILY_FOURIER ? Nl / 2 + 3 : nl;
     const long long S = dsc.ndim == 1 ? (long long)Wl : (long long)Wl * dsc.n[0];
     const int chunk = hobc::gcv_chunk_for(S, dsc.n_mu, dsc.prec == HOBC_FP64);
@@ -121,7 +124,7 @@ extern "C" hobc_status hobc_gcv_noalloc(const hobc_plan_desc* desc, const void* 
     geo.ndim = dsc.ndim;
     geo.fam = fam;
     geo.n0 = dsc.n[0];
-    geo.N0 = fam == HOBC_FAMILY_SINE_CUBIC ? dsc.n[0] - 4 : dsc.n[0] - 2;
+    geo.N0 = two_borders ? dsc.n[0] - 4 : dsc.n[0] - 2;
     geo.n1 = nl;
     geo.N1 = Nl;
     geo.W1 = Wl;

@@ -138,6 +138,7 @@ hobc_status run_analysis(hobc_plan_s* p, const void* g, void* ghat) {
     switch (p->fam) {
         case FAM_S: return analysis_fam<T, FAM_S>(p, gt, ghat);
         case FAM_S3: return analysis_fam<T, FAM_S3>(p, gt, ghat);
+        case FAM_C4: return analysis_fam<T, FAM_C4>(p, gt, ghat);
         case FAM_C: return analysis_fam<T, FAM_C>(p, gt, ghat);
         default: return analysis_fam<T, FAM_F>(p, gt, ghat);
     }
@@ -178,6 +179,7 @@ hobc_status run_synthesis(hobc_plan_s* p, const void* c, void* y) {
     switch (p->fam) {
         case FAM_S: return synthesis_fam<T, FAM_S, false>(p, c, yt, fd);
         case FAM_S3: return synthesis_fam<T, FAM_S3, false>(p, c, yt, fd);
+        case FAM_C4: return synthesis_fam<T, FAM_C4, false>(p, c, yt, fd);
         case FAM_C: return synthesis_fam<T, FAM_C, false>(p, c, yt, fd);
         default: return synthesis_fam<T, FAM_F, false>(p, c, yt, fd);
     }
@@ -191,6 +193,7 @@ hobc_status run_filter_synthesis(hobc_plan_s* p, const void* ghat, const void* D
     switch (p->fam) {
         case FAM_S: return synthesis_fam<T, FAM_S, true>(p, ghat, ft, fd);
         case FAM_S3: return synthesis_fam<T, FAM_S3, true>(p, ghat, ft, fd);
+        case FAM_C4: return synthesis_fam<T, FAM_C4, true>(p, ghat, ft, fd);
         case FAM_C: return synthesis_fam<T, FAM_C, true>(p, ghat, ft, fd);
         default: return synthesis_fam<T, FAM_F, true>(p, ghat, ft, fd);
     }
@@ -206,6 +209,7 @@ hobc_status run_filter_synthesis_mu(hobc_plan_s* p, const void* ghat, const void
     switch (p->fam) {
         case FAM_S: return synthesis_fam<T, FAM_S, true>(p, ghat, ft, fd);
         case FAM_S3: return synthesis_fam<T, FAM_S3, true>(p, ghat, ft, fd);
+        case FAM_C4: return synthesis_fam<T, FAM_C4, true>(p, ghat, ft, fd);
         case FAM_C: return synthesis_fam<T, FAM_C, true>(p, ghat, ft, fd);
         default: return synthesis_fam<T, FAM_F, true>(p, ghat, ft, fd);
     }
@@ -311,6 +315,10 @@ hobc_status prepare_kernels(hobc_plan_s* p) {
     HOBC_SMEM((k_pair_synthesis<T, FAM_S3, 0>));
     HOBC_SMEM((k_pair_synthesis<T, FAM_S3, 1>));
     HOBC_SMEM((k_pair_synthesis<T, FAM_S3, 2>));
+    HOBC_SMEM((k_pair_analysis<T, FAM_C4>));
+    HOBC_SMEM((k_pair_synthesis<T, FAM_C4, 0>));
+    HOBC_SMEM((k_pair_synthesis<T, FAM_C4, 1>));
+    HOBC_SMEM((k_pair_synthesis<T, FAM_C4, 2>));
     HOBC_SMEM((k_pair_analysis<T, FAM_C>));
     HOBC_SMEM((k_pair_analysis<T, FAM_F>));
     HOBC_SMEM((k_pair_synthesis<T, FAM_S, 0>));

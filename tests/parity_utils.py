@@ -8,7 +8,8 @@ import numpy as np
 from oracle import hobc_oracle as O
 from paper_0906_2704_gb300 import synth
 
-FAM_LETTER = {"sine": "S", "cosine": "C", "fourier": "F", "sine3": "S3", "reflective": "R", "periodic": "PH"}
+FAM_LETTER = {"sine": "S", "cosine": "C", "fourier": "F", "sine3": "S3", "reflective": "R", "periodic": "PH",
+              "cosine4": "C4"}
 EPS32 = 2.0 ** -24
 
 
@@ -110,7 +111,7 @@ def log2_fft(fam: str, shape) -> float:
     """log2 of the largest power-of-two FFT the kernels use for these lengths."""
     out = 0.0
     for n in shape:
-        N = n - 4 if fam == "S3" else n - 2
+        N = n - 4 if fam in ("S3", "C4") else n - 2
         L = 2 * (N + 1) if fam in ("S", "S3") else N
         M = L if (L >= 8 and L & (L - 1) == 0) else max(8, 1 << int(np.ceil(np.log2(2 * L - 1))))
         out = max(out, np.log2(M))

@@ -45,7 +45,11 @@ def _create(hobc, **kw):
     (dict(n=2048), "HOBC_ERR_SIZE"),                    # n > 1024
     (dict(psf=4), "HOBC_ERR_SIZE"),                     # even PSF
     (dict(n=8, psf=7), "HOBC_ERR_SIZE"),                # 2m+1 > n-2
-    (dict(bc_degree=4), "HOBC_ERR_UNSUPPORTED"),
+    (dict(bc_degree=5), "HOBC_ERR_UNSUPPORTED"),
+    (dict(bc_degree=4, psf_symmetric=False), "HOBC_ERR_UNSUPPORTED"),   # quartic cosine family needs symmetry
+    (dict(family="cosine4", bc_degree=2), "HOBC_ERR_UNSUPPORTED"),
+    (dict(bc_degree=4, n=9, psf=7), "HOBC_ERR_SIZE"),               # 2m+1 <= n-4 for degree 4
+    (dict(prec="split_bf16", bc_degree=4), "HOBC_ERR_UNSUPPORTED"),  # no dense matrices for degree 4
     (dict(bc_degree=3, psf_symmetric=False), "HOBC_ERR_UNSUPPORTED"),   # cubic sine family needs symmetry
     (dict(family="sine3", bc_degree=2), "HOBC_ERR_UNSUPPORTED"),
     (dict(bc_degree=3, n=9, psf=7), "HOBC_ERR_SIZE"),               # 2m+1 <= n-4 for degree 3
