@@ -85,8 +85,8 @@ typedef enum {
                                   the paper names higher orders in Sec. 7 without a
                                   construction.  cond(T) grows like n^3.5 (1e8 at n = 256):
                                   FP32 is meaningful only for small n.  Plain method
-                                  (plans, steps, host call, binned / refined / learned mu);
-                                  not in the dense, exact-GCV, batched or 3D paths        */
+                                  (plans, steps, host call, binned / refined / learned mu)
+                                  and the exact GCV; not in the dense, batched or 3D paths */
 } hobc_family;
 
 typedef enum {

@@ -20,7 +20,7 @@
  * every term a sum of squares, so rounding is amplified by cond(T), not
  * cond(T)^2.  Per (entry, mu) this costs 1 + 2k reciprocals and about 4k(k+1)
  * products beside the approximation's terms (complex for the Fourier
- * family).  Every family: sine, cosine and Fourier k = 1, degree 3 k = 2; the
+ * family).  Every family: sine, cosine and Fourier k = 1, degrees 3 and 4 k = 2; the
  * classical reflective and periodic conditions of HOBC_SPLIT_BF16 plans have
  * orthogonal T, k = 0, and G_ex equals the approximation.  The Fourier family
  * stores half of the last axis: a full column of the other half is the

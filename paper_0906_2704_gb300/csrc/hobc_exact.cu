@@ -93,7 +93,7 @@ hobc_status axis_matrix(int fam, int n, cudaStream_t st, std::vector<cdx>& T) {
     hobc_plan_desc q;
     memset(&q, 0, sizeof(q));
     q.ndim = 1; q.n[0] = n; q.psf[0] = 1; q.family = (hobc_family)fam; q.psf_symmetric = 1;
-    q.bc_degree = fam == HOBC_FAMILY_SINE ? 1 : (fam == HOBC_FAMILY_SINE_CUBIC ? 3 : 2);
+    q.bc_degree = fam == HOBC_FAMILY_SINE ? 1 : fam == HOBC_FAMILY_SINE_CUBIC ? 3 : fam == HOBC_FAMILY_COSINE_QUARTIC ? 4 : 2;
     q.L = HOBC_L_IDENTITY; q.prec = HOBC_FP64; q.n_mu = 1; q.batch = items; q.psf_per_item = 0;
     const double one = 1.0;
     hobc_plan* ip = nullptr;
@@ -648,7 +648,7 @@ namespace {
 
 int border_count(int fam) {
     if (fam == HOBC_FAMILY_SINE || fam == HOBC_FAMILY_COSINE || fam == HOBC_FAMILY_FOURIER) return 1;
-    if (fam == HOBC_FAMILY_SINE_CUBIC) return 2;
+    if (fam == HOBC_FAMILY_SINE_CUBIC || fam == HOBC_FAMILY_COSINE_QUARTIC) return 2;
     if (fam == HOBC_FAMILY_REFLECTIVE || fam == HOBC_FAMILY_PERIODIC) return 0;   // T orthogonal
     return -1;
 }

@@ -17,6 +17,7 @@ PSF with L = I gives f = g / (1 + mu*) with the smallest mu chosen.
 import numpy as np
 import pytest
 
+from oracle import exact_gcv_oracle as X
 from oracle import hobc_oracle as O
 from paper_0906_2704_gb300 import synth
 import parity_utils as P
@@ -197,7 +198,7 @@ def test_delta_psf_closed_form(prec):
 
 
 def test_degree4_outside_the_plain_path_is_rejected():
-    """Degree 4 needs a symmetric PSF and runs on the FFT path of 1D/2D plans only."""
+    """Degree 4 needs a symmetric PSF; the dense engine and 3D plans reject it."""
     mus = synth.mu_grid(4)
     with pytest.raises(hobc.HobcError) as e:
         hobc.Plan(2, (16, 16), (5, 5), 4, mus, prec="fp32", family="auto", psf_symmetric=False)
@@ -211,8 +212,32 @@ def test_degree4_outside_the_plain_path_is_rejected():
     with pytest.raises(hobc.HobcError) as e:
         hobc.Volume((8, 10, 10), (3, 3, 3), 4, mus, prec="fp64", family="cosine4", psf_symmetric=True)
     assert e.value.status == 2
-    plan = hobc.Plan(2, (16, 16), (5, 5), 4, mus, prec="fp64", family="cosine4", psf_symmetric=True)
-    with pytest.raises(hobc.HobcError):
-        plan.gcv_exact(torch.zeros((1, plan.spec_elems), dtype=torch.float64, device="cuda"),
-                       torch.ones((1, plan.spec_elems), dtype=torch.float64, device="cuda"), None,
-                       torch.zeros(1, dtype=torch.int32, device="cuda"))
+
+
+@pytest.mark.parametrize("L", ["I", "lap"])
+@pytest.mark.parametrize("ndim,n,taps", [(1, (14,), 5), (2, (12, 13), (3, 5))])
+def test_degree4_exact_gcv_matches_oracle(ndim, n, taps, L):
+    """The exact GCV functional (Eq. (eq:gcv), T_X kept in the numerator) on identical
+    FP64 inputs against the oracle's dense synthesis per mu, within 64 eps cond(T)."""
+    h = P.psf_for("C", ndim, taps)
+    h = h / h.sum()
+    g, _ = P.problems(ndim, n, h, 2, 9)
+    mus = synth.mu_grid(12, 1e-6, 1.0)
+    plan = hobc.Plan(ndim, n, h.shape, 4, mus, L=L, prec="fp64", family="cosine4", psf_symmetric=True, batch=2)
+    gin = np.zeros((2, plan.spec_elems))
+    full = []
+    for b in range(2):
+        ghat, d, s, _, _ = P.oracle_steps("C4", ndim, h, g[b], L, mus)
+        full.append((ghat.real, d.real, s))
+        gin[b] = P.to_layout("C4", ghat.real).reshape(-1)
+    din = P.to_layout("C4", full[0][1]).reshape(-1)[None]
+    G_d = torch.empty((2, len(mus)), dtype=torch.float64, device="cuda")
+    mi_d = torch.empty(2, dtype=torch.int32, device="cuda")
+    plan.gcv_exact(_dev(gin, np.float64), _dev(din, np.float64), G_d, mi_d)
+    G, mi = G_d.cpu().numpy(), mi_d.cpu().numpy()
+    tol = max(1e-10, 64 * EPS["fp64"] * _cond(n))
+    for b, (gr, dr, s) in enumerate(full):
+        Go = X.gcv_exact_curve("C4", gr, dr, s, mus)
+        assert np.all(np.abs(G[b] - Go) <= tol * Go), np.max(np.abs(G[b] - Go) / Go)
+        k, ko = int(mi[b]), int(np.argmin(Go))
+        assert k == ko or Go[k] <= (1 + 2 * tol) * Go.min()
