@@ -25,8 +25,7 @@ Families (per axis):
 Comparison (classical) families, used by the pins:
   'P'  periodic (Sec. 2.1, Eq. (eq:permat));  'R' reflective (Sec. 2.1, Eq. (eq:refm))
 
-Readings where the paper is silent, garbled or inconsistent (each listed in
-DESIGN.md):
+Readings where the paper is silent, garbled or inconsistent:
   R2  p in Eq. (eq:ART) is normalised to unit 2-norm (the printed factor is the
       reciprocal of the one that makes ||p|| = 1, which Sec. 2.2 asserts).
   R3  convolution convention g_i = sum_j h_j f_{i-j} (Eq. (eq:mod_cont)); the
