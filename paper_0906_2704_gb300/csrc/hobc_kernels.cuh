@@ -12,9 +12,10 @@
 
 #include "hobc_device.cuh"
 
-// Minimum resident 512-thread blocks per SM asked of the FP32 line kernels
-// (caps their registers at 65536 / (512 x this)): 2 gives the 64 registers
-// that the 16 values per thread of the radix-16 FFT stages need.
+// Register cap of the FP32 line kernels.  64 keeps eight 128-thread FFT
+// groups (four 256-thread CTAs) resident per SM at the cost of a few spilled
+// bytes; 72 (no spills, six groups) ran the 1024^2 passes 11% slower.  FP64
+// kernels may use 128 (512 threads x 128 = the register file).
 #ifndef HOBC_LINE_REGS
 #define HOBC_LINE_REGS 64
 #endif
