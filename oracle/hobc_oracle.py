@@ -22,6 +22,8 @@ Families (per axis):
   'C4' quartic-preserving, cosine basis, symmetric PSF: degree 4, the cosine
       family with two border columns per side (Sec. 7 names higher orders);
       built as reading R16 below.
+  'F4' quartic-preserving, Fourier basis, any PSF: degree 4, the construction of
+      Sec. 3.2 with two border columns per side (reading R17 below).
 Comparison (classical) families, used by the pins:
   'P'  periodic (Sec. 2.1, Eq. (eq:permat));  'R' reflective (Sec. 2.1, Eq. (eq:refm))
 
@@ -46,6 +48,13 @@ Readings where the paper is silent, garbled or inconsistent:
       (x-a)^4, each of unit norm, with eigenvalue z(0); with the cosine of
       frequency 0 they span the quartics.  Interior eigenvalues are those of the
       reflective matrix of order n-4 (angles (t-2) pi/N).
+  R17 degree 4, Fourier basis ('F4'): the construction of Sec. 3.2 with two
+      border columns per side: DFT of order N = n-4 on x_i = (i-2) 2 pi/N,
+      i = 0..n-1 (x_2..x_{n-3} the DFT samples; two points added at each end by
+      continuity, a periodic wrap: rows 0, 1 repeat rows n-4, n-3 and rows n-2,
+      n-1 repeat rows 2, 3), interval [a, b] = [x_0, x_{n-1}], border columns
+      (b-x)^2, (b-x)^4 and their flips, unit norm, eigenvalue z(0); interior
+      eigenvalues z(-theta) of the circulant of order n-4 (angles (t-2) 2 pi/N).
   GCV with complex spectra uses |sigma_i ghat_i|^2 (Eq. (eq:gcv2) is written for
       real data).
 
@@ -167,9 +176,18 @@ def quartic_grid(n: int):
     return x, x[0], x[-1]
 
 
-def quartic_border_columns(n: int):
-    """Q1 = (b-x)^2, Q2 = (b-x)^4 of the degree-4 transform (reading R16), unit 2-norm."""
-    x, a, b = quartic_grid(n)
+def fourier4_grid(n: int):
+    """Grid x_0..x_{n-1} and interval [a, b] of the degree-4 Fourier transform
+    (reading R17): x_i = (i - 2) 2 pi / N, N = n - 4."""
+    N = n - 4
+    x = (np.arange(n) - 2) * 2 * np.pi / N
+    return x, x[0], x[-1]
+
+
+def quartic_border_columns(n: int, grid=None):
+    """Q1 = (b-x)^2, Q2 = (b-x)^4 of the degree-4 transforms (readings R16, R17), unit
+    2-norm, on the cosine grid (default) or the grid ``grid(n)`` returns."""
+    x, a, b = (grid or quartic_grid)(n)
     Q1 = (b - x) ** 2
     Q2 = (b - x) ** 4
     return Q1 / np.linalg.norm(Q1), Q2 / np.linalg.norm(Q2)
@@ -221,6 +239,9 @@ def eigen_angles(family: str, n: int) -> np.ndarray:
     elif family == "C4":                                 # reading R16
         th = (i - 3) * np.pi / (n - 4)
         th[[0, 1, n - 2, n - 1]] = 0.0
+    elif family == "F4":                                 # reading R17
+        th = (i - 3) * 2 * np.pi / (n - 4)
+        th[[0, 1, n - 2, n - 1]] = 0.0
     elif family in ("P", "PH"):
         th = 2 * (i - 1) * np.pi / n
     elif family == "R":
@@ -252,6 +273,16 @@ def transform_matrix(family: str, n: int) -> np.ndarray:
         return hartley_matrix(n)
     if family == "R":
         return dct2_matrix(n).T
+    if family == "F4":                                   # reading R17
+        N = n - 4
+        Q1, Q2 = quartic_border_columns(n, fourier4_grid)
+        x, a, b = fourier4_grid(n)
+        j = np.arange(N)
+        T = np.zeros((n, n), dtype=np.complex128)
+        T[:, 0], T[:, 1] = Q1, Q2
+        T[:, n - 2], T[:, n - 1] = Q2[::-1], Q1[::-1]
+        T[:, 2:N + 2] = np.exp(1j * np.outer(x, j)) / np.sqrt(N)   # the columns of F^H, extended
+        return T
     if family == "C4":                                   # reading R16
         N = n - 4
         Q1, Q2 = quartic_border_columns(n)
@@ -412,6 +443,13 @@ def extension_matrix(family: str, n: int) -> np.ndarray:
         E[0, 0] = -1.0
         E[n - 1, N - 1] = -1.0
         return E
+    if family == "F4":                                   # periodic wrap by two samples
+        N = n - 4
+        E = np.zeros((n, N))
+        E[2:N + 2, :] = np.eye(N)
+        E[0, N - 2] = E[1, N - 1] = 1.0
+        E[n - 2, 0] = E[n - 1, 1] = 1.0
+        return E
     if family == "C4":                                   # half-sample reflection by two samples
         N = n - 4
         E = np.zeros((n, N))
@@ -448,7 +486,8 @@ def blur_matrix_bcfree(family: str, h: np.ndarray, n: int) -> np.ndarray:
     """
     E = extension_matrix(family, n)
     N = E.shape[1]
-    rule = {"C": "reflective", "F": "periodic", "S": "odd", "S3": "odd", "C4": "reflective"}[family]
+    rule = {"C": "reflective", "F": "periodic", "S": "odd", "S3": "odd", "C4": "reflective",
+            "F4": "periodic"}[family]
     AN = bc_matrix(h, N, rule)
     z0 = float(np.sum(h))
     t = np.arange(n, dtype=np.float64) / n
@@ -456,7 +495,7 @@ def blur_matrix_bcfree(family: str, h: np.ndarray, n: int) -> np.ndarray:
         P = [np.ones(n), t]                     # span{1, x} = linear functions
     elif family == "S3":
         P = [np.ones(n), t, t * t, t ** 3]      # cubics
-    elif family == "C4":
+    elif family in ("C4", "F4"):
         P = [t, t * t, t ** 3, t ** 4]          # with the constant in range(E): quartics
     else:
         P = [t * t, t]                          # with the constant in range(E): quadratics

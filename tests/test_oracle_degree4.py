@@ -186,3 +186,87 @@ def test_pins_catch_a_wrong_second_border_column(monkeypatch):
     t = np.linspace(-0.7, 1.9, n)
     assert np.abs(A @ t ** 4 - t ** 4).max() > 1e-4
     assert np.abs(A - O.blur_matrix_bcfree("C4", H_SYM, n)).max() > 1e-6
+
+
+# ----------------------------------------------- degree 4, Fourier basis (R17)
+
+H_NONSYM = np.array([0.05, 0.3, 0.4, 0.15, 0.1])
+
+
+def _condF(n):
+    return np.linalg.cond(O.transform_matrix("F4", n))
+
+
+def test_fourier4_interior_block_is_the_dft_and_border_rows_wrap():
+    """Rows 2..n-3 of the interior columns are F^H of order n-4 (unitary DFT); rows 0, 1
+    repeat rows n-4, n-3 and rows n-2, n-1 repeat rows 2, 3 (periodic wrap, R17)."""
+    n = 14
+    N = n - 4
+    T = O.transform_matrix("F4", n)
+    assert np.allclose(T[2:N + 2, 2:N + 2], O.dft_matrix(N).conj().T, atol=1e-14)
+    assert np.allclose(T[0, 2:N + 2], T[n - 4, 2:N + 2], atol=1e-13)
+    assert np.allclose(T[1, 2:N + 2], T[n - 3, 2:N + 2], atol=1e-13)
+    assert np.allclose(T[n - 2, 2:N + 2], T[2, 2:N + 2], atol=1e-13)
+    assert np.allclose(T[n - 1, 2:N + 2], T[3, 2:N + 2], atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [9, 13, 24])
+def test_fourier4_matrix_equals_transform_free_construction(n):
+    """T diag(z(-theta)) T^{-1} for a nonsymmetric PSF equals the transform-free matrix
+    from the periodic rule of order n-4 on the extended interior and quartic
+    preservation; it is real."""
+    As = O.blur_matrix_spectral("F4", H_NONSYM, n)
+    assert np.abs(As - O.blur_matrix_bcfree("F4", H_NONSYM, n)).max() < 64 * EPS * _condF(n)
+    assert np.abs(As.imag).max() < 64 * EPS * _condF(n)
+
+
+def test_fourier4_literal_symbol_is_the_mirrored_model():
+    """Reading R3 holds for degree 4 too: z(+theta) gives the model of the mirrored PSF."""
+    n = 13
+    T = O.transform_matrix("F4", n)
+    lit = T @ np.diag(O.symbol(H_NONSYM, O.eigen_angles("F4", n))) @ np.linalg.inv(T)
+    assert np.abs(lit - O.blur_matrix_bcfree("F4", H_NONSYM, n)).max() > 1e-2
+    assert np.abs(lit - O.blur_matrix_bcfree("F4", H_NONSYM[::-1], n)).max() < 64 * EPS * _condF(n)
+
+
+def test_fourier4_quartics_preserved_and_quintics_not():
+    n = 20
+    A = O.blur_matrix_spectral("F4", H_NONSYM, n)
+    t = np.linspace(-0.7, 1.9, n)
+    tol = 64 * EPS * _condF(n) * 10
+    for k in range(5):
+        assert np.abs(A @ t ** k - t ** k).max() < tol * max(1.0, np.abs(t ** k).max())
+    assert np.abs(A @ t ** 5 - t ** 5).max() > 1e-4
+
+
+@pytest.mark.parametrize("L", ["I", "lap"])
+@pytest.mark.parametrize("mu", [1e-6, 1e-2, 3.0])
+def test_fourier4_filter_equals_reblurred_normal_equations(L, mu):
+    """Eq. (eq:freg) = dense solve of (A'A + mu L'L) f = A'g with A' the matrix of the
+    rotated PSF (Sec. 4.1)."""
+    n = 13
+    g = np.random.default_rng(7).standard_normal(n)
+    d = O.eigenvalues_1d("F4", H_NONSYM, n)
+    s = O.smoothing_1d("F4", n, L)
+    fs = O.synthesis_1d("F4", O.filter_factors(d, s, mu) * O.analysis_1d("F4", g)).real
+    fn = O.tikhonov_normal_equations_1d("F4", H_NONSYM, g, L, mu)
+    c = _condF(n)
+    assert np.abs(fs - fn).max() < 64 * EPS * c * c * max(1.0, np.abs(fn).max())
+
+
+@pytest.mark.parametrize("L", ["I", "lap"])
+def test_fourier4_2d_separable_mode_equals_dense_normal_equations(L):
+    n0, n1 = 9, 10
+    h = synth.gaussian_psf_2d_rotated(1.0, 0.6, 30, 3, 0.2, -0.1)
+    g = np.random.default_rng(2).standard_normal((n0, n1))
+    mu = 0.02
+    A = O.blur_matrix_2d_spectral("F4", h, n0, n1)
+    Ar = O.blur_matrix_2d_spectral("F4", h[::-1, ::-1], n0, n1)
+    lap5 = np.array([[0, -1.0, 0], [-1.0, 4.0, -1.0], [0, -1.0, 0]])
+    Lm = np.eye(n0 * n1) if L == "I" else O.blur_matrix_2d_spectral("F4", lap5, n0, n1)
+    fn = np.linalg.solve(Ar @ A + mu * Lm @ Lm, Ar @ g.ravel()).real.reshape(n0, n1)
+    d = O.eigenvalues_2d("F4", h, n0, n1)
+    s = O.smoothing_2d("F4", n0, n1, L)
+    fs = O.synthesis_2d("F4", O.filter_factors(d, s, mu) * O.analysis_2d("F4", g)).real
+    c = _condF(n0) * _condF(n1)
+    assert np.abs(fs - fn).max() < 64 * EPS * c * c * max(1.0, np.abs(fn).max())
