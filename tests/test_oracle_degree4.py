@@ -270,3 +270,43 @@ def test_fourier4_2d_separable_mode_equals_dense_normal_equations(L):
     fs = O.synthesis_2d("F4", O.filter_factors(d, s, mu) * O.analysis_2d("F4", g)).real
     c = _condF(n0) * _condF(n1)
     assert np.abs(fs - fn).max() < 64 * EPS * c * c * max(1.0, np.abs(fn).max())
+
+
+def test_pins_catch_planted_mistakes_in_grids_and_angles(monkeypatch):
+    """A Fourier grid of the wrong step, a shifted cosine angle grid and a swapped wrap
+    row each break the transform-free equality the pins above rely on."""
+    n = 13
+    tol = 1e-6
+    # the degree-4 Fourier grid with the step of order n-3 (a shift of the whole grid
+    # would only rephase the columns, which leaves A unchanged)
+    good = O.fourier4_grid
+
+    def shifted(m):
+        x = (np.arange(m) - 2) * 2 * np.pi / (m - 3)
+        return x, x[0], x[-1]
+    monkeypatch.setattr(O, "fourier4_grid", shifted)
+    assert np.abs(O.blur_matrix_spectral("F4", H_NONSYM, n) - O.blur_matrix_bcfree("F4", H_NONSYM, n)).max() > tol
+    monkeypatch.setattr(O, "fourier4_grid", good)
+    # the interior angles of the cosine family off by one frequency
+    angles = O.eigen_angles
+
+    def off_by_one(fam, m):
+        th = angles(fam, m)
+        if fam == "C4":
+            th = th.copy()
+            th[2:m - 2] = (np.arange(2, m - 2) - 1) * np.pi / (m - 4)
+        return th
+    monkeypatch.setattr(O, "eigen_angles", off_by_one)
+    assert np.abs(O.blur_matrix_spectral("C4", H_SYM, n) - O.blur_matrix_bcfree("C4", H_SYM, n)).max() > tol
+    monkeypatch.setattr(O, "eigen_angles", angles)
+    # the wrap rows of the Fourier extension swapped
+    ext = O.extension_matrix
+
+    def swapped(fam, m):
+        E = ext(fam, m)
+        if fam == "F4":
+            E = E.copy()
+            E[[0, 1]] = E[[1, 0]]
+        return E
+    monkeypatch.setattr(O, "extension_matrix", swapped)
+    assert np.abs(O.blur_matrix_spectral("F4", H_NONSYM, n) - O.blur_matrix_bcfree("F4", H_NONSYM, n)).max() > tol
