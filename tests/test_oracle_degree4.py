@@ -310,3 +310,40 @@ def test_pins_catch_planted_mistakes_in_grids_and_angles(monkeypatch):
         return E
     monkeypatch.setattr(O, "extension_matrix", swapped)
     assert np.abs(O.blur_matrix_spectral("F4", H_NONSYM, n) - O.blur_matrix_bcfree("F4", H_NONSYM, n)).max() > tol
+
+
+@pytest.mark.parametrize("L", ["I", "lap"])
+def test_fourier4_gcv_brute_force_tiny(L):
+    """n = 10, nonsymmetric PSF: per mu the dense solve with A' the rotated-PSF matrix,
+    ||T^{-1}(g - A f)||^2 / trace(I - A R)^2, equals the G of the spectral sums."""
+    n = 10
+    rng = np.random.default_rng(13)
+    g = np.cumsum(rng.standard_normal(n)) + 0.3 * rng.standard_normal(n)
+    mus = synth.mu_grid(17, 1e-5, 10.0)
+    A = O.blur_matrix_spectral("F4", H_NONSYM, n)
+    Ar = O.blur_matrix_spectral("F4", H_NONSYM[::-1], n)
+    Lm = np.eye(n) if L == "I" else O.blur_matrix_spectral("F4", np.array([-1.0, 2.0, -1.0]), n)
+    T = O.transform_matrix("F4", n)
+    brute = []
+    for mu in mus:
+        R = np.linalg.solve(Ar @ A + mu * Lm @ Lm, Ar)
+        r = g - A @ (R @ g)
+        brute.append(np.linalg.norm(np.linalg.solve(T, r)) ** 2 / abs(np.trace(np.eye(n) - A @ R)) ** 2)
+    brute = np.array(brute)
+    _, G, k, _ = O.deblur_1d("F4", H_NONSYM, g, L, mus)
+    assert np.allclose(G, brute, rtol=64 * EPS * _condF(n) ** 2)
+    assert k == int(np.argmin(brute))
+
+
+def test_fourier4_2d_interior_is_periodic_and_biquartics_preserved():
+    n0, n1 = 10, 11
+    h = synth.gaussian_psf_2d_rotated(1.2, 0.7, 30, 5, 0.4, -0.3)
+    A2 = O.blur_matrix_2d_spectral("F4", h, n0, n1)
+    E0, E1 = O.extension_matrix("F4", n0), O.extension_matrix("F4", n1)
+    E = np.kron(E0, E1)
+    tol = 64 * EPS * _condF(n0) * _condF(n1)
+    assert np.abs(A2 @ E - E @ O.bc_matrix_2d(h, n0 - 4, n1 - 4, "periodic")).max() < tol
+    t0 = np.arange(n0)[:, None] / 3.0
+    t1 = np.arange(n1)[None, :] / 4.0
+    u = sum(t0 ** a for a in range(5)) * sum((-0.7 * t1) ** a for a in range(5))
+    assert np.abs(A2 @ u.ravel() - u.ravel()).max() < tol * np.abs(u).max()
