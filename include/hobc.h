@@ -170,6 +170,10 @@ hobc_status hobc_deblur_host(hobc_plan* plan, const void* g_host, const void* ps
  * returns once the PSF has been read (it is copied into the plan's staging).
  * g_host must stay unchanged and f_host, mu_index_host, gcv_host unread until
  * hobc_plan_wait returns; with page-locked buffers the host returns at once.
+ * All four host buffers must be page-locked for that: mu_index_host and
+ * gcv_host are copied on the plan's stream, and a copy into pageable memory
+ * makes the host wait for every kernel queued before it (pass NULL for them, or
+ * page-locked buffers, to keep the call asynchronous).
  * Consecutive calls on one plan overlap: a call's uploads run while the
  * previous call's kernels do, each chunk's upload waiting only until the
  * previous call's analysis has read that chunk's input slots, and each chunk's
@@ -230,13 +234,22 @@ hobc_status hobc_filter_synthesis(hobc_plan* plan, const void* ghat_dev, const v
  *         not checked here because they live on the device);
  *   gcv_dev: [batch][K] output (nullable); mu_index_dev: [batch] output;
  *   cuda_stream: the stream to run on (NULL: legacy default stream).
- * The per-CTA partial sums live in one statically allocated device array of
+ * It runs the kernels hobc_gcv runs, with the same chunking, so its results
+ * equal hobc_gcv's bit for bit.  The per-CTA partial sums and the grid's
+ * working-precision copy live in one statically allocated device array of
  * hobc_gcv_noalloc_max_bytes() bytes (16 MiB) that every GPU loading the
- * library holds until the process exits.  A request that needs more --
+ * library holds until the process exits (1D problems with K <= 256 in FP32,
+ * K <= 128 in FP64 need only the grid there: one thread group sums each
+ * problem's whole spectrum).  A request that needs more --
  * batch * ceil(spectrum/chunk) * 2 * K doubles plus the grid -- is rejected
  * with HOBC_ERR_SIZE and a message in hobc_last_error().  The first call on
  * each device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.
+ * that device current, and keeps it with the id of the device's context; the
+ * first call after that context was destroyed (cudaDeviceReset) looks it up
+ * again in the new one.  Make such a first call before any stream capture.
+ * The description is checked as hobc_plan_create checks it (psf ignored);
+ * HOBC_SPLIT_BF16 and the REFLECTIVE / PERIODIC families are rejected
+ * (HOBC_ERR_UNSUPPORTED): their spectra come from the dense engine.
  * All calls share the one array and it keeps the last call's contents; every
  * entry a call reads is written earlier in the same call, so nothing needs
  * clearing, but calls whose work overlaps on the GPU (different streams, or

@@ -439,6 +439,61 @@ void free_axis(AxisHost& a) {
     memset(&a, 0, sizeof(a));
 }
 
+// Checks the parts of a plan description that fix the geometry, the family and
+// the precision, and resolves HOBC_FAMILY_AUTO.  check_psf: the PSF extents are
+// part of the request (plans) or ignored (the allocation-free scan).
+hobc_status resolve_desc(const hobc_plan_desc& d, bool check_psf, int* fam_out) {
+    if (d.ndim != 1 && d.ndim != 2) return HOBC_ERR_ARG;
+    if (d.n_mu < 1 || d.batch < 1) return HOBC_ERR_ARG;
+    if (d.ndim == 2 && d.batch > 65535) return HOBC_ERR_SIZE;     // items ride on gridDim.y
+    if (d.prec != HOBC_FP64 && d.prec != HOBC_FP32 && d.prec != HOBC_SPLIT_BF16) return HOBC_ERR_ARG;
+    if (d.L != HOBC_L_IDENTITY && d.L != HOBC_L_LAPLACIAN) return HOBC_ERR_ARG;
+    if (d.psf_per_item != 0 && d.psf_per_item != 1) return HOBC_ERR_ARG;
+    for (int i = 0; i < d.ndim; ++i) {
+        if (d.n[i] < 6 || d.n[i] > 1024) return HOBC_ERR_SIZE;
+        if (!check_psf) continue;
+        if (d.psf[i] < 1 || d.psf[i] % 2 == 0 || d.psf[i] > 63) return HOBC_ERR_SIZE;
+        if (d.psf[i] > d.n[i] - 2) return HOBC_ERR_SIZE;       // 2m+1 <= n-2
+    }
+    const bool cubic = d.family == HOBC_FAMILY_SINE_CUBIC || d.family == HOBC_FAMILY_COSINE_QUARTIC ||
+                       (d.family == HOBC_FAMILY_AUTO && (d.bc_degree == 3 || d.bc_degree == 4));
+    if (cubic)
+        for (int i = 0; i < d.ndim; ++i) {
+            if (d.n[i] < 8) return HOBC_ERR_SIZE;                               // N = n-4 >= 4
+            if (check_psf && d.psf[i] > d.n[i] - 4) return HOBC_ERR_SIZE;      // 2m+1 <= n-4
+        }
+    int fam = d.family;
+    const bool comparison = fam == HOBC_FAMILY_REFLECTIVE || fam == HOBC_FAMILY_PERIODIC;
+    if (comparison) {
+        // classical conditions (Sec. 2): constants preserved, symmetric PSF, dense mode only
+        if (d.bc_degree != 0 || !d.psf_symmetric || d.prec != HOBC_SPLIT_BF16) return HOBC_ERR_UNSUPPORTED;
+    } else {
+        if (d.bc_degree < 1 || d.bc_degree > 4) return HOBC_ERR_UNSUPPORTED;
+        if (fam == HOBC_FAMILY_AUTO) {
+            if (d.bc_degree == 1) fam = d.psf_symmetric ? HOBC_FAMILY_SINE : -1;
+            else if (d.bc_degree == 2) fam = d.psf_symmetric ? HOBC_FAMILY_COSINE : HOBC_FAMILY_FOURIER;
+            else if (d.bc_degree == 3) fam = d.psf_symmetric ? HOBC_FAMILY_SINE_CUBIC : -1;
+            else fam = d.psf_symmetric ? HOBC_FAMILY_COSINE_QUARTIC : -1;
+            if (fam < 0) return HOBC_ERR_UNSUPPORTED;   // sine families need a symmetric PSF (Sec. 2.2)
+        }
+        if (fam == HOBC_FAMILY_SINE && d.bc_degree != 1) return HOBC_ERR_UNSUPPORTED;
+        if ((fam == HOBC_FAMILY_COSINE || fam == HOBC_FAMILY_FOURIER) && d.bc_degree != 2)
+            return HOBC_ERR_UNSUPPORTED;
+        if (fam == HOBC_FAMILY_SINE_CUBIC && d.bc_degree != 3) return HOBC_ERR_UNSUPPORTED;
+        if (fam == HOBC_FAMILY_COSINE_QUARTIC && (d.bc_degree != 4 || !d.psf_symmetric))
+            return HOBC_ERR_UNSUPPORTED;
+        if (fam != HOBC_FAMILY_COSINE_QUARTIC && (fam < HOBC_FAMILY_SINE || fam > HOBC_FAMILY_SINE_CUBIC))
+            return HOBC_ERR_ARG;
+    }
+    if (d.prec == HOBC_SPLIT_BF16 && fam == HOBC_FAMILY_FOURIER) return HOBC_ERR_UNSUPPORTED;   // complex T_F
+    // degree 4 runs on the FFT path only (the dense engine has no matrices for it), and in
+    // FP64 only: cond(T) is 644 already at n = 8 (7.5e4 at n = 32), so the FP32 rounding
+    // bound 64 eps32 cond(T) exceeds 1e-3 at every size
+    if (fam == HOBC_FAMILY_COSINE_QUARTIC && d.prec != HOBC_FP64) return HOBC_ERR_UNSUPPORTED;
+    *fam_out = fam;
+    return HOBC_OK;
+}
+
 }  // namespace hobc
 
 using namespace hobc;
@@ -494,52 +549,15 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
     *out = nullptr;
     if (!desc || !mu_grid_host) return HOBC_ERR_ARG;
     const hobc_plan_desc d = *desc;
-    if (d.ndim != 1 && d.ndim != 2) return HOBC_ERR_ARG;
-    if (d.n_mu < 1 || d.batch < 1) return HOBC_ERR_ARG;
-    if (d.ndim == 2 && d.batch > 65535) return HOBC_ERR_SIZE;     // items ride on gridDim.y
-    if (d.prec != HOBC_FP64 && d.prec != HOBC_FP32 && d.prec != HOBC_SPLIT_BF16) return HOBC_ERR_ARG;
-    if (d.L != HOBC_L_IDENTITY && d.L != HOBC_L_LAPLACIAN) return HOBC_ERR_ARG;
-    if (d.psf_per_item != 0 && d.psf_per_item != 1) return HOBC_ERR_ARG;
-    for (int i = 0; i < d.ndim; ++i) {
-        if (d.n[i] < 6 || d.n[i] > 1024) return HOBC_ERR_SIZE;
-        if (d.psf[i] < 1 || d.psf[i] % 2 == 0 || d.psf[i] > 63) return HOBC_ERR_SIZE;
-        if (d.psf[i] > d.n[i] - 2) return HOBC_ERR_SIZE;       // 2m+1 <= n-2
-    }
-    const bool cubic = d.family == HOBC_FAMILY_SINE_CUBIC || d.family == HOBC_FAMILY_COSINE_QUARTIC ||
-                       (d.family == HOBC_FAMILY_AUTO && (d.bc_degree == 3 || d.bc_degree == 4));
-    if (cubic)
-        for (int i = 0; i < d.ndim; ++i)
-            if (d.n[i] < 8 || d.psf[i] > d.n[i] - 4) return HOBC_ERR_SIZE;   // 2m+1 <= n-4
+    int fam = 0;
+    const hobc_status vs = resolve_desc(d, true, &fam);
+    if (vs != HOBC_OK) return vs;
     for (int j = 0; j < d.n_mu; ++j) {
         if (!std::isfinite(mu_grid_host[j])) return HOBC_ERR_NONFINITE;
         if (!(mu_grid_host[j] > 0)) return HOBC_ERR_ARG;
         // FP32 GCV pairs grid values: (a + mu1)(a + mu2) must stay a normal float
         if (d.prec != HOBC_FP64 && (mu_grid_host[j] < 1e-18 || mu_grid_host[j] > 1e18)) return HOBC_ERR_ARG;
     }
-    int fam = d.family;
-    const bool comparison = fam == HOBC_FAMILY_REFLECTIVE || fam == HOBC_FAMILY_PERIODIC;
-    if (comparison) {
-        // classical conditions (Sec. 2): constants preserved, symmetric PSF, dense mode only
-        if (d.bc_degree != 0 || !d.psf_symmetric || d.prec != HOBC_SPLIT_BF16) return HOBC_ERR_UNSUPPORTED;
-    } else {
-    if (d.bc_degree < 1 || d.bc_degree > 4) return HOBC_ERR_UNSUPPORTED;
-    if (fam == HOBC_FAMILY_AUTO) {
-        if (d.bc_degree == 1) fam = d.psf_symmetric ? HOBC_FAMILY_SINE : -1;
-        else if (d.bc_degree == 2) fam = d.psf_symmetric ? HOBC_FAMILY_COSINE : HOBC_FAMILY_FOURIER;
-        else if (d.bc_degree == 3) fam = d.psf_symmetric ? HOBC_FAMILY_SINE_CUBIC : -1;
-        else fam = d.psf_symmetric ? HOBC_FAMILY_COSINE_QUARTIC : -1;
-        if (fam < 0) return HOBC_ERR_UNSUPPORTED;   // sine families need a symmetric PSF (Sec. 2.2)
-    }
-    if (fam == HOBC_FAMILY_SINE && d.bc_degree != 1) return HOBC_ERR_UNSUPPORTED;
-    if ((fam == HOBC_FAMILY_COSINE || fam == HOBC_FAMILY_FOURIER) && d.bc_degree != 2) return HOBC_ERR_UNSUPPORTED;
-    if (fam == HOBC_FAMILY_SINE_CUBIC && d.bc_degree != 3) return HOBC_ERR_UNSUPPORTED;
-    if (fam == HOBC_FAMILY_COSINE_QUARTIC && (d.bc_degree != 4 || !d.psf_symmetric)) return HOBC_ERR_UNSUPPORTED;
-    if (fam != HOBC_FAMILY_COSINE_QUARTIC && (fam < HOBC_FAMILY_SINE || fam > HOBC_FAMILY_SINE_CUBIC))
-        return HOBC_ERR_ARG;
-    }
-    if (d.prec == HOBC_SPLIT_BF16 && fam == HOBC_FAMILY_FOURIER) return HOBC_ERR_UNSUPPORTED;   // complex T_F
-    // degree 4 runs on the FFT path only (the dense engine has no matrices for it)
-    if (d.prec == HOBC_SPLIT_BF16 && fam == HOBC_FAMILY_COSINE_QUARTIC) return HOBC_ERR_UNSUPPORTED;
 
     hobc_plan_s* p = new hobc_plan_s;
     memset(p, 0, sizeof(*p));

@@ -149,6 +149,9 @@ template <typename T> hobc_status run3_gcv(hobc_volume_s* q, const void* ghat, c
 // index t of a family's axis as the fraction num / den (hobc_api.cu)
 std::complex<double> expm_ipi(long long a, long long b);
 void theta_frac(int fam, int n, int t, long long& num, long long& den);
+// Checks a plan description (geometry, family, precision; the PSF extents too if
+// check_psf) and resolves HOBC_FAMILY_AUTO into *fam (hobc_api.cu).
+hobc_status resolve_desc(const hobc_plan_desc& d, bool check_psf, int* fam);
 void set_last_error(const char* what, cudaError_t e);
 void set_last_error_text(const char* text);
 hobc_status launch_gcv_finalize(hobc_plan_s* p, double* gcv, int* mu_idx);

@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "hobc_internal.h"
 #include "hobc_kernels.cuh"
 
@@ -18,25 +20,78 @@ static __device__ __align__(256) unsigned char g_gcv_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {};   // device address of g_gcv_scratch, per device
+void* g_scratch_addr[kMaxDevices] = {};               // device address of g_gcv_scratch, per device ...
+unsigned long long g_scratch_ctx_id[kMaxDevices] = {};  // ... in the context with this unique id
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Driver entry points for the current context and its process-unique id, looked up once.
+hobc_status driver_entry_points() {
+    static cudaError_t lookup = cudaErrorUnknown;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        void* g = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        lookup = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1);
+        if (lookup == cudaSuccess)
+            lookup = cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2);
+        if (lookup == cudaSuccess &&
+            (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f || !g))
+            lookup = cudaErrorSymbolNotFound;
+        g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(g);
+    });
+    if (lookup != cudaSuccess) {
+        hobc::set_last_error("hobc_gcv_noalloc: driver entry points", lookup);
+        return HOBC_ERR_CUDA;
+    }
+    return HOBC_OK;
+}
+
+// Unique id of the context current on this thread; false if none is current or
+// it has been destroyed.
+bool current_context_id(unsigned long long* id) {
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return g_ctx_get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 // Device address of the scratch array on the current device.  In host code the
-// array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and kept.
+// array's name is only a host-side stand-in, so the address is looked up with
+// the device current (cudaGetSymbolAddress, once per device) and kept.  The
+// address belongs to the module loaded in the device's context; a device reset
+// destroys that context and the next runtime call creates a new one in which the
+// module has a new address.  So the address is kept together with the unique id
+// of the context it was taken in, and looked up again when the current context
+// has another id (or none yet: the lookup itself makes the runtime set it up).
 hobc_status scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) { hobc::set_last_error("hobc_gcv_noalloc: cudaGetDevice", e); return HOBC_ERR_CUDA; }
     if (dev < 0 || dev >= kMaxDevices) return HOBC_ERR_UNSUPPORTED;
+    hobc_status s = driver_entry_points();
+    if (s != HOBC_OK) return s;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    unsigned long long id = 0;
+    const bool have = current_context_id(&id);
+    if (!have || !g_scratch_addr[dev] || id != g_scratch_ctx_id[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_gcv_scratch);
         if (e != cudaSuccess) {
             hobc::set_last_error("hobc_gcv_noalloc: cudaGetSymbolAddress", e);
             return HOBC_ERR_CUDA;
         }
+        if (!current_context_id(&id)) {
+            hobc::set_last_error_text("hobc_gcv_noalloc: no current context after the symbol lookup");
+            return HOBC_ERR_CUDA;
+        }
         g_scratch_addr[dev] = p;
+        g_scratch_ctx_id[dev] = id;
     }
     *out = g_scratch_addr[dev];
     return HOBC_OK;
@@ -55,6 +110,33 @@ hobc_status launch(const hobc::GcvGeom& geo, int cplx, int batch, int chunks, co
     T* muT = reinterpret_cast<T*>(scratch);
     double* partials = reinterpret_cast<double*>(scratch + mu_bytes);
     k_mu_to_working<T><<<(geo.K + 255) / 256, 256, 0, st>>>(mu, muT, geo.K);
+    if (geo.ndim == 1) {
+        // as hobc_gcv does for 1D plans: one thread group per problem sums its whole
+        // spectrum, so the scan needs no partial sums (only the grid in scratch)
+        const int per = sizeof(T) == 4 ? 8 : 4;
+        int tpi = 1;
+        while (tpi * per < geo.K) tpi *= 2;
+        if (tpi <= 32) {
+            const unsigned grid = (unsigned)((batch + 256 / tpi - 1) / (256 / tpi));
+#define HOBC_NOALLOC_ITEMS(TPI_)                                                                             \
+    if (tpi == TPI_) {                                                                                       \
+        if (cplx)                                                                                            \
+            k_gcv_items<T, true, TPI_><<<grid, 256, 0, st>>>(reinterpret_cast<const C2<T>*>(ghat),          \
+                                                             reinterpret_cast<const C2<T>*>(d), d_psf_stride, \
+                                                             psf_per, muT, geo, batch, gcv, mu_idx);         \
+        else                                                                                                 \
+            k_gcv_items<T, false, TPI_><<<grid, 256, 0, st>>>(reinterpret_cast<const T*>(ghat),             \
+                                                              reinterpret_cast<const T*>(d), d_psf_stride,   \
+                                                              psf_per, muT, geo, batch, gcv, mu_idx);        \
+    }
+            HOBC_NOALLOC_ITEMS(1) HOBC_NOALLOC_ITEMS(2) HOBC_NOALLOC_ITEMS(4) HOBC_NOALLOC_ITEMS(8)
+            HOBC_NOALLOC_ITEMS(16) HOBC_NOALLOC_ITEMS(32)
+#undef HOBC_NOALLOC_ITEMS
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) { set_last_error("hobc_gcv_noalloc launch", e); return HOBC_ERR_CUDA; }
+            return HOBC_OK;
+        }
+    }
     const dim3 grid((unsigned)((long long)chunks * batch));
     const size_t smem = 4 * (size_t)geo.chunk * sizeof(T);
     if (cplx)
@@ -80,24 +162,11 @@ extern "C" hobc_status hobc_gcv_noalloc(const hobc_plan_desc* desc, const void* 
                                         void* cuda_stream) {
     if (!desc || !ghat_dev || !d_dev || !mu_dev || !mu_index_dev) return HOBC_ERR_ARG;
     const hobc_plan_desc& dsc = *desc;
-    if (dsc.ndim != 1 && dsc.ndim != 2) return HOBC_ERR_ARG;
-    if (dsc.n_mu < 1 || dsc.batch < 1) return HOBC_ERR_ARG;
-    if (dsc.prec != HOBC_FP64 && dsc.prec != HOBC_FP32) return HOBC_ERR_ARG;
-    if (dsc.L != HOBC_L_IDENTITY && dsc.L != HOBC_L_LAPLACIAN) return HOBC_ERR_ARG;
-    if (dsc.psf_per_item != 0 && dsc.psf_per_item != 1) return HOBC_ERR_ARG;
-    for (int i = 0; i < dsc.ndim; ++i)
-        if (dsc.n[i] < 6 || dsc.n[i] > 1024) return HOBC_ERR_SIZE;
-    int fam = dsc.family;
-    if (fam == HOBC_FAMILY_AUTO) {
-        if (dsc.bc_degree == 1) fam = dsc.psf_symmetric ? HOBC_FAMILY_SINE : -1;
-        else if (dsc.bc_degree == 2) fam = dsc.psf_symmetric ? HOBC_FAMILY_COSINE : HOBC_FAMILY_FOURIER;
-        else if (dsc.bc_degree == 3) fam = dsc.psf_symmetric ? HOBC_FAMILY_SINE_CUBIC : -1;
-        else if (dsc.bc_degree == 4) fam = dsc.psf_symmetric ? HOBC_FAMILY_COSINE_QUARTIC : -1;
-        else fam = -1;
-        if (fam < 0) return HOBC_ERR_UNSUPPORTED;
-    }
-    if (fam != HOBC_FAMILY_COSINE_QUARTIC && (fam < HOBC_FAMILY_SINE || fam > HOBC_FAMILY_SINE_CUBIC))
-        return HOBC_ERR_ARG;
+    // the same checks as hobc_plan_create (the PSF extents are not part of the request)
+    int fam = 0;
+    const hobc_status vs = hobc::resolve_desc(dsc, false, &fam);
+    if (vs != HOBC_OK) return vs;
+    if (dsc.prec != HOBC_FP64 && dsc.prec != HOBC_FP32) return HOBC_ERR_UNSUPPORTED;   // FFT-path spectra only
     const bool two_borders = fam == HOBC_FAMILY_SINE_CUBIC || fam == HOBC_FAMILY_COSINE_QUARTIC;
 
     // geometry of the stored spectrum (include/hobc.h, "Spectrum layout")
@@ -109,7 +178,13 @@ extern "C" hobc_status hobc_gcv_noalloc(const hobc_plan_desc* desc, const void* 
     const long long chunks = (S + chunk - 1) / chunk;
     const size_t esz = dsc.prec == HOBC_FP64 ? 8 : 4;
     const size_t mu_bytes = ((size_t)dsc.n_mu * esz + 255) / 256 * 256;
-    const double need = (double)mu_bytes + (double)dsc.batch * (double)chunks * 2.0 * dsc.n_mu * sizeof(double);
+    // 1D problems run as hobc_gcv runs them (one thread group per problem, no
+    // partial sums) when a group of at most 32 threads covers the grid
+    int tpi = 1;
+    while (tpi * (dsc.prec == HOBC_FP64 ? 4 : 8) < dsc.n_mu) tpi *= 2;
+    const bool items_path = dsc.ndim == 1 && tpi <= 32;
+    const double need = (double)mu_bytes +
+                        (items_path ? 0.0 : (double)dsc.batch * (double)chunks * 2.0 * dsc.n_mu * sizeof(double));
     if (need > (double)kScratchBytes) {
         char msg[256];
         snprintf(msg, sizeof(msg),

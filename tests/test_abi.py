@@ -124,3 +124,39 @@ def test_learned_entry_points_reject_bad_arguments_on_the_host(hobc):
     lib.hobc_volume_destroy(None)
     assert lib.hobc_deblur_exact(None, None, None, None, None, None) == arg
     lib.hobc_mlp_destroy(None)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(n=5), dict(n=2048), dict(bc_degree=5), dict(bc_degree=4, psf_symmetric=False),
+    dict(family="cosine4", bc_degree=2), dict(bc_degree=3, psf_symmetric=False),
+    dict(family="sine3", bc_degree=2), dict(bc_degree=1, psf_symmetric=False),
+    dict(family="sine", bc_degree=2), dict(family="fourier", bc_degree=1), dict(batch=0),
+    dict(ndim=3), dict(family="sine3", bc_degree=3, n=7, psf=1), dict(family="cosine4", bc_degree=4, n=6, psf=1),
+    dict(bc_degree=3, n=7, psf=1), dict(bc_degree=4, n=7, psf=1),
+    dict(bc_degree=4, prec="fp32", n=16, psf=3),                   # degree 4 is FP64 only
+    dict(family="periodic", bc_degree=0, prec="fp64"),             # comparison families: dense engine only
+])
+def test_noalloc_rejects_what_plan_create_rejects(hobc, kw):
+    """hobc_gcv_noalloc checks a description as hobc_plan_create does (the PSF
+    extents aside), so no geometry that a plan refuses runs there."""
+    with pytest.raises(hobc.HobcError) as ei:
+        _create(hobc, **kw)
+    args = dict(ndim=1, n=64, bc_degree=2, psf_symmetric=True)
+    args.update({k: v for k, v in kw.items() if k != "psf"})
+    ndim = args.pop("ndim")
+    n = args.pop("n")
+    deg = args.pop("bc_degree")
+    desc = hobc.make_desc(ndim, n, deg, 2, **args)
+    lib = hobc.library()
+    got = lib.hobc_gcv_noalloc(ctypes.byref(desc), ctypes.c_void_p(256), ctypes.c_void_p(256),
+                               ctypes.c_void_p(256), None, ctypes.c_void_p(256), None)
+    assert got == ei.value.status, (kw, hobc.STATUS[got], hobc.STATUS[ei.value.status])
+
+
+def test_fp32_degree4_rejected(hobc):
+    """Degree 4 is offered in FP64 only: its cond(T) is 644 at the smallest field of
+    view (n = 8), so the FP32 rounding bound 64 eps32 cond(T) is above 1e-3 at every size."""
+    for n in (8, 12, 64):
+        with pytest.raises(hobc.HobcError) as ei:
+            _create(hobc, n=n, psf=3, bc_degree=4, prec="fp32")
+        assert hobc.STATUS[ei.value.status] == "HOBC_ERR_UNSUPPORTED"

@@ -54,7 +54,7 @@ def _cond(shape):
 CASES = [(1, (13,), 5), (1, (40,), 7), (2, (12, 15), (5, 3)), (2, (20, 17), (5, 5))]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64"])
 @pytest.mark.parametrize("L", ["I", "lap"])
 @pytest.mark.parametrize("ndim,n,taps", CASES)
 def test_degree4_steps_and_whole_path(ndim, n, taps, L, prec):
@@ -151,11 +151,10 @@ def test_degree4_steps_and_whole_path(ndim, n, taps, L, prec):
             assert G_o[k] <= (1 + 1e-6) * G_o.min(), f"whole-path argmin {k} vs {k_o}"
 
 
-@pytest.mark.parametrize("ndim,prec,n", [(1, "fp64", (14,)), (2, "fp64", (12, 13)), (1, "fp32", (10,))])
+@pytest.mark.parametrize("ndim,prec,n", [(1, "fp64", (14,)), (2, "fp64", (12, 13))])
 def test_quartics_come_back_unchanged(ndim, prec, n):
     """A sampled quartic is preserved by A_X and annihilated by the Laplacian, so the
-    reblurred Tikhonov solution with L = Laplacian returns it for every mu (FP32 only
-    where cond(T) leaves the check some teeth)."""
+    reblurred Tikhonov solution with L = Laplacian returns it for every mu."""
     dt, tdt = _dt(prec)
     taps = 5 if ndim == 1 else (5, 5)
     h = P.psf_for("C", ndim, taps)
@@ -176,7 +175,7 @@ def test_quartics_come_back_unchanged(ndim, prec, n):
     assert err <= max(TOL[prec], 64 * EPS[prec] * _cond(n)), err
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64"])
 def test_delta_psf_closed_form(prec):
     """h = delta: d = 1, so G is the same for every mu (to rounding) and f = g/(1+mu*)
     at whichever grid value is chosen."""
@@ -198,8 +197,14 @@ def test_delta_psf_closed_form(prec):
 
 
 def test_degree4_outside_the_plain_path_is_rejected():
-    """Degree 4 needs a symmetric PSF; the dense engine and 3D plans reject it."""
+    """Degree 4 needs a symmetric PSF and FP64 (cond(T) >= 644 puts the FP32 rounding
+    bound 64 eps32 cond(T) above 1e-3 at every size); the dense engine and 3D plans
+    reject it."""
     mus = synth.mu_grid(4)
+    for n in ((8,), (12, 15), (40,)):
+        with pytest.raises(hobc.HobcError) as e:
+            hobc.Plan(len(n), n, (3,) * len(n), 4, mus, prec="fp32", family="cosine4", psf_symmetric=True)
+        assert e.value.status == 2
     with pytest.raises(hobc.HobcError) as e:
         hobc.Plan(2, (16, 16), (5, 5), 4, mus, prec="fp32", family="auto", psf_symmetric=False)
     assert e.value.status == 2

@@ -2,6 +2,9 @@
 memory (their process runs under an allocator they do not own, or a fixed
 device-memory budget, or a path that cannot take cudaMalloc's synchronisation)
 -- must give the answer of hobc_gcv, the plan-based call, on the same spectra.
+Both run the same kernels with the same chunking, so the answer must be the
+same bit for bit; one case also checks it against the oracle on identical
+inputs (the oracle's spectra rounded to the working precision).
 
 Its scratch is one static device array shared by every call and never
 cleared, so each case runs the allocation-free call twice in a row, and one
@@ -11,6 +14,8 @@ every other test.  It also passes alone, in a fresh process.
 """
 import numpy as np
 import pytest
+
+from oracle import hobc_oracle as O
 
 from paper_0906_2704_gb300 import synth
 import parity_utils as P
@@ -61,8 +66,7 @@ def _noalloc(case):
 def _check(case, got, prec):
     G_ref, mi_ref = case[4], case[5]
     G, mi = got
-    rel = ((G - G_ref).abs() / G_ref.abs()).max().item()
-    assert rel <= TOL[prec], f"G differs from hobc_gcv by {rel:.3e}"
+    assert torch.equal(G, G_ref), f"G differs from hobc_gcv by {((G - G_ref).abs() / G_ref.abs()).max().item():.3e}"
     assert torch.equal(mi, mi_ref)
 
 
@@ -96,3 +100,55 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
         hobc.gcv_noalloc(desc, 16, 16, 16, None, 16)   # rejected before any device access
     assert hobc.STATUS[ei.value.status] == "HOBC_ERR_SIZE"
     assert "maximum" in str(ei.value)
+
+
+@pytest.mark.parametrize("ndim,n,fam,L,prec", [
+    (2, (34, 21), "fourier", "lap", "fp32"),
+    (1, 90, "sine3", "I", "fp64"),
+])
+def test_noalloc_against_the_oracle(ndim, n, fam, L, prec):
+    """G of the allocation-free scan against the oracle's Eq. (eq:gcv2) on identical
+    inputs: the oracle's spectrum and eigenvalues, rounded to the working precision,
+    go to the GPU, and the oracle evaluates G on the same rounded values."""
+    letter = P.FAM_LETTER[fam]
+    dt = np.float64 if prec == "fp64" else np.float32
+    shape = (n,) if ndim == 1 else n
+    taps = 5 if ndim == 1 else (5, 5)
+    h = P.psf_for(letter, ndim, taps)
+    batch, K = 3, 40
+    g, _ = P.problems(ndim, shape, h, batch, seed=11)
+    mus = synth.mu_grid(K, 1e-7, 1.0)
+    deg = {"S": 1, "C": 2, "F": 2, "S3": 3}[letter]
+    orc = [P.oracle_steps(letter, ndim, h, g[b], L, mus) for b in range(batch)]
+
+    cplx = letter == "F"          # the other families keep real spectra (the symbol's
+                                  # imaginary rounding residue of a symmetric PSF is dropped)
+
+    def rounded(full):
+        re = full.real.astype(dt).astype(np.float64)
+        return re + 1j * full.imag.astype(dt).astype(np.float64) if cplx else re
+
+    def stored(full):
+        lay = P.to_layout(letter, full).reshape(-1)
+        if cplx:
+            return np.stack([lay.real, lay.imag], axis=-1).astype(dt)
+        return lay.real.astype(dt)
+
+    gh_full = [rounded(o[0]) for o in orc]
+    d_full = rounded(orc[0][1])
+    gh = torch.from_numpy(np.stack([stored(x) for x in gh_full])).cuda()
+    d = torch.from_numpy(stored(d_full)[None]).cuda()
+    desc = hobc.make_desc(ndim, shape, deg, K, L=L, prec=prec, family=fam, psf_symmetric=letter != "F",
+                          batch=batch)
+    G = torch.empty((batch, K), dtype=torch.float64, device="cuda")
+    mi = torch.empty(batch, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        hobc.gcv_noalloc(desc, gh, d, torch.from_numpy(mus).cuda(), G, mi)
+        torch.cuda.synchronize()
+        Gn, min_ = G.cpu().numpy(), mi.cpu().numpy()
+        for b in range(batch):
+            Gref = O.gcv_curve(gh_full[b], d_full, orc[b][2], mus)
+            rel = np.max(np.abs(Gn[b] - Gref) / np.abs(Gref))
+            assert rel <= TOL[prec], f"item {b}: G differs from the oracle by {rel:.3e}"
+            k = int(min_[b])
+            assert k == O.gcv_argmin(Gref) or Gref[k] <= (1 + TOL[prec]) * Gref.min()
