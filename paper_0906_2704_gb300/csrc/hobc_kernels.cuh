@@ -619,8 +619,9 @@ template <typename T> __device__ __forceinline__ T a_cap() { return sizeof(T) ==
 // elements and combine their sums with shuffles.
 
 // Elements per CTA of the GCV scan.  In FP32 every thread sums its share of
-// the chunk in float and converts to double once, so a chunk holds at most
-// 256 elements per thread of a grid-value group; FP64 sums in double.
+// the chunk in float (blocked, see gcv_scan) and converts to double once, so a
+// chunk holds at most 256 elements per thread of a grid-value group; FP64 sums
+// in double.
 __host__ __device__ inline int gcv_threads_per_group(int K, bool fp64) {
     const int per = fp64 ? 4 : 8;            // grid values per thread
     const int groups = (K + per - 1) / per;
@@ -671,15 +672,60 @@ __device__ __forceinline__ void gcv_scan(const double4* __restrict__ pk, int cnt
     }
 }
 
+// One packed entry v = (a, e, w) evaluated at the eight grid values of mA / mB
+// (lanes as in gcv_scan below), added to the packed sums.
+__device__ __forceinline__ void eval_group(const float4 v, const float2 (&mA)[2], const float2 (&mB)[2],
+                                           float2 (&NA)[2], float2 (&NB)[2], float2 (&DA)[2], float2 (&DB)[2]) {
+    const float2 aa = make_float2(v.x, v.x), ee = make_float2(v.y, v.y), ww = make_float2(v.z, v.z);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float2 A = __fadd2_rn(aa, mA[h]);
+        const float2 B = __fadd2_rn(aa, mB[h]);
+        const float2 P = __fmul2_rn(A, B);
+        const float2 R = make_float2(pair_rcp(P.x), pair_rcp(P.y));
+        const float2 SA = __fmul2_rn(B, R);
+        const float2 SB = __fmul2_rn(A, R);
+        DA[h] = __ffma2_rn(ww, SA, DA[h]);
+        DB[h] = __ffma2_rn(ww, SB, DB[h]);
+        NA[h] = __ffma2_rn(__fmul2_rn(ee, SA), SA, NA[h]);
+        NB[h] = __ffma2_rn(__fmul2_rn(ee, SB), SB, NB[h]);
+    }
+}
+
+// As eval_group, for the first entry of a block: sets the sums instead of adding.
+__device__ __forceinline__ void eval_group_first(const float4 v, const float2 (&mA)[2], const float2 (&mB)[2],
+                                                 float2 (&NA)[2], float2 (&NB)[2], float2 (&DA)[2],
+                                                 float2 (&DB)[2]) {
+    const float2 aa = make_float2(v.x, v.x), ee = make_float2(v.y, v.y), ww = make_float2(v.z, v.z);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float2 A = __fadd2_rn(aa, mA[h]);
+        const float2 B = __fadd2_rn(aa, mB[h]);
+        const float2 P = __fmul2_rn(A, B);
+        const float2 R = make_float2(pair_rcp(P.x), pair_rcp(P.y));
+        const float2 SA = __fmul2_rn(B, R);
+        const float2 SB = __fmul2_rn(A, R);
+        DA[h] = __fmul2_rn(ww, SA);
+        DB[h] = __fmul2_rn(ww, SB);
+        NA[h] = __fmul2_rn(__fmul2_rn(ee, SA), SA);
+        NB[h] = __fmul2_rn(__fmul2_rn(ee, SB), SB);
+    }
+}
+
 // FP32: eight grid values per thread in packed f32x2 lanes.  Lanes hold
 // (mu0, mu2) / (mu1, mu3) and (mu4, mu6) / (mu5, mu7), so one packed product
 // forms both shared denominators of a pair of pairs and each packed op
-// advances two evaluations; one rcp.approx per two evaluations.  A thread's
-// terms (at most 256 elements, see gcv_chunk_for) are summed in float and the
-// tpm threads of a group (at most 32) combined in float by a shuffle tree, at
-// most 256 + 5 roundings per sum; each grid value's CTA sum is then converted
-// to double once (FP64 runs at a small fraction of the FP32 rate on this part,
-// so the combine stays off the FP64 pipe).
+// advances two evaluations; one rcp.approx per two evaluations.
+// Summation: a thread's terms (at most 256 elements, see gcv_chunk_for) go to
+// float accumulators of at most GCV_BLOCK elements each, which are added to a
+// second float accumulator; the tpm threads of a group (at most 32) are then
+// combined in float by a shuffle tree and each grid value's CTA sum is
+// converted to double once.  Every term is non-negative, so the relative error
+// of a sum is at most (depth of its summation tree) x u: 15 + 16 + 5 = 36
+// roundings, 2.2e-6, against 256 + 5 for one float accumulator.  FP64
+// accumulators would cost two FP64 adds per term (FP64 runs at about 1/64 of
+// the FP32 rate on this part) for no gain beyond that bound.
+constexpr int GCV_BLOCK = 16;
 __device__ __forceinline__ void gcv_scan(const float4* __restrict__ pk, int cnt, const float* __restrict__ muT,
                                          int K, double* __restrict__ outp) {
     const int NO = (K + 7) / 8;
@@ -695,22 +741,23 @@ __device__ __forceinline__ void gcv_scan(const float4* __restrict__ pk, int cnt,
         const float2 mB[2] = {make_float2(mu[1], mu[3]), make_float2(mu[5], mu[7])};
         const float2 z = make_float2(0.f, 0.f);
         float2 NA[2] = {z, z}, NB[2] = {z, z}, DA[2] = {z, z}, DB[2] = {z, z};
-#pragma unroll 4
-        for (int i = sub; i < cnt; i += tpm) {
-            const float4 v = pk[i];
-            const float2 aa = make_float2(v.x, v.x), ee = make_float2(v.y, v.y), ww = make_float2(v.z, v.z);
+        for (int i0 = sub; i0 < cnt; i0 += GCV_BLOCK * tpm) {
+            float2 nA[2], nB[2], dA[2], dB[2];
+            if (i0 + (GCV_BLOCK - 1) * tpm < cnt) {         // a full block
+                eval_group_first(pk[i0], mA, mB, nA, nB, dA, dB);
+#pragma unroll
+                for (int r = 1; r < GCV_BLOCK; ++r) eval_group(pk[i0 + r * tpm], mA, mB, nA, nB, dA, dB);
+            } else {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) { nA[h] = z; nB[h] = z; dA[h] = z; dB[h] = z; }
+                for (int i = i0; i < cnt; i += tpm) eval_group(pk[i], mA, mB, nA, nB, dA, dB);
+            }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const float2 A = __fadd2_rn(aa, mA[h]);
-                const float2 B = __fadd2_rn(aa, mB[h]);
-                const float2 P = __fmul2_rn(A, B);
-                const float2 R = make_float2(pair_rcp(P.x), pair_rcp(P.y));
-                const float2 SA = __fmul2_rn(B, R);      // sigma of the A lanes
-                const float2 SB = __fmul2_rn(A, R);      // sigma of the B lanes
-                DA[h] = __ffma2_rn(ww, SA, DA[h]);
-                DB[h] = __ffma2_rn(ww, SB, DB[h]);
-                NA[h] = __ffma2_rn(__fmul2_rn(ee, SA), SA, NA[h]);
-                NB[h] = __ffma2_rn(__fmul2_rn(ee, SB), SB, NB[h]);
+                NA[h] = __fadd2_rn(NA[h], nA[h]);
+                NB[h] = __fadd2_rn(NB[h], nB[h]);
+                DA[h] = __fadd2_rn(DA[h], dA[h]);
+                DB[h] = __fadd2_rn(DB[h], dB[h]);
             }
         }
         float nf[8], df[8];
@@ -800,7 +847,7 @@ __device__ __forceinline__ void gcv_partials_body(const typename ElemT<T, CPLX>:
 }
 
 template <typename T, bool CPLX>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_gcv_partials(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
                long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo,
                double* __restrict__ partials) {
@@ -819,27 +866,11 @@ k_gcv_partials(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typena
 // the problem's entries pass through shared memory in tiles (32 KB per CTA), every
 // thread sweeps all of them for its values, so the sums need no cross-thread
 // reduction: G(mu_j) = num/den^2 and the first minimiser (NaN never wins)
-// come out of the same kernel.  FP32 per-thread sums are folded into FP64
-// every 256 entries.  grid = ceil(items / (256 / TPI)), block = 256.
+// come out of the same kernel.  FP32 terms are summed per tile (at most 32
+// entries) in float, the tiles in a second float accumulator, and that is
+// folded into FP64 every 256 entries: at most 31 + 8 roundings per sum of
+// non-negative terms.  grid = ceil(items / (256 / TPI)), block = 256.
 // ---------------------------------------------------------------------
-__device__ __forceinline__ void eval_group(const float4 v, const float2 (&mA)[2], const float2 (&mB)[2],
-                                           float2 (&NA)[2], float2 (&NB)[2], float2 (&DA)[2], float2 (&DB)[2]) {
-    const float2 aa = make_float2(v.x, v.x), ee = make_float2(v.y, v.y), ww = make_float2(v.z, v.z);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const float2 A = __fadd2_rn(aa, mA[h]);
-        const float2 B = __fadd2_rn(aa, mB[h]);
-        const float2 P = __fmul2_rn(A, B);
-        const float2 R = make_float2(pair_rcp(P.x), pair_rcp(P.y));
-        const float2 SA = __fmul2_rn(B, R);
-        const float2 SB = __fmul2_rn(A, R);
-        DA[h] = __ffma2_rn(ww, SA, DA[h]);
-        DB[h] = __ffma2_rn(ww, SB, DB[h]);
-        NA[h] = __ffma2_rn(__fmul2_rn(ee, SA), SA, NA[h]);
-        NB[h] = __ffma2_rn(__fmul2_rn(ee, SB), SB, NB[h]);
-    }
-}
-
 template <typename T, bool CPLX, int TPI>
 __global__ void __launch_bounds__(256)
 k_gcv_items(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
@@ -886,8 +917,16 @@ k_gcv_items(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename 
         __syncthreads();
         if (item < items) {
             if constexpr (sizeof(T) == 4) {
+                float2 nA[2] = {}, nB[2] = {}, dA[2] = {}, dB[2] = {};
 #pragma unroll 4
-                for (int k = 0; k < cnt; ++k) eval_group(tile[slot][k], mA, mB, NA, NB, DA, DB);
+                for (int k = 0; k < cnt; ++k) eval_group(tile[slot][k], mA, mB, nA, nB, dA, dB);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    NA[h] = __fadd2_rn(NA[h], nA[h]);
+                    NB[h] = __fadd2_rn(NB[h], nB[h]);
+                    DA[h] = __fadd2_rn(DA[h], dA[h]);
+                    DB[h] = __fadd2_rn(DB[h], dB[h]);
+                }
                 since_fold += cnt;
                 if (since_fold >= 256 || e0 + GT_TILE >= geo.S) {        // fold into FP64
 #pragma unroll
