@@ -4,13 +4,15 @@
 // operands K-major in HBM and each operand held as a pair of bfloat16 arrays
 // (hi = bf16(x), lo = bf16(x - hi)); the three products hi.hi + hi.lo + lo.hi
 // accumulate in FP32 in tensor memory, which keeps about 16 significant bits
-// of every product.  A persistent CTA per SM computes 128 x 256 tiles with a
-// warp-specialised three-stage pipeline (two CTAs per SM): one thread issues
+// of every product.  One persistent CTA of six warps per SM computes 128 x 256
+// tiles with a warp-specialised four-stage pipeline: one thread of warp 0 issues
 // TMA loads of 32-wide K slices (64-byte swizzled shared memory, completion counted in
-// bytes on a per-stage mbarrier), one thread issues tcgen05.mma and commits
-// each stage back to the producer, and the four warps read their 32
-// accumulator lanes back with tcgen05.ld for the epilogue.  Every mbarrier
-// wait is bounded; a wait that gives up sets an error word that the host reads.
+// bytes on a per-stage mbarrier), one thread of warp 1 issues tcgen05.mma into one
+// of two 256-column tensor-memory accumulators and commits each stage back to the
+// producer, and the four epilogue warps read the other accumulator's 32 lanes each
+// back with tcgen05.ld, so a tile's epilogue overlaps the next tile's products.
+// Every mbarrier wait is bounded; a wait that gives up sets an error word that
+// the host reads.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
