@@ -346,6 +346,13 @@ def run_ours(args):
     ms_x = max_over_ranks(ms_x, dist, dev)
     G_x = torch.empty((B, K_MU), dtype=torch.float64, device=dev)
     plan.deblur_exact(g_d, h_d, f_x, mi_x, G_x)
+    # the same functional, its grid minimiser found by the coarse-to-fine search
+    f_xs = torch.empty_like(g_d)
+    mi_xs = torch.empty(B, dtype=torch.int32, device=dev)
+    ms_xs, clk_xs = _timed(lambda: plan.deblur_exact_search(g_d, h_d, f_xs, mi_xs), stream, args.steps,
+                           args.warmup)
+    search_launches = plan.last_launch_count
+    ms_xs = max_over_ranks(ms_xs, dist, dev)
 
     plan.deblur(g_d, h_d, f_d, mi_d, None)
     r_full, r_bin = rre(f_d), rre(f_b)
@@ -358,6 +365,14 @@ def run_ours(args):
                            "exact": float(np.median(mus[mi_x.cpu().numpy()]))},
              "rre_mean": {"approximate": float(r_full.mean()), "exact": float(r_x.mean())},
              "clocks": clk_x}
+    r_xs = rre(f_xs)
+    exact_search = {"value": whole_job_rate(world, B, args.steps, ms_xs / 1e3), "unit": "deblurs/s",
+                    "ms_per_step": ms_xs / args.steps, "gpu_launches": search_launches * args.steps,
+                    "evaluations_per_image": int(np.isfinite(G_xs_probe(plan, g_d, h_d, B)).sum() // B),
+                    "index_agreement_with_full_exact_scan": float((mi_xs == mi_x).float().mean()),
+                    "rre_mean": {"full_exact_scan": float(r_x.mean()), "search": float(r_xs.mean())},
+                    "rre_ratio_to_full_exact_scan": float(r_xs.mean() / r_x.mean()),
+                    "clocks": clk_xs}
     refined = {"value": whole_job_rate(world, B, args.steps, ms_r / 1e3), "unit": "deblurs/s",
                "ms_per_step": ms_r / args.steps, "gpu_launches": refined_launches * args.steps,
                "G_ratio_to_grid_min": {"mean": float((G_ref / g_min).mean()), "max": float((G_ref / g_min).max())},
@@ -433,7 +448,7 @@ def run_ours(args):
         cpu = {"value": 1.0 / sec, "unit": "deblurs/s", "cores": blas_threads(), "kind": "oracle",
                "sample": f"{n_img} images of the same workload, dense FP64 oracle (separable mode)"}
         oracle_error = default_oracle_error(kept, h, mus, f_d, mi_d, G_grid, f_b, mi_b, f_r, mu_r, G_ref,
-                                            f_x, mi_x, G_x)
+                                            f_x, mi_x, G_x, f_xs, mi_xs)
 
     if rank == 0:
         line = {
@@ -444,7 +459,8 @@ def run_ours(args):
                        "l2": "inputs+outputs %.0f MB per step > 129 MB L2 (no flush)" % (2 * B * N_SIDE ** 2 * esz / 1e6)},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
             "hbm_roofline": hbm, "steps_ms": steps_ms, "cpu_baseline": cpu, "clocks": clocks,
-            "binned_mu": binned, "refined_mu": refined, "exact_gcv": exact, "oracle_error": oracle_error,
+            "binned_mu": binned, "refined_mu": refined, "exact_gcv": exact, "exact_gcv_search": exact_search,
+            "oracle_error": oracle_error,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -454,21 +470,32 @@ def run_ours(args):
     return 0
 
 
-def default_oracle_error(kept, h, mus, f_d, mi_d, G_grid, f_b, mi_b, f_r, mu_r, G_ref, f_x, mi_x, G_x):
+def G_xs_probe(plan, g_d, h_d, B):
+    """G_ex at the grid values the coarse-to-fine search evaluated (NaN elsewhere)."""
+    import torch
+    G = torch.empty((B, K_MU), dtype=torch.float64, device=g_d.device)
+    f = torch.empty_like(g_d)
+    plan.deblur_exact_search(g_d, h_d, f, None, G)
+    return G.cpu().numpy()
+
+
+def default_oracle_error(kept, h, mus, f_d, mi_d, G_grid, f_b, mi_b, f_r, mu_r, G_ref, f_x, mi_x, G_x, f_xs,
+                         mi_xs):
     """Error of every arm of the 1024^2 line against the FP64 oracle on the images
     the CPU baseline ran: f in relative 2-norm at the mu the arm chose (the oracle
     filters its own spectrum at that mu), and G where the arm reports one."""
     from oracle import exact_gcv_oracle as X
     from oracle import hobc_oracle as O
     n = len(kept)
-    fs = {k: v.cpu().numpy()[:n] for k, v in (("full", f_d), ("binned", f_b), ("refined", f_r), ("exact", f_x))}
-    ks = {k: v.cpu().numpy()[:n] for k, v in (("full", mi_d), ("binned", mi_b), ("exact", mi_x))}
+    fs = {k: v.cpu().numpy()[:n] for k, v in (("full", f_d), ("binned", f_b), ("refined", f_r), ("exact", f_x),
+                                              ("search", f_xs))}
+    ks = {k: v.cpu().numpy()[:n] for k, v in (("full", mi_d), ("binned", mi_b), ("exact", mi_x), ("search", mi_xs))}
     Gg, Gr, Gx, mr = G_grid.cpu().numpy(), G_ref.cpu().numpy(), G_x.cpu().numpy(), mu_r.cpu().numpy()
     d = O.eigenvalues_2d("F", h, N_SIDE, N_SIDE)
     s = O.smoothing_2d("F", N_SIDE, N_SIDE, "I")
     out = {"images": n, "reference": "dense FP64 oracle (separable mode) on the same g",
            "measure": "f: ||f_gpu - f_oracle(mu)||_2 / ||f_oracle(mu)||_2 at the arm's mu; G: max relative"}
-    arms = {"full_scan": [], "binned_mu": [], "refined_mu": [], "exact_gcv": []}
+    arms = {"full_scan": [], "binned_mu": [], "refined_mu": [], "exact_gcv": [], "exact_gcv_search": []}
     g_err, g_ref_err, g_ex_err, agree = [], [], [], []
     for i, (f_o, G_o, k_o, ghat) in enumerate(kept):
         cache = {int(k_o): f_o}
@@ -481,6 +508,7 @@ def default_oracle_error(kept, h, mus, f_d, mi_d, G_grid, f_b, mi_b, f_r, mu_r, 
         arms["binned_mu"].append(rel2(fs["binned"][i], f_at_index(int(ks["binned"][i]))))
         arms["refined_mu"].append(rel2(fs["refined"][i], oracle_f_2d("F", h, ghat, "I", float(mr[i]))))
         arms["exact_gcv"].append(rel2(fs["exact"][i], f_at_index(int(ks["exact"][i]))))
+        arms["exact_gcv_search"].append(rel2(fs["search"][i], f_at_index(int(ks["search"][i]))))
         g_err.append(float(np.max(np.abs(Gg[i] - G_o) / G_o)))
         agree.append(int(ks["full"][i]) == int(k_o))
         G_at = O.gcv_curve(ghat, d, s, np.array([mr[i]]))[0]
@@ -493,6 +521,7 @@ def default_oracle_error(kept, h, mus, f_d, mi_d, G_grid, f_b, mi_b, f_r, mu_r, 
     out["binned_mu"] = {"f_rel_2norm_max": max(arms["binned_mu"])}
     out["refined_mu"] = {"f_rel_2norm_max": max(arms["refined_mu"]), "G_rel_at_mu_max": float(max(g_ref_err))}
     out["exact_gcv"] = {"f_rel_2norm_max": max(arms["exact_gcv"]), "G_rel_at_mu_max": float(max(g_ex_err))}
+    out["exact_gcv_search"] = {"f_rel_2norm_max": max(arms["exact_gcv_search"])}
     return out
 
 

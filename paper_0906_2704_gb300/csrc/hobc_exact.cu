@@ -37,6 +37,13 @@ struct hobc_exact_s {
     void* col_out;         // [batch][stored columns][2 + 2k (x2 complex)][K]: ww, den, (V0 P)[r][c]
     void* row_out;         // [batch][n_0][2k (x2 complex)][K]: (P V1^T)[a][r]
     double* G;             // [batch][K] when the caller passes no curve
+    // coarse-to-fine search (allocated on its first call)
+    int* s_idx;            // [batch][32] grid indices of a level
+    void* s_mu;            // [batch][32] their mu, plan precision
+    double* s_G;           // [batch][32] G_ex at them
+    double* s_best;        // [batch] G_ex of the incumbent
+    double* red;           // reduction partials [batch][P][K][4 + 2 NB^2]
+    size_t red_cap;        // doubles allocated in red
 };
 
 namespace hobc {
@@ -45,6 +52,7 @@ constexpr int kExKMax = 2;             // border vectors per side at most (degre
 constexpr int kExB = 2 * kExKMax;
 constexpr int kExSlots = 4;            // reduction: line slices per grid value
 constexpr int kExCB = 4;               // stored columns per CTA of the column pass
+constexpr int kExParts = 16;           // reduction: line partitions (CTAs per grid value block) at most
 
 // ------------------------------------------------- real or complex entries
 __device__ __forceinline__ float xm(float a, float b) { return a * b; }
@@ -68,6 +76,17 @@ template <> __device__ __forceinline__ float xz<float>() { return 0.f; }
 template <> __device__ __forceinline__ double xz<double>() { return 0.0; }
 template <> __device__ __forceinline__ float2 xz<float2>() { return make_float2(0.f, 0.f); }
 template <> __device__ __forceinline__ double2 xz<double2>() { return make_double2(0.0, 0.0); }
+
+// Butterfly sums over the rs adjacent lanes that share a grid value (rs a power
+// of two <= 32; every lane of the warp takes part).
+__device__ __forceinline__ float shx(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shx(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float2 shx(float2 v, int o) { return make_float2(shx(v.x, o), shx(v.y, o)); }
+__device__ __forceinline__ double2 shx(double2 v, int o) { return make_double2(shx(v.x, o), shx(v.y, o)); }
+template <typename E> __device__ __forceinline__ E lane_sum(E v, int rs) {
+    for (int o = rs / 2; o > 0; o >>= 1) v = xa(v, shx(v, o));
+    return v;
+}
 
 // Fourier half spectrum along an axis of n (N = n - 2): spectral index of a
 // stored entry, whether it stands alone (no conjugate partner), and t -> -t.
@@ -229,11 +248,11 @@ __device__ __forceinline__ void ex_stage(const typename ElemT<T, CPLX>::t* sp, c
 // pair).  The V0 P W1^T term is formed from the projections in k_ex_reduce.
 // grid = (ceil(stored columns / kExCB), items), block <= 256;
 // dynamic shared memory (kExCB + 2k) n0 (sizeof(T) + sizeof(E)).
-template <typename T, bool CPLX, int NB>
+template <typename T, bool CPLX, int NB, bool SL>
 __global__ void __launch_bounds__(256)
 k_ex_cols(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
-          long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo, ExAxis A0, ExAxis A1,
-          T* __restrict__ out) {
+          long long d_psf_stride, int psf_per, const T* __restrict__ muT, int mu_stride, int rs_arg, GcvGeom geo,
+          ExAxis A0, ExAxis A1, T* __restrict__ out) {
     typedef typename ElemT<T, CPLX>::t E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int nb = NB, k = NB / 2, NB1 = NB > 0 ? NB : 1, ns = kExCB + NB;
@@ -269,9 +288,12 @@ k_ex_cols(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
     }
     const int K = geo.K;
     const int nval = 2 + nb * (CPLX ? 2 : 1);
-    for (int jb = 0; jb < K; jb += blockDim.x) {
-        const int j = jb + threadIdx.x;
-        const T mu = j < K ? muT[j] : (T)1;
+    const int rs = SL ? rs_arg : 1;           // lanes per grid value (1: one value per thread)
+    const int sl = threadIdx.x % rs, jpb = blockDim.x / rs;
+    const T* mup = muT + item * mu_stride;
+    for (int jb = 0; jb < K; jb += jpb) {
+        const int j = jb + threadIdx.x / rs;
+        const T mu = j < K ? mup[j] : (T)1;
         E gam[kExCB][NB1];                    // P[bk][t] + sum_bl P[bk][bl] bhat1[bl][j(t)]
 #pragma unroll
         for (int bk = 0; bk < NB; ++bk) {
@@ -302,7 +324,7 @@ k_ex_cols(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
 #pragma unroll
             for (int r = 0; r < NB; ++r) s[q][r] = xz<E>();
         }
-        for (int a = 0; a < n0; ++a) {
+        for (int a = sl; a < n0; a += rs) {
             E Pb[NB1], v0[NB1], bb[NB1];
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
@@ -329,7 +351,15 @@ k_ex_cols(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
                 }
             }
         }
-        if (j < K)
+        if (rs > 1)
+#pragma unroll
+            for (int q = 0; q < kExCB; ++q) {
+                ww[q] = lane_sum(ww[q], rs);
+                den[q] = lane_sum(den[q], rs);
+#pragma unroll
+                for (int r = 0; r < NB; ++r) s[q][r] = lane_sum(s[q][r], rs);
+            }
+        if (j < K && sl == 0)
 #pragma unroll
             for (int q = 0; q < kExCB; ++q) {
                 const int c = c0 + q;
@@ -361,11 +391,11 @@ k_ex_cols(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
 // both rows' sums from one reciprocal per stored entry.  The W0 P V1^T term
 // is formed from the projections in k_ex_reduce.
 // dynamic shared memory (1 or 2) W1 (sizeof(T) + sizeof(E)).
-template <typename T, bool CPLX, int NB>
+template <typename T, bool CPLX, int NB, bool SL>
 __global__ void __launch_bounds__(256)
 k_ex_rows(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
-          long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo, ExAxis A0, ExAxis A1,
-          T* __restrict__ out) {
+          long long d_psf_stride, int psf_per, const T* __restrict__ muT, int mu_stride, int rs_arg, GcvGeom geo,
+          ExAxis A0, ExAxis A1, T* __restrict__ out) {
     typedef typename ElemT<T, CPLX>::t E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int nb = NB, NB1 = NB > 0 ? NB : 1;
@@ -390,13 +420,16 @@ k_ex_rows(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
     const E* V1 = reinterpret_cast<const E*>(A1.V);
     T* o = out + (item * n0 + a) * (long long)nval * K;
     T* op = out + (item * n0 + ap) * (long long)nval * K;
-    for (int jb = 0; jb < K; jb += blockDim.x) {
-        const int j = jb + threadIdx.x;
-        const T mu = j < K ? muT[j] : (T)1;
+    const int rs = SL ? rs_arg : 1;           // lanes per grid value (1: one value per thread)
+    const int sl = threadIdx.x % rs, jpb = blockDim.x / rs;
+    const T* mup = muT + item * mu_stride;
+    for (int jb = 0; jb < K; jb += jpb) {
+        const int j = jb + threadIdx.x / rs;
+        const T mu = j < K ? mup[j] : (T)1;
         E u[NB1], up[NB1];
 #pragma unroll
         for (int r = 0; r < NB1; ++r) { u[r] = xz<E>(); up[r] = xz<E>(); }
-        for (int c = 0; c < W1; ++c) {
+        for (int c = sl; c < W1; c += rs) {
             const int t = CPLX ? hx_t(c, n1, W1) : c;
             const E P0 = xs(sg[c], pair_rcp(sa[c] + mu));
             if constexpr (CPLX) {
@@ -419,7 +452,13 @@ k_ex_rows(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
                 for (int r = 0; r < NB; ++r) u[r] = xa(u[r], xm(V1[(size_t)r * n1 + t], P0));
             }
         }
-        if (j < K)
+        if (rs > 1)
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+                u[r] = lane_sum(u[r], rs);
+                if constexpr (CPLX) up[r] = lane_sum(up[r], rs);
+            }
+        if (j < K && sl == 0)
 #pragma unroll
             for (int r = 0; r < NB; ++r) {
                 if constexpr (CPLX) {
@@ -436,27 +475,34 @@ k_ex_rows(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename El
     }
 }
 
-// 2D: G_ex from the line sums.  Slot s of grid value j (lane) covers the
-// stored columns and rows = s mod kExSlots: the column sums ww and den, the
-// column terms |(V0 P W1^T)[r][j]|^2 = |(V0 P)[r][c] + sum_bl (V0 P)[r][bl]
-// bhat1[bl][j]|^2 (pair-weighted), the row terms |(W0 P V1^T)[i][r]|^2 =
-// |u_r(a) + sum_bk bhat0[bk][i] u_r(bk)|^2, and its share of (V0 P V1^T)[r][r']
-// = sum over full columns of (V0 P)[r][t] V1[r'][t] (a stored Fourier column
-// that stands for a pair adds conj((V0 P)[r][c]) at V1's column -t).  Line
-// terms in the working precision, sums in FP64; slot 0 adds the slots in
-// order.  num = ww + vw + wv + |V0 P V1^T|^2, G = num / den^2.
-// grid = (items, ceil(K / 32)), block = (32, kExSlots).
+// 2D: G_ex from the line sums, in two kernels.  k_ex_reduce: CTA (item,
+// y, z) takes grid values y*jpc .. y*jpc + jpc - 1, jpc = 32 / LS (LS = 2^ls_log2
+// adjacent lanes per value), and the stored columns and rows c = (z kExSlots +
+// s) LS + l mod (P kExSlots LS) for slot s, lane offset l and P = gridDim.z:
+// the column sums ww and den, the column terms |(V0 P W1^T)[r][j]|^2 =
+// |(V0 P)[r][c] + sum_bl (V0 P)[r][bl] bhat1[bl][j]|^2 (pair-weighted), the
+// row terms |(W0 P V1^T)[i][r]|^2 = |u_r(a) + sum_bk bhat0[bk][i] u_r(bk)|^2,
+// and its share of (V0 P V1^T)[r][r'] = sum over full columns of (V0 P)[r][t]
+// V1[r'][t] (a stored Fourier column that stands for a pair adds
+// conj((V0 P)[r][c]) at V1's column -t).  Line terms in the working precision,
+// sums in FP64; the lanes of a value and the slots are added in a fixed order
+// and the CTA's sums go to part[item][z][j][0 .. 4 + 2 NB^2).  k_ex_finish adds
+// the P partitions in order and forms num = ww + vw + wv + |V0 P V1^T|^2,
+// G = num / den^2.  grid = (items, ceil(K / jpc), P), block = (32, kExSlots).
 template <typename T, bool CPLX, int NB>
 __global__ void __launch_bounds__(32 * kExSlots)
 k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, ExAxis A0, ExAxis A1,
-            const double* __restrict__ V1d, int K, double* __restrict__ G) {
+            const double* __restrict__ V1d, int K, int ls_log2, double* __restrict__ part_out) {
     typedef typename ElemT<T, CPLX>::t E;
-    constexpr int nb = NB, k = NB / 2, NB1 = NB > 0 ? NB : 1;
-    __shared__ double part[4][kExSlots][32];
-    __shared__ double vre[kExSlots][NB1 * NB1][32], vim[kExSlots][NB1 * NB1][32];
+    constexpr int nb = NB, k = NB / 2, NB1 = NB > 0 ? NB : 1, NV = 4 + 2 * NB1 * NB1;
+    __shared__ double part[NV][kExSlots][32];
+    const int LS = 1 << ls_log2;
     const int lane = threadIdx.x, s = threadIdx.y;
-    const int j = blockIdx.y * 32 + lane;
+    const int jl = lane >> ls_log2, l = lane & (LS - 1), jpc = 32 >> ls_log2;
+    const int j = blockIdx.y * jpc + jl;
     const long long item = blockIdx.x;
+    const int z = blockIdx.z, P = gridDim.z;
+    const int stride = P * kExSlots * LS, start = (z * kExSlots + s) * LS + l;
     const int n0 = A0.n, n1 = A1.n, W1 = A1.W;
     const int cv = nb * (CPLX ? 2 : 1), ncol = 2 + cv;
     const E* b0 = reinterpret_cast<const E*>(A0.bhat);
@@ -479,7 +525,7 @@ k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, ExAxis
                 sB[b][r] = (b < nb && r < nb) ? ld(co + (long long)A1.bcol[b] * ncol * K + 2 * K, r) : xz<E>();
                 uB[b][r] = (b < nb && r < nb) ? ld(ro + (long long)A0.bidx[b] * cv * K, r) : xz<E>();
             }
-        for (int c = s; c < W1; c += kExSlots) {
+        for (int c = start; c < W1; c += stride) {
             const T* oc = co + (long long)c * ncol * K;
             ww += (double)oc[j];
             den += (double)oc[K + j];
@@ -511,7 +557,7 @@ k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, ExAxis
             }
             vw += (pair ? 2.0 : 1.0) * (double)term;
         }
-        for (int a = s; a < n0; a += kExSlots) {
+        for (int a = start; a < n0; a += stride) {
             if (a < k || a >= n0 - k) continue;
             const T* orow = ro + (long long)a * cv * K;
             T term = 0;
@@ -523,33 +569,57 @@ k_ex_reduce(const T* __restrict__ col_out, const T* __restrict__ row_out, ExAxis
             wv += (double)term;
         }
     }
-    part[0][s][lane] = ww; part[1][s][lane] = vw; part[2][s][lane] = den; part[3][s][lane] = wv;
+    for (int o = LS / 2; o > 0; o >>= 1) {           // the lanes of one grid value
+        ww += shx(ww, o); vw += shx(vw, o); den += shx(den, o); wv += shx(wv, o);
 #pragma unroll
-    for (int q = 0; q < NB1 * NB1; ++q) { vre[s][q][lane] = mr[q]; vim[s][q][lane] = mi[q]; }
+        for (int q = 0; q < NB1 * NB1; ++q) { mr[q] += shx(mr[q], o); mi[q] += shx(mi[q], o); }
+    }
+    if (l == 0) {
+        part[0][s][jl] = ww; part[1][s][jl] = vw; part[2][s][jl] = den; part[3][s][jl] = wv;
+#pragma unroll
+        for (int q = 0; q < NB1 * NB1; ++q) { part[4 + 2 * q][s][jl] = mr[q]; part[5 + 2 * q][s][jl] = mi[q]; }
+    }
     __syncthreads();
-    if (s != 0 || j >= K) return;
-    ww = vw = den = wv = 0;
-    for (int q = 0; q < kExSlots; ++q) {
-        ww += part[0][q][lane]; vw += part[1][q][lane]; den += part[2][q][lane]; wv += part[3][q][lane];
+    if (s != 0 || l != 0 || j >= K) return;
+    double* o = part_out + ((item * P + z) * (long long)K + j) * NV;
+    for (int v = 0; v < NV; ++v) {
+        double acc = 0;
+        for (int q = 0; q < kExSlots; ++q) acc += part[v][q][jl];
+        o[v] = acc;
     }
-    double vsq = 0;
-    for (int q = 0; q < NB1 * NB1; ++q) {
-        double ar = 0, ai = 0;
-        for (int t = 0; t < kExSlots; ++t) { ar += vre[t][q][lane]; ai += vim[t][q][lane]; }
-        vsq += ar * ar + ai * ai;
+}
+
+// G_ex of every (item, grid value) from the P partitions of k_ex_reduce, added
+// in partition order.  grid = items, block = min(256, K rounded up to 32).
+template <int NB>
+__global__ void k_ex_finish(const double* __restrict__ part_in, int K, int P, double* __restrict__ G) {
+    constexpr int NB1 = NB > 0 ? NB : 1, NV = 4 + 2 * NB1 * NB1;
+    const long long item = blockIdx.x;
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        double acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] = 0;
+        for (int z = 0; z < P; ++z) {
+            const double* pz = part_in + ((item * P + z) * (long long)K + j) * NV;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) acc[v] += pz[v];
+        }
+        double vsq = 0;
+#pragma unroll
+        for (int q = 0; q < NB1 * NB1; ++q) vsq += acc[4 + 2 * q] * acc[4 + 2 * q] + acc[5 + 2 * q] * acc[5 + 2 * q];
+        G[item * K + j] = (acc[0] + acc[1] + acc[3] + vsq) / (acc[2] * acc[2]);
     }
-    G[item * K + j] = (ww + vw + wv + vsq) / (den * den);
 }
 
 // 1D: one CTA per problem, one grid value per thread:
 // num = sum_i |(W P)[i]|^2 + sum_r |(V P)[r]|^2, G = num / (sum sigma)^2 (Fourier
 // half spectrum: pair weights on the first two sums, partner entries in V P).
 // grid = items, block <= 256; dynamic shared memory W (sizeof(T) + sizeof(E)).
-template <typename T, bool CPLX, int NB>
+template <typename T, bool CPLX, int NB, bool SL>
 __global__ void __launch_bounds__(256)
 k_ex_1d(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
-        long long d_psf_stride, int psf_per, const T* __restrict__ muT, GcvGeom geo, ExAxis A0,
-        double* __restrict__ G) {
+        long long d_psf_stride, int psf_per, const T* __restrict__ muT, int mu_stride, int rs_arg, GcvGeom geo,
+        ExAxis A0, double* __restrict__ G) {
     typedef typename ElemT<T, CPLX>::t E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int nb = NB, k = NB / 2, NB1 = NB > 0 ? NB : 1;
@@ -564,9 +634,12 @@ k_ex_1d(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename Elem
     const E* b0 = reinterpret_cast<const E*>(A0.bhat);
     const E* V0 = reinterpret_cast<const E*>(A0.V);
     const int K = geo.K;
-    for (int jb = 0; jb < K; jb += blockDim.x) {
-        const int j = jb + threadIdx.x;
-        const T mu = j < K ? muT[j] : (T)1;
+    const int rs = SL ? rs_arg : 1;           // lanes per grid value (1: one value per thread)
+    const int sl = threadIdx.x % rs, jpb = blockDim.x / rs;
+    const T* mup = muT + item * mu_stride;
+    for (int jb = 0; jb < K; jb += jpb) {
+        const int j = jb + threadIdx.x / rs;
+        const T mu = j < K ? mup[j] : (T)1;
         E pb[NB1];
 #pragma unroll
         for (int b = 0; b < NB; ++b)
@@ -575,7 +648,7 @@ k_ex_1d(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename Elem
         E s[NB1];
 #pragma unroll
         for (int r = 0; r < NB; ++r) s[r] = xz<E>();
-        for (int c = 0; c < W; ++c) {
+        for (int c = sl; c < W; c += rs) {
             const int t = CPLX ? hx_t(c, n, W) : c;
             const bool pair = CPLX && !hx_self(c, n, W);
             const T wg = pair ? (T)2 : (T)1;
@@ -596,11 +669,17 @@ k_ex_1d(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename Elem
                 ww += wg * abs2_of(w);
             }
         }
+        if (rs > 1) {
+            ww = lane_sum(ww, rs);
+            den = lane_sum(den, rs);
+#pragma unroll
+            for (int r = 0; r < NB; ++r) s[r] = lane_sum(s[r], rs);
+        }
         T vsq = 0;
 #pragma unroll
         for (int r = 0; r < NB; ++r)
             if (r < nb) vsq += abs2_of(s[r]);
-        if (j < K) G[item * K + j] = ((double)ww + (double)vsq) / ((double)den * (double)den);
+        if (j < K && sl == 0) G[item * K + j] = ((double)ww + (double)vsq) / ((double)den * (double)den);
     }
 }
 
@@ -640,6 +719,7 @@ void exact_free(hobc_plan_s* p) {
     cudaFree(x->col_out);
     cudaFree(x->row_out);
     cudaFree(x->G);
+    cudaFree(x->s_idx); cudaFree(x->s_mu); cudaFree(x->s_G); cudaFree(x->s_best); cudaFree(x->red);
     delete x;
     p->exact = nullptr;
 }
@@ -713,67 +793,232 @@ ExAxis ex_axis(const hobc_exact_s* x, const hobc_plan_s* p, int a) {
     return A;
 }
 
+// Lanes per grid value: one grid value per thread for K >= 256; for fewer
+// values the lines are cut into rs slices (adjacent lanes, summed by
+// butterflies) so that a CTA still runs 256 threads.
+int lane_slices(int K) {
+    int jp = 1;
+    while (jp < K && jp < 256) jp *= 2;
+    return std::min(32, std::max(1, 256 / jp));
+}
+
+// G_ex at Kp values of mu per problem (muT + item * mu_stride, plan
+// precision) into Gout [batch][Kp].
 template <typename T, bool CPLX, int NB>
-hobc_status run_gcv_exact(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx) {
+hobc_status run_exact_pass(hobc_plan_s* p, const void* ghat, const void* D, const T* muT, int mu_stride, int Kp,
+                           double* Gout) {
     typedef typename ElemT<T, CPLX>::t E;
     hobc_exact_s* x = p->exact;
     GcvGeom geo = exact_geo(p);
-    const int B = p->desc.batch, K = p->K;
+    geo.K = Kp;
+    const int B = p->desc.batch;
     constexpr int k = NB / 2;
     const E* sp = reinterpret_cast<const E*>(ghat);
     const E* dp = reinterpret_cast<const E*>(D);
-    const T* muT = reinterpret_cast<const T*>(p->muT);
     const long long dps = (long long)p->spec_elems;
-    double* Gout = gcv ? gcv : x->G;
-    const int threads = std::min(256, (K + 31) / 32 * 32);
+    const int rs = lane_slices(Kp);
+    const int threads = rs > 1 ? 256 : std::min(256, (Kp + 31) / 32 * 32);
     const size_t el = sizeof(T) + sizeof(E);
     cudaError_t e = cudaSuccess;
     if (p->nax == 1) {
         const ExAxis A0 = ex_axis(x, p, 0);
-        k_ex_1d<T, CPLX, NB><<<B, threads, (size_t)A0.W * el, p->stream>>>(sp, dp, dps, p->desc.psf_per_item, muT,
-                                                                          geo, A0, Gout);
+        (rs > 1 ? k_ex_1d<T, CPLX, NB, true> : k_ex_1d<T, CPLX, NB, false>)<<<B, threads, (size_t)A0.W * el, p->stream>>>(sp, dp, dps, p->desc.psf_per_item, muT,
+                                                                          mu_stride, rs, geo, A0, Gout);
         p->launches += 1;
     } else {
         const ExAxis A0 = ex_axis(x, p, 0), A1 = ex_axis(x, p, 1);
         const int n0 = A0.n, W1 = A1.W;
         const size_t sc = (size_t)(kExCB + 2 * k) * n0 * el, sr = (size_t)(CPLX ? 2 : 1) * W1 * el;
-        e = cudaFuncSetAttribute(k_ex_cols<T, CPLX, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_ex_rows<T, CPLX, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
+        auto cols = rs > 1 ? k_ex_cols<T, CPLX, NB, true> : k_ex_cols<T, CPLX, NB, false>;
+        auto rows = rs > 1 ? k_ex_rows<T, CPLX, NB, true> : k_ex_rows<T, CPLX, NB, false>;
+        e = cudaFuncSetAttribute(cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
         if (e != cudaSuccess) { set_last_error("hobc_gcv_exact", e); return HOBC_ERR_CUDA; }
-        k_ex_cols<T, CPLX, NB><<<dim3((unsigned)((W1 + kExCB - 1) / kExCB), (unsigned)B), threads, sc, p->stream>>>(
-            sp, dp, dps, p->desc.psf_per_item, muT, geo, A0, A1, reinterpret_cast<T*>(x->col_out));
+        cols<<<dim3((unsigned)((W1 + kExCB - 1) / kExCB), (unsigned)B), threads, sc, p->stream>>>(
+            sp, dp, dps, p->desc.psf_per_item, muT, mu_stride, rs, geo, A0, A1, reinterpret_cast<T*>(x->col_out));
         if (NB > 0)
-            k_ex_rows<T, CPLX, NB><<<dim3((unsigned)(CPLX ? (n0 - 2) / 2 + 3 : n0), (unsigned)B), threads, sr,
-                                     p->stream>>>(
-                sp, dp, dps, p->desc.psf_per_item, muT, geo, A0, A1, reinterpret_cast<T*>(x->row_out));
-        k_ex_reduce<T, CPLX, NB><<<dim3((unsigned)B, (unsigned)((K + 31) / 32)), dim3(32, kExSlots), 0, p->stream>>>(
+            rows<<<dim3((unsigned)(CPLX ? (n0 - 2) / 2 + 3 : n0), (unsigned)B), threads, sr, p->stream>>>(
+                sp, dp, dps, p->desc.psf_per_item, muT, mu_stride, rs, geo, A0, A1, reinterpret_cast<T*>(x->row_out));
+        // lanes per grid value and line partitions so that the reduction keeps
+        // the SMs busy however few values a pass evaluates
+        int ls_log2 = 0;
+        while ((32 >> (ls_log2 + 1)) >= Kp && ls_log2 < 5) ++ls_log2;
+        const int jpc = 32 >> ls_log2;
+        const int cy = (Kp + jpc - 1) / jpc;
+        const int P = std::max(1, std::min(kExParts, (2 * 152 + B * cy - 1) / (B * cy)));
+        constexpr int NV = 4 + 2 * (NB > 0 ? NB : 1) * (NB > 0 ? NB : 1);
+        const size_t need = (size_t)B * P * Kp * NV;
+        if (need > x->red_cap) {
+            cudaFree(x->red);
+            x->red = nullptr;
+            x->red_cap = 0;
+            e = cudaMalloc((void**)&x->red, need * sizeof(double));
+            if (e != cudaSuccess) { set_last_error("hobc_gcv_exact (workspace)", e); return HOBC_ERR_CUDA; }
+            x->red_cap = need;
+        }
+        k_ex_reduce<T, CPLX, NB><<<dim3((unsigned)B, (unsigned)cy, (unsigned)P), dim3(32, kExSlots), 0, p->stream>>>(
             reinterpret_cast<const T*>(x->col_out), reinterpret_cast<const T*>(x->row_out), A0, A1,
-            reinterpret_cast<const double*>(x->Vd[1]), K, Gout);
-        p->launches += NB > 0 ? 3 : 2;
+            reinterpret_cast<const double*>(x->Vd[1]), Kp, ls_log2, x->red);
+        k_ex_finish<NB><<<B, std::min(256, (Kp + 31) / 32 * 32), 0, p->stream>>>(x->red, Kp, P, Gout);
+        p->launches += NB > 0 ? 4 : 3;
     }
-    k_ex_argmin<<<B, 256, 0, p->stream>>>(Gout, K, mu_idx);
-    p->launches += 1;
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_last_error("hobc_gcv_exact", e); return HOBC_ERR_CUDA; }
     return HOBC_OK;
 }
 
-// Border vectors per axis: 2 (sine, cosine, Fourier), 4 (degree 3), 0 (orthogonal T).
+template <typename T, bool CPLX, int NB>
+hobc_status run_gcv_exact(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx) {
+    double* Gout = gcv ? gcv : p->exact->G;
+    hobc_status s = run_exact_pass<T, CPLX, NB>(p, ghat, D, reinterpret_cast<const T*>(p->muT), 0, p->K, Gout);
+    if (s != HOBC_OK) return s;
+    k_ex_argmin<<<p->desc.batch, 256, 0, p->stream>>>(Gout, p->K, mu_idx);
+    p->launches += 1;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { set_last_error("hobc_gcv_exact", e); return HOBC_ERR_CUDA; }
+    return HOBC_OK;
+}
+
+// ------------------------------------------------ coarse-to-fine search
+// Three levels for 32 < K <= 1921, with s1 = ceil((K - 1) / 15) and
+// s2 = min(s1, max(4, ceil(s1 / 8))): level 0 evaluates the grid values 0, s1,
+// 2 s1, ... and K - 1 (at most 16); level 1 the incumbent +- s2 m, m = 1 ..
+// ceil(s1 / s2) - 1; level 2 the incumbent +- 1 .. s2 - 1 (the incumbent: the
+// first minimiser of every value evaluated so far; indices clamped into the
+// grid).  Where G_ex is unimodal over the grid this reaches the grid's
+// minimiser; at K = 256 after 16 + 8 + 6 evaluations.
+constexpr int kExsSlots = 32;      // list slots per problem and level
+
+__host__ __device__ inline bool exs_searched(int K) { return K > 32 && K <= 1921; }
+__host__ __device__ inline int exs_s1(int K) { return (K - 1 + 14) / 15; }
+__host__ __device__ inline int exs_s2(int K) {
+    const int s1 = exs_s1(K), q = (s1 + 7) / 8;
+    return s1 < (q > 4 ? q : 4) ? s1 : (q > 4 ? q : 4);
+}
+__host__ __device__ inline int exs_level_count(int level, int K) {
+    const int s1 = exs_s1(K), s2 = exs_s2(K);
+    if (level == 0) return (K - 1) / s1 + 1 + ((K - 1) % s1 != 0);
+    if (level == 1) return 2 * ((s1 + s2 - 1) / s2 - 1);
+    return 2 * (s2 - 1);
+}
+
+// The list of grid indices of one level (and their mu in plan precision).
 template <typename T>
-hobc_status gcv_exact_real(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx) {
-    switch (p->exact->k) {
-        case 0: return run_gcv_exact<T, false, 0>(p, ghat, D, gcv, mu_idx);
-        case 2: return run_gcv_exact<T, false, 4>(p, ghat, D, gcv, mu_idx);
-        default: return run_gcv_exact<T, false, 2>(p, ghat, D, gcv, mu_idx);
+__global__ void k_exs_list(int level, int K, const T* __restrict__ muT, const int* __restrict__ best_idx,
+                           int* __restrict__ idx, T* __restrict__ mu) {
+    const long long item = blockIdx.x;
+    const int n = exs_level_count(level, K);
+    const int s1 = exs_s1(K), s2 = exs_s2(K);
+    for (int j = threadIdx.x; j < kExsSlots; j += blockDim.x) {
+        int k = 0;
+        if (j < n) {
+            if (level == 0) {
+                k = j * s1 < K ? j * s1 : K - 1;
+            } else {
+                const int m = j / 2 + 1;                             // -m, +m in turn
+                k = best_idx[item] + ((j & 1) ? 1 : -1) * m * (level == 1 ? s2 : 1);
+                k = k < 0 ? 0 : (k > K - 1 ? K - 1 : k);
+            }
+        }
+        idx[item * kExsSlots + j] = k;
+        mu[item * kExsSlots + j] = muT[k];
     }
 }
 
+// Folds one level's values into each problem's incumbent (smaller G, or equal
+// G at a smaller index; NaN never wins) and copies them into the curve.
+// grid = items, block = 32.
+__global__ void k_exs_pick(int level, int K, const double* __restrict__ Gl, const int* __restrict__ idx,
+                           double* __restrict__ best_val, int* __restrict__ best_idx, double* __restrict__ curve) {
+    const long long item = blockIdx.x;
+    const int n = exs_level_count(level, K);
+    const int j = threadIdx.x;
+    double key = INFINITY;
+    int bi = 0x7fffffff;
+    if (j < n) {
+        const double v = Gl[item * n + j];
+        const int k = idx[item * kExsSlots + j];
+        key = isnan(v) ? INFINITY : v;
+        bi = k;
+        if (curve) curve[item * K + k] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ok = __shfl_xor_sync(0xffffffffu, key, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ok < key || (ok == key && oi < bi)) { key = ok; bi = oi; }
+    }
+    if (j == 0) {
+        double bv = level == 0 ? INFINITY : best_val[item];
+        int bk = level == 0 ? 0x7fffffff : best_idx[item];
+        if (key < bv || (key == bv && bi < bk)) { bv = key; bk = bi; }
+        best_val[item] = bv;
+        best_idx[item] = bk == 0x7fffffff ? 0 : bk;
+    }
+}
+
+__global__ void k_exs_fill_nan(double* __restrict__ curve, long long count) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+        curve[i] = __longlong_as_double(0x7ff8000000000000LL);
+}
+
+template <typename T, bool CPLX, int NB>
+hobc_status run_gcv_exact_search(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx) {
+    const int B = p->desc.batch, K = p->K;
+    if (!exs_searched(K)) return run_gcv_exact<T, CPLX, NB>(p, ghat, D, gcv, mu_idx);
+    hobc_exact_s* x = p->exact;
+    cudaError_t e = cudaSuccess;
+    if (!x->s_idx) {
+        e = cudaMalloc((void**)&x->s_idx, (size_t)B * kExsSlots * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&x->s_mu, (size_t)B * kExsSlots * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&x->s_G, (size_t)B * kExsSlots * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&x->s_best, (size_t)B * sizeof(double));
+        if (e != cudaSuccess) { set_last_error("hobc_gcv_exact_search (workspace)", e); return HOBC_ERR_CUDA; }
+    }
+    if (gcv) {
+        k_exs_fill_nan<<<std::min(1024, (B * K + 255) / 256), 256, 0, p->stream>>>(gcv, (long long)B * K);
+        p->launches += 1;
+    }
+    T* smu = reinterpret_cast<T*>(x->s_mu);
+    const T* muT = reinterpret_cast<const T*>(p->muT);
+    for (int level = 0; level < 3; ++level) {
+        const int n = exs_level_count(level, K);
+        if (n == 0) continue;
+        k_exs_list<T><<<B, 32, 0, p->stream>>>(level, K, muT, mu_idx, x->s_idx, smu);
+        p->launches += 1;
+        hobc_status s = run_exact_pass<T, CPLX, NB>(p, ghat, D, smu, kExsSlots, n, x->s_G);
+        if (s != HOBC_OK) return s;
+        k_exs_pick<<<B, 32, 0, p->stream>>>(level, K, x->s_G, x->s_idx, x->s_best, mu_idx, gcv);
+        p->launches += 1;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { set_last_error("hobc_gcv_exact_search", e); return HOBC_ERR_CUDA; }
+    return HOBC_OK;
+}
+
+// Border vectors per axis: 2 (sine, cosine, Fourier), 4 (degree 3), 0 (orthogonal T).
+template <typename T, bool SEARCH>
+hobc_status gcv_exact_real(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx) {
+    switch (p->exact->k) {
+        case 0: return SEARCH ? run_gcv_exact_search<T, false, 0>(p, ghat, D, gcv, mu_idx)
+                              : run_gcv_exact<T, false, 0>(p, ghat, D, gcv, mu_idx);
+        case 2: return SEARCH ? run_gcv_exact_search<T, false, 4>(p, ghat, D, gcv, mu_idx)
+                              : run_gcv_exact<T, false, 4>(p, ghat, D, gcv, mu_idx);
+        default: return SEARCH ? run_gcv_exact_search<T, false, 2>(p, ghat, D, gcv, mu_idx)
+                               : run_gcv_exact<T, false, 2>(p, ghat, D, gcv, mu_idx);
+    }
+}
+
+template <bool SEARCH>
 hobc_status gcv_exact_dispatch(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx) {
     const bool F = p->exact->cplx;
-    if (p->prec == HOBC_FP64)
-        return F ? run_gcv_exact<double, true, 2>(p, ghat, D, gcv, mu_idx) : gcv_exact_real<double>(p, ghat, D, gcv, mu_idx);
-    return F ? run_gcv_exact<float, true, 2>(p, ghat, D, gcv, mu_idx) : gcv_exact_real<float>(p, ghat, D, gcv, mu_idx);
+    if (p->prec == HOBC_FP64) {
+        if (F) return SEARCH ? run_gcv_exact_search<double, true, 2>(p, ghat, D, gcv, mu_idx)
+                             : run_gcv_exact<double, true, 2>(p, ghat, D, gcv, mu_idx);
+        return gcv_exact_real<double, SEARCH>(p, ghat, D, gcv, mu_idx);
+    }
+    if (F) return SEARCH ? run_gcv_exact_search<float, true, 2>(p, ghat, D, gcv, mu_idx)
+                         : run_gcv_exact<float, true, 2>(p, ghat, D, gcv, mu_idx);
+    return gcv_exact_real<float, SEARCH>(p, ghat, D, gcv, mu_idx);
 }
 
 }  // namespace
@@ -781,17 +1026,9 @@ hobc_status gcv_exact_dispatch(hobc_plan_s* p, const void* ghat, const void* D, 
 
 using namespace hobc;
 
-extern "C" {
-
-hobc_status hobc_gcv_exact(hobc_plan* p, const void* ghat_dev, const void* d_dev, double* gcv_dev, int* mu_index_dev) {
-    if (!p || !ghat_dev || !d_dev || !mu_index_dev) return HOBC_ERR_ARG;
-    hobc_status s = ensure_exact(p);
-    if (s != HOBC_OK) return s;
-    p->launches = 0;
-    return gcv_exact_dispatch(p, ghat_dev, d_dev, gcv_dev, mu_index_dev);
-}
-
-hobc_status hobc_deblur_exact(hobc_plan* p, const void* g_dev, const void* psf_dev, void* f_dev, int* mu_index_dev,
+namespace {
+template <bool SEARCH>
+hobc_status deblur_exact_impl(hobc_plan* p, const void* g_dev, const void* psf_dev, void* f_dev, int* mu_index_dev,
                               double* gcv_dev) {
     if (!p || !g_dev || !psf_dev || !f_dev) return HOBC_ERR_ARG;
     if (g_dev == f_dev) return HOBC_ERR_ARG;
@@ -802,11 +1039,42 @@ hobc_status hobc_deblur_exact(hobc_plan* p, const void* g_dev, const void* psf_d
     const bool fp64 = p->prec == HOBC_FP64;
     s = fp64 ? run_eig<double>(p, psf_dev, p->D) : run_eig<float>(p, psf_dev, p->D);
     if (s == HOBC_OK) s = fp64 ? run_analysis<double>(p, g_dev, p->G) : run_analysis<float>(p, g_dev, p->G);
-    if (s == HOBC_OK) s = gcv_exact_dispatch(p, p->G, p->D, gcv_dev, mi);
+    if (s == HOBC_OK) s = gcv_exact_dispatch<SEARCH>(p, p->G, p->D, gcv_dev, mi);
     if (s == HOBC_OK)
         s = fp64 ? run_filter_synthesis<double>(p, p->G, p->D, mi, f_dev)
                  : run_filter_synthesis<float>(p, p->G, p->D, mi, f_dev);
     return s;
+}
+}  // namespace
+
+extern "C" {
+
+hobc_status hobc_gcv_exact(hobc_plan* p, const void* ghat_dev, const void* d_dev, double* gcv_dev, int* mu_index_dev) {
+    if (!p || !ghat_dev || !d_dev || !mu_index_dev) return HOBC_ERR_ARG;
+    hobc_status s = ensure_exact(p);
+    if (s != HOBC_OK) return s;
+    p->launches = 0;
+    return gcv_exact_dispatch<false>(p, ghat_dev, d_dev, gcv_dev, mu_index_dev);
+}
+
+hobc_status hobc_gcv_exact_search(hobc_plan* p, const void* ghat_dev, const void* d_dev, double* gcv_dev,
+                                  int* mu_index_dev) {
+    if (!p || !ghat_dev || !d_dev || !mu_index_dev) return HOBC_ERR_ARG;
+    hobc_status s = ensure_exact(p);
+    if (s != HOBC_OK) return s;
+    p->launches = 0;
+    return gcv_exact_dispatch<true>(p, ghat_dev, d_dev, gcv_dev, mu_index_dev);
+}
+
+
+hobc_status hobc_deblur_exact(hobc_plan* p, const void* g_dev, const void* psf_dev, void* f_dev, int* mu_index_dev,
+                              double* gcv_dev) {
+    return deblur_exact_impl<false>(p, g_dev, psf_dev, f_dev, mu_index_dev, gcv_dev);
+}
+
+hobc_status hobc_deblur_exact_search(hobc_plan* p, const void* g_dev, const void* psf_dev, void* f_dev,
+                                     int* mu_index_dev, double* gcv_dev) {
+    return deblur_exact_impl<true>(p, g_dev, psf_dev, f_dev, mu_index_dev, gcv_dev);
 }
 
 }  // extern "C"

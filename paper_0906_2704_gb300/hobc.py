@@ -137,6 +137,10 @@ _lib.hobc_gcv_exact.argtypes = [_vp] * 5
 _lib.hobc_gcv_exact.restype = ctypes.c_int
 _lib.hobc_deblur_exact.argtypes = [_vp] * 6
 _lib.hobc_deblur_exact.restype = ctypes.c_int
+_lib.hobc_gcv_exact_search.argtypes = [_vp] * 5
+_lib.hobc_gcv_exact_search.restype = ctypes.c_int
+_lib.hobc_deblur_exact_search.argtypes = [_vp] * 6
+_lib.hobc_deblur_exact_search.restype = ctypes.c_int
 _lib.hobc_features.argtypes = [_vp] * 4
 _lib.hobc_features.restype = ctypes.c_int
 _lib.hobc_deblur_learned.argtypes = [_vp] * 7
@@ -396,6 +400,15 @@ class Plan:
     def deblur_exact(self, g, psf, f, mu_index=None, gcv=None) -> None:
         _check(_lib.hobc_deblur_exact(self._handle, _ptr(g), _ptr(psf), _ptr(f), _ptr(mu_index), _ptr(gcv)),
                "hobc_deblur_exact")
+
+    def gcv_exact_search(self, ghat, d, gcv, mu_index) -> None:
+        """Grid minimiser of G_ex by the coarse-to-fine search (strides 16, 4, 1)."""
+        _check(_lib.hobc_gcv_exact_search(self._handle, _ptr(ghat), _ptr(d), _ptr(gcv), _ptr(mu_index)),
+               "hobc_gcv_exact_search")
+
+    def deblur_exact_search(self, g, psf, f, mu_index=None, gcv=None) -> None:
+        _check(_lib.hobc_deblur_exact_search(self._handle, _ptr(g), _ptr(psf), _ptr(f), _ptr(mu_index),
+                                             _ptr(gcv)), "hobc_deblur_exact_search")
 
     def deblur_refined(self, g, psf, f, mu_index=None, mu=None) -> None:
         _check(_lib.hobc_deblur_refined(self._handle, _ptr(g), _ptr(psf), _ptr(f), _ptr(mu_index), _ptr(mu)),
