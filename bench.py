@@ -158,7 +158,8 @@ def oracle_f_2d(family: str, h, ghat, L: str, mu: float):
 
 
 def esz_of(prec: str) -> int:
-    return 4 if prec == "fp32" else 8
+    """Bytes of one real value of the plan's I/O and spectra (split-BF16 plans keep FP32 I/O)."""
+    return 8 if prec == "fp64" else 4
 
 
 def dist_env():
@@ -251,8 +252,8 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     B = args.batch
     prec = args.prec
-    npdt = np.float32 if prec == "fp32" else np.float64
-    tdt = torch.float32 if prec == "fp32" else torch.float64
+    npdt = np.float64 if prec == "fp64" else np.float32
+    tdt = torch.float64 if prec == "fp64" else torch.float32
     h, g, ft = make_inputs(B, seed=rank_seed(rank))
     mus = synth.mu_grid(K_MU)
     stream = torch.cuda.current_stream()
@@ -431,6 +432,29 @@ def run_ours(args):
                 "traffic_source": "ncu dram__bytes_read+write of an 8-image launch (37.92 MB), scaled per image",
                 "peak_source": f"derived, not measured: 152 SMs x 128 FP32 lanes / 5 operations per evaluation "
                                f"(1 division + 4 FMA) x {sm_max:.0f} MHz ({peak_kind} max clock)"}
+    if prec == "fp64":
+        # FP64 scan: 2 FP64 operations per SM-clock on this part (1.25 TFLOP/s), five per evaluation
+        peak = 152 * (2 / 5.0) * sm_max * 1e6 / 1e9
+        roofline.update({"peak": peak, "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"derived, not measured: 152 SMs x 2 FP64 operations per clock / 5 "
+                                        f"per evaluation x {sm_max:.0f} MHz ({peak_kind} max clock)"})
+    transform_roofline = None
+    if prec == "split_bf16":
+        # the four transform products of a step on the tensor cores (real form of the
+        # complex Fourier products): 3 split products x 2 M N K each, padded tile shapes
+        tm, tn, tk = hobc.tc_tiles()
+        pad = lambda x, t: -(-x // t) * t
+        n, W = N_SIDE, S // N_SIDE
+        shapes = [(n, 2 * W, pad(n, tk)), (W, 2 * n, 2 * pad(n, tk)),
+                  (2 * n, W, pad(2 * n, tk)), (n, n, 2 * pad(W, tk))]
+        flops = sum(3 * 2.0 * pad(m_, tm) * pad(n_, tn) * k_ for m_, n_, k_ in shapes) * B
+        t_tr = (steps_ms["analysis"] + steps_ms["filter_synthesis"]) / 1e3
+        pk = peaks.get("bf16_tflops", 1900.0)
+        transform_roofline = {"bound": "tensor", "kernel": "k_gemm_split (4 products per step)",
+                              "achieved": flops / t_tr / 1e12, "peak": pk, "unit": "TFLOP/s",
+                              "frac": flops / t_tr / 1e12 / pk, "peak_kind": peak_kind,
+                              "flops_per_step": flops,
+                              "note": "analysis and filter + synthesis calls, their split and filter kernels included"}
     hbm_bytes = B * N_SIDE * N_SIDE * esz * 2 + h.size * esz
     hbm_frac = hbm_bytes / (ms / args.steps / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)
     hbm = {"algorithmic_bytes_per_step": hbm_bytes,
@@ -454,13 +478,14 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "deblurs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "split_bf16": "bf16x3 (split) / f32"}[prec],
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "batch_per_gpu": B, "n": N_SIDE, "n_mu": K_MU,
                        "l2": "inputs+outputs %.0f MB per step > 129 MB L2 (no flush)" % (2 * B * N_SIDE ** 2 * esz / 1e6)},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
             "hbm_roofline": hbm, "steps_ms": steps_ms, "cpu_baseline": cpu, "clocks": clocks,
             "binned_mu": binned, "refined_mu": refined, "exact_gcv": exact, "exact_gcv_search": exact_search,
-            "oracle_error": oracle_error,
+            "oracle_error": oracle_error, "precision": prec, "transform_roofline": transform_roofline,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

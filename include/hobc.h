@@ -99,11 +99,13 @@ typedef enum {
     HOBC_FP64 = 0,             /* all arithmetic and I/O in double                        */
     HOBC_FP32 = 1,             /* transforms, filter and GCV terms in float; boundary 2x2
                                   solve, eigenvalues and GCV sums in double; float I/O     */
-    HOBC_SPLIT_BF16 = 2        /* real families (SINE, COSINE, SINE_CUBIC) only: every
-                                  transform pass is a dense product with T_X or T_X^{-1}
-                                  on the tensor cores, operands split into bf16 hi/lo,
-                                  FP32 accumulation (include/hobc_tc.h); eigenvalues,
-                                  filter and GCV as FP32; float I/O                        */
+    HOBC_SPLIT_BF16 = 2        /* SINE, COSINE, SINE_CUBIC, FOURIER and the comparison
+                                  families: every transform pass is a dense product with
+                                  T_X or T_X^{-1} on the tensor cores, operands split into
+                                  bf16 hi/lo, FP32 accumulation (include/hobc_tc.h); the
+                                  Fourier family's complex products run as real products
+                                  on (re, im) pairs; eigenvalues, filter and GCV as FP32;
+                                  float I/O                                               */
 } hobc_precision;
 
 typedef struct {

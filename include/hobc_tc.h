@@ -6,7 +6,12 @@
  * operand split into two bfloat16 arrays (hi = bf16(x), lo = bf16(x - hi))
  * and the three products hi.hi + hi.lo + lo.hi accumulated in FP32.  The
  * result keeps about 16 significant bits of each product: per entry
- * |C - A.B^T| <= (2^-14 + K 2^-24) (|A| |B|^T).
+ * |C - A.B^T| <= (2^-14 + K 2^-24) (|A| |B|^T).  The Fourier family's T_F is
+ * complex (Eq. (eq:Tf)); its products run as real products on (re, im) pairs:
+ * the row analysis against the (Re, Im) rows of T_1^{-1} on the stored half
+ * spectrum, the column analysis and synthesis against the real 2 x 2 block form
+ * of T_0^{-1} and T_0, and the row synthesis against the FP64 path's response
+ * to a unit real or imaginary entry of the half spectrum.
  *
  * Conventions are those of hobc.h: device pointers, asynchronous on the given
  * stream, errors as hobc_status with hobc_last_error() for CUDA failures.

@@ -485,7 +485,6 @@ hobc_status resolve_desc(const hobc_plan_desc& d, bool check_psf, int* fam_out) 
         if (fam != HOBC_FAMILY_COSINE_QUARTIC && (fam < HOBC_FAMILY_SINE || fam > HOBC_FAMILY_SINE_CUBIC))
             return HOBC_ERR_ARG;
     }
-    if (d.prec == HOBC_SPLIT_BF16 && fam == HOBC_FAMILY_FOURIER) return HOBC_ERR_UNSUPPORTED;   // complex T_F
     // degree 4 runs on the FFT path only (the dense engine has no matrices for it), and in
     // FP64 only: cond(T) is 644 already at n = 8 (7.5e4 at n = 32), so the FP32 rounding
     // bound 64 eps32 cond(T) exceeds 1e-3 at every size

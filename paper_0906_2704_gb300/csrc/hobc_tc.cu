@@ -309,6 +309,21 @@ __global__ void k_split_f64_t(const double* __restrict__ src, long long src_ld, 
     }
 }
 
+// Row-major FP64 matrix (src[r][c] at r * src_ld + c) -> split operand rows r < rows,
+// columns c < cols.
+__global__ void k_split_f64(const double* __restrict__ src, long long src_ld, int rows, int cols,
+                            __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long long ld) {
+    const long long total = (long long)rows * cols;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / cols), c = (int)(i - (long long)r * cols);
+        const double v = src[(long long)r * src_ld + c];
+        const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+        hi[(long long)r * ld + c] = h;
+        lo[(long long)r * ld + c] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+    }
+}
+
 // Filter (Eq. (eq:freg)) of the spectrum and split into the A operand of the
 // first synthesis pass.  2D: spectrum [item][t1][t0] -> rows t1, columns t0;
 // 1D: [item][t] -> row item, column t.  fd.D null: no filter (plain synthesis).
@@ -333,6 +348,36 @@ __global__ void k_filter_split(const float* __restrict__ spec, long long S, int 
         const long long o = ndim == 2 ? item * bs + (long long)r * ld + c : (item) * ld + c;
         hi[o] = h;
         lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+// Fourier family: filter (Eq. (eq:freg), complex) of the half spectrum and
+// split, re and im interleaved along K.  2D: spectrum [item][c][t0] -> rows c,
+// columns 2 t0 + part; 1D: [item][c] -> row item, columns 2 c + part.
+// fd.D null: no filter (plain synthesis).
+__global__ void k_filter_split_cplx(const float2* __restrict__ spec, long long S, int nrows, int ncols, int ndim,
+                                    Axis<float> ax0, FilterDesc fd, int items, __nv_bfloat16* __restrict__ hi,
+                                    __nv_bfloat16* __restrict__ lo, long long ld, long long bs) {
+    const long long per = (long long)nrows * ncols;
+    const long long total = per * items;
+    const float2* D = static_cast<const float2*>(fd.D);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long item = i / per, e = i - item * per;
+        const int r = (int)(e / ncols), c = (int)(e - (long long)r * ncols);
+        float2 v = spec[item * S + e];
+        if (D) {
+            const int problem = (int)item;
+            const float2 d = D[(fd.psf_per ? item : 0) * fd.d_psf_stride + e];
+            const float s2 = smoothing2<float>(fd, ndim == 2 ? 2 : 1, ax0, ndim == 2 ? r : problem, c);
+            v = apply_filter(v, d, s2, (float)mu_of(fd, problem));
+        }
+        const long long o = ndim == 2 ? item * bs + (long long)r * ld + 2 * c : item * ld + 2 * c;
+        const __nv_bfloat16 hx = __float2bfloat16_rn(v.x), hy = __float2bfloat16_rn(v.y);
+        hi[o] = hx;
+        lo[o] = __float2bfloat16_rn(v.x - __bfloat162float(hx));
+        hi[o + 1] = hy;
+        lo[o + 1] = __float2bfloat16_rn(v.y - __bfloat162float(hy));
     }
 }
 
@@ -396,6 +441,10 @@ struct hobc_dense_s {
     __nv_bfloat16* w_lo[4];
     long long w_ld[4], w_bs[4];
     int* err;
+    // Fourier family: stored columns of the last axis and the padded K of its
+    // (c, part) pairs (kw per part), and the padded K of axis 0's (t0, part) pairs
+    int fourier, W;
+    long long kw, k2;
 };
 
 namespace {
@@ -468,6 +517,205 @@ hobc_status dense_synthesis_from_x(hobc_plan_s* p, float* y) {
 
 namespace hobc {
 
+// Responses of the FP64 path of a 1D Fourier axis of n samples to unit inputs:
+// A[j][c] (complex, W per j) = analysis of the real unit e_j, i.e. T^{-1}[t(c)][j];
+// Y[u][i] (n per u) = synthesis of the half spectrum with a real (u = 2c) or
+// imaginary (u = 2c + 1) unit at stored entry c.
+static hobc_status fourier_unit_responses(int n, cudaStream_t st, std::vector<double>& A, std::vector<double>& Y) {
+    const int N = n - 2, W = N / 2 + 3;
+    const int items = std::max(n, 2 * W);
+    hobc_plan_desc q;
+    memset(&q, 0, sizeof(q));
+    q.ndim = 1; q.n[0] = n; q.psf[0] = 1; q.family = HOBC_FAMILY_FOURIER; q.bc_degree = 2;
+    q.L = HOBC_L_IDENTITY; q.prec = HOBC_FP64; q.n_mu = 1; q.batch = items; q.psf_per_item = 0;
+    const double one = 1.0;
+    hobc_plan* ip = nullptr;
+    hobc_status s = hobc_plan_create(&q, &one, st, &ip);
+    if (s != HOBC_OK) return s;
+    std::vector<double> in_real((size_t)items * n, 0.0), in_spec((size_t)items * 2 * W, 0.0);
+    for (int j = 0; j < n; ++j) in_real[(size_t)j * n + j] = 1.0;
+    for (int u = 0; u < 2 * W; ++u) in_spec[(size_t)u * 2 * W + u] = 1.0;     // item u: unit at (c, part) = u
+    double *dr = nullptr, *ds = nullptr, *dout = nullptr;
+    cudaError_t e = cudaMalloc((void**)&dr, in_real.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ds, in_spec.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dout, (size_t)items * std::max(n, 2 * W) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(dr, in_real.data(), in_real.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ds, in_spec.data(), in_spec.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) s = hobc_analysis(ip, dr, dout);
+    if (e == cudaSuccess && s == HOBC_OK) e = cudaStreamSynchronize(st);
+    A.assign((size_t)n * 2 * W, 0.0);
+    if (e == cudaSuccess && s == HOBC_OK) e = cudaMemcpy(A.data(), dout, A.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && s == HOBC_OK) s = hobc_synthesis(ip, ds, dout);
+    if (e == cudaSuccess && s == HOBC_OK) e = cudaStreamSynchronize(st);
+    Y.assign((size_t)2 * W * n, 0.0);
+    if (e == cudaSuccess && s == HOBC_OK) e = cudaMemcpy(Y.data(), dout, Y.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(dr);
+    cudaFree(ds);
+    cudaFree(dout);
+    hobc_plan_destroy(ip);
+    if (s != HOBC_OK) return s;
+    if (e != cudaSuccess) { set_last_error("hobc_plan_create (dense Fourier matrices)", e); return HOBC_ERR_CUDA; }
+    return HOBC_OK;
+}
+
+// Dense split-BF16 mode of the Fourier family (real arithmetic on the tensor
+// cores).  Each complex product is a real GEMM on (re, im) pairs:
+//   2D analysis   rows: C[r][2c+p]  = g[r][:] . M1a[2c+p][:],   M1a = (Re, Im) of T1^{-1} on the stored half;
+//                 stored transposed, so row c of the result holds (Re | Im) of column c over r;
+//                 columns: ghat[c][2t0+p] = [Re | Im](c) . M0a[2t0+p][:], M0a the real form of T0^{-1};
+//   2D synthesis  columns: Y[2r+p][c] = M0s[2r+p][:] . X[c][:] (X interleaved (t0, part)), M0s the real
+//                 form of T0; rows 2r, 2r+1 of Y read as one row of (Re | Im) over c;
+//                 rows: f[r][j] = M1s[j][:] . Y(r), M1s[j][(p, c)] the FP64 synthesis of a unit at (c, p);
+//   1D            the last-axis products alone, with K interleaved (c, part).
+// The matrices are the FP64 path's own responses to unit inputs (fourier_unit_responses).
+static hobc_status dense_prepare_fourier(hobc_plan_s* p) {
+    hobc_dense_s* d = p->dense;
+    d->fourier = 1;
+    const int B = p->desc.batch;
+    const int nl = d->n[p->nax - 1];
+    const int W = p->ax[p->nax - 1].W;
+    d->W = W;
+    cudaError_t e = cudaSuccess;
+    auto alloc2 = [&](__nv_bfloat16** hi, __nv_bfloat16** lo, size_t elems) {
+        if (e == cudaSuccess) e = cudaMalloc((void**)hi, elems * 2);
+        if (e == cudaSuccess) e = cudaMalloc((void**)lo, elems * 2);
+        if (e == cudaSuccess) e = cudaMemset(*hi, 0, elems * 2);
+        if (e == cudaSuccess) e = cudaMemset(*lo, 0, elems * 2);
+    };
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(d->err, 0, sizeof(int));
+    const long long kl = d->kp[p->nax - 1];                  // K of the last axis (samples j)
+    d->kw = pad_to(W, tc::BK);
+    std::vector<std::vector<double>> host(4);
+    std::vector<int> mrows(4, 0), mcols(4, 0);
+    // last axis: analysis rows (2c + p) over j; synthesis columns over (c, p)
+    std::vector<double> A1, Y1;
+    hobc_status s = fourier_unit_responses(nl, p->stream, A1, Y1);
+    if (s != HOBC_OK) return s;
+    {
+        const long long rows = pad_to(2 * W, tc::BN);
+        d->m_ld[0] = kl;
+        alloc2(&d->m_hi[0], &d->m_lo[0], (size_t)rows * kl);
+        host[0].assign((size_t)2 * W * nl, 0.0);
+        for (int c = 0; c < W; ++c)
+            for (int j = 0; j < nl; ++j) {
+                host[0][(size_t)(2 * c) * nl + j] = A1[((size_t)j * W + c) * 2];
+                host[0][(size_t)(2 * c + 1) * nl + j] = A1[((size_t)j * W + c) * 2 + 1];
+            }
+        mrows[0] = 2 * W; mcols[0] = nl;
+    }
+    if (p->nax == 1) {
+        // synthesis: f[item][j] = X[item][2c + p] . M[j][2c + p]
+        d->k2 = pad_to(2 * W, tc::BK);
+        const long long rows = pad_to(nl, tc::BN);
+        d->m_ld[2] = d->k2;
+        alloc2(&d->m_hi[2], &d->m_lo[2], (size_t)rows * d->k2);
+        host[2].assign((size_t)nl * 2 * W, 0.0);
+        for (int j = 0; j < nl; ++j)
+            for (int u = 0; u < 2 * W; ++u) host[2][(size_t)j * 2 * W + u] = Y1[(size_t)u * nl + j];
+        mrows[2] = nl; mcols[2] = 2 * W;
+        const long long wrows = pad_to(B, tc::BM) + tc::BM;   // a chunk's last tile may run past the batch
+        d->w_ld[0] = kl; d->w_bs[0] = 0;
+        alloc2(&d->w_hi[0], &d->w_lo[0], (size_t)wrows * kl);
+        d->w_ld[2] = d->k2; d->w_bs[2] = 0;
+        alloc2(&d->w_hi[2], &d->w_lo[2], (size_t)wrows * d->k2);
+    } else {
+        const int n0 = d->n[0], n1 = d->n[1];
+        const long long k0 = d->kp[0];
+        d->k2 = pad_to(2 * n0, tc::BK);
+        // synthesis rows: M1s[j][p * kw + c] = Y1[2c + p][j]
+        {
+            const long long rows = pad_to(n1, tc::BM);
+            d->m_ld[3] = 2 * d->kw;
+            alloc2(&d->m_hi[3], &d->m_lo[3], (size_t)rows * 2 * d->kw);
+            host[3].assign((size_t)n1 * 2 * d->kw, 0.0);
+            for (int j = 0; j < n1; ++j)
+                for (int c = 0; c < W; ++c)
+                    for (int pp = 0; pp < 2; ++pp)
+                        host[3][(size_t)j * 2 * d->kw + pp * d->kw + c] = Y1[(size_t)(2 * c + pp) * n1 + j];
+            mrows[3] = n1; mcols[3] = (int)(2 * d->kw);
+        }
+        // axis 0: the full complex T0^{-1} and T0 from the unit responses of a 1D axis of n0
+        std::vector<double> A0, Y0;
+        s = fourier_unit_responses(n0, p->stream, A0, Y0);
+        if (s != HOBC_OK) return s;
+        const int N0 = n0 - 2, W0 = N0 / 2 + 3;
+        auto t_of = [&](int c) { return c == W0 - 1 ? n0 - 1 : c; };
+        auto self_of = [&](int c) { return c == 0 || c == W0 - 1 || c == 1 || 2 * (c - 1) == N0; };
+        auto neg = [&](int t) { return (t == 0 || t == n0 - 1) ? t : 1 + (N0 - (t - 1)) % N0; };
+        std::vector<double> Tir((size_t)n0 * n0), Tii((size_t)n0 * n0), Tr((size_t)n0 * n0), Ti((size_t)n0 * n0);
+        for (int c = 0; c < W0; ++c) {
+            const int t = t_of(c), tn = neg(t);
+            for (int r = 0; r < n0; ++r) {
+                const double re = A0[((size_t)r * W0 + c) * 2], im = A0[((size_t)r * W0 + c) * 2 + 1];
+                Tir[(size_t)t * n0 + r] = re; Tii[(size_t)t * n0 + r] = im;           // T0^{-1}[t][r]
+                if (!self_of(c)) { Tir[(size_t)tn * n0 + r] = re; Tii[(size_t)tn * n0 + r] = -im; }
+                const double yr = Y0[(size_t)(2 * c) * n0 + r], yi = Y0[(size_t)(2 * c + 1) * n0 + r];
+                if (self_of(c)) {
+                    Tr[(size_t)r * n0 + t] = yr; Ti[(size_t)r * n0 + t] = 0.0;         // T0[r][t]
+                } else {
+                    Tr[(size_t)r * n0 + t] = 0.5 * yr; Ti[(size_t)r * n0 + t] = -0.5 * yi;
+                    Tr[(size_t)r * n0 + tn] = 0.5 * yr; Ti[(size_t)r * n0 + tn] = 0.5 * yi;
+                }
+            }
+        }
+        // analysis columns: M0a[2t0 + po][pi * k0 + r]
+        {
+            const long long rows = pad_to(2 * n0, tc::BN);
+            d->m_ld[1] = 2 * k0;
+            alloc2(&d->m_hi[1], &d->m_lo[1], (size_t)rows * 2 * k0);
+            host[1].assign((size_t)2 * n0 * 2 * k0, 0.0);
+            for (int t = 0; t < n0; ++t)
+                for (int r = 0; r < n0; ++r) {
+                    const double re = Tir[(size_t)t * n0 + r], im = Tii[(size_t)t * n0 + r];
+                    double* row0 = &host[1][(size_t)(2 * t) * 2 * k0];
+                    double* row1 = &host[1][(size_t)(2 * t + 1) * 2 * k0];
+                    row0[r] = re; row0[k0 + r] = -im;
+                    row1[r] = im; row1[k0 + r] = re;
+                }
+            mrows[1] = 2 * n0; mcols[1] = (int)(2 * k0);
+        }
+        // synthesis columns: M0s[2r + po][2t0 + pi]
+        {
+            const long long rows = pad_to(2 * n0, tc::BM);
+            d->m_ld[2] = d->k2;
+            alloc2(&d->m_hi[2], &d->m_lo[2], (size_t)rows * d->k2);
+            host[2].assign((size_t)2 * n0 * d->k2, 0.0);
+            for (int r = 0; r < n0; ++r)
+                for (int t = 0; t < n0; ++t) {
+                    const double re = Tr[(size_t)r * n0 + t], im = Ti[(size_t)r * n0 + t];
+                    double* row0 = &host[2][(size_t)(2 * r) * d->k2];
+                    double* row1 = &host[2][(size_t)(2 * r + 1) * d->k2];
+                    row0[2 * t] = re; row0[2 * t + 1] = -im;
+                    row1[2 * t] = im; row1[2 * t + 1] = re;
+                }
+            mrows[2] = 2 * n0; mcols[2] = (int)d->k2;
+        }
+        // operand workspace (per problem)
+        const long long r0 = pad_to(n0, tc::BM), rw = pad_to(W, tc::BM), rwb = pad_to(W, tc::BN), r0b = pad_to(n0, tc::BN);
+        d->w_ld[0] = kl;          d->w_bs[0] = r0 * kl;              // g split (A)
+        d->w_ld[1] = 2 * k0;      d->w_bs[1] = rw * 2 * k0;          // row-pass output, read as [c][(p, r)] (A)
+        d->w_ld[2] = d->k2;       d->w_bs[2] = rwb * d->k2;          // filtered spectrum [c][(t0, p)] (B)
+        d->w_ld[3] = 2 * d->kw;   d->w_bs[3] = r0b * 2 * d->kw;      // column-synthesis output, read as [r][(p, c)] (B)
+        for (int w = 0; w < 4; ++w) alloc2(&d->w_hi[w], &d->w_lo[w], (size_t)B * d->w_bs[w]);
+    }
+    if (e != cudaSuccess) { set_last_error("hobc_plan_create (dense)", e); return HOBC_ERR_CUDA; }
+    for (int m = 0; m < 4 && e == cudaSuccess; ++m) {
+        if (host[m].empty()) continue;
+        double* dev = nullptr;
+        e = cudaMalloc((void**)&dev, host[m].size() * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemcpy(dev, host[m].data(), host[m].size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            tc::k_split_f64<<<1024, 256, 0, p->stream>>>(dev, mcols[m], mrows[m], mcols[m], d->m_hi[m], d->m_lo[m],
+                                                         d->m_ld[m]);
+            e = cudaStreamSynchronize(p->stream);
+        }
+        cudaFree(dev);
+    }
+    if (e != cudaSuccess) { set_last_error("hobc_plan_create (dense)", e); return HOBC_ERR_CUDA; }
+    return HOBC_OK;
+}
+
 void dense_free(hobc_plan_s* p) {
     hobc_dense_s* d = p->dense;
     if (!d) return;
@@ -488,6 +736,7 @@ hobc_status dense_prepare(hobc_plan_s* p) {
         d->n[a] = p->ax[a].n;
         d->kp[a] = pad_to(d->n[a], tc::BK);
     }
+    if (p->fam == HOBC_FAMILY_FOURIER) return dense_prepare_fourier(p);
     cudaError_t e = cudaSuccess;
     auto alloc2 = [&](__nv_bfloat16** hi, __nv_bfloat16** lo, size_t elems) {
         if (e == cudaSuccess) e = cudaMalloc((void**)hi, elems * 2);
@@ -606,8 +855,40 @@ hobc_status dense_prepare(hobc_plan_s* p) {
     return HOBC_OK;
 }
 
+// Fourier family (see dense_prepare_fourier): g real -> half spectrum [c][t0] (re, im).
+static hobc_status dense_analysis_fourier(hobc_plan_s* p, const float* gf, float* out) {
+    hobc_dense_s* d = p->dense;
+    const int B = p->desc.batch;
+    const size_t z0 = p->item0;
+    const int W = d->W;
+    if (d->nax == 1) {
+        const int n = d->n[0];
+        hobc_status s = hobc_tc_split(gf, n, 0, B, n, d->w_hi[0] + z0 * d->w_ld[0], d->w_lo[0] + z0 * d->w_ld[0],
+                                      d->w_ld[0], 0, B, 1, p->stream);
+        if (s != HOBC_OK) return s;
+        ++p->launches;
+        return gemm(p, d->w_hi[0] + z0 * d->w_ld[0], d->w_lo[0] + z0 * d->w_ld[0], d->w_ld[0], 0, d->m_hi[0],
+                    d->m_lo[0], d->m_ld[0], 0, B, 2 * W, d->kp[0], 1, HOBC_TC_OUT_F32, out, nullptr, nullptr, 2 * W, 0);
+    }
+    const int n0 = d->n[0], n1 = d->n[1];
+    hobc_status s = hobc_tc_split(gf, n1, (long long)n0 * n1, n0, n1, d->w_hi[0] + z0 * d->w_bs[0],
+                                  d->w_lo[0] + z0 * d->w_bs[0], d->w_ld[0], d->w_bs[0], n0, B, p->stream);
+    if (s != HOBC_OK) return s;
+    ++p->launches;
+    // rows: C[r][2c + p] = sum_j g[r][j] M1a[2c + p][j], stored transposed: row 2c + p of length k0
+    s = gemm(p, d->w_hi[0] + z0 * d->w_bs[0], d->w_lo[0] + z0 * d->w_bs[0], d->w_ld[0], d->w_bs[0], d->m_hi[0],
+             d->m_lo[0], d->m_ld[0], 0, n0, 2 * W, d->kp[1], B, HOBC_TC_OUT_SPLIT_T, nullptr,
+             d->w_hi[1] + z0 * d->w_bs[1], d->w_lo[1] + z0 * d->w_bs[1], d->kp[0], d->w_bs[1]);
+    if (s != HOBC_OK) return s;
+    // columns: ghat[c][2t0 + p] = sum_(q, r) R[c][(q, r)] M0a[2t0 + p][(q, r)]
+    return gemm(p, d->w_hi[1] + z0 * d->w_bs[1], d->w_lo[1] + z0 * d->w_bs[1], d->w_ld[1], d->w_bs[1], d->m_hi[1],
+                d->m_lo[1], d->m_ld[1], 0, W, 2 * n0, 2 * d->kp[0], B, HOBC_TC_OUT_F32, out, nullptr, nullptr,
+                2 * n0, (long long)W * 2 * n0);
+}
+
 hobc_status dense_analysis(hobc_plan_s* p, const void* g, void* ghat) {
     hobc_dense_s* d = p->dense;
+    if (d->fourier) return dense_analysis_fourier(p, static_cast<const float*>(g), static_cast<float*>(ghat));
     const int B = p->desc.batch;
     const size_t z0 = p->item0;
     const float* gf = static_cast<const float*>(g);
@@ -637,12 +918,50 @@ hobc_status dense_analysis(hobc_plan_s* p, const void* g, void* ghat) {
                 (long long)n0 * n1);
 }
 
+// Fourier family: filter (complex) + split, then the synthesis products.
+static hobc_status dense_filter_synthesis_fourier(hobc_plan_s* p, const float2* spec, const FilterDesc& fd,
+                                                  float* f) {
+    hobc_dense_s* d = p->dense;
+    const int B = p->desc.batch;
+    const size_t z0 = p->item0;
+    const int W = d->W;
+    if (d->nax == 1) {
+        const int n = d->n[0];
+        tc::k_filter_split_cplx<<<1024, 256, 0, p->stream>>>(spec, (long long)p->spec_elems, 1, W, 1, axis0(p), fd, B,
+                                                              d->w_hi[2] + z0 * d->w_ld[2], d->w_lo[2] + z0 * d->w_ld[2],
+                                                              d->w_ld[2], 0);
+        hobc_status s = check("k_filter_split_cplx");
+        if (s != HOBC_OK) return s;
+        ++p->launches;
+        return gemm(p, d->w_hi[2] + z0 * d->w_ld[2], d->w_lo[2] + z0 * d->w_ld[2], d->w_ld[2], 0, d->m_hi[2],
+                    d->m_lo[2], d->m_ld[2], 0, B, n, d->k2, 1, HOBC_TC_OUT_F32, f, nullptr, nullptr, n, 0);
+    }
+    const int n0 = d->n[0], n1 = d->n[1];
+    tc::k_filter_split_cplx<<<1024, 256, 0, p->stream>>>(spec, (long long)p->spec_elems, W, n0, 2, axis0(p), fd, B,
+                                                          d->w_hi[2] + z0 * d->w_bs[2], d->w_lo[2] + z0 * d->w_bs[2],
+                                                          d->w_ld[2], d->w_bs[2]);
+    hobc_status s = check("k_filter_split_cplx");
+    if (s != HOBC_OK) return s;
+    ++p->launches;
+    // columns: Y[2r + p][c] = sum_(t0, q) M0s[2r + p][(t0, q)] X[c][(t0, q)]
+    s = gemm(p, d->m_hi[2], d->m_lo[2], d->m_ld[2], 0, d->w_hi[2] + z0 * d->w_bs[2], d->w_lo[2] + z0 * d->w_bs[2],
+             d->w_ld[2], d->w_bs[2], 2 * n0, W, d->k2, B, HOBC_TC_OUT_SPLIT, nullptr, d->w_hi[3] + z0 * d->w_bs[3],
+             d->w_lo[3] + z0 * d->w_bs[3], d->kw, d->w_bs[3]);
+    if (s != HOBC_OK) return s;
+    // rows: f[r][j] = sum_(q, c) M1s[j][(q, c)] Y(r)[(q, c)], computed as C[j][r] and stored transposed
+    return gemm(p, d->m_hi[3], d->m_lo[3], d->m_ld[3], 0, d->w_hi[3] + z0 * d->w_bs[3], d->w_lo[3] + z0 * d->w_bs[3],
+                d->w_ld[3], d->w_bs[3], n1, n0, 2 * d->kw, B, HOBC_TC_OUT_F32_T, f, nullptr, nullptr, n1,
+                (long long)n0 * n1);
+}
+
 hobc_status dense_filter_synthesis(hobc_plan_s* p, const void* ghat, const void* D, const int* mu_idx,
                                    const double* mu_val, void* f) {
     hobc_dense_s* d = p->dense;
     const int B = p->desc.batch;
     const size_t z0 = p->item0;
     const FilterDesc fd = filter_desc(p, D, mu_idx, mu_val);
+    if (d->fourier)
+        return dense_filter_synthesis_fourier(p, static_cast<const float2*>(ghat), fd, static_cast<float*>(f));
     const int rows = d->nax == 2 ? d->n[1] : 1, cols = d->nax == 2 ? d->n[0] : d->n[0];
     __nv_bfloat16* xh = d->w_hi[2] + z0 * (d->nax == 2 ? d->w_bs[2] : d->w_ld[2]);
     __nv_bfloat16* xl = d->w_lo[2] + z0 * (d->nax == 2 ? d->w_bs[2] : d->w_ld[2]);

@@ -12,6 +12,9 @@ again.  Two passes (2D) stay below 2^-11 of the absolute product:
   whole path        G within 1e-2 relative; mu* an index whose oracle G is within
                     that of the minimum; f within the analysis bound carried
                     through the filter and |T| plus the synthesis bound.
+The Fourier family runs each complex product as a real product on (re, im)
+pairs, so every output sums twice the terms and a complex entry has two
+rounded parts: its bounds are four times those above (on the modulus).
 """
 import numpy as np
 import pytest
@@ -26,8 +29,24 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 from paper_0906_2704_gb300 import hobc  # noqa: E402
 
-DEG = {"sine": 1, "cosine": 2, "sine3": 3, "reflective": 0, "periodic": 0}
+DEG = {"sine": 1, "cosine": 2, "sine3": 3, "reflective": 0, "periodic": 0, "fourier": 2}
 EPS = 2.0 ** -11
+
+
+def _eps(F):
+    return 4 * EPS if F == "F" else EPS
+
+
+def _stored(F, full):
+    """Oracle spectrum (full layout) -> the stored layout as float32 (re, im pairs for F)."""
+    lay = P.to_layout(F, full).reshape(-1)
+    if F == "F":
+        return np.stack([lay.real, lay.imag], axis=-1)
+    return lay.real
+
+
+def _complex(F, arr):
+    return arr[..., 0] + 1j * arr[..., 1] if F == "F" else arr
 
 
 def _dev(a):
@@ -56,33 +75,41 @@ def _status(plan):
 
 
 @pytest.mark.parametrize("L", ["I", "lap"])
-@pytest.mark.parametrize("fam", ["sine", "cosine", "sine3", "reflective", "periodic"])
+@pytest.mark.parametrize("fam", ["sine", "cosine", "sine3", "reflective", "periodic", "fourier"])
 @pytest.mark.parametrize("ndim,n,taps", [(1, 70, 5), (1, 130, 7), (2, (40, 52), (5, 5)), (2, (66, 34), (7, 7))])
 def test_dense_steps_match_oracle(ndim, n, taps, fam, L):
     F, n, h, g, mus, plan = _case(ndim, fam, n, taps, L)
     batch = g.shape[0]
     S = plan.spec_elems
+    cs = (2,) if plan.spec_complex else ()
     g_d = _dev(g)
-    gh_d = torch.empty((batch, S), dtype=torch.float32, device="cuda")
+    gh_d = torch.empty((batch, S) + cs, dtype=torch.float32, device="cuda")
     plan.analysis(g_d, gh_d)
     y_d = torch.empty(g.shape, dtype=torch.float32, device="cuda")
     rng = np.random.default_rng(1)
     c = _r32(rng.standard_normal((batch,) + n))                 # a spectrum in the oracle's full layout
-    c_d = _dev(np.stack([P.to_layout(F, c[b]).reshape(-1) for b in range(batch)]))
+    if F == "F":                                                # the half spectrum of a real signal
+        c = np.stack([O.analysis_1d(F, c[b]) if ndim == 1 else O.analysis_2d(F, c[b]) for b in range(batch)])
+        c = _r32(c.real) + 1j * _r32(c.imag)
+    c_d = _dev(np.stack([_stored(F, c[b]) for b in range(batch)]))
     plan.synthesis(c_d, y_d)
     _status(plan)
-    gh, y = gh_d.cpu().numpy().astype(np.float64), y_d.cpu().numpy().astype(np.float64)
+    gh, y = _complex(F, gh_d.cpu().numpy().astype(np.float64)), y_d.cpu().numpy().astype(np.float64)
+    eps = _eps(F)
     for b in range(batch):
         ref = O.analysis_1d(F, g[b]) if ndim == 1 else O.analysis_2d(F, g[b])
-        bound = EPS * P.abs_apply(F, g[b], inverse=True) + 1e-30
-        got = gh[b].reshape(P.to_layout(F, ref).shape)
-        assert np.all(np.abs(got - P.to_layout(F, ref)) <= P.to_layout(F, bound)), f"analysis item {b}"
+        bound = eps * P.abs_apply(F, g[b], inverse=True) + 1e-30
+        want = P.to_layout(F, ref if F == "F" else ref.real)
+        got = gh[b].reshape(want.shape)
+        assert np.all(np.abs(got - want) <= P.to_layout(F, bound)), \
+            f"analysis item {b}: {np.max(np.abs(got - want) / P.to_layout(F, bound)):.2f} of bound"
         yref = (O.synthesis_1d(F, c[b]) if ndim == 1 else O.synthesis_2d(F, c[b])).real
-        ybound = EPS * P.abs_apply(F, c[b]) + 1e-30
-        assert np.all(np.abs(y[b] - yref) <= ybound), f"synthesis item {b}"
+        ybound = eps * P.abs_apply(F, c[b]) + 1e-30
+        assert np.all(np.abs(y[b] - yref) <= ybound), \
+            f"synthesis item {b}: {np.max(np.abs(y[b] - yref) / ybound):.2f} of bound"
 
 
-@pytest.mark.parametrize("fam", ["sine", "cosine", "sine3", "reflective", "periodic"])
+@pytest.mark.parametrize("fam", ["sine", "cosine", "sine3", "reflective", "periodic", "fourier"])
 @pytest.mark.parametrize("ndim,n,taps", [(1, 90, 5), (2, (48, 40), (5, 5))])
 def test_dense_deblur_matches_oracle(ndim, n, taps, fam):
     F, n, h, g, mus, plan = _case(ndim, fam, n, taps, "lap", batch=4, K=32, seed=3)
@@ -99,9 +126,9 @@ def test_dense_deblur_matches_oracle(ndim, n, taps, fam):
         k = int(mi[b])
         assert k == ko or Go[k] <= (1 + 2e-2) * Go.min(), f"mu* item {b}"
         phi = np.abs(O.filter_factors(d, s, mus[k]))
-        dg = EPS * P.abs_apply(F, g[b], inverse=True)
+        dg = _eps(F) * P.abs_apply(F, g[b], inverse=True)
         X = O.filter_factors(d, s, mus[k]) * ghat
-        bound = P.abs_apply(F, phi * dg) + EPS * P.abs_apply(F, X) + 1e-30
+        bound = P.abs_apply(F, phi * dg) + _eps(F) * P.abs_apply(F, X) + 1e-30
         fo = P.oracle_filtered(F, ndim, ghat, d, s, mus[k])
         assert np.all(np.abs(f[b] - fo) <= bound), f"f item {b}: {np.max(np.abs(f[b] - fo) / bound):.2f} of bound"
 
@@ -131,7 +158,6 @@ def test_comparison_families_need_the_dense_mode_and_degree_zero():
         hobc.Plan(2, (32, 32), (5, 5), 0, synth.mu_grid(8), prec="split_bf16", family="periodic")
 
 
-def test_dense_mode_rejects_the_fourier_family():
-    with pytest.raises(hobc.HobcError) as e:
-        hobc.Plan(2, (32, 32), (5, 5), 2, synth.mu_grid(8), prec="split_bf16", family="fourier")
-    assert e.value.status == hobc.STATUS.index("HOBC_ERR_UNSUPPORTED")
+def test_dense_fourier_plan_for_a_nonsymmetric_psf():
+    plan = hobc.Plan(2, (32, 32), (5, 5), 2, synth.mu_grid(8), prec="split_bf16", family="auto")
+    assert plan.family == "fourier" and plan.spec_complex
