@@ -366,6 +366,41 @@ def run_ours(args):
                            "exact": float(np.median(mus[mi_x.cpu().numpy()]))},
              "rre_mean": {"approximate": float(r_full.mean()), "exact": float(r_x.mean())},
              "clocks": clk_x}
+    # the learned choice of mu (histogram features), its network trained here, outside
+    # the timed region, on GCV labels of problems drawn on the GPU like this workload
+    # (rotated anisotropic Gaussian PSFs of random shape, noise log-uniform in [1e-3, 3e-2])
+    from paper_0906_2704_gb300 import learned as LR
+    t_tr = time.time()
+    plan_tr = hobc.Plan(2, (N_SIDE, N_SIDE), h.shape, 2, mus, L="I", prec="fp32" if prec != "fp64" else "fp64",
+                        family="fourier", batch=16, psf_per_item=True, stream=stream)
+    Xtr, ttr = LR.training_set(plan_tr, args.learned_train, 5, "rotated", h.shape[0], kind="hist", chunk=128)
+    net = LR.init_network(Xtr, 256, seed=0, stream=stream.cuda_stream, kind="hist")
+    hist_l = LR.fit(net, Xtr, ttr, epochs=60, batch=128, lr=1e-3)
+    plan_tr.close()
+    torch.cuda.synchronize()
+    t_tr = time.time() - t_tr
+    f_l = torch.empty_like(g_d)
+    mu_l = torch.empty(B, dtype=torch.float64, device=dev)
+    fb_l = torch.empty(B, dtype=torch.int32, device=dev)
+    ms_l, clk_l = _timed(lambda: plan.deblur_learned(net, g_d, h_d, f_l, mu_l, fb_l), stream, args.steps,
+                         args.warmup)
+    learned_launches = plan.last_launch_count
+    ms_l = max_over_ranks(ms_l, dist, dev)
+    r_l = rre(f_l)
+    grid_mu = torch.from_numpy(mus).to(dev)[mi_d.long()]
+    learned_arm = {"value": whole_job_rate(world, B, args.steps, ms_l / 1e3), "unit": "deblurs/s",
+                   "ms_per_step": ms_l / args.steps, "gpu_launches": learned_launches * args.steps,
+                   "fallback_rate": float(fb_l.float().mean()),
+                   "mu_ratio_to_full_scan": {"median": float((mu_l / grid_mu).median()),
+                                             "max_abs_log10": float((mu_l / grid_mu).log10().abs().max())},
+                   "rre_mean": {"full_scan": float(r_full.mean()), "learned": float(r_l.mean())},
+                   "rre_ratio_to_full_scan": float(r_l.mean() / r_full.mean()),
+                   "speedup_vs_full_scan": ms / ms_l,
+                   "train": {"problems": int(Xtr.shape[0]), "seconds": t_tr, "epochs": 60,
+                             "loss_first": hist_l[0], "loss_last": hist_l[-1], "features": "hist"},
+                   "clocks": clk_l}
+    del Xtr, ttr
+
     r_xs = rre(f_xs)
     exact_search = {"value": whole_job_rate(world, B, args.steps, ms_xs / 1e3), "unit": "deblurs/s",
                     "ms_per_step": ms_xs / args.steps, "gpu_launches": search_launches * args.steps,
@@ -471,6 +506,9 @@ def run_ours(args):
         sec = oracle_seconds_per_image(h, g, mus, n_img, keep=kept)
         cpu = {"value": 1.0 / sec, "unit": "deblurs/s", "cores": blas_threads(), "kind": "oracle",
                "sample": f"{n_img} images of the same workload, dense FP64 oracle (separable mode)"}
+        sec1 = single_core_oracle_seconds(1)
+        cpu["single_core"] = {"value": (1.0 / sec1) if sec1 else None, "unit": "deblurs/s", "cores": 1,
+                              "sample": "1 image of the same workload, one BLAS thread"}
         oracle_error = default_oracle_error(kept, h, mus, f_d, mi_d, G_grid, f_b, mi_b, f_r, mu_r, G_ref,
                                             f_x, mi_x, G_x, f_xs, mi_xs)
 
@@ -484,6 +522,7 @@ def run_ours(args):
                        "l2": "inputs+outputs %.0f MB per step > 129 MB L2 (no flush)" % (2 * B * N_SIDE ** 2 * esz / 1e6)},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
             "hbm_roofline": hbm, "steps_ms": steps_ms, "cpu_baseline": cpu, "clocks": clocks,
+            "learned_mu": learned_arm,
             "binned_mu": binned, "refined_mu": refined, "exact_gcv": exact, "exact_gcv_search": exact_search,
             "oracle_error": oracle_error, "precision": prec, "transform_roofline": transform_roofline,
         }
@@ -566,6 +605,55 @@ def _timed(step, stream, steps, warmup):
         b.record(stream)
         torch.cuda.synchronize()
     return a.elapsed_time(b), clk.summary()
+
+
+def oracle_error_items(samples, K):
+    """Errors of sampled problems of a workload against the FP64 oracle.  samples:
+    (family letter, h, g, L, mus, f_gpu, k_gpu, G_gpu or None) per problem (1D, 2D or
+    3D); the oracle deblurs g, then filters its own spectrum at the GPU's grid index."""
+    from oracle import hobc_oracle as O
+    from oracle import volume_oracle as V
+    f_err, g_err, agree = [], [], []
+    for fam, h, g, L, mus, f_gpu, k_gpu, G_gpu in samples:
+        if g.ndim == 1:
+            f_o, G_o, k_o, ghat = O.deblur_1d(fam, h, g, L, mus)
+        elif g.ndim == 2:
+            f_o, G_o, k_o, ghat = O.deblur_2d(fam, h, g, L, mus)
+        else:
+            f_o, G_o, k_o, ghat = V.deblur_3d(fam, h, g, L, mus)
+        if int(k_gpu) != int(k_o):
+            if g.ndim == 1:
+                d, s_ = O.eigenvalues_1d(fam, h, g.shape[0]), O.smoothing_1d(fam, g.shape[0], L)
+                f_o = O.synthesis_1d(fam, O.filter_factors(d, s_, mus[k_gpu]) * ghat).real
+            elif g.ndim == 2:
+                f_o = oracle_f_2d(fam, h, ghat, L, float(mus[k_gpu]))
+            else:
+                d, s_ = V.eigenvalues_3d(fam, h, *g.shape), V.smoothing_3d(fam, *g.shape, L)
+                f_o = V.synthesis_3d(fam, O.filter_factors(d, s_, mus[k_gpu]) * ghat).real
+        f_err.append(rel2(f_gpu, f_o))
+        agree.append(int(k_gpu) == int(k_o))
+        if G_gpu is not None:
+            g_err.append(float(np.max(np.abs(np.asarray(G_gpu) - G_o) / G_o)))
+    out = {"problems": len(samples), "reference": "dense FP64 oracle on the same g",
+           "f_rel_2norm_max": max(f_err), "mu_index_agreement": float(np.mean(agree))}
+    if g_err:
+        out["G_rel_max"] = max(g_err)
+    return out
+
+
+def single_core_oracle_seconds(n_img: int = 1) -> float | None:
+    """The 1024^2 oracle deblur on one host core: a child process with every BLAS
+    pool held to one thread (the pools read these variables when numpy loads)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    code = ("import sys, time; sys.path.insert(0, %r); import bench; from paper_0906_2704_gb300 import synth; "
+            "h, g, _ = bench.make_inputs(%d, seed=11, distinct=%d); mus = synth.mu_grid(bench.K_MU); "
+            "print(bench.oracle_seconds_per_image(h, g, mus, %d))") % (ROOT, n_img, n_img, n_img)
+    try:
+        res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+        return float(res.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
 
 
 def run_other(args):
@@ -722,6 +810,38 @@ def run_other(args):
                                      "achieved": flops / t_s / 1e12, "peak": pk, "unit": "TFLOP/s",
                                      "frac": flops / t_s / 1e12 / pk if pk else None, "traffic": None,
                                      "flops_per_step": flops}
+    if rank == 0 and not args.no_cpu_baseline:
+        # error against the FP64 oracle on a sample of the workload's problems
+        mus_w = synth.mu_grid(K)
+        G_d = torch.empty((mi.numel(), K), dtype=torch.float64, device=dev)
+        samples = []
+        if args.workload == "batched":
+            batch.deblur(g, h, f, mi, G_d)
+            torch.cuda.synchronize()      # the plan runs on its own stream
+            offs = np.concatenate([[0], np.cumsum([it[0] * it[1] for it in items])])
+            fam_of = {1: "S", 2: "C", 3: "S3"}
+            fn, Gn, kn = f.cpu().numpy(), G_d.cpu().numpy(), mi.cpu().numpy()
+            for deg in (1, 2, 3):           # the two smallest problems of each degree
+                idx = sorted([i for i, it in enumerate(items) if it[4] == deg], key=lambda i: items[i][0])[:2]
+                for i in idx:
+                    nn = items[i][0]
+                    samples.append((fam_of[deg], hs[i], gs[i], "lap", mus_w,
+                                    fn[offs[i]:offs[i + 1]].reshape(nn, nn), kn[i], Gn[i]))
+        elif args.workload == "signals1d":
+            plan.deblur(g, h, f, mi, G_d)
+            torch.cuda.synchronize()      # the plan runs on its own stream
+            fn, Gn, kn = f[:8].cpu().numpy(), G_d[:8].cpu().numpy(), mi[:8].cpu().numpy()
+            samples = [("S", hh, gg[i], "I", mus_w, fn[i], kn[i], Gn[i]) for i in range(8)]
+        elif args.workload == "volume128":
+            vol.deblur(g, h, f, mi, G_d)
+            torch.cuda.synchronize()      # the plan runs on its own stream
+            samples = [("C", hh, gg[0], "lap", mus_w, f[0].cpu().numpy(), int(mi[0]), G_d[0].cpu().numpy())]
+        else:
+            plan.deblur(g, h, f, mi, G_d)
+            torch.cuda.synchronize()      # the plan runs on its own stream
+            fn, Gn, kn = f[:2].cpu().numpy(), G_d[:2].cpu().numpy(), mi[:2].cpu().numpy()
+            samples = [("C", hh, gg[i], "lap", mus_w, fn[i], kn[i], Gn[i]) for i in range(2)]
+        extra["oracle_error"] = oracle_error_items(samples, K)
     peaks, kind = measured_peaks()
     sec = ms / args.steps / 1e3
     if rank != 0:
@@ -745,158 +865,113 @@ def run_other(args):
     return 0
 
 
-def _learned_chunk(seed: int, count: int, n: int, taps: int, truth: bool):
-    """One worker's share of the learned-mu problems (float32 to keep transfers small)."""
-    from paper_0906_2704_gb300 import synth
-    g, ft, h, eta = synth.learned_set(seed, count, n, taps)
-    return g.astype(np.float32), (ft.astype(np.float32) if truth else None), h.astype(np.float32), eta
-
-
-def _learned_data(pool, seed: int, count: int, n: int, taps: int, truth: bool, per: int = 64):
-    jobs = [(seed * 100003 + i, min(per, count - i * per), n, taps, truth) for i in range((count + per - 1) // per)]
-    parts = pool.starmap(_learned_chunk, jobs)
-    g = np.concatenate([p[0] for p in parts])
-    ft = np.concatenate([p[1] for p in parts]) if truth else None
-    h = np.concatenate([p[2] for p in parts])
-    eta = np.concatenate([p[3] for p in parts])
-    return g, ft, h, eta
-
-
 def run_learned(args):
     """Learned choice of mu against the full GCV scan, at equal relative error.
 
-    Problems: images as in the other 2D workloads blurred by out-of-focus disks
-    (radius U[1.5, 5], 11 x 11 PSF array, one per image), noise log-uniform in
-    [1e-3, 3e-2]; degree 2 (cosine family), Laplacian, 256 mu in [1e-8, 1], FP32.
-    The network is trained here (outside the timed region) on GCV labels of
-    ``--train`` problems at 256^2 and timed on 1024 other problems at 256^2
-    (plus a 1024^2 pass of 64 problems)."""
-    import multiprocessing as mp
-    cores = os.cpu_count() or 1
-    n, taps, K = 256, 11, 256
-    t0 = time.time()
-    with mp.get_context("spawn").Pool(min(16, cores)) as pool:      # before the first GPU call
-        gtr, _, htr, _ = _learned_data(pool, 1, args.train, n, taps, False)
-        gte, fte, hte, etate = _learned_data(pool, 2, 1024, n, taps, True)
-        gbig, fbig, hbig, _ = _learned_data(pool, 3, 64, 1024, taps, True, per=4)
-    t_data = time.time() - t0
+    Problems (drawn on the GPU, learned.gpu_problems): images as in the other 2D
+    workloads blurred by out-of-focus disks (radius U[1.5, 5], 11 x 11 PSF array,
+    one per image), noise log-uniform in [1e-3, 3e-2]; degree 2 (cosine family),
+    Laplacian, 256 mu in [1e-8, 1], FP32.  The network (histogram features,
+    hobc_features_hist) is trained here, outside the timed region, on GCV labels
+    of ``--train`` problems at 256^2; it is timed on 8192 other problems at 256^2
+    and on 8192 at 1024^2 (in chunks of 512, each chunk's three arms timed in
+    turn), against the full scan and the binned choice on the same problems."""
     import torch
     from paper_0906_2704_gb300 import hobc, learned, synth
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
+    n, taps, K = 256, 11, 256
     mus = synth.mu_grid(K)
     B = 512
     plan = hobc.Plan(2, (n, n), (taps, taps), 2, mus, L="lap", prec="fp32", family="cosine", psf_symmetric=True,
                      batch=B, psf_per_item=True, stream=stream)
-    # ---- training (not timed)
+    # ---- training (not timed): data drawn and labelled on the GPU
+    t0 = time.time()
+    Xtr, ttr = learned.training_set(plan, args.train, 1, "disk", taps, kind="hist")
+    torch.cuda.synchronize()
+    t_data = time.time() - t0
     t1 = time.time()
-    Xs, ts = [], []
-    for s in range(0, len(gtr) - B + 1, B):
-        X, t, _ = learned.features_and_labels(plan, torch.from_numpy(gtr[s:s + B]).to(dev),
-                                              torch.from_numpy(htr[s:s + B]).to(dev))
-        Xs.append(X)
-        ts.append(t)
-    Xtr, ttr = torch.cat(Xs), torch.cat(ts)
-    net = learned.init_network(Xtr, 256, seed=0, stream=stream.cuda_stream)
+    net = learned.init_network(Xtr, 256, seed=0, stream=stream.cuda_stream, kind="hist")
     hist = learned.fit(net, Xtr, ttr, epochs=args.epochs, batch=256, lr=1e-3)
     torch.cuda.synchronize()
     t_train = time.time() - t1
-    # ---- inference: learned vs full scan on the same 1024 test problems
-    g_d = torch.from_numpy(gte).to(dev)
-    h_d = torch.from_numpy(hte).to(dev)
-    f_l = torch.empty_like(g_d)
-    f_g = torch.empty_like(g_d)
-    mu_l = torch.empty(len(gte), dtype=torch.float64, device=dev)
-    fb_l = torch.empty(len(gte), dtype=torch.int32, device=dev)
-    mi_g = torch.empty(len(gte), dtype=torch.int32, device=dev)
-    chunks = [slice(s, s + B) for s in range(0, len(gte), B)]
-
-    def step_learned():
-        for c in chunks:
-            plan.deblur_learned(net, g_d[c], h_d[c], f_l[c], mu_l[c], fb_l[c])
-
-    def step_gcv():
-        for c in chunks:
-            plan.deblur(g_d[c], h_d[c], f_g[c], mi_g[c])
-
-    f_b = torch.empty_like(g_d)
-    mi_b = torch.empty(len(gte), dtype=torch.int32, device=dev)
-    fb_b = torch.empty(len(gte), dtype=torch.int32, device=dev)
-
-    def step_binned():
-        for c in chunks:
-            plan.deblur_binned(g_d[c], h_d[c], f_b[c], mi_b[c], fb_b[c])
-
-    ms_l, clk_l = _timed(step_learned, stream, args.steps, args.warmup)
-    launches = plan.last_launch_count * len(chunks)
-    ms_g, clk_g = _timed(step_gcv, stream, args.steps, args.warmup)
-    ms_b, clk_b = _timed(step_binned, stream, args.steps, args.warmup)
 
     def rre(f, ft):
-        d = (f.astype(np.float64) - ft).reshape(len(ft), -1)
-        return np.linalg.norm(d, axis=1) / np.linalg.norm(ft.reshape(len(ft), -1), axis=1)
+        d = (f.double() - ft.double()).flatten(1)
+        return (d.norm(dim=1) / ft.double().flatten(1).norm(dim=1)).cpu().numpy()
 
-    r_l, r_g = rre(f_l.cpu().numpy(), fte), rre(f_g.cpu().numpy(), fte)
-    r_b = rre(f_b.cpu().numpy(), fte)
-    fb = fb_l.cpu().numpy()
-    lab = np.log10(mus)[mi_g.cpu().numpy()]
-    pred_err = np.abs(np.log10(mu_l.cpu().numpy()) - lab)
-    # ---- the same network on 64 problems at 1024^2 (a size it was not trained on)
-    Bb = 16
-    plan_b = hobc.Plan(2, (1024, 1024), (taps, taps), 2, mus, L="lap", prec="fp32", family="cosine",
-                       psf_symmetric=True, batch=Bb, psf_per_item=True, stream=stream)
-    gb_d, hb_d = torch.from_numpy(gbig).to(dev), torch.from_numpy(hbig).to(dev)
-    fb_lb, fb_gb = torch.empty_like(gb_d), torch.empty_like(gb_d)
-    fbb = torch.empty(len(gbig), dtype=torch.int32, device=dev)
-    mib = torch.empty(len(gbig), dtype=torch.int32, device=dev)
-    cb = [slice(s, s + Bb) for s in range(0, len(gbig), Bb)]
-    ms_lb, _ = _timed(lambda: [plan_b.deblur_learned(net, gb_d[c], hb_d[c], fb_lb[c], None, fbb[c]) for c in cb],
-                      stream, max(1, args.steps // 2), 3)
-    ms_gb, _ = _timed(lambda: [plan_b.deblur(gb_d[c], hb_d[c], fb_gb[c], mib[c]) for c in cb],
-                      stream, max(1, args.steps // 2), 3)
-    fb_bb = torch.empty_like(gb_d)
-    mib_b = torch.empty(len(gbig), dtype=torch.int32, device=dev)
-    ms_bb, _ = _timed(lambda: [plan_b.deblur_binned(gb_d[c], hb_d[c], fb_bb[c], mib_b[c]) for c in cb],
-                      stream, max(1, args.steps // 2), 3)
-    rb_l, rb_g = rre(fb_lb.cpu().numpy(), fbig), rre(fb_gb.cpu().numpy(), fbig)
-    rb_b = rre(fb_bb.cpu().numpy(), fbig)
-    sec_l, sec_g = ms_l / args.steps / 1e3, ms_g / args.steps / 1e3
+    def evaluate(size, count, batch, seed, steps):
+        """The three arms on ``count`` problems of one size, chunk by chunk."""
+        pl = plan if size == n else hobc.Plan(2, (size, size), (taps, taps), 2, mus, L="lap", prec="fp32",
+                                              family="cosine", psf_symmetric=True, batch=batch, psf_per_item=True,
+                                              stream=stream)
+        chunk = 512
+        ms = {"learned": 0.0, "gcv": 0.0, "binned": 0.0}
+        r = {"learned": [], "gcv": [], "binned": []}
+        fbs, agree_b, lab_err = [], [], []
+        clk = {}
+        launches = 0
+        for c0 in range(0, count, chunk):
+            g, h, ft, _ = learned.gpu_problems(chunk, size, seed * 1000003 + c0, dev, psf="disk", taps=taps,
+                                               truth=True)
+            f_l, f_g, f_b = torch.empty_like(g), torch.empty_like(g), torch.empty_like(g)
+            mu_l = torch.empty(chunk, dtype=torch.float64, device=dev)
+            fb_l = torch.empty(chunk, dtype=torch.int32, device=dev)
+            mi_g = torch.empty(chunk, dtype=torch.int32, device=dev)
+            mi_b = torch.empty(chunk, dtype=torch.int32, device=dev)
+            fb_b = torch.empty(chunk, dtype=torch.int32, device=dev)
+            cs = [slice(s, s + batch) for s in range(0, chunk, batch)]
+            arms = {"learned": lambda: [pl.deblur_learned(net, g[c], h[c], f_l[c], mu_l[c], fb_l[c]) for c in cs],
+                    "gcv": lambda: [pl.deblur(g[c], h[c], f_g[c], mi_g[c]) for c in cs],
+                    "binned": lambda: [pl.deblur_binned(g[c], h[c], f_b[c], mi_b[c], fb_b[c]) for c in cs]}
+            for name, fn in arms.items():
+                t_ms, c_ = _timed(fn, stream, steps, 3 if c0 == 0 else 1)
+                ms[name] += t_ms / steps
+                clk.setdefault(name, c_)
+                if name == "learned":
+                    launches += pl.last_launch_count * len(cs)
+            r["learned"].append(rre(f_l, ft))
+            r["gcv"].append(rre(f_g, ft))
+            r["binned"].append(rre(f_b, ft))
+            fbs.append(fb_l.cpu().numpy())
+            agree_b.append((mi_b == mi_g).cpu().numpy())
+            lab = np.log10(mus)[mi_g.cpu().numpy()]
+            lab_err.append(np.abs(np.log10(mu_l.cpu().numpy()) - lab))
+            del g, h, ft, f_l, f_g, f_b
+        rl, rg, rb = (np.concatenate(r[k]) for k in ("learned", "gcv", "binned"))
+        err = np.concatenate(lab_err)
+        out = {"images": count, "batch": batch,
+               "learned": {"images_per_s": count / (ms["learned"] / 1e3), "fallback_rate": float(np.mean(np.concatenate(fbs))),
+                           "rre_mean": float(rl.mean()), "rre_ratio_to_gcv": float(rl.mean() / rg.mean()),
+                           "log10_mu_abs_err_vs_gcv": {"median": float(np.median(err)),
+                                                       "p90": float(np.quantile(err, 0.9))}},
+               "gcv_scan": {"images_per_s": count / (ms["gcv"] / 1e3), "rre_mean": float(rg.mean())},
+               "binned_mu": {"images_per_s": count / (ms["binned"] / 1e3), "rre_ratio_to_gcv": float(rb.mean() / rg.mean()),
+                             "index_agreement_with_full_scan": float(np.mean(np.concatenate(agree_b)))},
+               "speedup_learned_vs_gcv_scan": ms["gcv"] / ms["learned"]}
+        return out, ms, clk, launches
+
+    res256, ms256, clk256, launches = evaluate(n, 8192, B, 2, args.steps)
+    res1024, _, _, _ = evaluate(1024, args.count_1024, 64, 3, max(1, args.steps // 2))
     peaks, _ = measured_peaks()
-    io_bytes = 2 * gte.size * 4
-    line = {"metric": "learned-mu deblurs/s at equal relative error (256x256, cosine family, disk PSF)",
-            "value": len(gte) / sec_l, "unit": "images/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_l / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "1024 problems 256x256, disk PSF r~U[1.5,5] (11x11), noise log-U[1e-3,3e-2], "
-                                   "degree 2 (cosine), Laplacian, 256 mu in [1e-8,1], learned mu with bracket "
-                                   "check; inputs 268 MB (> L2)", "batch": B, "train_problems": int(len(gtr))},
-            "gcv_scan": {"value": len(gte) / sec_g, "unit": "images/s", "ms_per_step": ms_g / args.steps},
-            "speedup_vs_gcv_scan": sec_g / sec_l,
-            "rre": {"learned_mean": float(r_l.mean()), "gcv_mean": float(r_g.mean()),
-                    "ratio": float(r_l.mean() / r_g.mean()),
-                    "worst_item_ratio": float(np.max(r_l / r_g))},
-            "fallback_rate": float(fb.mean()),
-            "binned_mu": {"value": len(gte) / (ms_b / args.steps / 1e3), "unit": "images/s",
-                          "fallback_rate": float(fb_b.float().mean()),
-                          "index_agreement_with_full_scan": float((mi_b == mi_g).float().mean()),
-                          "rre_ratio": float(r_b.mean() / r_g.mean()), "clocks": clk_b},
-            "rre_median": {"learned": float(np.median(r_l)), "gcv": float(np.median(r_g)),
-                           "binned": float(np.median(r_b))},
-            "log10_mu_abs_err_vs_gcv": {"median": float(np.median(pred_err)), "p90": float(np.quantile(pred_err, 0.9))},
+    sec_l = ms256["learned"] / 1e3
+    io_bytes = 2 * 8192 * n * n * 4
+    line = {"metric": "learned-mu deblurs/s at equal relative error (256x256 and 1024x1024, cosine family, disk PSF)",
+            "value": res256["learned"]["images_per_s"], "unit": "images/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms256["learned"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (drawn on the GPU)",
+            "config": {"workload": "8192 problems 256x256 and 1024x1024, disk PSF r~U[1.5,5] (11x11), noise "
+                                   "log-U[1e-3,3e-2], degree 2 (cosine), Laplacian, 256 mu in [1e-8,1], learned mu "
+                                   "(histogram features) with bracket check", "batch": B,
+                       "train_problems": int(Xtr.shape[0]), "features": "hist"},
+            "at_256": res256, "at_1024": res1024,
             "train": {"seconds": t_train, "data_seconds": t_data, "epochs": args.epochs,
                       "loss_first": hist[0], "loss_last": hist[-1]},
-            "at_1024": {"images": int(len(gbig)), "learned_images_per_s": len(gbig) / (ms_lb / max(1, args.steps // 2) / 1e3),
-                        "gcv_images_per_s": len(gbig) / (ms_gb / max(1, args.steps // 2) / 1e3),
-                        "fallback_rate": float(fbb.cpu().numpy().mean()),
-                        "rre_ratio": float(rb_l.mean() / rb_g.mean()),
-                        "binned_images_per_s": len(gbig) / (ms_bb / max(1, args.steps // 2) / 1e3),
-                        "binned_index_agreement": float((mib_b == mib).float().mean()),
-                        "binned_rre_ratio": float(rb_b.mean() / rb_g.mean())},
             "gpu_launches": launches * args.steps,
             "hbm_roofline": {"algorithmic_bytes_per_step": io_bytes, "achieved_gbs": io_bytes / sec_l / 1e9,
                              "peak_gbs": peaks.get("hbm_gbs"), "frac": io_bytes / sec_l / 1e9 / peaks.get("hbm_gbs")},
-            "clocks": clk_l, "clocks_gcv_scan": clk_g}
+            "clocks": clk256.get("learned"), "clocks_gcv_scan": clk256.get("gcv")}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -991,8 +1066,12 @@ def main():
     ap.add_argument("--workload", choices=["fourier1024", "batched", "signals1d", "cosine512", "cosine1024",
                                            "learned", "bccompare", "volume128"],
                     default="fourier1024")
-    ap.add_argument("--train", type=int, default=8192, help="training problems of the learned workload")
-    ap.add_argument("--epochs", type=int, default=60, help="training epochs of the learned workload")
+    ap.add_argument("--train", type=int, default=200000, help="training problems of the learned workload")
+    ap.add_argument("--epochs", type=int, default=30, help="training epochs of the learned workload")
+    ap.add_argument("--count-1024", dest="count_1024", type=int, default=8192,
+                    help="1024^2 problems of the learned workload")
+    ap.add_argument("--learned-train", dest="learned_train", type=int, default=4096,
+                    help="training problems of the default line's learned arm")
     ap.add_argument("--count", type=int, default=4096, help="problems of the batched workload")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -2,7 +2,8 @@
  * Learned choice of the regularisation parameter: an extension of the method
  * with no counterpart in the paper.  The paper picks mu* by scanning the GCV
  * functional (Eq. (eq:gcv2), (eq:mugcv)) over a grid of K values; here a small
- * network predicts log10(mu*) from two radial spectra of the problem, the GCV
+ * network predicts log10(mu*) from two radial spectra of the problem (or from
+ * the shares of the GCV terms over log10 a, hobc_features_hist), the GCV
  * functional is evaluated at the prediction and at the nearest grid values
  * only, and a problem whose prediction looks poor falls back to the full scan.
  * The transforms, eigenvalues and filter are the paper's, unchanged.
@@ -33,6 +34,23 @@ extern "C" {
  * HOBC_ERR_UNSUPPORTED on a 1D plan.  Allocates the plan's learned workspace
  * on first use. */
 hobc_status hobc_features(hobc_plan* plan, const void* ghat_dev, const void* d_dev, float* x_dev);
+
+/* Feature kinds the learned path can form (hobc_mlp_set_feature_kind). */
+#define HOBC_FEATURES_RADIAL 0     /* hobc_features: radial spectra of |ghat|^2 and |d|^2 (2D plans) */
+#define HOBC_FEATURES_HIST 1       /* hobc_features_hist: shares of the GCV terms over log10 a      */
+
+/* Step: histogram features of every problem, x_dev [batch][2 * 64] float.  G
+ * of Eq. (eq:gcv2) depends on a spectral entry only through a = |d|^2 / |s|^2
+ * and |ghat|^2 (entries with s = 0 drop out), so the features are the shares
+ * of those terms over a: the entries are grouped by log10 a into 64 bins of
+ * 0.25 decade over [1e-12, 1e4) (values outside go to the end bins; an
+ * entry's bin is the number of interior edges 10^(-12 + b / 4) <= a, compared
+ * in the plan's precision), and x[b] = log10(E_b / E + 1e-12), x[64 + b] =
+ * log10(W_b / W + 1e-12), with E_b the sum of |ghat|^2 and W_b the number of
+ * entries in bin b (a stored Fourier entry that stands for a conjugate pair
+ * counts twice) and E, W their totals.  1D and 2D plans.  Allocates the plan's
+ * learned workspace on first use. */
+hobc_status hobc_features_hist(hobc_plan* plan, const void* ghat_dev, const void* d_dev, float* x_dev);
 
 /* ---------------------------------------------------------------------------
  * The network: x (n_in) -> GELU(W1 x' + b1) (n_hidden) -> GELU(W2 h1 + b2)
@@ -78,6 +96,19 @@ hobc_status hobc_mlp_train_step(hobc_mlp* net, const float* x_dev, const float* 
 hobc_status hobc_mlp_save(const hobc_mlp* net, const char* path);
 hobc_status hobc_mlp_load(hobc_mlp* net, const char* path);
 
+/* Input standardisation from training features: mean[j] and scale[j] =
+ * standard deviation + 1e-3 of column j of x_dev [rows][n_in], in FP64 on the
+ * GPU (two passes, fixed summation order).  Asynchronous on the network's
+ * stream; leaves the weights and optimiser state as they are. */
+hobc_status hobc_mlp_fit_scaling(hobc_mlp* net, const float* x_dev, int rows);
+
+/* The features hobc_deblur_learned forms for this network: HOBC_FEATURES_RADIAL
+ * (the default on creation) or HOBC_FEATURES_HIST (HOBC_ERR_ARG otherwise).
+ * The kind is not part of the checkpoint; set it after hobc_mlp_load.
+ * hobc_mlp_feature_kind returns it (-1 for NULL). */
+hobc_status hobc_mlp_set_feature_kind(hobc_mlp* net, int kind);
+int hobc_mlp_feature_kind(const hobc_mlp* net);
+
 /* Kernel launches of the last forward / gradients / train_step call. */
 int hobc_mlp_last_launch_count(const hobc_mlp* net);
 
@@ -89,8 +120,9 @@ int hobc_mlp_last_launch_count(const hobc_mlp* net);
  * edge inside the grid; then that problem falls back to the full grid scan and
  * mu* is its GCV minimiser (lowest index on ties).  Filter and synthesis as
  * hobc_deblur.  mu_dev [batch] (nullable) receives mu*, fell_back_dev [batch]
- * (nullable) 1 where the full scan ran.  The network must have n_in = 128
- * (HOBC_ERR_UNSUPPORTED otherwise, and on a 1D plan); the plan's mu grid must
+ * (nullable) 1 where the full scan ran.  The features are those of the
+ * network's feature kind.  The network must have n_in = 128
+ * (HOBC_ERR_UNSUPPORTED otherwise, and on a 1D plan with radial features); the plan's mu grid must
  * be strictly increasing (HOBC_ERR_ARG otherwise).  The first call on a plan
  * allocates its learned workspace and reads the grid back (synchronous). */
 hobc_status hobc_deblur_learned(hobc_plan* plan, hobc_mlp* net, const void* g_dev, const void* psf_dev, void* f_dev,

@@ -14,6 +14,14 @@ below is written from its plain definition:
     bin b = min(B-1, floor(B rho)).  Feature b is log10 of the mean |ghat|^2
     over the entries of bin b, feature B + b the same for |d|^2 (1e-30 is
     added before the log; an empty bin gives log10(1e-30)).
+  histogram features (per problem, 2 x B bins; the GCV functional's own
+    statistics): entries with s != 0 grouped by a = |d|^2 / |s|^2 into B bins of
+    equal width in log10 a over [1e-12, 1e4) (values outside go to the end
+    bins; the edges of the binned choice's 2B bins, every other one); feature b
+    is log10(E_b / E + 1e-12) with E_b = sum |ghat|^2 over bin b and E over all
+    bins, feature B + b the same for the entry counts W_b.  G of Eq. (eq:gcv2)
+    is a function of the (a, |ghat|^2) pairs alone, so these shares carry what
+    the GCV choice depends on, to the resolution of the bins.
   network: x (128) -> GELU(W1 x + b1) (256) -> GELU(W2 h1 + b2) (256) -> w3 . h2 + b3,
     GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2; inputs are standardised
     with per-feature mean and scale stored with the weights.  The GPU uses the
@@ -23,7 +31,8 @@ below is written from its plain definition:
   optimiser: AdamW (decoupled weight decay, bias-corrected moments).
 
 parity status: pinned by tests/test_mlp_oracle.py (finite differences, a
-closed-form single-layer case, the features of a constant spectrum).
+closed-form single-layer case, the features of a constant spectrum, histogram
+features of spectra with hand-placed values of a).
 """
 from __future__ import annotations
 
@@ -89,6 +98,13 @@ def features(family: str, ghat: np.ndarray, d: np.ndarray, nbins: int = NBINS) -
         mg = np.where(cnt > 0, sg / np.maximum(cnt, 1), 0.0)
         md = np.where(cnt > 0, sd / np.maximum(cnt, 1), 0.0)
     return np.concatenate([np.log10(mg + 1e-30), np.log10(md + 1e-30)])
+
+
+def hist_features(ghat: np.ndarray, d: np.ndarray, s: np.ndarray, nbins: int = NBINS) -> np.ndarray:
+    """The 2 x nbins histogram features of one problem (full spectra, any shape)."""
+    from . import binned_oracle as Bo
+    W, E, _ = Bo.histogram(ghat, d, s, nb=nbins)
+    return np.concatenate([np.log10(E / E.sum() + 1e-12), np.log10(W / W.sum() + 1e-12)])
 
 
 def bf16_round(x) -> np.ndarray:

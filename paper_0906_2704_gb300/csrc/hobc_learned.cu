@@ -320,6 +320,40 @@ __global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, floa
     }
 }
 
+// Per input feature j (one CTA each): mean and standard deviation of column j
+// of x [rows][nin] in FP64, two passes, fixed-order tree sums; scale = std +
+// 1e-3.  grid = nin, block = 256.
+__global__ void k_fit_scaling(const float* __restrict__ x, int rows, int nin, float* __restrict__ mean,
+                              float* __restrict__ scale) {
+    __shared__ double red[256];
+    const int j = blockIdx.x;
+    double acc = 0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) acc += (double)x[(long long)r * nin + j];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double mu = red[0] / rows;
+    __syncthreads();
+    acc = 0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const double dlt = (double)x[(long long)r * nin + j] - mu;
+        acc += dlt * dlt;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        mean[j] = (float)mu;
+        scale[j] = (float)(sqrt(red[0] / rows) + 1e-3);
+    }
+}
+
 __global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__ q, int count) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) q[i] = __float2bfloat16_rn(p[i]);
 }
@@ -770,6 +804,39 @@ __global__ void k_binned_khat(const double* __restrict__ partials, int nchunks, 
     }
 }
 
+// Histogram features of each problem (the learned choice's second feature
+// kind): the chunk sums of k_ahist in chunk order, adjacent bins merged in
+// pairs (kABins / 2 = kBins bins of 0.25 decade in log10 a), x[b] =
+// log10(E_b / E + 1e-12) and x[kBins + b] = log10(W_b / W + 1e-12).
+// grid = items, block = kABins.
+__global__ void k_hist_features(const double* __restrict__ partials, int nchunks, float* __restrict__ X) {
+    __shared__ double sw[kABins], se[kABins];
+    __shared__ double tot[2];
+    const int item = blockIdx.x, k = threadIdx.x;
+    const double* p = partials + (long long)item * nchunks * 3 * kABins;
+    double w = 0, e = 0;
+    for (int c = 0; c < nchunks; ++c) {
+        w += p[(long long)c * 3 * kABins + k];
+        e += p[(long long)c * 3 * kABins + kABins + k];
+    }
+    sw[k] = w;
+    se[k] = e;
+    __syncthreads();
+    if (k == 0) {
+        double tw = 0, te = 0;
+        for (int b = 0; b < kABins; ++b) { tw += sw[b]; te += se[b]; }
+        tot[0] = tw;
+        tot[1] = te;
+    }
+    __syncthreads();
+    if (k < kBins) {
+        const double eb = se[2 * k] + se[2 * k + 1], wb = sw[2 * k] + sw[2 * k + 1];
+        X[(long long)item * 2 * kBins + k] = (float)log10(eb / tot[1] + 1e-12);
+        X[(long long)item * 2 * kBins + kBins + k] = (float)log10(wb / tot[0] + 1e-12);
+    }
+}
+static_assert(kABins == 2 * kBins, "feature bins merge pairs of histogram bins");
+
 // The exact G on the bracket: its first minimiser is mu* unless it lies on a
 // bracket edge that is not an end of the grid (then the problem falls back).
 __global__ void k_binned_decide(const double* __restrict__ Gb, int K, const int* __restrict__ k0,
@@ -808,6 +875,7 @@ using namespace hobc;
 
 struct hobc_mlp_s {
     int nin, nh, P, cap, step;
+    int feature_kind;        // HOBC_FEATURES_RADIAL or HOBC_FEATURES_HIST: the inputs hobc_deblur_learned forms
     cudaStream_t stream;
     float *params, *grads, *m, *v, *mean, *scale;
     __nv_bfloat16 *w1h, *w2h, *w3h;
@@ -1089,12 +1157,12 @@ cudaError_t ensure_learned_ws(hobc_plan_s* p) {
     const size_t bch = (S + kBracketChunk - 1) / kBracketChunk;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** ptr, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(ptr, bytes); };
-    if (p->nax == 2) {            // features of the learned choice (2D only)
+    if (p->nax == 2) {            // radial features (2D only)
         alloc((void**)&p->feat_partials, B * fch * 3 * kBins * sizeof(double));
-        alloc((void**)&p->feat, B * kFeat * sizeof(float));
-        alloc((void**)&p->mlp_y, B * sizeof(float));
         alloc((void**)&p->bin_tab, S);
     }
+    alloc((void**)&p->feat, B * kFeat * sizeof(float));
+    alloc((void**)&p->mlp_y, B * sizeof(float));
     alloc(&p->bracket_mu, B * kJ * p->esz);
     alloc((void**)&p->mu_hat, B * sizeof(double));
     alloc((void**)&p->bracket_k0, B * sizeof(int));
@@ -1160,6 +1228,34 @@ hobc_status run_features(hobc_plan_s* p, const void* ghat, const void* D, float*
     return check("hobc_features");
 }
 
+// Histogram features: the binned choice's histogram over log10 a, then
+// k_hist_features.
+template <typename T>
+hobc_status run_features_hist(hobc_plan_s* p, const void* ghat, const void* D, float* X) {
+    const int B = p->desc.batch;
+    GcvGeom geo;
+    memset(&geo, 0, sizeof(geo));
+    const AxisHost& last = p->ax[p->nax - 1];
+    geo.ndim = p->nax; geo.fam = p->fam; geo.n0 = p->ax[0].n; geo.N0 = p->ax[0].N;
+    geo.n1 = last.n; geo.N1 = last.N; geo.W1 = last.W; geo.lap = p->desc.L == HOBC_L_LAPLACIAN;
+    geo.S = (long long)p->spec_elems;
+    geo.chunk = kAChunk;
+    const int nch = (int)((geo.S + kAChunk - 1) / kAChunk);
+    const unsigned gridA = (unsigned)(nch * (long long)B);
+    const T* edges = reinterpret_cast<const T*>(p->a_edges);
+    if (p->fam == HOBC_FAMILY_FOURIER)
+        k_ahist<T, true><<<gridA, 256, 0, p->stream>>>(reinterpret_cast<const C2<T>*>(ghat),
+                                                        reinterpret_cast<const C2<T>*>(D), geo.S, p->desc.psf_per_item,
+                                                        geo, edges, p->ahist_partials);
+    else
+        k_ahist<T, false><<<gridA, 256, 0, p->stream>>>(reinterpret_cast<const T*>(ghat),
+                                                         reinterpret_cast<const T*>(D), geo.S, p->desc.psf_per_item,
+                                                         geo, edges, p->ahist_partials);
+    k_hist_features<<<B, kABins, 0, p->stream>>>(p->ahist_partials, nch, X);
+    p->launches += 2;
+    return check("hobc_features_hist");
+}
+
 template <typename T>
 hobc_status run_learned(hobc_plan_s* p, hobc_mlp_s* q, const void* g, const void* psf, void* f, double* mu_out,
                         int* fb_out) {
@@ -1167,7 +1263,9 @@ hobc_status run_learned(hobc_plan_s* p, hobc_mlp_s* q, const void* g, const void
     const int J = bracket_size(p);
     hobc_status s = run_eig<T>(p, psf, p->D);
     if (s == HOBC_OK) s = run_analysis<T>(p, g, p->G);
-    if (s == HOBC_OK) s = run_features<T>(p, p->G, p->D, p->feat);
+    if (s == HOBC_OK)
+        s = q->feature_kind == HOBC_FEATURES_HIST ? run_features_hist<T>(p, p->G, p->D, p->feat)
+                                                  : run_features<T>(p, p->G, p->D, p->feat);
     if (s != HOBC_OK) return s;
     cudaError_t e = ensure_capacity(q, B);
     if (e != cudaSuccess) { set_last_error("hobc_deblur_learned", e); return HOBC_ERR_CUDA; }
@@ -1353,10 +1451,36 @@ hobc_status hobc_features(hobc_plan* p, const void* ghat_dev, const void* d_dev,
                                 : run_features<float>(p, ghat_dev, d_dev, x_dev);
 }
 
+hobc_status hobc_features_hist(hobc_plan* p, const void* ghat_dev, const void* d_dev, float* x_dev) {
+    if (!p || !ghat_dev || !d_dev || !x_dev) return HOBC_ERR_ARG;
+    if (p->fam == HOBC_FAMILY_REFLECTIVE || p->fam == HOBC_FAMILY_PERIODIC) return HOBC_ERR_UNSUPPORTED;
+    cudaError_t e = ensure_learned_ws(p);
+    if (e != cudaSuccess) { set_last_error("hobc_features_hist", e); return HOBC_ERR_CUDA; }
+    p->launches = 0;
+    return p->prec == HOBC_FP64 ? run_features_hist<double>(p, ghat_dev, d_dev, x_dev)
+                                : run_features_hist<float>(p, ghat_dev, d_dev, x_dev);
+}
+
+hobc_status hobc_mlp_fit_scaling(hobc_mlp* q, const float* x_dev, int rows) {
+    if (!q || !x_dev || rows < 1) return HOBC_ERR_ARG;
+    k_fit_scaling<<<q->nin, 256, 0, q->stream>>>(x_dev, rows, q->nin, q->mean, q->scale);
+    q->launches = 1;
+    return check("hobc_mlp_fit_scaling");
+}
+
+hobc_status hobc_mlp_set_feature_kind(hobc_mlp* q, int kind) {
+    if (!q || (kind != HOBC_FEATURES_RADIAL && kind != HOBC_FEATURES_HIST)) return HOBC_ERR_ARG;
+    q->feature_kind = kind;
+    return HOBC_OK;
+}
+
+int hobc_mlp_feature_kind(const hobc_mlp* q) { return q ? q->feature_kind : -1; }
+
 hobc_status hobc_deblur_learned(hobc_plan* p, hobc_mlp* q, const void* g_dev, const void* psf_dev, void* f_dev,
                                 double* mu_dev, int* fell_back_dev) {
     if (!p || !q || !g_dev || !psf_dev || !f_dev) return HOBC_ERR_ARG;
-    if (p->nax != 2 || q->nin != kFeat || p->fam == HOBC_FAMILY_REFLECTIVE || p->fam == HOBC_FAMILY_PERIODIC)
+    if ((p->nax != 2 && q->feature_kind == HOBC_FEATURES_RADIAL) || q->nin != kFeat ||
+        p->fam == HOBC_FAMILY_REFLECTIVE || p->fam == HOBC_FAMILY_PERIODIC)
         return HOBC_ERR_UNSUPPORTED;
     cudaError_t e = ensure_learned_ws(p);
     if (e != cudaSuccess) { set_last_error("hobc_deblur_learned", e); return HOBC_ERR_CUDA; }

@@ -137,6 +137,14 @@ _lib.hobc_gcv_exact.argtypes = [_vp] * 5
 _lib.hobc_gcv_exact.restype = ctypes.c_int
 _lib.hobc_deblur_exact.argtypes = [_vp] * 6
 _lib.hobc_deblur_exact.restype = ctypes.c_int
+_lib.hobc_features_hist.argtypes = [_vp] * 4
+_lib.hobc_features_hist.restype = ctypes.c_int
+_lib.hobc_mlp_set_feature_kind.argtypes = [_vp, ctypes.c_int]
+_lib.hobc_mlp_set_feature_kind.restype = ctypes.c_int
+_lib.hobc_mlp_feature_kind.argtypes = [_vp]
+_lib.hobc_mlp_feature_kind.restype = ctypes.c_int
+_lib.hobc_mlp_fit_scaling.argtypes = [_vp, _vp, ctypes.c_int]
+_lib.hobc_mlp_fit_scaling.restype = ctypes.c_int
 _lib.hobc_gcv_exact_search.argtypes = [_vp] * 5
 _lib.hobc_gcv_exact_search.restype = ctypes.c_int
 _lib.hobc_deblur_exact_search.argtypes = [_vp] * 6
@@ -417,6 +425,10 @@ class Plan:
     def features(self, ghat, d, x) -> None:
         _check(_lib.hobc_features(self._handle, _ptr(ghat), _ptr(d), _ptr(x)), "hobc_features")
 
+    def features_hist(self, ghat, d, x) -> None:
+        """Shares of the GCV terms over log10 a (include/hobc_learned.h)."""
+        _check(_lib.hobc_features_hist(self._handle, _ptr(ghat), _ptr(d), _ptr(x)), "hobc_features_hist")
+
     def deblur_learned(self, net: "MLP", g, psf, f, mu=None, fell_back=None) -> None:
         _check(_lib.hobc_deblur_learned(self._handle, net._handle, _ptr(g), _ptr(psf), _ptr(f), _ptr(mu),
                                         _ptr(fell_back)), "hobc_deblur_learned")
@@ -596,6 +608,19 @@ class MLP:
         _check(_lib.hobc_mlp_create(n_in, n_hidden, _vp(stream), ctypes.byref(self._handle)), "hobc_mlp_create")
         self.n_in, self.n_hidden = n_in, n_hidden
         self.param_count = _lib.hobc_mlp_param_count(self._handle)
+
+    def fit_scaling(self, x) -> None:
+        """Input mean and scale from training features x [rows, n_in] (device)."""
+        _check(_lib.hobc_mlp_fit_scaling(self._handle, _ptr(x), int(x.shape[0])), "hobc_mlp_fit_scaling")
+
+    @property
+    def feature_kind(self) -> str:
+        return {0: "radial", 1: "hist"}[int(_lib.hobc_mlp_feature_kind(self._handle))]
+
+    def set_feature_kind(self, kind: str) -> None:
+        """'radial' (hobc_features) or 'hist' (hobc_features_hist)."""
+        _check(_lib.hobc_mlp_set_feature_kind(self._handle, {"radial": 0, "hist": 1}[kind]),
+               "hobc_mlp_set_feature_kind")
 
     @property
     def last_launch_count(self) -> int:

@@ -105,6 +105,74 @@ def test_features_match_oracle(fam, prec, n):
             assert np.all(err <= bound), f"item {b} part {part}: worst {np.max(err - bound):.3e} over bound"
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("fam,ndim", [("cosine", 2), ("fourier", 2), ("sine3", 2), ("sine", 1), ("fourier", 1)])
+def test_hist_features_match_oracle(fam, ndim, prec):
+    """Histogram features on identical inputs (the oracle's spectra rounded to the
+    working precision): shares within the mass of the entries whose a lies within
+    rounding of a bin edge (they may land on either side) plus 1e-5 relative."""
+    F = P.FAM_LETTER[fam]
+    dt = np.float64 if prec == "fp64" else np.float32
+    eps = 2.0 ** -53 if prec == "fp64" else P.EPS32
+    batch = 3
+    n = (40, 52) if ndim == 2 else (130,)
+    if ndim == 2:
+        g, hs = _problems(n, batch, 13, dt=dt)
+        plan = _plan(fam, n, batch, prec, synth.mu_grid(16))
+    else:
+        h = P.psf_for(F, 1, 7).astype(dt).astype(np.float64)
+        hs = np.stack([h] * batch)
+        g, _ = P.problems(1, n, h, batch, 13)
+        g = g.astype(dt).astype(np.float64)
+        plan = hobc.Plan(1, n, 7, DEG[fam], synth.mu_grid(16), L="lap", prec=prec, family=fam,
+                         psf_symmetric=F != "F", batch=batch, psf_per_item=True)
+    cplx = plan.spec_complex
+
+    def stored(full):
+        lay = P.to_layout(F, full).reshape(-1)
+        return np.stack([lay.real, lay.imag], axis=-1) if cplx else lay.real
+
+    def rnd(x):
+        return x.real.astype(dt).astype(np.float64) + (1j * x.imag.astype(dt).astype(np.float64) if cplx else 0)
+    full = []
+    for b in range(batch):
+        ghat, d, s, _, _ = P.oracle_steps(F, ndim, hs[b], g[b], "lap", synth.mu_grid(16))
+        full.append((rnd(ghat), rnd(d), s))
+    G = _dev(np.stack([stored(x[0]) for x in full]), dt)
+    D = _dev(np.stack([stored(x[1]) for x in full]), dt)
+    X = torch.empty((batch, 2 * M.NBINS), dtype=torch.float32, device="cuda")
+    plan.features_hist(G, D, X)
+    x = X.cpu().numpy().astype(np.float64)
+    from oracle import binned_oracle as Bo
+    edges = Bo.bin_edges(M.NBINS)[1:-1]
+    for b, (gr, dr, s) in enumerate(full):
+        xo = M.hist_features(gr, dr, s)
+        m, a = Bo.a_values(dr.ravel(), s.ravel())
+        e = np.abs(gr.ravel()[m]) ** 2
+        near = np.min(np.abs(a[:, None] / edges[None, :] - 1.0), axis=1) < 16 * eps
+        amb = {"E": e[near].sum() / e.sum(), "W": near.sum() / len(a)}
+        for part, key in ((0, "E"), (1, "W")):
+            sl = slice(part * M.NBINS, (part + 1) * M.NBINS)
+            sg, so = 10.0 ** x[b, sl], 10.0 ** xo[sl]
+            bound = 2 * amb[key] + 1e-5 * so + 1e-11
+            assert np.all(np.abs(sg - so) <= bound), f"item {b} part {key}: {np.max(np.abs(sg - so) - bound):.3e}"
+
+
+def test_fit_scaling_matches_mean_and_std():
+    rng = np.random.default_rng(4)
+    X = (rng.standard_normal((1000, 128)) * rng.uniform(0.1, 3, 128) + rng.uniform(-5, 5, 128)).astype(np.float32)
+    net = hobc.MLP(128, 32)
+    net.fit_scaling(_dev(X, np.float32))
+    torch.cuda.synchronize()
+    flat = net.get_params()
+    _, mean, scale = hobc.unpack_params(flat, 128, 32)
+    X64 = X.astype(np.float64)
+    assert np.allclose(mean, X64.mean(axis=0), rtol=1e-6, atol=1e-6)
+    assert np.allclose(scale, X64.std(axis=0) + 1e-3, rtol=1e-6, atol=1e-6)
+    net.set_feature_kind("hist")
+    assert net.feature_kind == "hist"
+
+
 # ---------------------------------------------------------------------- network
 
 def _net_case(n_in, nh, B, seed):
@@ -229,9 +297,10 @@ def _run_learned(plan, net, g, hs, dt, tdt):
     return f.cpu().numpy(), mu.cpu().numpy(), fb.cpu().numpy()
 
 
+@pytest.mark.parametrize("kind", ["radial", "hist"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("fam", ["sine", "cosine", "fourier", "sine3"])
-def test_deblur_learned_matches_oracle(fam, prec):
+def test_deblur_learned_matches_oracle(fam, prec, kind):
     F = P.FAM_LETTER[fam]
     dt = np.float64 if prec == "fp64" else np.float32
     tdt = torch.float64 if prec == "fp64" else torch.float32
@@ -248,11 +317,15 @@ def test_deblur_learned_matches_oracle(fam, prec):
     nh = 48
     rng = np.random.default_rng(2)
     p = M.init_params(rng, 2 * M.NBINS, nh)
-    xo = np.stack([M.features(F, orc[b][0], orc[b][1]) for b in range(batch)])
+    if kind == "radial":
+        xo = np.stack([M.features(F, orc[b][0], orc[b][1]) for b in range(batch)])
+    else:
+        xo = np.stack([M.hist_features(orc[b][0], orc[b][1], orc[b][2]) for b in range(batch)])
     c0 = np.log10(mus[orc[0][4]])
     p["b3"] = np.array([c0])
     net = hobc.MLP(2 * M.NBINS, nh)
     net.set_params(hobc.pack_params(p, xo.mean(axis=0), xo.std(axis=0) + 1e-3))
+    net.set_feature_kind(kind)
     checked = 0
     for case in ("random", "constant", "low", "high"):
         if case == "constant":
@@ -269,7 +342,10 @@ def test_deblur_learned_matches_oracle(fam, prec):
         plan.eigenvalues(_dev(hs, dt), D)
         plan.analysis(_dev(g, dt), G)
         X = torch.empty((batch, 2 * M.NBINS), dtype=torch.float32, device="cuda")
-        plan.features(G, D, X)
+        if kind == "radial":
+            plan.features(G, D, X)
+        else:
+            plan.features_hist(G, D, X)
         y = torch.empty(batch, dtype=torch.float32, device="cuda")
         net.forward(X, y)
         y = y.cpu().numpy().astype(np.float64)

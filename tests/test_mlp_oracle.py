@@ -159,3 +159,37 @@ def test_learned_choice_cases():
     small = 10.0 ** np.linspace(-2, 0, 5)         # K = 5 < 9: the bracket is the grid
     mu, fb = M.learned_choice(_bowl(-1.0), small, -1.0)
     assert not fb and np.isclose(mu, 0.1)
+
+
+def test_hist_features_of_hand_placed_spectra():
+    """Histogram features from their definition: entries whose a = |d|^2/|s|^2 sits
+    at the centre of known bins of width 0.25 decade in log10 a over [1e-12, 1e4)."""
+    nb = 64
+    centres = -12.0 + 0.25 * (np.arange(nb) + 0.5)          # log10 a of each bin's centre
+    # three entries in bin 10, one in bin 40, two below the range (end bin 0)
+    la = np.array([centres[10]] * 3 + [centres[40]] + [-15.0, -13.0])
+    a = 10.0 ** la
+    d = np.sqrt(a)                    # s = 1 (L = I), so a = |d|^2
+    s = np.ones_like(d)
+    g = np.array([1.0, 1.0, 2.0, 4.0, 0.5, 0.5])
+    x = M.hist_features(g, d, s, nb)
+    E = np.zeros(nb)
+    W = np.zeros(nb)
+    E[10], W[10] = 1 + 1 + 4, 3
+    E[40], W[40] = 16, 1
+    E[0], W[0] = 0.25 + 0.25, 2
+    assert np.allclose(x[:nb], np.log10(E / E.sum() + 1e-12), atol=1e-12)
+    assert np.allclose(x[nb:], np.log10(W / W.sum() + 1e-12), atol=1e-12)
+    # entries with s = 0 are left out; the features do not change with a common scale of ghat
+    x2 = M.hist_features(np.append(g, 100.0) * 3.0, np.append(d, 0.7), np.append(s, 0.0), nb)
+    assert np.allclose(x2, x, atol=1e-12)
+
+
+def test_hist_feature_bins_are_every_other_binned_choice_bin():
+    """The 64 feature bins merge pairs of the binned choice's 128 bins exactly."""
+    from oracle import binned_oracle as Bo
+    rng = np.random.default_rng(3)
+    a = 10.0 ** rng.uniform(-13, 5, 2000)
+    b64 = Bo.bin_of(a, 64)
+    b128 = Bo.bin_of(a, 128)
+    assert np.array_equal(b64, b128 // 2)
