@@ -114,7 +114,7 @@ int hobc_mlp_last_launch_count(const hobc_mlp* net);
 
 /* The whole method on a 2D plan with the learned choice of mu*: eigenvalues,
  * analysis, features, network, then G (Eq. (eq:gcv2)) at the prediction
- * mu_hat (clamped to the grid's range) and at the J - 1 = min(9, K) grid
+ * mu_hat (clamped to the grid's range) and at the J - 1 = min(17, K) grid
  * values around it.  mu* = mu_hat unless G(mu_hat) exceeds 1.05 times the
  * smallest of those grid values of G, or that minimum sits on the bracket's
  * edge inside the grid; then that problem falls back to the full grid scan and

@@ -163,7 +163,7 @@ def loss_and_grads(p, X, t):
     return loss, g
 
 
-def learned_choice(G_at, grid: np.ndarray, y: float, width: int = 9, tol: float = 1.05):
+def learned_choice(G_at, grid: np.ndarray, y: float, width: int = 17, tol: float = 1.05):
     """mu* of the learned path for one problem and whether it fell back.
 
     G_at(mus) returns the GCV functional at an array of mu values.

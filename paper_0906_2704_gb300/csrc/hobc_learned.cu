@@ -27,7 +27,8 @@ namespace hobc {
 constexpr int kBins = 64;            // radial bins per spectrum
 constexpr int kFeat = 2 * kBins;     // network inputs
 static_assert(kBins == 64, "k_features gives each lane of a warp two bins");
-constexpr int kJ = 10;               // bracket width: mu_hat and up to 9 grid values
+constexpr int kJ = 10;               // bracket slots of the binned choice and the refinement: mu_hat and up to 9 grid values
+constexpr int kJL = 18;              // bracket slots of the learned choice: mu_hat and up to 17 grid values
 constexpr int kBracketChunk = 4096;  // spectral entries per bracket-scan CTA
 constexpr int kBracketU = 4;         // entries per thread whose loads are issued together
 
@@ -363,7 +364,7 @@ __global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict
 // mu lists of the bracket check, kJ wide: [mu_hat, grid[k0 .. k0 + J - 2]], k0
 // around the grid index nearest to mu_hat (in log10), clamped to the grid;
 // entries past J repeat the last one.
-template <typename T>
+template <typename T, int JS>
 __global__ void k_bracket_setup(const float* __restrict__ y, const double* __restrict__ grid,
                                 const double* __restrict__ lg, int K, int J, T* __restrict__ lists,
                                 double* __restrict__ mu_hat, int* __restrict__ k0_out, int B) {
@@ -384,19 +385,19 @@ __global__ void k_bracket_setup(const float* __restrict__ y, const double* __res
     k0 = max(0, min(k0, K - span));
     mu_hat[item] = mh;
     k0_out[item] = k0;
-    T* o = lists + (long long)item * kJ;
+    T* o = lists + (long long)item * JS;
     o[0] = (T)mh;
-    for (int j = 1; j < kJ; ++j) o[j] = (T)grid[k0 + min(j, J - 1) - 1];
+    for (int j = 1; j < JS; ++j) o[j] = (T)grid[k0 + min(j, J - 1) - 1];
 }
 
 // G at the bracket values: accept mu_hat unless it raises G by more than 5% over
 // the bracket minimum or that minimum is on an edge that is not the grid's end.
-__global__ void k_bracket_decide(const double* __restrict__ Gb, int J, const int* __restrict__ k0, int K,
+__global__ void k_bracket_decide(const double* __restrict__ Gb, int J, int JS, const int* __restrict__ k0, int K,
                                  const double* __restrict__ mu_hat, double* __restrict__ mu_val,
                                  int* __restrict__ fell_back, int B) {
     const int item = blockIdx.x * blockDim.x + threadIdx.x;
     if (item >= B) return;
-    const double* g = Gb + (long long)item * kJ;
+    const double* g = Gb + (long long)item * JS;
     double mn = INFINITY;
     int am = 1;
     for (int j = 1; j < J; ++j)
@@ -409,17 +410,17 @@ __global__ void k_bracket_decide(const double* __restrict__ Gb, int J, const int
     mu_val[item] = mu_hat[item];
 }
 
-// G's sums at the kJ bracket values of every problem: each thread takes its
-// elements' terms once and accumulates all kJ values (reciprocals shared by
+// G's sums at the JS bracket values of every problem: each thread takes its
+// elements' terms once and accumulates all JS values (reciprocals shared by
 // pairs, as in the grid scan); sums per thread and per warp in T, across
 // warps in double.
-// grid = items x ceil(S / kBracketChunk), block = 256; partials [CTA][2 kJ].
-template <typename T, bool CPLX>
+// grid = items x ceil(S / kBracketChunk), block = 256; partials [CTA][2 JS].
+template <typename T, bool CPLX, int JS = kJ>
 __global__ void __launch_bounds__(256)
 k_gcv_bracket(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typename ElemT<T, CPLX>::t* __restrict__ D,
               long long d_psf_stride, int psf_per, const T* __restrict__ lists, GcvGeom geo,
               double* __restrict__ partials) {
-    __shared__ double red[8][2 * kJ];
+    __shared__ double red[8][2 * JS];
     const int nch = (int)((geo.S + kBracketChunk - 1) / kBracketChunk);
     const long long item = blockIdx.x / nch;
     const int chunk = blockIdx.x - (int)(item * nch);
@@ -427,9 +428,9 @@ k_gcv_bracket(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typenam
     const int cnt = (int)min((long long)kBracketChunk, geo.S - e0);
     const typename ElemT<T, CPLX>::t* sp = spec + item * geo.S + e0;
     const typename ElemT<T, CPLX>::t* dp = D + (psf_per ? item : 0) * d_psf_stride + e0;
-    T mu[kJ], nd[kJ], dd[kJ];
+    T mu[JS], nd[JS], dd[JS];
 #pragma unroll
-    for (int j = 0; j < kJ; ++j) { mu[j] = lists[item * kJ + j]; nd[j] = 0; dd[j] = 0; }
+    for (int j = 0; j < JS; ++j) { mu[j] = lists[item * JS + j]; nd[j] = 0; dd[j] = 0; }
     // kBracketU entries per thread and step, all loads issued before the math:
     // with ten evaluations per entry the pass is bound by load latency
     typedef typename ElemT<T, CPLX>::t E;
@@ -446,7 +447,7 @@ k_gcv_bracket(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typenam
             if (i >= cnt) break;
             const typename Pack4<T>::t v = gcv_term<T, CPLX>(sv[u], dv[u], geo, e0 + i);
 #pragma unroll
-            for (int j = 0; j < kJ; j += 2) {
+            for (int j = 0; j < JS; j += 2) {
                 const T t1 = v.x + mu[j], t2 = v.x + mu[j + 1];
                 const T r = pair_rcp(t1 * t2);
                 const T s1 = t2 * r, s2 = t1 * r;
@@ -462,27 +463,28 @@ k_gcv_bracket(const typename ElemT<T, CPLX>::t* __restrict__ spec, const typenam
     // conversion per warp: FP64 runs at a small fraction of the FP32 rate
     const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
 #pragma unroll
-    for (int j = 0; j < kJ; ++j) {
+    for (int j = 0; j < JS; ++j) {
         T a = nd[j], b = dd[j];
         for (int off = 16; off > 0; off >>= 1) {
             a += __shfl_down_sync(0xffffffffu, a, off);
             b += __shfl_down_sync(0xffffffffu, b, off);
         }
-        if (lane == 0) { red[warp][j] = (double)a; red[warp][kJ + j] = (double)b; }
+        if (lane == 0) { red[warp][j] = (double)a; red[warp][JS + j] = (double)b; }
     }
     __syncthreads();
-    if (threadIdx.x < 2 * kJ) {
+    if (threadIdx.x < 2 * JS) {
         double acc = 0;
         for (int w = 0; w < (int)(blockDim.x / 32); ++w) acc += red[w][threadIdx.x];
-        partials[(long long)blockIdx.x * 2 * kJ + threadIdx.x] = acc;
+        partials[(long long)blockIdx.x * 2 * JS + threadIdx.x] = acc;
     }
 }
 
-// G at the kJ bracket values of every problem from the per-CTA sums: twelve
-// groups of 20 threads split the chunks, then combine in group order.
-// grid = items, block = 256; G [item][kJ].
+// G at the JS bracket values of every problem from the per-CTA sums: 256 / (2 JS)
+// groups of 2 JS threads split the chunks, then combine in group order.
+// grid = items, block = 256; G [item][JS].
+template <int JS = kJ>
 __global__ void k_bracket_finalize(const double* __restrict__ partials, int nchunks, double* __restrict__ G) {
-    constexpr int V = 2 * kJ, NG = 256 / V;
+    constexpr int V = 2 * JS, NG = 256 / V;
     __shared__ double acc[NG][V];
     const int item = blockIdx.x;
     const int g = threadIdx.x / V, v = threadIdx.x % V;
@@ -492,10 +494,10 @@ __global__ void k_bracket_finalize(const double* __restrict__ partials, int nchu
         acc[g][v] = a;
     }
     __syncthreads();
-    if (threadIdx.x < kJ) {
+    if (threadIdx.x < JS) {
         double num = 0, den = 0;
-        for (int q = 0; q < NG; ++q) { num += acc[q][threadIdx.x]; den += acc[q][kJ + threadIdx.x]; }
-        G[(long long)item * kJ + threadIdx.x] = num / (den * den);
+        for (int q = 0; q < NG; ++q) { num += acc[q][threadIdx.x]; den += acc[q][JS + threadIdx.x]; }
+        G[(long long)item * JS + threadIdx.x] = num / (den * den);
     }
 }
 
@@ -1147,7 +1149,7 @@ namespace {
 
 constexpr int kFeatChunk = 2048;     // spectral entries per features CTA
 
-int bracket_size(const hobc_plan_s* p) { return 1 + std::min(kJ - 1, p->K); }
+int bracket_size(const hobc_plan_s* p) { return 1 + std::min(kJL - 1, p->K); }   // the learned choice's J
 
 cudaError_t ensure_learned_ws(hobc_plan_s* p) {
     if (p->log_grid) return cudaSuccess;
@@ -1163,11 +1165,11 @@ cudaError_t ensure_learned_ws(hobc_plan_s* p) {
     }
     alloc((void**)&p->feat, B * kFeat * sizeof(float));
     alloc((void**)&p->mlp_y, B * sizeof(float));
-    alloc(&p->bracket_mu, B * kJ * p->esz);
+    alloc(&p->bracket_mu, B * kJL * p->esz);                 // kJL >= kJ slots serve every bracket scan
     alloc((void**)&p->mu_hat, B * sizeof(double));
     alloc((void**)&p->bracket_k0, B * sizeof(int));
-    alloc((void**)&p->bracket_partials, B * bch * 2 * kJ * sizeof(double));
-    alloc((void**)&p->bracket_G, B * kJ * sizeof(double));
+    alloc((void**)&p->bracket_partials, B * bch * 2 * kJL * sizeof(double));
+    alloc((void**)&p->bracket_G, B * kJL * sizeof(double));
     alloc((void**)&p->bracket_idx, B * sizeof(int));
     alloc((void**)&p->mu_val, B * sizeof(double));
     alloc((void**)&p->fell_back, B * sizeof(int));
@@ -1275,7 +1277,7 @@ hobc_status run_learned(hobc_plan_s* p, hobc_mlp_s* q, const void* g, const void
     q->stream = own;
     p->launches += 6;
     T* lists = reinterpret_cast<T*>(p->bracket_mu);
-    k_bracket_setup<T><<<(B + 127) / 128, 128, 0, p->stream>>>(p->mlp_y, p->mu, p->log_grid, K, J, lists, p->mu_hat,
+    k_bracket_setup<T, kJL><<<(B + 127) / 128, 128, 0, p->stream>>>(p->mlp_y, p->mu, p->log_grid, K, J, lists, p->mu_hat,
                                                                 p->bracket_k0, B);
     // G at the bracket values
     GcvGeom geo;
@@ -1284,22 +1286,22 @@ hobc_status run_learned(hobc_plan_s* p, hobc_mlp_s* q, const void* g, const void
     geo.ndim = p->nax; geo.fam = p->fam; geo.n0 = p->ax[0].n; geo.N0 = p->ax[0].N;
     geo.n1 = last.n; geo.N1 = last.N; geo.W1 = last.W; geo.lap = p->desc.L == HOBC_L_LAPLACIAN;
     geo.S = (long long)p->spec_elems;
-    geo.K = kJ;
+    geo.K = kJL;
     geo.chunk = kBracketChunk;
     const int nchJ = (int)((geo.S + kBracketChunk - 1) / kBracketChunk);
     const unsigned gridJ = (unsigned)(nchJ * (long long)B);
     if (p->fam == HOBC_FAMILY_FOURIER)
-        k_gcv_bracket<T, true><<<gridJ, 256, 0, p->stream>>>(
+        k_gcv_bracket<T, true, kJL><<<gridJ, 256, 0, p->stream>>>(
             reinterpret_cast<const C2<T>*>(p->G), reinterpret_cast<const C2<T>*>(p->D), (long long)p->spec_elems,
             p->desc.psf_per_item, lists, geo, p->bracket_partials);
     else
-        k_gcv_bracket<T, false><<<gridJ, 256, 0, p->stream>>>(
+        k_gcv_bracket<T, false, kJL><<<gridJ, 256, 0, p->stream>>>(
             reinterpret_cast<const T*>(p->G), reinterpret_cast<const T*>(p->D), (long long)p->spec_elems,
             p->desc.psf_per_item, lists, geo, p->bracket_partials);
-    k_bracket_finalize<<<B, 256, 0, p->stream>>>(p->bracket_partials, nchJ, p->bracket_G);
+    k_bracket_finalize<kJL><<<B, 256, 0, p->stream>>>(p->bracket_partials, nchJ, p->bracket_G);
     double* mu_val = mu_out ? mu_out : p->mu_val;
     int* fb = fb_out ? fb_out : p->fell_back;
-    k_bracket_decide<<<(B + 127) / 128, 128, 0, p->stream>>>(p->bracket_G, J, p->bracket_k0, K, p->mu_hat, mu_val, fb, B);
+    k_bracket_decide<<<(B + 127) / 128, 128, 0, p->stream>>>(p->bracket_G, J, kJL, p->bracket_k0, K, p->mu_hat, mu_val, fb, B);
     // the full scan, only for the problems that fell back
     geo.K = K;
     geo.chunk = p->gcv_chunk;

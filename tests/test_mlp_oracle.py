@@ -156,7 +156,11 @@ def test_learned_choice_cases():
     Gend = _bowl(0.0)                             # minimum at the grid's last value
     mu, fb = M.learned_choice(Gend, grid, 5.0)    # clamped to 1: edge is the grid end
     assert not fb and np.isclose(mu, 1.0)
-    small = 10.0 ** np.linspace(-2, 0, 5)         # K = 5 < 9: the bracket is the grid
+    mu, fb = M.learned_choice(G, grid, c + 0.7)   # 7 steps off: inside the +-8 bracket, G = 1.49
+    assert fb and np.isclose(mu, 1e-4)
+    mu, fb = M.learned_choice(G, grid, c + 0.7, width=9)   # a 9-wide bracket: minimum on its edge
+    assert fb and np.isclose(mu, 1e-4)
+    small = 10.0 ** np.linspace(-2, 0, 5)         # K = 5 < 17: the bracket is the grid
     mu, fb = M.learned_choice(_bowl(-1.0), small, -1.0)
     assert not fb and np.isclose(mu, 0.1)
 
