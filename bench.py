@@ -696,7 +696,18 @@ def run_other(args):
             items, gs, hs = items[lo:hi], gs[lo:hi], hs[lo:hi]
             count = len(items)
             K = 128
-            batch = hobc.Batch(items, synth.mu_grid(K), L="lap", prec=prec, stream=stream)
+            # the FFT schedule (radix per degree and FFT length), measured on this GPU by
+            # the autotuner (outside the timed region; cached as JSON for later runs);
+            # --no-autotune keeps the default schedule (radix 16 from FFT length 256 up)
+            schedule, tuned, t_tune = None, None, 0.0
+            if not args.no_autotune:
+                from paper_0906_2704_gb300 import autotune
+                t_tune = time.time()
+                cache = os.path.join(tempfile.gettempdir(), "hobc_bench_fft_schedule.json")
+                schedule, tuned = autotune.tune_batched(items, synth.mu_grid(K), L="lap", prec=prec, cache=cache,
+                                                        refresh=True)
+                t_tune = time.time() - t_tune
+            batch = hobc.Batch(items, synth.mu_grid(K), L="lap", prec=prec, stream=stream, schedule=schedule)
             g = torch.from_numpy(np.concatenate([x.ravel() for x in gs]).astype(npdt)).to(dev)
             h = torch.from_numpy(np.concatenate([x.ravel() for x in hs]).astype(npdt)).to(dev)
             f = torch.empty_like(g)
@@ -710,7 +721,14 @@ def run_other(args):
             pixels = int(g.numel())
             extra = {"pixels_per_step": pixels, "pixels_per_s": pixels * args.steps / (ms / 1e3),
                      "degrees": np.bincount([it[4] for it in items], minlength=4)[1:].tolist(),
-                     "graph": True}
+                     "graph": True, "persistent": True}
+            if tuned is not None:
+                # the same batch with the default schedule (radix 16 from FFT length 256 up)
+                default = hobc.Batch(items, synth.mu_grid(K), L="lap", prec=prec, stream=stream)
+                ms_def, _ = _timed(lambda: default.deblur(g, h, f, mi), stream, args.steps, args.warmup)
+                default.close()
+                extra["autotune"] = {"seconds": t_tune, "schedule": tuned}
+                extra["default_schedule"] = {"value": total / (ms_def / args.steps / 1e3), "unit": "images/s"}
             cfg = {"workload": f"{args.count} uneven 2D problems per GPU (side log-uniform in [64,512], own "
                                f"Gaussian PSF, degree 1/2/3, Laplacian, 128 mu, 1% noise), one CUDA-graph launch",
                    "count": total, "parallelism": f"dp{max(world, 1)} (pixel-balanced contiguous shards)"}
@@ -1089,6 +1107,8 @@ def main():
     ap.add_argument("--learned-train", dest="learned_train", type=int, default=16384,
                     help="training problems of the default line's learned arm")
     ap.add_argument("--count", type=int, default=4096, help="problems of the batched workload")
+    ap.add_argument("--no-autotune", dest="no_autotune", action="store_true",
+                    help="batched workload: the default FFT schedule, no autotuning run")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

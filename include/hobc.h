@@ -287,18 +287,49 @@ typedef struct {
 typedef struct hobc_batch_s hobc_batch;
 
 /* Build the batch plan: transform tables once per distinct (family, n), work
- * lists of every pass, workspace.  With a non-NULL stream the whole launch
+ * lists of every pass, workspace.  Every pass is one launch of a persistent
+ * kernel for all families: resident CTAs (the SMs times the CTAs that fit on
+ * one) take the pass's work items -- (problem, block of lines) for the line
+ * transforms, (problem, chunk) for the GCV scan, (problem, column) for the
+ * eigenvalues -- from a device counter, costliest first; the counters are
+ * zeroed at the head of each call.  With a non-NULL stream the whole launch
  * sequence is captured once into a CUDA graph that hobc_deblur_batched
  * replays; with the legacy NULL stream the kernels are launched directly.
  * Synchronous; allocates device memory. */
 hobc_status hobc_batch_create(const hobc_batch_desc* desc, const hobc_batch_item* items_host,
                               const double* mu_grid_host, void* cuda_stream, hobc_batch** out);
+
+/* The FFT schedule of one kind of line: problems of this boundary-condition
+ * degree whose lines need an FFT of length fft_length (hobc_fft_length) run
+ * their FFT stages in radix 16 (16 values a thread, fft_length/16 threads a
+ * line pair; fft_length >= 256 only, else radix 8) or radix 8 (fft_length/8
+ * threads); 0 keeps the default (radix 16 from 256 up).  Tables of these
+ * choices are what an autotuner measures (paper_0906_2704_gb300/autotune.py). */
+typedef struct {
+    int bc_degree;             /* 1, 2 or 3                                                */
+    int fft_length;            /* power of two                                             */
+    int radix;                 /* 0, 8 or 16                                               */
+} hobc_fft_schedule;
+
+/* hobc_batch_create with an FFT schedule (schedule_len entries, copied; kinds
+ * of line it does not list keep the default).  HOBC_ERR_ARG on a malformed
+ * entry. */
+hobc_status hobc_batch_create_tuned(const hobc_batch_desc* desc, const hobc_batch_item* items_host,
+                                    const double* mu_grid_host, const hobc_fft_schedule* schedule,
+                                    int schedule_len, void* cuda_stream, hobc_batch** out);
+
+/* FFT length of a line of n samples (8 <= n <= 1024) under boundary-condition
+ * degree 1, 2 or 3 (0 otherwise): the power of two the transform of that line
+ * runs on (N = n - 2, or n - 4 for degree 3; a core DFT of length N, or
+ * 2(N + 1) for degrees 1 and 3, padded to 2^k >= 2 L - 1 for the chirp-z form
+ * unless it is a power of two itself). */
+int hobc_fft_length(int bc_degree, int n);
 void hobc_batch_destroy(hobc_batch* batch);
 
 /* Packed-layout offsets (host arrays of count + 1 elements each, nullable). */
 hobc_status hobc_batch_offsets(const hobc_batch* batch, size_t* img_off, size_t* psf_off);
 
-/* Kernel launches per batched deblur (one per pass and family present). */
+/* Kernel launches per batched deblur (one per pass). */
 int hobc_batch_launch_count(const hobc_batch* batch);
 
 /* The whole method on every problem of the batch: g_dev, f_dev packed images,

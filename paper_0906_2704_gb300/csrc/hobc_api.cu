@@ -285,8 +285,19 @@ static void* upload_real(const std::vector<double>& h, cudaError_t& err) {
     return d;
 }
 
+// Power-of-two FFT length M of a line of n samples of a family (the core DFT
+// of length L = N, or 2(N + 1) for the sine families, padded for Bluestein).
+int fft_length_of(int fam, int n) {
+    const int N = (fam == FAM_S3 || fam == FAM_C4) ? n - 4 : n - 2;
+    const int L = (fam == FAM_S || fam == FAM_S3) ? 2 * (N + 1) : N;
+    if (L >= 8 && (L & (L - 1)) == 0) return L;
+    int M = 8;
+    while (M < 2 * L - 1) M *= 2;
+    return M;
+}
+
 template <typename T>
-cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half) {
+cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half, int radix) {
     memset(&a, 0, sizeof(a));
     a.fam = fam;
     a.n = n;
@@ -310,7 +321,9 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half) {
     }
     a.log2M = 0;
     while ((1 << a.log2M) < a.M) ++a.log2M;
-    a.tpg = hobc::fft_r16(a.M) ? a.M / 16 : a.M / 8;
+    const bool can16 = a.M >= 256 && a.log2M <= 12;
+    a.r16 = radix == 0 ? (hobc::fft_r16(a.M) && can16) : (radix == 16 && can16);
+    a.tpg = a.r16 ? a.M / 16 : a.M / 8;
     a.H = fam == hobc::FAM_F ? N / 2 + 1 : N;
     a.W = (fam == hobc::FAM_F && half) ? a.H + 2 : n;
 
@@ -320,7 +333,7 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half) {
     // W_M^{pw (M / (Ns R)) k}, k < Ns, for pw = 1, 2, 3, 4, 8, 12 (radix 16)
     // or pw = 1, 2, 4 (those < R)
     std::vector<cd> tw;
-    const int rmax = hobc::fft_r16(a.M) ? 16 : 8;
+    const int rmax = a.r16 ? 16 : 8;
     for (int Ns = 1, rem = a.log2M; rem > 0;) {
         const int R = (1 << rem) >= rmax ? rmax : (1 << rem);
         std::vector<int> pws;
@@ -430,8 +443,8 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half) {
     return err;
 }
 
-template cudaError_t build_axis_host<float>(AxisHost&, int, int, int, bool);
-template cudaError_t build_axis_host<double>(AxisHost&, int, int, int, bool);
+template cudaError_t build_axis_host<float>(AxisHost&, int, int, int, bool, int);
+template cudaError_t build_axis_host<double>(AxisHost&, int, int, int, bool, int);
 
 void free_axis(AxisHost& a) {
     cudaFree(a.tw); cudaFree(a.chirp); cudaFree(a.bhat); cudaFree(a.post); cudaFree(a.q); cudaFree(a.q2);
@@ -623,6 +636,12 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
 }
 
 hobc_family hobc_plan_family(const hobc_plan* p) { return p ? (hobc_family)p->fam : HOBC_FAMILY_AUTO; }
+
+int hobc_fft_length(int bc_degree, int n) {
+    if (n < 8 || n > 1024) return 0;
+    const int fam = bc_degree == 1 ? FAM_S : bc_degree == 2 ? FAM_C : bc_degree == 3 ? FAM_S3 : -1;
+    return fam < 0 ? 0 : fft_length_of(fam, n);
+}
 
 hobc_status hobc_spectrum_size(const hobc_plan* p, size_t* spec, int* is_complex, size_t* psf) {
     if (!p) return HOBC_ERR_ARG;

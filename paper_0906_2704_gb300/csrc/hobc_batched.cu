@@ -56,80 +56,6 @@ static const int kBatchThreads = 256;
 
 // ------------------------------------------------------------------ kernels
 
-template <typename T, int FAM>
-__global__ void __launch_bounds__(256)
-kb_pair_analysis(const LineWork* __restrict__ work, const Axis<T>* __restrict__ axes, const T* __restrict__ in_fixed,
-                 int in_from_io, const BatchIO* __restrict__ io, T* __restrict__ out) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const LineWork w = work[blockIdx.x];
-    const T* in = (in_from_io ? reinterpret_cast<const T*>(io->g) : in_fixed) + w.in_off;
-    pair_analysis_body<T, FAM>(in, 0, w.in_rs, out + w.out_off, 0, w.out_rs, w.out_cs, w.nlines, axes[w.axis], 0,
-                               w.r0, smem_raw);
-}
-
-template <typename T, int FAM, int FMODE>
-__global__ void __launch_bounds__(256)
-kb_pair_synthesis(const LineWork* __restrict__ work, const Axis<T>* __restrict__ axes, const T* __restrict__ in,
-                  T* __restrict__ out_fixed, int out_to_io, const BatchIO* __restrict__ io, const T* __restrict__ D,
-                  FilterDesc fd) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const LineWork w = work[blockIdx.x];
-    if (FMODE == 2) {
-        const Axis<T>& ao = axes[w.axis_o];
-        fd.D = D + w.in_off;             // eigenvalues share the spectrum layout
-        fd.d_psf_stride = 0;
-        fd.psf_per = 0;
-        fd.mu_idx = io->mu_idx + w.item;
-        fd.o_fam = ao.fam; fd.o_n = ao.n; fd.o_N = ao.N; fd.o_W = ao.W;
-    }
-    T* out = (out_to_io ? reinterpret_cast<T*>(io->f) : out_fixed) + w.out_off;
-    pair_synthesis_body<T, FAM, FMODE>(in + w.in_off, 0, w.in_rs, w.in_cs, out, 0, w.out_rs, w.nlines, axes[w.axis],
-                                       fd, 0, w.r0, smem_raw);
-}
-
-// Eigenvalues of a symmetric PSF on the real families: d = sum h cos(j0 th0) cos(j1 th1)
-// (Eq. (eq:symbol) at -theta, Sec. 6): partial sums over j1 for the column,
-// then the sum over j0 for every entry, tap offsets +-k folded; the cosines
-// cos(k theta_t) come from per-axis tables built on the host with the
-// argument reduced exactly; FP64 sums.  One CTA per (problem, column).
-template <typename T>
-__global__ void __launch_bounds__(256)
-kb_eig(const int2* __restrict__ work, const ItemDev* __restrict__ items, const BatchIO* __restrict__ io,
-       const double* __restrict__ costab, T* __restrict__ D) {
-    __shared__ double P[64];
-    const int2 w = work[blockIdx.x];
-    const ItemDev it = items[w.x];
-    const int c = w.y;
-    const T* h = reinterpret_cast<const T*>(io->psf) + it.psf_off;
-    const int m0 = it.p0 / 2, m1 = it.p1 / 2;
-    const double* c1t = costab + it.cos1 + c;             // cos(k theta_c) at c1t[k n1]
-    for (int j0 = threadIdx.x; j0 < it.p0; j0 += blockDim.x) {
-        const T* hr = h + j0 * it.p1;
-        double acc = (double)hr[m1];
-        for (int k = 1; k <= m1; ++k) acc += ((double)hr[m1 + k] + (double)hr[m1 - k]) * c1t[(long long)k * it.n1];
-        P[j0] = acc;
-    }
-    __syncthreads();
-    T* o = D + it.img_off + (long long)c * it.n0;
-    const double* c0t = costab + it.cos0;
-    for (int t0 = threadIdx.x; t0 < it.n0; t0 += blockDim.x) {
-        double acc = P[m0];
-        for (int k = 1; k <= m0; ++k) acc += (P[m0 + k] + P[m0 - k]) * c0t[(long long)k * it.n0 + t0];
-        o[t0] = (T)acc;
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256)
-kb_gcv(const int2* __restrict__ work, const GcvItem* __restrict__ gi, const T* __restrict__ G,
-       const T* __restrict__ D, const T* __restrict__ muT, double* __restrict__ partials) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int2 w = work[blockIdx.x];
-    const GcvItem g = gi[w.x];
-    gcv_partials_body<T, false>(G + g.spec_off, D + g.spec_off, muT, g.geo, (long long)w.y * g.geo.chunk,
-                                partials + g.part_off + (long long)w.y * 2 * g.geo.K, smem_raw);
-}
-
 __global__ void kb_gcv_finalize(const GcvItem* __restrict__ gi, const double* __restrict__ partials,
                                 const BatchIO* __restrict__ io, int K) {
     __shared__ double sv[256];
@@ -164,6 +90,202 @@ __global__ void kb_gcv_finalize(const GcvItem* __restrict__ gi, const double* __
     if (threadIdx.x == 0) io->mu_idx[item] = si[0] == 0x7fffffff ? 0 : si[0];
 }
 
+// ----------------------------------------------------- persistent passes
+// One launch per pass for every family: resident CTAs (the SMs times the CTAs
+// that fit on one) take the work items of the pass's list in order from a
+// device counter, one at a time, and run the same device code as the
+// per-family kernels above on each.  The lists are sorted on the host by
+// decreasing cost (FFT length, then lines), so the longest items start first
+// and the short ones fill the tail.  The counters are zeroed by a memset node
+// at the head of the graph.  Work items are independent within a pass, so no
+// CTA waits on another.
+// The work queue of a persistent pass: a CTA draws item k from the counter,
+// and while it works on k its thread 0 has already drawn the next one (the
+// atomic's latency hides behind the work); the hand-over's barriers also keep
+// an item's shared memory from being overwritten while it is still read.
+__device__ __forceinline__ int queue_first(int* counter, int& slot) {
+    if (threadIdx.x == 0) slot = atomicAdd(counter, 1);
+    __syncthreads();
+    return slot;
+}
+__device__ __forceinline__ int queue_draw(int* counter) { return threadIdx.x == 0 ? atomicAdd(counter, 1) : 0; }
+__device__ __forceinline__ int queue_handover(int drawn, int& slot) {
+    __syncthreads();
+    if (threadIdx.x == 0) slot = drawn;
+    __syncthreads();
+    return slot;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
+kp_analysis(const LineWork* __restrict__ work, int count, int* __restrict__ counter,
+            const Axis<T>* __restrict__ axes, const T* __restrict__ in_fixed, int in_from_io,
+            const BatchIO* __restrict__ io, T* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int slot;
+    for (int k = queue_first(counter, slot); k < count;) {
+        const int drawn = queue_draw(counter);
+        const LineWork w = work[k];
+        const Axis<T>& ax = axes[w.axis];
+        const T* in = (in_from_io ? reinterpret_cast<const T*>(io->g) : in_fixed) + w.in_off;
+        if (ax.fam == FAM_S)
+            pair_analysis_body<T, FAM_S>(in, 0, w.in_rs, out + w.out_off, 0, w.out_rs, w.out_cs, w.nlines, ax, 0,
+                                         w.r0, smem_raw);
+        else if (ax.fam == FAM_C)
+            pair_analysis_body<T, FAM_C>(in, 0, w.in_rs, out + w.out_off, 0, w.out_rs, w.out_cs, w.nlines, ax, 0,
+                                         w.r0, smem_raw);
+        else
+            pair_analysis_body<T, FAM_S3>(in, 0, w.in_rs, out + w.out_off, 0, w.out_rs, w.out_cs, w.nlines, ax, 0,
+                                          w.r0, smem_raw);
+        k = queue_handover(drawn, slot);
+    }
+}
+
+template <typename T, int FMODE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
+kp_synthesis(const LineWork* __restrict__ work, int count, int* __restrict__ counter,
+             const Axis<T>* __restrict__ axes, const T* __restrict__ in, T* __restrict__ out_fixed, int out_to_io,
+             const BatchIO* __restrict__ io, const T* __restrict__ D, FilterDesc fd0) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int slot;
+    for (int k = queue_first(counter, slot); k < count;) {
+        const int drawn = queue_draw(counter);
+        const LineWork w = work[k];
+        const Axis<T>& ax = axes[w.axis];
+        FilterDesc fd = fd0;
+        if (FMODE == 2) {
+            const Axis<T>& ao = axes[w.axis_o];
+            fd.D = D + w.in_off;             // eigenvalues share the spectrum layout
+            fd.d_psf_stride = 0;
+            fd.psf_per = 0;
+            fd.mu_idx = io->mu_idx + w.item;
+            fd.o_fam = ao.fam; fd.o_n = ao.n; fd.o_N = ao.N; fd.o_W = ao.W;
+        }
+        T* out = (out_to_io ? reinterpret_cast<T*>(io->f) : out_fixed) + w.out_off;
+        if (ax.fam == FAM_S)
+            pair_synthesis_body<T, FAM_S, FMODE>(in + w.in_off, 0, w.in_rs, w.in_cs, out, 0, w.out_rs, w.nlines, ax,
+                                                 fd, 0, w.r0, smem_raw);
+        else if (ax.fam == FAM_C)
+            pair_synthesis_body<T, FAM_C, FMODE>(in + w.in_off, 0, w.in_rs, w.in_cs, out, 0, w.out_rs, w.nlines, ax,
+                                                 fd, 0, w.r0, smem_raw);
+        else
+            pair_synthesis_body<T, FAM_S3, FMODE>(in + w.in_off, 0, w.in_rs, w.in_cs, out, 0, w.out_rs, w.nlines,
+                                                  ax, fd, 0, w.r0, smem_raw);
+        k = queue_handover(drawn, slot);
+    }
+}
+
+// Eigenvalues of a symmetric PSF on the real families: d = sum h cos(j0 th0) cos(j1 th1)
+// (Eq. (eq:symbol) at -theta, Sec. 6): partial sums over j1 for the column,
+// then the sum over j0 for every entry, tap offsets +-k folded; the cosines
+// cos(k theta_t) come from per-axis tables built on the host with the
+// argument reduced exactly.  One work item per (problem, kEigCols columns):
+// the cosine of an entry t0 is loaded once for all the item's columns.
+// The partial sums are FP64.  The sums over j0 are FP64 in FP64 batches; in
+// FP32 batches they are compensated dot products in float-float arithmetic
+// (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005: exact
+// products by FMA, error-free TwoSum of the running sum, the errors summed
+// apart) of the operands split into float pairs hi + lo, within about 2^-45 of
+// sum |terms| -- FP64 runs at 1/64 of the FP32 rate on this GPU, and these
+// sums are n0 n1 p0 / 2 products per problem.
+static const int kEigCols = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+kp_eig(const int2* __restrict__ work, int count, int* __restrict__ counter, const ItemDev* __restrict__ items,
+       const BatchIO* __restrict__ io, const double* __restrict__ costab, const float2* __restrict__ costab2,
+       T* __restrict__ D) {
+    __shared__ double P[kEigCols][64];
+    __shared__ double A[kEigCols][32];          // FP64 batches: A_q = P_{m0+q} + P_{m0-q}, A_0 = P_{m0}
+    __shared__ float2 Af[32][kEigCols];         // FP32 batches: A_q as (hi, lo)
+    __shared__ int slot;
+    for (int k = queue_first(counter, slot); k < count;) {
+        const int drawn = queue_draw(counter);
+        const int2 w = work[k];
+        const ItemDev it = items[w.x];
+        const int c0 = w.y, nc = min(kEigCols, it.n1 - c0);
+        const T* h = reinterpret_cast<const T*>(io->psf) + it.psf_off;
+        const int m0 = it.p0 / 2, m1 = it.p1 / 2;
+        for (int e = threadIdx.x; e < nc * it.p0; e += blockDim.x) {
+            const int cc = e / it.p0, j0 = e - cc * it.p0;
+            const double* c1t = costab + it.cos1 + c0 + cc;
+            const T* hr = h + j0 * it.p1;
+            double acc = (double)hr[m1];
+            for (int q = 1; q <= m1; ++q) acc += ((double)hr[m1 + q] + (double)hr[m1 - q]) * c1t[(long long)q * it.n1];
+            P[cc][j0] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < nc * (m0 + 1); e += blockDim.x) {
+            const int cc = e / (m0 + 1), q = e - cc * (m0 + 1);
+            const double v = q == 0 ? P[cc][m0] : P[cc][m0 + q] + P[cc][m0 - q];
+            if constexpr (sizeof(T) == 8) {
+                A[cc][q] = v;
+            } else {
+                const float hi = (float)v;
+                Af[q][cc] = make_float2(hi, (float)(v - (double)hi));
+            }
+        }
+        __syncthreads();
+        T* o = D + it.img_off + (long long)c0 * it.n0;
+        for (int t0 = threadIdx.x; t0 < it.n0; t0 += blockDim.x) {
+            if constexpr (sizeof(T) == 8) {
+                const double* c0t = costab + it.cos0 + t0;
+                double acc[kEigCols];
+#pragma unroll
+                for (int cc = 0; cc < kEigCols; ++cc) acc[cc] = A[cc][0];
+                for (int q = 1; q <= m0; ++q) {
+                    const double cq = c0t[(long long)q * it.n0];
+#pragma unroll
+                    for (int cc = 0; cc < kEigCols; ++cc) acc[cc] += A[cc][q] * cq;
+                }
+#pragma unroll
+                for (int cc = 0; cc < kEigCols; ++cc)
+                    if (cc < nc) o[(long long)cc * it.n0 + t0] = (T)acc[cc];
+            } else {
+                const float2* c0t = costab2 + it.cos0 + t0;
+                float s[kEigCols], r[kEigCols];
+#pragma unroll
+                for (int cc = 0; cc < kEigCols; ++cc) { s[cc] = Af[0][cc].x; r[cc] = Af[0][cc].y; }
+                for (int q = 1; q <= m0; ++q) {
+                    const float2 cq = c0t[(long long)q * it.n0];
+#pragma unroll
+                    for (int cc = 0; cc < kEigCols; ++cc) {
+                        const float2 a = Af[q][cc];
+                        // the _rn intrinsics keep the compiler from fusing these into FMAs
+                        const float p = __fmul_rn(a.x, cq.x);
+                        const float pe = __fmaf_rn(a.x, cq.x, -p);           // a.x cq.x = p + pe exactly
+                        const float sn = __fadd_rn(s[cc], p);                // TwoSum: s + p = sn + se exactly
+                        const float bv = __fsub_rn(sn, s[cc]);
+                        const float se = __fadd_rn(__fsub_rn(s[cc], __fsub_rn(sn, bv)), __fsub_rn(p, bv));
+                        s[cc] = sn;
+                        r[cc] += se + pe + __fmaf_rn(a.x, cq.y, a.y * cq.x);
+                    }
+                }
+#pragma unroll
+                for (int cc = 0; cc < kEigCols; ++cc)
+                    if (cc < nc) o[(long long)cc * it.n0 + t0] = s[cc] + r[cc];
+            }
+        }
+        k = queue_handover(drawn, slot);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+kp_gcv(const int2* __restrict__ work, int count, int* __restrict__ counter, const GcvItem* __restrict__ gi,
+       const T* __restrict__ G, const T* __restrict__ D, const T* __restrict__ muT, double* __restrict__ partials) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int slot;
+    for (int k = queue_first(counter, slot); k < count;) {
+        const int drawn = queue_draw(counter);
+        const int2 w = work[k];
+        const GcvItem g = gi[w.x];
+        gcv_partials_body<T, false>(G + g.spec_off, D + g.spec_off, muT, g.geo, (long long)w.y * g.geo.chunk,
+                                    partials + g.part_off + (long long)w.y * 2 * g.geo.K, smem_raw);
+        k = queue_handover(drawn, slot);
+    }
+}
+
 }  // namespace hobc
 
 using namespace hobc;
@@ -192,7 +314,10 @@ struct hobc_batch_s {
     int gcv_count;
     int2* eig_work;
     int eig_count;
-    std::vector<PassList> rowA, colA, colS, rowS;
+    PassList pass[4];        // row analysis, column analysis, column synthesis (+ filter), row synthesis
+    int* counters;           // [6] work counters of the persistent passes (eig, 4 line passes, gcv)
+    int grid[6];             // resident CTAs of each persistent pass
+    std::vector<hobc_fft_schedule> schedule;   // the radix of every (degree, FFT length) the caller chose
     double* mu;
     void* muT;
     void *R, *G, *D;
@@ -201,6 +326,7 @@ struct hobc_batch_s {
     double* gcv_ws;
     BatchIO* io_dev;
     double* costab;          // per-axis tables cos(k theta_t), k <= the largest PSF half-width
+    float2* costab2;         // the same split into float pairs hi + lo (FP32 batches)
     cudaGraphExec_t graph;
     int launches;
 };
@@ -220,24 +346,28 @@ hobc_status launch_all(hobc_batch_s* b) {
     T* G = reinterpret_cast<T*>(b->G);
     T* D = reinterpret_cast<T*>(b->D);
     int launches = 0;
-    if (b->eig_count) { kb_eig<T><<<b->eig_count, 256, 0, st>>>(b->eig_work, b->items_dev, io, b->costab, D); ++launches; }
-    for (const PassList& l : b->rowA) {
-        if (!l.count) continue;
-        if (l.fam == FAM_S) kb_pair_analysis<T, FAM_S><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, nullptr, 1, io, R);
-        else if (l.fam == FAM_C) kb_pair_analysis<T, FAM_C><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, nullptr, 1, io, R);
-        else kb_pair_analysis<T, FAM_S3><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, nullptr, 1, io, R);
+    cudaError_t e = cudaMemsetAsync(b->counters, 0, 6 * sizeof(int), st);
+    if (e != cudaSuccess) { set_last_error("hobc_deblur_batched", e); return HOBC_ERR_CUDA; }
+    int* ctr = b->counters;
+    if (b->eig_count) {
+        kp_eig<T><<<b->grid[0], 256, 0, st>>>(b->eig_work, b->eig_count, ctr + 0, b->items_dev, io, b->costab, b->costab2,
+                                               D);
         ++launches;
     }
-    for (const PassList& l : b->colA) {
-        if (!l.count) continue;
-        if (l.fam == FAM_S) kb_pair_analysis<T, FAM_S><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, R, 0, io, G);
-        else if (l.fam == FAM_C) kb_pair_analysis<T, FAM_C><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, R, 0, io, G);
-        else kb_pair_analysis<T, FAM_S3><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, R, 0, io, G);
+    const PassList* P = b->pass;
+    if (P[0].count) {
+        kp_analysis<T><<<b->grid[1], kBatchThreads, P[0].smem, st>>>(P[0].dev, P[0].count, ctr + 1, axes, nullptr, 1,
+                                                                      io, R);
+        ++launches;
+    }
+    if (P[1].count) {
+        kp_analysis<T><<<b->grid[2], kBatchThreads, P[1].smem, st>>>(P[1].dev, P[1].count, ctr + 2, axes, R, 0, io,
+                                                                      G);
         ++launches;
     }
     const size_t gsmem = 4 * (size_t)gcv_chunk_for(1LL << 40, b->K, sizeof(T) == 8) * sizeof(T);
-    kb_gcv<T><<<b->gcv_count, 256, gsmem, st>>>(b->gcv_work, b->gcv_items_dev, G, D, reinterpret_cast<const T*>(b->muT),
-                                                b->partials);
+    kp_gcv<T><<<b->grid[5], 256, gsmem, st>>>(b->gcv_work, b->gcv_count, ctr + 5, b->gcv_items_dev, G, D,
+                                              reinterpret_cast<const T*>(b->muT), b->partials);
     kb_gcv_finalize<<<b->count, 256, 0, st>>>(b->gcv_items_dev, b->partials, io, b->K);
     launches += 2;
     FilterDesc fd;
@@ -245,24 +375,30 @@ hobc_status launch_all(hobc_batch_s* b) {
     fd.mu = b->mu;
     fd.K = b->K;
     fd.lap = b->desc.L == HOBC_L_LAPLACIAN;
-    for (const PassList& l : b->colS) {
-        if (!l.count) continue;
-        if (l.fam == FAM_S) kb_pair_synthesis<T, FAM_S, 2><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, G, R, 0, io, D, fd);
-        else if (l.fam == FAM_C) kb_pair_synthesis<T, FAM_C, 2><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, G, R, 0, io, D, fd);
-        else kb_pair_synthesis<T, FAM_S3, 2><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, G, R, 0, io, D, fd);
+    if (P[2].count) {
+        kp_synthesis<T, 2><<<b->grid[3], kBatchThreads, P[2].smem, st>>>(P[2].dev, P[2].count, ctr + 3, axes, G, R, 0,
+                                                                          io, D, fd);
         ++launches;
     }
-    for (const PassList& l : b->rowS) {
-        if (!l.count) continue;
-        if (l.fam == FAM_S) kb_pair_synthesis<T, FAM_S, 0><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, R, nullptr, 1, io, D, fd);
-        else if (l.fam == FAM_C) kb_pair_synthesis<T, FAM_C, 0><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, R, nullptr, 1, io, D, fd);
-        else kb_pair_synthesis<T, FAM_S3, 0><<<l.count, kBatchThreads, l.smem, st>>>(l.dev, axes, R, nullptr, 1, io, D, fd);
+    if (P[3].count) {
+        kp_synthesis<T, 0><<<b->grid[4], kBatchThreads, P[3].smem, st>>>(P[3].dev, P[3].count, ctr + 4, axes, R,
+                                                                          nullptr, 1, io, D, fd);
         ++launches;
     }
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) { set_last_error("hobc_deblur_batched launch", e); return HOBC_ERR_CUDA; }
     b->launches = launches;
     return HOBC_OK;
+}
+
+// Resident CTAs of a persistent kernel: the SMs times the CTAs that fit on one.
+template <typename K>
+int resident_ctas(K kernel, size_t smem, int work) {
+    int dev = 0, sms = 1, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, smem) != cudaSuccess || per < 1) per = 1;
+    return std::max(1, std::min(work, sms * per));
 }
 
 template <typename T>
@@ -270,15 +406,10 @@ cudaError_t prepare_batched() {
     const int lim = 200 * 1024;
     cudaError_t e = cudaSuccess;
 #define HOBC_BSMEM(k) if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
-    HOBC_BSMEM((kb_pair_analysis<T, FAM_S>));
-    HOBC_BSMEM((kb_pair_analysis<T, FAM_C>));
-    HOBC_BSMEM((kb_pair_analysis<T, FAM_S3>));
-    HOBC_BSMEM((kb_pair_synthesis<T, FAM_S, 0>));
-    HOBC_BSMEM((kb_pair_synthesis<T, FAM_C, 0>));
-    HOBC_BSMEM((kb_pair_synthesis<T, FAM_S3, 0>));
-    HOBC_BSMEM((kb_pair_synthesis<T, FAM_S, 2>));
-    HOBC_BSMEM((kb_pair_synthesis<T, FAM_C, 2>));
-    HOBC_BSMEM((kb_pair_synthesis<T, FAM_S3, 2>));
+    HOBC_BSMEM((kp_analysis<T>));
+    HOBC_BSMEM((kp_synthesis<T, 0>));
+    HOBC_BSMEM((kp_synthesis<T, 2>));
+    HOBC_BSMEM((kp_gcv<T>));
 #undef HOBC_BSMEM
     return e;
 }
@@ -288,7 +419,7 @@ Axis<T> to_dev_axis(const AxisHost& a) {
     Axis<T> x;
     memset(&x, 0, sizeof(x));
     x.fam = a.fam; x.n = a.n; x.N = a.N; x.L = a.L; x.M = a.M; x.log2M = a.log2M;
-    x.blue = a.blue; x.tpg = a.tpg; x.Mp = group_slots(a.M); x.H = a.H; x.W = a.W;
+    x.blue = a.blue; x.tpg = a.tpg; x.r16 = a.r16; x.Mp = group_slots(a.M); x.H = a.H; x.W = a.W;
     x.tw = reinterpret_cast<const C2<T>*>(a.tw);
     x.chirp = reinterpret_cast<const C2<T>*>(a.chirp);
     x.bhat = reinterpret_cast<const C2<T>*>(a.bhat);
@@ -321,20 +452,28 @@ extern "C" void hobc_batch_destroy(hobc_batch* b) {
         cudaFree(a.tw); cudaFree(a.chirp); cudaFree(a.bhat); cudaFree(a.post); cudaFree(a.q); cudaFree(a.q2);
         cudaFree(a.etab);
     }
-    for (auto* lists : {&b->rowA, &b->colA, &b->colS, &b->rowS})
-        for (PassList& l : *lists) cudaFree(l.dev);
+    for (PassList& l : b->pass) cudaFree(l.dev);
+    cudaFree(b->counters);
     cudaFree(b->axes_dev); cudaFree(b->items_dev); cudaFree(b->gcv_items_dev); cudaFree(b->gcv_work);
     cudaFree(b->costab);
+    cudaFree(b->costab2);
     cudaFree(b->eig_work); cudaFree(b->mu); cudaFree(b->muT); cudaFree(b->R); cudaFree(b->G); cudaFree(b->D);
     cudaFree(b->partials); cudaFree(b->mu_idx_ws); cudaFree(b->gcv_ws); cudaFree(b->io_dev);
     delete b;
 }
 
-extern "C" hobc_status hobc_batch_create(const hobc_batch_desc* desc, const hobc_batch_item* items,
-                                         const double* mu_grid_host, void* cuda_stream, hobc_batch** out) {
+extern "C" hobc_status hobc_batch_create_tuned(const hobc_batch_desc* desc, const hobc_batch_item* items,
+                                               const double* mu_grid_host, const hobc_fft_schedule* schedule,
+                                               int schedule_len, void* cuda_stream, hobc_batch** out) {
     if (!out) return HOBC_ERR_ARG;
     *out = nullptr;
-    if (!desc || !items || !mu_grid_host) return HOBC_ERR_ARG;
+    if (!desc || !items || !mu_grid_host || schedule_len < 0 || (schedule_len > 0 && !schedule)) return HOBC_ERR_ARG;
+    for (int k = 0; k < schedule_len; ++k) {
+        const hobc_fft_schedule& e = schedule[k];
+        if (family_of(e.bc_degree) < 0 || e.fft_length < 8 || (e.fft_length & (e.fft_length - 1)) ||
+            (e.radix != 0 && e.radix != 8 && e.radix != 16))
+            return HOBC_ERR_ARG;
+    }
     const hobc_batch_desc d = *desc;
     if (d.count < 1 || d.n_mu < 1) return HOBC_ERR_ARG;
     if (d.prec != HOBC_FP64 && d.prec != HOBC_FP32) return HOBC_ERR_ARG;
@@ -357,6 +496,7 @@ extern "C" hobc_status hobc_batch_create(const hobc_batch_desc* desc, const hobc
         }
     }
     hobc_batch_s* b = new hobc_batch_s();
+    b->schedule.assign(schedule, schedule + schedule_len);
     b->desc = d;
     b->count = d.count;
     b->K = d.n_mu;
@@ -372,9 +512,16 @@ extern "C" hobc_status hobc_batch_create(const hobc_batch_desc* desc, const hobc
         auto key = std::make_pair(fam, n);
         auto itr = axis_id.find(key);
         if (itr != axis_id.end()) return itr->second;
+        // the radix the schedule gives this (degree, FFT length), else the default
+        const int deg = fam == FAM_S ? 1 : fam == FAM_C ? 2 : 3;
+        const int M = fft_length_of(fam, n);
+        int radix = 0;
+        for (const hobc_fft_schedule& e : b->schedule)
+            if (e.bc_degree == deg && e.fft_length == M) radix = e.radix;
         AxisHost a;
         if (err == cudaSuccess)
-            err = d.prec == HOBC_FP64 ? build_axis_host<double>(a, fam, n, 1, false) : build_axis_host<float>(a, fam, n, 1, false);
+            err = d.prec == HOBC_FP64 ? build_axis_host<double>(a, fam, n, 1, false, radix)
+                                      : build_axis_host<float>(a, fam, n, 1, false, radix);
         b->axes_host.push_back(a);
         const int id = (int)b->axes_host.size() - 1;
         axis_id[key] = id;
@@ -422,6 +569,12 @@ extern "C" hobc_status hobc_batch_create(const hobc_batch_desc* desc, const hobc
             idev[i].cos1 = base[ax1[i]];
         }
         b->costab = reinterpret_cast<double*>(upload(tab, err));
+        std::vector<float2> tab2(tab.size());
+        for (size_t k = 0; k < tab.size(); ++k) {
+            const float hi = (float)tab[k];
+            tab2[k] = make_float2(hi, (float)(tab[k] - (double)hi));
+        }
+        b->costab2 = reinterpret_cast<float2*>(upload(tab2, err));
     }
     if (err == cudaSuccess) {
         if (d.prec == HOBC_FP64) {
@@ -436,46 +589,52 @@ extern "C" hobc_status hobc_batch_create(const hobc_batch_desc* desc, const hobc
     }
     b->items_dev = reinterpret_cast<ItemDev*>(upload(idev, err));
 
-    // line work lists: every pass, per family; a CTA covers 2G lines, G = 256/tpg
+    // line work lists of the four passes, every family in one list: a work item
+    // covers 2G lines of a problem, G = 256/tpg; items sorted by decreasing FFT
+    // length, then decreasing line count, so the costliest start first
     const size_t csz = 2 * b->esz;
-    auto build_pass = [&](std::vector<PassList>& lists, int pass) {
-        for (int fam : {FAM_S, FAM_C, FAM_S3}) {
-            std::vector<LineWork> w;
-            size_t smem = 0;
-            for (int i = 0; i < d.count; ++i) {
-                if (idev[i].fam != fam) continue;
-                const int n0 = idev[i].n0, n1 = idev[i].n1;
-                const bool rows = pass == 0 || pass == 3;         // row passes run along axis 1
-                const int ax = rows ? ax1[i] : ax0[i];
-                const AxisHost& a = b->axes_host[ax];
-                const int G = kBatchThreads / a.tpg;
-                const int nl = rows ? n0 : n1;
-                smem = std::max(smem, (size_t)G * group_slots(a.M) * csz + (size_t)2 * G * a.W * b->esz);
-                for (int r0 = 0; r0 < nl; r0 += 2 * G) {
-                    LineWork e;
-                    memset(&e, 0, sizeof(e));
-                    e.item = i; e.axis = ax; e.r0 = r0; e.nlines = nl;
-                    e.in_off = e.out_off = idev[i].img_off;
-                    e.axis_o = ax1[i];
-                    if (pass == 0) { e.in_rs = n1; e.out_rs = 1; e.out_cs = n0; }            // rows -> R[c][r]
-                    else if (pass == 1) { e.in_rs = n0; e.out_rs = n0; e.out_cs = 1; }       // R columns -> G
-                    else if (pass == 2) { e.in_rs = n0; e.in_cs = 1; e.out_rs = n0; }        // G -> R (filter)
-                    else { e.in_rs = 1; e.in_cs = n0; e.out_rs = n1; }                        // R -> f rows
-                    w.push_back(e);
-                }
+    auto build_pass = [&](PassList& l, int pass) {
+        std::vector<LineWork> w;
+        std::vector<int> cost;
+        size_t smem = 0;
+        for (int i = 0; i < d.count; ++i) {
+            const int n0 = idev[i].n0, n1 = idev[i].n1;
+            const bool rows = pass == 0 || pass == 3;         // row passes run along axis 1
+            const int ax = rows ? ax1[i] : ax0[i];
+            const AxisHost& a = b->axes_host[ax];
+            const int G = kBatchThreads / a.tpg;
+            const int nl = rows ? n0 : n1;
+            smem = std::max(smem, (size_t)G * group_slots(a.M) * csz + (size_t)2 * G * a.W * b->esz);
+            for (int r0 = 0; r0 < nl; r0 += 2 * G) {
+                LineWork e;
+                memset(&e, 0, sizeof(e));
+                e.item = i; e.axis = ax; e.r0 = r0; e.nlines = nl;
+                e.in_off = e.out_off = idev[i].img_off;
+                e.axis_o = ax1[i];
+                if (pass == 0) { e.in_rs = n1; e.out_rs = 1; e.out_cs = n0; }            // rows -> R[c][r]
+                else if (pass == 1) { e.in_rs = n0; e.out_rs = n0; e.out_cs = 1; }       // R columns -> G
+                else if (pass == 2) { e.in_rs = n0; e.in_cs = 1; e.out_rs = n0; }        // G -> R (filter)
+                else { e.in_rs = 1; e.in_cs = n0; e.out_rs = n1; }                        // R -> f rows
+                w.push_back(e);
+                cost.push_back(a.M * std::min(2 * G, nl - r0));
             }
-            PassList l;
-            l.fam = fam;
-            l.count = (int)w.size();
-            l.smem = smem;
-            l.dev = reinterpret_cast<LineWork*>(upload(w, err));
-            lists.push_back(l);
         }
+        std::vector<int> order(w.size());
+        for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+        // equal costs grouped by family: CTAs that run at the same time then mostly
+        // run the same family's code
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            if (cost[x] != cost[y]) return cost[x] > cost[y];
+            return b->axes_host[w[x].axis].fam < b->axes_host[w[y].axis].fam;
+        });
+        std::vector<LineWork> sorted(w.size());
+        for (size_t k = 0; k < order.size(); ++k) sorted[k] = w[order[k]];
+        l.fam = -1;
+        l.count = (int)sorted.size();
+        l.smem = smem;
+        l.dev = reinterpret_cast<LineWork*>(upload(sorted, err));
     };
-    build_pass(b->rowA, 0);
-    build_pass(b->colA, 1);
-    build_pass(b->colS, 2);
-    build_pass(b->rowS, 3);
+    for (int ps = 0; ps < 4; ++ps) build_pass(b->pass[ps], ps);
 
     // GCV and eigenvalue work
     std::vector<GcvItem> gi(d.count);
@@ -497,8 +656,17 @@ extern "C" hobc_status hobc_batch_create(const hobc_batch_desc* desc, const hobc
         g.part_off = part;
         part += (long long)g.nchunks * 2 * b->K;
         for (int c = 0; c < g.nchunks; ++c) gw.push_back(make_int2(i, c));
-        for (int c = 0; c < idev[i].n1; ++c) ew.push_back(make_int2(i, c));
+        for (int c = 0; c < idev[i].n1; c += kEigCols) ew.push_back(make_int2(i, c));
     }
+    // costliest first: eigenvalue columns by n0 p0, GCV chunks by their size
+    std::stable_sort(ew.begin(), ew.end(), [&](const int2& x, const int2& y) {
+        return (long long)idev[x.x].n0 * idev[x.x].p0 > (long long)idev[y.x].n0 * idev[y.x].p0;
+    });
+    std::stable_sort(gw.begin(), gw.end(), [&](const int2& x, const int2& y) {
+        const long long cx = std::min((long long)gi[x.x].geo.chunk, gi[x.x].geo.S - (long long)x.y * gi[x.x].geo.chunk);
+        const long long cy = std::min((long long)gi[y.x].geo.chunk, gi[y.x].geo.S - (long long)y.y * gi[y.x].geo.chunk);
+        return cx > cy;
+    });
     b->gcv_count = (int)gw.size();
     b->eig_count = (int)ew.size();
     b->gcv_items_dev = reinterpret_cast<GcvItem*>(upload(gi, err));
@@ -514,6 +682,22 @@ extern "C" hobc_status hobc_batch_create(const hobc_batch_desc* desc, const hobc
     alloc((void**)&b->mu_idx_ws, (size_t)d.count * sizeof(int));
     alloc((void**)&b->gcv_ws, (size_t)d.count * b->K * sizeof(double));
     alloc((void**)&b->io_dev, sizeof(BatchIO));
+    alloc((void**)&b->counters, 6 * sizeof(int));
+    if (err == cudaSuccess) {
+        const size_t gsmem = 4 * (size_t)gcv_chunk_for(1LL << 40, b->K, d.prec == HOBC_FP64) * b->esz;
+        const bool f64 = d.prec == HOBC_FP64;
+        b->grid[0] = f64 ? resident_ctas(kp_eig<double>, 0, b->eig_count) : resident_ctas(kp_eig<float>, 0, b->eig_count);
+        b->grid[1] = f64 ? resident_ctas(kp_analysis<double>, b->pass[0].smem, b->pass[0].count)
+                         : resident_ctas(kp_analysis<float>, b->pass[0].smem, b->pass[0].count);
+        b->grid[2] = f64 ? resident_ctas(kp_analysis<double>, b->pass[1].smem, b->pass[1].count)
+                         : resident_ctas(kp_analysis<float>, b->pass[1].smem, b->pass[1].count);
+        b->grid[3] = f64 ? resident_ctas(kp_synthesis<double, 2>, b->pass[2].smem, b->pass[2].count)
+                         : resident_ctas(kp_synthesis<float, 2>, b->pass[2].smem, b->pass[2].count);
+        b->grid[4] = f64 ? resident_ctas(kp_synthesis<double, 0>, b->pass[3].smem, b->pass[3].count)
+                         : resident_ctas(kp_synthesis<float, 0>, b->pass[3].smem, b->pass[3].count);
+        b->grid[5] = f64 ? resident_ctas(kp_gcv<double>, gsmem, b->gcv_count)
+                         : resident_ctas(kp_gcv<float>, gsmem, b->gcv_count);
+    }
     alloc((void**)&b->mu, sizeof(double) * b->K);
     alloc(&b->muT, b->esz * b->K);
     if (err == cudaSuccess) err = cudaMemcpy(b->mu, mu_grid_host, sizeof(double) * b->K, cudaMemcpyHostToDevice);
@@ -548,6 +732,11 @@ extern "C" hobc_status hobc_batch_create(const hobc_batch_desc* desc, const hobc
     }
     *out = b;
     return HOBC_OK;
+}
+
+extern "C" hobc_status hobc_batch_create(const hobc_batch_desc* desc, const hobc_batch_item* items,
+                                         const double* mu_grid_host, void* cuda_stream, hobc_batch** out) {
+    return hobc_batch_create_tuned(desc, items, mu_grid_host, nullptr, 0, cuda_stream, out);
 }
 
 extern "C" hobc_status hobc_batch_offsets(const hobc_batch* b, size_t* img_off, size_t* psf_off) {

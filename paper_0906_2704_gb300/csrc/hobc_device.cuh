@@ -46,7 +46,8 @@ struct Axis {
     int M;          // power-of-two FFT length (== L when L is a power of two >= 8)
     int log2M;
     int blue;       // 1: Bluestein (M >= 2L-1), 0: direct
-    int tpg;        // threads per group: M/16 when fft_r16(M), else M/8
+    int tpg;        // threads per group: M/16 with radix-16 stages (r16), else M/8
+    int r16;        // 1: radix-16 stages (M >= 256, log2M <= 12), 0: radix 8
     int Mp;         // shared-memory slots per group: group_slots(M)
     int H;          // FOURIER: floor(N/2)+1 stored frequencies; else N
     int W;          // spectrum entries stored on this axis: n (S, C) or H+2 (F)
@@ -290,6 +291,8 @@ __host__ __device__ __forceinline__ constexpr int dft16_slot(int q) { return 4 *
 
 // FFT lengths M >= 256 run with 16 values per thread (radix-16 stages, M/16
 // threads per group), smaller ones with 8 (radix-8 stages, M/8 threads).
+// Default radix of an FFT of length M: radix-16 stages from M = 256 up (the
+// batched path's autotuned schedule may choose radix 8 instead).
 __host__ __device__ __forceinline__ bool fft_r16(int M) { return M >= 256; }
 
 // A stage of the 16-values-per-thread FFT: PER = 16/R butterflies of radix R
@@ -423,7 +426,7 @@ __device__ __forceinline__ C2<T> dft_in(const Axis<T>& ax, int p, C2<T> x) {
 // such that dft_out(k), k < L, is output k; positions >= L are left undefined.
 template <typename T>
 __device__ __forceinline__ void group_dft(C2<T>* buf, const Axis<T>& ax, int t) {
-    const bool r16 = fft_r16(ax.M) && ax.log2M <= 12;
+    const bool r16 = ax.r16;
     const bool ct = ax.log2M >= 7 && ax.log2M <= 12;
     if (ax.blue) {
         // the second FFT's first stage applies the pointwise product with the

@@ -15,6 +15,7 @@ namespace hobc {
 // precision (float or double), the eigen-exponential table always in double.
 struct AxisHost {
     int fam, n, N, L, M, log2M, blue, tpg, H, W;
+    int r16;        // radix-16 FFT stages (else radix 8)
     void* tw;       // [M] complex
     void* chirp;    // [L] complex (Bluestein only)
     void* bhat;     // [M] complex (Bluestein only)
@@ -136,7 +137,10 @@ hobc_status dense_synthesis(hobc_plan_s* p, const void* c, void* y);
 hobc_status dense_filter_synthesis(hobc_plan_s* p, const void* ghat, const void* D, const int* mu_idx,
                                    const double* mu_val, void* f);
 
-template <typename T> cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half);
+// power-of-two FFT length of a line of n samples of a family (hobc_api.cu)
+int fft_length_of(int fam, int n);
+// radix: 0 the default (fft_r16), 16 or 8 to choose (16 only where M >= 256 and log2 M <= 12)
+template <typename T> cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half, int radix = 0);
 void free_axis(AxisHost& a);
 // 3D launch sequences (hobc_volume.cuh); D == nullptr: plain synthesis
 template <typename T> hobc_status run3_analysis(hobc_volume_s* q, const void* g, void* ghat);

@@ -13,7 +13,7 @@ template <typename T>
 static Axis<T> dev_axis(const AxisHost& a) {
     Axis<T> x;
     x.fam = a.fam; x.n = a.n; x.N = a.N; x.L = a.L; x.M = a.M; x.log2M = a.log2M;
-    x.blue = a.blue; x.tpg = a.tpg; x.Mp = group_slots(a.M); x.H = a.H; x.W = a.W;
+    x.blue = a.blue; x.tpg = a.tpg; x.r16 = a.r16; x.Mp = group_slots(a.M); x.H = a.H; x.W = a.W;
     x.tw = reinterpret_cast<const C2<T>*>(a.tw);
     x.chirp = reinterpret_cast<const C2<T>*>(a.chirp);
     x.bhat = reinterpret_cast<const C2<T>*>(a.bhat);

@@ -88,6 +88,16 @@ class BatchDesc(ctypes.Structure):
 _lib.hobc_batch_create.argtypes = [ctypes.POINTER(BatchDesc), ctypes.POINTER(BatchItem),
                                    ctypes.POINTER(ctypes.c_double), _vp, ctypes.POINTER(_vp)]
 _lib.hobc_batch_create.restype = ctypes.c_int
+class FftSchedule(ctypes.Structure):
+    _fields_ = [("bc_degree", ctypes.c_int), ("fft_length", ctypes.c_int), ("radix", ctypes.c_int)]
+
+
+_lib.hobc_batch_create_tuned.argtypes = [ctypes.POINTER(BatchDesc), ctypes.POINTER(BatchItem),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(FftSchedule), ctypes.c_int,
+                                         _vp, ctypes.POINTER(_vp)]
+_lib.hobc_batch_create_tuned.restype = ctypes.c_int
+_lib.hobc_fft_length.argtypes = [ctypes.c_int, ctypes.c_int]
+_lib.hobc_fft_length.restype = ctypes.c_int
 _lib.hobc_batch_destroy.argtypes = [_vp]
 _lib.hobc_batch_destroy.restype = None
 _lib.hobc_batch_offsets.argtypes = [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]
@@ -281,6 +291,11 @@ def tc_split(src, src_ld, src_bs, rows, cols, hi, lo, ld, bs, rows_padded, batch
     st = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(_lib.hobc_tc_split(_ptr(src), src_ld, src_bs, rows, cols, _ptr(hi), _ptr(lo), ld, bs, rows_padded,
                               batch, _vp(st)), "hobc_tc_split")
+
+
+def fft_length(bc_degree: int, n: int) -> int:
+    """FFT length of a line of n samples under a boundary-condition degree (hobc_fft_length)."""
+    return int(_lib.hobc_fft_length(int(bc_degree), int(n)))
 
 
 def gcv_noalloc_max_bytes() -> int:
@@ -553,8 +568,9 @@ class Batch:
     """A batch plan: many 2D problems of uneven sizes, each with its own
     symmetric PSF and boundary degree (1, 2, 3), deblurred in one call."""
 
-    def __init__(self, items, mu_grid, L: str = "lap", prec: str = "fp64", stream=None):
-        """items: sequence of (n0, n1, psf0, psf1, bc_degree)."""
+    def __init__(self, items, mu_grid, L: str = "lap", prec: str = "fp64", stream=None, schedule=None):
+        """items: sequence of (n0, n1, psf0, psf1, bc_degree); schedule: optional
+        sequence of (bc_degree, fft_length, radix) (hobc_batch_create_tuned)."""
         arr = (BatchItem * len(items))()
         for i, (n0, n1, p0, p1, deg) in enumerate(items):
             arr[i].n[0], arr[i].n[1], arr[i].psf[0], arr[i].psf[1], arr[i].bc_degree = n0, n1, p0, p1, deg
@@ -567,9 +583,15 @@ class Batch:
         elif not isinstance(stream, int):
             stream = stream.cuda_stream
         self._handle = _vp()
-        _check(_lib.hobc_batch_create(ctypes.byref(d), arr, mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                      _vp(stream), ctypes.byref(self._handle)), "hobc_batch_create")
+        sched = list(schedule or [])
+        sarr = (FftSchedule * max(1, len(sched)))()
+        for i, (deg, M, rad) in enumerate(sched):
+            sarr[i].bc_degree, sarr[i].fft_length, sarr[i].radix = int(deg), int(M), int(rad)
+        _check(_lib.hobc_batch_create_tuned(ctypes.byref(d), arr, mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            sarr, len(sched), _vp(stream), ctypes.byref(self._handle)),
+               "hobc_batch_create_tuned")
         self.items, self.mu_grid, self.prec, self.L = list(items), mu, prec, L
+        self.schedule = sched
         io = (_sz * (len(items) + 1))()
         po = (_sz * (len(items) + 1))()
         _check(_lib.hobc_batch_offsets(self._handle, io, po), "hobc_batch_offsets")

@@ -160,3 +160,24 @@ def test_fp32_degree4_rejected(hobc):
         with pytest.raises(hobc.HobcError) as ei:
             _create(hobc, n=n, psf=3, bc_degree=4, prec="fp32")
         assert hobc.STATUS[ei.value.status] == "HOBC_ERR_UNSUPPORTED"
+
+
+def test_fft_length_and_schedule_validation(hobc):
+    """FFT lengths of the batched path's lines (host arithmetic, no device): the
+    core DFT (N = n - 2, n - 4 for degree 3; 2(N + 1) for degrees 1 and 3) if it is
+    a power of two, else the chirp-z padding 2^k >= 2 L - 1."""
+    assert hobc.fft_length(2, 66) == 64          # N = 64
+    assert hobc.fft_length(2, 512) == 1024       # L = 510 -> 2^k >= 1019
+    assert hobc.fft_length(1, 129) == 256        # L = 2 * 128 = 256
+    assert hobc.fft_length(1, 130) == 1024       # L = 258 -> 2^k >= 515
+    assert hobc.fft_length(3, 100) == 512        # N = 96, L = 194 -> 2^k >= 387
+    assert hobc.fft_length(4, 100) == 0 and hobc.fft_length(2, 5) == 0
+    lib = hobc.library()
+    bad = (hobc.FftSchedule * 1)()
+    bad[0].bc_degree, bad[0].fft_length, bad[0].radix = 2, 500, 8
+    out = ctypes.c_void_p()
+    d = hobc.BatchDesc()
+    d.count, d.n_mu = 1, 1
+    it = (hobc.BatchItem * 1)()
+    mu = (ctypes.c_double * 1)(1e-2)
+    assert lib.hobc_batch_create_tuned(ctypes.byref(d), it, mu, bad, 1, None, ctypes.byref(out)) == 1

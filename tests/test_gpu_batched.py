@@ -67,7 +67,11 @@ def test_batched_matches_plan_and_oracle(prec, L):
         plan.deblur(torch.from_numpy(gs[i][None].astype(dt)).cuda(), torch.from_numpy(hs[i].astype(dt)).cuda(),
                     fp, mp, Gp)
         torch.cuda.synchronize()
-        assert np.max(np.abs(G[i] - Gp.cpu().numpy()[0]) / Gp.cpu().numpy()[0]) <= tol, f"G vs plan, item {i}"
+        # the two paths sum the eigenvalues differently (cosine recurrence here, complex
+        # tables there) before rounding them to the working precision, so an FP32 d may
+        # differ by an ulp, which the GCV terms carry: G is compared at 4 tol in FP32
+        gtol_plan = tol if prec == "fp64" else 4 * tol
+        assert np.max(np.abs(G[i] - Gp.cpu().numpy()[0]) / Gp.cpu().numpy()[0]) <= gtol_plan, f"G vs plan, item {i}"
         assert mi[i] == mp.cpu().numpy()[0], f"mu* vs plan, item {i}"
         # the two paths differ only in how the eigenvalues are summed (cosine recurrence
         # here, complex tables there); the difference is magnified by cond(T0) cond(T1)
@@ -110,3 +114,70 @@ def test_batched_rejects_bad_items():
         with pytest.raises(hobc.HobcError) as ei:
             hobc.Batch([(20, 20, 3, 3, 2), bad], mus)
         assert hobc.STATUS[ei.value.status] == status
+
+
+BIG = [(130, 140, 5, 5, 1), (200, 150, 7, 7, 2), (150, 100, 5, 5, 3), (96, 257, 3, 9, 2), (64, 64, 3, 3, 1)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fft_schedule_radix8_matches_radix16_and_the_oracle(prec):
+    """A schedule that runs every FFT of length >= 256 in radix 8 (hobc_batch_create_tuned)
+    gives the default (radix 16) results to rounding, and the oracle's in FP64."""
+    dt = np.float64 if prec == "fp64" else np.float32
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    K = 24
+    mus = synth.mu_grid(K, 1e-6, 1.0)
+    gs, hs = _problems(BIG, 23)
+    gs = [x.astype(dt).astype(np.float64) for x in gs]
+    hs = [x.astype(dt).astype(np.float64) for x in hs]
+    kinds = sorted({(deg, hobc.fft_length(deg, n)) for (n0, n1, _, _, deg) in BIG for n in (n0, n1)})
+    assert any(M >= 256 for _, M in kinds)
+    sched8 = [(deg, M, 8) for deg, M in kinds if M >= 256]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b16 = hobc.Batch(BIG, mus, L="lap", prec=prec, stream=stream)
+        b8 = hobc.Batch(BIG, mus, L="lap", prec=prec, stream=stream, schedule=sched8)
+        f16, m16, G16 = _run(b16, gs, hs, dt, K)
+        f8, m8, G8 = _run(b8, gs, hs, dt, K)
+    assert b8.last_launch_count <= 7
+    for i, (n0, n1, p0, p1, deg) in enumerate(BIG):
+        fam = P.FAM_LETTER[FAM[deg]]
+        cond = np.linalg.cond(O.transform_matrix(fam, n0)) * np.linalg.cond(O.transform_matrix(fam, n1))
+        eps = 2.0 ** -53 if prec == "fp64" else 2.0 ** -24
+        assert np.max(np.abs(G8[i] - G16[i]) / G16[i]) <= max(tol, 64 * eps * cond), f"G item {i}"
+        assert m8[i] == m16[i] or G16[i][m8[i]] <= (1 + tol) * G16[i].min(), f"mu* item {i}"
+        a = f8[b8.img_off[i]:b8.img_off[i + 1]]
+        c = f16[b16.img_off[i]:b16.img_off[i + 1]]
+        if m8[i] == m16[i]:
+            assert np.abs(a - c).max() <= max(1e3 * tol, 64 * eps * cond) * max(1.0, np.abs(c).max()), f"f item {i}"
+        if prec == "fp64":
+            ghat, d, s, Go, ko = P.oracle_steps(fam, 2, hs[i], gs[i], "lap", mus)
+            gtol = max(1e-8, 1e-14 * cond)
+            assert np.max(np.abs(G8[i] - Go) / Go) <= gtol, f"G vs oracle, item {i}"
+            fo = P.oracle_filtered(fam, 2, ghat, d, s, mus[m8[i]])
+            assert np.abs(a.reshape(n0, n1) - fo).max() <= max(1e-10, 1e-13 * cond) * max(1.0, np.abs(fo).max())
+
+
+def test_schedule_entries_are_checked():
+    mus = synth.mu_grid(4)
+    for bad in ((4, 512, 8), (2, 500, 8), (2, 512, 4)):
+        with pytest.raises(hobc.HobcError) as ei:
+            hobc.Batch([(20, 20, 3, 3, 2)], mus, schedule=[bad])
+        assert hobc.STATUS[ei.value.status] == "HOBC_ERR_ARG"
+
+
+def test_autotuner_writes_and_reuses_its_table(tmp_path):
+    from paper_0906_2704_gb300 import autotune
+    items = [(n, n, 3, 3, deg) for deg in (1, 2) for n in (130, 200, 300)]
+    mus = synth.mu_grid(16)
+    cache = str(tmp_path / "sched.json")
+    sched, rec = autotune.tune_batched(items, mus, L="lap", prec="fp32", cache=cache, per_kind=8, reps=2, warmup=1)
+    kinds = {(deg, hobc.fft_length(deg, n)) for (n, _, _, _, deg) in items}
+    assert {(d_, M) for d_, M, _ in sched} == {k for k in kinds if k[1] >= 256}
+    assert all(r in (8, 16) for _, _, r in sched)
+    for name, v in rec.items():
+        assert v["radix"] == (16 if v["ms_radix16"] <= v["ms_radix8"] else 8)
+    sched2, _ = autotune.tune_batched(items, mus, L="lap", prec="fp32", cache=cache)   # from the cache
+    assert sched2 == sched
+    b = hobc.Batch(items, mus, L="lap", prec="fp32", stream=torch.cuda.current_stream(), schedule=sched)
+    assert b.last_launch_count >= 0
