@@ -30,17 +30,20 @@
  * and the layout of hobc_eigenvalues):  spectral index t of one axis is column
  * t of T_X on that axis: t = 0 is the left border vector (p or q), t = 1..n-2
  * the trigonometric columns in the natural order of the transform, t = n-1 the
- * right border vector.  SINE_CUBIC and COSINE_QUARTIC have two border columns
- * on each side: t = 0, 1 (L1, L2 or Q1, Q2) and t = n-2, n-1 (their flips),
- * t = 2..n-3 trigonometric.
+ * right border vector.  SINE_CUBIC, COSINE_QUARTIC and FOURIER_QUARTIC have two
+ * border columns on each side: t = 0, 1 (L1, L2 or Q1, Q2) and t = n-2, n-1
+ * (their flips), t = 2..n-3 trigonometric.  PERIODIC on the FFT path has none:
+ * t = 0..n-1 are the DFT frequencies.
  *   Families SINE, SINE_CUBIC, COSINE and COSINE_QUARTIC keep real spectra: one item is n values (1D) or
  *   n1 x n0 values stored as [t1][t0] (2D, t0 fastest).
  *   Family FOURIER stores complex values (re, im interleaved) and, because g is
  *   real, only the half of axis 1 that determines the rest:
  *   W = floor((n-2)/2) + 3 entries, index c = 0 -> t = 0, c = 1..W-2 -> t = c
  *   (frequencies 0..floor((n-2)/2)), c = W-1 -> t = n-1.  One item is W values
- *   (1D) or W1 x n0 values stored as [c][t0] (2D).  hobc_spectrum_size reports
- *   the per-item element counts.
+ *   (1D) or W1 x n0 values stored as [c][t0] (2D).  FOURIER_QUARTIC stores the
+ *   same way with W = floor((n-4)/2) + 5 (c = 0, 1 -> t = 0, 1; c = W-2, W-1 ->
+ *   t = n-2, n-1), PERIODIC with W = floor(n/2) + 1 (c = t).  hobc_spectrum_size
+ *   reports the per-item element counts.
  */
 #ifndef HOBC_H
 #define HOBC_H
@@ -64,7 +67,8 @@ typedef enum {
 typedef enum {
     HOBC_FAMILY_AUTO = 0,      /* degree 1 -> SINE; degree 2 -> COSINE if the desc says
                                   the PSF is symmetric, else FOURIER; degree 3 -> SINE_CUBIC;
-                                  degree 4 -> COSINE_QUARTIC                               */
+                                  degree 4 -> COSINE_QUARTIC if symmetric, else
+                                  FOURIER_QUARTIC                                          */
     HOBC_FAMILY_SINE = 1,      /* antireflective, Sec. 2.2, Eq. (eq:ART), (eq:jcf)       */
     HOBC_FAMILY_COSINE = 2,    /* degree 2, symmetric PSF, Sec. 3.1, Eq. (eq:Tc), (eq:Ac) */
     HOBC_FAMILY_FOURIER = 3,   /* degree 2, any PSF, Sec. 3.2, Eq. (eq:Tf), (eq:Af)      */
@@ -74,11 +78,16 @@ typedef enum {
     HOBC_FAMILY_REFLECTIVE = 5, /* classical reflective conditions (Sec. 2, Eq. (eq:refm)):
                                   T = C^T, the orthonormal DCT-II of order n, theta_k =
                                   k pi / n; bc_degree 0, symmetric PSF, HOBC_SPLIT_BF16 only */
-    HOBC_FAMILY_PERIODIC = 6,   /* classical periodic conditions (Sec. 2, Eq. (eq:permat)) in
-                                  the real Hartley basis (for a symmetric PSF it
-                                  diagonalises the circulant as F^H does), theta_k =
-                                  2 pi k / n; bc_degree 0, symmetric PSF, HOBC_SPLIT_BF16 only */
-    HOBC_FAMILY_COSINE_QUARTIC = 7 /* degree 4, symmetric PSF: the construction of Sec. 3.1
+    HOBC_FAMILY_PERIODIC = 6,   /* classical periodic conditions (Sec. 2, Eq. (eq:permat)),
+                                  theta_k = 2 pi k / n, bc_degree 0.  FP64 / FP32: T = F^H,
+                                  the unitary DFT of order n on the FFT path (no border
+                                  columns), any PSF, complex spectrum stored like FOURIER's
+                                  without border entries (a half of floor(n/2)+1 entries on
+                                  the last axis); plain method, steps, host calls and the
+                                  allocation-free scan.  HOBC_SPLIT_BF16: the real Hartley
+                                  basis (for a symmetric PSF it diagonalises the circulant
+                                  as F^H does), symmetric PSF only                        */
+    HOBC_FAMILY_COSINE_QUARTIC = 7, /* degree 4, symmetric PSF: the construction of Sec. 3.1
                                   with two border columns per side, DCT-II of order n-4 on
                                   x_a = (2a-3) pi/(2(n-4)), border columns (b-x)^2, (b-x)^4
                                   and their flips spanning the quartics with the constant;
@@ -87,6 +96,15 @@ typedef enum {
                                   FP32 is meaningful only for small n.  Plain method
                                   (plans, steps, host call, binned / refined / learned mu)
                                   and the exact GCV; not in the dense, batched or 3D paths */
+    HOBC_FAMILY_FOURIER_QUARTIC = 8 /* degree 4, any PSF (reading R17): the construction of
+                                  Sec. 3.2 with two border columns per side, DFT of order
+                                  N = n-4 on x_a = (a-2) 2 pi/N (rows 0, 1 repeat rows n-4,
+                                  n-3 and rows n-2, n-1 repeat rows 2, 3), border columns
+                                  (b-x)^2, (b-x)^4 and their flips; the quartic-preserving
+                                  (and so also cubic-preserving) answer for a nonsymmetric
+                                  PSF.  Stored like FOURIER with two border entries on each
+                                  side (W = floor(N/2)+5 on the last axis).  FP64 only; plain
+                                  method, steps, host calls and the allocation-free scan   */
 } hobc_family;
 
 typedef enum {
@@ -114,8 +132,8 @@ typedef struct {
                                   each in [6, 1024]                                        */
     int psf[2];                /* PSF mask size (odd): 1D psf[0] = 2m+1; 2D rows x cols;
                                   needs psf[i] <= n[i] - 2 (Sec. 2.2, Sec. 3), or
-                                  psf[i] <= n[i] - 4 (and n[i] >= 8) for SINE_CUBIC and
-                                  COSINE_QUARTIC                                          */
+                                  psf[i] <= n[i] - 4 (and n[i] >= 8) for SINE_CUBIC,
+                                  COSINE_QUARTIC and FOURIER_QUARTIC                      */
     int bc_degree;             /* 1, 2, 3 or 4 (0 with the REFLECTIVE / PERIODIC families) */
     hobc_family family;
     int psf_symmetric;         /* caller asserts h_{-j} = h_j on every axis (used by AUTO) */

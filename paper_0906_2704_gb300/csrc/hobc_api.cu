@@ -162,8 +162,13 @@ cd expm_ipi(long long a, long long b) {
 void theta_frac(int fam, int n, int t, long long& num, long long& den) {
     const int N = n - 2;
     if (fam == hobc::FAM_R) { num = t; den = n; return; }          // comparison families: no border columns
-    if (fam == hobc::FAM_PH) { num = 2LL * t; den = n; return; }
+    if (fam == hobc::FAM_PH || fam == hobc::FAM_P) { num = 2LL * t; den = n; return; }
     if (t == 0 || t == n - 1) { num = 0; den = 1; return; }
+    if (fam == hobc::FAM_F4) {                     // degree 4, Fourier basis: DFT of order n - 4
+        if (t == 1 || t == n - 2) { num = 0; den = 1; }
+        else { num = 2LL * (t - 2); den = n - 4; }
+        return;
+    }
     if (fam == hobc::FAM_S3) {                     // N of the cubic family is n - 4
         if (t == 1 || t == n - 2) { num = 0; den = 1; }
         else { num = t - 1; den = n - 3; }
@@ -242,6 +247,26 @@ static void quartic_columns(int n, std::vector<double>& Q1, std::vector<double>&
     for (int a = 0; a < n; ++a) { Q1[a] /= sqrt(n1); Q2[a] /= sqrt(n2); }
 }
 
+// Border columns Q1, Q2 of the degree-4 Fourier family (reading R17) on
+// x_a = (a - 2) 2 pi/N, a = 0..n-1, N = n - 4, b = x_{n-1}: Q1 = (b - x)^2,
+// Q2 = (b - x)^4, each of unit norm.
+static void fourier_quartic_columns(int n, std::vector<double>& Q1, std::vector<double>& Q2) {
+    const int N = n - 4;
+    const double b = (n - 3.0) * 2.0 * M_PI / N;
+    Q1.assign(n, 0.0);
+    Q2.assign(n, 0.0);
+    double n1 = 0, n2 = 0;
+    for (int a = 0; a < n; ++a) {
+        const double x = (a - 2.0) * 2.0 * M_PI / N;
+        const double u = (b - x) * (b - x);
+        Q1[a] = u;
+        Q2[a] = u * u;
+        n1 += Q1[a] * Q1[a];
+        n2 += Q2[a] * Q2[a];
+    }
+    for (int a = 0; a < n; ++a) { Q1[a] /= sqrt(n1); Q2[a] /= sqrt(n2); }
+}
+
 // Gauss-Jordan inverse of a 4x4 matrix with partial pivoting; false if singular.
 static bool invert4(const double* A, double* inv) {
     double m[4][8];
@@ -287,8 +312,12 @@ static void* upload_real(const std::vector<double>& h, cudaError_t& err) {
 
 // Power-of-two FFT length M of a line of n samples of a family (the core DFT
 // of length L = N, or 2(N + 1) for the sine families, padded for Bluestein).
+static int order_of(int fam, int n) {
+    return fam == FAM_P ? n : fam_nb(fam) == 2 ? n - 4 : n - 2;
+}
+
 int fft_length_of(int fam, int n) {
-    const int N = (fam == FAM_S3 || fam == FAM_C4) ? n - 4 : n - 2;
+    const int N = order_of(fam, n);
     const int L = (fam == FAM_S || fam == FAM_S3) ? 2 * (N + 1) : N;
     if (L >= 8 && (L & (L - 1)) == 0) return L;
     int M = 8;
@@ -308,7 +337,7 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half, int r
         // FFT or border tables, only the grid and the eigen-exponential table
         a.N = n; a.L = n; a.M = 8; a.log2M = 3; a.tpg = 1; a.H = n; a.W = n;
     } else {
-    a.N = (fam == hobc::FAM_S3 || fam == hobc::FAM_C4) ? n - 4 : n - 2;
+    a.N = order_of(fam, n);
     const int N = a.N;
     a.L = (fam == hobc::FAM_S || fam == hobc::FAM_S3) ? 2 * (N + 1) : N;
     if (a.L >= 8 && (a.L & (a.L - 1)) == 0) {
@@ -324,8 +353,8 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half, int r
     const bool can16 = a.M >= 256 && a.log2M <= 12;
     a.r16 = radix == 0 ? (hobc::fft_r16(a.M) && can16) : (radix == 16 && can16);
     a.tpg = a.r16 ? a.M / 16 : a.M / 8;
-    a.H = fam == hobc::FAM_F ? N / 2 + 1 : N;
-    a.W = (fam == hobc::FAM_F && half) ? a.H + 2 : n;
+    a.H = fam_fourier(fam) ? N / 2 + 1 : N;
+    a.W = (fam_fourier(fam) && half) ? a.H + 2 * fam_nb(fam) : n;
 
     // per-stage twiddle tables in the order the FFT runs its stages: radix 16
     // while four or more bits remain (fft_r16) or radix 8 while three remain,
@@ -380,6 +409,26 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half, int r
             K[3 * 4 + b] = B(b, n - 1) + B(b, n - 3);
         }
         if (!invert4(K, a.k4) && err == cudaSuccess) err = cudaErrorInvalidValue;
+    } else if (fam == hobc::FAM_F4) {
+        std::vector<double> Q2;
+        fourier_quartic_columns(n, q, Q2);
+        a.q2 = upload_real<T>(Q2, err);
+        // rows 0-(n-4), 1-(n-3), (n-2)-2, (n-1)-3 of T restricted to the border
+        // columns (Q1, Q2, flip Q2, flip Q1): the periodic wrap cancels the
+        // Fourier columns in these differences
+        auto B = [&](int b, int r) {
+            return b == 0 ? q[r] : b == 1 ? Q2[r] : b == 2 ? Q2[n - 1 - r] : q[n - 1 - r];
+        };
+        double K[16];
+        for (int b = 0; b < 4; ++b) {
+            K[0 * 4 + b] = B(b, 0) - B(b, n - 4);
+            K[1 * 4 + b] = B(b, 1) - B(b, n - 3);
+            K[2 * 4 + b] = B(b, n - 2) - B(b, 2);
+            K[3 * 4 + b] = B(b, n - 1) - B(b, 3);
+        }
+        if (!invert4(K, a.k4) && err == cudaSuccess) err = cudaErrorInvalidValue;
+    } else if (fam == hobc::FAM_P) {
+        q.assign(n, 0.0);                    // periodic: no border columns
     } else if (fam == hobc::FAM_C4) {
         std::vector<double> Q2;
         quartic_columns(n, q, Q2);
@@ -403,7 +452,7 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half, int r
     }
     a.q = upload_real<T>(q, err);
     a.q1 = q[0];
-    if (fam == hobc::FAM_C4) {               // the 4x4 solve replaces the 2x2 one
+    if (fam == hobc::FAM_C4 || fam == hobc::FAM_F4 || fam == hobc::FAM_P) {   // 4x4 solve, or none
         a.ka = 0.0;
         a.kb = 0.0;
     } else if (fam == hobc::FAM_S || fam == hobc::FAM_S3) {
@@ -416,7 +465,7 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half, int r
         a.ka = al / det;
         a.kb = -be / det;
     }
-    a.sc = fam == hobc::FAM_F ? 1.0 / sqrt((double)N) : sqrt(2.0 / (N + 1)) / 2.0;
+    a.sc = fam_fourier(fam) ? 1.0 / sqrt((double)N) : sqrt(2.0 / (N + 1)) / 2.0;
     a.s0 = sqrt(1.0 / N);
     a.s1 = sqrt(2.0 / N);
     a.is0 = sqrt((double)N);
@@ -427,7 +476,7 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half, int r
     const int m = p / 2;
     std::vector<double> et(2 * ((size_t)a.W * p + 1));
     for (int ts = 0; ts < a.W; ++ts) {
-        const int t = (fam == hobc::FAM_F && half && ts == a.W - 1) ? n - 1 : ts;
+        const int t = (fam_fourier(fam) && half && ts >= a.W - fam_nb(fam)) ? n - (a.W - ts) : ts;
         long long num, den;
         theta_frac(fam, n, t, num, den);
         for (int j = 0; j < p; ++j) {
@@ -469,6 +518,7 @@ hobc_status resolve_desc(const hobc_plan_desc& d, bool check_psf, int* fam_out) 
         if (d.psf[i] > d.n[i] - 2) return HOBC_ERR_SIZE;       // 2m+1 <= n-2
     }
     const bool cubic = d.family == HOBC_FAMILY_SINE_CUBIC || d.family == HOBC_FAMILY_COSINE_QUARTIC ||
+                       d.family == HOBC_FAMILY_FOURIER_QUARTIC ||
                        (d.family == HOBC_FAMILY_AUTO && (d.bc_degree == 3 || d.bc_degree == 4));
     if (cubic)
         for (int i = 0; i < d.ndim; ++i) {
@@ -477,8 +527,13 @@ hobc_status resolve_desc(const hobc_plan_desc& d, bool check_psf, int* fam_out) 
         }
     int fam = d.family;
     const bool comparison = fam == HOBC_FAMILY_REFLECTIVE || fam == HOBC_FAMILY_PERIODIC;
-    if (comparison) {
-        // classical conditions (Sec. 2): constants preserved, symmetric PSF, dense mode only
+    if (fam == HOBC_FAMILY_PERIODIC && d.prec != HOBC_SPLIT_BF16) {
+        // classical periodic conditions (Sec. 2, Eq. (eq:permat)) on the FFT path: the
+        // DFT of order n, no border columns, any PSF
+        if (d.bc_degree != 0) return HOBC_ERR_UNSUPPORTED;
+        fam = FAM_P;
+    } else if (comparison) {
+        // classical conditions (Sec. 2): constants preserved, symmetric PSF; in the dense mode
         if (d.bc_degree != 0 || !d.psf_symmetric || d.prec != HOBC_SPLIT_BF16) return HOBC_ERR_UNSUPPORTED;
     } else {
         if (d.bc_degree < 1 || d.bc_degree > 4) return HOBC_ERR_UNSUPPORTED;
@@ -486,7 +541,7 @@ hobc_status resolve_desc(const hobc_plan_desc& d, bool check_psf, int* fam_out) 
             if (d.bc_degree == 1) fam = d.psf_symmetric ? HOBC_FAMILY_SINE : -1;
             else if (d.bc_degree == 2) fam = d.psf_symmetric ? HOBC_FAMILY_COSINE : HOBC_FAMILY_FOURIER;
             else if (d.bc_degree == 3) fam = d.psf_symmetric ? HOBC_FAMILY_SINE_CUBIC : -1;
-            else fam = d.psf_symmetric ? HOBC_FAMILY_COSINE_QUARTIC : -1;
+            else fam = d.psf_symmetric ? HOBC_FAMILY_COSINE_QUARTIC : HOBC_FAMILY_FOURIER_QUARTIC;
             if (fam < 0) return HOBC_ERR_UNSUPPORTED;   // sine families need a symmetric PSF (Sec. 2.2)
         }
         if (fam == HOBC_FAMILY_SINE && d.bc_degree != 1) return HOBC_ERR_UNSUPPORTED;
@@ -495,13 +550,16 @@ hobc_status resolve_desc(const hobc_plan_desc& d, bool check_psf, int* fam_out) 
         if (fam == HOBC_FAMILY_SINE_CUBIC && d.bc_degree != 3) return HOBC_ERR_UNSUPPORTED;
         if (fam == HOBC_FAMILY_COSINE_QUARTIC && (d.bc_degree != 4 || !d.psf_symmetric))
             return HOBC_ERR_UNSUPPORTED;
-        if (fam != HOBC_FAMILY_COSINE_QUARTIC && (fam < HOBC_FAMILY_SINE || fam > HOBC_FAMILY_SINE_CUBIC))
+        if (fam == HOBC_FAMILY_FOURIER_QUARTIC && d.bc_degree != 4) return HOBC_ERR_UNSUPPORTED;
+        if (fam != HOBC_FAMILY_COSINE_QUARTIC && fam != HOBC_FAMILY_FOURIER_QUARTIC &&
+            (fam < HOBC_FAMILY_SINE || fam > HOBC_FAMILY_SINE_CUBIC))
             return HOBC_ERR_ARG;
     }
     // degree 4 runs on the FFT path only (the dense engine has no matrices for it), and in
     // FP64 only: cond(T) is 644 already at n = 8 (7.5e4 at n = 32), so the FP32 rounding
     // bound 64 eps32 cond(T) exceeds 1e-3 at every size
-    if (fam == HOBC_FAMILY_COSINE_QUARTIC && d.prec != HOBC_FP64) return HOBC_ERR_UNSUPPORTED;
+    if ((fam == HOBC_FAMILY_COSINE_QUARTIC || fam == HOBC_FAMILY_FOURIER_QUARTIC) && d.prec != HOBC_FP64)
+        return HOBC_ERR_UNSUPPORTED;
     *fam_out = fam;
     return HOBC_OK;
 }
@@ -589,7 +647,7 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
     }
     const AxisHost& last = p->ax[d.ndim - 1];
     p->spec_elems = d.ndim == 1 ? (size_t)last.W : (size_t)last.W * p->ax[0].n;
-    const size_t ebytes = p->esz * (fam == HOBC_FAMILY_FOURIER ? 2 : 1);
+    const size_t ebytes = p->esz * (fam_fourier(fam) ? 2 : 1);
     p->spec_bytes = p->spec_elems * ebytes;
     p->img_elems = d.ndim == 1 ? (size_t)d.n[0] : (size_t)d.n[0] * d.n[1];
     p->psf_elems = d.ndim == 1 ? (size_t)d.psf[0] : (size_t)d.psf[0] * d.psf[1];
@@ -635,7 +693,10 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
     return HOBC_OK;
 }
 
-hobc_family hobc_plan_family(const hobc_plan* p) { return p ? (hobc_family)p->fam : HOBC_FAMILY_AUTO; }
+hobc_family hobc_plan_family(const hobc_plan* p) {
+    if (!p) return HOBC_FAMILY_AUTO;
+    return p->fam == FAM_P ? HOBC_FAMILY_PERIODIC : (hobc_family)p->fam;
+}
 
 int hobc_fft_length(int bc_degree, int n) {
     if (n < 8 || n > 1024) return 0;
@@ -646,7 +707,7 @@ int hobc_fft_length(int bc_degree, int n) {
 hobc_status hobc_spectrum_size(const hobc_plan* p, size_t* spec, int* is_complex, size_t* psf) {
     if (!p) return HOBC_ERR_ARG;
     if (spec) *spec = p->spec_elems;
-    if (is_complex) *is_complex = p->fam == HOBC_FAMILY_FOURIER;
+    if (is_complex) *is_complex = fam_fourier(p->fam);
     if (psf) *psf = p->psf_elems;
     return HOBC_OK;
 }

@@ -18,7 +18,17 @@
 
 namespace hobc {
 
-enum { FAM_S = 1, FAM_C = 2, FAM_F = 3, FAM_S3 = 4, FAM_R = 5, FAM_PH = 6, FAM_C4 = 7 };   // same values as hobc_family
+// FAM_S..FAM_F4 have the values of hobc_family; FAM_P is the periodic family
+// on the FFT path (HOBC_FAMILY_PERIODIC outside the dense mode), FAM_PH the same
+// conditions in the Hartley basis of the dense mode.
+enum { FAM_S = 1, FAM_C = 2, FAM_F = 3, FAM_S3 = 4, FAM_R = 5, FAM_PH = 6, FAM_C4 = 7, FAM_F4 = 8, FAM_P = 9 };
+
+// Families with a complex spectrum (Fourier basis) and their border entries
+// on each side of a line: F 1, F4 2, P none.
+__host__ __device__ constexpr bool fam_fourier(int fam) { return fam == FAM_F || fam == FAM_F4 || fam == FAM_P; }
+__host__ __device__ constexpr int fam_nb(int fam) {
+    return (fam == FAM_S3 || fam == FAM_C4 || fam == FAM_F4) ? 2 : (fam == FAM_P || fam == FAM_R || fam == FAM_PH) ? 0 : 1;
+}
 
 template <typename T> struct V2;
 template <> struct V2<float> { typedef float2 t; };
@@ -39,28 +49,29 @@ template <typename T> __device__ __forceinline__ T cabs2(C2<T> a) { return a.x *
 // its length-L complex DFT core.  Built on the host (hobc_api.cu), passed by value.
 template <typename T>
 struct Axis {
-    int fam;        // FAM_S / FAM_C / FAM_F
+    int fam;        // FAM_*
     int n;          // field-of-view length on this axis
-    int N;          // order of the trigonometric block: n - 2 (n - 4 for S3)
-    int L;          // length of the complex DFT core: N (C, F) or 2(N+1) (S, S3)
+    int N;          // order of the trigonometric block: n - 2 (n - 4 for S3, C4, F4; n for P)
+    int L;          // length of the complex DFT core: N (C, F, C4, F4, P) or 2(N+1) (S, S3)
     int M;          // power-of-two FFT length (== L when L is a power of two >= 8)
     int log2M;
     int blue;       // 1: Bluestein (M >= 2L-1), 0: direct
     int tpg;        // threads per group: M/16 with radix-16 stages (r16), else M/8
     int r16;        // 1: radix-16 stages (M >= 256, log2M <= 12), 0: radix 8
     int Mp;         // shared-memory slots per group: group_slots(M)
-    int H;          // FOURIER: floor(N/2)+1 stored frequencies; else N
-    int W;          // spectrum entries stored on this axis: n (S, C) or H+2 (F)
+    int H;          // Fourier families: floor(N/2)+1 stored frequencies; else N
+    int W;          // spectrum entries stored on this axis: n, or H + 2 NB on a half axis of a
+                    // Fourier family (NB border entries on each side)
     const C2<T>* tw;      // per-stage twiddle tables of the FFT, concatenated (< M entries)
     const C2<T>* chirp;   // [L] exp(-i pi (k^2 mod 2L) / L)
     const C2<T>* bhat;    // [M] FFT_M(conj-chirp, wrapped) / M
     const C2<T>* post;    // COSINE: [N] exp(-i pi k / (2N))
-    const T* q;           // [n] left border column of T_X (p for S, q for C, F, L1 for S3)
-    const T* q2;          // S3: [n] second left border column L2
+    const T* q;           // [n] left border column of T_X (p for S, q for C, F, L1 for S3, Q1 for C4, F4)
+    const T* q2;          // S3, C4, F4: [n] second left border column (L2, Q2)
     double ka, kb;        // inverse of the 2x2 border system, [[ka, kb], [kb, ka]]
-    double k4[16];        // S3: inverse of the 4x4 border system, row-major
+    double k4[16];        // S3, C4, F4: inverse of the 4x4 border system, row-major
     T q1;                 // q[0]
-    T sc;                 // F: 1/sqrt(N); S, S3: sqrt(2/(N+1))/2
+    T sc;                 // Fourier families: 1/sqrt(N); S, S3: sqrt(2/(N+1))/2
     T s0, s1;             // C: DCT-II row scales sqrt(1/N), sqrt(2/N)
     T is0, is1;           // C: their reciprocals
     T invN;               // C: 1/N
@@ -485,20 +496,24 @@ __device__ __forceinline__ double border_coeff(const Axis<T>& ax, double y0, dou
     return which ? ax.kb * r1 + ax.ka * r2 : ax.ka * r1 + ax.kb * r2;
 }
 
-// Families with two border columns on each side (S3: degree 3; C4: degree 4):
+// Families with two border columns on each side (S3: degree 3; C4, F4: degree 4):
 // y = sum_b c_b B_b + E w with border columns B = (B1, B2, flip B2, flip B1).
 // S3's odd extension E has rows 0 and n-1 equal to minus the first and last
 // interior samples and rows 1 and n-2 zero; C4's half-sample reflection has
 // rows 0, 1 equal to interior rows 1, 0 (rows 3, 2 of y) and rows n-2, n-1
-// equal to rows n-3, n-4.  Four row combinations of y therefore involve only
-// the border coefficients (S3: rows 0+2, 1, n-2, n-1+n-3; C4: rows 0-3, 1-2,
-// n-2-(n-3), n-1-(n-4)): a 4x4 system whose inverse is precomputed in double.
+// equal to rows n-3, n-4; F4's periodic wrap has rows 0, 1 equal to rows n-4,
+// n-3 and rows n-2, n-1 equal to rows 2, 3.  Four row combinations of y
+// therefore involve only the border coefficients (S3: rows 0+2, 1, n-2,
+// n-1+n-3; C4: rows 0-3, 1-2, n-2-(n-3), n-1-(n-4); F4: rows 0-(n-4),
+// 1-(n-3), (n-2)-2, (n-1)-3): a 4x4 system whose inverse is precomputed in double.
 // y[0..3] are the first four samples, ym[0..3] the last four (ym[3] = y_{n-1}).
 template <typename T>
 __device__ __forceinline__ double border_coeff4(const Axis<T>& ax, const double* y, const double* ym, int b) {
     double r[4];
     if (ax.fam == FAM_C4) {
         r[0] = y[0] - y[3]; r[1] = y[1] - y[2]; r[2] = ym[2] - ym[1]; r[3] = ym[3] - ym[0];
+    } else if (ax.fam == FAM_F4) {
+        r[0] = y[0] - ym[0]; r[1] = y[1] - ym[1]; r[2] = ym[2] - y[2]; r[3] = ym[3] - y[3];
     } else {
         r[0] = y[0] + y[2]; r[1] = y[1]; r[2] = ym[2]; r[3] = ym[3] + ym[1];
     }
@@ -519,8 +534,9 @@ __device__ __forceinline__ T border_sum4(const Axis<T>& ax, const T* c, int a) {
 template <typename T>
 __device__ __forceinline__ T theta_over_pi(int fam, int n, int N, int t) {
     if (fam == FAM_R) return (T)t / (T)n;                 // reflective (Eq. (eq:refm)): no border columns
-    if (fam == FAM_PH) return (T)(2 * t) / (T)n;          // periodic (Eq. (eq:permat))
+    if (fam == FAM_PH || fam == FAM_P) return (T)(2 * t) / (T)n;   // periodic (Eq. (eq:permat))
     if (t == 0 || t == n - 1) return (T)0;
+    if (fam == FAM_F4) return (t == 1 || t == n - 2) ? (T)0 : (T)(2 * (t - 2)) / (T)N;   // reading R17
     if (fam == FAM_S3) return (t == 1 || t == n - 2) ? (T)0 : (T)(t - 1) / (T)(N + 1);
     if (fam == FAM_C4) return (t == 1 || t == n - 2) ? (T)0 : (T)(t - 2) / (T)N;
     if (fam == FAM_S) return (T)t / (T)(N + 1);
@@ -528,9 +544,12 @@ __device__ __forceinline__ T theta_over_pi(int fam, int n, int N, int t) {
     return (T)(2 * (t - 1)) / (T)N;
 }
 
-// Spectral index t of stored entry c on an axis (FOURIER stores a half).
+// Spectral index t of stored entry c on an axis (a Fourier family stores a half
+// on its last axis: the left border entries, H frequencies, the right border
+// entries; elsewhere W = n and t = c).
 __device__ __forceinline__ int stored_to_t(int fam, int n, int W, int c) {
-    return (fam == FAM_F && c == W - 1) ? n - 1 : c;
+    const int nb = fam_nb(fam);
+    return (fam_fourier(fam) && c >= W - nb) ? n - (W - c) : c;
 }
 
 // Laplacian eigenvalue s = 2 - 2 cos(theta) = 4 sin^2(theta/2) (Sec. 4), in the

@@ -8,6 +8,7 @@
 
 #include "../../include/hobc.h"
 #include "../../include/hobc_volume.h"
+#include "hobc_device.cuh"
 
 namespace hobc {
 
@@ -21,9 +22,9 @@ struct AxisHost {
     void* bhat;     // [M] complex (Bluestein only)
     void* post;     // [N] complex (COSINE only)
     void* q;        // [n] real
-    void* q2;       // [n] real, S3 only (second border column)
+    void* q2;       // [n] real, S3, C4, F4 (second border column)
     double ka, kb, q1, sc, s0, s1, is0, is1, invN;
-    double k4[16];  // S3: inverse of the 4x4 border system
+    double k4[16];  // S3, C4, F4: inverse of the 4x4 border system
     int p;          // PSF extent on this axis
     double2* etab;  // [W][p] exp(-i (j - m) theta_t) for the stored entries t
 };
@@ -136,6 +137,10 @@ hobc_status dense_analysis(hobc_plan_s* p, const void* g, void* ghat);
 hobc_status dense_synthesis(hobc_plan_s* p, const void* c, void* y);
 hobc_status dense_filter_synthesis(hobc_plan_s* p, const void* ghat, const void* D, const int* mu_idx,
                                    const double* mu_val, void* f);
+
+// Families run by the plain method alone (plans, steps, host calls, the
+// allocation-free scan): periodic on the FFT path and the degree-4 Fourier family.
+inline bool plain_only_family(int fam) { return fam == FAM_P || fam == FAM_F4; }
 
 // power-of-two FFT length of a line of n samples of a family (hobc_api.cu)
 int fft_length_of(int fam, int n);

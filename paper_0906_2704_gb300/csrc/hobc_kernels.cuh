@@ -95,11 +95,12 @@ __device__ __forceinline__ T smoothing2(const FilterDesc& f, int mode, const Axi
 // =====================================================================
 template <typename T, int FAM>
 __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, long long in_item, long long in_rs,
-                                                   typename ElemT<T, FAM == FAM_F>::t* __restrict__ out,
+                                                   typename ElemT<T, fam_fourier(FAM)>::t* __restrict__ out,
                                                    long long out_item, long long out_rs, long long out_cs,
                                                    int nlines, const Axis<T>& ax, long long item, int r0,
                                                    unsigned char* smem_raw) {
-    typedef typename ElemT<T, FAM == FAM_F>::t E;
+    constexpr bool FOUR = fam_fourier(FAM);
+    typedef typename ElemT<T, FOUR>::t E;
     const int G = blockDim.x / ax.tpg;
     const int g = threadIdx.x / ax.tpg;
     const int t = threadIdx.x - g * ax.tpg;
@@ -112,11 +113,11 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
     const T* yb = in + item * in_item + (long long)(vb ? rb : 0) * in_rs;
 
     constexpr bool CUBIC = (FAM == FAM_S3);
-    constexpr bool K2 = (FAM == FAM_S3 || FAM == FAM_C4);   // two border columns on each side
+    constexpr int NB = fam_nb(FAM);              // border entries on each side
+    constexpr bool K2 = NB == 2;                 // two border columns on each side (S3, C4, F4)
     constexpr bool DCT = (FAM == FAM_C || FAM == FAM_C4);
-    constexpr int NB = K2 ? 2 : 1;               // border entries on each side
     // border coefficients of both lines, one per thread: (c_1, c_n) of line a
-    // then of line b, or the four coefficients of each (S3, C4)
+    // then of line b, or the four coefficients of each (S3, C4, F4); none for P
     T* xs = reinterpret_cast<T*>(buf + ax.M + ax.M / 16);
     for (int l = t; l < 4 * NB; l += ax.tpg) {
         const int side = K2 ? l >> 2 : l >> 1;
@@ -134,7 +135,8 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
         xs[l] = (T)c;
     }
     __syncthreads();
-    const T c1af = xs[0], cnaf = xs[1], c1bf = xs[2], cnbf = xs[3];
+    T c1af = 0, cnaf = 0, c1bf = 0, cnbf = 0;
+    if constexpr (NB == 1) { c1af = xs[0]; cnaf = xs[1]; c1bf = xs[2]; cnbf = xs[3]; }
     T ca4f[4] = {0, 0, 0, 0}, cb4f[4] = {0, 0, 0, 0};
     if constexpr (K2)
 #pragma unroll
@@ -146,12 +148,15 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
         if constexpr (K2) {
             wa = va ? ya[2 + j] - border_sum4<T>(ax, ca4f, 2 + j) : (T)0;
             wb = vb ? yb[2 + j] - border_sum4<T>(ax, cb4f, 2 + j) : (T)0;
+        } else if constexpr (NB == 0) {
+            wa = va ? ya[j] : (T)0;
+            wb = vb ? yb[j] : (T)0;
         } else {
             const T ql = ax.q[1 + j], qr = ax.q[n - 2 - j];
             wa = va ? ya[1 + j] - ql * c1af - qr * cnaf : (T)0;
             wb = vb ? yb[1 + j] - ql * c1bf - qr * cnbf : (T)0;
         }
-        if constexpr (FAM == FAM_F) {
+        if constexpr (FOUR) {
             buf[pidx(j)] = dft_in<T>(ax, j, cmk<T>(wa, wb));
         } else if constexpr (DCT) {
             const int p = pos_C(j, N);
@@ -168,18 +173,25 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
 
     E* sa = stage + (size_t)(2 * g) * W;
     E* sb = sa + W;
-    if constexpr (FAM == FAM_F) {
+    if constexpr (FOUR) {
         for (int k = t; k < ax.H; k += ax.tpg) {
             const C2<T> zk = dft_out<T>(buf, ax, k);
             const C2<T> zr = cconj<T>(dft_out<T>(buf, ax, k == 0 ? 0 : N - k));
             const C2<T> s = cadd<T>(zk, zr), d = csub<T>(zk, zr);
             const T h = (T)0.5 * ax.sc;
-            sa[1 + k] = cmk<T>(s.x * h, s.y * h);
-            sb[1 + k] = cmk<T>(d.y * h, -d.x * h);        // -i (zk - zr) / 2
+            sa[NB + k] = cmk<T>(s.x * h, s.y * h);
+            sb[NB + k] = cmk<T>(d.y * h, -d.x * h);       // -i (zk - zr) / 2
         }
         if (t == 0) {
-            sa[0] = cmk<T>(xs[0], 0); sa[W - 1] = cmk<T>(xs[1], 0);
-            sb[0] = cmk<T>(xs[2], 0); sb[W - 1] = cmk<T>(xs[3], 0);
+            if constexpr (K2) {
+                sa[0] = cmk<T>(xs[0], 0); sa[1] = cmk<T>(xs[1], 0); sa[W - 2] = cmk<T>(xs[2], 0);
+                sa[W - 1] = cmk<T>(xs[3], 0);
+                sb[0] = cmk<T>(xs[4], 0); sb[1] = cmk<T>(xs[5], 0); sb[W - 2] = cmk<T>(xs[6], 0);
+                sb[W - 1] = cmk<T>(xs[7], 0);
+            } else if constexpr (NB == 1) {
+                sa[0] = cmk<T>(xs[0], 0); sa[W - 1] = cmk<T>(xs[1], 0);
+                sb[0] = cmk<T>(xs[2], 0); sb[W - 1] = cmk<T>(xs[3], 0);
+            }
         }
     } else if constexpr (DCT) {
         for (int k = t; k < N; k += ax.tpg) {
@@ -236,7 +248,7 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
 template <typename T, int FAM>
 __global__ void HOBC_LINE_BOUNDS
 k_pair_analysis(const T* __restrict__ in, long long in_item, long long in_rs,
-                typename ElemT<T, FAM == FAM_F>::t* __restrict__ out, long long out_item,
+                typename ElemT<T, fam_fourier(FAM)>::t* __restrict__ out, long long out_item,
                 long long out_rs, long long out_cs, int nlines, Axis<T> ax) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = blockDim.x / ax.tpg;
@@ -252,12 +264,14 @@ k_pair_analysis(const T* __restrict__ in, long long in_item, long long in_rs,
 // the line index is the axis-1 stored index).
 // =====================================================================
 template <typename T, int FAM, int FMODE>
-__device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in,
+__device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, fam_fourier(FAM)>::t* __restrict__ in,
                                                     long long in_item, long long in_rs, long long in_cs,
                                                     T* __restrict__ out, long long out_item, long long out_rs,
                                                     int nlines, const Axis<T>& ax, const FilterDesc& fd,
                                                     long long item, int r0, unsigned char* smem_raw) {
-    typedef typename ElemT<T, FAM == FAM_F>::t E;
+    constexpr bool FOUR = fam_fourier(FAM);
+    constexpr int NBF = fam_nb(FAM);
+    typedef typename ElemT<T, FOUR>::t E;
     const int G = blockDim.x / ax.tpg;
     const int g = threadIdx.x / ax.tpg;
     const int t = threadIdx.x - g * ax.tpg;
@@ -298,18 +312,18 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM 
     const E* sa = stage + (size_t)(2 * g) * W;
     const E* sb = sa + W;
     const C2<T> zero = cmk<T>(0, 0);
-    if constexpr (FAM == FAM_F) {
+    if constexpr (FOUR) {
         const int H = ax.H;
         for (int k = t; k < N; k += ax.tpg) {
             C2<T> z;
             if (k < H) {
-                C2<T> a = reinterpret_cast<const C2<T>*>(sa)[1 + k];
-                C2<T> b = reinterpret_cast<const C2<T>*>(sb)[1 + k];
+                C2<T> a = reinterpret_cast<const C2<T>*>(sa)[NBF + k];
+                C2<T> b = reinterpret_cast<const C2<T>*>(sb)[NBF + k];
                 if (k == 0 || 2 * k == N) { a.y = 0; b.y = 0; }
                 z = cmk<T>(a.x - b.y, a.y + b.x);                // a + i b
             } else {
-                const C2<T> a = reinterpret_cast<const C2<T>*>(sa)[1 + N - k];
-                const C2<T> b = reinterpret_cast<const C2<T>*>(sb)[1 + N - k];
+                const C2<T> a = reinterpret_cast<const C2<T>*>(sa)[NBF + N - k];
+                const C2<T> b = reinterpret_cast<const C2<T>*>(sb)[NBF + N - k];
                 z = cmk<T>(a.x + b.y, -a.y + b.x);               // conj(a) + i conj(b)
             }
             buf[pidx(k)] = dft_in<T>(ax, k, cconj<T>(z));
@@ -346,7 +360,7 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM 
     T* ob = out + item * out_item + (long long)rb * out_rs;
     // interior sample j of the trigonometric part, for both lines
     auto wval = [&](int j, T& wa, T& wb) {
-        if constexpr (FAM == FAM_F) {
+        if constexpr (FOUR) {
             const C2<T> z = dft_out<T>(buf, ax, j);
             wa = z.x * ax.sc;
             wb = -z.y * ax.sc;
@@ -360,7 +374,16 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM 
             wb = z.x * ax.sc;
         }
     };
-    if constexpr (FAM == FAM_S3 || FAM == FAM_C4) {
+    if constexpr (NBF == 0) {
+        for (int j = t; j < N; j += ax.tpg) {
+            T wa, wb;
+            wval(j, wa, wb);
+            if (va) oa[j] = wa;
+            if (vb) ob[j] = wb;
+        }
+        return;
+    }
+    if constexpr (NBF == 2) {
         const T c4a[4] = {re_of(sa[0]), re_of(sa[1]), re_of(sa[W - 2]), re_of(sa[W - 1])};
         const T c4b[4] = {re_of(sb[0]), re_of(sb[1]), re_of(sb[W - 2]), re_of(sb[W - 1])};
         for (int j = t; j < N; j += ax.tpg) {
@@ -369,7 +392,23 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM 
             if (va) oa[2 + j] = wa + border_sum4<T>(ax, c4a, 2 + j);
             if (vb) ob[2 + j] = wb + border_sum4<T>(ax, c4b, 2 + j);
         }
-        if (FAM == FAM_C4 && t == 0) {
+        if (FAM == FAM_F4 && t == 0) {
+            // periodic wrap: rows 0, 1 add interior samples N-2, N-1 and rows
+            // n-2, n-1 interior samples 0, 1
+            T w0a, w0b, w1a, w1b, wNa, wNb, wMa, wMb;
+            wval(0, w0a, w0b);
+            wval(1, w1a, w1b);
+            wval(N - 2, wMa, wMb);
+            wval(N - 1, wNa, wNb);
+            if (va) {
+                oa[0] = border_sum4<T>(ax, c4a, 0) + wMa; oa[1] = border_sum4<T>(ax, c4a, 1) + wNa;
+                oa[n - 2] = border_sum4<T>(ax, c4a, n - 2) + w0a; oa[n - 1] = border_sum4<T>(ax, c4a, n - 1) + w1a;
+            }
+            if (vb) {
+                ob[0] = border_sum4<T>(ax, c4b, 0) + wMb; ob[1] = border_sum4<T>(ax, c4b, 1) + wNb;
+                ob[n - 2] = border_sum4<T>(ax, c4b, n - 2) + w0b; ob[n - 1] = border_sum4<T>(ax, c4b, n - 1) + w1b;
+            }
+        } else if (FAM == FAM_C4 && t == 0) {
             // half-sample reflection: rows 0, 1 add interior samples 1, 0 and
             // rows n-2, n-1 interior samples N-1, N-2
             T w0a, w0b, w1a, w1b, wNa, wNb, wMa, wMb;
@@ -422,7 +461,7 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, FAM 
 
 template <typename T, int FAM, int FMODE>
 __global__ void HOBC_LINE_BOUNDS
-k_pair_synthesis(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in, long long in_item,
+k_pair_synthesis(const typename ElemT<T, fam_fourier(FAM)>::t* __restrict__ in, long long in_item,
                  long long in_rs, long long in_cs, T* __restrict__ out, long long out_item,
                  long long out_rs, int nlines, Axis<T> ax, FilterDesc fd) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -432,14 +471,16 @@ k_pair_synthesis(const typename ElemT<T, FAM == FAM_F>::t* __restrict__ in, long
 }
 
 // =====================================================================
-// Fourier family, complex lines along axis 0 (one line per thread group).
-// Line c of item i: in[i*item_stride + c*n + t].
+// Fourier families (F, F4, P), complex lines along axis 0 (one line per thread
+// group).  Line c of item i: in[i*item_stride + c*n + t].  The border solve
+// of a complex line is the real one applied to its real and imaginary parts.
 // =====================================================================
-template <typename T>
+template <typename T, int FAM>
 __global__ void HOBC_LINE_BOUNDS
 k_cplx_analysis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long item_stride,
                 int nlines, Axis<T> ax) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NB = fam_nb(FAM);
     const int G = blockDim.x / ax.tpg;
     const int g = threadIdx.x / ax.tpg;
     const int t = threadIdx.x - g * ax.tpg;
@@ -449,26 +490,48 @@ k_cplx_analysis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long
     const int c = blockIdx.x * G + g;
     const bool valid = c < nlines;
     const C2<T>* y = in + item * item_stride + (long long)(valid ? c : 0) * n;
-    // border coefficients, one per thread: c_1 and c_n of the real part, then
-    // of the imaginary part
+    // border coefficients, one per thread: those of the real part (c_1, c_n;
+    // or the four of F4), then those of the imaginary part
     T* xs = reinterpret_cast<T*>(buf + ax.M + ax.M / 16);
-    for (int l = t; l < 4; l += ax.tpg) {
-        double c = 0;
+    for (int l = t; l < 4 * NB; l += ax.tpg) {
+        double cf = 0;
         if (valid) {
-            const C2<T> y0 = y[0], y1 = y[1], ym2 = y[n - 2], ym1 = y[n - 1];
-            c = l < 2 ? border_coeff<T>(ax, y0.x, y1.x, ym2.x, ym1.x, l & 1)
-                      : border_coeff<T>(ax, y0.y, y1.y, ym2.y, ym1.y, l & 1);
+            if constexpr (NB == 2) {
+                const bool im = l >= 4;
+                double y4[4], ym4[4];
+                for (int a = 0; a < 4; ++a) {
+                    const C2<T> u = y[a], v = y[n - 4 + a];
+                    y4[a] = im ? u.y : u.x;
+                    ym4[a] = im ? v.y : v.x;
+                }
+                cf = border_coeff4<T>(ax, y4, ym4, l & 3);
+            } else {
+                const C2<T> y0 = y[0], y1 = y[1], ym2 = y[n - 2], ym1 = y[n - 1];
+                cf = l < 2 ? border_coeff<T>(ax, y0.x, y1.x, ym2.x, ym1.x, l & 1)
+                           : border_coeff<T>(ax, y0.y, y1.y, ym2.y, ym1.y, l & 1);
+            }
         }
-        xs[l] = (T)c;
+        xs[l] = (T)cf;
     }
     __syncthreads();
-    const C2<T> c1 = cmk<T>(xs[0], xs[2]), cn = cmk<T>(xs[1], xs[3]);
+    C2<T> c1 = cmk<T>(0, 0), cn = cmk<T>(0, 0);
+    T cre[4] = {0, 0, 0, 0}, cim[4] = {0, 0, 0, 0};
+    if constexpr (NB == 1) { c1 = cmk<T>(xs[0], xs[2]); cn = cmk<T>(xs[1], xs[3]); }
+    if constexpr (NB == 2)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) { cre[b] = xs[b]; cim[b] = xs[4 + b]; }
     for (int j = t; j < N; j += ax.tpg) {
-        const T ql = ax.q[1 + j], qr = ax.q[n - 2 - j];
         C2<T> w = cmk<T>(0, 0);
         if (valid) {
-            const C2<T> v = y[1 + j];
-            w = cmk<T>(v.x - ql * c1.x - qr * cn.x, v.y - ql * c1.y - qr * cn.y);
+            const C2<T> v = y[NB + j];
+            if constexpr (NB == 2) {
+                w = cmk<T>(v.x - border_sum4<T>(ax, cre, 2 + j), v.y - border_sum4<T>(ax, cim, 2 + j));
+            } else if constexpr (NB == 1) {
+                const T ql = ax.q[1 + j], qr = ax.q[n - 2 - j];
+                w = cmk<T>(v.x - ql * c1.x - qr * cn.x, v.y - ql * c1.y - qr * cn.y);
+            } else {
+                w = v;
+            }
         }
         buf[pidx(j)] = dft_in<T>(ax, j, w);
     }
@@ -476,15 +539,22 @@ k_cplx_analysis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long
     group_dft<T>(buf, ax, t);
     if (!valid) return;
     C2<T>* o = out + item * item_stride + (long long)c * n;
-    for (int k = t; k < N; k += ax.tpg) o[1 + k] = cscale<T>(dft_out<T>(buf, ax, k), ax.sc);
-    if (t == 0) { o[0] = cmk<T>(xs[0], xs[2]); o[n - 1] = cmk<T>(xs[1], xs[3]); }   // xs outlives the FFT
+    for (int k = t; k < N; k += ax.tpg) o[NB + k] = cscale<T>(dft_out<T>(buf, ax, k), ax.sc);
+    if (t == 0) {                                   // xs outlives the FFT
+        if constexpr (NB == 1) { o[0] = cmk<T>(xs[0], xs[2]); o[n - 1] = cmk<T>(xs[1], xs[3]); }
+        if constexpr (NB == 2) {
+            o[0] = cmk<T>(xs[0], xs[4]); o[1] = cmk<T>(xs[1], xs[5]);
+            o[n - 2] = cmk<T>(xs[2], xs[6]); o[n - 1] = cmk<T>(xs[3], xs[7]);
+        }
+    }
 }
 
-template <typename T, bool FILTER>
+template <typename T, int FAM, bool FILTER>
 __global__ void HOBC_LINE_BOUNDS
 k_cplx_synthesis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long long item_stride,
                  int nlines, Axis<T> ax, FilterDesc fd) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NB = fam_nb(FAM);
     const int G = blockDim.x / ax.tpg;
     const int g = threadIdx.x / ax.tpg;
     const int t = threadIdx.x - g * ax.tpg;
@@ -504,24 +574,43 @@ k_cplx_synthesis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long lon
         return v;
     };
     for (int k = t; k < N; k += ax.tpg) {
-        const C2<T> v = valid ? coef(1 + k) : cmk<T>(0, 0);
+        const C2<T> v = valid ? coef(NB + k) : cmk<T>(0, 0);
         buf[pidx(k)] = dft_in<T>(ax, k, cconj<T>(v));
     }
     __syncthreads();
     group_dft<T>(buf, ax, t);
     if (!valid) return;
-    const C2<T> c1 = coef(0), cn = coef(n - 1);
     C2<T>* o = out + item * item_stride + (long long)c * n;
-    for (int j = t; j < N; j += ax.tpg) {
-        const C2<T> w = cscale<T>(cconj<T>(dft_out<T>(buf, ax, j)), ax.sc);
-        const T ql = ax.q[1 + j], qr = ax.q[n - 2 - j];
-        o[1 + j] = cmk<T>(w.x + ql * c1.x + qr * cn.x, w.y + ql * c1.y + qr * cn.y);
-    }
-    if (t == 0) {
-        const C2<T> w0 = cscale<T>(cconj<T>(dft_out<T>(buf, ax, 0)), ax.sc);
-        const C2<T> wN = cscale<T>(cconj<T>(dft_out<T>(buf, ax, N - 1)), ax.sc);
-        o[0] = cmk<T>(ax.q1 * c1.x + wN.x, ax.q1 * c1.y + wN.y);      // y_1 = q_1 c_1 + w_N
-        o[n - 1] = cmk<T>(ax.q1 * cn.x + w0.x, ax.q1 * cn.y + w0.y);  // y_n = q_1 c_n + w_1
+    auto wout = [&](int j) { return cscale<T>(cconj<T>(dft_out<T>(buf, ax, j)), ax.sc); };
+    if constexpr (NB == 0) {
+        for (int j = t; j < N; j += ax.tpg) o[j] = wout(j);
+    } else if constexpr (NB == 1) {
+        const C2<T> c1 = coef(0), cn = coef(n - 1);
+        for (int j = t; j < N; j += ax.tpg) {
+            const C2<T> w = wout(j);
+            const T ql = ax.q[1 + j], qr = ax.q[n - 2 - j];
+            o[1 + j] = cmk<T>(w.x + ql * c1.x + qr * cn.x, w.y + ql * c1.y + qr * cn.y);
+        }
+        if (t == 0) {
+            const C2<T> w0 = wout(0), wN = wout(N - 1);
+            o[0] = cmk<T>(ax.q1 * c1.x + wN.x, ax.q1 * c1.y + wN.y);      // y_1 = q_1 c_1 + w_N
+            o[n - 1] = cmk<T>(ax.q1 * cn.x + w0.x, ax.q1 * cn.y + w0.y);  // y_n = q_1 c_n + w_1
+        }
+    } else {
+        T cre[4], cim[4];
+        const int bpos[4] = {0, 1, n - 2, n - 1};
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const C2<T> v = coef(bpos[b]);
+            cre[b] = v.x; cim[b] = v.y;
+        }
+        auto put = [&](int row, C2<T> w) {
+            o[row] = cmk<T>(w.x + border_sum4<T>(ax, cre, row), w.y + border_sum4<T>(ax, cim, row));
+        };
+        for (int j = t; j < N; j += ax.tpg) put(2 + j, wout(j));
+        if (t == 0) {           // periodic wrap (reading R17): rows 0, 1, n-2, n-1
+            put(0, wout(N - 2)); put(1, wout(N - 1)); put(n - 2, wout(0)); put(n - 1, wout(1));
+        }
     }
 }
 
@@ -817,7 +906,9 @@ __device__ __forceinline__ typename Pack4<T>::t gcv_term(const typename ElemT<T,
     const T s2 = lap_s2<T>(geo, e, c);
     T w = 1;
     if (CPLX) {
-        const bool self = (c == 0 || c == geo.W1 - 1 || c == 1 || 2 * (c - 1) == geo.N1);
+        // border entries and the frequencies 0 and N/2 stand for themselves
+        const int nb = fam_nb(geo.fam), k = c - nb;
+        const bool self = (c < nb || c >= geo.W1 - nb || k == 0 || 2 * k == geo.N1);
         w = self ? (T)1 : (T)2;
     }
     const T lam = abs2_of(dpv);

@@ -1445,7 +1445,8 @@ extern "C" {
 
 hobc_status hobc_features(hobc_plan* p, const void* ghat_dev, const void* d_dev, float* x_dev) {
     if (!p || !ghat_dev || !d_dev || !x_dev) return HOBC_ERR_ARG;
-    if (p->nax != 2 || p->fam == HOBC_FAMILY_REFLECTIVE || p->fam == HOBC_FAMILY_PERIODIC) return HOBC_ERR_UNSUPPORTED;
+    if (p->nax != 2 || p->fam == HOBC_FAMILY_REFLECTIVE || p->fam == HOBC_FAMILY_PERIODIC || plain_only_family(p->fam))
+        return HOBC_ERR_UNSUPPORTED;
     cudaError_t e = ensure_learned_ws(p);
     if (e != cudaSuccess) { set_last_error("hobc_features", e); return HOBC_ERR_CUDA; }
     p->launches = 0;
@@ -1455,7 +1456,8 @@ hobc_status hobc_features(hobc_plan* p, const void* ghat_dev, const void* d_dev,
 
 hobc_status hobc_features_hist(hobc_plan* p, const void* ghat_dev, const void* d_dev, float* x_dev) {
     if (!p || !ghat_dev || !d_dev || !x_dev) return HOBC_ERR_ARG;
-    if (p->fam == HOBC_FAMILY_REFLECTIVE || p->fam == HOBC_FAMILY_PERIODIC) return HOBC_ERR_UNSUPPORTED;
+    if (p->fam == HOBC_FAMILY_REFLECTIVE || p->fam == HOBC_FAMILY_PERIODIC || plain_only_family(p->fam))
+        return HOBC_ERR_UNSUPPORTED;
     cudaError_t e = ensure_learned_ws(p);
     if (e != cudaSuccess) { set_last_error("hobc_features_hist", e); return HOBC_ERR_CUDA; }
     p->launches = 0;
@@ -1482,7 +1484,7 @@ hobc_status hobc_deblur_learned(hobc_plan* p, hobc_mlp* q, const void* g_dev, co
                                 double* mu_dev, int* fell_back_dev) {
     if (!p || !q || !g_dev || !psf_dev || !f_dev) return HOBC_ERR_ARG;
     if ((p->nax != 2 && q->feature_kind == HOBC_FEATURES_RADIAL) || q->nin != kFeat ||
-        p->fam == HOBC_FAMILY_REFLECTIVE || p->fam == HOBC_FAMILY_PERIODIC)
+        p->fam == HOBC_FAMILY_REFLECTIVE || p->fam == HOBC_FAMILY_PERIODIC || plain_only_family(p->fam))
         return HOBC_ERR_UNSUPPORTED;
     cudaError_t e = ensure_learned_ws(p);
     if (e != cudaSuccess) { set_last_error("hobc_deblur_learned", e); return HOBC_ERR_CUDA; }
@@ -1498,6 +1500,7 @@ hobc_status hobc_deblur_learned(hobc_plan* p, hobc_mlp* q, const void* g_dev, co
 hobc_status hobc_gcv_binned(hobc_plan* p, const void* ghat_dev, const void* d_dev, int* mu_index_dev,
                             int* fell_back_dev, int* k_hat_dev) {
     if (!p || !ghat_dev || !d_dev || !mu_index_dev) return HOBC_ERR_ARG;
+    if (plain_only_family(p->fam)) return HOBC_ERR_UNSUPPORTED;
     cudaError_t e = ensure_learned_ws(p);
     if (e != cudaSuccess) { set_last_error("hobc_gcv_binned", e); return HOBC_ERR_CUDA; }
     if (!p->grid_ascending) {
@@ -1514,6 +1517,7 @@ hobc_status hobc_gcv_binned(hobc_plan* p, const void* ghat_dev, const void* d_de
 hobc_status hobc_deblur_binned(hobc_plan* p, const void* g_dev, const void* psf_dev, void* f_dev, int* mu_index_dev,
                                int* fell_back_dev) {
     if (!p || !g_dev || !psf_dev || !f_dev) return HOBC_ERR_ARG;
+    if (plain_only_family(p->fam)) return HOBC_ERR_UNSUPPORTED;
     cudaError_t e = ensure_learned_ws(p);
     if (e != cudaSuccess) { set_last_error("hobc_deblur_binned", e); return HOBC_ERR_CUDA; }
     if (!p->grid_ascending) {
@@ -1530,6 +1534,7 @@ hobc_status hobc_deblur_binned(hobc_plan* p, const void* g_dev, const void* psf_
 hobc_status hobc_gcv_refine(hobc_plan* p, const void* ghat_dev, const void* d_dev, const int* mu_index_dev,
                             double* mu_dev, double* gcv_dev) {
     if (!p || !ghat_dev || !d_dev || !mu_index_dev || !mu_dev) return HOBC_ERR_ARG;
+    if (plain_only_family(p->fam)) return HOBC_ERR_UNSUPPORTED;
     cudaError_t e = ensure_learned_ws(p);
     if (e != cudaSuccess) { set_last_error("hobc_gcv_refine", e); return HOBC_ERR_CUDA; }
     if (!p->grid_ascending) {
@@ -1553,6 +1558,7 @@ hobc_status hobc_filter_synthesis_mu(hobc_plan* p, const void* ghat_dev, const v
 hobc_status hobc_deblur_refined(hobc_plan* p, const void* g_dev, const void* psf_dev, void* f_dev, int* mu_index_dev,
                                 double* mu_dev) {
     if (!p || !g_dev || !psf_dev || !f_dev) return HOBC_ERR_ARG;
+    if (plain_only_family(p->fam)) return HOBC_ERR_UNSUPPORTED;
     cudaError_t e = ensure_learned_ws(p);
     if (e != cudaSuccess) { set_last_error("hobc_deblur_refined", e); return HOBC_ERR_CUDA; }
     if (!p->grid_ascending) {

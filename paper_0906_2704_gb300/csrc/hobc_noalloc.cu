@@ -167,12 +167,13 @@ extern "C" hobc_status hobc_gcv_noalloc(const hobc_plan_desc* desc, const void* 
     const hobc_status vs = hobc::resolve_desc(dsc, false, &fam);
     if (vs != HOBC_OK) return vs;
     if (dsc.prec != HOBC_FP64 && dsc.prec != HOBC_FP32) return HOBC_ERR_UNSUPPORTED;   // FFT-path spectra only
-    const bool two_borders = fam == HOBC_FAMILY_SINE_CUBIC || fam == HOBC_FAMILY_COSINE_QUARTIC;
-
-    // geometry of the stored spectrum (include/hobc.h, "Spectrum layout")
+    // geometry of the stored spectrum (include/hobc.h, "Spectrum layout"): the
+    // trigonometric order N of an axis and the stored entries of the last one
+    const int nb = hobc::fam_nb(fam);
+    auto order = [&](int n) { return fam == hobc::FAM_P ? n : n - 2 * nb; };
     const int nl = dsc.n[dsc.ndim - 1];
-    const int Nl = two_borders ? nl - 4 : nl - 2;
-    const int Wl = fam == HOBC_FAMILY_FOURIER ? Nl / 2 + 3 : nl;
+    const int Nl = order(nl);
+    const int Wl = hobc::fam_fourier(fam) ? Nl / 2 + 1 + 2 * nb : nl;
     const long long S = dsc.ndim == 1 ? (long long)Wl : (long long)Wl * dsc.n[0];
     const int chunk = hobc::gcv_chunk_for(S, dsc.n_mu, dsc.prec == HOBC_FP64);
     const long long chunks = (S + chunk - 1) / chunk;
@@ -199,7 +200,7 @@ extern "C" hobc_status hobc_gcv_noalloc(const hobc_plan_desc* desc, const void* 
     geo.ndim = dsc.ndim;
     geo.fam = fam;
     geo.n0 = dsc.n[0];
-    geo.N0 = two_borders ? dsc.n[0] - 4 : dsc.n[0] - 2;
+    geo.N0 = order(dsc.n[0]);
     geo.n1 = nl;
     geo.N1 = Nl;
     geo.W1 = Wl;
@@ -213,7 +214,7 @@ extern "C" hobc_status hobc_gcv_noalloc(const hobc_plan_desc* desc, const void* 
     if (s != HOBC_OK) return s;
     unsigned char* scratch = static_cast<unsigned char*>(base);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
-    const int cplx = fam == HOBC_FAMILY_FOURIER;
+    const int cplx = hobc::fam_fourier(fam);
     if (dsc.prec == HOBC_FP64)
         return launch<double>(geo, cplx, dsc.batch, (int)chunks, ghat_dev, d_dev, S, dsc.psf_per_item, mu_dev,
                               scratch, mu_bytes, gcv_dev, mu_index_dev, st);

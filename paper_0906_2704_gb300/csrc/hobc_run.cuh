@@ -73,7 +73,7 @@ template <typename T, int FAM>
 static hobc_status pair_analysis(hobc_plan_s* p, const AxisHost& a, const T* in, long long in_item,
                                  long long in_rs, void* out, long long out_item, long long out_rs,
                                  long long out_cs, int nlines, int items) {
-    typedef typename ElemT<T, FAM == FAM_F>::t E;
+    typedef typename ElemT<T, fam_fourier(FAM)>::t E;
     Launch l = pair_launch(a, sizeof(C2<T>), sizeof(E), nlines, items, out_rs == 1);
     k_pair_analysis<T, FAM><<<l.grid, l.block, l.smem, p->stream>>>(
         in, in_item, in_rs, reinterpret_cast<E*>(out), out_item, out_rs, out_cs, nlines, dev_axis<T>(a));
@@ -84,7 +84,7 @@ template <typename T, int FAM, int FMODE>
 static hobc_status pair_synthesis(hobc_plan_s* p, const AxisHost& a, const void* in, long long in_item,
                                   long long in_rs, long long in_cs, T* out, long long out_item,
                                   long long out_rs, int nlines, int items, const FilterDesc& fd) {
-    typedef typename ElemT<T, FAM == FAM_F>::t E;
+    typedef typename ElemT<T, fam_fourier(FAM)>::t E;
     Launch l = pair_launch(a, sizeof(C2<T>), sizeof(E), nlines, items, in_rs == 1);
     k_pair_synthesis<T, FAM, FMODE><<<l.grid, l.block, l.smem, p->stream>>>(
         reinterpret_cast<const E*>(in), in_item, in_rs, in_cs, out, out_item, out_rs, nlines, dev_axis<T>(a), fd);
@@ -121,9 +121,9 @@ static hobc_status analysis_fam(hobc_plan_s* p, const T* g, void* ghat) {
     const int n0 = a0.n, n1 = a1.n;
     hobc_status s = pair_analysis<T, FAM>(p, a1, g, (long long)n0 * n1, n1, p->R, S, 1, n0, n0, B);
     if (s != HOBC_OK) return s;
-    if constexpr (FAM == FAM_F) {
+    if constexpr (fam_fourier(FAM)) {
         Launch l = cplx_launch(a0, sizeof(C2<T>), a1.W, B);
-        k_cplx_analysis<T><<<l.grid, l.block, l.smem, p->stream>>>(
+        k_cplx_analysis<T, FAM><<<l.grid, l.block, l.smem, p->stream>>>(
             reinterpret_cast<const C2<T>*>(p->R), reinterpret_cast<C2<T>*>(ghat), S, a1.W, dev_axis<T>(a0));
         return check_launch(p, "k_cplx_analysis");
     } else {
@@ -140,6 +140,10 @@ hobc_status run_analysis(hobc_plan_s* p, const void* g, void* ghat) {
         case FAM_S3: return analysis_fam<T, FAM_S3>(p, gt, ghat);
         case FAM_C4: return analysis_fam<T, FAM_C4>(p, gt, ghat);
         case FAM_C: return analysis_fam<T, FAM_C>(p, gt, ghat);
+        case FAM_P: return analysis_fam<T, FAM_P>(p, gt, ghat);
+        case FAM_F4:
+            if constexpr (sizeof(T) == 8) return analysis_fam<T, FAM_F4>(p, gt, ghat);   // FP64 only
+            return HOBC_ERR_UNSUPPORTED;
         default: return analysis_fam<T, FAM_F>(p, gt, ghat);
     }
 }
@@ -158,9 +162,9 @@ static hobc_status synthesis_fam(hobc_plan_s* p, const void* c, T* y, const Filt
     const long long S = (long long)p->spec_elems;
     const int n0 = a0.n, n1 = a1.n;
     hobc_status s;
-    if constexpr (FAM == FAM_F) {
+    if constexpr (fam_fourier(FAM)) {
         Launch l = cplx_launch(a0, sizeof(C2<T>), a1.W, B);
-        k_cplx_synthesis<T, FILTER><<<l.grid, l.block, l.smem, p->stream>>>(
+        k_cplx_synthesis<T, FAM, FILTER><<<l.grid, l.block, l.smem, p->stream>>>(
             reinterpret_cast<const C2<T>*>(c), reinterpret_cast<C2<T>*>(p->R), S, a1.W, dev_axis<T>(a0), fd);
         s = check_launch(p, "k_cplx_synthesis");
     } else {
@@ -181,6 +185,10 @@ hobc_status run_synthesis(hobc_plan_s* p, const void* c, void* y) {
         case FAM_S3: return synthesis_fam<T, FAM_S3, false>(p, c, yt, fd);
         case FAM_C4: return synthesis_fam<T, FAM_C4, false>(p, c, yt, fd);
         case FAM_C: return synthesis_fam<T, FAM_C, false>(p, c, yt, fd);
+        case FAM_P: return synthesis_fam<T, FAM_P, false>(p, c, yt, fd);
+        case FAM_F4:
+            if constexpr (sizeof(T) == 8) return synthesis_fam<T, FAM_F4, false>(p, c, yt, fd);
+            return HOBC_ERR_UNSUPPORTED;
         default: return synthesis_fam<T, FAM_F, false>(p, c, yt, fd);
     }
 }
@@ -195,6 +203,10 @@ hobc_status run_filter_synthesis(hobc_plan_s* p, const void* ghat, const void* D
         case FAM_S3: return synthesis_fam<T, FAM_S3, true>(p, ghat, ft, fd);
         case FAM_C4: return synthesis_fam<T, FAM_C4, true>(p, ghat, ft, fd);
         case FAM_C: return synthesis_fam<T, FAM_C, true>(p, ghat, ft, fd);
+        case FAM_P: return synthesis_fam<T, FAM_P, true>(p, ghat, ft, fd);
+        case FAM_F4:
+            if constexpr (sizeof(T) == 8) return synthesis_fam<T, FAM_F4, true>(p, ghat, ft, fd);
+            return HOBC_ERR_UNSUPPORTED;
         default: return synthesis_fam<T, FAM_F, true>(p, ghat, ft, fd);
     }
 }
@@ -211,6 +223,10 @@ hobc_status run_filter_synthesis_mu(hobc_plan_s* p, const void* ghat, const void
         case FAM_S3: return synthesis_fam<T, FAM_S3, true>(p, ghat, ft, fd);
         case FAM_C4: return synthesis_fam<T, FAM_C4, true>(p, ghat, ft, fd);
         case FAM_C: return synthesis_fam<T, FAM_C, true>(p, ghat, ft, fd);
+        case FAM_P: return synthesis_fam<T, FAM_P, true>(p, ghat, ft, fd);
+        case FAM_F4:
+            if constexpr (sizeof(T) == 8) return synthesis_fam<T, FAM_F4, true>(p, ghat, ft, fd);
+            return HOBC_ERR_UNSUPPORTED;
         default: return synthesis_fam<T, FAM_F, true>(p, ghat, ft, fd);
     }
 }
@@ -220,7 +236,7 @@ hobc_status run_filter_synthesis_mu(hobc_plan_s* p, const void* ghat, const void
 template <typename T>
 hobc_status run_eig(hobc_plan_s* p, const void* psf, void* D) {
     const AxisHost& last = p->ax[p->nax - 1];
-    const bool cplx = p->fam == FAM_F;
+    const bool cplx = fam_fourier(p->fam);
     const double2* E0;
     int p0, n0;
     if (p->nax == 2) { E0 = p->ax[0].etab; p0 = p->ax[0].p; n0 = p->ax[0].n; }
@@ -266,7 +282,7 @@ hobc_status run_gcv(hobc_plan_s* p, const void* ghat, const void* D, double* gcv
             typedef typename ElemT<T, true>::t CT;
 #define HOBC_ITEMS(TPI_)                                                                                   \
     if (tpi == TPI_) {                                                                                     \
-        if (p->fam == FAM_F)                                                                               \
+        if (fam_fourier(p->fam))                                                                           \
             k_gcv_items<T, true, TPI_><<<grid, 256, 0, p->stream>>>(                                        \
                 reinterpret_cast<const CT*>(ghat), reinterpret_cast<const CT*>(D), (long long)p->spec_elems, \
                 p->desc.psf_per_item, reinterpret_cast<const T*>(p->muT), geo, B, gcv, mu_idx);            \
@@ -282,7 +298,7 @@ hobc_status run_gcv(hobc_plan_s* p, const void* ghat, const void* D, double* gcv
     }
     dim3 grid((unsigned)(p->gcv_chunks * (long long)p->desc.batch));
     const size_t smem = 4 * (size_t)p->gcv_chunk * sizeof(T);
-    if (p->fam == FAM_F)
+    if (fam_fourier(p->fam))
         k_gcv_partials<T, true><<<grid, 256, smem, p->stream>>>(
             reinterpret_cast<const C2<T>*>(ghat), reinterpret_cast<const C2<T>*>(D), (long long)p->spec_elems,
             p->desc.psf_per_item, reinterpret_cast<const T*>(p->muT), geo, p->partials);
@@ -329,9 +345,23 @@ hobc_status prepare_kernels(hobc_plan_s* p) {
     HOBC_SMEM((k_pair_synthesis<T, FAM_C, 2>));
     HOBC_SMEM((k_pair_synthesis<T, FAM_F, 0>));
     HOBC_SMEM((k_pair_synthesis<T, FAM_F, 1>));
-    HOBC_SMEM((k_cplx_analysis<T>));
-    HOBC_SMEM((k_cplx_synthesis<T, false>));
-    HOBC_SMEM((k_cplx_synthesis<T, true>));
+    HOBC_SMEM((k_cplx_analysis<T, FAM_F>));
+    HOBC_SMEM((k_cplx_synthesis<T, FAM_F, false>));
+    HOBC_SMEM((k_cplx_synthesis<T, FAM_F, true>));
+    HOBC_SMEM((k_pair_analysis<T, FAM_P>));
+    HOBC_SMEM((k_pair_synthesis<T, FAM_P, 0>));
+    HOBC_SMEM((k_pair_synthesis<T, FAM_P, 1>));
+    HOBC_SMEM((k_cplx_analysis<T, FAM_P>));
+    HOBC_SMEM((k_cplx_synthesis<T, FAM_P, false>));
+    HOBC_SMEM((k_cplx_synthesis<T, FAM_P, true>));
+    if constexpr (sizeof(T) == 8) {
+        HOBC_SMEM((k_pair_analysis<T, FAM_F4>));
+        HOBC_SMEM((k_pair_synthesis<T, FAM_F4, 0>));
+        HOBC_SMEM((k_pair_synthesis<T, FAM_F4, 1>));
+        HOBC_SMEM((k_cplx_analysis<T, FAM_F4>));
+        HOBC_SMEM((k_cplx_synthesis<T, FAM_F4, false>));
+        HOBC_SMEM((k_cplx_synthesis<T, FAM_F4, true>));
+    }
     HOBC_SMEM((k_gcv_partials<T, false>));
     HOBC_SMEM((k_gcv_partials<T, true>));
 #undef HOBC_SMEM

@@ -67,7 +67,10 @@ hobc_status hobc_volume_create(const hobc_volume_desc* desc, const double* mu_gr
     hobc_status s = hobc_plan_create(&sd, mu_grid_host, cuda_stream, &q->slice);
     if (s != HOBC_OK) { volume_free(q); return s; }
     q->fam = q->slice->fam;
-    if (q->fam == HOBC_FAMILY_COSINE_QUARTIC) { volume_free(q); return HOBC_ERR_UNSUPPORTED; }   // 2D and 1D only
+    if (q->fam == HOBC_FAMILY_COSINE_QUARTIC || plain_only_family(q->fam)) {   // 2D and 1D only
+        volume_free(q);
+        return HOBC_ERR_UNSUPPORTED;
+    }
     const int need = q->fam == HOBC_FAMILY_SINE_CUBIC ? 4 : 2;
     if (d.psf[0] > d.n[0] - need) { volume_free(q); return HOBC_ERR_SIZE; }
     const bool fp64 = d.prec == HOBC_FP64;

@@ -120,7 +120,7 @@ hobc_status run3_analysis(hobc_volume_s* q, const void* g, void* ghat) {
         s = vol_transpose<C2<T>>(q, sl->G, q->X, n0, S2);           // [B][S2][n0]
         if (s != HOBC_OK) return s;
         Launch l = cplx_launch(q->az, sizeof(C2<T>), (int)S2, B);
-        k_cplx_analysis<T><<<l.grid, l.block, l.smem, q->stream>>>(reinterpret_cast<const C2<T>*>(q->X),
+        k_cplx_analysis<T, FAM_F><<<l.grid, l.block, l.smem, q->stream>>>(reinterpret_cast<const C2<T>*>(q->X),
                                                                    reinterpret_cast<C2<T>*>(ghat), S3, (int)S2,
                                                                    dev_axis<T>(q->az));
         return check_launch(sl, "k_cplx_analysis");
@@ -162,7 +162,7 @@ hobc_status run3_synthesis(hobc_volume_s* q, const void* c, void* y, const void*
     FilterDesc none = make_filter(sl, nullptr, nullptr);
     if (F) {
         Launch l = cplx_launch(q->az, sizeof(C2<T>), (int)S2, B);
-        k_cplx_synthesis<T, false><<<l.grid, l.block, l.smem, q->stream>>>(
+        k_cplx_synthesis<T, FAM_F, false><<<l.grid, l.block, l.smem, q->stream>>>(
             reinterpret_cast<const C2<T>*>(src), reinterpret_cast<C2<T>*>(q->X), S3, (int)S2, dev_axis<T>(q->az), none);
         s = check_launch(sl, "k_cplx_synthesis");
         if (s == HOBC_OK) s = vol_transpose<C2<T>>(q, q->X, sl->G, (int)S2, n0);

@@ -33,7 +33,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 FAMILY = {"auto": 0, "sine": 1, "cosine": 2, "fourier": 3, "sine3": 4, "reflective": 5, "periodic": 6,
-          "cosine4": 7}
+          "cosine4": 7, "fourier4": 8}
 FAMILY_NAME = {v: k for k, v in FAMILY.items()}
 SMOOTHING = {"I": 0, "identity": 0, "lap": 1, "laplacian": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "split_bf16": 2}

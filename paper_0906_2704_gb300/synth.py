@@ -251,6 +251,27 @@ def disk_psf(radius: float) -> np.ndarray:
     return h / h.sum()
 
 
+def motion_defocus_psf(radius: float, length: float, angle_deg: float, taps: int) -> np.ndarray:
+    """A nonsymmetric PSF: out-of-focus blur (a disk of ``radius``) combined with a
+    one-sided linear motion of ``length`` pixels from the centre at ``angle_deg``
+    (the path sampled every 1/8 pixel, spread bilinearly), in a taps x taps array
+    (odd), normalised to sum 1."""
+    m = taps // 2
+    motion = np.zeros((taps, taps))
+    a = np.deg2rad(angle_deg)
+    for t in np.arange(0.0, length, 0.125):
+        x, y = m + t * np.cos(a), m - t * np.sin(a)
+        c0, r0 = int(np.floor(x)), int(np.floor(y))
+        fx, fy = x - c0, y - r0
+        for dr, wr in ((0, 1 - fy), (1, fy)):
+            for dc, wc in ((0, 1 - fx), (1, fx)):
+                motion[r0 + dr, c0 + dc] += wr * wc
+    from scipy.signal import fftconvolve
+    h = fftconvolve(motion, disk_psf(radius), mode="same")
+    h = np.clip(h, 0.0, None)
+    return h / h.sum()
+
+
 def learned_set(seed: int, count: int, n: int, taps: int = 11, r_lo: float = 1.5, r_hi: float = 5.0,
                 eta_lo: float = 1e-3, eta_hi: float = 3e-2):
     """``count`` n x n problems for the learned choice of mu, each with its own

@@ -9,7 +9,7 @@ from oracle import hobc_oracle as O
 from paper_0906_2704_gb300 import synth
 
 FAM_LETTER = {"sine": "S", "cosine": "C", "fourier": "F", "sine3": "S3", "reflective": "R", "periodic": "PH",
-              "cosine4": "C4"}
+              "cosine4": "C4", "fourier4": "F4"}
 EPS32 = 2.0 ** -24
 
 
@@ -18,6 +18,11 @@ def stored_t(fam: str, n: int, half: bool) -> np.ndarray:
     if fam == "F" and half:
         H = (n - 2) // 2 + 1
         return np.concatenate([np.arange(H + 1), [n - 1]])
+    if fam == "F4" and half:
+        H = (n - 4) // 2 + 1
+        return np.concatenate([np.arange(H + 2), [n - 2, n - 1]])
+    if fam == "P" and half:
+        return np.arange(n // 2 + 1)
     return np.arange(n)
 
 
@@ -31,7 +36,10 @@ def to_layout(fam: str, full: np.ndarray) -> np.ndarray:
 
 
 def psf_for(fam: str, ndim: int, taps):
-    """A PSF of the right symmetry for the family (nonsymmetric only for F)."""
+    """A PSF of the right symmetry for the family (nonsymmetric for the Fourier
+    families F, F4 and the periodic family P)."""
+    if fam in ("F4", "P"):
+        fam = "F"
     if ndim == 1:
         if fam == "F":
             h = synth.gaussian_psf_1d(1.2, taps) * np.linspace(0.6, 1.4, taps)
@@ -111,7 +119,7 @@ def log2_fft(fam: str, shape) -> float:
     """log2 of the largest power-of-two FFT the kernels use for these lengths."""
     out = 0.0
     for n in shape:
-        N = n - 4 if fam in ("S3", "C4") else n - 2
+        N = n - 4 if fam in ("S3", "C4", "F4") else n if fam == "P" else n - 2
         L = 2 * (N + 1) if fam in ("S", "S3") else N
         M = L if (L >= 8 and L & (L - 1) == 0) else max(8, 1 << int(np.ceil(np.log2(2 * L - 1))))
         out = max(out, np.log2(M))

@@ -46,7 +46,11 @@ def _create(hobc, **kw):
     (dict(psf=4), "HOBC_ERR_SIZE"),                     # even PSF
     (dict(n=8, psf=7), "HOBC_ERR_SIZE"),                # 2m+1 > n-2
     (dict(bc_degree=5), "HOBC_ERR_UNSUPPORTED"),
-    (dict(bc_degree=4, psf_symmetric=False), "HOBC_ERR_UNSUPPORTED"),   # quartic cosine family needs symmetry
+    (dict(family="cosine4", bc_degree=4, psf_symmetric=False), "HOBC_ERR_UNSUPPORTED"),   # needs symmetry
+    (dict(family="fourier4", bc_degree=2), "HOBC_ERR_UNSUPPORTED"),
+    (dict(family="fourier4", bc_degree=4, prec="fp32", psf_symmetric=False), "HOBC_ERR_UNSUPPORTED"),
+    (dict(family="fourier4", bc_degree=4, n=7, psf=1), "HOBC_ERR_SIZE"),   # N = n - 4 >= 4
+    (dict(family="periodic", bc_degree=2), "HOBC_ERR_UNSUPPORTED"),       # periodic: degree 0
     (dict(family="cosine4", bc_degree=2), "HOBC_ERR_UNSUPPORTED"),
     (dict(bc_degree=4, n=9, psf=7), "HOBC_ERR_SIZE"),               # 2m+1 <= n-4 for degree 4
     (dict(prec="split_bf16", bc_degree=4), "HOBC_ERR_UNSUPPORTED"),  # no dense matrices for degree 4
@@ -127,14 +131,15 @@ def test_learned_entry_points_reject_bad_arguments_on_the_host(hobc):
 
 
 @pytest.mark.parametrize("kw", [
-    dict(n=5), dict(n=2048), dict(bc_degree=5), dict(bc_degree=4, psf_symmetric=False),
+    dict(n=5), dict(n=2048), dict(bc_degree=5), dict(family="cosine4", bc_degree=4, psf_symmetric=False),
+    dict(family="fourier4", bc_degree=4, prec="fp32", n=16, psf=3), dict(family="periodic", bc_degree=2),
     dict(family="cosine4", bc_degree=2), dict(bc_degree=3, psf_symmetric=False),
     dict(family="sine3", bc_degree=2), dict(bc_degree=1, psf_symmetric=False),
     dict(family="sine", bc_degree=2), dict(family="fourier", bc_degree=1), dict(batch=0),
     dict(ndim=3), dict(family="sine3", bc_degree=3, n=7, psf=1), dict(family="cosine4", bc_degree=4, n=6, psf=1),
     dict(bc_degree=3, n=7, psf=1), dict(bc_degree=4, n=7, psf=1),
     dict(bc_degree=4, prec="fp32", n=16, psf=3),                   # degree 4 is FP64 only
-    dict(family="periodic", bc_degree=0, prec="fp64"),             # comparison families: dense engine only
+    dict(family="reflective", bc_degree=0, prec="fp64"),           # reflective: dense engine only
 ])
 def test_noalloc_rejects_what_plan_create_rejects(hobc, kw):
     """hobc_gcv_noalloc checks a description as hobc_plan_create does (the PSF

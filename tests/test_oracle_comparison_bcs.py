@@ -55,3 +55,33 @@ def test_gcv_is_the_same_in_the_hartley_and_dft_bases():
         f, _, _, _ = O.deblur_2d(fam, h, g, "lap", mus)
         fs.append(f)
     assert np.allclose(fs[0], fs[1], atol=1e-10)
+
+
+@pytest.mark.parametrize("n", [9, 16, 31])
+def test_periodic_dft_form_equals_the_circulant_for_a_nonsymmetric_psf(n):
+    """The periodic family in the DFT basis ('P', the form the FFT path runs): for a
+    nonsymmetric PSF, F^H diag(z(-theta)) F is the circulant of the periodic rule
+    (Sec. 2.1, Eq. (eq:permat)); the eigenvalues at +theta (a sign slip) are not, nor
+    is the Hartley form."""
+    h = synth.gaussian_psf_1d(1.2, 7) * np.linspace(0.5, 1.5, 7)
+    h /= h.sum()
+    A = O.bc_matrix(h, n, "periodic")
+    assert np.allclose(O.blur_matrix_spectral("P", h, n), A, atol=1e-13)
+    T = O.transform_matrix("P", n)
+    wrong = T @ np.diag(O.symbol(h, O.eigen_angles("P", n))) @ np.linalg.inv(T)
+    assert not np.allclose(wrong, A, atol=1e-6)
+    assert np.allclose(wrong, O.bc_matrix(h[::-1], n, "periodic"), atol=1e-13)
+
+
+def test_periodic_dft_form_2d_nonsymmetric():
+    h = synth.gaussian_psf_2d_rotated(1.6, 0.9, 30.0, 5, 0.6, -0.4)
+    n0, n1 = 8, 9
+    A = O.bc_matrix_2d(h, n0, n1, "periodic")
+    assert np.allclose(O.blur_matrix_2d_spectral("P", h, n0, n1), A, atol=1e-12)
+    # the Laplacian of the periodic rule has eigenvalues s(t0) + s(t1) in the same basis
+    lap = np.zeros((3, 3))
+    lap[1, :] += [-1.0, 2.0, -1.0]
+    lap[:, 1] += [-1.0, 2.0, -1.0]
+    T = np.kron(O.transform_matrix("P", n0), O.transform_matrix("P", n1))
+    s = O.smoothing_2d("P", n0, n1, "lap").ravel()
+    assert np.allclose(T @ np.diag(s) @ np.linalg.inv(T), O.bc_matrix_2d(lap, n0, n1, "periodic"), atol=1e-12)

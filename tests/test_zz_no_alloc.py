@@ -31,16 +31,16 @@ TOL = {"fp64": 1e-10, "fp32": 1e-5}
 
 def _setup(ndim, n, fam, L, prec, batch, K, seed):
     """Spectra, eigenvalues and the plan-based GCV answer for one case."""
-    letter = P.FAM_LETTER[fam]
+    letter = "P" if fam == "periodic" else P.FAM_LETTER[fam]     # periodic: the FFT-path family
+    sym = letter not in ("F", "F4", "P")
     dt = np.float64 if prec == "fp64" else np.float32
     tdt = torch.float64 if prec == "fp64" else torch.float32
     taps = 5 if ndim == 1 else (5, 5)
     h = P.psf_for(letter, ndim, taps)
     g, _ = P.problems(ndim, (n,) if ndim == 1 else n, h, batch, seed)
     mus = synth.mu_grid(K, 1e-6, 1.0)
-    deg = 1 if letter == "S" else 2
-    plan = hobc.Plan(ndim, n, h.shape, deg, mus, L=L, prec=prec, family=fam, psf_symmetric=letter != "F",
-                     batch=batch)
+    deg = {"S": 1, "F4": 4, "P": 0}.get(letter, 2)
+    plan = hobc.Plan(ndim, n, h.shape, deg, mus, L=L, prec=prec, family=fam, psf_symmetric=sym, batch=batch)
     cs = (2,) if plan.spec_complex else ()
     gh = torch.empty((batch, plan.spec_elems) + cs, dtype=tdt, device="cuda")
     d = torch.empty((1, plan.spec_elems) + cs, dtype=tdt, device="cuda")
@@ -49,7 +49,7 @@ def _setup(ndim, n, fam, L, prec, batch, K, seed):
     G_ref = torch.empty((batch, K), dtype=torch.float64, device="cuda")
     mi_ref = torch.empty(batch, dtype=torch.int32, device="cuda")
     plan.gcv(gh, d, G_ref, mi_ref)
-    desc = hobc.make_desc(ndim, n, deg, K, L=L, prec=prec, family=fam, psf_symmetric=letter != "F", batch=batch)
+    desc = hobc.make_desc(ndim, n, deg, K, L=L, prec=prec, family=fam, psf_symmetric=sym, batch=batch)
     mu_d = torch.from_numpy(mus).cuda()
     return desc, gh, d, mu_d, G_ref, mi_ref
 
@@ -74,6 +74,9 @@ CASES = [
     (1, 77, "sine", "I", "fp64", 5, 24),
     (2, (34, 21), "cosine", "lap", "fp64", 3, 17),
     (2, (66, 40), "fourier", "I", "fp32", 4, 256),
+    (2, (20, 17), "fourier4", "lap", "fp64", 2, 32),
+    (1, 50, "periodic", "I", "fp32", 3, 40),
+    (2, (33, 40), "periodic", "lap", "fp32", 3, 64),
 ]
 
 
@@ -105,12 +108,15 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
 @pytest.mark.parametrize("ndim,n,fam,L,prec", [
     (2, (34, 21), "fourier", "lap", "fp32"),
     (1, 90, "sine3", "I", "fp64"),
+    (2, (20, 17), "periodic", "lap", "fp64"),
+    (1, 30, "fourier4", "I", "fp64"),
 ])
 def test_noalloc_against_the_oracle(ndim, n, fam, L, prec):
     """G of the allocation-free scan against the oracle's Eq. (eq:gcv2) on identical
     inputs: the oracle's spectrum and eigenvalues, rounded to the working precision,
     go to the GPU, and the oracle evaluates G on the same rounded values."""
-    letter = P.FAM_LETTER[fam]
+    letter = "P" if fam == "periodic" else P.FAM_LETTER[fam]     # periodic: the FFT-path family
+    sym = letter not in ("F", "F4", "P")
     dt = np.float64 if prec == "fp64" else np.float32
     shape = (n,) if ndim == 1 else n
     taps = 5 if ndim == 1 else (5, 5)
@@ -118,10 +124,10 @@ def test_noalloc_against_the_oracle(ndim, n, fam, L, prec):
     batch, K = 3, 40
     g, _ = P.problems(ndim, shape, h, batch, seed=11)
     mus = synth.mu_grid(K, 1e-7, 1.0)
-    deg = {"S": 1, "C": 2, "F": 2, "S3": 3}[letter]
+    deg = {"S": 1, "C": 2, "F": 2, "S3": 3, "P": 0, "F4": 4}[letter]
     orc = [P.oracle_steps(letter, ndim, h, g[b], L, mus) for b in range(batch)]
 
-    cplx = letter == "F"          # the other families keep real spectra (the symbol's
+    cplx = not sym                # the other families keep real spectra (the symbol's
                                   # imaginary rounding residue of a symmetric PSF is dropped)
 
     def rounded(full):
@@ -138,8 +144,7 @@ def test_noalloc_against_the_oracle(ndim, n, fam, L, prec):
     d_full = rounded(orc[0][1])
     gh = torch.from_numpy(np.stack([stored(x) for x in gh_full])).cuda()
     d = torch.from_numpy(stored(d_full)[None]).cuda()
-    desc = hobc.make_desc(ndim, shape, deg, K, L=L, prec=prec, family=fam, psf_symmetric=letter != "F",
-                          batch=batch)
+    desc = hobc.make_desc(ndim, shape, deg, K, L=L, prec=prec, family=fam, psf_symmetric=sym, batch=batch)
     G = torch.empty((batch, K), dtype=torch.float64, device="cuda")
     mi = torch.empty(batch, dtype=torch.int32, device="cuda")
     for _ in range(2):
