@@ -326,6 +326,34 @@ def run_ours(args):
         d = (f.cpu().numpy().astype(np.float64) - ft).reshape(B, -1)
         return np.linalg.norm(d, axis=1) / np.linalg.norm(ft.reshape(B, -1), axis=1)
 
+    # the same method with G(mu_j) evaluated by bin expansion (hobc_plan_set_gcv_mode):
+    # every grid value, within the stated truncation bound of the direct scan's curve
+    expansion, f_e, mi_e = None, None, None
+    if prec != "fp64":
+        plan_x = hobc.Plan(2, (N_SIDE, N_SIDE), h.shape, 2, mus, L="I", prec=prec, family="fourier", batch=B,
+                           stream=stream)
+        plan_x.set_gcv_mode("expansion")
+        f_e = torch.empty_like(g_d)
+        mi_e = torch.empty(B, dtype=torch.int32, device=dev)
+        ms_e, clk_e = _timed(lambda: plan_x.deblur(g_d, h_d, f_e, mi_e), stream, args.steps, args.warmup)
+        e_launches = plan_x.last_launch_count
+        ms_e = max_over_ranks(ms_e, dist, dev)
+        G_e = torch.empty((B, K_MU), dtype=torch.float64, device=dev)
+        mi_e2 = torch.empty_like(mi_e)
+        ms_eg, _ = _timed(lambda: plan_x.gcv(ghat, dbuf, G_e, mi_e2), stream, args.steps, args.warmup)
+        G_dir = torch.empty_like(G_e)
+        mi_dir = torch.empty_like(mi_e)
+        plan.gcv(ghat, dbuf, G_dir, mi_dir)
+        torch.cuda.synchronize()
+        r_e = rre(f_e)
+        expansion = {"value": whole_job_rate(world, B, args.steps, ms_e / 1e3), "unit": "deblurs/s",
+                     "ms_per_step": ms_e / args.steps, "gpu_launches": e_launches * args.steps,
+                     "gcv_ms": ms_eg / args.steps, "truncation_bound": plan_x.gcv_expansion_bound,
+                     "G_rel_diff_to_direct_scan_max": float(((G_e - G_dir).abs() / G_dir.abs()).max()),
+                     "index_agreement_with_full_scan": float((mi_e2 == mi_dir).float().mean()),
+                     "rre_mean": {"expansion": float(r_e.mean())}, "clocks": clk_e}
+        plan_x.close()
+
     # the grid argmin refined over continuous mu (5 rounds of 9 points in its bracket)
     f_r = torch.empty_like(g_d)
     mi_r = torch.empty(B, dtype=torch.int32, device=dev)
@@ -422,6 +450,8 @@ def run_ours(args):
               "index_agreement_with_full_scan": float((mi_b == mi_d).float().mean()),
               "rre_mean": {"full_scan": float(r_full.mean()), "binned": float(r_bin.mean())},
               "clocks": clk_b}
+    if expansion is not None:
+        expansion["rre_mean"]["full_scan"] = float(r_full.mean())
 
     # end to end through the host-buffer entry point (pinned host memory)
     g_h = torch.from_numpy(g.astype(npdt)).pin_memory().numpy()
@@ -510,7 +540,7 @@ def run_ours(args):
         cpu["single_core"] = {"value": (1.0 / sec1) if sec1 else None, "unit": "deblurs/s", "cores": 1,
                               "sample": "1 image of the same workload, one BLAS thread"}
         oracle_error = default_oracle_error(kept, h, mus, f_d, mi_d, G_grid, f_b, mi_b, f_r, mu_r, G_ref,
-                                            f_x, mi_x, G_x, f_xs, mi_xs)
+                                            f_x, mi_x, G_x, f_xs, mi_xs, f_e, mi_e)
 
     if rank == 0:
         line = {
@@ -524,6 +554,7 @@ def run_ours(args):
             "hbm_roofline": hbm, "steps_ms": steps_ms, "cpu_baseline": cpu, "clocks": clocks,
             "learned_mu": learned_arm,
             "binned_mu": binned, "refined_mu": refined, "exact_gcv": exact, "exact_gcv_search": exact_search,
+            "gcv_expansion": expansion,
             "oracle_error": oracle_error, "precision": prec, "transform_roofline": transform_roofline,
         }
         print(json.dumps(line), flush=True)
@@ -544,7 +575,7 @@ def G_xs_probe(plan, g_d, h_d, B):
 
 
 def default_oracle_error(kept, h, mus, f_d, mi_d, G_grid, f_b, mi_b, f_r, mu_r, G_ref, f_x, mi_x, G_x, f_xs,
-                         mi_xs):
+                         mi_xs, f_e=None, mi_e=None):
     """Error of every arm of the 1024^2 line against the FP64 oracle on the images
     the CPU baseline ran: f in relative 2-norm at the mu the arm chose (the oracle
     filters its own spectrum at that mu), and G where the arm reports one."""
@@ -560,7 +591,7 @@ def default_oracle_error(kept, h, mus, f_d, mi_d, G_grid, f_b, mi_b, f_r, mu_r, 
     out = {"images": n, "reference": "dense FP64 oracle (separable mode) on the same g",
            "measure": "f: ||f_gpu - f_oracle(mu)||_2 / ||f_oracle(mu)||_2 at the arm's mu; G: max relative"}
     arms = {"full_scan": [], "binned_mu": [], "refined_mu": [], "exact_gcv": [], "exact_gcv_search": []}
-    g_err, g_ref_err, g_ex_err, agree = [], [], [], []
+    g_err, g_ref_err, g_ex_err, agree, agree_e = [], [], [], [], []
     for i, (f_o, G_o, k_o, ghat) in enumerate(kept):
         cache = {int(k_o): f_o}
 
@@ -573,6 +604,10 @@ def default_oracle_error(kept, h, mus, f_d, mi_d, G_grid, f_b, mi_b, f_r, mu_r, 
         arms["refined_mu"].append(rel2(fs["refined"][i], oracle_f_2d("F", h, ghat, "I", float(mr[i]))))
         arms["exact_gcv"].append(rel2(fs["exact"][i], f_at_index(int(ks["exact"][i]))))
         arms["exact_gcv_search"].append(rel2(fs["search"][i], f_at_index(int(ks["search"][i]))))
+        if f_e is not None:
+            ke = int(mi_e.cpu().numpy()[i])
+            arms.setdefault("gcv_expansion", []).append(rel2(f_e.cpu().numpy()[i], f_at_index(ke)))
+            agree_e.append(ke == int(k_o))
         g_err.append(float(np.max(np.abs(Gg[i] - G_o) / G_o)))
         agree.append(int(ks["full"][i]) == int(k_o))
         G_at = O.gcv_curve(ghat, d, s, np.array([mr[i]]))[0]
@@ -586,6 +621,9 @@ def default_oracle_error(kept, h, mus, f_d, mi_d, G_grid, f_b, mi_b, f_r, mu_r, 
     out["refined_mu"] = {"f_rel_2norm_max": max(arms["refined_mu"]), "G_rel_at_mu_max": float(max(g_ref_err))}
     out["exact_gcv"] = {"f_rel_2norm_max": max(arms["exact_gcv"]), "G_rel_at_mu_max": float(max(g_ex_err))}
     out["exact_gcv_search"] = {"f_rel_2norm_max": max(arms["exact_gcv_search"])}
+    if f_e is not None:
+        out["gcv_expansion"] = {"f_rel_2norm_max": max(arms["gcv_expansion"]),
+                                "mu_index_agreement": float(np.mean(agree_e))}
     return out
 
 

@@ -233,6 +233,37 @@ hobc_status hobc_eigenvalues(hobc_plan* plan, const void* psf_dev, void* d_dev);
 hobc_status hobc_gcv(hobc_plan* plan, const void* ghat_dev, const void* d_dev,
                      double* gcv_dev, int* mu_index_dev);
 
+/* How hobc_gcv and hobc_deblur (and the host calls) evaluate the curve of
+ * Eq. (eq:gcv2).  DIRECT (every plan's default): every (entry, mu_j) term, as
+ * described above.  EXPANSION: the same G(mu_j) for every grid value through
+ * per-bin moments of the entries: a = |d|^2/|s|^2 is grouped in 256 bins
+ * uniform in log a over [1e-3 mu_min, 1e3 mu_max) plus one bin below and one
+ * above; in a bin of centre abar, 1/(a+mu)^k is expanded in powers of
+ * (a - abar)/(abar + mu) up to the 7th, so a bin contributes through 8 moments
+ * of e = w|ghat|^2 and 8 of w, and the curve costs bins x K evaluations instead
+ * of entries x K.  The series' truncation changes each term by a relative
+ * 9 U^8/(1-U)^2 at most (U = sqrt(r) - 1, r the bins' ratio: 3.3e-9 for a grid
+ * [1e-8, 1]; hobc_gcv_expansion_bound); the moments are FP32 over pieces of at
+ * most 256 entries and FP64 over the pieces, the curve FP32 per bin with
+ * float-float sums over the bins.  Deterministic (fixed summation orders).
+ * Offered for FP32 and split-BF16 2D plans with one PSF for the batch
+ * (HOBC_ERR_UNSUPPORTED otherwise, or when the grid spans so many decades that
+ * the bound would exceed 1e-8).  Setting EXPANSION allocates its workspace
+ * (about 32 bytes per stored entry plus 32 bytes per 256 entries per problem)
+ * and copies the grid to the host once: call it outside stream capture.
+ * hobc_gcv_noalloc and the binned, refined, learned and exact choices are not
+ * affected. */
+typedef enum {
+    HOBC_GCV_DIRECT = 0,
+    HOBC_GCV_EXPANSION = 1
+} hobc_gcv_mode;
+hobc_status hobc_plan_set_gcv_mode(hobc_plan* plan, int mode);
+/* The plan's mode (-1 for a NULL plan). */
+int hobc_plan_gcv_mode(const hobc_plan* plan);
+/* The expansion's truncation bound for the plan's grid (relative, per term),
+ * or -1 if the mode was never set. */
+double hobc_gcv_expansion_bound(const hobc_plan* plan);
+
 /* Step: filter at mu* and synthesis, f = T_X diag(conj(d)/(|d|^2 + mu*|s|^2)) ghat
  * (Eq. (eq:freg)).  mu_index_dev [batch] grid indices. */
 hobc_status hobc_filter_synthesis(hobc_plan* plan, const void* ghat_dev, const void* d_dev,

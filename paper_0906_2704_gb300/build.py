@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhobc.so")
 SOURCES = ["hobc_api.cu", "hobc_f32.cu", "hobc_f64.cu", "hobc_noalloc.cu", "hobc_batched.cu", "hobc_learned.cu", "hobc_tc.cu",
-           "hobc_exact.cu", "hobc_volume.cu"]
+           "hobc_exact.cu", "hobc_volume.cu", "hobc_gcvx.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

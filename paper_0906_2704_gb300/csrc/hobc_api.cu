@@ -598,6 +598,7 @@ void hobc_plan_destroy(hobc_plan* p) {
     cudaFree(p->partials); cudaFree(p->gcv); cudaFree(p->mu_idx);
     cudaFree(p->g_in); cudaFree(p->f_out); cudaFree(p->psf_in);
     free_learned_ws(p);
+    gcvx_free(p);
     dense_free(p);
     exact_free(p);
     for (int i = 0; i < 2; ++i)

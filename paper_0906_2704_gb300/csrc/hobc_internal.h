@@ -94,6 +94,8 @@ struct hobc_plan_s {
     struct hobc_dense_s* dense;   // HOBC_SPLIT_BF16: matrices and operand workspace (hobc_tc.cu)
     struct hobc_exact_s* exact;   // exact GCV: Gram factors and line sums, allocated on first use (hobc_exact.cu)
     size_t item0;            // first problem of this view of the plan (0 for the plan itself)
+    int gcv_mode;            // HOBC_GCV_DIRECT / HOBC_GCV_EXPANSION (hobc_plan_set_gcv_mode)
+    struct hobc_gcvx_s* gx;  // the expansion's workspace, allocated when the mode is set (hobc_gcvx.cu)
 };
 
 // A 3D plan (include/hobc_volume.h): 2D passes over the slices, a transpose
@@ -131,6 +133,9 @@ template <typename T> hobc_status run_filter_synthesis_mu(hobc_plan_s* p, const 
                                                           const double* mu_val, void* f);
 template <typename T> hobc_status prepare_kernels(hobc_plan_s* p);
 void free_learned_ws(hobc_plan_s* p);
+void gcvx_free(hobc_plan_s* p);
+bool gcvx_active(const hobc_plan_s* p);
+hobc_status run_gcv_expansion(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx);
 hobc_status dense_prepare(hobc_plan_s* p);
 void dense_free(hobc_plan_s* p);
 hobc_status dense_analysis(hobc_plan_s* p, const void* g, void* ghat);

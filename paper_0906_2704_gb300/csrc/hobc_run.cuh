@@ -258,6 +258,8 @@ hobc_status run_eig(hobc_plan_s* p, const void* psf, void* D) {
 
 template <typename T>
 hobc_status run_gcv(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx) {
+    if constexpr (sizeof(T) == 4)
+        if (gcvx_active(p) && p->nax == 2) return run_gcv_expansion(p, ghat, D, gcv, mu_idx);
     GcvGeom geo;
     const AxisHost& last = p->ax[p->nax - 1];
     geo.ndim = p->nax;

@@ -66,6 +66,13 @@ _lib.hobc_plan_destroy.argtypes = [_vp]
 _lib.hobc_plan_destroy.restype = None
 _lib.hobc_plan_family.argtypes = [_vp]
 _lib.hobc_plan_family.restype = ctypes.c_int
+_lib.hobc_plan_set_gcv_mode.argtypes = [_vp, ctypes.c_int]
+_lib.hobc_plan_set_gcv_mode.restype = ctypes.c_int
+_lib.hobc_plan_gcv_mode.argtypes = [_vp]
+_lib.hobc_plan_gcv_mode.restype = ctypes.c_int
+_lib.hobc_gcv_expansion_bound.argtypes = [_vp]
+_lib.hobc_gcv_expansion_bound.restype = ctypes.c_double
+GCV_MODE = {"direct": 0, "expansion": 1}
 _lib.hobc_spectrum_size.argtypes = [_vp, ctypes.POINTER(_sz), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_sz)]
 _lib.hobc_spectrum_size.restype = ctypes.c_int
 for _name, _n in (("hobc_deblur", 6), ("hobc_deblur_host", 6), ("hobc_deblur_host_async", 6), ("hobc_plan_wait", 1),
@@ -363,6 +370,18 @@ class Plan:
     @property
     def last_launch_count(self) -> int:
         return _lib.hobc_last_launch_count(self._handle)
+
+    @property
+    def gcv_mode(self) -> str:
+        return {v: k for k, v in GCV_MODE.items()}[_lib.hobc_plan_gcv_mode(self._handle)]
+
+    def set_gcv_mode(self, mode: str) -> None:
+        """'direct' (default) or 'expansion' (include/hobc.h, hobc_plan_set_gcv_mode)."""
+        _check(_lib.hobc_plan_set_gcv_mode(self._handle, GCV_MODE[mode]), "hobc_plan_set_gcv_mode")
+
+    @property
+    def gcv_expansion_bound(self) -> float:
+        return _lib.hobc_gcv_expansion_bound(self._handle)
 
     # C ABI calls --------------------------------------------------------------
     def deblur(self, g, psf, f, mu_index=None, gcv=None) -> None:
