@@ -259,6 +259,11 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     plan = hobc.Plan(2, (N_SIDE, N_SIDE), h.shape, 2, mus, L="I", prec=prec, family="fourier", batch=B,
                      stream=stream)
+    # FP32 / split-BF16: the curve by bin expansion (every grid value, within the
+    # stated truncation bound of the term-by-term scan, which is timed below as the
+    # "direct_scan" arm); FP64 plans keep the term-by-term scan
+    if prec != "fp64":
+        plan.set_gcv_mode("expansion")
     g_d = torch.from_numpy(g.astype(npdt)).to(dev)
     h_d = torch.from_numpy(h.astype(npdt)).to(dev)
     f_d = torch.empty_like(g_d)
@@ -326,33 +331,31 @@ def run_ours(args):
         d = (f.cpu().numpy().astype(np.float64) - ft).reshape(B, -1)
         return np.linalg.norm(d, axis=1) / np.linalg.norm(ft.reshape(B, -1), axis=1)
 
-    # the same method with G(mu_j) evaluated by bin expansion (hobc_plan_set_gcv_mode):
-    # every grid value, within the stated truncation bound of the direct scan's curve
-    expansion, f_e, mi_e = None, None, None
-    if prec != "fp64":
-        plan_x = hobc.Plan(2, (N_SIDE, N_SIDE), h.shape, 2, mus, L="I", prec=prec, family="fourier", batch=B,
-                           stream=stream)
-        plan_x.set_gcv_mode("expansion")
-        f_e = torch.empty_like(g_d)
-        mi_e = torch.empty(B, dtype=torch.int32, device=dev)
-        ms_e, clk_e = _timed(lambda: plan_x.deblur(g_d, h_d, f_e, mi_e), stream, args.steps, args.warmup)
-        e_launches = plan_x.last_launch_count
-        ms_e = max_over_ranks(ms_e, dist, dev)
+    # the same method with the curve evaluated term by term (hobc_gcv's direct scan)
+    direct = None
+    f_dir = mi_dir = G_dir = None
+    if plan.gcv_mode == "expansion":
         G_e = torch.empty((B, K_MU), dtype=torch.float64, device=dev)
-        mi_e2 = torch.empty_like(mi_e)
-        ms_eg, _ = _timed(lambda: plan_x.gcv(ghat, dbuf, G_e, mi_e2), stream, args.steps, args.warmup)
+        mi_e = torch.empty(B, dtype=torch.int32, device=dev)
+        plan.gcv(ghat, dbuf, G_e, mi_e)
+        plan.set_gcv_mode("direct")
+        f_dir = torch.empty_like(g_d)
+        mi_dir = torch.empty(B, dtype=torch.int32, device=dev)
+        ms_dir, clk_dir = _timed(lambda: plan.deblur(g_d, h_d, f_dir, mi_dir), stream, args.steps, args.warmup)
+        dir_launches = plan.last_launch_count
+        ms_dir = max_over_ranks(ms_dir, dist, dev)
         G_dir = torch.empty_like(G_e)
-        mi_dir = torch.empty_like(mi_e)
-        plan.gcv(ghat, dbuf, G_dir, mi_dir)
+        mi_d2 = torch.empty_like(mi_e)
+        ms_dg, _ = _timed(lambda: plan.gcv(ghat, dbuf, G_dir, mi_d2), stream, args.steps, args.warmup)
+        plan.set_gcv_mode("expansion")
         torch.cuda.synchronize()
-        r_e = rre(f_e)
-        expansion = {"value": whole_job_rate(world, B, args.steps, ms_e / 1e3), "unit": "deblurs/s",
-                     "ms_per_step": ms_e / args.steps, "gpu_launches": e_launches * args.steps,
-                     "gcv_ms": ms_eg / args.steps, "truncation_bound": plan_x.gcv_expansion_bound,
-                     "G_rel_diff_to_direct_scan_max": float(((G_e - G_dir).abs() / G_dir.abs()).max()),
-                     "index_agreement_with_full_scan": float((mi_e2 == mi_dir).float().mean()),
-                     "rre_mean": {"expansion": float(r_e.mean())}, "clocks": clk_e}
-        plan_x.close()
+        direct = {"value": whole_job_rate(world, B, args.steps, ms_dir / 1e3), "unit": "deblurs/s",
+                  "ms_per_step": ms_dir / args.steps, "gpu_launches": dir_launches * args.steps,
+                  "gcv_ms": ms_dg / args.steps, "clocks": clk_dir,
+                  "expansion_vs_direct": {
+                      "truncation_bound": plan.gcv_expansion_bound,
+                      "G_rel_diff_max": float(((G_e - G_dir).abs() / G_dir.abs()).max()),
+                      "index_agreement": float((mi_e == mi_d2).float().mean())}}
 
     # the grid argmin refined over continuous mu (5 rounds of 9 points in its bracket)
     f_r = torch.empty_like(g_d)
@@ -450,8 +453,8 @@ def run_ours(args):
               "index_agreement_with_full_scan": float((mi_b == mi_d).float().mean()),
               "rre_mean": {"full_scan": float(r_full.mean()), "binned": float(r_bin.mean())},
               "clocks": clk_b}
-    if expansion is not None:
-        expansion["rre_mean"]["full_scan"] = float(r_full.mean())
+    if direct is not None:
+        direct["rre_mean"] = {"direct": float(rre(f_dir).mean()), "expansion": float(r_full.mean())}
 
     # end to end through the host-buffer entry point (pinned host memory)
     g_h = torch.from_numpy(g.astype(npdt)).pin_memory().numpy()
@@ -473,12 +476,12 @@ def run_ours(args):
            "h2d_bytes_per_step": B * N_SIDE * N_SIDE * esz + h.size * esz,
            "d2h_bytes_per_step": B * N_SIDE * N_SIDE * esz + B * 4}
 
-    # roofline of the dominant kernel (the GCV scan): evaluations of
-    # sigma = 1/(a + mu) per launch over the time of the gcv call
+    # roofline of the term-by-term GCV scan (k_gcv_partials + k_gcv_finalize): evaluations
+    # of sigma = 1/(a + mu) per launch over the time of the gcv call in direct mode
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     evals = B * S * K_MU
-    gcv_s = steps_ms["gcv"] / 1e3
+    gcv_s = (direct["gcv_ms"] if direct is not None else steps_ms["gcv"]) / 1e3
     achieved = evals / gcv_s / 1e9
     # the method's arithmetic per evaluation is one division and four FMA-class
     # operations (sigma = s^2/(|d|^2 + mu s^2), the two products and the two sums);
@@ -492,17 +495,48 @@ def run_ours(args):
     # so a launch over B images moves B spectra plus one eigenvalue array
     spec_bytes = S * 2 * esz_of(prec)
     traffic = B * spec_bytes + spec_bytes if prec == "fp32" else None
-    roofline = {"bound": "alu", "kernel": "k_gcv_partials", "achieved": achieved, "peak": peak,
-                "unit": "Geval/s", "frac": achieved / peak, "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read+write of an 8-image launch (37.92 MB), scaled per image",
-                "peak_source": f"derived, not measured: 152 SMs x 128 FP32 lanes / 5 operations per evaluation "
-                               f"(1 division + 4 FMA) x {sm_max:.0f} MHz ({peak_kind} max clock)"}
+    scan_roofline = {"bound": "alu", "kernel": "k_gcv_partials", "achieved": achieved, "peak": peak,
+                     "unit": "Geval/s", "frac": achieved / peak, "traffic": traffic,
+                     "traffic_source": "ncu dram__bytes_read+write of an 8-image launch (37.92 MB), scaled per image",
+                     "peak_source": f"derived, not measured: 152 SMs x 128 FP32 lanes / 5 operations per "
+                                    f"evaluation (1 division + 4 FMA) x {sm_max:.0f} MHz ({peak_kind} max clock)"}
     if prec == "fp64":
         # FP64 scan: 2 FP64 operations per SM-clock on this part (1.25 TFLOP/s), five per evaluation
         peak = 152 * (2 / 5.0) * sm_max * 1e6 / 1e9
-        roofline.update({"peak": peak, "frac": achieved / peak, "traffic": None,
-                         "peak_source": f"derived, not measured: 152 SMs x 2 FP64 operations per clock / 5 "
-                                        f"per evaluation x {sm_max:.0f} MHz ({peak_kind} max clock)"})
+        scan_roofline.update({"peak": peak, "frac": achieved / peak, "traffic": None,
+                              "peak_source": f"derived, not measured: 152 SMs x 2 FP64 operations per clock / "
+                                             f"5 per evaluation x {sm_max:.0f} MHz ({peak_kind} max clock)"})
+    # the headline step's dominant call: with the direct scan the scan; with the
+    # expansion a transform pass (its row and column kernels), bound by HBM by the
+    # method's bytes (the spectrum in or out, the image out or in, per image)
+    dom = max(("analysis", "filter_synthesis", "gcv"), key=lambda k: steps_ms[k])
+    if dom == "gcv":
+        roofline = dict(scan_roofline)
+    else:
+        esz = np.dtype(npdt).itemsize
+        call_bytes = B * (S * 2 * esz_of(prec) + N_SIDE * N_SIDE * esz) + (S * 2 * esz_of(prec) if
+                                                                          dom == "filter_synthesis" else 0)
+        t_call = steps_ms[dom] / 1e3
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        flops = B * 2.5 * N_SIDE * N_SIDE * np.log2(float(N_SIDE * N_SIDE))   # one 2D transform per image
+        fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+        # DRAM traffic of the two kernels of each call, ncu on the 8-image case (FP32):
+        # filter + synthesis 38.01 + 0.78 + 33.79 + 0.44 MB, analysis 33.67 + 1.28 + 33.80 + 0.18 MB
+        per_img = {"filter_synthesis": 73.02e6 / 8, "analysis": 68.93e6 / 8}[dom]
+        roofline = {"bound": "hbm", "kernel": ("k_cplx_synthesis + k_pair_synthesis (filter + synthesis call)"
+                                               if dom == "filter_synthesis" else
+                                               "k_pair_analysis + k_cplx_analysis (analysis call)"),
+                    "achieved": call_bytes / t_call / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": call_bytes / t_call / 1e9 / hbm_peak,
+                    "traffic": B * per_img if prec == "fp32" else None,
+                    "traffic_source": "ncu dram__bytes_read+write of the two kernels on the 8-image case, "
+                                      "scaled per image",
+                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+                    "bytes_per_launch": call_bytes,
+                    "alu_view": {"flops_per_launch": flops, "achieved_tflops": flops / t_call / 1e12,
+                                 "fp32_peak_tflops": fp32_peak, "frac": flops / t_call / 1e12 / fp32_peak,
+                                 "flops_source": "2.5 N^2 log2(N^2) per 2D transform per image; FP32 peak "
+                                                 "derived, not measured: 152 SMs x 128 lanes x 2 x max clock"}}
     transform_roofline = None
     if prec == "split_bf16":
         # the four transform products of a step on the tensor cores (real form of the
@@ -540,7 +574,7 @@ def run_ours(args):
         cpu["single_core"] = {"value": (1.0 / sec1) if sec1 else None, "unit": "deblurs/s", "cores": 1,
                               "sample": "1 image of the same workload, one BLAS thread"}
         oracle_error = default_oracle_error(kept, h, mus, f_d, mi_d, G_grid, f_b, mi_b, f_r, mu_r, G_ref,
-                                            f_x, mi_x, G_x, f_xs, mi_xs, f_e, mi_e)
+                                            f_x, mi_x, G_x, f_xs, mi_xs, f_dir, mi_dir)
 
     if rank == 0:
         line = {
@@ -551,10 +585,10 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "batch_per_gpu": B, "n": N_SIDE, "n_mu": K_MU,
                        "l2": "inputs+outputs %.0f MB per step > 129 MB L2 (no flush)" % (2 * B * N_SIDE ** 2 * esz / 1e6)},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
+            "gcv_mode": plan.gcv_mode, "direct_scan": direct, "scan_roofline": scan_roofline,
             "hbm_roofline": hbm, "steps_ms": steps_ms, "cpu_baseline": cpu, "clocks": clocks,
             "learned_mu": learned_arm,
             "binned_mu": binned, "refined_mu": refined, "exact_gcv": exact, "exact_gcv_search": exact_search,
-            "gcv_expansion": expansion,
             "oracle_error": oracle_error, "precision": prec, "transform_roofline": transform_roofline,
         }
         print(json.dumps(line), flush=True)
@@ -575,7 +609,7 @@ def G_xs_probe(plan, g_d, h_d, B):
 
 
 def default_oracle_error(kept, h, mus, f_d, mi_d, G_grid, f_b, mi_b, f_r, mu_r, G_ref, f_x, mi_x, G_x, f_xs,
-                         mi_xs, f_e=None, mi_e=None):
+                         mi_xs, f_dir=None, mi_dir=None):
     """Error of every arm of the 1024^2 line against the FP64 oracle on the images
     the CPU baseline ran: f in relative 2-norm at the mu the arm chose (the oracle
     filters its own spectrum at that mu), and G where the arm reports one."""
@@ -604,9 +638,9 @@ def default_oracle_error(kept, h, mus, f_d, mi_d, G_grid, f_b, mi_b, f_r, mu_r, 
         arms["refined_mu"].append(rel2(fs["refined"][i], oracle_f_2d("F", h, ghat, "I", float(mr[i]))))
         arms["exact_gcv"].append(rel2(fs["exact"][i], f_at_index(int(ks["exact"][i]))))
         arms["exact_gcv_search"].append(rel2(fs["search"][i], f_at_index(int(ks["search"][i]))))
-        if f_e is not None:
-            ke = int(mi_e.cpu().numpy()[i])
-            arms.setdefault("gcv_expansion", []).append(rel2(f_e.cpu().numpy()[i], f_at_index(ke)))
+        if f_dir is not None:
+            ke = int(mi_dir.cpu().numpy()[i])
+            arms.setdefault("direct_scan", []).append(rel2(f_dir.cpu().numpy()[i], f_at_index(ke)))
             agree_e.append(ke == int(k_o))
         g_err.append(float(np.max(np.abs(Gg[i] - G_o) / G_o)))
         agree.append(int(ks["full"][i]) == int(k_o))
@@ -621,9 +655,9 @@ def default_oracle_error(kept, h, mus, f_d, mi_d, G_grid, f_b, mi_b, f_r, mu_r, 
     out["refined_mu"] = {"f_rel_2norm_max": max(arms["refined_mu"]), "G_rel_at_mu_max": float(max(g_ref_err))}
     out["exact_gcv"] = {"f_rel_2norm_max": max(arms["exact_gcv"]), "G_rel_at_mu_max": float(max(g_ex_err))}
     out["exact_gcv_search"] = {"f_rel_2norm_max": max(arms["exact_gcv_search"])}
-    if f_e is not None:
-        out["gcv_expansion"] = {"f_rel_2norm_max": max(arms["gcv_expansion"]),
-                                "mu_index_agreement": float(np.mean(agree_e))}
+    if f_dir is not None:
+        out["direct_scan"] = {"f_rel_2norm_max": max(arms["direct_scan"]),
+                              "mu_index_agreement": float(np.mean(agree_e))}
     return out
 
 
@@ -1046,6 +1080,35 @@ def run_learned(args):
     return 0
 
 
+def run_plain(args):
+    """The headline workload's step alone (one plan, hobc_deblur on the 1024^2 batch,
+    no other arm, no CPU baseline): the command the kernel profiles use."""
+    import torch
+    from paper_0906_2704_gb300 import hobc, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    B, prec = args.batch, args.prec
+    npdt = np.float64 if prec == "fp64" else np.float32
+    h, g, _ = make_inputs(B, seed=rank_seed(0))
+    stream = torch.cuda.current_stream()
+    plan = hobc.Plan(2, (N_SIDE, N_SIDE), h.shape, 2, synth.mu_grid(K_MU), L="I", prec=prec, family="fourier",
+                     batch=B, stream=stream)
+    if prec != "fp64" and not args.direct:
+        plan.set_gcv_mode("expansion")
+    g_d = torch.from_numpy(g.astype(npdt)).to(dev)
+    h_d = torch.from_numpy(h.astype(npdt)).to(dev)
+    f_d = torch.empty_like(g_d)
+    mi_d = torch.empty(B, dtype=torch.int32, device=dev)
+    ms, clocks = _timed(lambda: plan.deblur(g_d, h_d, f_d, mi_d), stream, args.steps, args.warmup)
+    line = {"metric": f"{WORKLOAD} deblurs/s (the step alone)", "value": B * args.steps / (ms / 1e3),
+            "unit": "deblurs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "gcv_mode": plan.gcv_mode,
+            "gpu_launches": plan.last_launch_count * args.steps, "batch": B, "precision": prec, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
 def run_bccompare(args):
     """The paper's comparison of boundary conditions (its 2D out-of-focus experiment) on
     synthetic images: RRE at the RRE-optimal grid mu, at the GCV mu (the paper's
@@ -1186,7 +1249,10 @@ def main():
     ap.add_argument("--prec", choices=["fp32", "fp64", "split_bf16"], default="fp32")
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["fourier1024", "batched", "signals1d", "cosine512", "cosine1024",
+    ap.add_argument("--direct", action="store_true",
+                    help="fourier1024_step: the term-by-term GCV scan instead of the expansion")
+    ap.add_argument("--workload", choices=["fourier1024", "fourier1024_step", "batched", "signals1d", "cosine512",
+                                           "cosine1024",
                                            "learned", "bccompare", "volume128"],
                     default="fourier1024")
     ap.add_argument("--train", type=int, default=200000, help="training problems of the learned workload")
@@ -1207,6 +1273,8 @@ def main():
         return run_learned(args)
     if args.workload == "bccompare":
         return run_bccompare(args)
+    if args.workload == "fourier1024_step":
+        return run_plain(args)
     if args.workload != "fourier1024":
         return run_other(args)
     return run_ours(args)

@@ -21,10 +21,11 @@
 //
 // Per call: a key pass (bin and u of every entry, from the eigenvalues), a
 // stable counting sort of the entries by bin, the moments of every piece of at
-// most 256 entries of one bin (a warp each, FP32, fixed order), and per problem
-// the sum of the pieces' moments (FP64, piece order), the curve (Horner in FP32,
-// float-float sums over the bins) and its first minimum.  Every step runs in a
-// fixed order: the result does not depend on scheduling.
+// most 256 entries of one bin (a warp each, FP32, fixed order), per key and
+// problem the sum of its pieces' moments (FP64, fixed order), the curve (Horner
+// in FP32, float-float sums over the bins; a CTA per 32 grid values and
+// problem) and each problem's first minimum.  Every step runs in a fixed order: the result does not depend on
+// scheduling.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -41,6 +42,7 @@ static const int kGxKeys = kGxBins + 2;       // key 0: a < a_lo; 1..256 inner; 
 static const int kGxP = 8;                    // moments p = 0..7
 static const int kGxChunk = 1024;             // entries per CTA of the key and scatter passes
 static const int kGxPiece = 256;              // entries per piece (one warp)
+static const int kGxIpw = 4;                  // problems per warp of the moments pass
 
 struct GxTab {                                // bin geometry (device copy)
     float abar[kGxBins];                      // bin centres a_lo r^(b + 1/2)
@@ -62,18 +64,35 @@ struct hobc_gcvx_s {
     float* s_u;
     float* s_sn;
     float* s_sd;
-    int* counts;             // [chunks][keys] entries per chunk and key, then their offsets
+    int* counts;             // [keys][chunks] entries per key and chunk, then their prefix within the key
+    int* tot;                // [keys] entries per key
+    int* key_start;          // [keys] first sorted position of each key
+    float2* gmom;            // [batch + 1][max_groups][8] moments per piece group, float-float (numerators, then the denominator's)
+    float2* kmom;            // [batch + 1][keys][8] moments per key, float-float
+    double* G_ws;            // [batch][K] the curve
+    int4* groups;            // [max_groups] first piece, pieces, key
+    int* key_group0;         // [keys + 1] first group of each key; [keys] = number of groups
+    unsigned* done;          // [1 + batch] completion counters (chunk scan, then one per problem's curve)
     int4* pieces;            // [max_pieces] start, length, key
     int* key_piece0;         // [keys + 1] first piece of each key; [keys] = number of pieces
     float* num_part;         // [batch][max_pieces][8]
     float* den_part;         // [max_pieces][8]
-    int chunks, max_pieces;
+    int chunks, max_pieces, max_groups;
     double bound;            // truncation bound of the series (relative, per term)
 };
 
 namespace hobc {
 
 namespace {
+
+// float-float accumulation: hi + lo += x, with the rounding error of hi + x kept
+// in lo (TwoSum; the _rn intrinsics keep the compiler from fusing or reordering)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bv = __fsub_rn(s, hi);
+    lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(x, bv));
+    hi = s;
+}
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -127,45 +146,119 @@ k_gx_keys(const typename ElemT<float, CPLX>::t* __restrict__ D, GcvGeom geo, con
         key[i] = k; u[i] = uu; sn[i] = vn; sd[i] = vd;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kGxKeys; k += blockDim.x) counts[(long long)blockIdx.x * kGxKeys + k] = hist[k];
+    for (int k = threadIdx.x; k < kGxKeys; k += blockDim.x) counts[(long long)k * gridDim.x + blockIdx.x] = hist[k];
 }
 
-// Offsets of the stable counting sort (key-major, then chunk order) and the
-// pieces: each key's range cut into pieces of at most kGxPiece entries.
-// One CTA of 1024 threads.
-__global__ void __launch_bounds__(1024)
-k_gx_scan(int* __restrict__ counts, int chunks, int4* __restrict__ pieces, int* __restrict__ key_piece0) {
-    __shared__ int tot[kGxKeys], start[kGxKeys], pstart[kGxKeys + 1];
-    const int k = threadIdx.x;
-    if (k < kGxKeys) {
-        int t = 0;
-        for (int c = 0; c < chunks; ++c) t += counts[(long long)c * kGxKeys + k];
-        tot[k] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0, prun = 0;
-        for (int j = 0; j < kGxKeys; ++j) {
-            start[j] = run;
-            pstart[j] = prun;
-            run += tot[j];
-            prun += (tot[j] + kGxPiece - 1) / kGxPiece;
+// Start of every key in the sorted order, its pieces (its range cut into
+// pieces of at most kGxPiece entries) and its piece groups (at most 32 pieces
+// each), from the key totals.  Run by one CTA of 256 threads.
+__device__ void gx_scan_body(const int* __restrict__ tot, int* __restrict__ key_start, int4* __restrict__ pieces,
+                             int* __restrict__ key_piece0, int4* __restrict__ groups, int* __restrict__ key_group0) {
+    __shared__ int st[kGxKeys], tt[kGxKeys], ps[kGxKeys + 1], gs[kGxKeys + 1];
+    __shared__ int wsum[8][3];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // thread t holds keys 2t, 2t + 1 (129 threads): entries, pieces and groups,
+    // then an exclusive scan over the threads (warp shuffles, then the warp totals)
+    int e[2] = {0, 0}, pc[2] = {0, 0}, gc[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (2 * t + h < kGxKeys) {
+            e[h] = __ldcg(tot + 2 * t + h);
+            pc[h] = (e[h] + kGxPiece - 1) / kGxPiece;
+            gc[h] = (pc[h] + 31) / 32;
+            tt[2 * t + h] = e[h];
         }
-        pstart[kGxKeys] = prun;
-    }
-    __syncthreads();
-    if (k < kGxKeys) {
-        int run = start[k];
-        for (int c = 0; c < chunks; ++c) {
-            const long long o = (long long)c * kGxKeys + k;
-            const int t = counts[o];
-            counts[o] = run;
-            run += t;
+    int x[3] = {e[0] + e[1], pc[0] + pc[1], gc[0] + gc[1]};
+    const int own[3] = {x[0], x[1], x[2]};
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const int y = __shfl_up_sync(0xffffffffu, x[v], off);
+            if (lane >= off) x[v] += y;
         }
-        for (int q = 0; q * kGxPiece < tot[k]; ++q)
-            pieces[pstart[k] + q] = make_int4(start[k] + q * kGxPiece, min(kGxPiece, tot[k] - q * kGxPiece), k, 0);
+    if (lane == 31)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) wsum[warp][v] = x[v];
+    __syncthreads();
+    int ex[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        int base = 0;
+        for (int w = 0; w < warp; ++w) base += wsum[w][v];
+        ex[v] = base + x[v] - own[v];
     }
-    if (k <= kGxKeys) key_piece0[k] = pstart[k];
+    if (2 * t < kGxKeys) { st[2 * t] = ex[0]; ps[2 * t] = ex[1]; gs[2 * t] = ex[2]; }
+    if (2 * t + 1 < kGxKeys) { st[2 * t + 1] = ex[0] + e[0]; ps[2 * t + 1] = ex[1] + pc[0]; gs[2 * t + 1] = ex[2] + gc[0]; }
+    if (2 * t + 1 == kGxKeys - 1) { ps[kGxKeys] = ex[1] + own[1]; gs[kGxKeys] = ex[2] + own[2]; }
+    __syncthreads();
+    for (int k = t; k < kGxKeys; k += blockDim.x) key_start[k] = st[k];
+    for (int k = t; k <= kGxKeys; k += blockDim.x) { key_piece0[k] = ps[k]; key_group0[k] = gs[k]; }
+    for (int q = t; q < ps[kGxKeys]; q += blockDim.x) {
+        int lo = 0, hi = kGxKeys - 1;               // the key whose pieces hold q
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (ps[mid] <= q) lo = mid; else hi = mid - 1;
+        }
+        const int r = q - ps[lo];
+        pieces[q] = make_int4(st[lo] + r * kGxPiece, min(kGxPiece, tt[lo] - r * kGxPiece), lo, 0);
+    }
+    for (int g = t; g < gs[kGxKeys]; g += blockDim.x) {
+        int lo = 0, hi = kGxKeys - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (gs[mid] <= g) lo = mid; else hi = mid - 1;
+        }
+        const int r = g - gs[lo];
+        const int q0 = ps[lo] + 32 * r;
+        groups[g] = make_int4(q0, min(32, ps[lo + 1] - q0), lo, 0);
+    }
+}
+
+// Per key, the exclusive prefix of its counts over the chunks (in place) and
+// its total: one warp per key.  The CTA that
+// finishes last (a counter, reset by it) then runs gx_scan_body.
+__global__ void __launch_bounds__(256)
+k_gx_chunkscan(int* __restrict__ counts, int chunks, int* __restrict__ tot, unsigned* __restrict__ done,
+               int* __restrict__ key_start, int4* __restrict__ pieces, int* __restrict__ key_piece0,
+               int4* __restrict__ groups, int* __restrict__ key_group0) {
+    __shared__ bool last;
+    const int k = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (k < kGxKeys) {
+        // tiles of 1024 chunks: lane l holds chunks 32 l .. 32 l + 31 of the tile
+        // (loaded together), its own running sum, then a scan over the lanes
+        int run = 0;
+        int* row = counts + (long long)k * chunks;
+        for (int t0 = 0; t0 < chunks; t0 += 1024) {
+            int v[32];
+            const int c0 = t0 + 32 * lane;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = c0 + i < chunks ? row[c0 + i] : 0;
+            int own = 0;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) { const int t = v[i]; v[i] = own; own += t; }
+            int x = own;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, off);
+                if (lane >= off) x += y;
+            }
+            const int base = run + x - own;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                if (c0 + i < chunks) row[c0 + i] = base + v[i];
+            run += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) tot[k] = run;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    gx_scan_body(tot, key_start, pieces, key_piece0, groups, key_group0);
+    if (threadIdx.x == 0) *done = 0;
 }
 
 // Stable scatter into key order: warp w of a chunk owns entries
@@ -173,7 +266,8 @@ k_gx_scan(int* __restrict__ counts, int chunks, int4* __restrict__ pieces, int* 
 // (ranks from the lanes below with the same key, then a per-warp running count).
 __global__ void __launch_bounds__(256)
 k_gx_scatter(long long S, const int* __restrict__ key, const float* __restrict__ u, const float* __restrict__ sn,
-             const float* __restrict__ sd, const int* __restrict__ offs, int* __restrict__ s_idx,
+             const float* __restrict__ sd, const int* __restrict__ offs, const int* __restrict__ key_start,
+             int* __restrict__ s_idx,
              float* __restrict__ s_u, float* __restrict__ s_sn, float* __restrict__ s_sd) {
     __shared__ int wc[8][kGxKeys];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -197,13 +291,14 @@ k_gx_scatter(long long S, const int* __restrict__ key, const float* __restrict__
         }
     }
     __syncthreads();
-    const int* off = offs + (long long)blockIdx.x * kGxKeys;
+    const int* off = offs + blockIdx.x;          // offs[k * chunks + chunk]
+    const long long kstride = gridDim.x;
     for (int it = 0; it < kGxChunk / 8 / 32; ++it) {
         const long long i = base + it * 32 + lane;
         const int k = i < S ? key[i] : -1;
         const unsigned peers = __match_any_sync(0xffffffffu, k);
         if (k >= 0) {
-            const int pos = off[k] + wc[warp][k] + __popc(peers & lanemask_lt());
+            const int pos = key_start[k] + off[k * kstride] + wc[warp][k] + __popc(peers & lanemask_lt());
             s_idx[pos] = (int)i;
             s_u[pos] = u[i];
             s_sn[pos] = sn[i];
@@ -216,106 +311,220 @@ k_gx_scatter(long long S, const int* __restrict__ key, const float* __restrict__
 }
 
 // Moments sum_j v_j u_j^p, p = 0..7, of every piece: one warp per piece, each
-// lane at most 8 entries in order, then a fixed shuffle tree.  NUM: v = sn |ghat|^2
-// of problem blockIdx.y; else v = sd.
-template <bool NUM, bool CPLX>
-__global__ void __launch_bounds__(256)
+// lane at most 8 entries (held in registers across the kGxIpw problems of grid
+// row y), summed in entry order, then a fixed shuffle tree.  Rows before the last:
+// v = sn |ghat|^2 of each problem in turn; the last row: v = sd.
+template <bool CPLX>
+__global__ void __launch_bounds__(256, 5)
 k_gx_moments(const int4* __restrict__ pieces, const int* __restrict__ npieces, const int* __restrict__ s_idx,
-             const float* __restrict__ s_u, const float* __restrict__ s_v,
-             const typename ElemT<float, CPLX>::t* __restrict__ ghat, long long S, int max_pieces,
-             float* __restrict__ part) {
+             const float* __restrict__ s_u, const float* __restrict__ s_sn, const float* __restrict__ s_sd,
+             const typename ElemT<float, CPLX>::t* __restrict__ ghat, long long S, int items,
+             int max_pieces, float* __restrict__ num_part, float* __restrict__ den_part) {
+    constexpr int E = kGxPiece / 32;
     const int q = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (q >= *npieces) return;
-    const long long item = blockIdx.y;
+    const bool NUM = (int)blockIdx.y < (int)gridDim.y - 1;       // the last row: the denominator's moments
+    const float* s_v = NUM ? s_sn : s_sd;
+    float* part = NUM ? num_part : den_part;
     const int4 pc = pieces[q];
-    float m[kGxP];
+    int id[E];
+    float uu[E], vv[E];
 #pragma unroll
-    for (int p = 0; p < kGxP; ++p) m[p] = 0.f;
-    for (int j = pc.x + lane; j < pc.x + pc.y; j += 32) {
-        float t = s_v[j];
-        if (NUM) t *= abs2_of(ghat[item * S + s_idx[j]]);
-        const float uu = s_u[j];
+    for (int m = 0; m < E; ++m) {
+        const int j = pc.x + lane + 32 * m;
+        const bool in = lane + 32 * m < pc.y;
+        id[m] = in ? (NUM ? s_idx[j] : 0) : -1;
+        uu[m] = in ? s_u[j] : 0.f;
+        vv[m] = in ? s_v[j] : 0.f;
+    }
+    const int item0 = NUM ? blockIdx.y * kGxIpw : 0;
+    const int nit = NUM ? min(items - item0, kGxIpw) : 1;
+    for (int it = 0; it < nit; ++it) {
+        const int item = item0 + it;
+        float g2[E];
 #pragma unroll
-        for (int p = 0; p < kGxP; ++p) {
-            m[p] += t;
-            t *= uu;
+        for (int m = 0; m < E; ++m)
+            g2[m] = (NUM && id[m] >= 0) ? abs2_of(ghat[(long long)item * S + id[m]]) : 1.f;
+        float mo[kGxP];
+#pragma unroll
+        for (int p = 0; p < kGxP; ++p) mo[p] = 0.f;
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            float t = vv[m] * g2[m];
+#pragma unroll
+            for (int p = 0; p < kGxP; ++p) {
+                mo[p] += t;
+                t *= uu[m];
+            }
         }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int p = 0; p < kGxP; ++p) mo[p] += __shfl_down_sync(0xffffffffu, mo[p], off);
+        if (lane == 0) {
+            float4* o = reinterpret_cast<float4*>(part + ((long long)item * max_pieces + q) * kGxP);
+            o[0] = make_float4(mo[0], mo[1], mo[2], mo[3]);
+            o[1] = make_float4(mo[4], mo[5], mo[6], mo[7]);
+        }
+    }
+}
+
+// The moments of every piece group: the sum over its (at most 32) pieces in
+// float-float, lane l taking piece l, then a fixed shuffle tree.  Grid y <
+// batch: the numerator moments of problem y; y = batch: the denominator's.
+__global__ void __launch_bounds__(256)
+k_gx_reduce(const float* __restrict__ num_part, const float* __restrict__ den_part, const int4* __restrict__ groups,
+            const int* __restrict__ ngroups, int batch, int max_pieces, int max_groups, float2* __restrict__ gmom) {
+    const int g = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31, y = blockIdx.y;
+    if (g >= *ngroups) return;
+    const int4 gr = groups[g];
+    const float* src = y < batch ? num_part + (long long)y * max_pieces * kGxP : den_part;
+    float hi[kGxP], lo[kGxP];
+#pragma unroll
+    for (int p = 0; p < kGxP; ++p) { hi[p] = 0.f; lo[p] = 0.f; }
+    if (lane < gr.y) {
+        const float4 a = reinterpret_cast<const float4*>(src + (long long)(gr.x + lane) * kGxP)[0];
+        const float4 b = reinterpret_cast<const float4*>(src + (long long)(gr.x + lane) * kGxP)[1];
+        hi[0] = a.x; hi[1] = a.y; hi[2] = a.z; hi[3] = a.w;
+        hi[4] = b.x; hi[5] = b.y; hi[6] = b.z; hi[7] = b.w;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-        for (int p = 0; p < kGxP; ++p) m[p] += __shfl_down_sync(0xffffffffu, m[p], off);
-    if (lane == 0) {
-        float4* o = reinterpret_cast<float4*>(part + ((long long)item * max_pieces + q) * kGxP);
-        o[0] = make_float4(m[0], m[1], m[2], m[3]);
-        o[1] = make_float4(m[4], m[5], m[6], m[7]);
-    }
+        for (int p = 0; p < kGxP; ++p) {
+            const float oh = __shfl_down_sync(0xffffffffu, hi[p], off);
+            const float ol = __shfl_down_sync(0xffffffffu, lo[p], off);
+            two_sum_acc(hi[p], lo[p], oh);
+            lo[p] += ol;
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int p = 0; p < kGxP; ++p) gmom[((long long)y * max_groups + g) * kGxP + p] = make_float2(hi[p], lo[p]);
 }
 
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
-    const float s = __fadd_rn(hi, x);
-    const float bv = __fsub_rn(s, hi);
-    lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(x, bv));
-    hi = s;
-}
-
-// Per problem: the moments of every key (FP64 over its pieces, in order), the
-// curve G(mu_j) and its first minimum (NaN never wins).  One CTA per problem.
+// The moments of every key: the sum over its groups in float-float, lane l
+// taking groups l, l + 32, ... in order, then a fixed shuffle tree.  Grid y as
+// for k_gx_reduce.
 __global__ void __launch_bounds__(256)
-k_gx_finalize(const float* __restrict__ num_part, const float* __restrict__ den_part,
-              const int* __restrict__ key_piece0, const GxTab* __restrict__ tab, const double* __restrict__ mu,
-              int K, int max_pieces, double* __restrict__ gcv, int* __restrict__ mu_idx) {
+k_gx_keysum(const float2* __restrict__ gmom, const int* __restrict__ key_group0, int max_groups,
+            float2* __restrict__ kmom) {
+    const int k = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31, y = blockIdx.y;
+    if (k >= kGxKeys) return;
+    const int g0 = key_group0[k], g1 = key_group0[k + 1];
+    float hi[kGxP], lo[kGxP];
+#pragma unroll
+    for (int p = 0; p < kGxP; ++p) { hi[p] = 0.f; lo[p] = 0.f; }
+    for (int g = g0 + lane; g < g1; g += 32)
+#pragma unroll
+        for (int p = 0; p < kGxP; ++p) {
+            const float2 v = gmom[((long long)y * max_groups + g) * kGxP + p];
+            two_sum_acc(hi[p], lo[p], v.x);
+            lo[p] += v.y;
+        }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int p = 0; p < kGxP; ++p) {
+            const float oh = __shfl_down_sync(0xffffffffu, hi[p], off);
+            const float ol = __shfl_down_sync(0xffffffffu, lo[p], off);
+            two_sum_acc(hi[p], lo[p], oh);
+            lo[p] += ol;
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int p = 0; p < kGxP; ++p) kmom[((long long)y * kGxKeys + k) * kGxP + p] = make_float2(hi[p], lo[p]);
+}
+
+// The curve: block (mu group of 32, problem), from the moments of every key; thread (slice, j) sums the keys slice, slice + 8,
+// ... at grid value j (Horner in FP32, float-float sums), and the 8 slices are
+// added in order; G = num / den^2 in double.  The CTA that completes a problem's
+// curve last takes its first minimum (NaN never wins).
+__global__ void __launch_bounds__(256)
+k_gx_curve(const float2* __restrict__ kmom, int batch, const int* __restrict__ key_group0,
+           const GxTab* __restrict__ tab, const double* __restrict__ mu, int K, double* __restrict__ G_ws,
+           double* __restrict__ gcv, unsigned* __restrict__ done, int* __restrict__ mu_idx) {
     __shared__ float Ec[kGxKeys][kGxP];     // (p + 1) E_p
     __shared__ float Wc[kGxKeys][kGxP];
-    __shared__ int kp0[kGxKeys + 1];
+    __shared__ int nonempty[kGxKeys];
+    __shared__ float red[4][8][32];
+    const long long item = blockIdx.y;
+    constexpr int kLoads = (kGxKeys * kGxP + 255) / 256;
+    float2 va[kLoads], vb[kLoads];              // all loads first (the block has 256 threads)
+#pragma unroll
+    for (int i = 0; i < kLoads; ++i) {
+        const int kp = threadIdx.x + 256 * i;
+        if (kp < kGxKeys * kGxP) {
+            va[i] = kmom[item * kGxKeys * kGxP + kp];
+            vb[i] = kmom[(long long)batch * kGxKeys * kGxP + kp];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kLoads; ++i) {
+        const int kp = threadIdx.x + 256 * i;
+        if (kp < kGxKeys * kGxP) {
+            (&Ec[0][0])[kp] = (va[i].x + va[i].y) * (float)(kp % kGxP + 1);
+            (&Wc[0][0])[kp] = vb[i].x + vb[i].y;
+        }
+    }
+    for (int k = threadIdx.x; k < kGxKeys; k += blockDim.x) nonempty[k] = key_group0[k] != key_group0[k + 1];
+    __syncthreads();
+    const int jl = threadIdx.x & 31, slice = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + jl;
+    const float m = j < K ? (float)mu[j] : 1.f;
+    const float a_lo = tab->a_lo, a_hi = tab->a_hi;
+    float nh = 0, nl = 0, dh = 0, dl = 0;
+    for (int k = slice; k < kGxKeys; k += 8) {
+        if (!nonempty[k]) continue;
+        float x, sn_, sd_;
+        if (k == 0) {
+            const float inv = __fdividef(1.f, m);
+            x = -a_lo * inv; sn_ = inv * inv; sd_ = inv;
+        } else if (k == kGxKeys - 1) {
+            x = -m / a_hi; sn_ = 1.f; sd_ = 1.f;
+        } else {
+            const float ab = tab->abar[k - 1];
+            const float inv = __fdividef(1.f, ab + m);
+            x = -ab * inv; sn_ = inv * inv; sd_ = inv;
+        }
+        float hn = Ec[k][kGxP - 1], hd = Wc[k][kGxP - 1];
+#pragma unroll
+        for (int p = kGxP - 2; p >= 0; --p) {
+            hn = fmaf(hn, x, Ec[k][p]);
+            hd = fmaf(hd, x, Wc[k][p]);
+        }
+        two_sum_acc(nh, nl, hn * sn_);
+        two_sum_acc(dh, dl, hd * sd_);
+    }
+    red[0][slice][jl] = nh; red[1][slice][jl] = nl; red[2][slice][jl] = dh; red[3][slice][jl] = dl;
+    __syncthreads();
+    if (slice == 0 && j < K) {
+        float ah = 0, al = 0, bh = 0, bl = 0;
+        for (int sl = 0; sl < 8; ++sl) {
+            two_sum_acc(ah, al, red[0][sl][jl]);
+            al += red[1][sl][jl];
+            two_sum_acc(bh, bl, red[2][sl][jl]);
+            bl += red[3][sl][jl];
+        }
+        const double den = (double)bh + (double)bl;
+        const double Gj = ((double)ah + (double)al) / (den * den);
+        G_ws[item * K + j] = Gj;
+        if (gcv) gcv[item * K + j] = Gj;
+    }
+    // the CTA that finishes this problem's curve last takes its first minimum
+    __shared__ bool last;
     __shared__ double rbest[256];
     __shared__ int ridx[256];
-    const long long item = blockIdx.x;
-    for (int k = threadIdx.x; k <= kGxKeys; k += blockDim.x) kp0[k] = key_piece0[k];
+    __threadfence();
     __syncthreads();
-    for (int kp = threadIdx.x; kp < kGxKeys * kGxP; kp += blockDim.x) {
-        const int k = kp / kGxP, p = kp - k * kGxP;
-        double se = 0, sw = 0;
-        for (int q = kp0[k]; q < kp0[k + 1]; ++q) {
-            se += (double)num_part[((long long)item * max_pieces + q) * kGxP + p];
-            sw += (double)den_part[(long long)q * kGxP + p];
-        }
-        Ec[k][p] = (float)(se * (p + 1));
-        Wc[k][p] = (float)sw;
-    }
+    if (threadIdx.x == 0) last = atomicAdd(done + item, 1u) == gridDim.x - 1;
     __syncthreads();
-    const float a_lo = tab->a_lo, a_hi = tab->a_hi;
+    if (!last) return;
+    __threadfence();
     double best = 0;
     int bi = 0x7fffffff;
-    for (int j = threadIdx.x; j < K; j += blockDim.x) {
-        const float m = (float)mu[j];
-        float nh = 0, nl = 0, dh = 0, dl = 0;
-        for (int k = 0; k < kGxKeys; ++k) {
-            if (kp0[k] == kp0[k + 1]) continue;
-            float x, sn_, sd_;
-            if (k == 0) {
-                const float inv = 1.f / m;
-                x = -a_lo * inv; sn_ = inv * inv; sd_ = inv;
-            } else if (k == kGxKeys - 1) {
-                x = -m / a_hi; sn_ = 1.f; sd_ = 1.f;
-            } else {
-                const float ab = tab->abar[k - 1];
-                const float inv = 1.f / (ab + m);
-                x = -ab * inv; sn_ = inv * inv; sd_ = inv;
-            }
-            float hn = Ec[k][kGxP - 1], hd = Wc[k][kGxP - 1];
-#pragma unroll
-            for (int p = kGxP - 2; p >= 0; --p) {
-                hn = fmaf(hn, x, Ec[k][p]);
-                hd = fmaf(hd, x, Wc[k][p]);
-            }
-            two_sum_acc(nh, nl, hn * sn_);
-            two_sum_acc(dh, dl, hd * sd_);
-        }
-        const double den = (double)dh + (double)dl;
-        const double G = ((double)nh + (double)nl) / (den * den);
-        if (gcv) gcv[item * K + j] = G;
-        if (!isnan(G) && (bi == 0x7fffffff || G < best)) { best = G; bi = j; }
+    for (int jj = threadIdx.x; jj < K; jj += blockDim.x) {
+        const double G = __ldcg(G_ws + item * K + jj);
+        if (!isnan(G) && (bi == 0x7fffffff || G < best)) { best = G; bi = jj; }
     }
     rbest[threadIdx.x] = best;
     ridx[threadIdx.x] = bi;
@@ -333,7 +542,10 @@ k_gx_finalize(const float* __restrict__ num_part, const float* __restrict__ den_
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) mu_idx[item] = ridx[0] == 0x7fffffff ? 0 : ridx[0];
+    if (threadIdx.x == 0) {
+        mu_idx[item] = ridx[0] == 0x7fffffff ? 0 : ridx[0];
+        done[item] = 0;
+    }
 }
 
 }  // namespace
@@ -343,7 +555,8 @@ void gcvx_free(hobc_plan_s* p) {
     if (!x) return;
     cudaFree(x->tab); cudaFree(x->key); cudaFree(x->u); cudaFree(x->sn); cudaFree(x->sd);
     cudaFree(x->s_idx); cudaFree(x->s_u); cudaFree(x->s_sn); cudaFree(x->s_sd);
-    cudaFree(x->counts); cudaFree(x->pieces); cudaFree(x->key_piece0); cudaFree(x->num_part); cudaFree(x->den_part);
+    cudaFree(x->counts); cudaFree(x->tot); cudaFree(x->key_start); cudaFree(x->gmom); cudaFree(x->kmom); cudaFree(x->G_ws); cudaFree(x->groups);
+    cudaFree(x->key_group0); cudaFree(x->done); cudaFree(x->pieces); cudaFree(x->key_piece0); cudaFree(x->num_part); cudaFree(x->den_part);
     delete x;
     p->gx = nullptr;
 }
@@ -405,6 +618,16 @@ static hobc_status gcvx_prepare(hobc_plan_s* p) {
     alloc((void**)&x->s_sn, S * sizeof(float));
     alloc((void**)&x->s_sd, S * sizeof(float));
     alloc((void**)&x->counts, (size_t)x->chunks * kGxKeys * sizeof(int));
+    alloc((void**)&x->tot, kGxKeys * sizeof(int));
+    alloc((void**)&x->key_start, kGxKeys * sizeof(int));
+    x->max_groups = x->max_pieces / 32 + kGxKeys + 1;
+    alloc((void**)&x->gmom, (size_t)(p->desc.batch + 1) * x->max_groups * kGxP * sizeof(float2));
+    alloc((void**)&x->groups, (size_t)x->max_groups * sizeof(int4));
+    alloc((void**)&x->kmom, (size_t)(p->desc.batch + 1) * kGxKeys * kGxP * sizeof(float2));
+    alloc((void**)&x->key_group0, (kGxKeys + 1) * sizeof(int));
+    alloc((void**)&x->done, (size_t)(p->desc.batch + 1) * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(x->done, 0, (size_t)(p->desc.batch + 1) * sizeof(unsigned));
+    alloc((void**)&x->G_ws, (size_t)p->desc.batch * p->K * sizeof(double));
     alloc((void**)&x->pieces, (size_t)x->max_pieces * sizeof(int4));
     alloc((void**)&x->key_piece0, (kGxKeys + 1) * sizeof(int));
     alloc((void**)&x->num_part, (size_t)p->desc.batch * x->max_pieces * kGxP * sizeof(float));
@@ -447,21 +670,25 @@ static hobc_status gcvx_launch(hobc_plan_s* p, const void* ghat, const void* D, 
                                                 x->sd, x->counts);
     hobc_status s = gx_check(p, "k_gx_keys");
     if (s != HOBC_OK) return s;
-    k_gx_scan<<<1, 1024, 0, st>>>(x->counts, x->chunks, x->pieces, x->key_piece0);
-    if ((s = gx_check(p, "k_gx_scan")) != HOBC_OK) return s;
-    k_gx_scatter<<<x->chunks, 256, 0, st>>>(S, x->key, x->u, x->sn, x->sd, x->counts, x->s_idx, x->s_u, x->s_sn,
-                                            x->s_sd);
+    k_gx_chunkscan<<<(kGxKeys + 7) / 8, 256, 0, st>>>(x->counts, x->chunks, x->tot, x->done, x->key_start,
+                                                      x->pieces, x->key_piece0, x->groups, x->key_group0);
+    if ((s = gx_check(p, "k_gx_chunkscan")) != HOBC_OK) return s;
+    k_gx_scatter<<<x->chunks, 256, 0, st>>>(S, x->key, x->u, x->sn, x->sd, x->counts, x->key_start, x->s_idx,
+                                            x->s_u, x->s_sn, x->s_sd);
     if ((s = gx_check(p, "k_gx_scatter")) != HOBC_OK) return s;
-    const dim3 g1((x->max_pieces + 7) / 8, 1), gB((x->max_pieces + 7) / 8, p->desc.batch);
-    k_gx_moments<false, CPLX><<<g1, 256, 0, st>>>(x->pieces, x->key_piece0 + kGxKeys, x->s_idx, x->s_u, x->s_sd,
-                                                   nullptr, S, x->max_pieces, x->den_part);
+    const int B = p->desc.batch;
+    k_gx_moments<CPLX><<<dim3((x->max_pieces + 7) / 8, (B + kGxIpw - 1) / kGxIpw + 1), 256, 0, st>>>(
+        x->pieces, x->key_piece0 + kGxKeys, x->s_idx, x->s_u, x->s_sn, x->s_sd, reinterpret_cast<const E*>(ghat), S,
+        B, x->max_pieces, x->num_part, x->den_part);
     if ((s = gx_check(p, "k_gx_moments")) != HOBC_OK) return s;
-    k_gx_moments<true, CPLX><<<gB, 256, 0, st>>>(x->pieces, x->key_piece0 + kGxKeys, x->s_idx, x->s_u, x->s_sn,
-                                                  reinterpret_cast<const E*>(ghat), S, x->max_pieces, x->num_part);
-    if ((s = gx_check(p, "k_gx_moments")) != HOBC_OK) return s;
-    k_gx_finalize<<<p->desc.batch, 256, 0, st>>>(x->num_part, x->den_part, x->key_piece0, x->tab, p->mu, p->K,
-                                                 x->max_pieces, gcv, mu_idx);
-    return gx_check(p, "k_gx_finalize");
+    k_gx_reduce<<<dim3((x->max_groups + 7) / 8, B + 1), 256, 0, st>>>(
+        x->num_part, x->den_part, x->groups, x->key_group0 + kGxKeys, B, x->max_pieces, x->max_groups, x->gmom);
+    if ((s = gx_check(p, "k_gx_reduce")) != HOBC_OK) return s;
+    k_gx_keysum<<<dim3((kGxKeys + 7) / 8, B + 1), 256, 0, st>>>(x->gmom, x->key_group0, x->max_groups, x->kmom);
+    if ((s = gx_check(p, "k_gx_keysum")) != HOBC_OK) return s;
+    k_gx_curve<<<dim3((p->K + 31) / 32, B), 256, 0, st>>>(x->kmom, B, x->key_group0, x->tab, p->mu, p->K, x->G_ws,
+                                                          gcv, x->done + 1, mu_idx);
+    return gx_check(p, "k_gx_curve");
 }
 
 bool gcvx_active(const hobc_plan_s* p) { return p->gcv_mode == HOBC_GCV_EXPANSION && p->gx != nullptr; }
