@@ -25,7 +25,11 @@ below is written from its plain definition:
   network: x (128) -> GELU(W1 x + b1) (256) -> GELU(W2 h1 + b2) (256) -> w3 . h2 + b3,
     GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2; inputs are standardised
     with per-feature mean and scale stored with the weights.  The GPU uses the
-    weight matrices in bfloat16: a parity check rounds them with bf16_round.
+    weight matrices in bfloat16 (a parity check rounds them with bf16_round)
+    and runs the matrix products of the two hidden layers, of the weight
+    gradients and of the back-propagated gradient on tensor cores with both
+    operands rounded to bfloat16 and FP32 sums: forward and loss_and_grads take
+    that product as mm=bf16_matmul (default: the exact product).
   choice: learned_choice, the bracket test that keeps or rejects the prediction.
   loss: mean squared error of the prediction against the label.
   optimiser: AdamW (decoupled weight decay, bias-corrected moments).
@@ -116,6 +120,11 @@ def bf16_round(x) -> np.ndarray:
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+def bf16_matmul(A, B):
+    """A @ B with both operands rounded to bfloat16 first (sums exact in FP64)."""
+    return bf16_round(A) @ bf16_round(B)
+
+
 def gelu(z):
     return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
 
@@ -136,29 +145,31 @@ def init_params(rng: np.random.Generator, n_in=2 * NBINS, n_hidden=256):
     }
 
 
-def forward(p, X):
-    """Prediction for a batch X [B, n_in] (already standardised); returns (y, cache)."""
-    z1 = X @ p["W1"].T + p["b1"]
+def forward(p, X, mm=np.matmul):
+    """Prediction for a batch X [B, n_in] (already standardised); returns (y, cache).
+    mm: the product of the hidden layers."""
+    z1 = mm(X, p["W1"].T) + p["b1"]
     h1 = gelu(z1)
-    z2 = h1 @ p["W2"].T + p["b2"]
+    z2 = mm(h1, p["W2"].T) + p["b2"]
     h2 = gelu(z2)
     y = h2 @ p["w3"] + p["b3"][0]
     return y, (X, z1, h1, z2, h2)
 
 
-def loss_and_grads(p, X, t):
-    """Mean squared error and its gradient with respect to every parameter."""
-    y, (X, z1, h1, z2, h2) = forward(p, X)
+def loss_and_grads(p, X, t, mm=np.matmul):
+    """Mean squared error and its gradient with respect to every parameter.
+    mm: the product of the hidden layers, the weight gradients and dz1."""
+    y, (X, z1, h1, z2, h2) = forward(p, X, mm)
     B = X.shape[0]
     r = y - t
     loss = float(np.mean(r * r))
     dy = 2.0 * r / B
     g = {"w3": h2.T @ dy, "b3": np.array([dy.sum()])}
     dz2 = np.outer(dy, p["w3"]) * gelu_grad(z2)
-    g["W2"] = dz2.T @ h1
+    g["W2"] = mm(dz2.T, h1)
     g["b2"] = dz2.sum(axis=0)
-    dz1 = (dz2 @ p["W2"]) * gelu_grad(z1)
-    g["W1"] = dz1.T @ X
+    dz1 = mm(dz2, p["W2"]) * gelu_grad(z1)
+    g["W1"] = mm(dz1.T, X)
     g["b1"] = dz1.sum(axis=0)
     return loss, g
 

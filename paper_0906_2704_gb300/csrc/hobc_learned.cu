@@ -173,55 +173,81 @@ __global__ void k_features_finalize(const double* __restrict__ partials, int nch
 __device__ __forceinline__ float ldf(float x) { return x; }
 __device__ __forceinline__ float ldf(__nv_bfloat16 x) { return __bfloat162float(x); }
 
+__device__ __forceinline__ __nv_bfloat16 to_bf16(float x) { return __float2bfloat16_rn(x); }
+__device__ __forceinline__ __nv_bfloat16 to_bf16(__nv_bfloat16 x) { return x; }
+
 // C[m][n] = sum_k A(m,k) B(k,n) (+ bias[n]); A(m,k) = TRA ? A[k lda + m] : A[m lda + k],
-// B(k,n) = TRB ? B[n ldb + k] : B[k ldb + n].  64x64 tiles, K steps of 16,
-// 256 threads with 4x4 outputs each, FP32 accumulation.
+// B(k,n) = TRB ? B[n ldb + k] : B[k ldb + n].  On the tensor cores: both
+// operands rounded to bfloat16 (nearest, ties to even) as they are staged in
+// shared memory, mma.sync m16n8k16 with FP32 accumulation.  64x64 tiles, K
+// steps of 16; 4 warps, each a 32x32 quarter (2 x 4 MMA tiles of 16x8).
 template <typename TA, typename TB, bool TRA, bool TRB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_gemm(int M, int N, int K, const TA* __restrict__ A, int lda, const TB* __restrict__ B, int ldb,
        float* __restrict__ C, int ldc, const float* __restrict__ bias) {
-    __shared__ float As[16][64 + 4];
-    __shared__ float Bs[16][64 + 4];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    constexpr int LD = 16 + 8;                   // bf16 per tile row: k pairs stay 4-byte aligned
+    __shared__ __align__(16) __nv_bfloat16 As[64][LD];   // [m][k]
+    __shared__ __align__(16) __nv_bfloat16 Bs[64][LD];   // [n][k]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane >> 2, tig = lane & 3;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
     const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    float acc[4][4] = {};
+    float acc[2][4][4] = {};
     for (int k0 = 0; k0 < K; k0 += 16) {
-        for (int l = threadIdx.x; l < 1024; l += 256) {
+        for (int l = threadIdx.x; l < 1024; l += 128) {
             int mm, kk;
             if (TRA) { kk = l / 64; mm = l % 64; } else { mm = l / 16; kk = l % 16; }
             const int m = m0 + mm, k = k0 + kk;
-            float v = 0.f;
-            if (m < M && k < K) v = ldf(TRA ? A[(long long)k * lda + m] : A[(long long)m * lda + k]);
-            As[kk][mm] = v;
+            __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+            if (m < M && k < K) v = to_bf16(TRA ? A[(long long)k * lda + m] : A[(long long)m * lda + k]);
+            As[mm][kk] = v;
         }
-        for (int l = threadIdx.x; l < 1024; l += 256) {
+        for (int l = threadIdx.x; l < 1024; l += 128) {
             int kk, nn;
             if (TRB) { nn = l / 16; kk = l % 16; } else { kk = l / 64; nn = l % 64; }
             const int n = n0 + nn, k = k0 + kk;
-            float v = 0.f;
-            if (n < N && k < K) v = ldf(TRB ? B[(long long)n * ldb + k] : B[(long long)k * ldb + n]);
-            Bs[kk][nn] = v;
+            __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+            if (n < N && k < K) v = to_bf16(TRB ? B[(long long)n * ldb + k] : B[(long long)k * ldb + n]);
+            Bs[nn][kk] = v;
         }
         __syncthreads();
+        uint32_t af[2][4], bfr[4][2];
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) { a[i] = As[kk][ty * 4 + i]; b[i] = Bs[kk][tx * 4 + i]; }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int i = 0; i < 2; ++i) {
+            const int r = wm + 16 * i + grp;
+            af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][2 * tig]);
+            af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][2 * tig]);
+            af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][2 * tig + 8]);
+            af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][2 * tig + 8]);
         }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
-            if (m < M && n < N) C[(long long)m * ldc + n] = acc[i][j] + (bias ? bias[n] : 0.f);
+            const int c = wn + 8 * j + grp;
+            bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][2 * tig]);
+            bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][2 * tig + 8]);
         }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                asm volatile(
+                    "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                    "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+                    : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+                    : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bfr[j][0]), "r"(bfr[j][1]));
+        __syncthreads();
+    }
+    // accumulator (i, j): rows grp, grp + 8 of the 16x8 tile, columns 2 tig, 2 tig + 1
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int m = m0 + wm + 16 * i + grp + (h >> 1) * 8;
+                const int n = n0 + wn + 8 * j + 2 * tig + (h & 1);
+                if (m < M && n < N) C[(long long)m * ldc + n] = acc[i][j][h] + (bias ? bias[n] : 0.f);
+            }
 }
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
@@ -921,10 +947,10 @@ void forward(hobc_mlp_s* q, const float* x, int B, float* y_out) {
     cudaStream_t st = q->stream;
     const long long cx = (long long)B * q->nin, ch = (long long)B * q->nh;
     k_standardize<<<256, 256, 0, st>>>(x, q->mean, q->scale, q->xs, cx, q->nin);
-    k_gemm<float, __nv_bfloat16, false, true><<<gemm_grid(B, q->nh), 256, 0, st>>>(
+    k_gemm<float, __nv_bfloat16, false, true><<<gemm_grid(B, q->nh), 128, 0, st>>>(
         B, q->nh, q->nin, q->xs, q->nin, q->w1h, q->nin, q->z1, q->nh, q->params + ob1(q));
     k_gelu<<<256, 256, 0, st>>>(q->z1, q->h1, ch);
-    k_gemm<float, __nv_bfloat16, false, true><<<gemm_grid(B, q->nh), 256, 0, st>>>(
+    k_gemm<float, __nv_bfloat16, false, true><<<gemm_grid(B, q->nh), 128, 0, st>>>(
         B, q->nh, q->nh, q->h1, q->nh, q->w2h, q->nh, q->z2, q->nh, q->params + ob2(q));
     k_gelu<<<256, 256, 0, st>>>(q->z2, q->h2, ch);
     k_output<<<(B * 32 + 255) / 256, 256, 0, st>>>(q->h2, q->w3h, q->params + ob3(q), y_out, B, q->nh);
@@ -939,13 +965,13 @@ void backward(hobc_mlp_s* q, const float* t, int B, float* loss) {
     k_colsum<<<(q->nh + 255) / 256, 256, 0, st>>>(q->h2, q->dy, B, q->nh, g + ow3(q));
     k_sum<<<1, 256, 0, st>>>(q->dy, B, g + ob3(q));
     k_dz_out<<<256, 256, 0, st>>>(q->dy, q->w3h, q->z2, q->dz2, B, q->nh);
-    k_gemm<float, float, true, false><<<gemm_grid(q->nh, q->nh), 256, 0, st>>>(
+    k_gemm<float, float, true, false><<<gemm_grid(q->nh, q->nh), 128, 0, st>>>(
         q->nh, q->nh, B, q->dz2, q->nh, q->h1, q->nh, g + oW2(q), q->nh, nullptr);
     k_colsum<<<(q->nh + 255) / 256, 256, 0, st>>>(q->dz2, nullptr, B, q->nh, g + ob2(q));
-    k_gemm<float, __nv_bfloat16, false, false><<<gemm_grid(B, q->nh), 256, 0, st>>>(
+    k_gemm<float, __nv_bfloat16, false, false><<<gemm_grid(B, q->nh), 128, 0, st>>>(
         B, q->nh, q->nh, q->dz2, q->nh, q->w2h, q->nh, q->dh1, q->nh, nullptr);
     k_gelu_bwd<<<256, 256, 0, st>>>(q->dh1, q->z1, q->dz1, ch);
-    k_gemm<float, float, true, false><<<gemm_grid(q->nh, q->nin), 256, 0, st>>>(
+    k_gemm<float, float, true, false><<<gemm_grid(q->nh, q->nin), 128, 0, st>>>(
         q->nh, q->nin, B, q->dz1, q->nh, q->xs, q->nin, g + oW1(q), q->nin, nullptr);
     k_colsum<<<(q->nh + 255) / 256, 256, 0, st>>>(q->dz1, nullptr, B, q->nh, g + ob1(q));
     q->launches += 10;

@@ -209,14 +209,14 @@ def test_mlp_forward_and_gradients_match_oracle(n_in, nh, B):
     net.forward(x_d, y_d)
     pb = _bf16_weights(p32)
     Xs = (X.astype(np.float64) - mean) / scale
-    yo, (_, z1, h1, z2, h2) = M.forward(pb, Xs)
+    yo, (_, z1, h1, z2, h2) = M.forward(pb, Xs, mm=M.bf16_matmul)
     # FP32 accumulation: ~ (terms) * 2^-24 of the absolute sums, through two layers
     scale_y = np.abs(h2) @ np.abs(pb["w3"]) + 1.0
     assert np.all(np.abs(y_d.cpu().numpy() - yo) <= 2e-4 * scale_y)
     grad_d = torch.empty(net.param_count, dtype=torch.float32, device="cuda")
     loss_d = torch.empty(1, dtype=torch.float32, device="cuda")
     net.gradients(x_d, t_d, grad_d, loss_d)
-    lo, go = M.loss_and_grads(pb, Xs, t.astype(np.float64))
+    lo, go = M.loss_and_grads(pb, Xs, t.astype(np.float64), mm=M.bf16_matmul)
     assert abs(loss_d.item() - lo) <= 1e-4 * (1 + lo)
     got, _, _ = hobc.unpack_params(np.concatenate([grad_d.cpu().numpy(), np.zeros(2 * n_in)]), n_in, nh)
     for k in go:
@@ -226,30 +226,30 @@ def test_mlp_forward_and_gradients_match_oracle(n_in, nh, B):
 
 
 def test_adamw_steps_match_oracle():
+    """Two AdamW steps against the oracle's optimiser fed the same gradients (the
+    GPU's own, read before each step; their parity with the oracle's gradients is
+    the test above): the update arithmetic agrees to FP32 rounding."""
     n_in, nh, B = 128, 64, 96
     flat, p32, mean, scale, X, t = _net_case(n_in, nh, B, 3)
     net = hobc.MLP(n_in, nh)
     net.set_params(flat)
     x_d, t_d = _dev(X, np.float32), _dev(t, np.float32)
     lr, wd = 1e-3, 1e-2
-    po = {k: v.copy() for k, v in p32.items()}
+    po = {k: v.astype(np.float64).copy() for k, v in p32.items()}
     m = {k: np.zeros_like(v) for k, v in po.items()}
     v = {k: np.zeros_like(x) for k, x in po.items()}
-    Xs = (X.astype(np.float64) - mean) / scale
-    g1 = None
+    grad_d = torch.empty(net.param_count, dtype=torch.float32, device="cuda")
+    loss_d = torch.empty(1, dtype=torch.float32, device="cuda")
     for step in (1, 2):
+        net.gradients(x_d, t_d, grad_d, loss_d)
+        g, _, _ = hobc.unpack_params(np.concatenate([grad_d.cpu().numpy(), np.zeros(2 * n_in)]), n_in, nh)
+        g = {k: np.asarray(x, dtype=np.float64).reshape(po[k].shape) for k, x in g.items()}
         net.train_step(x_d, t_d, lr, wd)
-        _, g = M.loss_and_grads(_bf16_weights(po), Xs, t.astype(np.float64))
-        g1 = g if g1 is None else g1
         M.adamw_step(po, g, m, v, step, lr, wd=wd)
     got, _, _ = hobc.unpack_params(net.get_params(), n_in, nh)
     for k in po:
         diff = np.abs(got[k] - po[k])
-        # every entry moved by at most ~2.2 lr per step; where the first gradient is
-        # well above rounding the two updates agree closely
-        assert np.all(diff <= 5 * lr + 1e-6 * np.abs(po[k])), k
-        big = np.abs(g1[k]) > 1e-2 * np.abs(g1[k]).max()
-        assert np.all(diff[big] <= 2e-2 * lr + 1e-6 * np.abs(po[k][big])), k
+        assert np.all(diff <= 1e-3 * lr + 2e-6 * np.abs(po[k])), (k, float(diff.max()))
 
 
 def test_mlp_checkpoint_round_trip(tmp_path):

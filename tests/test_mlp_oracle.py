@@ -197,3 +197,21 @@ def test_hist_feature_bins_are_every_other_binned_choice_bin():
     b64 = Bo.bin_of(a, 64)
     b128 = Bo.bin_of(a, 128)
     assert np.array_equal(b64, b128 // 2)
+
+
+def test_bf16_matmul_rounds_both_operands():
+    """The tensor-core precision model: operands rounded to bfloat16, exact sums.
+    Equal to the exact product on bfloat16-representable inputs, not otherwise,
+    and the rounding of each operand is what moves it (a rounded-A-only product
+    differs too)."""
+    rng = np.random.default_rng(4)
+    A = M.bf16_round(rng.standard_normal((5, 7)))
+    B = M.bf16_round(rng.standard_normal((7, 3)))
+    assert np.array_equal(M.bf16_matmul(A, B), A @ B)
+    A2 = A + 1e-3 * rng.standard_normal(A.shape)
+    B2 = B + 1e-3 * rng.standard_normal(B.shape)
+    exact = A2 @ B2
+    got = M.bf16_matmul(A2, B2)
+    assert not np.allclose(got, exact, rtol=1e-6, atol=0)
+    assert np.allclose(got, exact, rtol=0, atol=2 * 2.0 ** -8 * (np.abs(A2) @ np.abs(B2)).max())
+    assert not np.array_equal(got, M.bf16_round(A2) @ B2)
