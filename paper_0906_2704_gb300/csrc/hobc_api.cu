@@ -331,6 +331,7 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half, int r
     a.fam = fam;
     a.n = n;
     a.p = p;
+    a.sslot = -1;
     cudaError_t err = cudaSuccess;
     if (fam == hobc::FAM_R || fam == hobc::FAM_PH) {
         // the classical comparison conditions run only in the dense mode: no
@@ -355,6 +356,17 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half, int r
     a.tpg = a.r16 ? a.M / 16 : a.M / 8;
     a.H = fam_fourier(fam) ? N / 2 + 1 : N;
     a.W = (fam_fourier(fam) && half) ? a.H + 2 * fam_nb(fam) : n;
+    // The pair kernels' two stage rows of a group fit in its own buffer above the
+    // slots their FFT input and output occupy (positions < L) and below the
+    // border-coefficient slots (M + M/16): with the chirp-z padding (M >= 2L - 1)
+    // and for the sine families that is always so, and the CTA then needs no
+    // separate stage (more of the SM's unified memory stays L1 for the tables).
+    {
+        const int esz_e = (fam_fourier(fam) ? 2 : 1) * (int)sizeof(T);
+        const int need = (2 * a.W * esz_e + 2 * (int)sizeof(T) - 1) / (2 * (int)sizeof(T));
+        const int first = (a.L - 1) + ((a.L - 1) >> 4) + 1;
+        a.sslot = first + need <= a.M + a.M / 16 ? first : -1;
+    }
 
     // per-stage twiddle tables in the order the FFT runs its stages: radix 16
     // while four or more bits remain (fft_r16) or radix 8 while three remain,

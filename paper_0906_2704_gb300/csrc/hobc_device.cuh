@@ -59,6 +59,9 @@ struct Axis {
     int tpg;        // threads per group: M/16 with radix-16 stages (r16), else M/8
     int r16;        // 1: radix-16 stages (M >= 256, log2M <= 12), 0: radix 8
     int Mp;         // shared-memory slots per group: group_slots(M)
+    int sslot;      // >= 0: the group's two stage rows of the pair kernels sit in its own
+                    // buffer from this slot on (free while they are used); -1: after
+                    // every group's buffer
     int H;          // Fourier families: floor(N/2)+1 stored frequencies; else N
     int W;          // spectrum entries stored on this axis: n, or H + 2 NB on a half axis of a
                     // Fourier family (NB border entries on each side)

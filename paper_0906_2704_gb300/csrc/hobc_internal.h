@@ -17,6 +17,7 @@ namespace hobc {
 struct AxisHost {
     int fam, n, N, L, M, log2M, blue, tpg, H, W;
     int r16;        // radix-16 FFT stages (else radix 8)
+    int sslot;      // stage rows of the pair kernels inside the group's buffer from this slot (-1: apart)
     void* tw;       // [M] complex
     void* chirp;    // [L] complex (Bluestein only)
     void* bhat;     // [M] complex (Bluestein only)

@@ -93,6 +93,16 @@ __device__ __forceinline__ T smoothing2(const FilterDesc& f, int mode, const Axi
 // (out_rs == 1 means a transposed store, staged so it stays coalesced).
 // grid = (ceil(nlines / 2G), items), block = G * ax.tpg.
 // =====================================================================
+// Stage row rr (0 <= rr < 2G) of a pair kernel: row rr & 1 of group rr >> 1,
+// inside that group's buffer from slot ax.sslot on (ax.sslot >= 0: above every
+// slot its FFT input or output occupies), or after all groups' buffers.
+template <typename E, typename T>
+__device__ __forceinline__ E* stage_row(unsigned char* smem_raw, const Axis<T>& ax, int G, int rr) {
+    C2<T>* base = reinterpret_cast<C2<T>*>(smem_raw);
+    if (ax.sslot >= 0) return reinterpret_cast<E*>(base + (size_t)(rr >> 1) * ax.Mp + ax.sslot) + (rr & 1) * ax.W;
+    return reinterpret_cast<E*>(base + (size_t)G * ax.Mp) + (size_t)rr * ax.W;
+}
+
 template <typename T, int FAM>
 __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, long long in_item, long long in_rs,
                                                    typename ElemT<T, fam_fourier(FAM)>::t* __restrict__ out,
@@ -105,7 +115,6 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
     const int g = threadIdx.x / ax.tpg;
     const int t = threadIdx.x - g * ax.tpg;
     C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.Mp;
-    E* stage = reinterpret_cast<E*>(reinterpret_cast<C2<T>*>(smem_raw) + (size_t)G * ax.Mp);
     const int n = ax.n, N = ax.N, W = ax.W;
     const int ra = r0 + 2 * g, rb = ra + 1;
     const bool va = ra < nlines, vb = rb < nlines;
@@ -171,8 +180,8 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
     __syncthreads();
     group_dft<T>(buf, ax, t);
 
-    E* sa = stage + (size_t)(2 * g) * W;
-    E* sb = sa + W;
+    E* sa = stage_row<E, T>(smem_raw, ax, G, 2 * g);
+    E* sb = stage_row<E, T>(smem_raw, ax, G, 2 * g + 1);
     if constexpr (FOUR) {
         for (int k = t; k < ax.H; k += ax.tpg) {
             const C2<T> zk = dft_out<T>(buf, ax, k);
@@ -235,12 +244,12 @@ __device__ __forceinline__ void pair_analysis_body(const T* __restrict__ in, lon
     if (out_rs == 1) {
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             const int c = idx / rows_here, rr = idx - c * rows_here;
-            o[rr + (long long)c * out_cs] = stage[(size_t)rr * W + c];
+            o[rr + (long long)c * out_cs] = stage_row<E, T>(smem_raw, ax, G, rr)[c];
         }
     } else {
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             const int rr = idx / W, c = idx - rr * W;
-            o[(long long)rr * out_rs + (long long)c * out_cs] = stage[(size_t)rr * W + c];
+            o[(long long)rr * out_rs + (long long)c * out_cs] = stage_row<E, T>(smem_raw, ax, G, rr)[c];
         }
     }
 }
@@ -276,7 +285,6 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, fam_
     const int g = threadIdx.x / ax.tpg;
     const int t = threadIdx.x - g * ax.tpg;
     C2<T>* buf = reinterpret_cast<C2<T>*>(smem_raw) + (size_t)g * ax.Mp;
-    E* stage = reinterpret_cast<E*>(reinterpret_cast<C2<T>*>(smem_raw) + (size_t)G * ax.Mp);
     const int n = ax.n, N = ax.N, W = ax.W;
     const int rows_here = min(2 * G, nlines - r0);
 
@@ -303,14 +311,23 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, fam_
                 const E d = Dp[(fd.psf_per ? item : 0) * fd.d_psf_stride + (long long)line * in_rs + (long long)c * in_cs];
                 v = apply_filter(v, d, smoothing2<T>(fd, 2, ax, line, c), mu_item);
             }
-            stage[(size_t)rr * W + c] = v;
+            stage_row<E, T>(smem_raw, ax, G, rr)[c] = v;
         }
-        for (int idx = total + threadIdx.x; idx < 2 * G * W; idx += blockDim.x) stage[idx] = E();
+        for (int idx = total + threadIdx.x; idx < 2 * G * W; idx += blockDim.x)
+            stage_row<E, T>(smem_raw, ax, G, idx / W)[idx % W] = E();
     }
     __syncthreads();
 
-    const E* sa = stage + (size_t)(2 * g) * W;
-    const E* sb = sa + W;
+    const E* sa = stage_row<E, T>(smem_raw, ax, G, 2 * g);
+    const E* sb = stage_row<E, T>(smem_raw, ax, G, 2 * g + 1);
+    // the border coefficients, read before the FFT may overwrite the stage
+    const T c1a = re_of(sa[0]), cna = re_of(sa[W - 1]);
+    const T c1b = re_of(sb[0]), cnb = re_of(sb[W - 1]);
+    T c4a[4], c4b[4];
+    if constexpr (NBF == 2) {
+        c4a[0] = re_of(sa[0]); c4a[1] = re_of(sa[1]); c4a[2] = re_of(sa[W - 2]); c4a[3] = re_of(sa[W - 1]);
+        c4b[0] = re_of(sb[0]); c4b[1] = re_of(sb[1]); c4b[2] = re_of(sb[W - 2]); c4b[3] = re_of(sb[W - 1]);
+    }
     const C2<T> zero = cmk<T>(0, 0);
     if constexpr (FOUR) {
         const int H = ax.H;
@@ -354,8 +371,6 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, fam_
 
     const int ra = r0 + 2 * g, rb = ra + 1;
     const bool va = ra < nlines, vb = rb < nlines;
-    const T c1a = re_of(sa[0]), cna = re_of(sa[W - 1]);
-    const T c1b = re_of(sb[0]), cnb = re_of(sb[W - 1]);
     T* oa = out + item * out_item + (long long)ra * out_rs;
     T* ob = out + item * out_item + (long long)rb * out_rs;
     // interior sample j of the trigonometric part, for both lines
@@ -384,8 +399,6 @@ __device__ __forceinline__ void pair_synthesis_body(const typename ElemT<T, fam_
         return;
     }
     if constexpr (NBF == 2) {
-        const T c4a[4] = {re_of(sa[0]), re_of(sa[1]), re_of(sa[W - 2]), re_of(sa[W - 1])};
-        const T c4b[4] = {re_of(sb[0]), re_of(sb[1]), re_of(sb[W - 2]), re_of(sb[W - 1])};
         for (int j = t; j < N; j += ax.tpg) {
             T wa, wb;
             wval(j, wa, wb);

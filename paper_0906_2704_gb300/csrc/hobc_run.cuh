@@ -14,6 +14,7 @@ static Axis<T> dev_axis(const AxisHost& a) {
     Axis<T> x;
     x.fam = a.fam; x.n = a.n; x.N = a.N; x.L = a.L; x.M = a.M; x.log2M = a.log2M;
     x.blue = a.blue; x.tpg = a.tpg; x.r16 = a.r16; x.Mp = group_slots(a.M); x.H = a.H; x.W = a.W;
+    x.sslot = a.sslot;
     x.tw = reinterpret_cast<const C2<T>*>(a.tw);
     x.chirp = reinterpret_cast<const C2<T>*>(a.chirp);
     x.bhat = reinterpret_cast<const C2<T>*>(a.bhat);
@@ -37,7 +38,7 @@ static inline Launch pair_launch(const AxisHost& a, size_t cbytes, size_t ebytes
     G = std::min(G, (nlines + 1) / 2);
     G = std::max(G, 1);
     const size_t Mp = (size_t)group_slots(a.M);
-    auto smem = [&](int g) { return (size_t)g * Mp * cbytes + (size_t)2 * g * a.W * ebytes; };
+    auto smem = [&](int g) { return (size_t)g * Mp * cbytes + (a.sslot >= 0 ? 0 : (size_t)2 * g * a.W * ebytes); };
     while (G > 1 && smem(G) > 200 * 1024) --G;
     Launch l;
     l.block = dim3(G * a.tpg);
