@@ -853,6 +853,13 @@ def run_other(args):
             h = torch.from_numpy(hh.astype(npdt)).to(dev)
             f = torch.empty_like(g)
             mi = torch.empty(B, dtype=torch.int32, device=dev)
+            # term-by-term scan first, then (FP32 / split-BF16) the curve by bin expansion,
+            # which is the line's value where it applies
+            ms_dir, _ = _timed(lambda: plan.deblur(g, h, f, mi), stream, args.steps, args.warmup)
+            plan.status()
+            mi_dir = mi.clone()
+            if prec != "fp64":
+                plan.set_gcv_mode("expansion")
             ms, clocks = _timed(lambda: plan.deblur(g, h, f, mi), stream, args.steps, args.warmup)
             plan.status()
             units, unit, launches = B, "deblurs/s", plan.last_launch_count
@@ -864,7 +871,10 @@ def run_other(args):
             gh = torch.empty((B, S), dtype=g.dtype, device=dev)
             ms_a, _ = _timed(lambda: plan.analysis(g, gh), stream, args.steps, 2)
             ms_s, _ = _timed(lambda: plan.synthesis(gh, f), stream, args.steps, 2)
-            extra = {"transform_ms_per_step": {"analysis": ms_a / args.steps, "synthesis": ms_s / args.steps}}
+            extra = {"transform_ms_per_step": {"analysis": ms_a / args.steps, "synthesis": ms_s / args.steps},
+                     "gcv_mode": plan.gcv_mode,
+                     "direct_scan": {"value": B / (ms_dir / args.steps / 1e3), "unit": "deblurs/s",
+                                     "index_agreement_with_line": float((mi_dir == mi).float().mean())}}
             f_b = torch.empty_like(g)
             mi_b = torch.empty(B, dtype=torch.int32, device=dev)
             ms_b, _ = _timed(lambda: plan.deblur_binned(g, h, f_b, mi_b), stream, args.steps, 2)
