@@ -186,6 +186,14 @@ hobc_status hobc_deblur(hobc_plan* plan, const void* g_dev, const void* psf_dev,
 hobc_status hobc_deblur_host(hobc_plan* plan, const void* g_host, const void* psf_host,
                              void* f_host, int* mu_index_host, double* gcv_host);
 
+/* Chunks of the host-buffer pipeline of hobc_deblur_host / hobc_deblur_host_async:
+ * the batch is cut into `chunks` (1..8; 0 restores the default, 4) whose uploads,
+ * kernels and downloads overlap.  More chunks hide more of the first upload and
+ * the last download, fewer keep the kernels' grids large.  HOBC_ERR_ARG outside
+ * 0..8.  Waits for the plan's queued work first (consecutive host calls are
+ * ordered chunk by chunk), so call it between calls, not inside stream capture. */
+hobc_status hobc_plan_set_host_chunks(hobc_plan* plan, int chunks);
+
 /* hobc_deblur_host without the final wait: queues the copies and kernels and
  * returns once the PSF has been read (it is copied into the plan's staging).
  * g_host must stay unchanged and f_host, mu_index_host, gcv_host unread until

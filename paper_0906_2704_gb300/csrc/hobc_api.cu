@@ -706,6 +706,18 @@ hobc_status hobc_plan_create(const hobc_plan_desc* desc, const double* mu_grid_h
     return HOBC_OK;
 }
 
+hobc_status hobc_plan_set_host_chunks(hobc_plan* p, int chunks) {
+    if (!p || chunks < 0 || chunks > 8) return HOBC_ERR_ARG;
+    // the per-chunk events order consecutive calls chunk by chunk: a new layout
+    // starts from an idle plan
+    cudaError_t e = p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize();
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        if (p->aux[i]) e = cudaStreamSynchronize(p->aux[i]);
+    if (e != cudaSuccess) { set_last_error("hobc_plan_set_host_chunks", e); return HOBC_ERR_CUDA; }
+    p->host_chunks = chunks;
+    return HOBC_OK;
+}
+
 hobc_family hobc_plan_family(const hobc_plan* p) {
     if (!p) return HOBC_FAMILY_AUTO;
     return p->fam == FAM_P ? HOBC_FAMILY_PERIODIC : (hobc_family)p->fam;
@@ -813,7 +825,8 @@ hobc_status hobc_deblur_host_async(hobc_plan* p, const void* g, const void* psf,
     const size_t B = (size_t)p->desc.batch;
     const size_t ib = p->img_elems * p->esz;
     const size_t pb = (size_t)p->npsf * p->psf_elems * p->esz;
-    const size_t nchunk = B >= kHostChunks ? kHostChunks : B;
+    const size_t want = p->host_chunks > 0 ? (size_t)p->host_chunks : kHostChunks;
+    const size_t nchunk = B >= want ? want : B;
     const size_t cb = (B + nchunk - 1) / nchunk;
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 2 && e == cudaSuccess; ++i)
@@ -837,6 +850,12 @@ hobc_status hobc_deblur_host_async(hobc_plan* p, const void* g, const void* psf,
     if (e != cudaSuccess) { set_last_error("hobc_deblur_host_async set-up", e); return HOBC_ERR_CUDA; }
     hobc_status s = HOBC_DISPATCH(p, run_eig, p->psf_in, p->D);
     if (s != HOBC_OK) return s;
+    // the expansion's steps that depend on the eigenvalues alone run once per call
+    const bool gx_once = gcvx_active(p) && p->nax == 2 && p->prec != HOBC_FP64;
+    if (gx_once) {
+        s = gcvx_prepare(p, p->D);
+        if (s != HOBC_OK) return s;
+    }
     // three-stage pipeline over chunks of the batch: every upload back to back
     // on aux[0], each chunk's kernels in order on the plan's stream once its
     // upload is done, each download on aux[1] once its kernels are done.
@@ -856,6 +875,7 @@ hobc_status hobc_deblur_host_async(hobc_plan* p, const void* g, const void* psf,
         e = cudaStreamWaitEvent(p->stream, p->ev_up[c], 0);
         if (e != cudaSuccess) break;
         hobc_plan_s v = chunk_view(p, c0, n, p->stream);
+        v.gx_prepared = gx_once ? 1 : 0;
         s = HOBC_DISPATCH(&v, run_analysis, v.g_in, v.G);
         if (s == HOBC_OK) e = cudaEventRecord(p->ev_an[c], p->stream);
         if (s == HOBC_OK && e == cudaSuccess) s = HOBC_DISPATCH(&v, run_gcv, v.G, v.D, gcv ? v.gcv : nullptr, v.mu_idx);

@@ -312,18 +312,18 @@ k_gx_scatter(long long S, const int* __restrict__ key, const float* __restrict__
 
 // Moments sum_j v_j u_j^p, p = 0..7, of every piece: one warp per piece, each
 // lane at most 8 entries (held in registers across the kGxIpw problems of grid
-// row y), summed in entry order, then a fixed shuffle tree.  Rows before the last:
-// v = sn |ghat|^2 of each problem in turn; the last row: v = sd.
+// row y), summed in entry order, then a fixed shuffle tree.  Rows y < num_rows:
+// v = sn |ghat|^2 of each problem in turn; a row past them: v = sd.
 template <bool CPLX>
 __global__ void __launch_bounds__(256, 5)
 k_gx_moments(const int4* __restrict__ pieces, const int* __restrict__ npieces, const int* __restrict__ s_idx,
              const float* __restrict__ s_u, const float* __restrict__ s_sn, const float* __restrict__ s_sd,
-             const typename ElemT<float, CPLX>::t* __restrict__ ghat, long long S, int items,
+             const typename ElemT<float, CPLX>::t* __restrict__ ghat, long long S, int items, int num_rows,
              int max_pieces, float* __restrict__ num_part, float* __restrict__ den_part) {
     constexpr int E = kGxPiece / 32;
     const int q = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (q >= *npieces) return;
-    const bool NUM = (int)blockIdx.y < (int)gridDim.y - 1;       // the last row: the denominator's moments
+    const bool NUM = (int)blockIdx.y < num_rows;                 // rows past num_rows: the denominator's moments
     const float* s_v = NUM ? s_sn : s_sd;
     float* part = NUM ? num_part : den_part;
     const int4 pc = pieces[q];
@@ -651,8 +651,10 @@ static hobc_status gx_check(hobc_plan_s* p, const char* what) {
     return HOBC_OK;
 }
 
+// The steps that depend on the eigenvalues alone: keys, the counting sort and
+// the denominator's piece moments.
 template <bool CPLX>
-static hobc_status gcvx_launch(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx) {
+static hobc_status gcvx_prepare_d(hobc_plan_s* p, const void* D) {
     typedef typename ElemT<float, CPLX>::t E;
     hobc_gcvx_s* x = p->gx;
     GcvGeom geo;
@@ -676,11 +678,27 @@ static hobc_status gcvx_launch(hobc_plan_s* p, const void* ghat, const void* D, 
     k_gx_scatter<<<x->chunks, 256, 0, st>>>(S, x->key, x->u, x->sn, x->sd, x->counts, x->key_start, x->s_idx,
                                             x->s_u, x->s_sn, x->s_sd);
     if ((s = gx_check(p, "k_gx_scatter")) != HOBC_OK) return s;
+    k_gx_moments<CPLX><<<dim3((x->max_pieces + 7) / 8, 1), 256, 0, st>>>(
+        x->pieces, x->key_piece0 + kGxKeys, x->s_idx, x->s_u, x->s_sn, x->s_sd, nullptr, S, 0, 0, x->max_pieces,
+        x->num_part, x->den_part);
+    return gx_check(p, "k_gx_moments");
+}
+
+// The steps of each batch of spectra: the numerators' piece moments, the group
+// and key sums and the curve.
+template <bool CPLX>
+static hobc_status gcvx_curves(hobc_plan_s* p, const void* ghat, double* gcv, int* mu_idx) {
+    typedef typename ElemT<float, CPLX>::t E;
+    hobc_gcvx_s* x = p->gx;
+    const long long S = (long long)p->spec_elems;
+    cudaStream_t st = p->stream;
     const int B = p->desc.batch;
-    k_gx_moments<CPLX><<<dim3((x->max_pieces + 7) / 8, (B + kGxIpw - 1) / kGxIpw + 1), 256, 0, st>>>(
+    const int rows = (B + kGxIpw - 1) / kGxIpw;
+    k_gx_moments<CPLX><<<dim3((x->max_pieces + 7) / 8, rows), 256, 0, st>>>(
         x->pieces, x->key_piece0 + kGxKeys, x->s_idx, x->s_u, x->s_sn, x->s_sd, reinterpret_cast<const E*>(ghat), S,
-        B, x->max_pieces, x->num_part, x->den_part);
-    if ((s = gx_check(p, "k_gx_moments")) != HOBC_OK) return s;
+        B, rows, x->max_pieces, x->num_part, x->den_part);
+    hobc_status s = gx_check(p, "k_gx_moments");
+    if (s != HOBC_OK) return s;
     k_gx_reduce<<<dim3((x->max_groups + 7) / 8, B + 1), 256, 0, st>>>(
         x->num_part, x->den_part, x->groups, x->key_group0 + kGxKeys, B, x->max_pieces, x->max_groups, x->gmom);
     if ((s = gx_check(p, "k_gx_reduce")) != HOBC_OK) return s;
@@ -693,9 +711,16 @@ static hobc_status gcvx_launch(hobc_plan_s* p, const void* ghat, const void* D, 
 
 bool gcvx_active(const hobc_plan_s* p) { return p->gcv_mode == HOBC_GCV_EXPANSION && p->gx != nullptr; }
 
+hobc_status gcvx_prepare(hobc_plan_s* p, const void* D) {
+    return fam_fourier(p->fam) ? gcvx_prepare_d<true>(p, D) : gcvx_prepare_d<false>(p, D);
+}
+
 hobc_status run_gcv_expansion(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx) {
-    return fam_fourier(p->fam) ? gcvx_launch<true>(p, ghat, D, gcv, mu_idx)
-                               : gcvx_launch<false>(p, ghat, D, gcv, mu_idx);
+    if (!p->gx_prepared) {                       // a view whose caller prepared the eigenvalue steps skips them
+        const hobc_status s = gcvx_prepare(p, D);
+        if (s != HOBC_OK) return s;
+    }
+    return fam_fourier(p->fam) ? gcvx_curves<true>(p, ghat, gcv, mu_idx) : gcvx_curves<false>(p, ghat, gcv, mu_idx);
 }
 
 }  // namespace hobc

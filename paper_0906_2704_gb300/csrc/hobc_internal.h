@@ -97,6 +97,8 @@ struct hobc_plan_s {
     size_t item0;            // first problem of this view of the plan (0 for the plan itself)
     int gcv_mode;            // HOBC_GCV_DIRECT / HOBC_GCV_EXPANSION (hobc_plan_set_gcv_mode)
     struct hobc_gcvx_s* gx;  // the expansion's workspace, allocated when the mode is set (hobc_gcvx.cu)
+    int gx_prepared;         // views of the host pipeline: the eigenvalue steps of the expansion already ran
+    int host_chunks;         // chunks of the host-buffer pipeline (0: the default)
 };
 
 // A 3D plan (include/hobc_volume.h): 2D passes over the slices, a transpose
@@ -137,6 +139,7 @@ void free_learned_ws(hobc_plan_s* p);
 void gcvx_free(hobc_plan_s* p);
 bool gcvx_active(const hobc_plan_s* p);
 hobc_status run_gcv_expansion(hobc_plan_s* p, const void* ghat, const void* D, double* gcv, int* mu_idx);
+hobc_status gcvx_prepare(hobc_plan_s* p, const void* D);
 hobc_status dense_prepare(hobc_plan_s* p);
 void dense_free(hobc_plan_s* p);
 hobc_status dense_analysis(hobc_plan_s* p, const void* g, void* ghat);

@@ -66,6 +66,8 @@ _lib.hobc_plan_destroy.argtypes = [_vp]
 _lib.hobc_plan_destroy.restype = None
 _lib.hobc_plan_family.argtypes = [_vp]
 _lib.hobc_plan_family.restype = ctypes.c_int
+_lib.hobc_plan_set_host_chunks.argtypes = [_vp, ctypes.c_int]
+_lib.hobc_plan_set_host_chunks.restype = ctypes.c_int
 _lib.hobc_plan_set_gcv_mode.argtypes = [_vp, ctypes.c_int]
 _lib.hobc_plan_set_gcv_mode.restype = ctypes.c_int
 _lib.hobc_plan_gcv_mode.argtypes = [_vp]
@@ -378,6 +380,10 @@ class Plan:
     def set_gcv_mode(self, mode: str) -> None:
         """'direct' (default) or 'expansion' (include/hobc.h, hobc_plan_set_gcv_mode)."""
         _check(_lib.hobc_plan_set_gcv_mode(self._handle, GCV_MODE[mode]), "hobc_plan_set_gcv_mode")
+
+    def set_host_chunks(self, chunks: int) -> None:
+        """Chunks of the host-buffer pipeline (1..8; 0: the default)."""
+        _check(_lib.hobc_plan_set_host_chunks(self._handle, int(chunks)), "hobc_plan_set_host_chunks")
 
     @property
     def gcv_expansion_bound(self) -> float:

@@ -160,3 +160,28 @@ def test_plans_the_expansion_does_not_serve_are_refused():
     with pytest.raises(hobc.HobcError) as e:           # 36 decades: the bound passes 1e-8
         plan.set_gcv_mode("expansion")
     assert e.value.status == 2 and plan.gcv_mode == "direct"
+
+
+@pytest.mark.parametrize("chunks", [1, 3, 8])
+def test_host_calls_in_expansion_mode_equal_the_device_call(chunks):
+    """hobc_deblur_host cuts the batch into chunks and prepares the expansion's
+    eigenvalue steps once per call: every problem's curve, mu index and f equal
+    those of hobc_deblur on device buffers, bit for bit, for any chunk count."""
+    F, h, mus, plan = _plan("fourier", (48, 66), (7, 7), "I", 64, 6)
+    plan.set_gcv_mode("expansion")
+    g, _ = P.problems(2, (48, 66), h, 6, 2, 0.01)
+    g32, h32 = g.astype(np.float32), h[None].astype(np.float32)
+    f_d = torch.empty((6, 48, 66), dtype=torch.float32, device="cuda")
+    mi_d = torch.empty(6, dtype=torch.int32, device="cuda")
+    G_d = torch.empty((6, 64), dtype=torch.float64, device="cuda")
+    plan.deblur(torch.from_numpy(g32).cuda(), torch.from_numpy(h32).cuda(), f_d, mi_d, G_d)
+    plan.set_host_chunks(chunks)
+    f_h = np.empty_like(g32)
+    mi_h = np.empty(6, dtype=np.int32)
+    G_h = np.empty((6, 64), dtype=np.float64)
+    for _ in range(2):                              # a second call reuses the staging
+        plan.deblur_host(g32, h32, f_h, mi_h, G_h)
+        assert np.array_equal(f_h, f_d.cpu().numpy()) and np.array_equal(mi_h, mi_d.cpu().numpy())
+        assert np.array_equal(G_h, G_d.cpu().numpy())
+    with pytest.raises(hobc.HobcError):
+        plan.set_host_chunks(9)
