@@ -792,7 +792,10 @@ def run_other(args):
                 schedule, tuned = autotune.tune_batched(items, synth.mu_grid(K), L="lap", prec=prec, cache=cache,
                                                         refresh=True)
                 t_tune = time.time() - t_tune
-            batch = hobc.Batch(items, synth.mu_grid(K), L="lap", prec=prec, stream=stream, schedule=schedule)
+            # FP32: the curve by bin expansion (the line's value); the term-by-term scan beside it
+            gmode = "expansion" if prec == "fp32" else "direct"
+            batch = hobc.Batch(items, synth.mu_grid(K), L="lap", prec=prec, stream=stream, schedule=schedule,
+                               gcv_mode=gmode)
             g = torch.from_numpy(np.concatenate([x.ravel() for x in gs]).astype(npdt)).to(dev)
             h = torch.from_numpy(np.concatenate([x.ravel() for x in hs]).astype(npdt)).to(dev)
             f = torch.empty_like(g)
@@ -806,10 +809,18 @@ def run_other(args):
             pixels = int(g.numel())
             extra = {"pixels_per_step": pixels, "pixels_per_s": pixels * args.steps / (ms / 1e3),
                      "degrees": np.bincount([it[4] for it in items], minlength=4)[1:].tolist(),
-                     "graph": True, "persistent": True}
+                     "graph": True, "persistent": True, "gcv_mode": gmode}
+            if gmode == "expansion":
+                mi_line = mi.clone()
+                direct = hobc.Batch(items, synth.mu_grid(K), L="lap", prec=prec, stream=stream, schedule=schedule)
+                ms_dir, _ = _timed(lambda: direct.deblur(g, h, f, mi), stream, args.steps, args.warmup)
+                ms_dir = max_over_ranks(ms_dir, dist, dev)
+                direct.close()
+                extra["direct_scan"] = {"value": total / (ms_dir / args.steps / 1e3), "unit": "images/s",
+                                        "index_agreement_with_line": float((mi_line == mi).float().mean())}
             if tuned is not None:
                 # the same batch with the default schedule (radix 16 from FFT length 256 up)
-                default = hobc.Batch(items, synth.mu_grid(K), L="lap", prec=prec, stream=stream)
+                default = hobc.Batch(items, synth.mu_grid(K), L="lap", prec=prec, stream=stream, gcv_mode=gmode)
                 ms_def, _ = _timed(lambda: default.deblur(g, h, f, mi), stream, args.steps, args.warmup)
                 default.close()
                 extra["autotune"] = {"seconds": t_tune, "schedule": tuned}

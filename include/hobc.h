@@ -339,6 +339,12 @@ typedef struct {
     hobc_smoothing L;
     hobc_precision prec;
     int n_mu;                  /* K >= 1 (FP32: every mu in [1e-18, 1e18])                 */
+    int gcv_mode;              /* HOBC_GCV_DIRECT (0) or HOBC_GCV_EXPANSION (FP32 batches):
+                                  the curve by bin expansion as for plans (the truncation
+                                  bound of hobc_plan_set_gcv_mode, HOBC_ERR_UNSUPPORTED when
+                                  it would pass 1e-8); each problem's entries are grouped by
+                                  key within chunks of 2048 entries, one record of 16 moments
+                                  per key present, and added chunk by chunk per problem  */
 } hobc_batch_desc;
 
 typedef struct hobc_batch_s hobc_batch;

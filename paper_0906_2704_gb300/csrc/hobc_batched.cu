@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "hobc_internal.h"
+#include "hobc_gcvx.cuh"
 #include "hobc_kernels.cuh"
 
 namespace hobc {
@@ -286,6 +287,386 @@ kp_gcv(const int2* __restrict__ work, int count, int* __restrict__ counter, cons
     }
 }
 
+// ------------------------------------------- GCV curve by bin expansion
+// The batch form of the plans' expansion (hobc_gcvx.cu): every problem has its
+// own eigenvalues, so the entries are grouped by key within chunks of
+// kGxBChunk entries of one problem instead of by a global sort.  A work item
+// (problem, chunk) classifies its entries (eight per thread, kept in registers),
+// sorts them by key into shared memory (stable: per-warp counts over entry
+// order, then ranks among equal keys), and writes, for every key present, the 8
+// numerator and 8 denominator moments of its entries into the key's slot of the
+// chunk's record, with a bit of the chunk's presence mask.  Each thread sums
+// eight consecutive sorted entries run by run; a run that crosses threads is
+// joined by a segmented scan over the threads (a fixed shuffle tree within a
+// warp, the warps in order), so every sum has a fixed order.  A problem's curve
+// then adds its chunks' moments key by key in chunk order (float-float) and
+// evaluates G on the grid.
+static const int kGxBChunk = 2048;
+static const int kGxBPer = kGxBChunk / 256;          // entries per thread
+static const int kGxLamN = 1024;                     // |s|^2 tables: positions along axis 0,
+static const int kGxLamRows = 64;                    // rows of one chunk
+static const int kGxMaskW = (kGxKeys + 31) / 32;     // presence mask words per chunk
+
+struct __align__(16) GxRec {     // one key's moments within one chunk
+    float E[kGxP];          // sum e u^p, e = w |ghat|^2 (w/a^2 above a_hi)
+    float W[kGxP];          // sum w u^p (w/a above a_hi)
+};
+
+// One key's place in a chunk's key-sorted order (run: the entries before it):
+// its start and count, and its entries' start in each of the eight warps'
+// slices (in warp order).
+__device__ __forceinline__ void gx_place_key(int key, int tot, int run, int (*wc)[kGxKeys], int* kstart, int* kcount) {
+    kstart[key] = run;
+    kcount[key] = tot;
+    int r = run;
+#pragma unroll
+    for (int w2 = 0; w2 < 8; ++w2) {
+        const int t = wc[w2][key];
+        wc[w2][key] = r;
+        r += t;
+    }
+}
+
+__device__ __forceinline__ void gx_put_rec(GxRec* rec, long long at, const float* E, const float* Wm) {
+    float4* o = reinterpret_cast<float4*>(rec + at);
+    o[0] = make_float4(E[0], E[1], E[2], E[3]);
+    o[1] = make_float4(E[4], E[5], E[6], E[7]);
+    o[2] = make_float4(Wm[0], Wm[1], Wm[2], Wm[3]);
+    o[3] = make_float4(Wm[4], Wm[5], Wm[6], Wm[7]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2)
+kp_gcvx(const int2* __restrict__ work, int count, int* __restrict__ counter, const GcvItem* __restrict__ gi,
+        const int* __restrict__ chunk0, const T* __restrict__ G, const T* __restrict__ D,
+        const GxTab* __restrict__ tab, unsigned* __restrict__ rec_mask, GxRec* __restrict__ rec) {
+    __shared__ __align__(16) float su[kGxBChunk], se[kGxBChunk], sd[kGxBChunk];   // key-sorted entries
+    __shared__ __align__(16) short sk[kGxBChunk];
+    __shared__ int wc[8][kGxKeys];
+    __shared__ int kstart[kGxKeys], kcount[kGxKeys];
+    __shared__ int wsum[8];
+    __shared__ float wagg[8][2 * kGxP], wcar[8][2 * kGxP];
+    __shared__ int wflag[8];
+    __shared__ float lam0[kGxLamN], lam1[kGxLamRows];
+    __shared__ GxTab stab;
+    __shared__ int ntot;
+    __shared__ int slot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    for (int j = threadIdx.x; j < (int)(sizeof(GxTab) / 4); j += blockDim.x)
+        reinterpret_cast<float*>(&stab)[j] = reinterpret_cast<const float*>(tab)[j];
+    for (int k = queue_first(counter, slot); k < count;) {
+        const int drawn = queue_draw(counter);
+        const int2 w = work[k];
+        const GcvItem g = gi[w.x];
+        const long long e0 = (long long)w.y * kGxBChunk;
+        const int cnt = (int)min((long long)kGxBChunk, g.geo.S - e0);
+        const T* Gp = G + g.spec_off;
+        const T* Dp = D + g.spec_off;
+        float dv[kGxBPer], gv[kGxBPer];
+#pragma unroll
+        for (int it = 0; it < kGxBPer; ++it) {
+            const int i = warp * (kGxBChunk / 8) + it * 32 + lane;
+            dv[it] = i < cnt ? (float)Dp[e0 + i] : 0.f;
+            gv[it] = i < cnt ? (float)Gp[e0 + i] : 0.f;
+        }
+        for (int j = threadIdx.x; j < 8 * kGxKeys; j += blockDim.x) (&wc[0][0])[j] = 0;
+        // |s|^2 by tables of the chunk's two Laplacian factors (the sums lap_s2 forms,
+        // the same operations): one per position along axis 0, one per row in the chunk
+        const GcvGeom& geo = g.geo;
+        const int c_lo = (int)(e0 / geo.n0);
+        const bool tabled = geo.lap && geo.ndim == 2 && geo.n0 <= kGxLamN &&
+                            (cnt + geo.n0 - 1) / geo.n0 + 1 <= kGxLamRows;
+        if (tabled) {
+            for (int t0 = threadIdx.x; t0 < geo.n0; t0 += blockDim.x)
+                lam0[t0] = lap_eig<float>(theta_over_pi<float>(geo.fam, geo.n0, geo.N0, t0));
+            const int rows = (int)((e0 + cnt - 1) / geo.n0) - c_lo + 1;
+            for (int r = threadIdx.x; r < rows; r += blockDim.x)
+                lam1[r] = lap_eig<float>(
+                    theta_over_pi<float>(geo.fam, geo.n1, geo.N1, stored_to_t(geo.fam, geo.n1, geo.W1, c_lo + r)));
+        }
+        __syncthreads();
+        // the entries of warp w: [256 w, 256 (w + 1)), in steps of 32; key, coordinate and
+        // the two terms (real families: weight 1); key -1 for entries outside the sums
+        int key[kGxBPer];
+        float uu[kGxBPer], vn[kGxBPer], vd[kGxBPer];
+        unsigned peers[kGxBPer];
+#pragma unroll
+        for (int it = 0; it < kGxBPer; ++it) {
+            const int i = warp * (kGxBChunk / 8) + it * 32 + lane;
+            key[it] = -1;
+            uu[it] = 0.f; vn[it] = 0.f; vd[it] = 0.f;
+            if (i < cnt) {
+                float s2;
+                if (tabled) {
+                    const int e = (int)(e0 - (long long)c_lo * geo.n0) + i;      // offset from row c_lo
+                    const int r = (unsigned)e / (unsigned)geo.n0;
+                    const float sv = lam1[r] + lam0[e - r * geo.n0];
+                    s2 = sv * sv;
+                } else {
+                    int c;
+                    s2 = (float)lap_s2<T>(geo, e0 + i, c);
+                }
+                if (s2 > 0.f) {
+                    const float a = fminf(dv[it] * dv[it] / s2, a_cap<float>());
+                    key[it] = gx_classify(a, 1.f, &stab, uu[it], vn[it], vd[it]);
+                    vn[it] *= gv[it] * gv[it];
+                }
+            }
+        }
+        // stable counting sort: counts per warp and key, in entry order
+#pragma unroll
+        for (int it = 0; it < kGxBPer; ++it) {
+            peers[it] = __match_any_sync(0xffffffffu, key[it]);
+            if (key[it] >= 0 && lane == __ffs(peers[it]) - 1) wc[warp][key[it]] += __popc(peers[it]);
+            __syncwarp();
+        }
+        __syncthreads();
+        const long long chunk = chunk0[w.x] + w.y;
+        {
+            // key starts in key order: one block-wide exclusive scan of the counts over
+            // keys 0..255 (a key per thread), keys 256 and 257 after them; then each key's
+            // warp prefixes, and the presence mask
+            const int kk = threadIdx.x;
+            int tk = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < 8; ++w2) tk += wc[w2][kk];
+            int tk2 = 0, t256 = 0;
+            if (threadIdx.x < kGxKeys - 256) {
+#pragma unroll
+                for (int w2 = 0; w2 < 8; ++w2) {
+                    t256 += wc[w2][256];
+                    tk2 += wc[w2][256 + threadIdx.x];
+                }
+            }
+            const unsigned present = __ballot_sync(0xffffffffu, tk > 0);
+            if (lane == 0) rec_mask[chunk * kGxMaskW + warp] = present;
+            const int v = tk;
+            int inc = v;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, off);
+                if (lane >= off) inc += y;
+            }
+            if (lane == 31) wsum[warp] = inc;
+            __syncthreads();
+            int base = 0, all = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < 8; ++w2) {
+                if (w2 < warp) base += wsum[w2];
+                all += wsum[w2];
+            }
+            gx_place_key(kk, tk, base + inc - v, wc, kstart, kcount);
+            if (threadIdx.x < kGxKeys - 256) {
+                gx_place_key(256 + threadIdx.x, tk2, all + (threadIdx.x == 1 ? t256 : 0), wc, kstart, kcount);
+                if (threadIdx.x == 1) {
+                    ntot = all + t256 + tk2;
+                    rec_mask[chunk * kGxMaskW + 8] = (t256 > 0 ? 1u : 0u) | (tk2 > 0 ? 2u : 0u);
+                }
+            }
+        }
+        __syncthreads();
+        // scatter into key order: the warp's start for the key, then the rank among equal keys
+#pragma unroll
+        for (int it = 0; it < kGxBPer; ++it) {
+            if (key[it] >= 0) {
+                const int pos = wc[warp][key[it]] + __popc(peers[it] & lt);
+                su[pos] = uu[it]; se[pos] = vn[it]; sd[pos] = vd[it]; sk[pos] = (short)key[it];
+            }
+            __syncwarp();
+            if (key[it] >= 0 && lane == __ffs(peers[it]) - 1) wc[warp][key[it]] += __popc(peers[it]);
+            __syncwarp();
+        }
+        __syncthreads();
+        // each thread: sorted entries [8 t, 8 t + 8), run by run.  A run inside the
+        // thread is written at once; one that began in an earlier thread and ends here
+        // (the thread owns it) waits for the carry; one that goes on past the thread is
+        // its contribution X to the segmented scan (flag F: a run begins here)
+        const long long rbase = chunk * kGxKeys;
+        const int p0 = threadIdx.x * kGxBPer, n = ntot;
+        float cE[kGxP], cW[kGxP], oE[kGxP], oW[kGxP];
+#pragma unroll
+        for (int p = 0; p < kGxP; ++p) { cE[p] = 0.f; cW[p] = 0.f; oE[p] = 0.f; oW[p] = 0.f; }
+        int curk = -1, okey = -1;
+        if (p0 < n) {
+            const float4 u4[2] = {reinterpret_cast<const float4*>(su + p0)[0],
+                                  reinterpret_cast<const float4*>(su + p0)[1]};
+            const float4 e4[2] = {reinterpret_cast<const float4*>(se + p0)[0],
+                                  reinterpret_cast<const float4*>(se + p0)[1]};
+            const float4 d4[2] = {reinterpret_cast<const float4*>(sd + p0)[0],
+                                  reinterpret_cast<const float4*>(sd + p0)[1]};
+            const short* kp = sk + p0;
+            const float* ua = reinterpret_cast<const float*>(u4);
+            const float* ea = reinterpret_cast<const float*>(e4);
+            const float* da = reinterpret_cast<const float*>(d4);
+#pragma unroll
+            for (int j = 0; j < kGxBPer; ++j) {
+                if (p0 + j < n) {
+                    const int kj = kp[j];
+                    if (kj != curk) {
+                        if (curk >= 0) {                // the run of curk ends at p0 + j - 1
+                            if (kstart[curk] < p0) {
+                                okey = curk;
+#pragma unroll
+                                for (int p = 0; p < kGxP; ++p) { oE[p] = cE[p]; oW[p] = cW[p]; }
+                            } else {
+                                gx_put_rec(rec, rbase + curk, cE, cW);
+                            }
+#pragma unroll
+                            for (int p = 0; p < kGxP; ++p) { cE[p] = 0.f; cW[p] = 0.f; }
+                        }
+                        curk = kj;
+                    }
+                    float te = ea[j], tw = da[j];
+                    const float u = ua[j];
+#pragma unroll
+                    for (int p = 0; p < kGxP; ++p) {
+                        cE[p] += te; cW[p] += tw;
+                        te *= u; tw *= u;
+                    }
+                }
+            }
+        }
+        int F = 1;
+        if (curk >= 0) {
+            const bool starts = kstart[curk] >= p0, ends = kstart[curk] + kcount[curk] <= p0 + kGxBPer;
+            if (ends) {
+                if (starts) {
+                    gx_put_rec(rec, rbase + curk, cE, cW);
+                } else {
+                    okey = curk;
+#pragma unroll
+                    for (int p = 0; p < kGxP; ++p) { oE[p] = cE[p]; oW[p] = cW[p]; }
+                }
+#pragma unroll
+                for (int p = 0; p < kGxP; ++p) { cE[p] = 0.f; cW[p] = 0.f; }
+            } else {
+                F = starts ? 1 : 0;
+            }
+        }
+        // segmented inclusive scan of (X, F) over the threads: within the warp...
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int yF = __shfl_up_sync(0xffffffffu, F, off);
+#pragma unroll
+            for (int p = 0; p < kGxP; ++p) {
+                const float yE = __shfl_up_sync(0xffffffffu, cE[p], off);
+                const float yW = __shfl_up_sync(0xffffffffu, cW[p], off);
+                if (lane >= off && !F) { cE[p] = yE + cE[p]; cW[p] = yW + cW[p]; }
+            }
+            if (lane >= off) F |= yF;
+        }
+        if (lane == 31) {
+#pragma unroll
+            for (int p = 0; p < kGxP; ++p) { wagg[warp][p] = cE[p]; wagg[warp][kGxP + p] = cW[p]; }
+            wflag[warp] = F;
+        }
+        __syncthreads();
+        // ...then the warps in order: the carry into each warp (a thread per warp and sum)
+        if (threadIdx.x < 8 * 2 * kGxP) {
+            const int wv = threadIdx.x / (2 * kGxP), q = threadIdx.x % (2 * kGxP);
+            float C = 0.f;
+            for (int w2 = 0; w2 < wv; ++w2) C = wflag[w2] ? wagg[w2][q] : C + wagg[w2][q];
+            wcar[wv][q] = C;
+        }
+        __syncthreads();
+        if (!F) {
+#pragma unroll
+            for (int p = 0; p < kGxP; ++p) { cE[p] = wcar[warp][p] + cE[p]; cW[p] = wcar[warp][kGxP + p] + cW[p]; }
+        }
+        // the owner of a run that began earlier: the previous thread's scanned sums + its own
+#pragma unroll
+        for (int p = 0; p < kGxP; ++p) {
+            const float yE = __shfl_up_sync(0xffffffffu, cE[p], 1);
+            const float yW = __shfl_up_sync(0xffffffffu, cW[p], 1);
+            oE[p] = (lane == 0 ? wcar[warp][p] : yE) + oE[p];
+            oW[p] = (lane == 0 ? wcar[warp][kGxP + p] : yW) + oW[p];
+        }
+        if (okey >= 0) gx_put_rec(rec, rbase + okey, oE, oW);
+        k = queue_handover(drawn, slot);
+    }
+}
+
+// The curve of every problem: its chunks' moments added key by key in chunk
+// order (float-float; a thread per key and moment, the chunks whose mask has
+// the key), G(mu_j) for every grid value (Horner in FP32 per key, float-float
+// over the keys, two key halves per grid value added in order), and the first
+// minimum (NaN never wins).  One CTA per problem.
+__global__ void __launch_bounds__(256)
+kb_gxcurve(const int* __restrict__ chunk0, const unsigned* __restrict__ rec_mask, const GxRec* __restrict__ rec,
+           const GxTab* __restrict__ tab, const double* __restrict__ mu, int K, const BatchIO* __restrict__ io) {
+    __shared__ float Ms[kGxKeys][2 * kGxP];       // E_p (p + 1), then W_p
+    __shared__ float red[4][2][128];
+    __shared__ double sv[256];
+    __shared__ int si[256];
+    const int item = blockIdx.x;
+    const long long c0 = chunk0[item];
+    const int nch = chunk0[item + 1] - chunk0[item];
+    for (int q = threadIdx.x; q < kGxKeys * 2 * kGxP; q += blockDim.x) {
+        const int key = q / (2 * kGxP), comp = q % (2 * kGxP);
+        const unsigned bit = 1u << (key & 31);
+        const unsigned* mk = rec_mask + c0 * kGxMaskW + (key >> 5);
+        const float* rv = reinterpret_cast<const float*>(rec + c0 * kGxKeys + key) + comp;
+        float hi = 0.f, lo = 0.f;
+#pragma unroll 4
+        for (int c = 0; c < nch; ++c)
+            if (__ldg(mk + (long long)c * kGxMaskW) & bit) two_sum_acc(hi, lo, __ldg(rv + (long long)c * kGxKeys * 2 * kGxP));
+        Ms[key][comp] = comp < kGxP ? (hi + lo) * (float)(comp + 1) : hi + lo;
+    }
+    __syncthreads();
+    double best = INFINITY;
+    int bi = 0x7fffffff;
+    const int half = threadIdx.x >> 7, jl = threadIdx.x & 127;   // two key halves per grid value
+    for (int jb = 0; jb < K; jb += 128) {
+        const int j = jb + jl;
+        const float m = j < K ? (float)mu[j] : 1.f;
+        float nh = 0, nl = 0, dh = 0, dl = 0;
+        for (int key = half; key < kGxKeys; key += 2) {
+            float x, sn_, sd_;
+            gx_key_terms(key, m, tab, x, sn_, sd_);
+            float hn = Ms[key][kGxP - 1], hd = Ms[key][2 * kGxP - 1];
+#pragma unroll
+            for (int p = kGxP - 2; p >= 0; --p) {
+                hn = fmaf(hn, x, Ms[key][p]);
+                hd = fmaf(hd, x, Ms[key][kGxP + p]);
+            }
+            two_sum_acc(nh, nl, hn * sn_);
+            two_sum_acc(dh, dl, hd * sd_);
+        }
+        red[0][half][jl] = nh; red[1][half][jl] = nl; red[2][half][jl] = dh; red[3][half][jl] = dl;
+        __syncthreads();
+        if (half == 0 && j < K) {
+            float ah = red[0][0][jl], al = red[1][0][jl], bh = red[2][0][jl], bl = red[3][0][jl];
+            two_sum_acc(ah, al, red[0][1][jl]);
+            al += red[1][1][jl];
+            two_sum_acc(bh, bl, red[2][1][jl]);
+            bl += red[3][1][jl];
+            const double den = (double)bh + (double)bl;
+            const double Gv = ((double)ah + (double)al) / (den * den);
+            if (io->gcv) io->gcv[(long long)item * K + j] = Gv;
+            const double key = isnan(Gv) ? INFINITY : Gv;
+            if (key < best || (key == best && j < bi)) { best = key; bi = j; }
+        }
+        __syncthreads();
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            const double v2 = sv[threadIdx.x + s];
+            const int i2 = si[threadIdx.x + s];
+            if (v2 < sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
+                sv[threadIdx.x] = v2;
+                si[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) io->mu_idx[item] = si[0] == 0x7fffffff ? 0 : si[0];
+}
+
 }  // namespace hobc
 
 using namespace hobc;
@@ -327,6 +708,15 @@ struct hobc_batch_s {
     BatchIO* io_dev;
     double* costab;          // per-axis tables cos(k theta_t), k <= the largest PSF half-width
     float2* costab2;         // the same split into float pairs hi + lo (FP32 batches)
+    int gcv_mode;            // HOBC_GCV_DIRECT / HOBC_GCV_EXPANSION (FP32 batches)
+    GxTab* gxtab;            // the expansion's bin geometry
+    int2* gx_work;           // (problem, chunk of kGxBChunk entries), costliest first
+    int gx_count;
+    int* gx_chunk0;          // [count + 1] first chunk of each problem
+    unsigned* rec_mask;      // [chunks][kGxMaskW] keys present in each chunk
+    GxRec* rec;              // [chunks][keys] their moments (slots of absent keys unwritten)
+    int gx_grid;
+    double gx_bound;
     cudaGraphExec_t graph;
     int launches;
 };
@@ -365,10 +755,17 @@ hobc_status launch_all(hobc_batch_s* b) {
                                                                       G);
         ++launches;
     }
-    const size_t gsmem = 4 * (size_t)gcv_chunk_for(1LL << 40, b->K, sizeof(T) == 8) * sizeof(T);
-    kp_gcv<T><<<b->grid[5], 256, gsmem, st>>>(b->gcv_work, b->gcv_count, ctr + 5, b->gcv_items_dev, G, D,
-                                              reinterpret_cast<const T*>(b->muT), b->partials);
-    kb_gcv_finalize<<<b->count, 256, 0, st>>>(b->gcv_items_dev, b->partials, io, b->K);
+    if (sizeof(T) == 4 && b->gcv_mode == HOBC_GCV_EXPANSION) {
+        kp_gcvx<T><<<b->gx_grid, 256, 0, st>>>(b->gx_work, b->gx_count, ctr + 5, b->gcv_items_dev, b->gx_chunk0, G,
+                                               D, b->gxtab, b->rec_mask, b->rec);
+        kb_gxcurve<<<b->count, 256, 0, st>>>(b->gx_chunk0, b->rec_mask, b->rec, b->gxtab, b->mu, b->K,
+                                             io);
+    } else {
+        const size_t gsmem = 4 * (size_t)gcv_chunk_for(1LL << 40, b->K, sizeof(T) == 8) * sizeof(T);
+        kp_gcv<T><<<b->grid[5], 256, gsmem, st>>>(b->gcv_work, b->gcv_count, ctr + 5, b->gcv_items_dev, G, D,
+                                                  reinterpret_cast<const T*>(b->muT), b->partials);
+        kb_gcv_finalize<<<b->count, 256, 0, st>>>(b->gcv_items_dev, b->partials, io, b->K);
+    }
     launches += 2;
     FilterDesc fd;
     memset(&fd, 0, sizeof(fd));
@@ -458,6 +855,7 @@ extern "C" void hobc_batch_destroy(hobc_batch* b) {
     cudaFree(b->axes_dev); cudaFree(b->items_dev); cudaFree(b->gcv_items_dev); cudaFree(b->gcv_work);
     cudaFree(b->costab);
     cudaFree(b->costab2);
+    cudaFree(b->gxtab); cudaFree(b->gx_work); cudaFree(b->gx_chunk0); cudaFree(b->rec_mask); cudaFree(b->rec);
     cudaFree(b->eig_work); cudaFree(b->mu); cudaFree(b->muT); cudaFree(b->R); cudaFree(b->G); cudaFree(b->D);
     cudaFree(b->partials); cudaFree(b->mu_idx_ws); cudaFree(b->gcv_ws); cudaFree(b->io_dev);
     delete b;
@@ -478,11 +876,25 @@ extern "C" hobc_status hobc_batch_create_tuned(const hobc_batch_desc* desc, cons
     const hobc_batch_desc d = *desc;
     if (d.count < 1 || d.n_mu < 1) return HOBC_ERR_ARG;
     if (d.prec != HOBC_FP64 && d.prec != HOBC_FP32) return HOBC_ERR_ARG;
+    if (d.gcv_mode != HOBC_GCV_DIRECT && d.gcv_mode != HOBC_GCV_EXPANSION) return HOBC_ERR_ARG;
     if (d.L != HOBC_L_IDENTITY && d.L != HOBC_L_LAPLACIAN) return HOBC_ERR_ARG;
     for (int j = 0; j < d.n_mu; ++j) {
         if (!std::isfinite(mu_grid_host[j])) return HOBC_ERR_NONFINITE;
         if (!(mu_grid_host[j] > 0)) return HOBC_ERR_ARG;
         if (d.prec == HOBC_FP32 && (mu_grid_host[j] < 1e-18 || mu_grid_host[j] > 1e18)) return HOBC_ERR_ARG;
+    }
+    GxTab gxt;
+    double gxb = 0;
+    if (d.gcv_mode == HOBC_GCV_EXPANSION) {
+        if (d.prec != HOBC_FP32) {
+            set_last_error_text("hobc_batch_create: the GCV expansion serves FP32 batches");
+            return HOBC_ERR_UNSUPPORTED;
+        }
+        gx_make_table(mu_grid_host, d.n_mu, gxt, &gxb);
+        if (!(gxb <= 1e-8)) {
+            set_last_error_text("hobc_batch_create: the mu grid spans too many decades for the GCV expansion");
+            return HOBC_ERR_UNSUPPORTED;
+        }
     }
     for (int i = 0; i < d.count; ++i) {
         const hobc_batch_item& it = items[i];
@@ -670,6 +1082,27 @@ extern "C" hobc_status hobc_batch_create_tuned(const hobc_batch_desc* desc, cons
     });
     b->gcv_count = (int)gw.size();
     b->eig_count = (int)ew.size();
+    // the expansion's work: chunks of kGxBChunk entries of each problem, costliest first
+    b->gcv_mode = d.gcv_mode;
+    b->gx_bound = gxb;
+    std::vector<int> gx_chunk0(d.count + 1, 0);
+    std::vector<int2> gxw;
+    if (d.gcv_mode == HOBC_GCV_EXPANSION) {
+        for (int i = 0; i < d.count; ++i) {
+            const int nch = (int)((gi[i].geo.S + kGxBChunk - 1) / kGxBChunk);
+            gx_chunk0[i + 1] = gx_chunk0[i] + nch;
+            for (int c = 0; c < nch; ++c) gxw.push_back(make_int2(i, c));
+        }
+        std::stable_sort(gxw.begin(), gxw.end(), [&](const int2& x, const int2& y) {
+            return std::min((long long)kGxBChunk, gi[x.x].geo.S - (long long)x.y * kGxBChunk) >
+                   std::min((long long)kGxBChunk, gi[y.x].geo.S - (long long)y.y * kGxBChunk);
+        });
+        b->gx_count = (int)gxw.size();
+        b->gx_work = reinterpret_cast<int2*>(upload(gxw, err));
+        b->gx_chunk0 = reinterpret_cast<int*>(upload(gx_chunk0, err));
+        std::vector<GxTab> tv(1, gxt);
+        b->gxtab = reinterpret_cast<GxTab*>(upload(tv, err));
+    }
     b->gcv_items_dev = reinterpret_cast<GcvItem*>(upload(gi, err));
     b->gcv_work = reinterpret_cast<int2*>(upload(gw, err));
     b->eig_work = reinterpret_cast<int2*>(upload(ew, err));
@@ -684,6 +1117,12 @@ extern "C" hobc_status hobc_batch_create_tuned(const hobc_batch_desc* desc, cons
     alloc((void**)&b->gcv_ws, (size_t)d.count * b->K * sizeof(double));
     alloc((void**)&b->io_dev, sizeof(BatchIO));
     alloc((void**)&b->counters, 6 * sizeof(int));
+    if (d.gcv_mode == HOBC_GCV_EXPANSION) {
+        const size_t nch = (size_t)gx_chunk0[d.count];
+        alloc((void**)&b->rec_mask, nch * kGxMaskW * sizeof(unsigned));
+        alloc((void**)&b->rec, nch * kGxKeys * sizeof(GxRec));
+        if (err == cudaSuccess) b->gx_grid = resident_ctas(kp_gcvx<float>, 0, b->gx_count);
+    }
     if (err == cudaSuccess) {
         const size_t gsmem = 4 * (size_t)gcv_chunk_for(1LL << 40, b->K, d.prec == HOBC_FP64) * b->esz;
         const bool f64 = d.prec == HOBC_FP64;

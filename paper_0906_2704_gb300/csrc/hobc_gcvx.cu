@@ -33,24 +33,13 @@
 #include <vector>
 
 #include "hobc_internal.h"
-#include "hobc_kernels.cuh"
+#include "hobc_gcvx.cuh"
 
 namespace hobc {
 
-static const int kGxBins = 256;               // inner bins, uniform in log a
-static const int kGxKeys = kGxBins + 2;       // key 0: a < a_lo; 1..256 inner; 257: a >= a_hi
-static const int kGxP = 8;                    // moments p = 0..7
 static const int kGxChunk = 1024;             // entries per CTA of the key and scatter passes
 static const int kGxPiece = 256;              // entries per piece (one warp)
 static const int kGxIpw = 4;                  // problems per warp of the moments pass
-
-struct GxTab {                                // bin geometry (device copy)
-    float abar[kGxBins];                      // bin centres a_lo r^(b + 1/2)
-    float inv_abar[kGxBins];
-    float edge[kGxBins + 1];                  // bin edges a_lo r^b
-    float a_lo, a_hi;
-    float log2_alo, bins_per_log2;            // b = floor((log2 a - log2 a_lo) bins_per_log2)
-};
 
 }  // namespace hobc
 
@@ -85,15 +74,6 @@ namespace hobc {
 
 namespace {
 
-// float-float accumulation: hi + lo += x, with the rounding error of hi + x kept
-// in lo (TwoSum; the _rn intrinsics keep the compiler from fusing or reordering)
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
-    const float s = __fadd_rn(hi, x);
-    const float bv = __fsub_rn(s, hi);
-    lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(x, bv));
-    hi = s;
-}
-
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -112,7 +92,6 @@ k_gx_keys(const typename ElemT<float, CPLX>::t* __restrict__ D, GcvGeom geo, con
     for (int k = threadIdx.x; k < kGxKeys; k += blockDim.x) hist[k] = 0;
     __syncthreads();
     const long long base = (long long)blockIdx.x * kGxChunk;
-    const float a_lo = tab->a_lo, a_hi = tab->a_hi;
     for (int r = 0; r < kGxChunk / 256; ++r) {
         const long long i = base + r * 256 + threadIdx.x;
         if (i >= S) break;
@@ -128,19 +107,7 @@ k_gx_keys(const typename ElemT<float, CPLX>::t* __restrict__ D, GcvGeom geo, con
         float uu = 0.f, vn = 0.f, vd = 0.f;
         if (s2 > 0.f) {
             const float a = fminf(abs2_of(D[i]) / s2, a_cap<float>());
-            if (a < a_lo) {
-                k = 0; uu = a / a_lo; vn = w; vd = w;
-            } else if (a >= a_hi) {
-                k = kGxKeys - 1; uu = a_hi / a; vd = w / a; vn = vd / a;
-            } else {
-                int b = (int)floorf((__log2f(a) - tab->log2_alo) * tab->bins_per_log2);
-                b = max(0, min(kGxBins - 1, b));
-                if (a < tab->edge[b] && b > 0) --b;                 // the approximate log2 may be one bin off
-                else if (a >= tab->edge[b + 1] && b < kGxBins - 1) ++b;
-                k = 1 + b;
-                uu = (a - tab->abar[b]) * tab->inv_abar[b];
-                vn = w; vd = w;
-            }
+            k = gx_classify(a, w, tab, uu, vn, vd);
             atomicAdd(&hist[k], 1);
         }
         key[i] = k; u[i] = uu; sn[i] = vn; sd[i] = vd;
@@ -471,21 +438,11 @@ k_gx_curve(const float2* __restrict__ kmom, int batch, const int* __restrict__ k
     const int jl = threadIdx.x & 31, slice = threadIdx.x >> 5;
     const int j = blockIdx.x * 32 + jl;
     const float m = j < K ? (float)mu[j] : 1.f;
-    const float a_lo = tab->a_lo, a_hi = tab->a_hi;
     float nh = 0, nl = 0, dh = 0, dl = 0;
     for (int k = slice; k < kGxKeys; k += 8) {
         if (!nonempty[k]) continue;
         float x, sn_, sd_;
-        if (k == 0) {
-            const float inv = __fdividef(1.f, m);
-            x = -a_lo * inv; sn_ = inv * inv; sd_ = inv;
-        } else if (k == kGxKeys - 1) {
-            x = -m / a_hi; sn_ = 1.f; sd_ = 1.f;
-        } else {
-            const float ab = tab->abar[k - 1];
-            const float inv = __fdividef(1.f, ab + m);
-            x = -ab * inv; sn_ = inv * inv; sd_ = inv;
-        }
+        gx_key_terms(k, m, tab, x, sn_, sd_);
         float hn = Ec[k][kGxP - 1], hd = Wc[k][kGxP - 1];
 #pragma unroll
         for (int p = kGxP - 2; p >= 0; --p) {
@@ -561,25 +518,13 @@ void gcvx_free(hobc_plan_s* p) {
     p->gx = nullptr;
 }
 
-// Truncation bound of the series for a grid [mu_min, mu_max] (relative error of
-// a numerator term; the denominator's is smaller): 9 U^8/(1-U)^2 with U the
-// largest |rho u| of an inner bin (and 9 (1e-3)^8 for the outer keys).
-static double gx_bound(double mu_min, double mu_max, double* r_out) {
-    const double decades = std::log10(mu_max / mu_min) + 6.0;
-    const double r = std::pow(10.0, decades / kGxBins);
-    const double U = std::sqrt(r) - 1.0 + 1e-6;             // margin for the rounding of the edges
-    if (r_out) *r_out = r;
-    return std::max(9.0 * std::pow(U, 8) / ((1 - U) * (1 - U)), 9.0 * std::pow(1e-3, 8));
-}
-
-static hobc_status gcvx_prepare(hobc_plan_s* p) {
+static hobc_status gcvx_setup(hobc_plan_s* p) {
     std::vector<double> mu(p->K);
     cudaError_t e = cudaMemcpy(mu.data(), p->mu, sizeof(double) * p->K, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) { set_last_error("hobc_plan_set_gcv_mode", e); return HOBC_ERR_CUDA; }
-    const double mu_min = *std::min_element(mu.begin(), mu.end());
-    const double mu_max = *std::max_element(mu.begin(), mu.end());
-    double r = 0;
-    const double bound = gx_bound(mu_min, mu_max, &r);
+    GxTab t;
+    double bound = 0;
+    gx_make_table(mu.data(), p->K, t, &bound);
     if (!(bound <= 1e-8)) {
         char msg[200];
         snprintf(msg, sizeof(msg), "hobc_plan_set_gcv_mode: the mu grid spans too many decades for the "
@@ -587,19 +532,6 @@ static hobc_status gcvx_prepare(hobc_plan_s* p) {
         set_last_error_text(msg);
         return HOBC_ERR_UNSUPPORTED;
     }
-    GxTab t;
-    memset(&t, 0, sizeof(t));
-    const double a_lo = 1e-3 * mu_min, a_hi = 1e3 * mu_max;
-    for (int b = 0; b <= kGxBins; ++b) t.edge[b] = (float)(a_lo * std::pow(r, b));
-    for (int b = 0; b < kGxBins; ++b) {
-        const double ab = a_lo * std::pow(r, b + 0.5);
-        t.abar[b] = (float)ab;
-        t.inv_abar[b] = (float)(1.0 / ab);
-    }
-    t.a_lo = (float)a_lo;
-    t.a_hi = (float)t.edge[kGxBins];
-    t.log2_alo = (float)std::log2(a_lo);
-    t.bins_per_log2 = (float)(1.0 / std::log2(r));
     hobc_gcvx_s* x = new hobc_gcvx_s();
     memset(x, 0, sizeof(*x));
     p->gx = x;
@@ -742,7 +674,7 @@ hobc_status hobc_plan_set_gcv_mode(hobc_plan* p, int mode) {
         return HOBC_ERR_UNSUPPORTED;
     }
     if (!p->gx) {
-        const hobc_status s = gcvx_prepare(p);
+        const hobc_status s = gcvx_setup(p);
         if (s != HOBC_OK) return s;
     }
     p->gcv_mode = HOBC_GCV_EXPANSION;

@@ -91,7 +91,8 @@ class BatchItem(ctypes.Structure):
 
 
 class BatchDesc(ctypes.Structure):
-    _fields_ = [("count", ctypes.c_int), ("L", ctypes.c_int), ("prec", ctypes.c_int), ("n_mu", ctypes.c_int)]
+    _fields_ = [("count", ctypes.c_int), ("L", ctypes.c_int), ("prec", ctypes.c_int), ("n_mu", ctypes.c_int),
+                ("gcv_mode", ctypes.c_int)]
 
 
 _lib.hobc_batch_create.argtypes = [ctypes.POINTER(BatchDesc), ctypes.POINTER(BatchItem),
@@ -593,14 +594,17 @@ class Batch:
     """A batch plan: many 2D problems of uneven sizes, each with its own
     symmetric PSF and boundary degree (1, 2, 3), deblurred in one call."""
 
-    def __init__(self, items, mu_grid, L: str = "lap", prec: str = "fp64", stream=None, schedule=None):
+    def __init__(self, items, mu_grid, L: str = "lap", prec: str = "fp64", stream=None, schedule=None,
+                 gcv_mode: str = "direct"):
         """items: sequence of (n0, n1, psf0, psf1, bc_degree); schedule: optional
-        sequence of (bc_degree, fft_length, radix) (hobc_batch_create_tuned)."""
+        sequence of (bc_degree, fft_length, radix) (hobc_batch_create_tuned);
+        gcv_mode: "direct" or "expansion" (FP32)."""
         arr = (BatchItem * len(items))()
         for i, (n0, n1, p0, p1, deg) in enumerate(items):
             arr[i].n[0], arr[i].n[1], arr[i].psf[0], arr[i].psf[1], arr[i].bc_degree = n0, n1, p0, p1, deg
         d = BatchDesc()
         d.count, d.L, d.prec = len(items), SMOOTHING[L], PRECISION[prec]
+        d.gcv_mode = GCV_MODE[gcv_mode]
         mu = np.ascontiguousarray(mu_grid, dtype=np.float64)
         d.n_mu = len(mu)
         if stream is None:
@@ -616,7 +620,7 @@ class Batch:
                                             sarr, len(sched), _vp(stream), ctypes.byref(self._handle)),
                "hobc_batch_create_tuned")
         self.items, self.mu_grid, self.prec, self.L = list(items), mu, prec, L
-        self.schedule = sched
+        self.schedule, self.gcv_mode = sched, gcv_mode
         io = (_sz * (len(items) + 1))()
         po = (_sz * (len(items) + 1))()
         _check(_lib.hobc_batch_offsets(self._handle, io, po), "hobc_batch_offsets")

@@ -181,3 +181,43 @@ def test_autotuner_writes_and_reuses_its_table(tmp_path):
     assert sched2 == sched
     b = hobc.Batch(items, mus, L="lap", prec="fp32", stream=torch.cuda.current_stream(), schedule=sched)
     assert b.last_launch_count >= 0
+
+
+@pytest.mark.parametrize("L", ["I", "lap"])
+def test_batched_gcv_expansion_matches_the_direct_scan_and_the_oracle(L):
+    """The batch's curve by bin expansion (gcv_mode="expansion"): every problem's G
+    within the FP32 tolerance of the term-by-term batch curve (itself pinned to the
+    plan path and the oracle above; two curves, each within 1e-5 of the exact one),
+    the same mu index or one within it, f equal where the index is; the graph and a
+    direct launch give the same bits; FP64 and over-wide grids refused."""
+    K = 64
+    mus = synth.mu_grid(K, 1e-8, 1.0)
+    items = ITEMS + BIG
+    gs, hs = _problems(items, 31)
+    gs = [x.astype(np.float32).astype(np.float64) for x in gs]
+    hs = [x.astype(np.float32).astype(np.float64) for x in hs]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        bd = hobc.Batch(items, mus, L=L, prec="fp32", stream=stream)
+        bx = hobc.Batch(items, mus, L=L, prec="fp32", stream=stream, gcv_mode="expansion")
+        fd, md, Gd = _run(bd, gs, hs, np.float32, K)
+        fx, mx, Gx = _run(bx, gs, hs, np.float32, K)
+        fx2, mx2, Gx2 = _run(bx, gs, hs, np.float32, K)
+    direct = hobc.Batch(items, mus, L=L, prec="fp32", stream=None, gcv_mode="expansion")
+    fx3, mx3, Gx3 = _run(direct, gs, hs, np.float32, K)
+    for a, b, c in ((fx, fx2, fx3), (mx, mx2, mx3), (Gx, Gx2, Gx3)):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+    assert np.max(np.abs(Gx - Gd) / Gd) <= 2e-5
+    for i, (n0, n1, p0, p1, deg) in enumerate(items):
+        k, kd = int(mx[i]), int(md[i])
+        assert k == kd or Gd[i, k] <= (1 + 2e-5) * Gd[i, kd], (i, k, kd)
+    same = mx == md
+    off = np.concatenate([[0], np.cumsum([n0 * n1 for (n0, n1, *_r) in items])])
+    for i in np.flatnonzero(same):
+        assert np.array_equal(fx[off[i]:off[i + 1]], fd[off[i]:off[i + 1]])
+    with pytest.raises(hobc.HobcError) as ei:
+        hobc.Batch(ITEMS, mus, prec="fp64", gcv_mode="expansion")
+    assert hobc.STATUS[ei.value.status] == "HOBC_ERR_UNSUPPORTED"
+    with pytest.raises(hobc.HobcError) as ei:
+        hobc.Batch(ITEMS, synth.mu_grid(8, 1e-18, 1e12), prec="fp32", gcv_mode="expansion")
+    assert hobc.STATUS[ei.value.status] == "HOBC_ERR_UNSUPPORTED"
