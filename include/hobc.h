@@ -343,8 +343,11 @@ typedef struct {
                                   the curve by bin expansion as for plans (the truncation
                                   bound of hobc_plan_set_gcv_mode, HOBC_ERR_UNSUPPORTED when
                                   it would pass 1e-8); each problem's entries are grouped by
-                                  key within chunks of 2048 entries, one record of 16 moments
-                                  per key present, and added chunk by chunk per problem  */
+                                  key within chunks of 2048 entries, 16 moments per key
+                                  present in the key's slot of the chunk's record, added
+                                  chunk by chunk per problem.  The records take a fixed
+                                  slot per key: 258 x 64 bytes per chunk (about 8 bytes per
+                                  spectrum entry) of device memory, allocated here       */
 } hobc_batch_desc;
 
 typedef struct hobc_batch_s hobc_batch;

@@ -327,37 +327,38 @@ __device__ __forceinline__ void gx_place_key(int key, int tot, int run, int (*wc
     }
 }
 
-__device__ __forceinline__ void gx_put_rec(GxRec* rec, long long at, const float* E, const float* Wm) {
+__device__ __forceinline__ void gx_put_rec(GxRec* rec, long long at, const float2* c) {
     float4* o = reinterpret_cast<float4*>(rec + at);
-    o[0] = make_float4(E[0], E[1], E[2], E[3]);
-    o[1] = make_float4(E[4], E[5], E[6], E[7]);
-    o[2] = make_float4(Wm[0], Wm[1], Wm[2], Wm[3]);
-    o[3] = make_float4(Wm[4], Wm[5], Wm[6], Wm[7]);
+    o[0] = make_float4(c[0].x, c[1].x, c[2].x, c[3].x);
+    o[1] = make_float4(c[4].x, c[5].x, c[6].x, c[7].x);
+    o[2] = make_float4(c[0].y, c[1].y, c[2].y, c[3].y);
+    o[3] = make_float4(c[4].y, c[5].y, c[6].y, c[7].y);
 }
 
+// Work items in a fixed round robin over the CTAs (chunks cost the same, but
+// for the last of each problem); the sums below are (E_p, W_p) pairs, added and
+// scaled two at a time.
 template <typename T>
-__global__ void __launch_bounds__(256, 2)
-kp_gcvx(const int2* __restrict__ work, int count, int* __restrict__ counter, const GcvItem* __restrict__ gi,
-        const int* __restrict__ chunk0, const T* __restrict__ G, const T* __restrict__ D,
-        const GxTab* __restrict__ tab, unsigned* __restrict__ rec_mask, GxRec* __restrict__ rec) {
+__global__ void __launch_bounds__(256, 3)
+kp_gcvx(const int2* __restrict__ work, int count, const GcvItem* __restrict__ gi, const int* __restrict__ chunk0,
+        const T* __restrict__ G, const T* __restrict__ D, const GxTab* __restrict__ tab,
+        unsigned* __restrict__ rec_mask, GxRec* __restrict__ rec) {
     __shared__ __align__(16) float su[kGxBChunk], se[kGxBChunk], sd[kGxBChunk];   // key-sorted entries
     __shared__ __align__(16) short sk[kGxBChunk];
     __shared__ int wc[8][kGxKeys];
     __shared__ int kstart[kGxKeys], kcount[kGxKeys];
     __shared__ int wsum[8];
-    __shared__ float wagg[8][2 * kGxP], wcar[8][2 * kGxP];
+    __shared__ float2 wagg[8][kGxP], wcar[8][kGxP];
     __shared__ int wflag[8];
     __shared__ float lam0[kGxLamN], lam1[kGxLamRows];
     __shared__ GxTab stab;
     __shared__ int ntot;
-    __shared__ int slot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned lt;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
     for (int j = threadIdx.x; j < (int)(sizeof(GxTab) / 4); j += blockDim.x)
         reinterpret_cast<float*>(&stab)[j] = reinterpret_cast<const float*>(tab)[j];
-    for (int k = queue_first(counter, slot); k < count;) {
-        const int drawn = queue_draw(counter);
+    for (int k = blockIdx.x; k < count; k += gridDim.x) {
         const int2 w = work[k];
         const GcvItem g = gi[w.x];
         const long long e0 = (long long)w.y * kGxBChunk;
@@ -386,6 +387,10 @@ kp_gcvx(const int2* __restrict__ work, int count, int* __restrict__ counter, con
                 lam1[r] = lap_eig<float>(
                     theta_over_pi<float>(geo.fam, geo.n1, geo.N1, stored_to_t(geo.fam, geo.n1, geo.W1, c_lo + r)));
         }
+        // the row of offset e from row c_lo: (e + 1/2)/n0 is at least 1/(2 n0) from an
+        // integer and below 2 + 2048/n0, so its FP32 product with 1/n0 truncates exactly
+        const float inv_n0 = 1.f / (float)geo.n0;
+        const int t_lo = (int)(e0 - (long long)c_lo * geo.n0);
         __syncthreads();
         // the entries of warp w: [256 w, 256 (w + 1)), in steps of 32; key, coordinate and
         // the two terms (real families: weight 1); key -1 for entries outside the sums
@@ -400,8 +405,8 @@ kp_gcvx(const int2* __restrict__ work, int count, int* __restrict__ counter, con
             if (i < cnt) {
                 float s2;
                 if (tabled) {
-                    const int e = (int)(e0 - (long long)c_lo * geo.n0) + i;      // offset from row c_lo
-                    const int r = (unsigned)e / (unsigned)geo.n0;
+                    const int e = t_lo + i;
+                    const int r = (int)(((float)e + 0.5f) * inv_n0);
                     const float sv = lam1[r] + lam0[e - r * geo.n0];
                     s2 = sv * sv;
                 } else {
@@ -409,7 +414,7 @@ kp_gcvx(const int2* __restrict__ work, int count, int* __restrict__ counter, con
                     s2 = (float)lap_s2<T>(geo, e0 + i, c);
                 }
                 if (s2 > 0.f) {
-                    const float a = fminf(dv[it] * dv[it] / s2, a_cap<float>());
+                    const float a = fminf(__fdividef(dv[it] * dv[it], s2), a_cap<float>());
                     key[it] = gx_classify(a, 1.f, &stab, uu[it], vn[it], vd[it]);
                     vn[it] *= gv[it] * gv[it];
                 }
@@ -442,8 +447,7 @@ kp_gcvx(const int2* __restrict__ work, int count, int* __restrict__ counter, con
             }
             const unsigned present = __ballot_sync(0xffffffffu, tk > 0);
             if (lane == 0) rec_mask[chunk * kGxMaskW + warp] = present;
-            const int v = tk;
-            int inc = v;
+            int inc = tk;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, inc, off);
@@ -457,7 +461,7 @@ kp_gcvx(const int2* __restrict__ work, int count, int* __restrict__ counter, con
                 if (w2 < warp) base += wsum[w2];
                 all += wsum[w2];
             }
-            gx_place_key(kk, tk, base + inc - v, wc, kstart, kcount);
+            gx_place_key(kk, tk, base + inc - tk, wc, kstart, kcount);
             if (threadIdx.x < kGxKeys - 256) {
                 gx_place_key(256 + threadIdx.x, tk2, all + (threadIdx.x == 1 ? t256 : 0), wc, kstart, kcount);
                 if (threadIdx.x == 1) {
@@ -485,9 +489,9 @@ kp_gcvx(const int2* __restrict__ work, int count, int* __restrict__ counter, con
         // its contribution X to the segmented scan (flag F: a run begins here)
         const long long rbase = chunk * kGxKeys;
         const int p0 = threadIdx.x * kGxBPer, n = ntot;
-        float cE[kGxP], cW[kGxP], oE[kGxP], oW[kGxP];
+        float2 c2[kGxP], o2[kGxP];
 #pragma unroll
-        for (int p = 0; p < kGxP; ++p) { cE[p] = 0.f; cW[p] = 0.f; oE[p] = 0.f; oW[p] = 0.f; }
+        for (int p = 0; p < kGxP; ++p) { c2[p] = make_float2(0.f, 0.f); o2[p] = make_float2(0.f, 0.f); }
         int curk = -1, okey = -1;
         if (p0 < n) {
             const float4 u4[2] = {reinterpret_cast<const float4*>(su + p0)[0],
@@ -509,21 +513,21 @@ kp_gcvx(const int2* __restrict__ work, int count, int* __restrict__ counter, con
                             if (kstart[curk] < p0) {
                                 okey = curk;
 #pragma unroll
-                                for (int p = 0; p < kGxP; ++p) { oE[p] = cE[p]; oW[p] = cW[p]; }
+                                for (int p = 0; p < kGxP; ++p) o2[p] = c2[p];
                             } else {
-                                gx_put_rec(rec, rbase + curk, cE, cW);
+                                gx_put_rec(rec, rbase + curk, c2);
                             }
 #pragma unroll
-                            for (int p = 0; p < kGxP; ++p) { cE[p] = 0.f; cW[p] = 0.f; }
+                            for (int p = 0; p < kGxP; ++p) c2[p] = make_float2(0.f, 0.f);
                         }
                         curk = kj;
                     }
-                    float te = ea[j], tw = da[j];
-                    const float u = ua[j];
+                    float2 t2 = make_float2(ea[j], da[j]);
+                    const float2 u2 = make_float2(ua[j], ua[j]);
 #pragma unroll
                     for (int p = 0; p < kGxP; ++p) {
-                        cE[p] += te; cW[p] += tw;
-                        te *= u; tw *= u;
+                        c2[p] = __fadd2_rn(c2[p], t2);
+                        t2 = __fmul2_rn(t2, u2);
                     }
                 }
             }
@@ -533,14 +537,14 @@ kp_gcvx(const int2* __restrict__ work, int count, int* __restrict__ counter, con
             const bool starts = kstart[curk] >= p0, ends = kstart[curk] + kcount[curk] <= p0 + kGxBPer;
             if (ends) {
                 if (starts) {
-                    gx_put_rec(rec, rbase + curk, cE, cW);
+                    gx_put_rec(rec, rbase + curk, c2);
                 } else {
                     okey = curk;
 #pragma unroll
-                    for (int p = 0; p < kGxP; ++p) { oE[p] = cE[p]; oW[p] = cW[p]; }
+                    for (int p = 0; p < kGxP; ++p) o2[p] = c2[p];
                 }
 #pragma unroll
-                for (int p = 0; p < kGxP; ++p) { cE[p] = 0.f; cW[p] = 0.f; }
+                for (int p = 0; p < kGxP; ++p) c2[p] = make_float2(0.f, 0.f);
             } else {
                 F = starts ? 1 : 0;
             }
@@ -551,40 +555,41 @@ kp_gcvx(const int2* __restrict__ work, int count, int* __restrict__ counter, con
             const int yF = __shfl_up_sync(0xffffffffu, F, off);
 #pragma unroll
             for (int p = 0; p < kGxP; ++p) {
-                const float yE = __shfl_up_sync(0xffffffffu, cE[p], off);
-                const float yW = __shfl_up_sync(0xffffffffu, cW[p], off);
-                if (lane >= off && !F) { cE[p] = yE + cE[p]; cW[p] = yW + cW[p]; }
+                float2 y;
+                y.x = __shfl_up_sync(0xffffffffu, c2[p].x, off);
+                y.y = __shfl_up_sync(0xffffffffu, c2[p].y, off);
+                if (lane >= off && !F) c2[p] = __fadd2_rn(y, c2[p]);
             }
             if (lane >= off) F |= yF;
         }
         if (lane == 31) {
 #pragma unroll
-            for (int p = 0; p < kGxP; ++p) { wagg[warp][p] = cE[p]; wagg[warp][kGxP + p] = cW[p]; }
+            for (int p = 0; p < kGxP; ++p) wagg[warp][p] = c2[p];
             wflag[warp] = F;
         }
         __syncthreads();
-        // ...then the warps in order: the carry into each warp (a thread per warp and sum)
-        if (threadIdx.x < 8 * 2 * kGxP) {
-            const int wv = threadIdx.x / (2 * kGxP), q = threadIdx.x % (2 * kGxP);
-            float C = 0.f;
-            for (int w2 = 0; w2 < wv; ++w2) C = wflag[w2] ? wagg[w2][q] : C + wagg[w2][q];
+        // ...then the warps in order: the carry into each warp (a thread per warp and pair)
+        if (threadIdx.x < 8 * kGxP) {
+            const int wv = threadIdx.x / kGxP, q = threadIdx.x % kGxP;
+            float2 C = make_float2(0.f, 0.f);
+            for (int w2 = 0; w2 < wv; ++w2) C = wflag[w2] ? wagg[w2][q] : __fadd2_rn(C, wagg[w2][q]);
             wcar[wv][q] = C;
         }
         __syncthreads();
         if (!F) {
 #pragma unroll
-            for (int p = 0; p < kGxP; ++p) { cE[p] = wcar[warp][p] + cE[p]; cW[p] = wcar[warp][kGxP + p] + cW[p]; }
+            for (int p = 0; p < kGxP; ++p) c2[p] = __fadd2_rn(wcar[warp][p], c2[p]);
         }
         // the owner of a run that began earlier: the previous thread's scanned sums + its own
 #pragma unroll
         for (int p = 0; p < kGxP; ++p) {
-            const float yE = __shfl_up_sync(0xffffffffu, cE[p], 1);
-            const float yW = __shfl_up_sync(0xffffffffu, cW[p], 1);
-            oE[p] = (lane == 0 ? wcar[warp][p] : yE) + oE[p];
-            oW[p] = (lane == 0 ? wcar[warp][kGxP + p] : yW) + oW[p];
+            float2 y;
+            y.x = __shfl_up_sync(0xffffffffu, c2[p].x, 1);
+            y.y = __shfl_up_sync(0xffffffffu, c2[p].y, 1);
+            o2[p] = __fadd2_rn(lane == 0 ? wcar[warp][p] : y, o2[p]);
         }
-        if (okey >= 0) gx_put_rec(rec, rbase + okey, oE, oW);
-        k = queue_handover(drawn, slot);
+        if (okey >= 0) gx_put_rec(rec, rbase + okey, o2);
+        __syncthreads();                // the shared arrays are reused by the next work item
     }
 }
 
@@ -756,8 +761,8 @@ hobc_status launch_all(hobc_batch_s* b) {
         ++launches;
     }
     if (sizeof(T) == 4 && b->gcv_mode == HOBC_GCV_EXPANSION) {
-        kp_gcvx<T><<<b->gx_grid, 256, 0, st>>>(b->gx_work, b->gx_count, ctr + 5, b->gcv_items_dev, b->gx_chunk0, G,
-                                               D, b->gxtab, b->rec_mask, b->rec);
+        kp_gcvx<T><<<b->gx_grid, 256, 0, st>>>(b->gx_work, b->gx_count, b->gcv_items_dev, b->gx_chunk0, G, D,
+                                               b->gxtab, b->rec_mask, b->rec);
         kb_gxcurve<<<b->count, 256, 0, st>>>(b->gx_chunk0, b->rec_mask, b->rec, b->gxtab, b->mu, b->K,
                                              io);
     } else {

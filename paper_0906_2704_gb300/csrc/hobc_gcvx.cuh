@@ -20,7 +20,7 @@ struct GxTab {                                // bin geometry (device copy)
     float abar[kGxBins];                      // bin centres a_lo r^(b + 1/2)
     float inv_abar[kGxBins];
     float edge[kGxBins + 1];                  // bin edges a_lo r^b
-    float a_lo, a_hi;
+    float a_lo, a_hi, inv_alo;
     float log2_alo, bins_per_log2;            // b = floor((log2 a - log2 a_lo) bins_per_log2)
 };
 
@@ -50,6 +50,7 @@ inline void gx_make_table(const double* mu, int K, GxTab& t, double* bound) {
     }
     t.a_lo = (float)a_lo;
     t.a_hi = t.edge[kGxBins];
+    t.inv_alo = (float)(1.0 / a_lo);
     t.log2_alo = (float)std::log2(a_lo);
     t.bins_per_log2 = (float)(1.0 / std::log2(r));
 }
@@ -64,24 +65,23 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
 }
 
 // The key of an entry with a = |d|^2/|s|^2 (capped) and weight w, its expansion
-// coordinate u and the scales of its numerator and denominator terms.
+// coordinate u and the scales of its numerator and denominator terms.  Branch
+// free: the inner bin is found for every a (clamped) and the outer keys chosen
+// by selects; 1/a is one correctly rounded reciprocal (key 257: u = a_hi/a,
+// w/a, w/a^2).
 __device__ __forceinline__ int gx_classify(float a, float w, const GxTab* __restrict__ tab, float& u, float& vn,
                                            float& vd) {
-    if (a < tab->a_lo) {
-        u = a / tab->a_lo; vn = w; vd = w;
-        return 0;
-    }
-    if (a >= tab->a_hi) {
-        u = tab->a_hi / a; vd = w / a; vn = vd / a;
-        return kGxKeys - 1;
-    }
     int b = (int)floorf((__log2f(a) - tab->log2_alo) * tab->bins_per_log2);
     b = max(0, min(kGxBins - 1, b));
     if (a < tab->edge[b] && b > 0) --b;                         // the approximate log2 may be one bin off
     else if (a >= tab->edge[b + 1] && b < kGxBins - 1) ++b;
-    u = (a - tab->abar[b]) * tab->inv_abar[b];
-    vn = w; vd = w;
-    return 1 + b;
+    const float ub = (a - tab->abar[b]) * tab->inv_abar[b];
+    const bool small = a < tab->a_lo, large = a >= tab->a_hi;
+    const float ra = __frcp_rn(large ? a : 1.f);
+    u = small ? a * tab->inv_alo : (large ? tab->a_hi * ra : ub);
+    vd = large ? w * ra : w;
+    vn = large ? vd * ra : w;
+    return small ? 0 : (large ? kGxKeys - 1 : 1 + b);
 }
 
 // The factors of key k at grid value m: the series variable x and the scales of
