@@ -501,6 +501,15 @@ cudaError_t build_axis_host(AxisHost& a, int fam, int n, int p, bool half, int r
     et[2 * (size_t)a.W * p + 1] = 0.0;
     if (err == cudaSuccess) err = cudaMalloc((void**)&a.etab, et.size() * sizeof(double));
     if (err == cudaSuccess) err = cudaMemcpy(a.etab, et.data(), et.size() * sizeof(double), cudaMemcpyHostToDevice);
+    // float-float split of the same table (FP32 eigenvalue sums): x = hi + lo
+    std::vector<float4> et2(et.size() / 2);
+    for (size_t i = 0; i < et2.size(); ++i) {
+        const float rh = (float)et[2 * i], ih = (float)et[2 * i + 1];
+        et2[i] = make_float4(rh, (float)(et[2 * i] - (double)rh), ih, (float)(et[2 * i + 1] - (double)ih));
+    }
+    if (err == cudaSuccess) err = cudaMalloc((void**)&a.etab2, et2.size() * sizeof(float4));
+    if (err == cudaSuccess)
+        err = cudaMemcpy(a.etab2, et2.data(), et2.size() * sizeof(float4), cudaMemcpyHostToDevice);
     return err;
 }
 
@@ -510,6 +519,7 @@ template cudaError_t build_axis_host<double>(AxisHost&, int, int, int, bool, int
 void free_axis(AxisHost& a) {
     cudaFree(a.tw); cudaFree(a.chirp); cudaFree(a.bhat); cudaFree(a.post); cudaFree(a.q); cudaFree(a.q2);
     cudaFree(a.etab);
+    cudaFree(a.etab2);
     memset(&a, 0, sizeof(a));
 }
 

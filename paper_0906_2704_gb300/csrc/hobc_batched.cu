@@ -854,6 +854,7 @@ extern "C" void hobc_batch_destroy(hobc_batch* b) {
     for (AxisHost& a : b->axes_host) {
         cudaFree(a.tw); cudaFree(a.chirp); cudaFree(a.bhat); cudaFree(a.post); cudaFree(a.q); cudaFree(a.q2);
         cudaFree(a.etab);
+        cudaFree(a.etab2);
     }
     for (PassList& l : b->pass) cudaFree(l.dev);
     cudaFree(b->counters);

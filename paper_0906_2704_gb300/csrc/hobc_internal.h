@@ -28,6 +28,7 @@ struct AxisHost {
     double k4[16];  // S3, C4, F4: inverse of the 4x4 border system
     int p;          // PSF extent on this axis
     double2* etab;  // [W][p] exp(-i (j - m) theta_t) for the stored entries t
+    float4* etab2;  // the same split into float pairs: (re hi, re lo, im hi, im lo)
 };
 
 struct Launch {     // grid/block/shared memory of one line-transform kernel

@@ -630,19 +630,46 @@ k_cplx_synthesis(const C2<T>* __restrict__ in, C2<T>* __restrict__ out, long lon
 // =====================================================================
 // Eigenvalues d[c][t0] = sum_{j0,j1} h[j0][j1] E0[t0][j0] E1[c][j1] with
 // E[t][j] = exp(-i (j - m) theta_t)  (Eq. (eq:symbol) at -theta, Sec. 6),
-// accumulated in double.  1D problems use n0 = p0 = 1 and E0 = [[1]].
+// accumulated in double (FP32 plans: the column sums in float-float, below).
+// 1D problems use n0 = p0 = 1 and E0 = [[1]].
 // The row stage P_k = sum_j1 h[m0 + k][j1] E1[c][j1] is combined over tap
 // offsets +-k:  P_k e^{-ik th} + P_{-k} e^{ik th} = A_k cos(k th) - i B_k sin(k th),
 // A_k = P_k + P_{-k}, B_k = P_k - P_{-k}, so the real part costs two products
 // per k (four with the imaginary part) instead of eight.
+// FP32 plans sum the column stage over k in float-float (the FP64 pipe of this
+// part runs at 1/64 of the FP32 rate): A_k, B_k and the table E0f = E0 split
+// into hi + lo float pairs, each product by TwoProduct (an FMA gives its
+// rounding error), the running sum by TwoSum (Ogita, Rump and Oishi's compensated
+// dot product): within about 2^-44 of the sum of |terms|, then rounded once to
+// FP32.
 // grid = (npsf, W1), block = 256.
 // =====================================================================
+
+// s + r += (xh + xl)(yh + yl), s + r a float-float running sum.  The _rn
+// intrinsics keep the compiler from fusing or reordering the error terms.
+__device__ __forceinline__ void ff_mac(float& s, float& r, float xh, float xl, float yh, float yl) {
+    const float p = __fmul_rn(xh, yh);
+    const float pe = __fmaf_rn(xh, yh, -p);                 // xh yh = p + pe exactly
+    const float sn = __fadd_rn(s, p);                       // s + p = sn + se exactly
+    const float bv = __fsub_rn(sn, s);
+    const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(sn, bv)), __fsub_rn(p, bv));
+    s = sn;
+    r += se + pe + __fmaf_rn(xh, yl, xl * yh);
+}
+
+__device__ __forceinline__ float4 ff_split(double2 v) {
+    const float rh = (float)v.x, ih = (float)v.y;
+    return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+
 template <typename T, bool CPLX>
 __global__ void k_eig(const T* __restrict__ psf, long long psf_stride, int p0, int p1,
-                      const double2* __restrict__ E0, const double2* __restrict__ E1, int n0,
+                      const double2* __restrict__ E0, const double2* __restrict__ E1,
+                      const float4* __restrict__ E0f, int n0,
                       typename ElemT<T, CPLX>::t* __restrict__ D, long long d_psf_stride) {
     __shared__ double2 P[64];
     __shared__ double2 A[32], Bk[32];
+    __shared__ float4 Af[32], Bf[32];      // FP32: A_k, B_k split (Af[0]: P_0)
     const int c = blockIdx.y;
     const long long ip = blockIdx.x;
     const T* h = psf + ip * psf_stride;
@@ -662,9 +689,34 @@ __global__ void k_eig(const T* __restrict__ psf, long long psf_stride, int p0, i
         const double2 pp = P[m0 + k], pm = P[m0 - k];
         A[k] = make_double2(pp.x + pm.x, pp.y + pm.y);
         Bk[k] = make_double2(pp.x - pm.x, pp.y - pm.y);
+        if constexpr (sizeof(T) == 4) {
+            Af[k] = ff_split(A[k]);
+            Bf[k] = ff_split(Bk[k]);
+        }
     }
+    if (sizeof(T) == 4 && threadIdx.x == 0) Af[0] = ff_split(P[m0]);
     __syncthreads();
     typename ElemT<T, CPLX>::t* o = D + ip * d_psf_stride + (long long)c * n0;
+    if constexpr (sizeof(T) == 4) {
+        for (int t0 = threadIdx.x; t0 < n0; t0 += blockDim.x) {
+            const float4 c0 = Af[0];
+            float rh = c0.x, rl = c0.y, ih = c0.z, il = c0.w;
+            const float4* e0 = E0f + (long long)t0 * p0 + m0;
+            for (int k = 1; k <= m0; ++k) {
+                const float4 e = e0[k];       // (cos k th, -sin k th), each hi + lo
+                const float4 a = Af[k], b = Bf[k];
+                ff_mac(rh, rl, a.x, a.y, e.x, e.y);                    // re += A.re cos
+                ff_mac(rh, rl, -b.z, -b.w, e.z, e.w);                  //    - B.im (-sin)
+                if constexpr (CPLX) {
+                    ff_mac(ih, il, a.z, a.w, e.x, e.y);                // im += A.im cos
+                    ff_mac(ih, il, b.x, b.y, e.z, e.w);                //    + B.re (-sin)
+                }
+            }
+            if constexpr (CPLX) o[t0] = cmk<T>(rh + rl, ih + il);
+            else o[t0] = rh + rl;
+        }
+        return;
+    }
     for (int t0 = threadIdx.x; t0 < n0; t0 += blockDim.x) {
         double re = P[m0].x, im = P[m0].y;
         const double2* e0 = E0 + (long long)t0 * p0 + m0;

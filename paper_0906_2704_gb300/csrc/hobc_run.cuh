@@ -239,18 +239,24 @@ hobc_status run_eig(hobc_plan_s* p, const void* psf, void* D) {
     const AxisHost& last = p->ax[p->nax - 1];
     const bool cplx = fam_fourier(p->fam);
     const double2* E0;
+    const float4* E0f;
     int p0, n0;
-    if (p->nax == 2) { E0 = p->ax[0].etab; p0 = p->ax[0].p; n0 = p->ax[0].n; }
-    else { E0 = last.etab + (size_t)last.W * last.p; p0 = 1; n0 = 1; }   // unit entry after the table
+    if (p->nax == 2) { E0 = p->ax[0].etab; E0f = p->ax[0].etab2; p0 = p->ax[0].p; n0 = p->ax[0].n; }
+    else {                                              // unit entry after the table
+        E0 = last.etab + (size_t)last.W * last.p;
+        E0f = last.etab2 + (size_t)last.W * last.p;
+        p0 = 1;
+        n0 = 1;
+    }
     const long long psf_stride = (long long)p->psf_elems;
     dim3 grid(p->npsf, last.W);
     if (cplx)
         k_eig<T, true><<<grid, 256, 0, p->stream>>>(reinterpret_cast<const T*>(psf), psf_stride, p0, last.p, E0,
-                                                    last.etab, n0, reinterpret_cast<C2<T>*>(D),
+                                                    last.etab, E0f, n0, reinterpret_cast<C2<T>*>(D),
                                                     (long long)p->spec_elems);
     else
         k_eig<T, false><<<grid, 256, 0, p->stream>>>(reinterpret_cast<const T*>(psf), psf_stride, p0, last.p, E0,
-                                                     last.etab, n0, reinterpret_cast<T*>(D),
+                                                     last.etab, E0f, n0, reinterpret_cast<T*>(D),
                                                      (long long)p->spec_elems);
     return check_launch(p, "k_eig");
 }

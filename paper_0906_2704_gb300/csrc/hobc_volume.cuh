@@ -192,12 +192,12 @@ hobc_status run3_eig(hobc_volume_s* q, const void* psf, void* D) {
     const int b3 = std::min(256, (q->az.n + 31) / 32 * 32);
     if (q->fam == FAM_F) {
         k_eig<T, true><<<g2, 256, 0, q->stream>>>(reinterpret_cast<const T*>(psf), slice_psf, a1.p, a2.p, a1.etab,
-                                                  a2.etab, a1.n, reinterpret_cast<C2<T>*>(q->D2), S2);
+                                                  a2.etab, a1.etab2, a1.n, reinterpret_cast<C2<T>*>(q->D2), S2);
         k_vol_eig<T, true><<<g3, b3, 0, q->stream>>>(reinterpret_cast<const C2<T>*>(q->D2), p0, S2, q->az.etab,
                                                       q->az.n, reinterpret_cast<C2<T>*>(D), S3);
     } else {
         k_eig<T, false><<<g2, 256, 0, q->stream>>>(reinterpret_cast<const T*>(psf), slice_psf, a1.p, a2.p, a1.etab,
-                                                   a2.etab, a1.n, reinterpret_cast<T*>(q->D2), S2);
+                                                   a2.etab, a1.etab2, a1.n, reinterpret_cast<T*>(q->D2), S2);
         k_vol_eig<T, false><<<g3, b3, 0, q->stream>>>(reinterpret_cast<const T*>(q->D2), p0, S2, q->az.etab,
                                                        q->az.n, reinterpret_cast<T*>(D), S3);
     }
