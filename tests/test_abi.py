@@ -186,3 +186,29 @@ def test_fft_length_and_schedule_validation(hobc):
     it = (hobc.BatchItem * 1)()
     mu = (ctypes.c_double * 1)(1e-2)
     assert lib.hobc_batch_create_tuned(ctypes.byref(d), it, mu, bad, 1, None, ctypes.byref(out)) == 1
+
+
+def test_gcv_mode_and_host_chunk_calls_reject_bad_arguments_on_the_host(hobc):
+    """The curve-by-expansion and host-chunk calls check their arguments before
+    any CUDA call; a batch description with an unknown gcv_mode, the expansion on
+    an FP64 batch, or a grid whose truncation bound would pass 1e-8 is refused
+    before any device work."""
+    lib = hobc.library()
+    assert lib.hobc_plan_set_gcv_mode(None, hobc.GCV_MODE["expansion"]) == 1
+    assert lib.hobc_plan_gcv_mode(None) == -1
+    assert lib.hobc_gcv_expansion_bound(None) == -1.0
+    assert lib.hobc_plan_set_host_chunks(None, 2) == 1
+    items = (hobc.BatchItem * 2)()
+    for it, n in zip(items, (32, 48)):
+        it.n[0], it.n[1], it.psf[0], it.psf[1], it.bc_degree = n, n, 5, 5, 2
+    cases = [("fp32", 7, (1e-8, 1.0), 1),                           # unknown mode: HOBC_ERR_ARG
+             ("fp64", hobc.GCV_MODE["expansion"], (1e-8, 1.0), 2),  # FP64: HOBC_ERR_UNSUPPORTED
+             ("fp32", hobc.GCV_MODE["expansion"], (1e-18, 1e12), 2)]  # 36 decades: bound > 1e-8
+    for prec, mode, (lo, hi), status in cases:
+        mus = np.geomspace(lo, hi, 16)
+        desc = hobc.BatchDesc(count=2, L=1, prec=hobc.PRECISION[prec], n_mu=16, gcv_mode=mode)
+        out = ctypes.c_void_p()
+        got = lib.hobc_batch_create(ctypes.byref(desc), items,
+                                    mus.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, ctypes.byref(out))
+        assert got == status, (prec, mode, lo, hi, got)
+        assert not out.value
