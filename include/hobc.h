@@ -358,7 +358,9 @@ typedef struct hobc_batch_s hobc_batch;
  * one) take the pass's work items -- (problem, block of lines) for the line
  * transforms, (problem, chunk) for the GCV scan, (problem, column) for the
  * eigenvalues -- from a device counter, costliest first; the counters are
- * zeroed at the head of each call.  With a non-NULL stream the whole launch
+ * zeroed at the head of each call.  With gcv_mode = HOBC_GCV_EXPANSION the GCV
+ * pass takes its (problem, chunk) items in a fixed round robin over its CTAs
+ * instead (the chunks cost the same), then one CTA per problem forms its curve.  With a non-NULL stream the whole launch
  * sequence is captured once into a CUDA graph that hobc_deblur_batched
  * replays; with the legacy NULL stream the kernels are launched directly.
  * Synchronous; allocates device memory. */
